@@ -1,0 +1,271 @@
+"""FP64 CPU oracle of the stochastic Lagrangian particle model (test infrastructure).
+
+Only the test-suite, the smoke check and the benchmark's CPU-baseline leg may import this
+package. The product library never imports, links or executes anything here, and this
+package imports nothing from the product library: the two share only the seeded input
+generators of ``lpm_inputs``.
+
+The arithmetic lives in ``lpm_oracle.c`` (plain C, double precision, plain loops); this
+module compiles it with gcc and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lpm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, -O2, no -ffast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OCfg(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("x0", C.c_double), ("y0", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
+        ("z_levels", C.POINTER(C.c_double)),
+        ("n_met_t", C.c_int), ("met_t0", C.c_double), ("met_dt", C.c_double),
+        ("uvwk", C.POINTER(C.c_float)), ("kh", C.POINTER(C.c_float)),
+        ("rain", C.POINTER(C.c_uint8)), ("wind_offset", C.POINTER(C.c_float)),
+        ("cx", C.c_int), ("cy", C.c_int), ("cz", C.c_int),
+        ("cx0", C.c_double), ("cy0", C.c_double), ("cz0", C.c_double),
+        ("cdx", C.c_double), ("cdy", C.c_double), ("cdz", C.c_double),
+        ("src_x", C.c_double), ("src_y", C.c_double), ("src_z", C.c_double),
+        ("dt", C.c_double), ("n_steps", C.c_int64), ("seed", C.c_uint64),
+        ("bin_every", C.c_int),
+        ("half_life_s", C.c_double), ("vd_dry", C.c_double), ("h_mix", C.c_double),
+        ("wet_lambda", C.c_double), ("kh_uniform", C.c_double),
+        ("reflect_ground", C.c_int), ("reflect_top", C.c_int), ("z_top", C.c_double),
+        ("lateral_exit", C.c_int), ("drift_correction", C.c_int),
+        ("n_particles", C.c_int64), ("q", C.POINTER(C.c_double)), ("n_q", C.c_int),
+        ("q_dt", C.c_double), ("first_step", C.c_int64), ("last_step", C.c_int64),
+        ("pid_offset", C.c_int64),
+        ("k_scale", C.c_double), ("bias_u", C.c_double), ("bias_v", C.c_double),
+    ]
+
+
+class OOut(C.Structure):
+    _fields_ = [
+        ("pos", C.POINTER(C.c_double)), ("status", C.POINTER(C.c_int32)),
+        ("release", C.POINTER(C.c_int64)), ("margin", C.POINTER(C.c_double)),
+        ("conc", C.POINTER(C.c_double)), ("conc_fixed", C.POINTER(C.c_int64)),
+        ("dep", C.POINTER(C.c_double)), ("dep_fixed", C.POINTER(C.c_int64)),
+        ("budget", C.POINTER(C.c_double)), ("counters", C.POINTER(C.c_int64)),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        u64p = C.POINTER(C.c_uint64)
+        u32p = C.POINTER(C.c_uint32)
+        L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.oracle_draw_many.argtypes = [C.c_uint64, u64p, u32p, C.c_uint32, C.c_int64, u32p]
+        L.oracle_normals_many.argtypes = [C.c_uint64, u64p, u32p, C.c_int64,
+                                          C.POINTER(C.c_double)]
+        L.oracle_uniform.argtypes = [C.c_uint32]
+        L.oracle_uniform.restype = C.c_double
+        L.oracle_interp_many.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_double), C.c_int64,
+                                         C.POINTER(C.c_double)]
+        L.oracle_release_many.argtypes = [C.c_int64, C.c_int64, C.c_int64,
+                                          C.POINTER(C.c_int64), C.c_int64,
+                                          C.POINTER(C.c_int64)]
+        L.oracle_release_count.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64]
+        L.oracle_release_count.restype = C.c_int64
+        L.oracle_total_mass.argtypes = [C.POINTER(OCfg)]
+        L.oracle_total_mass.restype = C.c_double
+        L.oracle_fixed_shift.argtypes = [C.c_double]
+        L.oracle_fixed_shift.restype = C.c_int
+        L.oracle_initial_mass.argtypes = [C.POINTER(OCfg), C.c_int64]
+        L.oracle_initial_mass.restype = C.c_double
+        L.oracle_threshold.argtypes = [C.c_double]
+        L.oracle_threshold.restype = C.c_uint32
+        L.oracle_run.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_int64), C.c_int64, C.c_int64,
+                                 C.POINTER(OOut)]
+        L.oracle_run.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray], ct):
+    if a is None:
+        return C.POINTER(ct)()
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class _Pinned:
+    """Keeps the numpy arrays referenced by an OCfg alive."""
+
+    def __init__(self):
+        self.keep = []
+
+    def arr(self, a, dtype):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self.keep.append(a)
+        return a
+
+
+def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
+              bias=(0.0, 0.0), src=None, q=None):
+    """Build the C record for one release of ``cfg`` (an ``lpm_inputs.LpmConfig``).
+    ``scenario`` selects a member of a batched ensemble (its source, release, global id
+    offset and wind offset). ``src``/``q`` override the source and emission series."""
+    pin = _Pinned()
+    o = OCfg()
+    for name in ("nx", "ny", "nz", "n_met_t", "cx", "cy", "cz", "bin_every",
+                 "reflect_ground", "reflect_top", "lateral_exit", "drift_correction"):
+        setattr(o, name, int(getattr(cfg, name)))
+    for name in ("x0", "y0", "dx", "dy", "met_t0", "met_dt", "cx0", "cy0", "cz0", "cdx",
+                 "cdy", "cdz", "src_x", "src_y", "src_z", "dt", "half_life_s", "vd_dry",
+                 "h_mix", "wet_lambda", "kh_uniform", "z_top"):
+        setattr(o, name, float(getattr(cfg, name)))
+    o.n_steps = int(cfg.n_steps)
+    o.seed = int(cfg.seed)
+    o.z_levels = _ptr(pin.arr(cfg.z_levels, np.float64), C.c_double)
+    o.uvwk = _ptr(pin.arr(cfg.uvwk, np.float32), C.c_float)
+    o.kh = _ptr(pin.arr(cfg.kh, np.float32), C.c_float)
+    o.rain = _ptr(pin.arr(cfg.rain, np.uint8), C.c_uint8)
+    rel = cfg.release
+    offset = 0
+    wind_offset = None
+    if scenario is not None:
+        sc = cfg.scenarios[scenario]
+        rel = sc.release
+        offset = int(sum(s.release.n_particles for s in cfg.scenarios[:scenario]))
+        o.src_x, o.src_y, o.src_z = sc.src_x, sc.src_y, sc.src_z
+        wind_offset = sc.wind_offset
+    if src is not None:
+        o.src_x, o.src_y, o.src_z = (float(v) for v in src)
+    o.wind_offset = _ptr(pin.arr(wind_offset, np.float32), C.c_float)
+    qa = pin.arr(rel.q if q is None else q, np.float64)
+    o.n_particles = int(rel.n_particles)
+    o.q = _ptr(qa, C.c_double)
+    o.n_q = int(qa.size)
+    o.q_dt = float(rel.q_dt)
+    o.first_step = int(rel.first_step)
+    o.last_step = int(rel.last_step)
+    o.pid_offset = offset
+    o.k_scale = float(k_scale)
+    o.bias_u, o.bias_v = float(bias[0]), float(bias[1])
+    o._pin = pin  # keep arrays alive with the record
+    return o
+
+
+# ------------------------------------------------------------------------------------
+# Thin wrappers
+# ------------------------------------------------------------------------------------
+def philox(key, ctr):
+    L = lib()
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    o = (C.c_uint32 * 4)()
+    L.oracle_philox4x32_10(k, c, o)
+    return [int(v) for v in o]
+
+
+def draws(seed: int, pid, step, stream: int = 0) -> np.ndarray:
+    pid = np.ascontiguousarray(pid, dtype=np.uint64)
+    step = np.ascontiguousarray(np.broadcast_to(step, pid.shape), dtype=np.uint32)
+    out = np.empty((pid.size, 4), dtype=np.uint32)
+    lib().oracle_draw_many(seed, _ptr(pid, C.c_uint64), _ptr(step, C.c_uint32), stream,
+                           pid.size, _ptr(out, C.c_uint32))
+    return out
+
+
+def normals(seed: int, pid, step) -> np.ndarray:
+    pid = np.ascontiguousarray(pid, dtype=np.uint64)
+    step = np.ascontiguousarray(np.broadcast_to(step, pid.shape), dtype=np.uint32)
+    out = np.empty((pid.size, 3), dtype=np.float64)
+    lib().oracle_normals_many(seed, _ptr(pid, C.c_uint64), _ptr(step, C.c_uint32), pid.size,
+                              _ptr(out, C.c_double))
+    return out
+
+
+def uniform(w: int) -> float:
+    return lib().oracle_uniform(int(w) & 0xFFFFFFFF)
+
+
+def interp(cfg, xyzt, **kw) -> np.ndarray:
+    """Weather at points [N][4] = (x, y, z, t) -> [N][6] = (u, v, w, K_z, K_h, dK_z/dz)."""
+    o = make_ocfg(cfg, **kw)
+    pts = np.ascontiguousarray(xyzt, dtype=np.float64).reshape(-1, 4)
+    out = np.empty((pts.shape[0], 6), dtype=np.float64)
+    lib().oracle_interp_many(C.byref(o), _ptr(pts, C.c_double), pts.shape[0],
+                             _ptr(out, C.c_double))
+    return out
+
+
+def release_steps(n: int, first: int, last: int, p) -> np.ndarray:
+    p = np.ascontiguousarray(p, dtype=np.int64)
+    out = np.empty_like(p)
+    lib().oracle_release_many(n, first, last, _ptr(p, C.c_int64), p.size, _ptr(out, C.c_int64))
+    return out
+
+
+def release_count(n: int, first: int, last: int, step: int) -> int:
+    return int(lib().oracle_release_count(n, first, last, step))
+
+
+def threshold(p: float) -> int:
+    return int(lib().oracle_threshold(float(p)))
+
+
+def fixed_shift(cfg, **kw) -> int:
+    o = make_ocfg(cfg, **kw)
+    return int(lib().oracle_fixed_shift(lib().oracle_total_mass(C.byref(o))))
+
+
+def total_mass(cfg, **kw) -> float:
+    o = make_ocfg(cfg, **kw)
+    return float(lib().oracle_total_mass(C.byref(o)))
+
+
+def run(cfg, sel=None, n_run: Optional[int] = None, **kw) -> dict:
+    """Run the oracle for steps [0, n_run) on the particles ``sel`` (local indices of the
+    release; None = all). Returns positions, status, release steps, decision margins,
+    the last concentration snapshot (FP64 and fixed point), the deposition grids, the
+    budget and the fixed-point counters."""
+    o = make_ocfg(cfg, **kw)
+    if n_run is None:
+        n_run = int(cfg.n_steps)
+    if sel is not None:
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        n = sel.size
+    else:
+        n = int(o.n_particles)
+    ncell = cfg.cx * cfg.cy * cfg.cz
+    out = dict(
+        pos=np.zeros((n, 3)), status=np.zeros(n, np.int32), release=np.zeros(n, np.int64),
+        margin=np.zeros(n), conc=np.zeros((cfg.cz, cfg.cy, cfg.cx)),
+        conc_fixed=np.zeros((cfg.cz, cfg.cy, cfg.cx), np.int64),
+        dep=np.zeros((2, cfg.cy, cfg.cx)), dep_fixed=np.zeros((2, cfg.cy, cfg.cx), np.int64),
+        budget=np.zeros(8), counters=np.zeros(6, np.int64))
+    oo = OOut(_ptr(out["pos"], C.c_double), _ptr(out["status"], C.c_int32),
+              _ptr(out["release"], C.c_int64), _ptr(out["margin"], C.c_double),
+              _ptr(out["conc"], C.c_double), _ptr(out["conc_fixed"], C.c_int64),
+              _ptr(out["dep"], C.c_double), _ptr(out["dep_fixed"], C.c_int64),
+              _ptr(out["budget"], C.c_double), _ptr(out["counters"], C.c_int64))
+    assert ncell == out["conc"].size
+    rc = lib().oracle_run(C.byref(o), _ptr(sel, C.c_int64), n, int(n_run), C.byref(oo))
+    if rc != 0:
+        raise ValueError(f"oracle_run rejected the configuration (code {rc})")
+    out["active_steps"] = int(out["counters"][4])
+    return out

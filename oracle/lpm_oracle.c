@@ -1,0 +1,582 @@
+/*
+ * lpm_oracle.c - FP64 CPU oracle of the stochastic Lagrangian particle model of
+ * Molnar, Szakaly, Meszaros, Lagzi, "Air pollution modelling using a graphics processing
+ * unit with CUDA" (arXiv:0912.3223).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test-suite, the smoke check and the benchmark's
+ * CPU-baseline leg load this file's library; the product path never links or calls it.
+ * It shares no code, header, table or constant generator with the CUDA library: the
+ * counter-based generator, the Box-Muller transform, the 4D interpolation, the particle
+ * step, the deposition tests, the binning and the adjoint are written out here again, in
+ * double precision, from their definitions, step by step in the order of the paper's
+ * main loop (Sec. 3.2 and Fig. 1): sample weather, compute K, move by wind, move by
+ * turbulent diffusion, test dry then wet deposition; every n-th step sum the decayed
+ * masses on a rectangular grid.
+ *
+ * Parity status of each function is stated at the function. Philox4x32-10 carries no
+ * published known-answer vector in this tree; it is pinned by statistical and structural
+ * properties only (see the philox comment).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_ACTIVE 0
+#define OR_UNRELEASED 1
+#define OR_DEP_DRY 2
+#define OR_DEP_WET 3
+#define OR_EXITED 4
+
+/* ---------------------------------------------------------------------------------
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2,
+ * 3", SC'11). A counter-based generator: a keyed bijection of a 128-bit counter. One
+ * round multiplies two of the four 32-bit words by the constants M0, M1 (full 64-bit
+ * products), swaps the roles of the words and mixes the high halves with the other two
+ * words and the round key; the key advances by the Weyl constants W0, W1 between rounds.
+ * It replaces the paper's Mersenne Twister (Sec. 2, Sec. 3.2) so that a realisation is
+ * a pure function of (seed, particle, step).
+ * Parity: pinned by properties (uniformity, avalanche, stream independence), no KAT.
+ * ------------------------------------------------------------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void oracle_philox4x32_10(const uint32_t key_in[2], const uint32_t ctr[4], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t prod0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* The draw for (seed, global particle id, step, stream): key = seed halves, counter =
+ * (id low, id high, step, stream). Stream 0: displacement normals; stream 1: deposition. */
+void oracle_draw(uint64_t seed, uint64_t pid, uint32_t step, uint32_t stream, uint32_t out[4])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)pid, (uint32_t)(pid >> 32), step, stream};
+    oracle_philox4x32_10(key, ctr, out);
+}
+
+/* Uniform on (0,1): the top 23 bits as the midpoint of one of 2^23 equal bins,
+ * u = (2*(w >> 9) + 1) * 2^-24 (exactly representable in FP32 and FP64). */
+double oracle_uniform(uint32_t w)
+{
+    return (double)(2u * (w >> 9) + 1u) * (1.0 / 16777216.0);
+}
+
+/* Basic (trigonometric) Box-Muller: two independent N(0,1) from two uniforms (Sec. 2,
+ * "Box-Muller transformation"). n0, n1 from (u0, u1); n2 from (u2, u3), its sine partner
+ * discarded. Parity: pinned by moments and a KS test against the normal CDF. */
+void oracle_normals(uint64_t seed, uint64_t pid, uint32_t step, double n[3])
+{
+    uint32_t w[4];
+    oracle_draw(seed, pid, step, 0u, w);
+    const double two_pi = 6.283185307179586476925286766559;
+    double u0 = oracle_uniform(w[0]), u1 = oracle_uniform(w[1]);
+    double u2 = oracle_uniform(w[2]), u3 = oracle_uniform(w[3]);
+    double r0 = sqrt(-2.0 * log(u0));
+    double r1 = sqrt(-2.0 * log(u2));
+    n[0] = r0 * cos(two_pi * u1);
+    n[1] = r0 * sin(two_pi * u1);
+    n[2] = r1 * cos(two_pi * u3);
+}
+
+/* ---------------------------------------------------------------------------------
+ * Configuration record (mirrors the C-ABI lpm_config plus the input arrays).
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+    int nx, ny, nz;
+    double x0, y0, dx, dy;
+    const double *z_levels;          /* [nz], ascending, z_levels[0] = 0 */
+    int n_met_t;
+    double met_t0, met_dt;
+    const float *uvwk;               /* [n_met_t][nz][ny][nx][4] (u, v, w, K_z) */
+    const float *kh;                 /* [n_met_t][nz][ny][nx] or NULL */
+    const uint8_t *rain;             /* [n_met_t][ny][nx] or NULL */
+    const float *wind_offset;        /* [n_met_t][2] domain-uniform (du, dv) or NULL */
+    int cx, cy, cz;
+    double cx0, cy0, cz0, cdx, cdy, cdz;
+    double src_x, src_y, src_z;
+    double dt;
+    int64_t n_steps;                 /* configured run length S (last step bins) */
+    uint64_t seed;
+    int bin_every;
+    double half_life_s, vd_dry, h_mix, wet_lambda, kh_uniform;
+    int reflect_ground, reflect_top;
+    double z_top;
+    int lateral_exit, drift_correction;
+    /* release */
+    int64_t n_particles;
+    const double *q;
+    int n_q;
+    double q_dt;
+    int64_t first_step, last_step;
+    int64_t pid_offset;              /* global id of this release's particle 0 */
+    /* differentiable parameters of the adjoint form: K scale and wind bias */
+    double k_scale, bias_u, bias_v;
+} ocfg;
+
+/* ---------------------------------------------------------------------------------
+ * Release schedule (Sec. 3.2: a priori assignment of masses from the emission profile
+ * and the particle budget). Particle p of N released over S steps starting at F leaves
+ * the source at step s_p = F + floor(p*S/N); step F+j releases
+ * n_j = ceil((j+1)N/S) - ceil(jN/S) particles, each of mass q(t)*dt/n_j.
+ * Parity: pinned by counting (sum n_j = N, max-min <= 1, agreement with a direct count).
+ * ------------------------------------------------------------------------------- */
+int64_t oracle_release_step(int64_t n, int64_t first, int64_t last, int64_t p)
+{
+    int64_t s = last - first;
+    return first + (p * s) / n;
+}
+
+int64_t oracle_release_count(int64_t n, int64_t first, int64_t last, int64_t step)
+{
+    int64_t s = last - first, j = step - first;
+    if (j < 0 || j >= s) return 0;
+    int64_t a = ((j + 1) * n + s - 1) / s;
+    int64_t b = (j * n + s - 1) / s;
+    return a - b;
+}
+
+static double emission_rate(const ocfg *c, int64_t step)
+{
+    double t = (double)step * c->dt;
+    int64_t idx = (int64_t)floor(t / c->q_dt);
+    if (idx < 0) idx = 0;
+    if (idx > c->n_q - 1) idx = c->n_q - 1;
+    return c->q[idx];
+}
+
+/* Initial mass of a particle released at step s. */
+double oracle_initial_mass(const ocfg *c, int64_t s)
+{
+    int64_t n = oracle_release_count(c->n_particles, c->first_step, c->last_step, s);
+    if (n <= 0) return 0.0;
+    return emission_rate(c, s) * c->dt / (double)n;
+}
+
+/* Total mass the release will emit (steps with no particle emit nothing). */
+double oracle_total_mass(const ocfg *c)
+{
+    double m = 0.0;
+    for (int64_t s = c->first_step; s < c->last_step; ++s) {
+        int64_t n = oracle_release_count(c->n_particles, c->first_step, c->last_step, s);
+        if (n > 0) m += emission_rate(c, s) * c->dt;
+    }
+    return m;
+}
+
+/* Fixed-point scale: masses are binned as round(m * 2^sigma) with the total released
+ * mass below 2^61 units, so no 64-bit counter can overflow. */
+int oracle_fixed_shift(double total_mass)
+{
+    int e = 0;
+    if (!(total_mass > 0.0)) return 0;
+    frexp(total_mass, &e);      /* total_mass < 2^e */
+    return 61 - e;
+}
+
+static double decay_rate(const ocfg *c)
+{
+    return c->half_life_s > 0.0 ? log(2.0) / c->half_life_s : 0.0;
+}
+
+/* Mass of a particle released at step s, at the end of step k (age (k+1-s)*dt):
+ * deterministic first-order decay from the half-life and the time since emission
+ * (Sec. 2 and Sec. 3.2). */
+double oracle_mass_at(const ocfg *c, int64_t s, int64_t k)
+{
+    double age = (double)(k + 1 - s) * c->dt;
+    return oracle_initial_mass(c, s) * exp(-decay_rate(c) * age);
+}
+
+/* ---------------------------------------------------------------------------------
+ * 4D linear interpolation of the weather in x, y, z and t (Sec. 3.2). x, y and t are
+ * uniform axes; z uses the stretched levels. The cell holding a coordinate is the one
+ * whose lower node is the last node <= the coordinate (ties go to the upper cell), the
+ * cell index is clamped to the grid and the fraction to [0, 1] (constant extension
+ * outside). The value is the plain 16-corner multilinear sum.
+ * Parity: pinned by exact reproduction of fields linear in x, y, z, t and of node values.
+ * ------------------------------------------------------------------------------- */
+static void axis_uniform(double coord, double c0, double d, int n, int *i, double *a)
+{
+    double f = (coord - c0) / d;
+    double fl = floor(f);
+    int ii;
+    if (fl < 0.0) ii = 0;
+    else if (fl > (double)(n - 2)) ii = n - 2;
+    else ii = (int)fl;
+    double aa = f - (double)ii;
+    if (aa < 0.0) aa = 0.0;
+    if (aa > 1.0) aa = 1.0;
+    *i = ii;
+    *a = aa;
+}
+
+static void axis_levels(double z, const double *lv, int nz, int *k, double *c)
+{
+    int kk = 0;
+    for (int m = 0; m < nz; ++m)
+        if (lv[m] <= z) kk = m;
+    if (kk > nz - 2) kk = nz - 2;
+    double cc = (z - lv[kk]) / (lv[kk + 1] - lv[kk]);
+    if (cc < 0.0) cc = 0.0;
+    if (cc > 1.0) cc = 1.0;
+    *k = kk;
+    *c = cc;
+}
+
+static void axis_time(const ocfg *c, double t, int *h0, int *h1, double *f)
+{
+    if (c->n_met_t < 2) {
+        *h0 = 0; *h1 = 0; *f = 0.0;
+        return;
+    }
+    int h;
+    axis_uniform(t, c->met_t0, c->met_dt, c->n_met_t, &h, f);
+    *h0 = h;
+    *h1 = h + 1;
+}
+
+/* Weather at (x, y, z, t): out = (u, v, w, K_z, K_h, dK_z/dz). K values clamped >= 0.
+ * dK_z/dz is the z-derivative of the multilinear K_z (0 outside the level range). */
+void oracle_interp(const ocfg *c, double x, double y, double z, double t, double out[6])
+{
+    int i, j, k, h0, h1;
+    double a, b, cz, f;
+    axis_uniform(x, c->x0, c->dx, c->nx, &i, &a);
+    axis_uniform(y, c->y0, c->dy, c->ny, &j, &b);
+    axis_levels(z, c->z_levels, c->nz, &k, &cz);
+    axis_time(c, t, &h0, &h1, &f);
+    double acc[4] = {0, 0, 0, 0}, kh = 0.0, kz_lo = 0.0, kz_hi = 0.0;
+    for (int dh = 0; dh < 2; ++dh) {
+        int h = dh ? h1 : h0;
+        double wt = dh ? f : 1.0 - f;
+        for (int dk = 0; dk < 2; ++dk) {
+            double wz = dk ? cz : 1.0 - cz;
+            for (int dj = 0; dj < 2; ++dj) {
+                double wy = dj ? b : 1.0 - b;
+                for (int di = 0; di < 2; ++di) {
+                    double wx = di ? a : 1.0 - a;
+                    size_t node = (((size_t)h * c->nz + (k + dk)) * c->ny + (j + dj)) * c->nx
+                                  + (i + di);
+                    const float *m = c->uvwk + 4 * node;
+                    double w = wt * wz * wy * wx;
+                    for (int q = 0; q < 4; ++q) acc[q] += w * (double)m[q];
+                    double wxyt = wt * wy * wx;
+                    if (dk) kz_hi += wxyt * (double)m[3];
+                    else kz_lo += wxyt * (double)m[3];
+                    if (c->kh) kh += w * (double)c->kh[node];
+                }
+            }
+        }
+    }
+    if (c->wind_offset) {
+        acc[0] += (1.0 - f) * (double)c->wind_offset[2 * h0] + f * (double)c->wind_offset[2 * h1];
+        acc[1] += (1.0 - f) * (double)c->wind_offset[2 * h0 + 1]
+                  + f * (double)c->wind_offset[2 * h1 + 1];
+    }
+    double dz = c->z_levels[k + 1] - c->z_levels[k];
+    int inside = z >= c->z_levels[0] && z <= c->z_levels[c->nz - 1];
+    out[0] = acc[0];
+    out[1] = acc[1];
+    out[2] = acc[2];
+    out[3] = acc[3] > 0.0 ? acc[3] : 0.0;
+    out[4] = c->kh ? (kh > 0.0 ? kh : 0.0) : (c->kh_uniform > 0.0 ? c->kh_uniform : 0.0);
+    out[5] = inside ? (kz_hi - kz_lo) / dz : 0.0;
+}
+
+/* Deposition thresholds: the probability of an event in one step, as a 32-bit integer
+ * threshold a uniform word is compared against (event iff word < T). */
+uint32_t oracle_threshold(double p)
+{
+    if (!(p > 0.0)) return 0u;
+    double t = floor(p * 4294967296.0);
+    if (t >= 4294967295.0) return 4294967295u;
+    return (uint32_t)t;
+}
+
+static double p_dry(const ocfg *c)
+{
+    /* well-mixed surface-flux scheme: removal at rate v_d / h_mix inside the mixing layer */
+    if (!(c->vd_dry > 0.0) || !(c->h_mix > 0.0)) return 0.0;
+    return 1.0 - exp(-c->vd_dry * c->dt / c->h_mix);
+}
+
+static double p_wet(const ocfg *c)
+{
+    if (!(c->wet_lambda > 0.0) || !c->rain) return 0.0;
+    return 1.0 - exp(-c->wet_lambda * c->dt);
+}
+
+/* ---------------------------------------------------------------------------------
+ * The simulation: the paper's main loop (Sec. 3.2, Fig. 1), step-major, particles in
+ * order. Outputs are per simulated particle and summed over the simulated particles.
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+    double *pos;          /* [n_sel][3] */
+    int32_t *status;      /* [n_sel] */
+    int64_t *release;     /* [n_sel] release step */
+    double *margin;       /* [n_sel] min distance to a decisive event boundary (m) */
+    double *conc;         /* [cz][cy][cx] mass per cell, exact FP64 sum (last snapshot) */
+    int64_t *conc_fixed;  /* [cz][cy][cx] fixed-point mass (last snapshot) */
+    double *dep;          /* [2][cy][cx] deposited mass (dry, wet), FP64 */
+    int64_t *dep_fixed;   /* [2][cy][cx] */
+    double *budget;       /* [8] released, air_in, air_out, dry, wet, exited, decayed, n_active */
+    int64_t *counters;    /* [6] fixed: bin_out, dep_out_dry, dep_out_wet, exited, steps, bins */
+} oout;
+
+static int64_t fixed_of(double m, int shift)
+{
+    return (int64_t)nearbyint(ldexp(m, shift));
+}
+
+/* Runs steps [0, n_run) for the particles listed in sel (local indices into the
+ * release; NULL = all). Returns 0 on success, nonzero on invalid input. */
+int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, const oout *o)
+{
+    if (c->nx < 2 || c->ny < 2 || c->nz < 2 || c->n_particles <= 0) return 1;
+    if (c->last_step <= c->first_step || c->dt <= 0.0 || c->bin_every <= 0) return 1;
+    int64_t n = sel ? n_sel : c->n_particles;
+    size_t ncell = (size_t)c->cx * c->cy * c->cz, ndep = (size_t)2 * c->cx * c->cy;
+    const int shift = oracle_fixed_shift(oracle_total_mass(c));
+    const double lam = decay_rate(c);
+    const uint32_t t_dry = oracle_threshold(p_dry(c));
+    const uint32_t t_wet = oracle_threshold(p_wet(c));
+    const double x_lo = c->x0, x_hi = c->x0 + (c->nx - 1) * c->dx;
+    const double y_lo = c->y0, y_hi = c->y0 + (c->ny - 1) * c->dy;
+
+    /* state */
+    double *P = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    int32_t *st = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *sp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *tev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    double *mg = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!P || !st || !sp || !tev || !mg) { free(P); free(st); free(sp); free(tev); free(mg); return 2; }
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t p = sel ? sel[q] : q;
+        sp[q] = oracle_release_step(c->n_particles, c->first_step, c->last_step, p);
+        st[q] = OR_UNRELEASED;
+        P[3 * q] = P[3 * q + 1] = P[3 * q + 2] = 0.0;
+        tev[q] = -1;
+        mg[q] = INFINITY;
+    }
+    memset(o->conc, 0, sizeof(double) * ncell);
+    memset(o->conc_fixed, 0, sizeof(int64_t) * ncell);
+    memset(o->dep, 0, sizeof(double) * ndep);
+    memset(o->dep_fixed, 0, sizeof(int64_t) * ndep);
+    for (int m = 0; m < 6; ++m) o->counters[m] = 0;
+    double dep_out[2] = {0.0, 0.0}, exited = 0.0, bin_out = 0.0;
+    int64_t steps = 0;
+
+    for (int64_t k = 0; k < n_run; ++k) {
+        const double t = (double)k * c->dt;
+        for (int64_t q = 0; q < n; ++q) {
+            int64_t p = sel ? sel[q] : q;
+            uint64_t gid = (uint64_t)(c->pid_offset + p);
+            double *X = P + 3 * q;
+            /* release at the source (Sec. 2: particles leave the point source each step) */
+            if (st[q] == OR_UNRELEASED && sp[q] == k) {
+                st[q] = OR_ACTIVE;
+                X[0] = c->src_x; X[1] = c->src_y; X[2] = c->src_z;
+            }
+            if (st[q] != OR_ACTIVE) continue;
+            ++steps;
+            /* 1. sample the weather at the old position and the step's start time */
+            double met[6];
+            oracle_interp(c, X[0], X[1], X[2], t, met);
+            /* 2. turbulent diffusion coefficients (K_h horizontal, K_z vertical) */
+            double kh = c->k_scale * met[4], kz = c->k_scale * met[3];
+            /* 3. N(0,1) draws for the three components */
+            double nrm[3];
+            oracle_normals(c->seed, gid, (uint32_t)k, nrm);
+            /* 4. Eq. (1)-(2): advection by the wind, then the random-walk displacement */
+            double u = met[0] + c->bias_u, v = met[1] + c->bias_v, w = met[2];
+            X[0] = X[0] + u * c->dt + nrm[0] * sqrt(2.0 * kh * c->dt);
+            X[1] = X[1] + v * c->dt + nrm[1] * sqrt(2.0 * kh * c->dt);
+            X[2] = X[2] + w * c->dt + nrm[2] * sqrt(2.0 * kz * c->dt);
+            if (c->drift_correction) X[2] += c->k_scale * met[5] * c->dt;
+            /* 5. reflection at the ground and the top, folded at most 4 times, then clamped */
+            for (int it = 0; it < 4; ++it) {
+                if (c->reflect_ground && X[2] < 0.0) X[2] = -X[2];
+                else if (c->reflect_top && X[2] > c->z_top) X[2] = 2.0 * c->z_top - X[2];
+                else break;
+            }
+            if (c->reflect_ground && X[2] < 0.0) X[2] = 0.0;
+            if (c->reflect_top && X[2] > c->z_top) X[2] = c->z_top;
+            /* leaving the horizontal domain inactivates the particle */
+            if (c->lateral_exit) {
+                double d = fmin(fmin(fabs(X[0] - x_lo), fabs(X[0] - x_hi)),
+                                fmin(fabs(X[1] - y_lo), fabs(X[1] - y_hi)));
+                if (d < mg[q]) mg[q] = d;
+                if (X[0] < x_lo || X[0] > x_hi || X[1] < y_lo || X[1] > y_hi) {
+                    st[q] = OR_EXITED;
+                    tev[q] = k;
+                    exited += oracle_mass_at(c, sp[q], k);
+                    o->counters[3] += fixed_of(oracle_mass_at(c, sp[q], k), shift);
+                    continue;
+                }
+            }
+            /* 6. stochastic dry deposition below the mixing height, then wet deposition
+             *    where it rains (Sec. 2); one uniform word per test */
+            if (t_dry || t_wet) {
+                uint32_t dw[4];
+                oracle_draw(c->seed, gid, (uint32_t)k, 1u, dw);
+                int kind = -1;
+                if (t_dry && dw[0] < t_dry) {
+                    double d = fabs(X[2] - c->h_mix);
+                    if (d < mg[q]) mg[q] = d;
+                    if (X[2] < c->h_mix) kind = 0;
+                }
+                if (kind < 0 && t_wet && dw[1] < t_wet) {
+                    double fx = (X[0] - c->x0) / c->dx + 0.5;
+                    double fy = (X[1] - c->y0) / c->dy + 0.5;
+                    double d = fmin(c->dx * fabs(fx - floor(fx + 0.5)),
+                                    c->dy * fabs(fy - floor(fy + 0.5)));
+                    if (d < mg[q]) mg[q] = d;
+                    int ir = (int)floor(fx), jr = (int)floor(fy);
+                    if (ir < 0) ir = 0;
+                    if (ir > c->nx - 1) ir = c->nx - 1;
+                    if (jr < 0) jr = 0;
+                    if (jr > c->ny - 1) jr = c->ny - 1;
+                    int hr = (int)floor((t - c->met_t0) / c->met_dt);
+                    if (hr < 0) hr = 0;
+                    if (hr > c->n_met_t - 1) hr = c->n_met_t - 1;
+                    if (c->rain[((size_t)hr * c->ny + jr) * c->nx + ir]) kind = 1;
+                }
+                if (kind >= 0) {
+                    st[q] = kind == 0 ? OR_DEP_DRY : OR_DEP_WET;
+                    tev[q] = k;
+                    double m = oracle_mass_at(c, sp[q], k);
+                    long ix = (long)floor((X[0] - c->cx0) / c->cdx);
+                    long iy = (long)floor((X[1] - c->cy0) / c->cdy);
+                    if (ix >= 0 && ix < c->cx && iy >= 0 && iy < c->cy) {
+                        size_t cell = ((size_t)kind * c->cy + iy) * c->cx + ix;
+                        o->dep[cell] += m;
+                        o->dep_fixed[cell] += fixed_of(m, shift);
+                    } else {
+                        dep_out[kind] += m;
+                        o->counters[1 + kind] += fixed_of(m, shift);
+                    }
+                }
+            }
+        }
+        /* every n-th step (and at the end of the run): sum decayed masses on the grid */
+        if ((k + 1) % c->bin_every == 0 || k == c->n_steps - 1) {
+            memset(o->conc, 0, sizeof(double) * ncell);
+            memset(o->conc_fixed, 0, sizeof(int64_t) * ncell);
+            bin_out = 0.0;
+            o->counters[0] = 0;
+            o->counters[5] += 1;
+            for (int64_t q = 0; q < n; ++q) {
+                if (st[q] != OR_ACTIVE) continue;
+                double *X = P + 3 * q;
+                double m = oracle_mass_at(c, sp[q], k);
+                long ix = (long)floor((X[0] - c->cx0) / c->cdx);
+                long iy = (long)floor((X[1] - c->cy0) / c->cdy);
+                long iz = (long)floor((X[2] - c->cz0) / c->cdz);
+                if (ix >= 0 && ix < c->cx && iy >= 0 && iy < c->cy && iz >= 0 && iz < c->cz) {
+                    size_t cell = ((size_t)iz * c->cy + iy) * c->cx + ix;
+                    o->conc[cell] += m;
+                    o->conc_fixed[cell] += fixed_of(m, shift);
+                } else {
+                    bin_out += m;
+                    o->counters[0] += fixed_of(m, shift);
+                }
+            }
+        }
+    }
+    o->counters[4] = steps;
+
+    /* budget at the current time t = n_run * dt */
+    double released = 0.0, air_in = 0.0, air_out = 0.0, dry = 0.0, wet = 0.0, decayed = 0.0;
+    int64_t n_active = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        if (st[q] == OR_UNRELEASED) continue;
+        double m0 = oracle_initial_mass(c, sp[q]);
+        released += m0;
+        int64_t kend = st[q] == OR_ACTIVE ? n_run - 1 : tev[q];
+        double m = m0 * exp(-lam * (double)(kend + 1 - sp[q]) * c->dt);
+        decayed += m0 - m;
+        double *X = P + 3 * q;
+        if (st[q] == OR_ACTIVE) {
+            ++n_active;
+            long ix = (long)floor((X[0] - c->cx0) / c->cdx);
+            long iy = (long)floor((X[1] - c->cy0) / c->cdy);
+            long iz = (long)floor((X[2] - c->cz0) / c->cdz);
+            if (ix >= 0 && ix < c->cx && iy >= 0 && iy < c->cy && iz >= 0 && iz < c->cz)
+                air_in += m;
+            else
+                air_out += m;
+        } else if (st[q] == OR_DEP_DRY) {
+            dry += m;
+        } else if (st[q] == OR_DEP_WET) {
+            wet += m;
+        }
+    }
+    o->budget[0] = released;
+    o->budget[1] = air_in;
+    o->budget[2] = air_out;
+    o->budget[3] = dry;
+    o->budget[4] = wet;
+    o->budget[5] = exited;
+    o->budget[6] = decayed;
+    o->budget[7] = (double)n_active;
+    (void)bin_out;
+    (void)dep_out;
+    for (int64_t q = 0; q < n; ++q) {
+        o->pos[3 * q] = P[3 * q];
+        o->pos[3 * q + 1] = P[3 * q + 1];
+        o->pos[3 * q + 2] = P[3 * q + 2];
+        o->status[q] = st[q];
+        o->release[q] = sp[q];
+        o->margin[q] = mg[q];
+    }
+    free(P); free(st); free(sp); free(tev); free(mg);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Batch helpers for the tests (plain loops over the single-item functions above).
+ * ------------------------------------------------------------------------------- */
+void oracle_draw_many(uint64_t seed, const uint64_t *pid, const uint32_t *step, uint32_t stream,
+                      int64_t n, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) oracle_draw(seed, pid[i], step[i], stream, out + 4 * i);
+}
+
+void oracle_normals_many(uint64_t seed, const uint64_t *pid, const uint32_t *step, int64_t n,
+                         double *out)
+{
+    for (int64_t i = 0; i < n; ++i) oracle_normals(seed, pid[i], step[i], out + 3 * i);
+}
+
+void oracle_interp_many(const ocfg *c, const double *xyzt, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        oracle_interp(c, xyzt[4 * i], xyzt[4 * i + 1], xyzt[4 * i + 2], xyzt[4 * i + 3],
+                      out + 6 * i);
+}
+
+void oracle_release_many(int64_t n, int64_t first, int64_t last, const int64_t *p, int64_t m,
+                         int64_t *out)
+{
+    for (int64_t i = 0; i < m; ++i) out[i] = oracle_release_step(n, first, last, p[i]);
+}
