@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the particle model on GB300.
+
+Workload (one bench "step" = one complete simulation on inputs resident in HBM): the
+realistic plain-method configuration: 1e7 particles released continuously from a point
+source over 24 h at dt = 30 s (2880 steps), hourly 200x200x30 weather (log profile plus
+seeded mesoscale modes, K_z profile), 8-day half-life, dry and wet deposition, lateral
+exit, hourly 400x400x20 concentration snapshots and a 400x400 deposition grid.
+Metric: ACTIVE particle-steps per second (a particle advanced one dt while airborne).
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead, on a
+bounded particle sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s on 1 GB300, % of roofline; batched & adjoint vs plain step"
+UNIT = "particle-steps/s"
+WORKLOAD = ("plain method, realistic: 1e7 particles, 24 h at dt=30 s (2880 steps), hourly "
+            "200x200x30 met, decay + dry/wet deposition + lateral exit, hourly 400x400x20 "
+            "snapshots")
+
+# Algorithmic 32-bit operations per active particle-step (FP32 + INT32 lane operations as
+# the method states them; transcendental = 1): Philox4x32-10 twice (displacement and
+# deposition streams) 2 x 98, uniforms 12, Box-Muller 11, 4D gather index and weight math
+# 30, 16-corner lerps of 4 components 120, move 18, reflection/exit 8, deposition test 4.
+OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
+SM_COUNT = 152
+LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
+SM_MAX_MHZ = 2070.0
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        loaded = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
+        out.update(sm_mhz=statistics.median(loaded) if loaded else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
+                   samples=len(rows))
+        return out
+
+
+# ------------------------------------------------------------------------------------
+# CPU baseline: the oracle on a deterministic particle sample of the same workload
+# ------------------------------------------------------------------------------------
+def oracle_sample(cfg, stride: int):
+    import numpy as np
+    import oracle
+    oracle.build()
+    sel = np.arange(0, cfg.n_particles, stride, dtype=np.int64)
+    t0 = time.perf_counter()
+    r = oracle.run(cfg, sel=sel)
+    dt = time.perf_counter() - t0
+    return r["active_steps"], dt, sel.size
+
+
+def cpu_baseline(cfg, stride: int = 100):
+    steps, dt, n = oracle_sample(cfg, stride)
+    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"every {stride}th particle ({n} particles) of the workload, all "
+                      f"{cfg.n_steps} steps: {steps} active particle-steps in {dt:.1f} s, "
+                      "FP64, single thread"}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    import lpm_inputs as li
+    cfg = li.make_cfg1()
+    stride = args.ref_stride
+    for _ in range(args.warmup):
+        oracle_sample(cfg, stride * 10)
+    tot_steps, tot_t, n = 0, 0.0, 0
+    for _ in range(args.steps):
+        s, dt, n = oracle_sample(cfg, stride)
+        tot_steps += s
+        tot_t += dt
+    value = tot_steps / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_stride": stride},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"every {stride}th particle ({n} particles), all steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim, lpm
+    from paper_0912_3223_gb300 import build as pkg_build
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    pkg_build.build()
+    lpm.load()
+
+    cfg = li.make_cfg1()
+    # weak scaling: each rank runs its own realisation (key seed + rank) of the workload
+    if world > 1:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, seed=cfg.seed + rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt))
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+
+    def one_run():
+        sim.reset()
+        sim.step(cfg.n_steps)
+
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+    lpm.lpm_stats(sim.ctx)
+    lpm.lpm_set_profiling(sim.ctx, True)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, active = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)                       # L2 flush between timed steps (256 MB > L2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        one_run()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        _, _, ctr, _ = sim.fixed_state()
+        active.append(int(ctr[4]))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches, adv_launches, adv_ms = lpm.lpm_stats(sim.ctx)
+    lpm.lpm_set_profiling(sim.ctx, False)
+    t_total = sum(times) / 1e3
+    psteps = sum(active)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p = torch.tensor([psteps], dtype=torch.float64, device="cuda")
+        dist.all_reduce(p)
+        t_total, psteps = float(t.item()), int(p.item())
+    value = psteps / t_total
+
+    # end to end through the C ABI with host buffers: met from pinned host memory in,
+    # snapshots, deposition and budget out, every step
+    pinned_uvwk = torch.from_numpy(cfg.uvwk).pin_memory()
+    pinned_rain = torch.from_numpy(cfg.rain).pin_memory()
+    conc = np.empty((cfg.cz, cfg.cy, cfg.cx))
+    h2d = pinned_uvwk.numel() * 4 + pinned_rain.numel()
+    d2h = conc.nbytes + 2 * cfg.cy * cfg.cx * 8 + 8 * 8
+    e2e_t, e2e_p = 0.0, 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for t in range(cfg.n_met_t):
+            lpm.lpm_set_met(sim.ctx, t, pinned_uvwk[t], None, pinned_rain[t])
+        one_run()
+        c = sim.concentration()
+        dry, wet = sim.deposition()
+        b = sim.budget()
+        e2e_t += time.perf_counter() - t0
+        _, _, ctr, _ = sim.fixed_state()
+        e2e_p += int(ctr[4])
+    e2e_value = e2e_p / e2e_t
+
+    peaks = read_peaks()
+    alu_peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # Tops/s
+    achieved = OPS_PER_PARTICLE_STEP * sum(active) / (adv_ms / 1e3) / 1e12 if adv_ms > 0 else None
+    roofline = {
+        "bound": "alu", "kernel": "advance_kernel",
+        "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+        "frac": achieved / alu_peak if achieved else None,
+        "traffic": None,
+        "peak_source": (f"derived: {SM_COUNT} SMs x {LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz "
+                        "(one 32-bit op per lane per clock)"),
+        "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
+        "advance_share_of_step": (adv_ms / 1e3) / (sum(times) / 1e3) if times else None,
+        "hbm_gbs_measured_peak": peaks.get("hbm_gbs"),
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": cfg.n_particles, "steps_per_run": cfg.n_steps,
+                   "dt_s": cfg.dt, "met": [cfg.n_met_t, cfg.nz, cfg.ny, cfg.nx],
+                   "launch": [args.block, args.ppt],
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "active_particle_steps_per_run": sum(active) // max(1, len(active)),
+                   "slot_steps_per_run": cfg.n_particles * cfg.n_steps},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, args.ref_stride)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--ppt", type=int, default=2)
+    ap.add_argument("--ref-stride", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

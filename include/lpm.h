@@ -1,0 +1,235 @@
+/*
+ * lpm.h - C ABI of the GB300 stochastic Lagrangian particle model.
+ *
+ * The method is the one of Molnar, Szakaly, Meszaros, Lagzi, "Air pollution modelling
+ * using a graphics processing unit with CUDA" (arXiv:0912.3223): particles released
+ * from a point source move by the interpolated wind plus a Gaussian random walk
+ * (Sec. 2, Eq. 1-2), decay with the time since emission, deposit stochastically (dry
+ * below the mixing height, wet where it rains), become inactive at the domain edge, and
+ * every n-th step their decayed masses are summed on a rectangular grid (Sec. 3.2).
+ *
+ * Conventions for every call:
+ *  - Every call returns an lpm_status; nothing throws or aborts across this boundary.
+ *    The text of the last failure is available from lpm_last_error().
+ *  - The caller owns every buffer it passes. The library copies inputs before
+ *    returning (or enqueues the copy on the context stream, see lpm_set_met) and keeps
+ *    no caller pointer. The library owns all device memory of a context until
+ *    lpm_destroy().
+ *  - Work is enqueued asynchronously on the CUDA stream given to lpm_create(). The
+ *    read-back calls (lpm_concentration, lpm_deposition, lpm_budget, lpm_particles,
+ *    lpm_fixed_state, lpm_sync) synchronise that stream and report device-side errors
+ *    (LPM_E_NUMERIC for a non-finite particle position).
+ *  - A context is used by one host thread at a time.
+ *  - Lengths are SI (m, s), masses are in the unit of the emission rate times seconds.
+ */
+#ifndef LPM_H
+#define LPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lpm_ctx lpm_ctx;
+
+typedef enum {
+    LPM_OK = 0,
+    LPM_E_INVALID = 1,   /* an argument or the configuration is invalid */
+    LPM_E_OOM = 2,       /* a device or host allocation failed */
+    LPM_E_CUDA = 3,      /* a CUDA runtime call failed */
+    LPM_E_STATE = 4,     /* the call is not allowed in the current state */
+    LPM_E_NUMERIC = 5,   /* a particle position became non-finite */
+    LPM_E_TIMEOUT = 6    /* a bounded device loop hit its iteration limit */
+} lpm_status;
+
+/* Particle status, bits 28..31 of the particle tag; bits 0..27 hold the release step. */
+enum {
+    LPM_ACTIVE = 0,
+    LPM_UNRELEASED = 1,
+    LPM_DEP_DRY = 2,
+    LPM_DEP_WET = 3,
+    LPM_EXITED = 4
+};
+
+/* Indices of lpm_budget()'s output (all masses at the context's current time). */
+enum {
+    LPM_B_RELEASED = 0,  /* initial mass of every particle released so far */
+    LPM_B_AIR_IN = 1,    /* decayed mass of active particles inside the concentration grid */
+    LPM_B_AIR_OUT = 2,   /* decayed mass of active particles outside it */
+    LPM_B_DRY = 3,       /* mass removed by dry deposition (at the deposition step) */
+    LPM_B_WET = 4,       /* mass removed by wet deposition */
+    LPM_B_EXITED = 5,    /* mass carried out of the lateral boundary */
+    LPM_B_DECAYED = 6,   /* released minus everything above: mass lost to decay */
+    LPM_B_N_ACTIVE = 7   /* number of active particles */
+};
+
+/*
+ * Configuration (Sec. 3.2: the weather grid, the isotope constants, the source and the
+ * output grid). Met nodes sit at x0 + i*dx, y0 + j*dy, z_levels[k] (stretched, the
+ * "nonlinear" vertical of Sec. 3.2) and times met_t0 + h*met_dt. The concentration
+ * grid has cx*cy*cz uniform cells starting at (cx0, cy0, cz0); the deposition grid
+ * uses its horizontal cells. Time step k runs from t_k = k*dt to t_{k+1}.
+ */
+typedef struct {
+    int nx, ny, nz;                 /* met nodes, each >= 2; nz <= 64 */
+    double x0, y0, dx, dy;
+    const double *z_levels;         /* [nz], strictly ascending, read during lpm_create */
+    int n_met_t;                    /* number of met time slabs, >= 1 */
+    double met_t0, met_dt;
+    int cx, cy, cz;                 /* concentration grid cells, each >= 1 */
+    double cx0, cy0, cz0, cdx, cdy, cdz;
+    double src_x, src_y, src_z;     /* point source of scenario 0 */
+    double dt;                      /* time step (s) > 0 */
+    int64_t n_steps;                /* run length S; the last step always bins */
+    uint64_t seed;                  /* key of the counter-based generator */
+    int bin_every;                  /* bin every n-th step (Sec. 3.2), >= 1 */
+    double half_life_s;             /* <= 0: no decay */
+    double vd_dry;                  /* dry deposition velocity (m/s); 0: off */
+    double h_mix;                   /* mixing-layer height (m) */
+    double wet_lambda;              /* wet scavenging coefficient (1/s); 0: off */
+    double kh_uniform;              /* horizontal K (m^2/s); < 0: gridded K_h field */
+    int reflect_ground, reflect_top;
+    double z_top;
+    int lateral_exit;               /* leaving [x0, x0+(nx-1)dx] x [y0, ...] inactivates */
+    int drift_correction;           /* 1: add (dK_z/dz) dt to z (not in Eq. 2) */
+    int n_scenarios;                /* 1: plain method; > 1: batched ensemble */
+    int64_t max_particles;          /* particle slots over all scenarios */
+} lpm_config;
+
+/* Creates a context on the current CUDA device and allocates its device memory.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream). On failure *out = NULL. */
+lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out);
+
+/* Frees the context and all its device memory (synchronises its stream). NULL is a no-op. */
+void lpm_destroy(lpm_ctx *ctx);
+
+/* Text of the last failure on this context (or of the last failed lpm_create when ctx
+ * is NULL). Valid until the next call on the context. */
+const char *lpm_last_error(const lpm_ctx *ctx);
+
+/*
+ * Weather slab t_index (time met_t0 + t_index*met_dt), Sec. 3.2 (weather sampled in x,
+ * y, z and time by linear interpolation).
+ *   uvwk: [nz][ny][nx][4] float = (u, v, w, K_z); required.
+ *   kh:   [nz][ny][nx] float K_h, required iff kh_uniform < 0, else must be NULL.
+ *   rain: [ny][nx] uint8, nonzero where it precipitates; NULL = no rain in this slab.
+ * on_device = 1: the pointers are device pointers (copied on the context stream, the
+ * caller keeps them valid until the stream reaches the copy); 0: host pointers (copied
+ * before the call returns).
+ */
+lpm_status lpm_set_met(lpm_ctx *ctx, int t_index, const float *uvwk, const float *kh,
+                       const uint8_t *rain, int on_device);
+
+/*
+ * Source and wind perturbation of a scenario (batched ensemble). (x, y, z): release
+ * point. wind_offset: NULL or host [n_met_t][2] float (du, dv), a domain-uniform wind
+ * offset interpolated in time like the met; copied. Scenario 0 defaults to the config's
+ * source and no offset.
+ */
+lpm_status lpm_set_source(lpm_ctx *ctx, int scenario, double x, double y, double z,
+                          const float *wind_offset);
+
+/*
+ * Continuous release of a scenario (Sec. 3.2: masses are assigned a priori from the
+ * emission profile and the particle budget): n_particles particles over steps
+ * [first_step, last_step); particle p leaves at step first + floor(p*S/N)
+ * (S = last - first) and carries q(h)*dt/n_s, with h = floor(t/q_dt) clamped to
+ * [0, n_q-1] and n_s the number of particles leaving at that step. q: host [n_q] rates
+ * (mass/s), copied. Scenarios are released once each, in order 0, 1, ..., before the
+ * first lpm_step; their particles take consecutive global ids (the generator's key).
+ */
+lpm_status lpm_release(lpm_ctx *ctx, int scenario, int64_t n_particles, const double *q,
+                       int n_q, double q_dt, int64_t first_step, int64_t last_step);
+
+/*
+ * Part of a release held by this context (particle-range partitioning across contexts
+ * or GPUs): of a release of n_total particles whose particle 0 has global id id_base,
+ * this context holds particles [first_particle, first_particle + count). Release steps,
+ * masses and the fixed-point scale are those of the whole release, so the integer grids
+ * of disjoint ranges add up exactly to the grid of the whole release. lpm_release(...)
+ * is lpm_release_range(..., n, 0, n, ..., id_base = sum of earlier releases' n_total).
+ * Particles hold their state independently (Sec. 4.2: particles never interact).
+ */
+lpm_status lpm_release_range(lpm_ctx *ctx, int scenario, int64_t n_total, int64_t first_particle,
+                             int64_t count, const double *q, int n_q, double q_dt,
+                             int64_t first_step, int64_t last_step, int64_t id_base);
+
+/* Restarts the run at step 0 with the same weather, sources and releases: particles back
+ * at their sources (UNRELEASED), grids, deposition, counters and the error word zeroed.
+ * Asynchronous. */
+lpm_status lpm_reset(lpm_ctx *ctx);
+
+/*
+ * Advances every scenario by n steps (Sec. 3.2 main loop; Eq. 1-2): weather sampled at
+ * the old position and t_k, displacement u*dt + N(0,1)*sqrt(2*K*dt) per axis,
+ * reflection at the ground/top, lateral exit, dry then wet deposition test, and at the
+ * end of every bin_every-th step (and of step n_steps-1) the concentration snapshot.
+ * Asynchronous. Fails with LPM_E_STATE if a needed met slab is missing, a scenario was
+ * not released, or the run would pass n_steps.
+ */
+lpm_status lpm_step(lpm_ctx *ctx, int64_t n);
+
+/* Current step index k (number of steps taken). */
+lpm_status lpm_current_step(const lpm_ctx *ctx, int64_t *k);
+
+/* Last concentration snapshot of a scenario as mass per m^3, [cz][cy][cx] doubles into
+ * the caller's host buffer of n_out = cz*cy*cx elements. Synchronises. */
+lpm_status lpm_concentration(lpm_ctx *ctx, int scenario, double *out, size_t n_out);
+
+/* Accumulated dry and wet deposition of a scenario as mass per m^2, [cy][cx] doubles
+ * each (n_out = cy*cx). Either pointer may be NULL. Synchronises. */
+lpm_status lpm_deposition(lpm_ctx *ctx, int scenario, double *dry, double *wet, size_t n_out);
+
+/* Mass budget of a scenario at the current time, out[8] indexed by LPM_B_*.
+ * released - decayed = air_in + air_out + dry + wet + exited. Synchronises. */
+lpm_status lpm_budget(lpm_ctx *ctx, int scenario, double out[8]);
+
+/* Particle slots [first, first+count) (global ids) to host: xyz [count][3] float and
+ * tag [count] (status << 28 | release step); either may be NULL. Synchronises. */
+lpm_status lpm_particles(lpm_ctx *ctx, int64_t first, int64_t count, float *xyz,
+                         uint32_t *tag);
+
+/*
+ * Raw fixed-point state of a scenario for exact checks. Masses are binned as
+ * round(m * 2^shift) into 64-bit integers (shift from the scenario's total released
+ * mass, below 2^61 units). conc: [cz][cy][cx], dep: [2][cy][cx] (either NULL);
+ * counters[16] (may be NULL) = { bin_out, dep_out_dry, dep_out_wet, exited,
+ * active_steps, n_bins, air_in, air_out, n_active, dep_total_dry, dep_total_wet,
+ * 0, 0, 0, 0, 0 }, air_* and n_active as of the last lpm_budget. *shift may be NULL.
+ */
+lpm_status lpm_fixed_state(lpm_ctx *ctx, int scenario, uint64_t *conc, size_t n_conc,
+                           uint64_t *dep, size_t n_dep, int64_t counters[16], int *shift);
+
+/* Launch shape of the particle kernels: threads per block (128, 256 or 512) and
+ * particles per thread (1, 2, 4 or 8). Default 256 x 2. Results do not depend on it. */
+lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread);
+
+/* Synchronises the context stream and reports device-side errors. */
+lpm_status lpm_sync(lpm_ctx *ctx);
+
+/* Instrumentation (no counterpart in the paper). With profiling on, every advance
+ * launch is bracketed by CUDA events on the context stream. lpm_stats returns, since
+ * the previous lpm_stats call, the number of kernels the context launched, how many of
+ * them were advance launches, and their summed device time in ms (0 unless profiling
+ * was on); it synchronises the stream and resets the tallies. Pointers may be NULL. */
+lpm_status lpm_set_profiling(lpm_ctx *ctx, int on);
+lpm_status lpm_stats(lpm_ctx *ctx, int64_t *launches, int64_t *advance_launches,
+                     double *advance_ms);
+
+/*
+ * The counter-based draws the step consumes (replacing the Mersenne Twister + Box-Muller
+ * of Sec. 2): for each i < n, words[4i..4i+3] = Philox4x32-10(key = seed, counter =
+ * (pid[i] low, pid[i] high, step[i], stream)) and normals[3i..3i+2] = the three N(0,1)
+ * the step derives from them (stream 0). Host buffers, caller-owned; synchronous on the
+ * legacy default stream; allocates temporary device memory. Errors: lpm_last_error(NULL).
+ */
+lpm_status lpm_draws(uint64_t seed, const uint64_t *pid, const uint32_t *step, uint32_t stream,
+                     int64_t n, uint32_t *words, float *normals);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPM_H */

@@ -1,0 +1,877 @@
+// lpm_api.cu - the C ABI (include/lpm.h): context, inputs, stepping, read-backs.
+//
+// Host-side bookkeeping only: validation, device allocations, the release tables
+// (initial mass per release step, fixed-point scale) and the segmentation of a run at
+// the binning steps. Every arithmetic step of the particle method runs in the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "../../include/lpm.h"
+#include "lpm_launch.h"
+
+using namespace lpm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct ScenHost {
+    bool released = false;
+    double src_x = 0, src_y = 0, src_z = 0;
+    long long first_slot = 0;        // state slot of the held range's first particle
+    long long n = 0;                 // particles held by this context
+    long long n_total = 0;           // particles of the whole release
+    long long part_first = 0;        // index of the held range's first particle
+    long long id_base = 0;           // global id of the release's particle 0
+    long long rel_first = 0, rel_last = 0;
+    std::vector<double> q;
+    double q_dt = 3600.0;
+    int shift = 0;
+    double total_mass = 0.0;
+    std::vector<double> m0;          // per release step (FP64, host)
+    std::vector<float> wind_offset;  // [n_met_t][2] or empty
+};
+
+}  // namespace
+
+struct lpm_ctx {
+    lpm_config cfg{};
+    std::vector<double> zlev;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+
+    // weather
+    float4 *d_uvwk = nullptr;
+    float *d_kh = nullptr;
+    uint8_t *d_rain = nullptr;
+    std::vector<char> met_set;
+    bool any_rain = false;
+
+    // particles and outputs
+    float4 *d_state = nullptr;
+    unsigned long long *d_conc = nullptr;   // [n_scen][cz*cy*cx]
+    unsigned long long *d_dep = nullptr;    // [n_scen][2*cy*cx]
+    unsigned long long *d_ctr = nullptr;    // [n_scen][N_COUNTERS]
+    unsigned int *d_err = nullptr;
+    unsigned int *d_queue = nullptr;
+    float *d_m0 = nullptr;
+    size_t d_m0_cap = 0;
+    ScenDev *d_scen = nullptr;
+    float2 *d_woff = nullptr;               // [n_scen][n_met_t]
+    Tile *d_tiles = nullptr;
+    size_t d_tiles_cap = 0;
+
+    std::vector<ScenHost> scen;
+    int n_released = 0;
+    long long n_slots_used = 0;
+    long long n_ids_used = 0;               // next global id for lpm_release
+    bool profiling = false;
+    long long n_launches = 0;               // kernels launched by this context
+    long long n_adv_launches = 0;
+    double adv_ms = 0.0;                    // device time of advance launches (profiling)
+    std::vector<cudaEvent_t> ev_pool;       // profiling events, reused
+    size_t ev_used = 0;
+    bool tables_dirty = true;
+    long long k = 0;                        // steps taken
+    long long n_bins = 0;                   // snapshots taken
+    int block = 256, ppt = 2;
+
+    // batched tile schedule
+    std::vector<Tile> tiles;
+    int tiles_for_k1 = -1;
+    int tiles_block = 0, tiles_ppt = 0;
+
+    size_t ncell() const { return (size_t)cfg.cx * cfg.cy * cfg.cz; }
+    size_t ndep() const { return (size_t)2 * cfg.cx * cfg.cy; }
+};
+
+namespace {
+
+lpm_status fail(lpm_ctx *c, lpm_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+
+lpm_status fail(lpm_ctx *c, lpm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+#define LPM_CUDA(c, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA,     \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+    } while (0)
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+lpm_status validate(const lpm_config *c)
+{
+    if (!c) return fail(nullptr, LPM_E_INVALID, "config is NULL");
+    if (c->nx < 2 || c->ny < 2 || c->nz < 2)
+        return fail(nullptr, LPM_E_INVALID, "met grid needs at least 2 nodes per axis");
+    if (c->nz > MAX_LEVELS)
+        return fail(nullptr, LPM_E_INVALID, "nz=%d exceeds %d levels", c->nz, MAX_LEVELS);
+    if (!c->z_levels) return fail(nullptr, LPM_E_INVALID, "z_levels is NULL");
+    for (int k = 0; k < c->nz; ++k) {
+        if (!is_finite(c->z_levels[k])) return fail(nullptr, LPM_E_INVALID, "z_levels not finite");
+        if (k && !(c->z_levels[k] > c->z_levels[k - 1]))
+            return fail(nullptr, LPM_E_INVALID, "z_levels must be strictly ascending");
+    }
+    if (!(c->dx > 0) || !(c->dy > 0) || !is_finite(c->x0) || !is_finite(c->y0))
+        return fail(nullptr, LPM_E_INVALID, "met spacing must be > 0");
+    if (c->n_met_t < 1 || !(c->met_dt > 0) || !is_finite(c->met_t0))
+        return fail(nullptr, LPM_E_INVALID, "need n_met_t >= 1 and met_dt > 0");
+    if (c->cx < 1 || c->cy < 1 || c->cz < 1 || !(c->cdx > 0) || !(c->cdy > 0) || !(c->cdz > 0))
+        return fail(nullptr, LPM_E_INVALID, "concentration grid must be non-empty");
+    if ((double)c->cx * c->cy * c->cz > 2147483647.0)
+        return fail(nullptr, LPM_E_INVALID, "concentration grid exceeds 2^31 cells");
+    if (!(c->dt > 0) || !is_finite(c->dt)) return fail(nullptr, LPM_E_INVALID, "dt must be > 0");
+    if (c->n_steps < 1 || c->n_steps > (int64_t)TAG_STEP)
+        return fail(nullptr, LPM_E_INVALID, "n_steps must be in [1, 2^28)");
+    if (c->bin_every < 1) return fail(nullptr, LPM_E_INVALID, "bin_every must be >= 1");
+    if (c->vd_dry < 0 || c->wet_lambda < 0 || !is_finite(c->vd_dry) || !is_finite(c->wet_lambda))
+        return fail(nullptr, LPM_E_INVALID, "deposition parameters must be >= 0");
+    if (c->vd_dry > 0 && !(c->h_mix > 0))
+        return fail(nullptr, LPM_E_INVALID, "dry deposition needs h_mix > 0");
+    if (c->reflect_top && !(c->z_top > 0))
+        return fail(nullptr, LPM_E_INVALID, "top reflection needs z_top > 0");
+    if (c->n_scenarios < 1) return fail(nullptr, LPM_E_INVALID, "n_scenarios must be >= 1");
+    if (c->max_particles < 1) return fail(nullptr, LPM_E_INVALID, "max_particles must be >= 1");
+    return LPM_OK;
+}
+
+// Probability of an event per step as a 32-bit threshold (event iff word < T).
+unsigned int threshold(double p)
+{
+    if (!(p > 0.0)) return 0u;
+    const double t = std::floor(p * 4294967296.0);
+    if (t >= 4294967295.0) return 4294967295u;
+    return (unsigned int)t;
+}
+
+float pow2f(int e) { return std::ldexp(1.0f, e); }
+
+void fill_params(const lpm_ctx *c, StepParams &P)
+{
+    const lpm_config &g = c->cfg;
+    std::memset(&P, 0, sizeof P);
+    P.uvwk = c->d_uvwk;
+    P.kh = c->d_kh;
+    P.rain = c->any_rain ? c->d_rain : nullptr;
+    P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.n_t = g.n_met_t;
+    P.slab = (long long)g.nx * g.ny * g.nz;
+    P.x0 = (float)g.x0; P.y0 = (float)g.y0;
+    P.dx = (float)g.dx; P.dy = (float)g.dy;
+    P.inv_dx = (float)(1.0 / g.dx); P.inv_dy = (float)(1.0 / g.dy);
+    P.met_t0 = (float)g.met_t0; P.met_dt = (float)g.met_dt;
+    P.x_lo = (float)g.x0; P.x_hi = (float)(g.x0 + (g.nx - 1) * g.dx);
+    P.y_lo = (float)g.y0; P.y_hi = (float)(g.y0 + (g.ny - 1) * g.dy);
+    for (int k = 0; k < g.nz; ++k) P.zlev[k] = (float)c->zlev[k];
+    P.dt = (float)g.dt;
+    P.kh_uniform = (float)g.kh_uniform;
+    P.k_scale = 1.0f;
+    P.bias_u = P.bias_v = 0.0f;
+    P.lambda = g.half_life_s > 0 ? (float)(std::log(2.0) / g.half_life_s) : 0.0f;
+    P.h_mix = (float)g.h_mix;
+    P.z_top = (float)g.z_top;
+    P.seed_lo = (unsigned int)(g.seed & 0xffffffffu);
+    P.seed_hi = (unsigned int)(g.seed >> 32);
+    const double p_dry = (g.vd_dry > 0 && g.h_mix > 0) ? 1.0 - std::exp(-g.vd_dry * g.dt / g.h_mix) : 0.0;
+    const double p_wet = (g.wet_lambda > 0 && c->any_rain) ? 1.0 - std::exp(-g.wet_lambda * g.dt) : 0.0;
+    P.t_dry = threshold(p_dry);
+    P.t_wet = threshold(p_wet);
+    P.reflect_ground = g.reflect_ground;
+    P.reflect_top = g.reflect_top;
+    P.lateral_exit = g.lateral_exit;
+    P.drift = g.drift_correction;
+    P.cx = g.cx; P.cy = g.cy; P.cz = g.cz;
+    P.cx0 = (float)g.cx0; P.cy0 = (float)g.cy0; P.cz0 = (float)g.cz0;
+    P.inv_cdx = (float)(1.0 / g.cdx); P.inv_cdy = (float)(1.0 / g.cdy);
+    P.inv_cdz = (float)(1.0 / g.cdz);
+    P.m0 = c->d_m0;
+    P.scen = c->d_scen;
+    P.err = c->d_err;
+}
+
+double emission_rate(const ScenHost &s, double dt, long long step)
+{
+    long long idx = (long long)std::floor((double)step * dt / s.q_dt);
+    idx = std::max(0LL, std::min(idx, (long long)s.q.size() - 1));
+    return s.q[(size_t)idx];
+}
+
+long long release_count(long long n, long long first, long long last, long long step)
+{
+    const long long S = last - first, j = step - first;
+    if (j < 0 || j >= S) return 0;
+    return ((j + 1) * n + S - 1) / S - (j * n + S - 1) / S;
+}
+
+lpm_status upload_tables(lpm_ctx *c)
+{
+    if (!c->tables_dirty) return LPM_OK;
+    std::vector<float> m0;
+    std::vector<ScenDev> sd(c->scen.size());
+    const size_t nt = (size_t)c->cfg.n_met_t;
+    std::vector<float2> woff(c->scen.size() * nt, make_float2(0.f, 0.f));
+    for (size_t s = 0; s < c->scen.size(); ++s) {
+        const ScenHost &h = c->scen[s];
+        ScenDev &d = sd[s];
+        std::memset(&d, 0, sizeof d);
+        d.src_x = (float)h.src_x; d.src_y = (float)h.src_y; d.src_z = (float)h.src_z;
+        d.scale = pow2f(h.shift);
+        d.first_slot = h.first_slot;
+        d.n = h.n;
+        d.id0 = h.id_base + h.part_first;
+        d.rel_first = (int)h.rel_first;
+        d.rel_last = (int)h.rel_last;
+        d.m0_off = (int)m0.size();
+        for (double v : h.m0) m0.push_back((float)v);
+        if (!h.wind_offset.empty()) {
+            for (size_t t = 0; t < nt; ++t)
+                woff[s * nt + t] = make_float2(h.wind_offset[2 * t], h.wind_offset[2 * t + 1]);
+            d.wind_offset = c->d_woff + s * nt;
+        }
+        d.conc = c->d_conc + s * c->ncell();
+        d.dep = c->d_dep + s * c->ndep();
+        d.ctr = c->d_ctr + s * N_COUNTERS;
+    }
+    if (m0.empty()) m0.push_back(0.f);
+    if (m0.size() > c->d_m0_cap) {
+        if (c->d_m0) cudaFree(c->d_m0);
+        c->d_m0 = nullptr;
+        LPM_CUDA(c, cudaMalloc(&c->d_m0, m0.size() * sizeof(float)));
+        c->d_m0_cap = m0.size();
+    }
+    // the stream may still read the old tables: order the copies on it
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    LPM_CUDA(c, cudaMemcpy(c->d_m0, m0.data(), m0.size() * sizeof(float), cudaMemcpyHostToDevice));
+    LPM_CUDA(c, cudaMemcpy(c->d_scen, sd.data(), sd.size() * sizeof(ScenDev), cudaMemcpyHostToDevice));
+    LPM_CUDA(c, cudaMemcpy(c->d_woff, woff.data(), woff.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    c->tables_dirty = false;
+    return LPM_OK;
+}
+
+lpm_status check_device_error(lpm_ctx *c)
+{
+    unsigned int e = 0;
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    LPM_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e & ERR_NAN) return fail(c, LPM_E_NUMERIC, "a particle position became non-finite");
+    if (e & ERR_INDEX) return fail(c, LPM_E_CUDA, "a grid index fell outside its array");
+    if (e & ERR_TIMEOUT) return fail(c, LPM_E_TIMEOUT, "a bounded device loop hit its limit");
+    return LPM_OK;
+}
+
+// Particles of a scenario's held range that leave before step k1.
+long long released_before(const ScenHost &h, long long k1)
+{
+    const long long S = h.rel_last - h.rel_first;
+    long long upto;                  // particles p < upto of the whole release
+    if (k1 <= h.rel_first) upto = 0;
+    else if (k1 >= h.rel_last) upto = h.n_total;
+    else upto = ((k1 - h.rel_first) * h.n_total + S - 1) / S;
+    return std::max(0LL, std::min(upto - h.part_first, h.n));
+}
+
+// Batched schedule: tiles of BLOCK*PPT particles of one scenario, only particles released
+// before k1, longest-running (earliest released) first.
+lpm_status build_tiles(lpm_ctx *c, long long k1)
+{
+    const int T = c->block * c->ppt;
+    std::vector<std::pair<long long, Tile>> items;
+    for (size_t s = 0; s < c->scen.size(); ++s) {
+        const ScenHost &h = c->scen[s];
+        const long long S = h.rel_last - h.rel_first;
+        const long long n_rel = released_before(h, k1);
+        for (long long p = 0; p < n_rel; p += T) {
+            Tile t;
+            t.scen = (int)s;
+            t.first = h.first_slot + p;
+            t.count = (int)std::min<long long>(T, n_rel - p);
+            const long long sp = h.rel_first + ((h.part_first + p) * S) / h.n_total;
+            items.push_back({sp, t});
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const auto &a, const auto &b) { return a.first < b.first; });
+    c->tiles.clear();
+    for (auto &it : items) c->tiles.push_back(it.second);
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->tiles.size() > c->d_tiles_cap) {
+        if (c->d_tiles) cudaFree(c->d_tiles);
+        c->d_tiles = nullptr;
+        LPM_CUDA(c, cudaMalloc(&c->d_tiles, std::max<size_t>(1, c->tiles.size()) * sizeof(Tile)));
+        c->d_tiles_cap = c->tiles.size();
+    }
+    if (!c->tiles.empty())
+        LPM_CUDA(c, cudaMemcpy(c->d_tiles, c->tiles.data(), c->tiles.size() * sizeof(Tile),
+                               cudaMemcpyHostToDevice));
+    return LPM_OK;
+}
+
+lpm_status relaunch_releases(lpm_ctx *c)
+{
+    for (const ScenHost &h : c->scen) {
+        if (!h.released) continue;
+        LPM_CUDA(c, launch_release(c->stream, c->d_state, h.first_slot, h.n, h.part_first,
+                                   h.n_total, (int)h.rel_first, (int)(h.rel_last - h.rel_first),
+                                   (float)h.src_x, (float)h.src_y, (float)h.src_z));
+        c->n_launches++;
+    }
+    return LPM_OK;
+}
+
+cudaEvent_t next_event(lpm_ctx *c)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// Adds the elapsed time of recorded (start, stop) pairs to adv_ms (synchronises).
+lpm_status collect_events(lpm_ctx *c)
+{
+    if (c->ev_used == 0) return LPM_OK;
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        float ms = 0.f;
+        LPM_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]));
+        c->adv_ms += ms;
+    }
+    c->ev_used = 0;
+    return LPM_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
+{
+    if (!out) return fail(nullptr, LPM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    lpm_status st = validate(cfg);
+    if (st != LPM_OK) return st;
+    lpm_ctx *c = new (std::nothrow) lpm_ctx();
+    if (!c) return fail(nullptr, LPM_E_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->zlev.assign(cfg->z_levels, cfg->z_levels + cfg->nz);
+    c->cfg.z_levels = nullptr;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->met_set.assign((size_t)cfg->n_met_t, 0);
+    c->scen.resize((size_t)cfg->n_scenarios);
+    c->scen[0].src_x = cfg->src_x;
+    c->scen[0].src_y = cfg->src_y;
+    c->scen[0].src_z = cfg->src_z;
+    auto bail = [&](lpm_status s) {
+        g_create_error = c->err;
+        lpm_destroy(c);
+        return s;
+    };
+#define CREATE_CUDA(call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            fail(c, e_ == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA, "%s: %s",   \
+                 #call, cudaGetErrorString(e_));                                           \
+            return bail(e_ == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA);         \
+        }                                                                                  \
+    } while (0)
+    CREATE_CUDA(cudaGetDevice(&c->device));
+    CREATE_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+    const size_t nodes = (size_t)cfg->nx * cfg->ny * cfg->nz;
+    const size_t ns = (size_t)cfg->n_scenarios;
+    CREATE_CUDA(cudaMalloc(&c->d_uvwk, nodes * cfg->n_met_t * sizeof(float4)));
+    if (cfg->kh_uniform < 0)
+        CREATE_CUDA(cudaMalloc(&c->d_kh, nodes * cfg->n_met_t * sizeof(float)));
+    CREATE_CUDA(cudaMalloc(&c->d_rain, (size_t)cfg->nx * cfg->ny * cfg->n_met_t));
+    CREATE_CUDA(cudaMemsetAsync(c->d_rain, 0, (size_t)cfg->nx * cfg->ny * cfg->n_met_t, c->stream));
+    CREATE_CUDA(cudaMalloc(&c->d_state, (size_t)cfg->max_particles * sizeof(float4)));
+    CREATE_CUDA(cudaMalloc(&c->d_conc, ns * c->ncell() * sizeof(unsigned long long)));
+    CREATE_CUDA(cudaMalloc(&c->d_dep, ns * c->ndep() * sizeof(unsigned long long)));
+    CREATE_CUDA(cudaMalloc(&c->d_ctr, ns * N_COUNTERS * sizeof(unsigned long long)));
+    CREATE_CUDA(cudaMalloc(&c->d_err, sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&c->d_queue, sizeof(unsigned int)));
+    CREATE_CUDA(cudaMalloc(&c->d_scen, ns * sizeof(ScenDev)));
+    CREATE_CUDA(cudaMalloc(&c->d_woff, ns * cfg->n_met_t * sizeof(float2)));
+    CREATE_CUDA(cudaMemsetAsync(c->d_conc, 0, ns * c->ncell() * sizeof(unsigned long long), c->stream));
+    CREATE_CUDA(cudaMemsetAsync(c->d_dep, 0, ns * c->ndep() * sizeof(unsigned long long), c->stream));
+    CREATE_CUDA(cudaMemsetAsync(c->d_ctr, 0, ns * N_COUNTERS * sizeof(unsigned long long), c->stream));
+    CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
+    CREATE_CUDA(cudaStreamSynchronize(c->stream));
+#undef CREATE_CUDA
+    *out = c;
+    return LPM_OK;
+}
+
+void lpm_destroy(lpm_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    void *ptrs[] = {c->d_uvwk, c->d_kh, c->d_rain, c->d_state, c->d_conc, c->d_dep, c->d_ctr,
+                    c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+const char *lpm_last_error(const lpm_ctx *c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+lpm_status lpm_set_met(lpm_ctx *c, int t_index, const float *uvwk, const float *kh,
+                       const uint8_t *rain, int on_device)
+{
+    if (!c) return LPM_E_INVALID;
+    const lpm_config &g = c->cfg;
+    if (t_index < 0 || t_index >= g.n_met_t)
+        return fail(c, LPM_E_INVALID, "t_index %d outside [0, %d)", t_index, g.n_met_t);
+    if (!uvwk) return fail(c, LPM_E_INVALID, "uvwk is NULL");
+    if ((g.kh_uniform < 0) != (kh != nullptr))
+        return fail(c, LPM_E_INVALID, "kh must be given iff kh_uniform < 0");
+    const size_t nodes = (size_t)g.nx * g.ny * g.nz;
+    const size_t cols = (size_t)g.nx * g.ny;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_uvwk + nodes * t_index, uvwk, nodes * sizeof(float4), kind,
+                                c->stream));
+    if (kh)
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_kh + nodes * t_index, kh, nodes * sizeof(float), kind,
+                                    c->stream));
+    if (rain) {
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_rain + cols * t_index, rain, cols, kind, c->stream));
+        c->any_rain = true;
+    } else {
+        LPM_CUDA(c, cudaMemsetAsync(c->d_rain + cols * t_index, 0, cols, c->stream));
+    }
+    // host sources must be consumed before returning (the caller owns them)
+    if (!on_device) LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->met_set[(size_t)t_index] = 1;
+    return LPM_OK;
+}
+
+lpm_status lpm_set_source(lpm_ctx *c, int scenario, double x, double y, double z,
+                          const float *wind_offset)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios)
+        return fail(c, LPM_E_INVALID, "scenario %d outside [0, %d)", scenario, c->cfg.n_scenarios);
+    if (!is_finite(x) || !is_finite(y) || !is_finite(z))
+        return fail(c, LPM_E_INVALID, "source must be finite");
+    ScenHost &h = c->scen[(size_t)scenario];
+    h.src_x = x; h.src_y = y; h.src_z = z;
+    if (wind_offset) {
+        h.wind_offset.assign(wind_offset, wind_offset + 2 * (size_t)c->cfg.n_met_t);
+        for (float v : h.wind_offset)
+            if (!std::isfinite(v)) return fail(c, LPM_E_INVALID, "wind offset not finite");
+    } else {
+        h.wind_offset.clear();
+    }
+    c->tables_dirty = true;
+    return LPM_OK;
+}
+
+lpm_status lpm_release_range(lpm_ctx *c, int scenario, int64_t n_total, int64_t first_particle,
+                             int64_t count, const double *q, int n_q, double q_dt,
+                             int64_t first, int64_t last, int64_t id_base)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario != c->n_released)
+        return fail(c, LPM_E_STATE, "scenarios must be released once each, in order (next is %d)",
+                    c->n_released);
+    if (scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "scenario out of range");
+    if (n_total < 1 || !q || n_q < 1 || !(q_dt > 0) || first < 0 || last <= first ||
+        last > c->cfg.n_steps)
+        return fail(c, LPM_E_INVALID, "invalid release (n=%lld, n_q=%d, steps [%lld, %lld))",
+                    (long long)n_total, n_q, (long long)first, (long long)last);
+    if (first_particle < 0 || count < 1 || first_particle + count > n_total || id_base < 0)
+        return fail(c, LPM_E_INVALID, "particle range [%lld, %lld) outside [0, %lld)",
+                    (long long)first_particle, (long long)(first_particle + count),
+                    (long long)n_total);
+    if (c->n_slots_used + count > c->cfg.max_particles)
+        return fail(c, LPM_E_INVALID, "release exceeds max_particles");
+    if (c->k > first)
+        return fail(c, LPM_E_STATE, "release starts before the current step");
+    for (int i = 0; i < n_q; ++i)
+        if (!is_finite(q[i]) || q[i] < 0) return fail(c, LPM_E_INVALID, "emission rates must be >= 0");
+    ScenHost &h = c->scen[(size_t)scenario];
+    h.first_slot = c->n_slots_used;
+    h.n = count;
+    h.n_total = n_total;
+    h.part_first = first_particle;
+    h.id_base = id_base;
+    h.rel_first = first;
+    h.rel_last = last;
+    h.q.assign(q, q + n_q);
+    h.q_dt = q_dt;
+    h.m0.assign((size_t)(last - first), 0.0);
+    h.total_mass = 0.0;
+    for (long long s = first; s < last; ++s) {
+        const long long cnt = release_count(n_total, first, last, s);
+        if (cnt <= 0) continue;
+        const double rate = emission_rate(h, c->cfg.dt, s);
+        h.m0[(size_t)(s - first)] = rate * c->cfg.dt / (double)cnt;
+        h.total_mass += rate * c->cfg.dt;
+    }
+    int e = 0;
+    if (h.total_mass > 0) std::frexp(h.total_mass, &e);
+    h.shift = h.total_mass > 0 ? 61 - e : 0;
+    if (h.shift > 120 || h.shift < -120)
+        return fail(c, LPM_E_INVALID, "total mass %g outside the fixed-point range", h.total_mass);
+    h.released = true;
+    c->n_slots_used += count;
+    c->n_ids_used = std::max<long long>(c->n_ids_used, id_base + n_total);
+    c->n_released++;
+    c->tables_dirty = true;
+    c->tiles_for_k1 = -1;
+    LPM_CUDA(c, launch_release(c->stream, c->d_state, h.first_slot, h.n, h.part_first, h.n_total,
+                               (int)first, (int)(last - first), (float)h.src_x, (float)h.src_y,
+                               (float)h.src_z));
+    c->n_launches++;
+    return LPM_OK;
+}
+
+lpm_status lpm_release(lpm_ctx *c, int scenario, int64_t n, const double *q, int n_q, double q_dt,
+                       int64_t first, int64_t last)
+{
+    if (!c) return LPM_E_INVALID;
+    return lpm_release_range(c, scenario, n, 0, n, q, n_q, q_dt, first, last, c->n_ids_used);
+}
+
+lpm_status lpm_reset(lpm_ctx *c)
+{
+    if (!c) return LPM_E_INVALID;
+    const size_t ns = (size_t)c->cfg.n_scenarios;
+    LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0, ns * c->ncell() * sizeof(unsigned long long), c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_dep, 0, ns * c->ndep() * sizeof(unsigned long long), c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_ctr, 0, ns * N_COUNTERS * sizeof(unsigned long long), c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
+    lpm_status st = relaunch_releases(c);
+    if (st != LPM_OK) return st;
+    c->k = 0;
+    c->n_bins = 0;
+    return LPM_OK;
+}
+
+lpm_status lpm_set_profiling(lpm_ctx *c, int on)
+{
+    if (!c) return LPM_E_INVALID;
+    lpm_status st = collect_events(c);
+    if (st != LPM_OK) return st;
+    c->profiling = on != 0;
+    return LPM_OK;
+}
+
+lpm_status lpm_stats(lpm_ctx *c, int64_t *launches, int64_t *advance_launches,
+                     double *advance_ms)
+{
+    if (!c) return LPM_E_INVALID;
+    lpm_status st = collect_events(c);
+    if (st != LPM_OK) return st;
+    if (launches) *launches = c->n_launches;
+    if (advance_launches) *advance_launches = c->n_adv_launches;
+    if (advance_ms) *advance_ms = c->adv_ms;
+    c->n_launches = 0;
+    c->n_adv_launches = 0;
+    c->adv_ms = 0.0;
+    return LPM_OK;
+}
+
+lpm_status lpm_set_launch(lpm_ctx *c, int block, int ppt)
+{
+    if (!c) return LPM_E_INVALID;
+    if (!(block == 128 || block == 256 || block == 512) ||
+        !(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8))
+        return fail(c, LPM_E_INVALID, "launch shape %d x %d not supported", block, ppt);
+    c->block = block;
+    c->ppt = ppt;
+    c->tiles_for_k1 = -1;
+    return LPM_OK;
+}
+
+lpm_status lpm_step(lpm_ctx *c, int64_t n)
+{
+    if (!c) return LPM_E_INVALID;
+    const lpm_config &g = c->cfg;
+    if (n < 0) return fail(c, LPM_E_INVALID, "n must be >= 0");
+    if (n == 0) return LPM_OK;
+    if (c->n_released != g.n_scenarios)
+        return fail(c, LPM_E_STATE, "%d of %d scenarios released", c->n_released, g.n_scenarios);
+    if (c->k + n > g.n_steps)
+        return fail(c, LPM_E_STATE, "stepping to %lld passes n_steps=%lld",
+                    (long long)(c->k + n), (long long)g.n_steps);
+    // met slabs touched by t in [t_k, t_{k+n-1}]
+    {
+        const double t_a = (double)c->k * g.dt, t_b = (double)(c->k + n - 1) * g.dt;
+        long long h_a = (long long)std::floor((t_a - g.met_t0) / g.met_dt);
+        long long h_b = (long long)std::floor((t_b - g.met_t0) / g.met_dt) + 1;
+        h_a = std::max(0LL, std::min(h_a, (long long)g.n_met_t - 1));
+        h_b = std::max(0LL, std::min(h_b, (long long)g.n_met_t - 1));
+        for (long long h = h_a; h <= h_b; ++h)
+            if (!c->met_set[(size_t)h])
+                return fail(c, LPM_E_STATE, "met slab %lld not set", h);
+    }
+    lpm_status st = upload_tables(c);
+    if (st != LPM_OK) return st;
+    StepParams P;
+    fill_params(c, P);
+    const bool batched = g.n_scenarios > 1;
+    long long k = c->k;
+    const long long k_end = c->k + n;
+    while (k < k_end) {
+        long long next_bin = (k / g.bin_every + 1) * (long long)g.bin_every;
+        long long e = std::min(k_end, std::min(next_bin, (long long)g.n_steps));
+        const bool do_bin = (e % g.bin_every == 0) || e == g.n_steps;
+        if (do_bin) {
+            LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0,
+                                        (size_t)g.n_scenarios * c->ncell() * sizeof(unsigned long long),
+                                        c->stream));
+            for (int s = 0; s < g.n_scenarios; ++s)
+                LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + (size_t)s * N_COUNTERS + C_BIN_OUT, 0,
+                                            sizeof(unsigned long long), c->stream));
+        }
+        AdvanceLaunch L{};
+        L.stream = c->stream;
+        L.params = &P;
+        L.state = c->d_state;
+        L.k0 = (int)k;
+        L.k1 = (int)e;
+        L.do_bin = do_bin ? 1 : 0;
+        L.block = c->block;
+        L.ppt = c->ppt;
+        const int T = c->block * c->ppt;
+        if (!batched) {
+            const long long n_rel = released_before(c->scen[0], e);
+            L.tiles = nullptr;
+            L.plain_n = n_rel;
+            L.n_tiles = (int)((n_rel + T - 1) / T);
+            L.queue = c->d_queue;
+            L.grid = (unsigned)std::max(1, L.n_tiles);
+        } else {
+            if (c->tiles_for_k1 != (int)e) {
+                st = build_tiles(c, e);
+                if (st != LPM_OK) return st;
+                c->tiles_for_k1 = (int)e;
+            }
+            LPM_CUDA(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), c->stream));
+            L.tiles = c->d_tiles;
+            L.n_tiles = (int)c->tiles.size();
+            L.queue = c->d_queue;
+            const int occ = std::max(1, advance_occupancy(c->block, c->ppt));
+            L.grid = (unsigned)std::max(1, std::min(L.n_tiles, occ * c->sm_count));
+        }
+        if (L.n_tiles > 0) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (c->profiling) {
+                e0 = next_event(c);
+                e1 = next_event(c);
+                if (!e0 || !e1) return fail(c, LPM_E_CUDA, "cudaEventCreate failed");
+                LPM_CUDA(c, cudaEventRecord(e0, c->stream));
+            }
+            LPM_CUDA(c, launch_advance(L));
+            if (c->profiling) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
+            c->n_launches++;
+            c->n_adv_launches++;
+        }
+        if (do_bin) c->n_bins++;
+        k = e;
+    }
+    c->k = k_end;
+    return LPM_OK;
+}
+
+lpm_status lpm_current_step(const lpm_ctx *c, int64_t *k)
+{
+    if (!c || !k) return LPM_E_INVALID;
+    *k = c->k;
+    return LPM_OK;
+}
+
+lpm_status lpm_sync(lpm_ctx *c)
+{
+    if (!c) return LPM_E_INVALID;
+    return check_device_error(c);
+}
+
+lpm_status lpm_concentration(lpm_ctx *c, int scenario, double *out, size_t n_out)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "bad scenario");
+    if (!out || n_out != c->ncell())
+        return fail(c, LPM_E_INVALID, "out must hold cz*cy*cx = %zu doubles", c->ncell());
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    std::vector<unsigned long long> h(c->ncell());
+    LPM_CUDA(c, cudaMemcpy(h.data(), c->d_conc + (size_t)scenario * c->ncell(),
+                           h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    const lpm_config &g = c->cfg;
+    const double f = std::ldexp(1.0, -c->scen[(size_t)scenario].shift) / (g.cdx * g.cdy * g.cdz);
+    for (size_t i = 0; i < h.size(); ++i) out[i] = (double)h[i] * f;
+    return LPM_OK;
+}
+
+lpm_status lpm_deposition(lpm_ctx *c, int scenario, double *dry, double *wet, size_t n_out)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "bad scenario");
+    const size_t plane = (size_t)c->cfg.cx * c->cfg.cy;
+    if (n_out != plane) return fail(c, LPM_E_INVALID, "n_out must be cy*cx = %zu", plane);
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    std::vector<unsigned long long> h(c->ndep());
+    LPM_CUDA(c, cudaMemcpy(h.data(), c->d_dep + (size_t)scenario * c->ndep(),
+                           h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    const double f = std::ldexp(1.0, -c->scen[(size_t)scenario].shift) / (c->cfg.cdx * c->cfg.cdy);
+    for (size_t i = 0; i < plane; ++i) {
+        if (dry) dry[i] = (double)h[i] * f;
+        if (wet) wet[i] = (double)h[plane + i] * f;
+    }
+    return LPM_OK;
+}
+
+lpm_status lpm_budget(lpm_ctx *c, int scenario, double out[8])
+{
+    if (!c || !out) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "bad scenario");
+    const ScenHost &h = c->scen[(size_t)scenario];
+    if (!h.released) return fail(c, LPM_E_STATE, "scenario %d not released", scenario);
+    lpm_status st = upload_tables(c);
+    if (st != LPM_OK) return st;
+    unsigned long long *ctr = c->d_ctr + (size_t)scenario * N_COUNTERS;
+    LPM_CUDA(c, cudaMemsetAsync(ctr + C_AIR_IN, 0, 3 * sizeof(unsigned long long), c->stream));
+    StepParams P;
+    fill_params(c, P);
+    LPM_CUDA(c, launch_budget(c->stream, P, c->d_state, scenario, h.n, (int)c->k));
+    c->n_launches++;
+    st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    unsigned long long v[N_COUNTERS];
+    LPM_CUDA(c, cudaMemcpy(v, ctr, sizeof v, cudaMemcpyDeviceToHost));
+    const double f = std::ldexp(1.0, -h.shift);
+    // initial mass of the held particles released before the current step
+    double released = 0.0;
+    const long long S = h.rel_last - h.rel_first;
+    for (long long s = h.rel_first; s < std::min<long long>(h.rel_last, c->k); ++s) {
+        const long long j = s - h.rel_first;
+        const long long a = std::max(h.part_first, (j * h.n_total + S - 1) / S);
+        const long long b = std::min(h.part_first + h.n, ((j + 1) * h.n_total + S - 1) / S);
+        if (b > a) released += (double)(b - a) * h.m0[(size_t)j];
+    }
+    out[LPM_B_RELEASED] = released;
+    out[LPM_B_AIR_IN] = (double)v[C_AIR_IN] * f;
+    out[LPM_B_AIR_OUT] = (double)v[C_AIR_OUT] * f;
+    out[LPM_B_DRY] = (double)v[C_DEP_DRY] * f;
+    out[LPM_B_WET] = (double)v[C_DEP_WET] * f;
+    out[LPM_B_EXITED] = (double)v[C_EXITED] * f;
+    out[LPM_B_DECAYED] = released - (out[1] + out[2] + out[3] + out[4] + out[5]);
+    out[LPM_B_N_ACTIVE] = (double)v[C_N_ACTIVE];
+    return LPM_OK;
+}
+
+lpm_status lpm_particles(lpm_ctx *c, int64_t first, int64_t count, float *xyz, uint32_t *tag)
+{
+    if (!c) return LPM_E_INVALID;
+    if (first < 0 || count < 0 || first + count > c->n_slots_used)
+        return fail(c, LPM_E_INVALID, "slots [%lld, %lld) outside the %lld released",
+                    (long long)first, (long long)(first + count), c->n_slots_used);
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    if (count == 0) return LPM_OK;
+    std::vector<float4> h((size_t)count);
+    LPM_CUDA(c, cudaMemcpy(h.data(), c->d_state + first, h.size() * sizeof(float4),
+                           cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < h.size(); ++i) {
+        if (xyz) {
+            xyz[3 * i] = h[i].x;
+            xyz[3 * i + 1] = h[i].y;
+            xyz[3 * i + 2] = h[i].z;
+        }
+        if (tag) {
+            uint32_t t;
+            std::memcpy(&t, &h[i].w, sizeof t);
+            tag[i] = t;
+        }
+    }
+    return LPM_OK;
+}
+
+lpm_status lpm_fixed_state(lpm_ctx *c, int scenario, uint64_t *conc, size_t n_conc, uint64_t *dep,
+                           size_t n_dep, int64_t counters[16], int *shift)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "bad scenario");
+    if (conc && n_conc != c->ncell()) return fail(c, LPM_E_INVALID, "n_conc must be %zu", c->ncell());
+    if (dep && n_dep != c->ndep()) return fail(c, LPM_E_INVALID, "n_dep must be %zu", c->ndep());
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    if (conc)
+        LPM_CUDA(c, cudaMemcpy(conc, c->d_conc + (size_t)scenario * c->ncell(),
+                               n_conc * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (dep)
+        LPM_CUDA(c, cudaMemcpy(dep, c->d_dep + (size_t)scenario * c->ndep(),
+                               n_dep * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (counters) {
+        unsigned long long v[N_COUNTERS];
+        LPM_CUDA(c, cudaMemcpy(v, c->d_ctr + (size_t)scenario * N_COUNTERS, sizeof v,
+                               cudaMemcpyDeviceToHost));
+        for (int i = 0; i < 16; ++i) counters[i] = (int64_t)v[i];
+        counters[C_N_BINS] = c->n_bins;
+    }
+    if (shift) *shift = c->scen[(size_t)scenario].shift;
+    return LPM_OK;
+}
+
+lpm_status lpm_draws(uint64_t seed, const uint64_t *pid, const uint32_t *step, uint32_t stream,
+                     int64_t n, uint32_t *words, float *normals)
+{
+    g_create_error.clear();
+    if (n < 0 || (n > 0 && (!pid || !step || !words || !normals)))
+        return fail(nullptr, LPM_E_INVALID, "lpm_draws: invalid arguments");
+    if (n == 0) return LPM_OK;
+    unsigned long long *d_pid = nullptr;
+    unsigned int *d_step = nullptr;
+    uint4 *d_w = nullptr;
+    float *d_n = nullptr;
+    lpm_status st = LPM_OK;
+    cudaError_t e = cudaMalloc(&d_pid, n * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&d_step, n * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_w, n * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMalloc(&d_n, n * 3 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(d_pid, pid, n * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_step, step, n * sizeof(unsigned int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_draws(nullptr, seed, d_pid, d_step, stream, n, d_w, d_n);
+    if (e == cudaSuccess) e = cudaMemcpy(words, d_w, n * sizeof(uint4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(normals, d_n, n * 3 * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        st = fail(nullptr, e == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA, "lpm_draws: %s",
+                  cudaGetErrorString(e));
+    cudaFree(d_pid);
+    cudaFree(d_step);
+    cudaFree(d_w);
+    cudaFree(d_n);
+    return st;
+}
+
+}  // extern "C"

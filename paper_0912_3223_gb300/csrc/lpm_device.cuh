@@ -1,0 +1,251 @@
+// lpm_device.cuh - device-side building blocks of the particle step (sm_103a).
+//
+// One thread advances PPT particles through many time steps with the particle state in
+// registers; the state crosses HBM once per launch as a 16-byte float4
+// (x, y, z, tag) with tag = status << 28 | release step. Weather slabs stay resident in
+// HBM and are gathered through L1/L2. Random numbers are Philox4x32-10 keyed on
+// (seed, particle id, step, stream), so nothing is buffered (the paper's Mersenne
+// Twister buffer of Sec. 3.2 disappears).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lpm {
+
+constexpr uint32_t ST_ACTIVE = 0u;
+constexpr uint32_t ST_UNRELEASED = 1u;
+constexpr uint32_t ST_DEP_DRY = 2u;
+constexpr uint32_t ST_DEP_WET = 3u;
+constexpr uint32_t ST_EXITED = 4u;
+constexpr int TAG_SHIFT = 28;
+constexpr uint32_t TAG_STEP = 0x0FFFFFFFu;
+constexpr int MAX_LEVELS = 64;
+
+// Per-scenario counters (64-bit, fixed point unless noted).
+enum {
+    C_BIN_OUT = 0, C_DEP_OUT_DRY = 1, C_DEP_OUT_WET = 2, C_EXITED = 3,
+    C_ACTIVE_STEPS = 4 /* count */, C_N_BINS = 5 /* count */, C_AIR_IN = 6, C_AIR_OUT = 7,
+    C_N_ACTIVE = 8 /* count */, C_DEP_DRY = 9, C_DEP_WET = 10, N_COUNTERS = 16
+};
+
+// Device error word bits.
+enum { ERR_NAN = 1u, ERR_INDEX = 2u, ERR_TIMEOUT = 4u };
+
+struct ScenDev {
+    float src_x, src_y, src_z;
+    float scale;                     // 2^shift (fixed-point scale), exact power of two
+    long long first_slot;            // state slot of the scenario's first particle here
+    long long n;                     // particles of the scenario held by this context
+    long long id0;                   // global id (generator key) of that first particle
+    int rel_first, rel_last;         // release steps [first, last)
+    int m0_off;                      // offset of the scenario's initial-mass table
+    int pad;
+    const float2 *wind_offset;       // [n_met_t] (du, dv) or nullptr
+    unsigned long long *conc;        // [cz][cy][cx]
+    unsigned long long *dep;         // [2][cy][cx]
+    unsigned long long *ctr;         // [N_COUNTERS]
+};
+
+// A tile = a contiguous run of particles of one scenario processed by one block.
+struct Tile {
+    int scen;
+    int count;
+    long long first;                 // state slot of the tile's first particle
+};
+
+struct StepParams {
+    // weather
+    const float4 *uvwk;              // [n_t][nz][ny][nx]
+    const float *kh;                 // [n_t][nz][ny][nx] or nullptr
+    const uint8_t *rain;             // [n_t][ny][nx] or nullptr
+    int nx, ny, nz, n_t;
+    long long slab;                  // nodes per slab
+    float x0, y0, inv_dx, inv_dy, dx, dy;
+    float met_t0, met_dt;
+    float x_lo, x_hi, y_lo, y_hi;
+    float zlev[MAX_LEVELS];
+    // time stepping and physics
+    float dt, kh_uniform, k_scale, bias_u, bias_v;
+    float lambda;                    // decay rate (1/s)
+    float h_mix, z_top;
+    unsigned int seed_lo, seed_hi;
+    unsigned int t_dry, t_wet;       // event iff word < threshold
+    int reflect_ground, reflect_top, lateral_exit, drift;
+    // concentration grid
+    int cx, cy, cz;
+    float cx0, cy0, cz0, inv_cdx, inv_cdy, inv_cdz;
+    // tables
+    const float *m0;                 // initial mass per release step (all scenarios)
+    const ScenDev *scen;
+    unsigned int *err;
+};
+
+// ---------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies with
+// word exchange, key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------------
+struct U4 {
+    uint32_t a, b, c, d;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// Uniform on (0,1): midpoint of one of 2^23 equal bins, exact in FP32.
+__device__ __forceinline__ float unit_uniform(uint32_t w)
+{
+    return __uint2float_rn(2u * (w >> 9) + 1u) * 5.9604644775390625e-08f;
+}
+
+// Three N(0,1) by the basic Box-Muller transform (Sec. 2): (u0,u1) -> n0, n1;
+// (u2,u3) -> n2.
+__device__ __forceinline__ void normals3(const U4 &w, float &n0, float &n1, float &n2)
+{
+    const float u0 = unit_uniform(w.a), u1 = unit_uniform(w.b);
+    const float u2 = unit_uniform(w.c), u3 = unit_uniform(w.d);
+    const float r0 = sqrtf(-2.0f * logf(u0));
+    const float r1 = sqrtf(-2.0f * logf(u2));
+    float s1, c1;
+    sincospif(2.0f * u1, &s1, &c1);
+    n0 = r0 * c1;
+    n1 = r0 * s1;
+    n2 = r1 * cospif(2.0f * u3);
+}
+
+// ---------------------------------------------------------------------------------
+// Weather at a point: 4D multilinear over (x, y, z, t), cell by floor with the index
+// clamped to the grid and the fraction to [0,1] (constant extension outside).
+// ---------------------------------------------------------------------------------
+struct TimeSlab {
+    int h0, h1;
+    float f;
+};
+
+__device__ __forceinline__ TimeSlab time_slab(const StepParams &P, float t)
+{
+    TimeSlab s;
+    if (P.n_t < 2) {
+        s.h0 = 0; s.h1 = 0; s.f = 0.0f;
+        return s;
+    }
+    // correctly rounded division: exact at slab boundaries (t_k on an hour mark)
+    const float ft = __fdiv_rn(t - P.met_t0, P.met_dt);
+    int h = (int)floorf(ft);
+    h = min(max(h, 0), P.n_t - 2);
+    s.h0 = h;
+    s.h1 = h + 1;
+    s.f = fminf(fmaxf(ft - (float)h, 0.0f), 1.0f);
+    return s;
+}
+
+__device__ __forceinline__ void axis(float coord, float c0, float inv_d, int n, int &i, float &a)
+{
+    const float f = (coord - c0) * inv_d;
+    int ii = (int)floorf(f);
+    ii = min(max(ii, 0), n - 2);
+    i = ii;
+    a = fminf(fmaxf(f - (float)ii, 0.0f), 1.0f);
+}
+
+// Level search in the shared-memory copy of z_levels: last level <= z, clamped.
+__device__ __forceinline__ void level(const float *szl, int nz, float z, int &k, float &c)
+{
+    int lo = 0, hi = nz - 1;          // invariant: szl[lo] <= z (or lo = 0), answer in [lo, hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (szl[mid] <= z) lo = mid;
+        else hi = mid;
+    }
+    k = lo;
+    const float z0 = szl[lo], z1 = szl[lo + 1];
+    c = fminf(fmaxf((z - z0) / (z1 - z0), 0.0f), 1.0f);
+}
+
+struct Met {
+    float u, v, w, kz, kh, dkz;
+};
+
+__device__ __forceinline__ float4 lerp4(const float4 a, const float4 b, float t)
+{
+    return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y),
+                       fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
+}
+
+__device__ __forceinline__ Met sample_met(const StepParams &P, const float *szl, const TimeSlab &ts,
+                                          float x, float y, float z)
+{
+    int i, j, k;
+    float a, b, c;
+    axis(x, P.x0, P.inv_dx, P.nx, i, a);
+    axis(y, P.y0, P.inv_dy, P.ny, j, b);
+    level(szl, P.nz, z, k, c);
+    const long long nxny = (long long)P.nx * P.ny;
+    const long long n00 = ((long long)k * P.ny + j) * P.nx + i;
+    const float4 *s0 = P.uvwk + (long long)ts.h0 * P.slab + n00;
+    const float4 *s1 = P.uvwk + (long long)ts.h1 * P.slab + n00;
+    // 16 corners: (di, dj, dk) x 2 time slabs, blended in time first
+    float4 q[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const long long off = (m & 1) + ((m >> 1) & 1) * (long long)P.nx + ((m >> 2) & 1) * nxny;
+        q[m] = lerp4(__ldg(s0 + off), __ldg(s1 + off), ts.f);
+    }
+    // x, then y, then z
+    const float4 x00 = lerp4(q[0], q[1], a), x10 = lerp4(q[2], q[3], a);
+    const float4 x01 = lerp4(q[4], q[5], a), x11 = lerp4(q[6], q[7], a);
+    const float4 y0 = lerp4(x00, x10, b), y1 = lerp4(x01, x11, b);
+    const float4 r = lerp4(y0, y1, c);
+    Met m;
+    m.u = r.x;
+    m.v = r.y;
+    m.w = r.z;
+    m.kz = fmaxf(r.w, 0.0f);
+    const bool inside = z >= szl[0] && z <= szl[P.nz - 1];
+    m.dkz = inside ? (y1.w - y0.w) / (szl[k + 1] - szl[k]) : 0.0f;
+    if (P.kh) {
+        const float *h0 = P.kh + (long long)ts.h0 * P.slab + n00;
+        const float *h1 = P.kh + (long long)ts.h1 * P.slab + n00;
+        float e[8];
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+            const long long off = (mm & 1) + ((mm >> 1) & 1) * (long long)P.nx +
+                                  ((mm >> 2) & 1) * nxny;
+            const float v0 = __ldg(h0 + off), v1 = __ldg(h1 + off);
+            e[mm] = fmaf(ts.f, v1 - v0, v0);
+        }
+        const float ex0 = fmaf(a, e[1] - e[0], e[0]), ex1 = fmaf(a, e[3] - e[2], e[2]);
+        const float ex2 = fmaf(a, e[5] - e[4], e[4]), ex3 = fmaf(a, e[7] - e[6], e[6]);
+        const float ey0 = fmaf(b, ex1 - ex0, ex0), ey1 = fmaf(b, ex3 - ex2, ex2);
+        m.kh = fmaxf(fmaf(c, ey1 - ey0, ey0), 0.0f);
+    } else {
+        m.kh = fmaxf(P.kh_uniform, 0.0f);
+    }
+    return m;
+}
+
+// Fixed-point mass: round-to-nearest-even of m * 2^shift (scale is an exact power of 2).
+__device__ __forceinline__ unsigned long long to_fixed(float m, float scale)
+{
+    return __float2ull_rn(m * scale);
+}
+
+}  // namespace lpm

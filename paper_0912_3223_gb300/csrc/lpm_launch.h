@@ -1,0 +1,32 @@
+// lpm_launch.h - host-side launch interface between the C-ABI layer and the kernels.
+#pragma once
+
+#include "lpm_device.cuh"
+
+namespace lpm {
+
+struct AdvanceLaunch {
+    cudaStream_t stream;
+    const StepParams *params;
+    float4 *state;
+    const Tile *tiles;        // nullptr: implicit tiles of scenario 0
+    int n_tiles;
+    unsigned int *queue;      // work-queue counter (zeroed before the launch)
+    long long plain_n;        // implicit tiles: particles [0, plain_n)
+    int k0, k1, do_bin;
+    int block, ppt;
+    unsigned int grid;
+};
+
+cudaError_t launch_release(cudaStream_t s, float4 *state, long long first_slot, long long count,
+                           long long part_first, long long n_total, int rel_first, int rel_len,
+                           float sx, float sy, float sz);
+cudaError_t launch_advance(const AdvanceLaunch &L);
+int advance_occupancy(int block, int ppt);
+cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned long long *pid,
+                         const unsigned int *step, unsigned int stream, long long n, uint4 *words,
+                         float *nrm);
+cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *state, int scen,
+                          long long n, int k_now);
+
+}  // namespace lpm

@@ -1,0 +1,393 @@
+"""Python binding of the C ABI in include/lpm.h (argument marshalling only).
+
+Functions keep the C names (``lpm_create``, ``lpm_set_met``, ``lpm_release``, ``lpm_step``,
+``lpm_concentration``, ``lpm_deposition``, ``lpm_budget``, ...). Every step of the
+particle method runs in the CUDA library; this module converts numpy arrays, torch
+tensors and streams into plain pointers. It raises if the library has not been built:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblpm.so")
+
+LPM_OK, LPM_E_INVALID, LPM_E_OOM, LPM_E_CUDA, LPM_E_STATE, LPM_E_NUMERIC, LPM_E_TIMEOUT = range(7)
+STATUS_NAMES = {0: "LPM_OK", 1: "LPM_E_INVALID", 2: "LPM_E_OOM", 3: "LPM_E_CUDA",
+                4: "LPM_E_STATE", 5: "LPM_E_NUMERIC", 6: "LPM_E_TIMEOUT"}
+B_RELEASED, B_AIR_IN, B_AIR_OUT, B_DRY, B_WET, B_EXITED, B_DECAYED, B_N_ACTIVE = range(8)
+
+# Exported symbols declared in include/lpm.h.
+SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_set_source",
+           "lpm_release", "lpm_step", "lpm_current_step", "lpm_concentration",
+           "lpm_deposition", "lpm_budget", "lpm_particles", "lpm_fixed_state",
+           "lpm_set_launch", "lpm_sync", "lpm_draws", "lpm_release_range", "lpm_reset",
+           "lpm_set_profiling", "lpm_stats"]
+
+
+class LpmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lpm_config(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("x0", C.c_double), ("y0", C.c_double), ("dx", C.c_double), ("dy", C.c_double),
+        ("z_levels", C.POINTER(C.c_double)),
+        ("n_met_t", C.c_int), ("met_t0", C.c_double), ("met_dt", C.c_double),
+        ("cx", C.c_int), ("cy", C.c_int), ("cz", C.c_int),
+        ("cx0", C.c_double), ("cy0", C.c_double), ("cz0", C.c_double),
+        ("cdx", C.c_double), ("cdy", C.c_double), ("cdz", C.c_double),
+        ("src_x", C.c_double), ("src_y", C.c_double), ("src_z", C.c_double),
+        ("dt", C.c_double), ("n_steps", C.c_int64), ("seed", C.c_uint64),
+        ("bin_every", C.c_int),
+        ("half_life_s", C.c_double), ("vd_dry", C.c_double), ("h_mix", C.c_double),
+        ("wet_lambda", C.c_double), ("kh_uniform", C.c_double),
+        ("reflect_ground", C.c_int), ("reflect_top", C.c_int), ("z_top", C.c_double),
+        ("lateral_exit", C.c_int), ("drift_correction", C.c_int),
+        ("n_scenarios", C.c_int), ("max_particles", C.c_int64),
+    ]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Loads liblpm.so (built by ``build.py``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, dp = C.c_void_p, C.c_int64, C.POINTER(C.c_double)
+    L.lpm_create.argtypes = [C.POINTER(lpm_config), vp, C.POINTER(vp)]
+    L.lpm_destroy.argtypes = [vp]
+    L.lpm_destroy.restype = None
+    L.lpm_last_error.argtypes = [vp]
+    L.lpm_last_error.restype = C.c_char_p
+    L.lpm_set_met.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int]
+    L.lpm_set_source.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double, vp]
+    L.lpm_release.argtypes = [vp, C.c_int, i64, dp, C.c_int, C.c_double, i64, i64]
+    L.lpm_step.argtypes = [vp, i64]
+    L.lpm_current_step.argtypes = [vp, C.POINTER(i64)]
+    L.lpm_concentration.argtypes = [vp, C.c_int, dp, C.c_size_t]
+    L.lpm_deposition.argtypes = [vp, C.c_int, dp, dp, C.c_size_t]
+    L.lpm_budget.argtypes = [vp, C.c_int, dp]
+    L.lpm_particles.argtypes = [vp, i64, i64, C.POINTER(C.c_float), C.POINTER(C.c_uint32)]
+    L.lpm_fixed_state.argtypes = [vp, C.c_int, C.POINTER(C.c_uint64), C.c_size_t,
+                                  C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(i64),
+                                  C.POINTER(C.c_int)]
+    L.lpm_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    L.lpm_sync.argtypes = [vp]
+    L.lpm_release_range.argtypes = [vp, C.c_int, i64, i64, i64, dp, C.c_int, C.c_double, i64,
+                                    i64, i64]
+    L.lpm_reset.argtypes = [vp]
+    L.lpm_set_profiling.argtypes = [vp, C.c_int]
+    L.lpm_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), dp]
+    L.lpm_draws.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
+                            C.c_uint32, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
+    for name in ("lpm_create", "lpm_set_met", "lpm_set_source", "lpm_release", "lpm_step",
+                 "lpm_current_step", "lpm_concentration", "lpm_deposition", "lpm_budget",
+                 "lpm_particles", "lpm_fixed_state", "lpm_set_launch", "lpm_sync",
+                 "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
+                 "lpm_stats"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a, ct):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _check(ctx, status: int):
+    if status != LPM_OK:
+        msg = load().lpm_last_error(ctx)
+        raise LpmError(status, msg.decode() if msg else "")
+
+
+def config_struct(cfg, max_particles: Optional[int] = None):
+    """C record for an ``lpm_inputs.LpmConfig``; returns (struct, keep-alive arrays)."""
+    z = np.ascontiguousarray(cfg.z_levels, dtype=np.float64)
+    s = lpm_config()
+    for name in ("nx", "ny", "nz", "n_met_t", "cx", "cy", "cz", "bin_every", "reflect_ground",
+                 "reflect_top", "lateral_exit", "drift_correction", "n_scenarios"):
+        setattr(s, name, int(getattr(cfg, name)))
+    for name in ("x0", "y0", "dx", "dy", "met_t0", "met_dt", "cx0", "cy0", "cz0", "cdx", "cdy",
+                 "cdz", "src_x", "src_y", "src_z", "dt", "half_life_s", "vd_dry", "h_mix",
+                 "wet_lambda", "kh_uniform", "z_top"):
+        setattr(s, name, float(getattr(cfg, name)))
+    s.n_steps = int(cfg.n_steps)
+    s.seed = int(cfg.seed)
+    s.z_levels = _ptr(z, C.c_double)
+    s.max_particles = int(max_particles if max_particles is not None else cfg.n_particles)
+    return s, [z]
+
+
+def lpm_create(cfg, stream=None, max_particles: Optional[int] = None) -> int:
+    L = load()
+    s, keep = config_struct(cfg, max_particles)
+    out = C.c_void_p()
+    st = L.lpm_create(C.byref(s), C.c_void_p(int(stream or 0)), C.byref(out))
+    del keep
+    _check(None, st)
+    return out.value
+
+
+def lpm_destroy(ctx) -> None:
+    load().lpm_destroy(C.c_void_p(ctx))
+
+
+def _addr(a):
+    """Host numpy array -> (address, on_device=0); torch CUDA tensor -> (address, 1)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    return a.ctypes.data, 0
+
+
+def lpm_set_met(ctx, t_index: int, uvwk, kh=None, rain=None) -> None:
+    """uvwk [nz][ny][nx][4] float32, kh [nz][ny][nx] float32, rain [ny][nx] uint8: all numpy
+    (host) or all torch CUDA tensors (device)."""
+    if not hasattr(uvwk, "data_ptr"):
+        uvwk = np.ascontiguousarray(uvwk, dtype=np.float32)
+        kh = None if kh is None else np.ascontiguousarray(kh, dtype=np.float32)
+        rain = None if rain is None else np.ascontiguousarray(rain, dtype=np.uint8)
+    a, dev = _addr(uvwk)
+    b, _ = _addr(kh)
+    r, _ = _addr(rain)
+    _check(ctx, load().lpm_set_met(C.c_void_p(ctx), int(t_index), a, b, r, dev))
+
+
+def lpm_set_source(ctx, scenario: int, x: float, y: float, z: float, wind_offset=None) -> None:
+    wo = None if wind_offset is None else np.ascontiguousarray(wind_offset, dtype=np.float32)
+    _check(ctx, load().lpm_set_source(C.c_void_p(ctx), int(scenario), float(x), float(y),
+                                      float(z), None if wo is None else wo.ctypes.data))
+
+
+def lpm_release(ctx, scenario: int, n_particles: int, q, q_dt: float, first_step: int,
+                last_step: int) -> None:
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    _check(ctx, load().lpm_release(C.c_void_p(ctx), int(scenario), int(n_particles),
+                                   _ptr(qa, C.c_double), int(qa.size), float(q_dt),
+                                   int(first_step), int(last_step)))
+
+
+def lpm_release_range(ctx, scenario: int, n_total: int, first_particle: int, count: int, q,
+                      q_dt: float, first_step: int, last_step: int, id_base: int = 0) -> None:
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    _check(ctx, load().lpm_release_range(C.c_void_p(ctx), int(scenario), int(n_total),
+                                         int(first_particle), int(count), _ptr(qa, C.c_double),
+                                         int(qa.size), float(q_dt), int(first_step),
+                                         int(last_step), int(id_base)))
+
+
+def lpm_reset(ctx) -> None:
+    _check(ctx, load().lpm_reset(C.c_void_p(ctx)))
+
+
+def lpm_set_profiling(ctx, on: bool) -> None:
+    _check(ctx, load().lpm_set_profiling(C.c_void_p(ctx), int(bool(on))))
+
+
+def lpm_stats(ctx):
+    """(kernels launched, advance launches, advance device ms) since the last call."""
+    a, b, ms = C.c_int64(), C.c_int64(), C.c_double()
+    _check(ctx, load().lpm_stats(C.c_void_p(ctx), C.byref(a), C.byref(b), C.byref(ms)))
+    return int(a.value), int(b.value), float(ms.value)
+
+
+def lpm_step(ctx, n: int) -> None:
+    _check(ctx, load().lpm_step(C.c_void_p(ctx), int(n)))
+
+
+def lpm_current_step(ctx) -> int:
+    k = C.c_int64()
+    _check(ctx, load().lpm_current_step(C.c_void_p(ctx), C.byref(k)))
+    return int(k.value)
+
+
+def lpm_concentration(ctx, scenario: int, shape) -> np.ndarray:
+    out = np.empty(shape, dtype=np.float64)
+    _check(ctx, load().lpm_concentration(C.c_void_p(ctx), int(scenario), _ptr(out, C.c_double),
+                                         out.size))
+    return out
+
+
+def lpm_deposition(ctx, scenario: int, shape):
+    dry = np.empty(shape, dtype=np.float64)
+    wet = np.empty(shape, dtype=np.float64)
+    _check(ctx, load().lpm_deposition(C.c_void_p(ctx), int(scenario), _ptr(dry, C.c_double),
+                                      _ptr(wet, C.c_double), dry.size))
+    return dry, wet
+
+
+def lpm_budget(ctx, scenario: int = 0) -> np.ndarray:
+    out = np.empty(8, dtype=np.float64)
+    _check(ctx, load().lpm_budget(C.c_void_p(ctx), int(scenario), _ptr(out, C.c_double)))
+    return out
+
+
+def lpm_particles(ctx, first: int, count: int):
+    xyz = np.empty((count, 3), dtype=np.float32)
+    tag = np.empty(count, dtype=np.uint32)
+    _check(ctx, load().lpm_particles(C.c_void_p(ctx), int(first), int(count),
+                                     _ptr(xyz, C.c_float), _ptr(tag, C.c_uint32)))
+    return xyz, tag
+
+
+def lpm_fixed_state(ctx, scenario: int, conc_shape, dep_shape):
+    conc = np.empty(conc_shape, dtype=np.uint64)
+    dep = np.empty(dep_shape, dtype=np.uint64)
+    ctr = np.empty(16, dtype=np.int64)
+    sh = C.c_int()
+    _check(ctx, load().lpm_fixed_state(C.c_void_p(ctx), int(scenario), _ptr(conc, C.c_uint64),
+                                       conc.size, _ptr(dep, C.c_uint64), dep.size,
+                                       _ptr(ctr, C.c_int64), C.byref(sh)))
+    return conc, dep, ctr, int(sh.value)
+
+
+def lpm_set_launch(ctx, block: int, particles_per_thread: int) -> None:
+    _check(ctx, load().lpm_set_launch(C.c_void_p(ctx), int(block), int(particles_per_thread)))
+
+
+def lpm_sync(ctx) -> None:
+    _check(ctx, load().lpm_sync(C.c_void_p(ctx)))
+
+
+def lpm_draws(seed: int, pid, step, stream: int = 0):
+    """Philox words [n][4] (uint32) and the step's normals [n][3] (float32)."""
+    pid = np.ascontiguousarray(pid, dtype=np.uint64)
+    step = np.ascontiguousarray(np.broadcast_to(step, pid.shape), dtype=np.uint32)
+    words = np.empty((pid.size, 4), dtype=np.uint32)
+    nrm = np.empty((pid.size, 3), dtype=np.float32)
+    _check(None, load().lpm_draws(int(seed), _ptr(pid, C.c_uint64), _ptr(step, C.c_uint32),
+                                  int(stream), pid.size, _ptr(words, C.c_uint32),
+                                  _ptr(nrm, C.c_float)))
+    return words, nrm
+
+
+# ------------------------------------------------------------------------------------
+# Convenience wrapper
+# ------------------------------------------------------------------------------------
+class Sim:
+    """One context set up from an ``lpm_inputs.LpmConfig``: met uploaded, sources set,
+    releases declared. ``stream`` is a torch.cuda.Stream (default: current stream)."""
+
+    def __init__(self, cfg, stream=None, met_on_device: bool = False, launch=None,
+                 part=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the particle model runs on a CUDA GPU; none is available")
+        self.cfg = cfg
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.part = part
+        n_slots = part[1] if part is not None else None
+        self.ctx = lpm_create(cfg, self.stream.cuda_stream, max_particles=n_slots)
+        try:
+            if launch is not None:
+                lpm_set_launch(self.ctx, *launch)
+            self._set_met(met_on_device)
+            if cfg.scenarios:
+                for i, sc in enumerate(cfg.scenarios):
+                    lpm_set_source(self.ctx, i, sc.src_x, sc.src_y, sc.src_z, sc.wind_offset)
+                for i, sc in enumerate(cfg.scenarios):
+                    r = sc.release
+                    lpm_release(self.ctx, i, r.n_particles, r.q, r.q_dt, r.first_step,
+                                r.last_step)
+            elif part is not None:
+                r = cfg.release
+                lpm_release_range(self.ctx, 0, r.n_particles, part[0], part[1], r.q, r.q_dt,
+                                  r.first_step, r.last_step, 0)
+            else:
+                r = cfg.release
+                lpm_release(self.ctx, 0, r.n_particles, r.q, r.q_dt, r.first_step, r.last_step)
+        except Exception:
+            lpm_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def _set_met(self, on_device: bool):
+        cfg = self.cfg
+        if on_device:
+            import torch
+            dev = torch.device("cuda", torch.cuda.current_device())
+            uvwk = torch.from_numpy(np.ascontiguousarray(cfg.uvwk)).to(dev)
+            kh = None if cfg.kh is None else torch.from_numpy(np.ascontiguousarray(cfg.kh)).to(dev)
+            rain = None if cfg.rain is None else torch.from_numpy(
+                np.ascontiguousarray(cfg.rain)).to(dev)
+            self._met_keep = (uvwk, kh, rain)
+            for t in range(cfg.n_met_t):
+                lpm_set_met(self.ctx, t, uvwk[t], None if kh is None else kh[t],
+                            None if rain is None else rain[t])
+        else:
+            for t in range(cfg.n_met_t):
+                lpm_set_met(self.ctx, t, cfg.uvwk[t], None if cfg.kh is None else cfg.kh[t],
+                            None if cfg.rain is None else cfg.rain[t])
+
+    def step(self, n: int):
+        lpm_step(self.ctx, n)
+        return self
+
+    def reset(self):
+        lpm_reset(self.ctx)
+        return self
+
+    @property
+    def k(self) -> int:
+        return lpm_current_step(self.ctx)
+
+    def concentration(self, scenario: int = 0) -> np.ndarray:
+        c = self.cfg
+        return lpm_concentration(self.ctx, scenario, (c.cz, c.cy, c.cx))
+
+    def deposition(self, scenario: int = 0):
+        c = self.cfg
+        return lpm_deposition(self.ctx, scenario, (c.cy, c.cx))
+
+    def budget(self, scenario: int = 0) -> np.ndarray:
+        return lpm_budget(self.ctx, scenario)
+
+    def particles(self, first: int = 0, count: Optional[int] = None):
+        if count is None:
+            held = self.part[1] if self.part is not None else self.cfg.n_particles
+            count = held - first
+        return lpm_particles(self.ctx, first, count)
+
+    def fixed_state(self, scenario: int = 0):
+        c = self.cfg
+        return lpm_fixed_state(self.ctx, scenario, (c.cz, c.cy, c.cx), (2, c.cy, c.cx))
+
+    def sync(self):
+        lpm_sync(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            lpm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

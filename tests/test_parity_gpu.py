@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle on the
+same seeded inputs, element by element, plus exact integer identities of the
+fixed-point binning. Bars: Philox words bit-exact; per-particle positions within
+0.5 m after 360 steps; grids within 1e-4 relative L1 outside face-ambiguous cells."""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+
+import lpm_inputs as li
+import oracle
+from parity_util import (POS_TOL_M, artificial_weather_cfg, compare, run_gpu)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0912_3223_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _integer_identity(g):
+    """Right after a bin step: the budget kernel's per-particle fixed-point masses (in and
+    out of the grid) equal the binned grid plus its out-of-grid counter, exactly."""
+    ctr = g["counters"]
+    assert int(g["conc_fixed"].sum()) + int(ctr[0]) == int(ctr[6]) + int(ctr[7])
+
+
+def test_draws_bit_exact():
+    rng = np.random.default_rng(5)
+    pid = np.concatenate([np.arange(1000), rng.integers(0, 2 ** 40, 3000)]).astype(np.uint64)
+    step = rng.integers(0, 2 ** 28, pid.size).astype(np.uint32)
+    from paper_0912_3223_gb300 import lpm
+    for seed in (1, 0xDEADBEEF12345678):
+        for stream in (0, 1):
+            w, n = lpm.lpm_draws(seed, pid, step, stream)
+            ref = oracle.draws(seed, pid, step, stream)
+            assert np.array_equal(w, ref)
+        ref_n = oracle.normals(seed, pid, step)
+        w, n = lpm.lpm_draws(seed, pid, step, 0)
+        assert np.abs(n.astype(np.float64) - ref_n).max() < 4e-6
+
+
+def test_cfg0_full_parity():
+    """Plain method, small: 1e4 particles, 360 steps, uniform weather."""
+    cfg = li.make_cfg0()
+    g = run_gpu(cfg)
+    o = oracle.run(cfg)
+    rep = compare(cfg, g, o)
+    assert rep["ambiguous"] == 0
+    assert rep["grid_rel_l1"] <= 1e-4
+    _integer_identity(g)
+    assert int(g["counters"][4]) == o["active_steps"] == 1_805_160
+    np.testing.assert_allclose(g["budget"][:6], o["budget"][:6], rtol=1e-5)
+    assert g["budget"][7] == o["budget"][7]
+
+
+def test_artificial_weather_of_the_paper():
+    """The paper's homogeneous case (Fig. 3b): 2160 particles, dt = 10 s. Per-particle
+    distances are gated after 360 steps and reported after 6 h."""
+    cfg = artificial_weather_cfg()
+    g = run_gpu(cfg, n_run=360)
+    o = oracle.run(cfg, n_run=360)
+    compare(cfg, g, o)
+    gf = run_gpu(cfg)
+    of = oracle.run(cfg)
+    rep = compare(cfg, gf, of, pos_tol=5.0, grid_tol=1e-3)
+    print("artificial weather after 6 h:", rep)
+    _integer_identity(gf)
+
+
+@pytest.fixture(scope="module")
+def cfg1_small():
+    return li.make_cfg1(n_particles=20_000, n_steps=2880, n_hours=25)
+
+
+def test_cfg1_parity_360_steps(cfg1_small):
+    """Realistic weather (log profile + mesoscale modes, K_z profile, decay, dry and wet
+    deposition, lateral exit), all 20000 particles after 360 steps."""
+    g = run_gpu(cfg1_small, n_run=360)
+    o = oracle.run(cfg1_small, n_run=360)
+    rep = compare(cfg1_small, g, o, check_grid=False)
+    print("cfg1 360 steps:", rep)
+    # budget after 360 steps (not a bin step: compare the airborne + event totals)
+    np.testing.assert_allclose(g["budget"][0], o["budget"][0], rtol=1e-6)
+    assert abs(g["budget"][7] - o["budget"][7]) <= rep["ambiguous"]
+
+
+def test_cfg1_parity_bin_step(cfg1_small):
+    """Same inputs stepped to the first hourly snapshot: grids and deposition compared."""
+    g = run_gpu(cfg1_small, n_run=120)
+    o = oracle.run(cfg1_small, n_run=120)
+    rep = compare(cfg1_small, g, o)
+    print("cfg1 120 steps:", rep)
+    _integer_identity(g)
+    assert int(g["counters"][4]) == o["active_steps"]
+
+
+def test_cfg1_full_run_report(cfg1_small):
+    """24 h: events and chaotic divergence in non-uniform wind (Sec. 4.1) make the late
+    distances grow; they are reported, with a loose bar, and the exact invariants hold."""
+    g = run_gpu(cfg1_small)
+    o = oracle.run(cfg1_small)
+    rep = compare(cfg1_small, g, o, pos_tol=10.0, check_grid=False, max_excluded_frac=0.05)
+    print("cfg1 24 h:", rep)
+    _integer_identity(g)
+    b = g["budget"]
+    assert b[0] - b[6] == pytest.approx(b[1] + b[2] + b[3] + b[4] + b[5], rel=1e-12)
+    np.testing.assert_allclose(b[0], o["budget"][0], rtol=1e-6)
+
+
+def test_cfg1_full_size_sampled():
+    """1e7 particles x 2880 steps in the benchmark's launch shape; a deterministic sample
+    of particle ids is recomputed one by one by the oracle."""
+    cfg = li.make_cfg1()
+    from paper_0912_3223_gb300 import Sim
+    sel = np.arange(0, cfg.n_particles, 9973, dtype=np.int64)
+    with Sim(cfg) as sim:
+        sim.step(360)
+        xyz, tag = sim.particles()
+        g360 = dict(pos=xyz[sel].astype(np.float64), tag=tag[sel])
+        sim.step(cfg.n_steps - 360)
+        xyz, tag = sim.particles()
+        cfix, dfix, ctr, shift = sim.fixed_state()
+        b = sim.budget()
+        cfix2, _, ctr2, _ = sim.fixed_state()
+    o360 = oracle.run(cfg, sel=sel, n_run=360)
+    ok = o360["margin"] >= POS_TOL_M
+    st = (g360["tag"] >> 28).astype(np.int32)
+    assert np.array_equal(st[ok], o360["status"][ok])
+    d = np.linalg.norm(g360["pos"][ok] - o360["pos"][ok], axis=1)
+    print(f"1e7 sample after 360 steps: max {d.max():.3g} m over {ok.sum()} particles")
+    assert d.max() <= POS_TOL_M
+    # integer identity at the final bin step, and the budget identity
+    assert int(cfix2.sum()) + int(ctr2[0]) == int(ctr2[6]) + int(ctr2[7])
+    assert b[0] - b[6] == pytest.approx(b[1] + b[2] + b[3] + b[4] + b[5], rel=1e-12)
+    assert b[0] == pytest.approx(oracle.total_mass(cfg), rel=1e-9)
+
+
+@pytest.mark.parametrize("block,ppt", [(128, 1), (256, 2), (256, 4), (512, 8), (128, 8)])
+def test_launch_shape_does_not_change_results(block, ppt):
+    """Results are bit-identical for every launch shape (integer binning, per-particle
+    keyed draws)."""
+    cfg = li.make_cfg1(n_particles=3001, n_steps=240, n_hours=5)
+    ref = run_gpu(cfg, launch=(256, 2))
+    g = run_gpu(cfg, launch=(block, ppt))
+    assert np.array_equal(g["pos"], ref["pos"]) and np.array_equal(g["tag"], ref["tag"])
+    assert np.array_equal(g["conc_fixed"], ref["conc_fixed"])
+    assert np.array_equal(g["dep_fixed"], ref["dep_fixed"])
+    assert np.array_equal(g["counters"], ref["counters"])
+
+
+def test_stepping_in_pieces_is_identical():
+    cfg = li.make_cfg1(n_particles=2000, n_steps=300, n_hours=4)
+    a = run_gpu(cfg)
+    b = run_gpu(cfg, pieces=[1, 7, 112, 3, 57, 120])
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["tag"], b["tag"])
+    assert np.array_equal(a["conc_fixed"], b["conc_fixed"])
+    assert np.array_equal(a["dep_fixed"], b["dep_fixed"])
+
+
+@pytest.mark.parametrize("n,first,last", [(1, 0, 50), (37, 0, 120), (1025, 3, 77),
+                                          (4099, 10, 200)])
+def test_ragged_and_sparse_releases(n, first, last):
+    """One particle, fewer particles than release steps (empty steps), ragged tile
+    tails and a delayed release window."""
+    base = li.make_cfg1(n_particles=n, n_steps=200, n_hours=4)
+    cfg = dataclasses.replace(base, bin_every=50,
+                              release=li.Release(n, np.array([1.0, 3.0, 0.5]), 1800.0,
+                                                 first, last))
+    g = run_gpu(cfg)
+    o = oracle.run(cfg)
+    compare(cfg, g, o)
+    _integer_identity(g)
+
+
+def test_gridded_kh_drift_and_emission_series():
+    """Gridded K_h, the drift-corrected variant and a 24-value emission series."""
+    base = li.make_cfg1(n_particles=5000, n_steps=240, n_hours=5)
+    rng = np.random.default_rng(9)
+    kh = (80.0 + 40.0 * rng.random(base.uvwk.shape[:-1])).astype(np.float32)
+    cfg = dataclasses.replace(base, kh=kh, kh_uniform=-1.0, drift_correction=1,
+                              release=li.Release(5000, np.exp(rng.normal(0, 0.5, 24)), 600.0,
+                                                 0, 240))
+    g = run_gpu(cfg)
+    o = oracle.run(cfg)
+    rep = compare(cfg, g, o)
+    print("gridded K_h + drift:", rep)
+
+
+def test_met_from_device_tensors():
+    cfg = li.make_cfg1(n_particles=2000, n_steps=120, n_hours=3)
+    a = run_gpu(cfg)
+    b = run_gpu(cfg, met_on_device=True)
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["conc_fixed"], b["conc_fixed"])
+
+
+def test_error_paths():
+    from paper_0912_3223_gb300 import lpm
+    cfg = li.make_cfg0(n_particles=100, n_steps=20)
+    ctx = lpm.lpm_create(cfg)
+    try:
+        # releasing out of order / stepping before every scenario is released
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_step(ctx, 1)
+        assert e.value.status == lpm.LPM_E_STATE
+        lpm.lpm_release(ctx, 0, 100, [1.0], 3600.0, 0, 20)
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_release(ctx, 0, 100, [1.0], 3600.0, 0, 20)
+        assert e.value.status == lpm.LPM_E_STATE
+        # met slab missing
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_step(ctx, 1)
+        assert e.value.status == lpm.LPM_E_STATE and "met slab" in str(e.value)
+        for t in range(cfg.n_met_t):
+            lpm.lpm_set_met(ctx, t, cfg.uvwk[t])
+        lpm.lpm_step(ctx, 20)
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_step(ctx, 1)
+        assert e.value.status == lpm.LPM_E_STATE
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_set_met(ctx, 5, cfg.uvwk[0])
+        assert e.value.status == lpm.LPM_E_INVALID
+    finally:
+        lpm.lpm_destroy(ctx)
+    # a NaN in the weather is reported as LPM_E_NUMERIC, the context stays usable
+    bad = dataclasses.replace(cfg, uvwk=cfg.uvwk.copy())
+    bad.uvwk[..., 0] = np.nan
+    from paper_0912_3223_gb300 import Sim
+    with Sim(bad) as sim:
+        sim.step(5)
+        with pytest.raises(lpm.LpmError) as e:
+            sim.sync()
+        assert e.value.status == lpm.LPM_E_NUMERIC
+    with Sim(cfg) as sim:
+        sim.step(cfg.n_steps)
+        sim.sync()
