@@ -63,6 +63,9 @@ struct lpm_ctx {
     unsigned int *d_queue = nullptr;
     float *d_m0 = nullptr;
     size_t d_m0_cap = 0;
+    unsigned char *d_zlut = nullptr;        // vertical level lookup table
+    int n_lut = 0;
+    float lut_z0 = 0.f, lut_inv_h = 0.f;
     ScenDev *d_scen = nullptr;
     float2 *d_woff = nullptr;               // [n_scen][n_met_t]
     Tile *d_tiles = nullptr;
@@ -202,6 +205,10 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.cx0 = (float)g.cx0; P.cy0 = (float)g.cy0; P.cz0 = (float)g.cz0;
     P.inv_cdx = (float)(1.0 / g.cdx); P.inv_cdy = (float)(1.0 / g.cdy);
     P.inv_cdz = (float)(1.0 / g.cdz);
+    P.zlut = c->n_lut > 0 ? c->d_zlut : nullptr;
+    P.n_lut = c->n_lut;
+    P.lut_z0 = c->lut_z0;
+    P.lut_inv_h = c->lut_inv_h;
     P.m0 = c->d_m0;
     P.scen = c->d_scen;
     P.err = c->d_err;
@@ -419,6 +426,31 @@ lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
     CREATE_CUDA(cudaMemsetAsync(c->d_dep, 0, ns * c->ndep() * sizeof(unsigned long long), c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->d_ctr, 0, ns * N_COUNTERS * sizeof(unsigned long long), c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
+    {
+        // vertical lookup table: bins of at most half the smallest level spacing, in the
+        // FP32 arithmetic the kernel uses to pick a bin
+        std::vector<float> zf(cfg->nz);
+        for (int k = 0; k < cfg->nz; ++k) zf[k] = (float)cfg->z_levels[k];
+        double min_sp = 1e300;
+        for (int k = 0; k + 1 < cfg->nz; ++k) min_sp = std::min(min_sp, (double)zf[k + 1] - zf[k]);
+        const double span = (double)zf[cfg->nz - 1] - zf[0];
+        const double n_need = min_sp > 0 ? std::ceil(span / (0.5 * min_sp)) + 1 : 1e300;
+        if (n_need <= MAX_LUT) {
+            c->n_lut = (int)n_need;
+            c->lut_z0 = zf[0];
+            c->lut_inv_h = (float)((c->n_lut - 1) / span);
+            std::vector<unsigned char> lut((size_t)c->n_lut);
+            for (int b = 0; b < c->n_lut; ++b) {
+                const double zb = (double)zf[0] + b / (double)c->lut_inv_h;
+                int k = 0;
+                for (int m = 0; m < cfg->nz; ++m)
+                    if ((double)zf[m] <= zb) k = m;
+                lut[(size_t)b] = (unsigned char)std::min(k, cfg->nz - 2);
+            }
+            CREATE_CUDA(cudaMalloc(&c->d_zlut, lut.size()));
+            CREATE_CUDA(cudaMemcpy(c->d_zlut, lut.data(), lut.size(), cudaMemcpyHostToDevice));
+        }
+    }
     CREATE_CUDA(cudaStreamSynchronize(c->stream));
 #undef CREATE_CUDA
     *out = c;
@@ -430,7 +462,8 @@ void lpm_destroy(lpm_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->d_uvwk, c->d_kh, c->d_rain, c->d_state, c->d_conc, c->d_dep, c->d_ctr,
-                    c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles};
+                    c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles,
+                    c->d_zlut};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

@@ -21,6 +21,7 @@ constexpr uint32_t ST_EXITED = 4u;
 constexpr int TAG_SHIFT = 28;
 constexpr uint32_t TAG_STEP = 0x0FFFFFFFu;
 constexpr int MAX_LEVELS = 64;
+constexpr int MAX_LUT = 4096;          // entries of the vertical level lookup table
 
 // Per-scenario counters (64-bit, fixed point unless noted).
 enum {
@@ -65,6 +66,9 @@ struct StepParams {
     float met_t0, met_dt;
     float x_lo, x_hi, y_lo, y_hi;
     float zlev[MAX_LEVELS];
+    const unsigned char *zlut;       // level at the start of each uniform z bin, or nullptr
+    int n_lut;
+    float lut_z0, lut_inv_h;         // bin b = (z - lut_z0) * lut_inv_h
     // time stepping and physics
     float dt, kh_uniform, k_scale, bias_u, bias_v;
     float lambda;                    // decay rate (1/s)
@@ -166,18 +170,58 @@ __device__ __forceinline__ void axis(float coord, float c0, float inv_d, int n, 
     a = fminf(fmaxf(f - (float)ii, 0.0f), 1.0f);
 }
 
-// Level search in the shared-memory copy of z_levels: last level <= z, clamped.
-__device__ __forceinline__ void level(const float *szl, int nz, float z, int &k, float &c)
+// Vertical cell: last level <= z, clamped to [0, nz-2]. With the lookup table (bins no
+// wider than half the smallest level spacing) one bin holds at most one level boundary,
+// so one step down and two steps up settle the exact answer; without it, bisection.
+struct Levels {
+    const float *z;                  // shared-memory copy of z_levels
+    const float *inv;                // 1 / (z[k+1] - z[k])
+    const unsigned char *lut;        // shared-memory copy of the table, or nullptr
+    int nz, n_lut;
+    float z0, inv_h;
+};
+
+__device__ __forceinline__ void level(const Levels &L, float z, int &k, float &c)
 {
-    int lo = 0, hi = nz - 1;          // invariant: szl[lo] <= z (or lo = 0), answer in [lo, hi)
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (szl[mid] <= z) lo = mid;
-        else hi = mid;
+    int kk;
+    if (L.lut) {
+        int b = (int)((z - L.z0) * L.inv_h);
+        b = min(max(b, 0), L.n_lut - 1);
+        kk = L.lut[b];
+        if (kk > 0 && z < L.z[kk]) --kk;
+        if (kk < L.nz - 2 && z >= L.z[kk + 1]) ++kk;
+        if (kk < L.nz - 2 && z >= L.z[kk + 1]) ++kk;
+    } else {
+        int lo = 0, hi = L.nz - 1;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (L.z[mid] <= z) lo = mid;
+            else hi = mid;
+        }
+        kk = lo;
     }
-    k = lo;
-    const float z0 = szl[lo], z1 = szl[lo + 1];
-    c = fminf(fmaxf((z - z0) / (z1 - z0), 0.0f), 1.0f);
+    k = kk;
+    c = fminf(fmaxf((z - L.z[kk]) * L.inv[kk], 0.0f), 1.0f);
+}
+
+// Fills the shared-memory level tables (call by the whole block, then __syncthreads()).
+__device__ __forceinline__ Levels load_levels(const StepParams &P, float *s_z, float *s_inv,
+                                              unsigned char *s_lut)
+{
+    for (int i = threadIdx.x; i < P.nz; i += blockDim.x) s_z[i] = P.zlev[i];
+    for (int i = threadIdx.x; i < P.nz - 1; i += blockDim.x)
+        s_inv[i] = 1.0f / (P.zlev[i + 1] - P.zlev[i]);
+    if (P.zlut)
+        for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.zlut[i];
+    Levels L;
+    L.z = s_z;
+    L.inv = s_inv;
+    L.lut = P.zlut ? s_lut : nullptr;
+    L.nz = P.nz;
+    L.n_lut = P.n_lut;
+    L.z0 = P.lut_z0;
+    L.inv_h = P.lut_inv_h;
+    return L;
 }
 
 struct Met {
@@ -190,14 +234,14 @@ __device__ __forceinline__ float4 lerp4(const float4 a, const float4 b, float t)
                        fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
 }
 
-__device__ __forceinline__ Met sample_met(const StepParams &P, const float *szl, const TimeSlab &ts,
+__device__ __forceinline__ Met sample_met(const StepParams &P, const Levels &L, const TimeSlab &ts,
                                           float x, float y, float z)
 {
     int i, j, k;
     float a, b, c;
     axis(x, P.x0, P.inv_dx, P.nx, i, a);
     axis(y, P.y0, P.inv_dy, P.ny, j, b);
-    level(szl, P.nz, z, k, c);
+    level(L, z, k, c);
     const long long nxny = (long long)P.nx * P.ny;
     const long long n00 = ((long long)k * P.ny + j) * P.nx + i;
     const float4 *s0 = P.uvwk + (long long)ts.h0 * P.slab + n00;
@@ -219,8 +263,8 @@ __device__ __forceinline__ Met sample_met(const StepParams &P, const float *szl,
     m.v = r.y;
     m.w = r.z;
     m.kz = fmaxf(r.w, 0.0f);
-    const bool inside = z >= szl[0] && z <= szl[P.nz - 1];
-    m.dkz = inside ? (y1.w - y0.w) / (szl[k + 1] - szl[k]) : 0.0f;
+    const bool inside = z >= L.z[0] && z <= L.z[P.nz - 1];
+    m.dkz = inside ? (y1.w - y0.w) * L.inv[k] : 0.0f;
     if (P.kh) {
         const float *h0 = P.kh + (long long)ts.h0 * P.slab + n00;
         const float *h1 = P.kh + (long long)ts.h1 * P.slab + n00;

@@ -79,11 +79,12 @@ __global__ void __launch_bounds__(BLOCK)
 advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__restrict__ tiles,
                int n_tiles, unsigned int *queue, long long plain_n, int k0, int k1, int do_bin)
 {
-    __shared__ float s_z[MAX_LEVELS];
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
     __shared__ unsigned long long s_acc[BLOCK];
     __shared__ int s_tile;
     __shared__ unsigned long long s_steps;
-    for (int i = threadIdx.x; i < P.nz; i += BLOCK) s_z[i] = P.zlev[i];
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     const int lane_base = threadIdx.x & ~31;
     unsigned long long *s_warp = s_acc + lane_base;
     const long long n_cells = (long long)P.cx * P.cy * P.cz;
@@ -165,7 +166,7 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
                 const long long gid = sc.id0 + (tile.first - sc.first_slot) + j * BLOCK +
                                       threadIdx.x;
                 // 1. weather at the old position and t_k; 2. diffusivities
-                const Met m = sample_met(P, s_z, ts, x[j], y[j], z[j]);
+                const Met m = sample_met(P, LV, ts, x[j], y[j], z[j]);
                 const float kh = P.k_scale * m.kh, kz = P.k_scale * m.kz;
                 // 3. N(0,1) draws
                 const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)((unsigned long long)gid >> 32),

@@ -99,11 +99,13 @@ def compare(cfg, g, o, pos_tol=POS_TOL_M, grid_tol=GRID_REL_L1, check_grid=True,
     particles (all of the release). Returns a report dict; asserts the bars."""
     rep = {}
     assert np.array_equal(g["release"], o["release"]), "release steps differ"
+    released = o["status"] != li.STATUS_UNRELEASED
+    assert np.array_equal(g["status"] == li.STATUS_UNRELEASED, ~released)
     # particles that took a decision within pos_tol of its boundary may branch either way
-    ambiguous = o["margin"] < pos_tol
+    ambiguous = (o["margin"] < pos_tol) & released
     rep["ambiguous"] = int(ambiguous.sum())
     assert ambiguous.mean() <= max_excluded_frac, rep
-    ok = ~ambiguous
+    ok = ~ambiguous & released
     st_eq = g["status"][ok] == o["status"][ok]
     assert st_eq.all(), f"{(~st_eq).sum()} status mismatches"
     dist = np.linalg.norm(g["pos"][ok] - o["pos"][ok], axis=1)
