@@ -169,6 +169,47 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------
+def measure_batched(args, stream, cfg=None):
+    """The batched ensemble form: 256 scenarios (log-uniform 1e4..1e6 particles, own
+    source, release height, 24-value emission series and wind offset), 12 h at dt = 30 s,
+    one persistent launch per run replayed from a CUDA graph."""
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = cfg or li.make_cfg2()
+    with torch.cuda.stream(stream):
+        sim = Sim(cfg, stream=stream, launch=(args.batched_block, args.batched_ppt,
+                                              args.batched_occ))
+    try:
+        for _ in range(max(1, args.warmup)):
+            sim.reset()
+            sim.step(cfg.n_steps)
+        torch.cuda.synchronize()
+        lpm.lpm_stats(sim.ctx)
+        times, active = [], 0
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            e0.record(stream)
+            sim.reset()
+            sim.step(cfg.n_steps)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            active += sum(int(sim.fixed_state(s)[2][4]) for s in range(cfg.n_scenarios))
+        launches, adv, _ = lpm.lpm_stats(sim.ctx)
+    finally:
+        sim.close()
+    t = sum(times) / 1e3
+    return {"value": active / t, "unit": UNIT, "ms_per_run": statistics.mean(times),
+            "scenarios": cfg.n_scenarios, "particles": cfg.n_particles,
+            "steps_per_run": cfg.n_steps, "graph_launches_per_run": adv // max(1, args.steps),
+            "kernel_launches_per_run": launches / max(1, args.steps),
+            "launch": [args.batched_block, args.batched_ppt, args.batched_occ]}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -194,7 +235,7 @@ def run_gpu(args):
         cfg = dataclasses.replace(cfg, seed=cfg.seed + rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt))
+        sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt, args.occ))
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
 
     def one_run():
@@ -261,6 +302,7 @@ def run_gpu(args):
         e2e_p += int(ctr[4])
     e2e_value = e2e_p / e2e_t
 
+    sim.close()
     peaks = read_peaks()
     alu_peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # Tops/s
     achieved = OPS_PER_PARTICLE_STEP * sum(active) / (adv_ms / 1e3) / 1e12 if adv_ms > 0 else None
@@ -282,7 +324,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": cfg.n_particles, "steps_per_run": cfg.n_steps,
                    "dt_s": cfg.dt, "met": [cfg.n_met_t, cfg.nz, cfg.ny, cfg.nx],
-                   "launch": [args.block, args.ppt],
+                   "launch": [args.block, args.ppt, args.occ],
                    "l2": "flushed (256 MB write) between timed steps",
                    "active_particle_steps_per_run": sum(active) // max(1, len(active)),
                    "slot_steps_per_run": cfg.n_particles * cfg.n_steps},
@@ -292,9 +334,13 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if not args.no_forms:
+        forms = {"batched": measure_batched(args, stream)}
+        for f in forms.values():
+            f["vs_plain"] = f["value"] / value
+        line["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, args.ref_stride)
-    sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -308,10 +354,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--block", type=int, default=256)
-    ap.add_argument("--ppt", type=int, default=2)
+    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--ppt", type=int, default=1)
+    ap.add_argument("--occ", type=int, default=1)
     ap.add_argument("--ref-stride", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and adjoint forms")
+    ap.add_argument("--batched-block", type=int, default=128)
+    ap.add_argument("--batched-ppt", type=int, default=1)
+    ap.add_argument("--batched-occ", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

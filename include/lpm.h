@@ -202,9 +202,12 @@ lpm_status lpm_particles(lpm_ctx *ctx, int64_t first, int64_t count, float *xyz,
 lpm_status lpm_fixed_state(lpm_ctx *ctx, int scenario, uint64_t *conc, size_t n_conc,
                            uint64_t *dep, size_t n_dep, int64_t counters[16], int *shift);
 
-/* Launch shape of the particle kernels: threads per block (128, 256 or 512) and
- * particles per thread (1, 2, 4 or 8). Default 256 x 2. Results do not depend on it. */
-lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread);
+/* Launch shape of the particle kernels: threads per block (128, 256 or 512), particles
+ * per thread (1, 2 or 4) and occupancy variant (0, 1, 2: at most 128, 80 or 64 registers
+ * per thread, i.e. 16, 24 or 32 resident warps per SM). Default 128 x 1 x 1. Results do
+ * not depend on it. The paper tuned its launch (32 blocks of 256 threads) with the
+ * occupancy calculator (Sec. 3.2); here the autotuner picks among these shapes. */
+lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int occupancy);
 
 /* Synchronises the context stream and reports device-side errors. */
 lpm_status lpm_sync(lpm_ctx *ctx);

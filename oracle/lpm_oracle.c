@@ -348,6 +348,93 @@ static int64_t fixed_of(double m, int shift)
     return (int64_t)nearbyint(ldexp(m, shift));
 }
 
+/* Per-run constants of the step. */
+typedef struct {
+    uint32_t t_dry, t_wet;
+    double x_lo, x_hi, y_lo, y_hi;
+} ostep;
+
+static ostep step_constants(const ocfg *c)
+{
+    ostep K;
+    K.t_dry = oracle_threshold(p_dry(c));
+    K.t_wet = oracle_threshold(p_wet(c));
+    K.x_lo = c->x0;
+    K.x_hi = c->x0 + (c->nx - 1) * c->dx;
+    K.y_lo = c->y0;
+    K.y_hi = c->y0 + (c->ny - 1) * c->dy;
+    return K;
+}
+
+/* One step k of one active particle, in the order of the paper's main loop (Sec. 3.2):
+ * sample the weather at the old position, compute K, move by the wind and by the
+ * random walk (Eq. 1-2), reflect, test the lateral boundary, then dry and wet
+ * deposition. Updates X; returns the new status. *margin is lowered to the distance of
+ * the particle from any decision boundary it met this step. Also returns, for the
+ * adjoint, the sign of dz/dz_pre from the folds (+1/-1, 0 if clamped), the normals and
+ * the weather sample. */
+static int particle_step(const ocfg *c, const ostep *K, uint64_t gid, int64_t k, double X[3],
+                         double *margin, double *fold, double nrm[3], double met[6])
+{
+    const double t = (double)k * c->dt;
+    /* 1. sample the weather at the old position and the step's start time */
+    oracle_interp(c, X[0], X[1], X[2], t, met);
+    /* 2. turbulent diffusion coefficients (K_h horizontal, K_z vertical) */
+    double kh = c->k_scale * met[4], kz = c->k_scale * met[3];
+    /* 3. N(0,1) draws for the three components */
+    oracle_normals(c->seed, gid, (uint32_t)k, nrm);
+    /* 4. Eq. (1)-(2): advection by the wind, then the random-walk displacement */
+    double u = met[0] + c->bias_u, v = met[1] + c->bias_v, w = met[2];
+    X[0] = X[0] + u * c->dt + nrm[0] * sqrt(2.0 * kh * c->dt);
+    X[1] = X[1] + v * c->dt + nrm[1] * sqrt(2.0 * kh * c->dt);
+    X[2] = X[2] + w * c->dt + nrm[2] * sqrt(2.0 * kz * c->dt);
+    if (c->drift_correction) X[2] += c->k_scale * met[5] * c->dt;
+    /* 5. reflection at the ground and the top, folded at most 4 times, then clamped */
+    *fold = 1.0;
+    for (int it = 0; it < 4; ++it) {
+        if (c->reflect_ground && X[2] < 0.0) { X[2] = -X[2]; *fold = -*fold; }
+        else if (c->reflect_top && X[2] > c->z_top) { X[2] = 2.0 * c->z_top - X[2]; *fold = -*fold; }
+        else break;
+    }
+    if (c->reflect_ground && X[2] < 0.0) { X[2] = 0.0; *fold = 0.0; }
+    if (c->reflect_top && X[2] > c->z_top) { X[2] = c->z_top; *fold = 0.0; }
+    /* leaving the horizontal domain inactivates the particle */
+    if (c->lateral_exit) {
+        double d = fmin(fmin(fabs(X[0] - K->x_lo), fabs(X[0] - K->x_hi)),
+                        fmin(fabs(X[1] - K->y_lo), fabs(X[1] - K->y_hi)));
+        if (d < *margin) *margin = d;
+        if (X[0] < K->x_lo || X[0] > K->x_hi || X[1] < K->y_lo || X[1] > K->y_hi)
+            return OR_EXITED;
+    }
+    /* 6. stochastic dry deposition below the mixing height, then wet deposition where it
+     *    rains (Sec. 2); one uniform word per test */
+    if (K->t_dry || K->t_wet) {
+        uint32_t dw[4];
+        oracle_draw(c->seed, gid, (uint32_t)k, 1u, dw);
+        if (K->t_dry && dw[0] < K->t_dry) {
+            double d = fabs(X[2] - c->h_mix);
+            if (d < *margin) *margin = d;
+            if (X[2] < c->h_mix) return OR_DEP_DRY;
+        }
+        if (K->t_wet && dw[1] < K->t_wet) {
+            double fx = (X[0] - c->x0) / c->dx + 0.5;
+            double fy = (X[1] - c->y0) / c->dy + 0.5;
+            double d = fmin(c->dx * fabs(fx - floor(fx + 0.5)), c->dy * fabs(fy - floor(fy + 0.5)));
+            if (d < *margin) *margin = d;
+            int ir = (int)floor(fx), jr = (int)floor(fy);
+            if (ir < 0) ir = 0;
+            if (ir > c->nx - 1) ir = c->nx - 1;
+            if (jr < 0) jr = 0;
+            if (jr > c->ny - 1) jr = c->ny - 1;
+            int hr = (int)floor((t - c->met_t0) / c->met_dt);
+            if (hr < 0) hr = 0;
+            if (hr > c->n_met_t - 1) hr = c->n_met_t - 1;
+            if (c->rain[((size_t)hr * c->ny + jr) * c->nx + ir]) return OR_DEP_WET;
+        }
+    }
+    return OR_ACTIVE;
+}
+
 /* Runs steps [0, n_run) for the particles listed in sel (local indices into the
  * release; NULL = all). Returns 0 on success, nonzero on invalid input. */
 int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, const oout *o)
@@ -358,10 +445,7 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
     size_t ncell = (size_t)c->cx * c->cy * c->cz, ndep = (size_t)2 * c->cx * c->cy;
     const int shift = oracle_fixed_shift(oracle_total_mass(c));
     const double lam = decay_rate(c);
-    const uint32_t t_dry = oracle_threshold(p_dry(c));
-    const uint32_t t_wet = oracle_threshold(p_wet(c));
-    const double x_lo = c->x0, x_hi = c->x0 + (c->nx - 1) * c->dx;
-    const double y_lo = c->y0, y_hi = c->y0 + (c->ny - 1) * c->dy;
+    const ostep K = step_constants(c);
 
     /* state */
     double *P = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -387,7 +471,6 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
     int64_t steps = 0;
 
     for (int64_t k = 0; k < n_run; ++k) {
-        const double t = (double)k * c->dt;
         for (int64_t q = 0; q < n; ++q) {
             int64_t p = sel ? sel[q] : q;
             uint64_t gid = (uint64_t)(c->pid_offset + p);
@@ -399,68 +482,17 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
             }
             if (st[q] != OR_ACTIVE) continue;
             ++steps;
-            /* 1. sample the weather at the old position and the step's start time */
-            double met[6];
-            oracle_interp(c, X[0], X[1], X[2], t, met);
-            /* 2. turbulent diffusion coefficients (K_h horizontal, K_z vertical) */
-            double kh = c->k_scale * met[4], kz = c->k_scale * met[3];
-            /* 3. N(0,1) draws for the three components */
-            double nrm[3];
-            oracle_normals(c->seed, gid, (uint32_t)k, nrm);
-            /* 4. Eq. (1)-(2): advection by the wind, then the random-walk displacement */
-            double u = met[0] + c->bias_u, v = met[1] + c->bias_v, w = met[2];
-            X[0] = X[0] + u * c->dt + nrm[0] * sqrt(2.0 * kh * c->dt);
-            X[1] = X[1] + v * c->dt + nrm[1] * sqrt(2.0 * kh * c->dt);
-            X[2] = X[2] + w * c->dt + nrm[2] * sqrt(2.0 * kz * c->dt);
-            if (c->drift_correction) X[2] += c->k_scale * met[5] * c->dt;
-            /* 5. reflection at the ground and the top, folded at most 4 times, then clamped */
-            for (int it = 0; it < 4; ++it) {
-                if (c->reflect_ground && X[2] < 0.0) X[2] = -X[2];
-                else if (c->reflect_top && X[2] > c->z_top) X[2] = 2.0 * c->z_top - X[2];
-                else break;
+            double fold, nrm[3], met[6];
+            int ns = particle_step(c, &K, gid, k, X, &mg[q], &fold, nrm, met);
+            if (ns == OR_EXITED) {
+                st[q] = OR_EXITED;
+                tev[q] = k;
+                exited += oracle_mass_at(c, sp[q], k);
+                o->counters[3] += fixed_of(oracle_mass_at(c, sp[q], k), shift);
+                continue;
             }
-            if (c->reflect_ground && X[2] < 0.0) X[2] = 0.0;
-            if (c->reflect_top && X[2] > c->z_top) X[2] = c->z_top;
-            /* leaving the horizontal domain inactivates the particle */
-            if (c->lateral_exit) {
-                double d = fmin(fmin(fabs(X[0] - x_lo), fabs(X[0] - x_hi)),
-                                fmin(fabs(X[1] - y_lo), fabs(X[1] - y_hi)));
-                if (d < mg[q]) mg[q] = d;
-                if (X[0] < x_lo || X[0] > x_hi || X[1] < y_lo || X[1] > y_hi) {
-                    st[q] = OR_EXITED;
-                    tev[q] = k;
-                    exited += oracle_mass_at(c, sp[q], k);
-                    o->counters[3] += fixed_of(oracle_mass_at(c, sp[q], k), shift);
-                    continue;
-                }
-            }
-            /* 6. stochastic dry deposition below the mixing height, then wet deposition
-             *    where it rains (Sec. 2); one uniform word per test */
-            if (t_dry || t_wet) {
-                uint32_t dw[4];
-                oracle_draw(c->seed, gid, (uint32_t)k, 1u, dw);
-                int kind = -1;
-                if (t_dry && dw[0] < t_dry) {
-                    double d = fabs(X[2] - c->h_mix);
-                    if (d < mg[q]) mg[q] = d;
-                    if (X[2] < c->h_mix) kind = 0;
-                }
-                if (kind < 0 && t_wet && dw[1] < t_wet) {
-                    double fx = (X[0] - c->x0) / c->dx + 0.5;
-                    double fy = (X[1] - c->y0) / c->dy + 0.5;
-                    double d = fmin(c->dx * fabs(fx - floor(fx + 0.5)),
-                                    c->dy * fabs(fy - floor(fy + 0.5)));
-                    if (d < mg[q]) mg[q] = d;
-                    int ir = (int)floor(fx), jr = (int)floor(fy);
-                    if (ir < 0) ir = 0;
-                    if (ir > c->nx - 1) ir = c->nx - 1;
-                    if (jr < 0) jr = 0;
-                    if (jr > c->ny - 1) jr = c->ny - 1;
-                    int hr = (int)floor((t - c->met_t0) / c->met_dt);
-                    if (hr < 0) hr = 0;
-                    if (hr > c->n_met_t - 1) hr = c->n_met_t - 1;
-                    if (c->rain[((size_t)hr * c->ny + jr) * c->nx + ir]) kind = 1;
-                }
+            {
+                int kind = ns == OR_DEP_DRY ? 0 : ns == OR_DEP_WET ? 1 : -1;
                 if (kind >= 0) {
                     st[q] = kind == 0 ? OR_DEP_DRY : OR_DEP_WET;
                     tev[q] = k;

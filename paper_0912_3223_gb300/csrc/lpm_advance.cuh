@@ -1,0 +1,356 @@
+// lpm_advance.cuh - the particle step of the paper's main loop (Sec. 3.2, Eq. 1-2),
+// fused over a whole segment of steps with the particle state in registers, in-kernel
+// deposition, and the concentration snapshot (every n-th step) at the segment end.
+// Instantiated per block size in lpm_advance_b*.cu.
+#pragma once
+
+#include "lpm_device.cuh"
+#include "lpm_launch.h"
+
+namespace lpm {
+
+constexpr int KEY_NONE = -1;
+constexpr int KEY_OUT = -2;
+
+// Warp-aggregated 64-bit fixed-point accumulation: lanes holding the same key add their
+// values once through the lowest lane of the group (key KEY_NONE: nothing; KEY_OUT: the
+// out-of-grid counter). Every lane of the warp must call it.
+__device__ __forceinline__ void warp_accumulate(int key, unsigned long long v,
+                                                unsigned long long *grid,
+                                                unsigned long long *out_ctr,
+                                                unsigned long long *s_warp, long long n_cells,
+                                                unsigned int *err)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    s_warp[lane] = v;
+    __syncwarp();
+    if (key != KEY_NONE && lane == __ffs(peers) - 1) {
+        unsigned long long sum = 0;
+        unsigned m = peers;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            sum += s_warp[b];
+            m &= m - 1;
+        }
+        if (key == KEY_OUT) atomicAdd(out_ctr, sum);
+        else if (key < n_cells) atomicAdd(grid + key, sum);
+        else atomicOr(err, ERR_INDEX);
+    }
+    __syncwarp();
+}
+
+// Weather at a point from the time-paired records: 8 spatial corners, each one 32-byte
+// load of (slab h, slab h+1), blended in time, then in x, y and z.
+__device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels &L,
+                                               const float4 *__restrict__ pair,
+                                               const float2 *__restrict__ khp, float f,
+                                               float x, float y, float z)
+{
+    int i, j, k;
+    float a, b, c;
+    axis(x, P.x0, P.inv_dx, P.nx, i, a);
+    axis(y, P.y0, P.inv_dy, P.ny, j, b);
+    level(L, z, k, c);
+    const int nx = P.nx, nxny = P.nx * P.ny;
+    const int n00 = (k * P.ny + j) * nx + i;
+    float4 q[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int off = (m & 1) + ((m >> 1) & 1) * nx + ((m >> 2) & 1) * nxny;
+        float4 lo, hi;
+        ld_pair(pair + 2 * (n00 + off), lo, hi);
+        q[m] = lerp4(lo, hi, f);
+    }
+    const float4 x00 = lerp4(q[0], q[1], a), x10 = lerp4(q[2], q[3], a);
+    const float4 x01 = lerp4(q[4], q[5], a), x11 = lerp4(q[6], q[7], a);
+    const float4 y0 = lerp4(x00, x10, b), y1 = lerp4(x01, x11, b);
+    const float4 r = lerp4(y0, y1, c);
+    Met m;
+    m.u = r.x;
+    m.v = r.y;
+    m.w = r.z;
+    m.kz = fmaxf(r.w, 0.0f);
+    const bool inside = z >= L.z[0] && z <= L.z[P.nz - 1];
+    m.dkz = inside ? (y1.w - y0.w) * L.inv[k] : 0.0f;
+    if (khp) {
+        float e[8];
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+            const int off = (mm & 1) + ((mm >> 1) & 1) * nx + ((mm >> 2) & 1) * nxny;
+            const float2 v = __ldg(khp + n00 + off);
+            e[mm] = fmaf(f, v.y - v.x, v.x);
+        }
+        const float ex0 = fmaf(a, e[1] - e[0], e[0]), ex1 = fmaf(a, e[3] - e[2], e[2]);
+        const float ex2 = fmaf(a, e[5] - e[4], e[4]), ex3 = fmaf(a, e[7] - e[6], e[6]);
+        const float ey0 = fmaf(b, ex1 - ex0, ex0), ey1 = fmaf(b, ex3 - ex2, ex2);
+        m.kh = fmaxf(fmaf(c, ey1 - ey0, ey0), 0.0f);
+    } else {
+        m.kh = 0.0f;
+    }
+    return m;
+}
+
+__device__ __forceinline__ float mass_at(const StepParams &P, const ScenDev &sc, int sp, int k_end)
+{
+    // decayed mass at the end of step k_end (age (k_end + 1 - s_p) dt), Sec. 2 / Sec. 3.2
+    const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
+    const float age = (float)(k_end + 1 - sp) * P.dt;
+    return m0 * expf(-P.lambda * age);
+}
+
+// Occupancy variants: the register budget per thread is 128 (OCC 0), 80 (OCC 1) or 64
+// (OCC 2), i.e. 16, 24 or 32 resident warps per SM.
+template <int BLOCK, int OCC>
+struct MinBlocks {
+    static constexpr int per_sm_threads = OCC == 0 ? 512 : OCC == 1 ? 768 : 1024;
+    static constexpr int value = per_sm_threads / BLOCK > 0 ? per_sm_threads / BLOCK : 1;
+};
+
+// Advance: each thread keeps PPT particles in registers and runs steps [k0, k1). Tiles
+// are implicit (plain form: tile t = slots [t*T, t*T+T) of scenario 0) or taken from a
+// table through an atomic queue by a persistent grid (batched form).
+template <int BLOCK, int PPT, int OCC>
+__global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
+advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__restrict__ tiles,
+               int n_tiles, unsigned int *queue, long long plain_n, int k0, int k1, int do_bin)
+{
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
+    __shared__ unsigned long long s_acc[BLOCK];
+    __shared__ int s_tile;
+    __shared__ unsigned long long s_steps;
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    unsigned long long *s_warp = s_acc + (threadIdx.x & ~31);
+    const long long n_cells = (long long)P.cx * P.cy * P.cz;
+    const long long n_dep = (long long)P.cx * P.cy;
+    constexpr int TILE = BLOCK * PPT;
+    // the uniform horizontal diffusivity gives one displacement scale for the run
+    const float sig_h_uniform = sqrt_approx(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
+
+    int iter = 0;
+    for (;;) {
+        // ---- fetch a tile -----------------------------------------------------------
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t;
+            if (tiles) t = (int)atomicAdd(queue, 1u);
+            else t = blockIdx.x + iter * gridDim.x;
+            s_tile = t;
+            s_steps = 0ull;
+        }
+        __syncthreads();
+        const int t = s_tile;
+        ++iter;
+        if (t >= n_tiles) break;
+        Tile tile;
+        if (tiles) {
+            tile = tiles[t];
+        } else {
+            tile.scen = 0;
+            tile.first = (long long)t * TILE;
+            tile.count = (int)min((long long)TILE, plain_n - tile.first);
+        }
+        const ScenDev &scg = P.scen[tile.scen];
+        const ScenDev sc = scg;
+        const long long gid0 = sc.id0 + (tile.first - sc.first_slot) + threadIdx.x;
+
+        // ---- load particles ---------------------------------------------------------
+        float x[PPT], y[PPT], z[PPT];
+        uint32_t tag[PPT];
+        int live = 0;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int local = j * BLOCK + threadIdx.x;
+            if (local < tile.count) {
+                const float4 s = state[tile.first + local];
+                x[j] = s.x; y[j] = s.y; z[j] = s.z;
+                tag[j] = __float_as_uint(s.w);
+                const uint32_t st = tag[j] >> TAG_SHIFT;
+                const int sp = (int)(tag[j] & TAG_STEP);
+                if (st == ST_ACTIVE || (st == ST_UNRELEASED && sp < k1)) ++live;
+            } else {
+                x[j] = y[j] = z[j] = 0.0f;
+                tag[j] = ST_EXITED << TAG_SHIFT;
+            }
+        }
+
+        // ---- time loop --------------------------------------------------------------
+        unsigned long long steps = 0;
+#pragma unroll 1
+        for (int k = k0; k < k1 && live > 0; ++k) {
+            const float tk = (float)k * P.dt;
+            const TimeSlab ts = time_slab(P, tk);
+            const float4 *pair = P.pair + (long long)ts.h0 * P.slab * 2;
+            const float2 *khp = P.khpair ? P.khpair + (long long)ts.h0 * P.slab : nullptr;
+            float du = P.bias_u, dv = P.bias_v;
+            if (sc.wind_offset) {
+                const float2 o0 = __ldg(sc.wind_offset + ts.h0);
+                const float2 o1 = __ldg(sc.wind_offset + ts.h1);
+                du += fmaf(ts.f, o1.x - o0.x, o0.x);
+                dv += fmaf(ts.f, o1.y - o0.y, o0.y);
+            }
+            live = 0;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                uint32_t st = tag[j] >> TAG_SHIFT;
+                const int sp = (int)(tag[j] & TAG_STEP);
+                if (st == ST_UNRELEASED && sp == k) {
+                    st = ST_ACTIVE;
+                    x[j] = sc.src_x; y[j] = sc.src_y; z[j] = sc.src_z;
+                }
+                if (st != ST_ACTIVE) {
+                    if (st == ST_UNRELEASED && sp < k1) ++live;
+                    continue;
+                }
+                ++steps;
+                const unsigned long long gid = (unsigned long long)(gid0 + j * BLOCK);
+                // 1. weather at the old position and t_k; 2. diffusivities
+                const Met m = sample_met_pair(P, LV, pair, khp, ts.f, x[j], y[j], z[j]);
+                const float sig_h = khp ? sqrt_approx(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
+                const float sig_z = sqrt_approx(2.0f * P.k_scale * m.kz * P.dt);
+                // 3. N(0,1) draws
+                const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
+                                           P.seed_lo, P.seed_hi);
+                float n0, n1, n2;
+                normals3(w, n0, n1, n2);
+                // 4. Eq. (1)-(2): wind then turbulent displacement
+                const float xn = x[j] + (m.u + du) * P.dt + n0 * sig_h;
+                const float yn = y[j] + (m.v + dv) * P.dt + n1 * sig_h;
+                float zn = z[j] + m.w * P.dt + n2 * sig_z;
+                if (P.drift) zn += P.k_scale * m.dkz * P.dt;
+                // 5. reflection, at most 4 folds, then clamp
+#pragma unroll 1
+                for (int it = 0; it < 4; ++it) {
+                    if (P.reflect_ground && zn < 0.0f) zn = -zn;
+                    else if (P.reflect_top && zn > P.z_top) zn = 2.0f * P.z_top - zn;
+                    else break;
+                }
+                if (P.reflect_ground && zn < 0.0f) zn = 0.0f;
+                if (P.reflect_top && zn > P.z_top) zn = P.z_top;
+                x[j] = xn; y[j] = yn; z[j] = zn;
+                if (!isfinite(xn + yn + zn)) {
+                    atomicOr(P.err, ERR_NAN);
+                    tag[j] = (ST_EXITED << TAG_SHIFT) | (uint32_t)sp;
+                    continue;
+                }
+                // lateral boundary
+                if (P.lateral_exit && (xn < P.x_lo || xn > P.x_hi || yn < P.y_lo || yn > P.y_hi)) {
+                    st = ST_EXITED;
+                    atomicAdd(scg.ctr + C_EXITED * P.ctr_stride,
+                              to_fixed(mass_at(P, sc, sp, k), sc.scale));
+                } else if (P.t_dry | P.t_wet) {
+                    // 6. dry deposition below the mixing height, then wet where it rains
+                    const U4 d = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 1u,
+                                               P.seed_lo, P.seed_hi);
+                    int kind = -1;
+                    if (d.a < P.t_dry && zn < P.h_mix) kind = 0;
+                    if (kind < 0 && d.b < P.t_wet && P.rain) {
+                        int ir = (int)floorf((xn - P.x0) * P.inv_dx + 0.5f);
+                        int jr = (int)floorf((yn - P.y0) * P.inv_dy + 0.5f);
+                        ir = min(max(ir, 0), P.nx - 1);
+                        jr = min(max(jr, 0), P.ny - 1);
+                        int hr = (int)floorf(__fdiv_rn(tk - P.met_t0, P.met_dt));
+                        hr = min(max(hr, 0), P.n_t - 1);
+                        if (__ldg(P.rain + ((long long)hr * P.ny + jr) * P.nx + ir)) kind = 1;
+                    }
+                    if (kind >= 0) {
+                        st = kind == 0 ? ST_DEP_DRY : ST_DEP_WET;
+                        const unsigned long long v = to_fixed(mass_at(P, sc, sp, k), sc.scale);
+                        const int ix = (int)floorf((xn - P.cx0) * P.inv_cdx);
+                        const int iy = (int)floorf((yn - P.cy0) * P.inv_cdy);
+                        if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy) {
+                            const long long cell = ((long long)kind * P.cy + iy) * P.cx + ix;
+                            if (cell < 2 * n_dep) atomicAdd(scg.dep + cell, v);
+                        } else {
+                            atomicAdd(scg.ctr + (C_DEP_OUT_DRY + kind) * P.ctr_stride, v);
+                        }
+                        atomicAdd(scg.ctr + (C_DEP_DRY + kind) * P.ctr_stride, v);
+                    }
+                }
+                tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
+                if (st == ST_ACTIVE) ++live;
+            }
+        }
+
+        // ---- store ------------------------------------------------------------------
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const int local = j * BLOCK + threadIdx.x;
+            if (local < tile.count)
+                state[tile.first + local] = make_float4(x[j], y[j], z[j], __uint_as_float(tag[j]));
+        }
+
+        // ---- end-of-segment concentration snapshot (every n-th step, Sec. 3.2) --------
+        if (do_bin) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int local = j * BLOCK + threadIdx.x;
+                int key = KEY_NONE;
+                unsigned long long v = 0ull;
+                const uint32_t st = tag[j] >> TAG_SHIFT;
+                if (local < tile.count && st == ST_ACTIVE) {
+                    const int sp = (int)(tag[j] & TAG_STEP);
+                    v = to_fixed(mass_at(P, sc, sp, k1 - 1), sc.scale);
+                    const int ix = (int)floorf((x[j] - P.cx0) * P.inv_cdx);
+                    const int iy = (int)floorf((y[j] - P.cy0) * P.inv_cdy);
+                    const int iz = (int)floorf((z[j] - P.cz0) * P.inv_cdz);
+                    if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz)
+                        key = (iz * P.cy + iy) * P.cx + ix;
+                    else
+                        key = KEY_OUT;
+                }
+                warp_accumulate(key, v, scg.conc, scg.ctr + C_BIN_OUT * P.ctr_stride, s_warp,
+                                n_cells, P.err);
+            }
+        }
+
+        // ---- active particle-steps of the tile -----------------------------------------
+        for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+        if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&s_steps, steps);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_steps) atomicAdd(scg.ctr + C_ACTIVE_STEPS * P.ctr_stride, s_steps);
+    }
+}
+
+template <int BLOCK, int PPT, int OCC>
+cudaError_t launch_adv(const AdvanceLaunch &L)
+{
+    advance_kernel<BLOCK, PPT, OCC><<<L.grid, BLOCK, 0, L.stream>>>(
+        *L.params, L.state, L.tiles, L.n_tiles, L.queue, L.plain_n, L.k0, L.k1, L.do_bin);
+    return cudaGetLastError();
+}
+
+template <int BLOCK, int PPT, int OCC>
+int occ_adv()
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC>, BLOCK, 0);
+    return n;
+}
+
+// (particles per thread, occupancy variant) -> instantiation, for one block size
+#define LPM_ADV_CASES(FN, BLOCK, ...)                                                  \
+    case 10: return FN<BLOCK, 1, 0>(__VA_ARGS__);                                      \
+    case 11: return FN<BLOCK, 1, 1>(__VA_ARGS__);                                      \
+    case 12: return FN<BLOCK, 1, 2>(__VA_ARGS__);                                      \
+    case 20: return FN<BLOCK, 2, 0>(__VA_ARGS__);                                      \
+    case 21: return FN<BLOCK, 2, 1>(__VA_ARGS__);                                      \
+    case 22: return FN<BLOCK, 2, 2>(__VA_ARGS__);                                      \
+    case 40: return FN<BLOCK, 4, 0>(__VA_ARGS__);                                      \
+    case 41: return FN<BLOCK, 4, 1>(__VA_ARGS__);                                      \
+    case 42: return FN<BLOCK, 4, 2>(__VA_ARGS__);
+
+#define LPM_ADVANCE_TU(BLOCK)                                                          \
+    cudaError_t launch_advance_b##BLOCK(const AdvanceLaunch &L)                         \
+    {                                                                                  \
+        switch (L.ppt * 10 + L.occ) { LPM_ADV_CASES(launch_adv, BLOCK, L) }            \
+        return cudaErrorInvalidValue;                                                  \
+    }                                                                                  \
+    int occupancy_b##BLOCK(int ppt, int occ)                                           \
+    {                                                                                  \
+        switch (ppt * 10 + occ) { LPM_ADV_CASES(occ_adv, BLOCK) }                      \
+        return 0;                                                                      \
+    }
+
+}  // namespace lpm

@@ -1,0 +1,7 @@
+// Advance-kernel instantiations for 512-thread blocks (one translation unit per block
+// size so that nvcc compiles them in parallel).
+#include "lpm_advance.cuh"
+
+namespace lpm {
+LPM_ADVANCE_TU(512)
+}  // namespace lpm

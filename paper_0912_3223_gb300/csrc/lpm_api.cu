@@ -48,8 +48,10 @@ struct lpm_ctx {
     std::string err;
 
     // weather
-    float4 *d_uvwk = nullptr;
+    float4 *d_uvwk = nullptr;               // slabs as given [n_t][nodes]
     float *d_kh = nullptr;
+    float4 *d_pair = nullptr;               // time-paired slabs [n_pair][nodes][2]
+    float2 *d_khpair = nullptr;             // [n_pair][nodes]
     uint8_t *d_rain = nullptr;
     std::vector<char> met_set;
     bool any_rain = false;
@@ -58,7 +60,7 @@ struct lpm_ctx {
     float4 *d_state = nullptr;
     unsigned long long *d_conc = nullptr;   // [n_scen][cz*cy*cx]
     unsigned long long *d_dep = nullptr;    // [n_scen][2*cy*cx]
-    unsigned long long *d_ctr = nullptr;    // [n_scen][N_COUNTERS]
+    unsigned long long *d_ctr = nullptr;    // [N_COUNTERS][n_scen]
     unsigned int *d_err = nullptr;
     unsigned int *d_queue = nullptr;
     float *d_m0 = nullptr;
@@ -84,12 +86,19 @@ struct lpm_ctx {
     bool tables_dirty = true;
     long long k = 0;                        // steps taken
     long long n_bins = 0;                   // snapshots taken
-    int block = 256, ppt = 2;
+    int block = 128, ppt = 1, occ = 1;
+
+    // batched form: one CUDA graph per segment (memsets + the persistent launch)
+    struct Graph {
+        long long k0, k1;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
 
     // batched tile schedule
     std::vector<Tile> tiles;
-    int tiles_for_k1 = -1;
-    int tiles_block = 0, tiles_ppt = 0;
+    std::vector<long long> tile_sp;         // release step of each tile's first particle
+    bool tiles_valid = false;
 
     size_t ncell() const { return (size_t)cfg.cx * cfg.cy * cfg.cz; }
     size_t ndep() const { return (size_t)2 * cfg.cx * cfg.cy; }
@@ -97,6 +106,7 @@ struct lpm_ctx {
 
 namespace {
 
+void drop_graphs(lpm_ctx *c);
 lpm_status fail(lpm_ctx *c, lpm_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
 
 lpm_status fail(lpm_ctx *c, lpm_status s, const char *fmt, ...)
@@ -172,8 +182,8 @@ void fill_params(const lpm_ctx *c, StepParams &P)
 {
     const lpm_config &g = c->cfg;
     std::memset(&P, 0, sizeof P);
-    P.uvwk = c->d_uvwk;
-    P.kh = c->d_kh;
+    P.pair = c->d_pair;
+    P.khpair = c->d_khpair;
     P.rain = c->any_rain ? c->d_rain : nullptr;
     P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.n_t = g.n_met_t;
     P.slab = (long long)g.nx * g.ny * g.nz;
@@ -211,6 +221,8 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.lut_inv_h = c->lut_inv_h;
     P.m0 = c->d_m0;
     P.scen = c->d_scen;
+    P.n_scen = g.n_scenarios;
+    P.ctr_stride = g.n_scenarios;
     P.err = c->d_err;
 }
 
@@ -255,7 +267,9 @@ lpm_status upload_tables(lpm_ctx *c)
         }
         d.conc = c->d_conc + s * c->ncell();
         d.dep = c->d_dep + s * c->ndep();
-        d.ctr = c->d_ctr + s * N_COUNTERS;
+        d.ctr = c->d_ctr + s;
+        d.n_total = h.n_total;
+        d.part_first = h.part_first;
     }
     if (m0.empty()) m0.push_back(0.f);
     if (m0.size() > c->d_m0_cap) {
@@ -270,6 +284,7 @@ lpm_status upload_tables(lpm_ctx *c)
     LPM_CUDA(c, cudaMemcpy(c->d_scen, sd.data(), sd.size() * sizeof(ScenDev), cudaMemcpyHostToDevice));
     LPM_CUDA(c, cudaMemcpy(c->d_woff, woff.data(), woff.size() * sizeof(float2), cudaMemcpyHostToDevice));
     c->tables_dirty = false;
+    drop_graphs(c);
     return LPM_OK;
 }
 
@@ -295,21 +310,21 @@ long long released_before(const ScenHost &h, long long k1)
     return std::max(0LL, std::min(upto - h.part_first, h.n));
 }
 
-// Batched schedule: tiles of BLOCK*PPT particles of one scenario, only particles released
-// before k1, longest-running (earliest released) first.
-lpm_status build_tiles(lpm_ctx *c, long long k1)
+// Batched schedule: tiles of BLOCK*PPT consecutive particles of one scenario, ordered by
+// the release step of their first particle (longest-running first). A segment ending at
+// step k1 runs the prefix of tiles whose first particle leaves before k1.
+lpm_status build_tiles(lpm_ctx *c)
 {
     const int T = c->block * c->ppt;
     std::vector<std::pair<long long, Tile>> items;
     for (size_t s = 0; s < c->scen.size(); ++s) {
         const ScenHost &h = c->scen[s];
         const long long S = h.rel_last - h.rel_first;
-        const long long n_rel = released_before(h, k1);
-        for (long long p = 0; p < n_rel; p += T) {
+        for (long long p = 0; p < h.n; p += T) {
             Tile t;
             t.scen = (int)s;
             t.first = h.first_slot + p;
-            t.count = (int)std::min<long long>(T, n_rel - p);
+            t.count = (int)std::min<long long>(T, h.n - p);
             const long long sp = h.rel_first + ((h.part_first + p) * S) / h.n_total;
             items.push_back({sp, t});
         }
@@ -317,7 +332,11 @@ lpm_status build_tiles(lpm_ctx *c, long long k1)
     std::stable_sort(items.begin(), items.end(),
                      [](const auto &a, const auto &b) { return a.first < b.first; });
     c->tiles.clear();
-    for (auto &it : items) c->tiles.push_back(it.second);
+    c->tile_sp.clear();
+    for (auto &it : items) {
+        c->tiles.push_back(it.second);
+        c->tile_sp.push_back(it.first);
+    }
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     if (c->tiles.size() > c->d_tiles_cap) {
         if (c->d_tiles) cudaFree(c->d_tiles);
@@ -328,18 +347,7 @@ lpm_status build_tiles(lpm_ctx *c, long long k1)
     if (!c->tiles.empty())
         LPM_CUDA(c, cudaMemcpy(c->d_tiles, c->tiles.data(), c->tiles.size() * sizeof(Tile),
                                cudaMemcpyHostToDevice));
-    return LPM_OK;
-}
-
-lpm_status relaunch_releases(lpm_ctx *c)
-{
-    for (const ScenHost &h : c->scen) {
-        if (!h.released) continue;
-        LPM_CUDA(c, launch_release(c->stream, c->d_state, h.first_slot, h.n, h.part_first,
-                                   h.n_total, (int)h.rel_first, (int)(h.rel_last - h.rel_first),
-                                   (float)h.src_x, (float)h.src_y, (float)h.src_z));
-        c->n_launches++;
-    }
+    c->tiles_valid = true;
     return LPM_OK;
 }
 
@@ -365,6 +373,21 @@ lpm_status collect_events(lpm_ctx *c)
     }
     c->ev_used = 0;
     return LPM_OK;
+}
+
+lpm_status read_counters(lpm_ctx *c, int scenario, unsigned long long v[N_COUNTERS])
+{
+    const size_t ns = (size_t)c->cfg.n_scenarios;
+    for (int i = 0; i < N_COUNTERS; ++i)
+        LPM_CUDA(c, cudaMemcpy(v + i, c->d_ctr + i * ns + scenario, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost));
+    return LPM_OK;
+}
+
+void drop_graphs(lpm_ctx *c)
+{
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
 }
 
 }  // namespace
@@ -409,9 +432,13 @@ lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
     CREATE_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
     const size_t nodes = (size_t)cfg->nx * cfg->ny * cfg->nz;
     const size_t ns = (size_t)cfg->n_scenarios;
+    const size_t n_pair = (size_t)std::max(1, cfg->n_met_t - 1);
     CREATE_CUDA(cudaMalloc(&c->d_uvwk, nodes * cfg->n_met_t * sizeof(float4)));
-    if (cfg->kh_uniform < 0)
+    CREATE_CUDA(cudaMalloc(&c->d_pair, nodes * n_pair * 2 * sizeof(float4)));
+    if (cfg->kh_uniform < 0) {
         CREATE_CUDA(cudaMalloc(&c->d_kh, nodes * cfg->n_met_t * sizeof(float)));
+        CREATE_CUDA(cudaMalloc(&c->d_khpair, nodes * n_pair * sizeof(float2)));
+    }
     CREATE_CUDA(cudaMalloc(&c->d_rain, (size_t)cfg->nx * cfg->ny * cfg->n_met_t));
     CREATE_CUDA(cudaMemsetAsync(c->d_rain, 0, (size_t)cfg->nx * cfg->ny * cfg->n_met_t, c->stream));
     CREATE_CUDA(cudaMalloc(&c->d_state, (size_t)cfg->max_particles * sizeof(float4)));
@@ -461,12 +488,13 @@ void lpm_destroy(lpm_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    void *ptrs[] = {c->d_uvwk, c->d_kh, c->d_rain, c->d_state, c->d_conc, c->d_dep, c->d_ctr,
+    void *ptrs[] = {c->d_uvwk, c->d_kh, c->d_pair, c->d_khpair, c->d_rain, c->d_state, c->d_conc, c->d_dep, c->d_ctr,
                     c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles,
                     c->d_zlut};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    drop_graphs(c);
     delete c;
 }
 
@@ -495,13 +523,26 @@ lpm_status lpm_set_met(lpm_ctx *c, int t_index, const float *uvwk, const float *
                                     c->stream));
     if (rain) {
         LPM_CUDA(c, cudaMemcpyAsync(c->d_rain + cols * t_index, rain, cols, kind, c->stream));
+        if (!c->any_rain) drop_graphs(c);    // captured launches baked in "no rain"
         c->any_rain = true;
     } else {
         LPM_CUDA(c, cudaMemsetAsync(c->d_rain + cols * t_index, 0, cols, c->stream));
     }
+    c->met_set[(size_t)t_index] = 1;
+    // time pairs (h, h+1) that this slab completes
+    for (int h = t_index - 1; h <= t_index; ++h) {
+        const int h1 = g.n_met_t > 1 ? h + 1 : h;
+        if (h < 0 || h1 > g.n_met_t - 1 || (g.n_met_t > 1 && h > g.n_met_t - 2)) continue;
+        if (!c->met_set[(size_t)h] || !c->met_set[(size_t)h1]) continue;
+        LPM_CUDA(c, launch_pack(c->stream, c->d_uvwk + nodes * h, c->d_uvwk + nodes * h1,
+                                c->d_kh ? c->d_kh + nodes * h : nullptr,
+                                c->d_kh ? c->d_kh + nodes * h1 : nullptr,
+                                c->d_pair + nodes * 2 * h, c->d_khpair ? c->d_khpair + nodes * h : nullptr,
+                                (long long)nodes));
+        c->n_launches++;
+    }
     // host sources must be consumed before returning (the caller owns them)
     if (!on_device) LPM_CUDA(c, cudaStreamSynchronize(c->stream));
-    c->met_set[(size_t)t_index] = 1;
     return LPM_OK;
 }
 
@@ -578,7 +619,7 @@ lpm_status lpm_release_range(lpm_ctx *c, int scenario, int64_t n_total, int64_t 
     c->n_ids_used = std::max<long long>(c->n_ids_used, id_base + n_total);
     c->n_released++;
     c->tables_dirty = true;
-    c->tiles_for_k1 = -1;
+    c->tiles_valid = false;
     LPM_CUDA(c, launch_release(c->stream, c->d_state, h.first_slot, h.n, h.part_first, h.n_total,
                                (int)first, (int)(last - first), (float)h.src_x, (float)h.src_y,
                                (float)h.src_z));
@@ -601,8 +642,12 @@ lpm_status lpm_reset(lpm_ctx *c)
     LPM_CUDA(c, cudaMemsetAsync(c->d_dep, 0, ns * c->ndep() * sizeof(unsigned long long), c->stream));
     LPM_CUDA(c, cudaMemsetAsync(c->d_ctr, 0, ns * N_COUNTERS * sizeof(unsigned long long), c->stream));
     LPM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
-    lpm_status st = relaunch_releases(c);
+    lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
+    StepParams P;
+    fill_params(c, P);
+    LPM_CUDA(c, launch_release_all(c->stream, P, c->d_state, c->n_slots_used));
+    c->n_launches++;
     c->k = 0;
     c->n_bins = 0;
     return LPM_OK;
@@ -632,15 +677,18 @@ lpm_status lpm_stats(lpm_ctx *c, int64_t *launches, int64_t *advance_launches,
     return LPM_OK;
 }
 
-lpm_status lpm_set_launch(lpm_ctx *c, int block, int ppt)
+lpm_status lpm_set_launch(lpm_ctx *c, int block, int ppt, int occupancy)
 {
     if (!c) return LPM_E_INVALID;
-    if (!(block == 128 || block == 256 || block == 512) ||
-        !(ppt == 1 || ppt == 2 || ppt == 4 || ppt == 8))
-        return fail(c, LPM_E_INVALID, "launch shape %d x %d not supported", block, ppt);
+    if (!(block == 128 || block == 256 || block == 512) || !(ppt == 1 || ppt == 2 || ppt == 4) ||
+        occupancy < 0 || occupancy > 2)
+        return fail(c, LPM_E_INVALID, "launch shape %d x %d (occupancy %d) not supported", block, ppt,
+                    occupancy);
     c->block = block;
     c->ppt = ppt;
-    c->tiles_for_k1 = -1;
+    c->occ = occupancy;
+    c->tiles_valid = false;
+    drop_graphs(c);
     return LPM_OK;
 }
 
@@ -677,14 +725,6 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
         long long next_bin = (k / g.bin_every + 1) * (long long)g.bin_every;
         long long e = std::min(k_end, std::min(next_bin, (long long)g.n_steps));
         const bool do_bin = (e % g.bin_every == 0) || e == g.n_steps;
-        if (do_bin) {
-            LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0,
-                                        (size_t)g.n_scenarios * c->ncell() * sizeof(unsigned long long),
-                                        c->stream));
-            for (int s = 0; s < g.n_scenarios; ++s)
-                LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + (size_t)s * N_COUNTERS + C_BIN_OUT, 0,
-                                            sizeof(unsigned long long), c->stream));
-        }
         AdvanceLaunch L{};
         L.stream = c->stream;
         L.params = &P;
@@ -694,37 +734,81 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
         L.do_bin = do_bin ? 1 : 0;
         L.block = c->block;
         L.ppt = c->ppt;
+        L.occ = c->occ;
         const int T = c->block * c->ppt;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->profiling) {
+            e0 = next_event(c);
+            e1 = next_event(c);
+            if (!e0 || !e1) return fail(c, LPM_E_CUDA, "cudaEventCreate failed");
+        }
         if (!batched) {
+            if (do_bin) {
+                LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0, c->ncell() * sizeof(unsigned long long),
+                                            c->stream));
+                LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + C_BIN_OUT, 0, sizeof(unsigned long long),
+                                            c->stream));
+            }
             const long long n_rel = released_before(c->scen[0], e);
             L.tiles = nullptr;
             L.plain_n = n_rel;
             L.n_tiles = (int)((n_rel + T - 1) / T);
             L.queue = c->d_queue;
             L.grid = (unsigned)std::max(1, L.n_tiles);
+            if (L.n_tiles > 0) {
+                if (e0) LPM_CUDA(c, cudaEventRecord(e0, c->stream));
+                LPM_CUDA(c, launch_advance(L));
+                if (e1) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
+                c->n_launches++;
+                c->n_adv_launches++;
+            } else if (e0) {
+                c->ev_used -= 2;
+            }
         } else {
-            if (c->tiles_for_k1 != (int)e) {
-                st = build_tiles(c, e);
+            if (!c->tiles_valid) {
+                st = build_tiles(c);
                 if (st != LPM_OK) return st;
-                c->tiles_for_k1 = (int)e;
             }
-            LPM_CUDA(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), c->stream));
-            L.tiles = c->d_tiles;
-            L.n_tiles = (int)c->tiles.size();
-            L.queue = c->d_queue;
-            const int occ = std::max(1, advance_occupancy(c->block, c->ppt));
-            L.grid = (unsigned)std::max(1, std::min(L.n_tiles, occ * c->sm_count));
-        }
-        if (L.n_tiles > 0) {
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (c->profiling) {
-                e0 = next_event(c);
-                e1 = next_event(c);
-                if (!e0 || !e1) return fail(c, LPM_E_CUDA, "cudaEventCreate failed");
-                LPM_CUDA(c, cudaEventRecord(e0, c->stream));
+            cudaGraphExec_t exec = nullptr;
+            for (auto &gr : c->graphs)
+                if (gr.k0 == k && gr.k1 == e) exec = gr.exec;
+            if (!exec) {
+                // the segment as one graph: snapshot reset, queue reset, persistent launch
+                L.tiles = c->d_tiles;
+                L.n_tiles = (int)(std::lower_bound(c->tile_sp.begin(), c->tile_sp.end(), e) -
+                                  c->tile_sp.begin());
+                L.queue = c->d_queue;
+                const int occ = std::max(1, advance_occupancy(c->block, c->ppt, c->occ));
+                L.grid = (unsigned)std::max(1, std::min(std::max(1, L.n_tiles), occ * c->sm_count));
+                LPM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t ce = cudaSuccess;
+                if (do_bin) {
+                    ce = cudaMemsetAsync(c->d_conc, 0, (size_t)g.n_scenarios * c->ncell() *
+                                                           sizeof(unsigned long long), c->stream);
+                    if (ce == cudaSuccess)
+                        ce = cudaMemsetAsync(c->d_ctr + (size_t)C_BIN_OUT * g.n_scenarios, 0,
+                                             (size_t)g.n_scenarios * sizeof(unsigned long long),
+                                             c->stream);
+                }
+                if (ce == cudaSuccess)
+                    ce = cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), c->stream);
+                if (ce == cudaSuccess && L.n_tiles > 0) ce = launch_advance(L);
+                cudaGraph_t graph = nullptr;
+                cudaError_t ce2 = cudaStreamEndCapture(c->stream, &graph);
+                if (ce != cudaSuccess || ce2 != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return fail(c, LPM_E_CUDA, "capturing the batched segment failed: %s",
+                                cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+                }
+                ce = cudaGraphInstantiate(&exec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (ce != cudaSuccess)
+                    return fail(c, LPM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
+                c->graphs.push_back({k, e, exec});
             }
-            LPM_CUDA(c, launch_advance(L));
-            if (c->profiling) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
+            if (e0) LPM_CUDA(c, cudaEventRecord(e0, c->stream));
+            LPM_CUDA(c, cudaGraphLaunch(exec, c->stream));
+            if (e1) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
             c->n_launches++;
             c->n_adv_launches++;
         }
@@ -792,8 +876,10 @@ lpm_status lpm_budget(lpm_ctx *c, int scenario, double out[8])
     if (!h.released) return fail(c, LPM_E_STATE, "scenario %d not released", scenario);
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
-    unsigned long long *ctr = c->d_ctr + (size_t)scenario * N_COUNTERS;
-    LPM_CUDA(c, cudaMemsetAsync(ctr + C_AIR_IN, 0, 3 * sizeof(unsigned long long), c->stream));
+    const size_t ns = (size_t)c->cfg.n_scenarios;
+    for (int i : {(int)C_AIR_IN, (int)C_AIR_OUT, (int)C_N_ACTIVE})
+        LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + i * ns + scenario, 0, sizeof(unsigned long long),
+                                    c->stream));
     StepParams P;
     fill_params(c, P);
     LPM_CUDA(c, launch_budget(c->stream, P, c->d_state, scenario, h.n, (int)c->k));
@@ -801,7 +887,8 @@ lpm_status lpm_budget(lpm_ctx *c, int scenario, double out[8])
     st = check_device_error(c);
     if (st != LPM_OK) return st;
     unsigned long long v[N_COUNTERS];
-    LPM_CUDA(c, cudaMemcpy(v, ctr, sizeof v, cudaMemcpyDeviceToHost));
+    st = read_counters(c, scenario, v);
+    if (st != LPM_OK) return st;
     const double f = std::ldexp(1.0, -h.shift);
     // initial mass of the held particles released before the current step
     double released = 0.0;
@@ -867,8 +954,8 @@ lpm_status lpm_fixed_state(lpm_ctx *c, int scenario, uint64_t *conc, size_t n_co
                                n_dep * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     if (counters) {
         unsigned long long v[N_COUNTERS];
-        LPM_CUDA(c, cudaMemcpy(v, c->d_ctr + (size_t)scenario * N_COUNTERS, sizeof v,
-                               cudaMemcpyDeviceToHost));
+        st = read_counters(c, scenario, v);
+        if (st != LPM_OK) return st;
         for (int i = 0; i < 16; ++i) counters[i] = (int64_t)v[i];
         counters[C_N_BINS] = c->n_bins;
     }

@@ -39,13 +39,15 @@ struct ScenDev {
     long long first_slot;            // state slot of the scenario's first particle here
     long long n;                     // particles of the scenario held by this context
     long long id0;                   // global id (generator key) of that first particle
+    long long n_total;               // particles of the whole release
+    long long part_first;            // index in the release of the first held particle
     int rel_first, rel_last;         // release steps [first, last)
     int m0_off;                      // offset of the scenario's initial-mass table
     int pad;
     const float2 *wind_offset;       // [n_met_t] (du, dv) or nullptr
     unsigned long long *conc;        // [cz][cy][cx]
     unsigned long long *dep;         // [2][cy][cx]
-    unsigned long long *ctr;         // [N_COUNTERS]
+    unsigned long long *ctr;         // counter i of this scenario at ctr[i * ctr_stride]
 };
 
 // A tile = a contiguous run of particles of one scenario processed by one block.
@@ -56,9 +58,9 @@ struct Tile {
 };
 
 struct StepParams {
-    // weather
-    const float4 *uvwk;              // [n_t][nz][ny][nx]
-    const float *kh;                 // [n_t][nz][ny][nx] or nullptr
+    // weather, time-paired: pair[h][node] = (slab h, slab h+1) as two float4 (32 B aligned)
+    const float4 *pair;              // [n_pair][nz][ny][nx][2], n_pair = max(1, n_t - 1)
+    const float2 *khpair;            // [n_pair][nz][ny][nx] (K_h at h, h+1) or nullptr
     const uint8_t *rain;             // [n_t][ny][nx] or nullptr
     int nx, ny, nz, n_t;
     long long slab;                  // nodes per slab
@@ -82,6 +84,8 @@ struct StepParams {
     // tables
     const float *m0;                 // initial mass per release step (all scenarios)
     const ScenDev *scen;
+    int n_scen;
+    int ctr_stride;                  // counters are laid out [N_COUNTERS][n_scen]
     unsigned int *err;
 };
 
@@ -114,6 +118,22 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
     return U4{c0, c1, c2, c3};
 }
 
+// 32-byte read-only load (sm_100+ 256-bit vector load); p must be 32-byte aligned.
+__device__ __forceinline__ void ld_pair(const float4 *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+// Square root on the special-function unit (relative error ~2^-23), for x >= 0.
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Uniform on (0,1): midpoint of one of 2^23 equal bins, exact in FP32.
 __device__ __forceinline__ float unit_uniform(uint32_t w)
 {
@@ -126,13 +146,16 @@ __device__ __forceinline__ void normals3(const U4 &w, float &n0, float &n1, floa
 {
     const float u0 = unit_uniform(w.a), u1 = unit_uniform(w.b);
     const float u2 = unit_uniform(w.c), u3 = unit_uniform(w.d);
-    const float r0 = sqrtf(-2.0f * logf(u0));
-    const float r1 = sqrtf(-2.0f * logf(u2));
+    // radius from the accurate logarithm (u close to 1 needs it), angle from the
+    // special-function unit on [0, 2pi) (absolute error ~4e-7)
+    const float r0 = sqrt_approx(-2.0f * logf(u0));
+    const float r1 = sqrt_approx(-2.0f * logf(u2));
+    const float two_pi = 6.28318530717958647692f;
     float s1, c1;
-    sincospif(2.0f * u1, &s1, &c1);
+    __sincosf(two_pi * u1, &s1, &c1);
     n0 = r0 * c1;
     n1 = r0 * s1;
-    n2 = r1 * cospif(2.0f * u3);
+    n2 = r1 * __cosf(two_pi * u3);
 }
 
 // ---------------------------------------------------------------------------------
@@ -232,58 +255,6 @@ __device__ __forceinline__ float4 lerp4(const float4 a, const float4 b, float t)
 {
     return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y),
                        fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
-}
-
-__device__ __forceinline__ Met sample_met(const StepParams &P, const Levels &L, const TimeSlab &ts,
-                                          float x, float y, float z)
-{
-    int i, j, k;
-    float a, b, c;
-    axis(x, P.x0, P.inv_dx, P.nx, i, a);
-    axis(y, P.y0, P.inv_dy, P.ny, j, b);
-    level(L, z, k, c);
-    const long long nxny = (long long)P.nx * P.ny;
-    const long long n00 = ((long long)k * P.ny + j) * P.nx + i;
-    const float4 *s0 = P.uvwk + (long long)ts.h0 * P.slab + n00;
-    const float4 *s1 = P.uvwk + (long long)ts.h1 * P.slab + n00;
-    // 16 corners: (di, dj, dk) x 2 time slabs, blended in time first
-    float4 q[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const long long off = (m & 1) + ((m >> 1) & 1) * (long long)P.nx + ((m >> 2) & 1) * nxny;
-        q[m] = lerp4(__ldg(s0 + off), __ldg(s1 + off), ts.f);
-    }
-    // x, then y, then z
-    const float4 x00 = lerp4(q[0], q[1], a), x10 = lerp4(q[2], q[3], a);
-    const float4 x01 = lerp4(q[4], q[5], a), x11 = lerp4(q[6], q[7], a);
-    const float4 y0 = lerp4(x00, x10, b), y1 = lerp4(x01, x11, b);
-    const float4 r = lerp4(y0, y1, c);
-    Met m;
-    m.u = r.x;
-    m.v = r.y;
-    m.w = r.z;
-    m.kz = fmaxf(r.w, 0.0f);
-    const bool inside = z >= L.z[0] && z <= L.z[P.nz - 1];
-    m.dkz = inside ? (y1.w - y0.w) * L.inv[k] : 0.0f;
-    if (P.kh) {
-        const float *h0 = P.kh + (long long)ts.h0 * P.slab + n00;
-        const float *h1 = P.kh + (long long)ts.h1 * P.slab + n00;
-        float e[8];
-#pragma unroll
-        for (int mm = 0; mm < 8; ++mm) {
-            const long long off = (mm & 1) + ((mm >> 1) & 1) * (long long)P.nx +
-                                  ((mm >> 2) & 1) * nxny;
-            const float v0 = __ldg(h0 + off), v1 = __ldg(h1 + off);
-            e[mm] = fmaf(ts.f, v1 - v0, v0);
-        }
-        const float ex0 = fmaf(a, e[1] - e[0], e[0]), ex1 = fmaf(a, e[3] - e[2], e[2]);
-        const float ex2 = fmaf(a, e[5] - e[4], e[4]), ex3 = fmaf(a, e[7] - e[6], e[6]);
-        const float ey0 = fmaf(b, ex1 - ex0, ex0), ey1 = fmaf(b, ex3 - ex2, ex2);
-        m.kh = fmaxf(fmaf(c, ey1 - ey0, ey0), 0.0f);
-    } else {
-        m.kh = fmaxf(P.kh_uniform, 0.0f);
-    }
-    return m;
 }
 
 // Fixed-point mass: round-to-nearest-even of m * 2^shift (scale is an exact power of 2).

@@ -14,15 +14,24 @@ struct AdvanceLaunch {
     unsigned int *queue;      // work-queue counter (zeroed before the launch)
     long long plain_n;        // implicit tiles: particles [0, plain_n)
     int k0, k1, do_bin;
-    int block, ppt;
+    int block, ppt, occ;
     unsigned int grid;
 };
 
 cudaError_t launch_release(cudaStream_t s, float4 *state, long long first_slot, long long count,
                            long long part_first, long long n_total, int rel_first, int rel_len,
                            float sx, float sy, float sz);
+cudaError_t launch_release_all(cudaStream_t s, const StepParams &P, float4 *state, long long n_slots);
 cudaError_t launch_advance(const AdvanceLaunch &L);
-int advance_occupancy(int block, int ppt);
+int advance_occupancy(int block, int ppt, int occ);
+cudaError_t launch_advance_b128(const AdvanceLaunch &L);
+cudaError_t launch_advance_b256(const AdvanceLaunch &L);
+cudaError_t launch_advance_b512(const AdvanceLaunch &L);
+int occupancy_b128(int ppt, int occ);
+int occupancy_b256(int ppt, int occ);
+int occupancy_b512(int ppt, int occ);
+cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
+                        const float *kb, float4 *pair, float2 *khpair, long long nodes);
 cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned long long *pid,
                          const unsigned int *step, unsigned int stream, long long n, uint4 *words,
                          float *nrm);

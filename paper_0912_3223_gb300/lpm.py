@@ -86,7 +86,7 @@ def load() -> C.CDLL:
     L.lpm_fixed_state.argtypes = [vp, C.c_int, C.POINTER(C.c_uint64), C.c_size_t,
                                   C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(i64),
                                   C.POINTER(C.c_int)]
-    L.lpm_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    L.lpm_set_launch.argtypes = [vp, C.c_int, C.c_int, C.c_int]
     L.lpm_sync.argtypes = [vp]
     L.lpm_release_range.argtypes = [vp, C.c_int, i64, i64, i64, dp, C.c_int, C.c_double, i64,
                                     i64, i64]
@@ -261,8 +261,9 @@ def lpm_fixed_state(ctx, scenario: int, conc_shape, dep_shape):
     return conc, dep, ctr, int(sh.value)
 
 
-def lpm_set_launch(ctx, block: int, particles_per_thread: int) -> None:
-    _check(ctx, load().lpm_set_launch(C.c_void_p(ctx), int(block), int(particles_per_thread)))
+def lpm_set_launch(ctx, block: int, particles_per_thread: int, occupancy: int = 1) -> None:
+    _check(ctx, load().lpm_set_launch(C.c_void_p(ctx), int(block), int(particles_per_thread),
+                                      int(occupancy)))
 
 
 def lpm_sync(ctx) -> None:

@@ -1,0 +1,121 @@
+"""Batched ensemble: many scenarios (own source, release, emission series, wind offset)
+in one persistent launch replayed from a CUDA graph, checked against the oracle scenario
+by scenario, against single-scenario contexts bit for bit, and across graph replays."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import lpm_inputs as li
+import oracle
+from parity_util import compare
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0912_3223_gb300 import build
+    build.build()
+    oracle.build()
+
+
+@pytest.fixture(scope="module")
+def small_ensemble():
+    return li.make_cfg2(n_scenarios=6, n_steps=240, n_min=500, n_max=3000)
+
+
+def _run(cfg, launch=None, repeat=1):
+    from paper_0912_3223_gb300 import Sim
+    out = []
+    with Sim(cfg, launch=launch) as sim:
+        for _ in range(repeat):
+            sim.reset()
+            sim.step(cfg.n_steps)
+            xyz, tag = sim.particles()
+            scen = []
+            for s in range(cfg.n_scenarios):
+                c, d, k, sh = sim.fixed_state(s)
+                scen.append(dict(conc=sim.concentration(s), dep=sim.deposition(s),
+                                 conc_fixed=c, dep_fixed=d, counters=k, budget=sim.budget(s)))
+            out.append((xyz, tag, scen))
+    return out
+
+
+def test_batched_matches_oracle_per_scenario(small_ensemble):
+    cfg = small_ensemble
+    (xyz, tag, scen), = _run(cfg)
+    off = 0
+    vol = cfg.cdx * cfg.cdy * cfg.cdz
+    area = cfg.cdx * cfg.cdy
+    for s, sc in enumerate(cfg.scenarios):
+        n = sc.release.n_particles
+        o = oracle.run(cfg, scenario=s)
+        g = dict(pos=xyz[off:off + n].astype(np.float64), tag=tag[off:off + n],
+                 status=(tag[off:off + n] >> 28).astype(np.int32),
+                 release=(tag[off:off + n] & 0x0FFFFFFF).astype(np.int64),
+                 conc_mass=scen[s]["conc"] * vol,
+                 dep_mass=np.stack(scen[s]["dep"]) * area)
+        rep = compare(cfg, g, o)
+        print(f"scenario {s}: {rep}")
+        c = scen[s]["counters"]
+        assert int(c[4]) == o["active_steps"]
+        off += n
+
+
+def test_graph_replay_is_identical(small_ensemble):
+    a, b = _run(small_ensemble, repeat=2)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for sa, sb in zip(a[2], b[2]):
+        assert np.array_equal(sa["conc_fixed"], sb["conc_fixed"])
+        assert np.array_equal(sa["dep_fixed"], sb["dep_fixed"])
+
+
+def test_scenario_equals_single_context(small_ensemble):
+    """Scenario s of the ensemble equals a plain context holding the same release with the
+    same global ids (id_base), source and wind offset."""
+    from paper_0912_3223_gb300 import lpm
+    cfg = small_ensemble
+    (xyz, tag, scen), = _run(cfg)
+    s = 3
+    sc = cfg.scenarios[s]
+    off = sum(x.release.n_particles for x in cfg.scenarios[:s])
+    one = dataclasses.replace(cfg, n_scenarios=1, scenarios=[], src_x=sc.src_x, src_y=sc.src_y,
+                              src_z=sc.src_z, release=sc.release)
+    ctx = lpm.lpm_create(one, torch.cuda.current_stream().cuda_stream,
+                         max_particles=sc.release.n_particles)
+    try:
+        for t in range(one.n_met_t):
+            lpm.lpm_set_met(ctx, t, one.uvwk[t], None, one.rain[t])
+        lpm.lpm_set_source(ctx, 0, sc.src_x, sc.src_y, sc.src_z, sc.wind_offset)
+        r = sc.release
+        lpm.lpm_release_range(ctx, 0, r.n_particles, 0, r.n_particles, r.q, r.q_dt,
+                              r.first_step, r.last_step, off)
+        lpm.lpm_step(ctx, one.n_steps)
+        pxyz, ptag = lpm.lpm_particles(ctx, 0, r.n_particles)
+        c, d, k, _ = lpm.lpm_fixed_state(ctx, 0, (one.cz, one.cy, one.cx), (2, one.cy, one.cx))
+    finally:
+        lpm.lpm_destroy(ctx)
+    n = sc.release.n_particles
+    assert np.array_equal(pxyz, xyz[off:off + n]) and np.array_equal(ptag, tag[off:off + n])
+    assert np.array_equal(c, scen[s]["conc_fixed"])
+    assert np.array_equal(d, scen[s]["dep_fixed"])
+
+
+def test_autotuner_keeps_results(small_ensemble, tmp_path, monkeypatch):
+    from paper_0912_3223_gb300 import Sim
+    from paper_0912_3223_gb300.autotune import autotune
+    monkeypatch.setenv("LPM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    ref = _run(small_ensemble)[0]
+    with Sim(small_ensemble) as sim:
+        shapes = [(128, 1, 2), (256, 2, 1), (512, 4, 0)]
+        shape = autotune(sim, shapes=shapes, reps=1)
+        assert shape in shapes
+        sim.step(small_ensemble.n_steps)
+        xyz, tag = sim.particles()
+        again = autotune(sim)                        # served from the cache
+        assert again == shape
+    assert np.array_equal(xyz, ref[0]) and np.array_equal(tag, ref[1])

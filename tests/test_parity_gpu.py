@@ -144,13 +144,14 @@ def test_cfg1_full_size_sampled():
     assert b[0] == pytest.approx(oracle.total_mass(cfg), rel=1e-9)
 
 
-@pytest.mark.parametrize("block,ppt", [(128, 1), (256, 2), (256, 4), (512, 8), (128, 8)])
-def test_launch_shape_does_not_change_results(block, ppt):
+@pytest.mark.parametrize("block,ppt,occ", [(128, 1, 0), (128, 1, 2), (256, 2, 1), (256, 4, 0),
+                                           (512, 1, 2), (512, 4, 1), (128, 4, 2)])
+def test_launch_shape_does_not_change_results(block, ppt, occ):
     """Results are bit-identical for every launch shape (integer binning, per-particle
     keyed draws)."""
     cfg = li.make_cfg1(n_particles=3001, n_steps=240, n_hours=5)
-    ref = run_gpu(cfg, launch=(256, 2))
-    g = run_gpu(cfg, launch=(block, ppt))
+    ref = run_gpu(cfg, launch=(256, 2, 0))
+    g = run_gpu(cfg, launch=(block, ppt, occ))
     assert np.array_equal(g["pos"], ref["pos"]) and np.array_equal(g["tag"], ref["tag"])
     assert np.array_equal(g["conc_fixed"], ref["conc_fixed"])
     assert np.array_equal(g["dep_fixed"], ref["dep_fixed"])
