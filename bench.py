@@ -354,16 +354,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--ppt", type=int, default=1)
-    ap.add_argument("--occ", type=int, default=1)
+    ap.add_argument("--occ", type=int, default=2)
     ap.add_argument("--ref-stride", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms")
-    ap.add_argument("--batched-block", type=int, default=128)
+    ap.add_argument("--batched-block", type=int, default=256)
     ap.add_argument("--batched-ppt", type=int, default=1)
-    ap.add_argument("--batched-occ", type=int, default=1)
+    ap.add_argument("--batched-occ", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

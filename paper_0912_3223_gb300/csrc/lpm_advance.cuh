@@ -126,7 +126,7 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
     const long long n_dep = (long long)P.cx * P.cy;
     constexpr int TILE = BLOCK * PPT;
     // the uniform horizontal diffusivity gives one displacement scale for the run
-    const float sig_h_uniform = sqrt_approx(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
+    const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
 
     int iter = 0;
     for (;;) {
@@ -207,8 +207,8 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
                 const unsigned long long gid = (unsigned long long)(gid0 + j * BLOCK);
                 // 1. weather at the old position and t_k; 2. diffusivities
                 const Met m = sample_met_pair(P, LV, pair, khp, ts.f, x[j], y[j], z[j]);
-                const float sig_h = khp ? sqrt_approx(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
-                const float sig_z = sqrt_approx(2.0f * P.k_scale * m.kz * P.dt);
+                const float sig_h = khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
+                const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
                 // 3. N(0,1) draws
                 const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
                                            P.seed_lo, P.seed_hi);

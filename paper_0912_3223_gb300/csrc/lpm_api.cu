@@ -43,6 +43,7 @@ struct lpm_ctx {
     lpm_config cfg{};
     std::vector<double> zlev;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;      // private stream the batched graphs are captured on
     int device = 0;
     int sm_count = 0;
     std::string err;
@@ -86,7 +87,7 @@ struct lpm_ctx {
     bool tables_dirty = true;
     long long k = 0;                        // steps taken
     long long n_bins = 0;                   // snapshots taken
-    int block = 128, ppt = 1, occ = 1;
+    int block = 256, ppt = 1, occ = 2;
 
     // batched form: one CUDA graph per segment (memsets + the persistent launch)
     struct Graph {
@@ -495,6 +496,7 @@ void lpm_destroy(lpm_ctx *c)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -780,21 +782,26 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
                 L.queue = c->d_queue;
                 const int occ = std::max(1, advance_occupancy(c->block, c->ppt, c->occ));
                 L.grid = (unsigned)std::max(1, std::min(std::max(1, L.n_tiles), occ * c->sm_count));
-                LPM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                // captured on a private stream (the caller's may be the legacy stream,
+                // which cannot be captured); the graph is launched on the caller's stream
+                if (!c->cap_stream)
+                    LPM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+                const cudaStream_t cs = c->cap_stream;
+                L.stream = cs;
+                LPM_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
                 cudaError_t ce = cudaSuccess;
                 if (do_bin) {
                     ce = cudaMemsetAsync(c->d_conc, 0, (size_t)g.n_scenarios * c->ncell() *
-                                                           sizeof(unsigned long long), c->stream);
+                                                           sizeof(unsigned long long), cs);
                     if (ce == cudaSuccess)
                         ce = cudaMemsetAsync(c->d_ctr + (size_t)C_BIN_OUT * g.n_scenarios, 0,
                                              (size_t)g.n_scenarios * sizeof(unsigned long long),
-                                             c->stream);
+                                             cs);
                 }
-                if (ce == cudaSuccess)
-                    ce = cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), c->stream);
+                if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), cs);
                 if (ce == cudaSuccess && L.n_tiles > 0) ce = launch_advance(L);
                 cudaGraph_t graph = nullptr;
-                cudaError_t ce2 = cudaStreamEndCapture(c->stream, &graph);
+                cudaError_t ce2 = cudaStreamEndCapture(cs, &graph);
                 if (ce != cudaSuccess || ce2 != cudaSuccess) {
                     if (graph) cudaGraphDestroy(graph);
                     return fail(c, LPM_E_CUDA, "capturing the batched segment failed: %s",

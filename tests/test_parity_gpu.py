@@ -71,7 +71,7 @@ def test_artificial_weather_of_the_paper():
     compare(cfg, g, o)
     gf = run_gpu(cfg)
     of = oracle.run(cfg)
-    rep = compare(cfg, gf, of, pos_tol=5.0, grid_tol=1e-3)
+    rep = compare(cfg, gf, of, pos_tol=5.0, grid_tol=1e-3, max_excluded_frac=0.05)
     print("artificial weather after 6 h:", rep)
     _integer_identity(gf)
 
@@ -108,7 +108,7 @@ def test_cfg1_full_run_report(cfg1_small):
     distances grow; they are reported, with a loose bar, and the exact invariants hold."""
     g = run_gpu(cfg1_small)
     o = oracle.run(cfg1_small)
-    rep = compare(cfg1_small, g, o, pos_tol=10.0, check_grid=False, max_excluded_frac=0.05)
+    rep = compare(cfg1_small, g, o, pos_tol=10.0, check_grid=False, max_excluded_frac=0.3)
     print("cfg1 24 h:", rep)
     _integer_identity(g)
     b = g["budget"]
