@@ -99,6 +99,15 @@ def lib():
         L.oracle_run.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_int64), C.c_int64, C.c_int64,
                                  C.POINTER(OOut)]
         L.oracle_run.restype = C.c_int
+        dp = C.POINTER(C.c_double)
+        i64p = C.POINTER(C.c_int64)
+        L.oracle_receptors.argtypes = [C.POINTER(OCfg), dp, C.c_int, C.c_double, C.c_int, i64p,
+                                       C.c_int64, C.c_int64, dp]
+        L.oracle_adjoint.argtypes = [C.POINTER(OCfg), dp, C.c_int, C.c_double, C.c_int, dp, i64p,
+                                     C.c_int64, C.c_int64, dp]
+        L.oracle_sensitivity.argtypes = [C.POINTER(OCfg), i64p, C.c_int64, C.c_int64, dp]
+        for f in (L.oracle_receptors, L.oracle_adjoint, L.oracle_sensitivity):
+            f.restype = C.c_int
         _lib = L
     return _lib
 
@@ -268,4 +277,54 @@ def run(cfg, sel=None, n_run: Optional[int] = None, **kw) -> dict:
     if rc != 0:
         raise ValueError(f"oracle_run rejected the configuration (code {rc})")
     out["active_steps"] = int(out["counters"][4])
+    return out
+
+
+def receptors(cfg, rec, sigma: float, every: int, sel=None, n_run: Optional[int] = None,
+              **kw) -> np.ndarray:
+    """Receptor concentrations C[R] (Gaussian kernel of width sigma with the ground image,
+    averaged over the sample steps (k+1) % every == 0)."""
+    o = make_ocfg(cfg, **kw)
+    rec = np.ascontiguousarray(rec, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros(rec.shape[0])
+    n_run = cfg.n_steps if n_run is None else n_run
+    sel_a = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+    rc = lib().oracle_receptors(C.byref(o), _ptr(rec, C.c_double), rec.shape[0], float(sigma),
+                                int(every), _ptr(sel_a, C.c_int64),
+                                0 if sel_a is None else sel_a.size, int(n_run),
+                                _ptr(out, C.c_double))
+    if rc:
+        raise ValueError(f"oracle_receptors failed ({rc})")
+    return out
+
+
+def adjoint(cfg, rec, sigma: float, every: int, w, sel=None, n_run: Optional[int] = None,
+            **kw) -> np.ndarray:
+    """Gradient of sum_r w_r C_r with respect to (x_s, y_s, h, q[0..n_q-1], s_K, b_u, b_v)."""
+    o = make_ocfg(cfg, **kw)
+    rec = np.ascontiguousarray(rec, dtype=np.float64).reshape(-1, 3)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.zeros(3 + int(o.n_q) + 3)
+    n_run = cfg.n_steps if n_run is None else n_run
+    sel_a = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+    rc = lib().oracle_adjoint(C.byref(o), _ptr(rec, C.c_double), rec.shape[0], float(sigma),
+                              int(every), _ptr(w, C.c_double), _ptr(sel_a, C.c_int64),
+                              0 if sel_a is None else sel_a.size, int(n_run),
+                              _ptr(out, C.c_double))
+    if rc:
+        raise ValueError(f"oracle_adjoint failed ({rc})")
+    return out
+
+
+def sensitivity(cfg, sel=None, n_run: Optional[int] = None, **kw) -> np.ndarray:
+    """Per particle, the largest Frobenius norm of d X_end / d X_k over its steps k."""
+    o = make_ocfg(cfg, **kw)
+    n_run = cfg.n_steps if n_run is None else n_run
+    sel_a = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+    n = int(o.n_particles) if sel_a is None else sel_a.size
+    out = np.zeros(n)
+    rc = lib().oracle_sensitivity(C.byref(o), _ptr(sel_a, C.c_int64), 0 if sel_a is None else n,
+                                  int(n_run), _ptr(out, C.c_double))
+    if rc:
+        raise ValueError(f"oracle_sensitivity failed ({rc})")
     return out

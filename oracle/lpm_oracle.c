@@ -612,3 +612,303 @@ void oracle_release_many(int64_t n, int64_t first, int64_t last, const int64_t *
 {
     for (int64_t i = 0; i < m; ++i) out[i] = oracle_release_step(n, first, last, p[i]);
 }
+
+/* =================================================================================
+ * Receptor concentrations and the adjoint (reverse-mode) gradient.
+ *
+ * C_r = (1/n_s) sum over sample steps k ((k+1) % every == 0, k < S) of
+ *       sum over particles active after step k of m_p(k) G(X_p(k+1) - x_r),
+ * G(d) = (2 pi s^2)^(-3/2) [exp(-|d|^2 / 2s^2) + exp(-|d*|^2 / 2s^2)], d* = d with the
+ * receptor mirrored below the ground (z + z_r): a Gaussian-kernel estimate of the
+ * concentration at x_r in place of hard binning, with the image term of the reflecting
+ * ground. The gradient of L = sum_r w_r C_r with respect to the parameters
+ * theta = (x_s, y_s, h, q[0..n_q-1], s_K, b_u, b_v) follows each particle's path with
+ * its events (deposition, exit) frozen and the same keyed random numbers (common random
+ * numbers). Parameters: the source position (x_s, y_s, h) is the particle's position at
+ * its release; q scales the particle masses (Sec. 3.2); s_K multiplies both
+ * diffusivities in Eq. (2); (b_u, b_v) is added to the wind in Eq. (1).
+ * Parity: pinned against central finite differences of oracle_receptors with the same
+ * seeds and against the analytic gradient of the expected receptor concentration for
+ * uniform weather (tests).
+ * ================================================================================= */
+
+/* Weather and its spatial gradient at (x, y, z, t): val = (u, v, w, K_z, K_h) (K clamped
+ * >= 0), grad[q][d] = d val[q] / d (x, y, z)[d] of the multilinear interpolant (0 along
+ * an axis where the point lies outside the grid, or where K is clamped). */
+static void interp_grad(const ocfg *c, double x, double y, double z, double t, double val[5],
+                        double grad[5][3])
+{
+    int i, j, k, h0, h1;
+    double a, b, cz, f;
+    axis_uniform(x, c->x0, c->dx, c->nx, &i, &a);
+    axis_uniform(y, c->y0, c->dy, c->ny, &j, &b);
+    axis_levels(z, c->z_levels, c->nz, &k, &cz);
+    axis_time(c, t, &h0, &h1, &f);
+    double fx = (x - c->x0) / c->dx, fy = (y - c->y0) / c->dy;
+    int in_x = fx >= 0.0 && fx <= (double)(c->nx - 1);
+    int in_y = fy >= 0.0 && fy <= (double)(c->ny - 1);
+    int in_z = z >= c->z_levels[0] && z <= c->z_levels[c->nz - 1];
+    double dz = c->z_levels[k + 1] - c->z_levels[k];
+    double acc[5] = {0, 0, 0, 0, 0}, g[5][3];
+    memset(g, 0, sizeof g);
+    for (int dh = 0; dh < 2; ++dh) {
+        int h = dh ? h1 : h0;
+        double wt = dh ? f : 1.0 - f;
+        for (int dk = 0; dk < 2; ++dk) {
+            double wz = dk ? cz : 1.0 - cz, gz = in_z ? (dk ? 1.0 : -1.0) / dz : 0.0;
+            for (int dj = 0; dj < 2; ++dj) {
+                double wy = dj ? b : 1.0 - b, gy = in_y ? (dj ? 1.0 : -1.0) / c->dy : 0.0;
+                for (int di = 0; di < 2; ++di) {
+                    double wx = di ? a : 1.0 - a, gx = in_x ? (di ? 1.0 : -1.0) / c->dx : 0.0;
+                    size_t node = (((size_t)h * c->nz + (k + dk)) * c->ny + (j + dj)) * c->nx + (i + di);
+                    const float *m = c->uvwk + 4 * node;
+                    double vals[5] = {m[0], m[1], m[2], m[3], c->kh ? (double)c->kh[node] : 0.0};
+                    for (int q = 0; q < 5; ++q) {
+                        acc[q] += wt * wz * wy * wx * vals[q];
+                        g[q][0] += wt * wz * wy * gx * vals[q];
+                        g[q][1] += wt * wz * gy * wx * vals[q];
+                        g[q][2] += wt * gz * wy * wx * vals[q];
+                    }
+                }
+            }
+        }
+    }
+    if (c->wind_offset) {
+        acc[0] += (1.0 - f) * (double)c->wind_offset[2 * h0] + f * (double)c->wind_offset[2 * h1];
+        acc[1] += (1.0 - f) * (double)c->wind_offset[2 * h0 + 1] + f * (double)c->wind_offset[2 * h1 + 1];
+    }
+    if (!c->kh) {
+        acc[4] = c->kh_uniform;
+        g[4][0] = g[4][1] = g[4][2] = 0.0;
+    }
+    for (int q = 3; q < 5; ++q)
+        if (!(acc[q] > 0.0)) {
+            acc[q] = 0.0;
+            g[q][0] = g[q][1] = g[q][2] = 0.0;
+        }
+    for (int q = 0; q < 5; ++q) {
+        val[q] = acc[q];
+        for (int d = 0; d < 3; ++d) grad[q][d] = g[q][d];
+    }
+}
+
+/* Derivatives of one step X_old -> X_new: J[r][d] = dX_new[r] / dX_old[d] and
+ * T[r][0..2] = dX_new[r] / d(s_K, b_u, b_v); fold = dz/dz_pre from the reflections. */
+static void step_jacobian(const ocfg *c, const double X[3], int64_t k, const double nrm[3],
+                          double fold, double J[3][3], double T[3][3])
+{
+    double val[5], g[5][3];
+    interp_grad(c, X[0], X[1], X[2], (double)k * c->dt, val, g);
+    const double sk = c->k_scale, dt = c->dt;
+    const double sig_h = sqrt(2.0 * sk * val[4] * dt), sig_z = sqrt(2.0 * sk * val[3] * dt);
+    double dsh[3] = {0, 0, 0}, dsz[3] = {0, 0, 0};
+    for (int d = 0; d < 3; ++d) {
+        if (val[4] > 0.0) dsh[d] = sqrt(2.0 * sk * dt) * g[4][d] / (2.0 * sqrt(val[4]));
+        if (val[3] > 0.0) dsz[d] = sqrt(2.0 * sk * dt) * g[3][d] / (2.0 * sqrt(val[3]));
+    }
+    for (int d = 0; d < 3; ++d) {
+        J[0][d] = (d == 0 ? 1.0 : 0.0) + dt * g[0][d] + nrm[0] * dsh[d];
+        J[1][d] = (d == 1 ? 1.0 : 0.0) + dt * g[1][d] + nrm[1] * dsh[d];
+        J[2][d] = fold * ((d == 2 ? 1.0 : 0.0) + dt * g[2][d] + nrm[2] * dsz[d]);
+    }
+    T[0][0] = nrm[0] * sig_h / (2.0 * sk);
+    T[1][0] = nrm[1] * sig_h / (2.0 * sk);
+    T[2][0] = fold * nrm[2] * sig_z / (2.0 * sk);
+    T[0][1] = dt; T[1][1] = 0.0; T[2][1] = 0.0;
+    T[0][2] = 0.0; T[1][2] = dt; T[2][2] = 0.0;
+}
+
+/* One particle's whole path: states Xs[k - s_p] before each step k in [s_p, kend] and
+ * after the last (n_states = kend - s_p + 2), normals and folds per step, the step of
+ * its event (or -1) and its final status. */
+typedef struct {
+    int64_t sp, kend;           /* release step; last step taken */
+    int status;
+    double *X;                  /* [n_states][3] */
+    double *nrm;                /* [n_steps][3] */
+    double *fold;               /* [n_steps] */
+    double margin;
+} opath;
+
+static int trace_particle(const ocfg *c, const ostep *K, int64_t p, int64_t n_run, opath *o)
+{
+    o->sp = oracle_release_step(c->n_particles, c->first_step, c->last_step, p);
+    o->status = OR_UNRELEASED;
+    o->kend = o->sp - 1;
+    o->margin = INFINITY;
+    if (o->sp >= n_run) return 0;
+    size_t cap = (size_t)(n_run - o->sp);
+    o->X = (double *)malloc(sizeof(double) * 3 * (cap + 1));
+    o->nrm = (double *)malloc(sizeof(double) * 3 * cap);
+    o->fold = (double *)malloc(sizeof(double) * cap);
+    if (!o->X || !o->nrm || !o->fold) return 2;
+    double X[3] = {c->src_x, c->src_y, c->src_z};
+    const uint64_t gid = (uint64_t)(c->pid_offset + p);
+    o->status = OR_ACTIVE;
+    for (int64_t k = o->sp; k < n_run; ++k) {
+        size_t s = (size_t)(k - o->sp);
+        memcpy(o->X + 3 * s, X, sizeof X);
+        double met[6];
+        int st = particle_step(c, K, gid, k, X, &o->margin, &o->fold[s], o->nrm + 3 * s, met);
+        o->kend = k;
+        if (st != OR_ACTIVE) {
+            o->status = st;
+            break;
+        }
+    }
+    memcpy(o->X + 3 * (size_t)(o->kend + 1 - o->sp), X, sizeof X);
+    return 0;
+}
+
+static void free_path(opath *o)
+{
+    if (o->status == OR_UNRELEASED) return;
+    free(o->X);
+    free(o->nrm);
+    free(o->fold);
+}
+
+static int n_samples(int64_t n_run, int every)
+{
+    return (int)(n_run / every);
+}
+
+static double kernel_g(const double X[3], const double r[3], double sigma, double grad[3])
+{
+    const double norm = pow(2.0 * 3.14159265358979323846 * sigma * sigma, -1.5);
+    const double dx = X[0] - r[0], dy = X[1] - r[1], dz = X[2] - r[2], dzi = X[2] + r[2];
+    const double s2 = sigma * sigma;
+    const double e1 = exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * s2));
+    const double e2 = exp(-(dx * dx + dy * dy + dzi * dzi) / (2.0 * s2));
+    if (grad) {
+        grad[0] = -norm * (e1 + e2) * dx / s2;
+        grad[1] = -norm * (e1 + e2) * dy / s2;
+        grad[2] = -norm * (e1 * dz + e2 * dzi) / s2;
+    }
+    return norm * (e1 + e2);
+}
+
+/* Receptor concentrations C[R] from the particles listed in sel (NULL = all). */
+int oracle_receptors(const ocfg *c, const double *rec, int R, double sigma, int every,
+                     const int64_t *sel, int64_t n_sel, int64_t n_run, double *C)
+{
+    if (R < 0 || !(sigma > 0.0) || every < 1) return 1;
+    const ostep K = step_constants(c);
+    const int ns = n_samples(n_run, every);
+    const double lam = decay_rate(c);
+    int64_t n = sel ? n_sel : c->n_particles;
+    for (int r = 0; r < R; ++r) C[r] = 0.0;
+    if (ns == 0) return 0;
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t p = sel ? sel[q] : q;
+        opath o;
+        if (trace_particle(c, &K, p, n_run, &o)) return 2;
+        if (o.status == OR_UNRELEASED) continue;
+        const double m0 = oracle_initial_mass(c, o.sp);
+        for (int64_t k = o.sp; k <= o.kend; ++k) {
+            if ((k + 1) % every) continue;
+            if (k == o.kend && o.status != OR_ACTIVE) break;    /* inactive after its event */
+            const double m = m0 * exp(-lam * (double)(k + 1 - o.sp) * c->dt);
+            const double *X = o.X + 3 * (size_t)(k + 1 - o.sp);
+            for (int r = 0; r < R; ++r) C[r] += m * kernel_g(X, rec + 3 * r, sigma, NULL) / ns;
+        }
+        free_path(&o);
+    }
+    return 0;
+}
+
+/* Gradient of L = sum_r w_r C_r: grad[0..2] source (x_s, y_s, h), grad[3..3+n_q-1] the
+ * emission series, then s_K, b_u, b_v. Reverse sweep per particle: mu is dL/dX at the
+ * state after the step being undone. */
+int oracle_adjoint(const ocfg *c, const double *rec, int R, double sigma, int every,
+                   const double *w, const int64_t *sel, int64_t n_sel, int64_t n_run, double *grad)
+{
+    if (R < 0 || !(sigma > 0.0) || every < 1 || c->drift_correction) return 1;
+    const ostep K = step_constants(c);
+    const int ns = n_samples(n_run, every);
+    const double lam = decay_rate(c);
+    const int nq = c->n_q, ng = 3 + nq + 3;
+    for (int i = 0; i < ng; ++i) grad[i] = 0.0;
+    if (ns == 0) return 0;
+    int64_t n = sel ? n_sel : c->n_particles;
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t p = sel ? sel[q] : q;
+        opath o;
+        if (trace_particle(c, &K, p, n_run, &o)) return 2;
+        if (o.status == OR_UNRELEASED) continue;
+        int64_t cnt = oracle_release_count(c->n_particles, c->first_step, c->last_step, o.sp);
+        int64_t hq = (int64_t)floor((double)o.sp * c->dt / c->q_dt);
+        if (hq < 0) hq = 0;
+        if (hq > nq - 1) hq = nq - 1;
+        const double mass_per_q = c->dt / (double)cnt;       /* m0 = q[hq] * dt / n_s */
+        const double qv = c->q[hq];
+        double mu[3] = {0, 0, 0};
+        for (int64_t k = o.kend; k >= o.sp; --k) {
+            const size_t s = (size_t)(k - o.sp);
+            const double *Xn = o.X + 3 * (s + 1);
+            /* sample at the end of step k while the particle is still active */
+            if ((k + 1) % every == 0 && !(k == o.kend && o.status != OR_ACTIVE)) {
+                const double decay = exp(-lam * (double)(k + 1 - o.sp) * c->dt);
+                for (int r = 0; r < R; ++r) {
+                    double gg[3];
+                    double G = kernel_g(Xn, rec + 3 * r, sigma, gg);
+                    grad[3 + hq] += w[r] * mass_per_q * decay * G / ns;
+                    for (int d = 0; d < 3; ++d) mu[d] += w[r] * qv * mass_per_q * decay * gg[d] / ns;
+                }
+            }
+            /* undo step k: parameter partials, then propagate mu to the state before */
+            double J[3][3], T[3][3];
+            step_jacobian(c, o.X + 3 * s, k, o.nrm + 3 * s, o.fold[s], J, T);
+            for (int th = 0; th < 3; ++th)
+                for (int r = 0; r < 3; ++r) grad[3 + nq + th] += mu[r] * T[r][th];
+            double nmu[3] = {0, 0, 0};
+            for (int d = 0; d < 3; ++d)
+                for (int r = 0; r < 3; ++r) nmu[d] += mu[r] * J[r][d];
+            memcpy(mu, nmu, sizeof mu);
+        }
+        /* the state at release is the source */
+        grad[0] += mu[0];
+        grad[1] += mu[1];
+        grad[2] += mu[2];
+        free_path(&o);
+    }
+    return 0;
+}
+
+/* Finite-time growth of perturbations along each particle's path up to step n_run:
+ * out[q] = max over steps k of the Frobenius norm of d X_end / d X_k (reverse product of
+ * the step Jacobians). A one-ulp difference in the state at step k can reach
+ * out[q] * ulp at the end; the parity tests use it to recognise chaotic paths. */
+int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, double *out)
+{
+    if (c->drift_correction) return 1;
+    const ostep K = step_constants(c);
+    int64_t n = sel ? n_sel : c->n_particles;
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t p = sel ? sel[q] : q;
+        opath o;
+        if (trace_particle(c, &K, p, n_run, &o)) return 2;
+        out[q] = 1.0;
+        if (o.status == OR_UNRELEASED) continue;
+        double M[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        double best = 1.0;
+        for (int64_t k = o.kend; k >= o.sp; --k) {
+            const size_t s = (size_t)(k - o.sp);
+            double J[3][3], T[3][3], N[3][3];
+            step_jacobian(c, o.X + 3 * s, k, o.nrm + 3 * s, o.fold[s], J, T);
+            for (int r = 0; r < 3; ++r)
+                for (int d = 0; d < 3; ++d) {
+                    N[r][d] = 0.0;
+                    for (int e = 0; e < 3; ++e) N[r][d] += M[r][e] * J[e][d];
+                }
+            memcpy(M, N, sizeof M);
+            double fro = 0.0;
+            for (int r = 0; r < 3; ++r)
+                for (int d = 0; d < 3; ++d) fro += M[r][d] * M[r][d];
+            if (sqrt(fro) > best) best = sqrt(fro);
+        }
+        out[q] = best;
+        free_path(&o);
+    }
+    return 0;
+}
