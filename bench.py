@@ -210,6 +210,47 @@ def measure_batched(args, stream, cfg=None):
             "launch": [args.batched_block, args.batched_ppt, args.batched_occ]}
 
 
+def measure_adjoint(args, stream):
+    """The adjoint form: 1e6 particles, 6 h at dt = 20 s on the realistic met, 64 receptors
+    (Gaussian kernel, 200 m), sampled every 18 steps; forward (receptors + checkpoints every
+    64 steps) and backward (segment recomputation + reverse sweep) per run."""
+    import numpy as np
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = li.make_cfg3()
+    rec = li.make_receptors()
+    w = np.linspace(-1.0, 1.0, rec.shape[0])[None, :]
+    with torch.cuda.stream(stream):
+        sim = Sim(cfg, stream=stream)
+    try:
+        sim.reset()
+        sim.step(cfg.n_steps)
+        active = int(sim.fixed_state()[2][4])         # same paths as the receptor run
+        for _ in range(max(1, args.warmup)):
+            lpm.lpm_receptors(sim.ctx, 1, rec, 200.0, 18)
+            lpm.lpm_adjoint(sim.ctx, rec, 200.0, 18, w, 24)
+        fwd, bwd = [], []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lpm.lpm_receptors(sim.ctx, 1, rec, 200.0, 18)
+            t1 = time.perf_counter()
+            lpm.lpm_adjoint(sim.ctx, rec, 200.0, 18, w, 24)
+            t2 = time.perf_counter()
+            fwd.append(t1 - t0)
+            bwd.append(t2 - t1)
+    finally:
+        sim.close()
+    tf, tb = statistics.mean(fwd), statistics.mean(bwd)
+    return {"value": active / (tf + tb), "unit": UNIT,
+            "note": "active particle-steps of the run / (forward + backward) wall time",
+            "ms_forward": 1e3 * tf, "ms_backward": 1e3 * tb, "particles": cfg.n_particles,
+            "steps_per_run": cfg.n_steps, "receptors": int(rec.shape[0]),
+            "active_particle_steps": active, "checkpoint_every": 64}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -335,7 +376,8 @@ def run_gpu(args):
         "clocks": clk,
     }
     if not args.no_forms:
-        forms = {"batched": measure_batched(args, stream)}
+        forms = {"batched": measure_batched(args, stream),
+                 "adjoint": measure_adjoint(args, stream)}
         for f in forms.values():
             f["vs_plain"] = f["value"] / value
         line["forms"] = forms

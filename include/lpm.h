@@ -222,6 +222,43 @@ lpm_status lpm_stats(lpm_ctx *ctx, int64_t *launches, int64_t *advance_launches,
                      double *advance_ms);
 
 /*
+ * Differentiable parameters of the step (adjoint form): k_scale multiplies both
+ * diffusivities in Eq. (2) and (bias_u, bias_v) is added to the interpolated wind in
+ * Eq. (1). They apply to lpm_step as well. Defaults 1, 0, 0.
+ */
+lpm_status lpm_set_params(lpm_ctx *ctx, double k_scale, double bias_u, double bias_v);
+
+/* Replaces a released scenario's emission series q[n_q] (rates for bins of the release's
+ * q_dt), keeping its particles and release steps (Sec. 3.2: the masses are assigned from
+ * the emission profile). Only at step 0 (after lpm_create or lpm_reset). n_q <= 64. */
+lpm_status lpm_set_emission(lpm_ctx *ctx, int scenario, const double *q, int n_q);
+
+/*
+ * Receptor concentrations of every scenario over a whole run from step 0 (the run state
+ * of lpm_step is not touched): C[s][r] = (1/n_s) sum over the steps k with
+ * (k+1) % sample_every == 0 of the sum over particles active after step k of
+ * m_p G(X_p - x_r), G a 3D Gaussian kernel of width `bandwidth` (m) plus its image below
+ * the ground (terms beyond 6 bandwidths are dropped), n_s = floor(n_steps / sample_every).
+ * receptors: host [R][3] (x, y, z), 1 <= R <= 256; C: host [n_scenarios][R]. Also stores
+ * the checkpoints (every 64 steps) that lpm_adjoint uses. Synchronous. Not with
+ * drift_correction.
+ */
+lpm_status lpm_receptors(lpm_ctx *ctx, const double *receptors, int R, double bandwidth,
+                         int sample_every, double *C);
+
+/*
+ * Reverse-mode gradient of L = sum_{s,r} dL_dC[s][r] C[s][r] (hand-written adjoint of the
+ * step, events frozen, same keyed random numbers): grad [n_scenarios][3 + nq + 3] =
+ * (dL/dx_s, dL/dy_s, dL/dh, dL/dq[0..nq-1], dL/dk_scale, dL/dbias_u, dL/dbias_v) per
+ * scenario, nq the longest emission series of the context (shorter series leave zeros).
+ * Uses the checkpoints of the last lpm_receptors with the same receptors, bandwidth,
+ * sample_every and parameters, else runs that forward first. Paths are recomputed from
+ * the checkpoints one 64-step segment at a time. Synchronous.
+ */
+lpm_status lpm_adjoint(lpm_ctx *ctx, const double *receptors, int R, double bandwidth,
+                       int sample_every, const double *dL_dC, double *grad);
+
+/*
  * The counter-based draws the step consumes (replacing the Mersenne Twister + Box-Muller
  * of Sec. 2): for each i < n, words[4i..4i+3] = Philox4x32-10(key = seed, counter =
  * (pid[i] low, pid[i] high, step[i], stream)) and normals[3i..3i+2] = the three N(0,1)

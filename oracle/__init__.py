@@ -317,14 +317,25 @@ def adjoint(cfg, rec, sigma: float, every: int, w, sel=None, n_run: Optional[int
 
 
 def sensitivity(cfg, sel=None, n_run: Optional[int] = None, **kw) -> np.ndarray:
-    """Per particle, the largest Frobenius norm of d X_end / d X_k over its steps k."""
+    """Per particle [n][2]: the largest norms of d X_end / d (x_k, y_k) and of
+    d X_end / d z_k over its steps k (finite-time perturbation growth)."""
     o = make_ocfg(cfg, **kw)
     n_run = cfg.n_steps if n_run is None else n_run
     sel_a = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     n = int(o.n_particles) if sel_a is None else sel_a.size
-    out = np.zeros(n)
+    out = np.zeros((n, 2))
     rc = lib().oracle_sensitivity(C.byref(o), _ptr(sel_a, C.c_int64), 0 if sel_a is None else n,
                                   int(n_run), _ptr(out, C.c_double))
     if rc:
         raise ValueError(f"oracle_sensitivity failed ({rc})")
     return out
+
+
+def chaotic(cfg, sens: np.ndarray, pos: np.ndarray, pos_tol: float) -> np.ndarray:
+    """Paths on which a single FP32 rounding of the state (2^-24 of its magnitude) can grow
+    past the position tolerance by the end of the run: their FP32 and FP64 realisations
+    are not expected to stay within the tolerance."""
+    eps = 2.0 ** -24
+    rh = np.maximum(np.abs(pos[:, 0]), np.abs(pos[:, 1]))
+    rz = np.maximum(pos[:, 2], 1.0)
+    return eps * (sens[:, 0] * rh + sens[:, 1] * rz) > pos_tol

@@ -876,9 +876,10 @@ int oracle_adjoint(const ocfg *c, const double *rec, int R, double sigma, int ev
 }
 
 /* Finite-time growth of perturbations along each particle's path up to step n_run:
- * out[q] = max over steps k of the Frobenius norm of d X_end / d X_k (reverse product of
- * the step Jacobians). A one-ulp difference in the state at step k can reach
- * out[q] * ulp at the end; the parity tests use it to recognise chaotic paths. */
+ * out[2q] = max over steps k of the Frobenius norm of d X_end / d (x_k, y_k) and
+ * out[2q+1] = max over k of the norm of d X_end / d z_k (reverse products of the step
+ * Jacobians). A one-ulp difference in the state at step k can reach these factors times
+ * the ulp at the end; the parity tests use them to recognise chaotic paths. */
 int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, double *out)
 {
     if (c->drift_correction) return 1;
@@ -888,10 +889,11 @@ int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t
         int64_t p = sel ? sel[q] : q;
         opath o;
         if (trace_particle(c, &K, p, n_run, &o)) return 2;
-        out[q] = 1.0;
+        out[2 * q] = 1.0;
+        out[2 * q + 1] = 1.0;
         if (o.status == OR_UNRELEASED) continue;
         double M[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-        double best = 1.0;
+        double best_h = 1.4142135623730951, best_z = 1.0;
         for (int64_t k = o.kend; k >= o.sp; --k) {
             const size_t s = (size_t)(k - o.sp);
             double J[3][3], T[3][3], N[3][3];
@@ -902,12 +904,16 @@ int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t
                     for (int e = 0; e < 3; ++e) N[r][d] += M[r][e] * J[e][d];
                 }
             memcpy(M, N, sizeof M);
-            double fro = 0.0;
-            for (int r = 0; r < 3; ++r)
-                for (int d = 0; d < 3; ++d) fro += M[r][d] * M[r][d];
-            if (sqrt(fro) > best) best = sqrt(fro);
+            double fh = 0.0, fz = 0.0;
+            for (int r = 0; r < 3; ++r) {
+                fh += M[r][0] * M[r][0] + M[r][1] * M[r][1];
+                fz += M[r][2] * M[r][2];
+            }
+            if (sqrt(fh) > best_h) best_h = sqrt(fh);
+            if (sqrt(fz) > best_z) best_z = sqrt(fz);
         }
-        out[q] = best;
+        out[2 * q] = best_h;
+        out[2 * q + 1] = best_z;
         free_path(&o);
     }
     return 0;

@@ -1,0 +1,316 @@
+// lpm_adjoint.cu - receptor concentrations and their reverse-mode gradient.
+//
+// Forward: every particle runs the whole horizon with the step of the main loop
+// (particle_step), the decayed mass is spread on the receptors with a Gaussian kernel
+// (with the ground image) every `every` steps, and the state at the start of every
+// CK-th step is checkpointed. Backward: each thread recomputes its particle's path one
+// CK-step segment at a time from the checkpoint (same keyed draws, same FP32 arithmetic,
+// so the same path and events), then sweeps the segment in reverse, carrying
+// mu = dL/dX and accumulating the parameter partials. Events (deposition, exit) are
+// frozen; sums over particles are reduced in FP64.
+#include "lpm_advance.cuh"
+#include "lpm_adjoint.h"
+
+namespace lpm {
+
+// Weather and its spatial gradient: val = (u, v, w, K_z, K_h), g[q][d] = d val[q] / d x_d.
+__device__ __forceinline__ void sample_met_grad(const StepParams &P, const Levels &L,
+                                                const StepTime &T, float sig_h_uniform, float x,
+                                                float y, float z, float val[5], float g[5][3])
+{
+    int i, j, k;
+    float a, b, c;
+    axis(x, P.x0, P.inv_dx, P.nx, i, a);
+    axis(y, P.y0, P.inv_dy, P.ny, j, b);
+    level(L, z, k, c);
+    const float fx = (x - P.x0) * P.inv_dx, fy = (y - P.y0) * P.inv_dy;
+    const float gx = (fx >= 0.0f && fx <= (float)(P.nx - 1)) ? P.inv_dx : 0.0f;
+    const float gy = (fy >= 0.0f && fy <= (float)(P.ny - 1)) ? P.inv_dy : 0.0f;
+    const float gz = (z >= L.z[0] && z <= L.z[P.nz - 1]) ? L.inv[k] : 0.0f;
+    const int nx = P.nx, nxny = P.nx * P.ny;
+    const int n00 = (k * P.ny + j) * nx + i;
+    float4 q[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int off = (m & 1) + ((m >> 1) & 1) * nx + ((m >> 2) & 1) * nxny;
+        float4 lo, hi;
+        ld_pair(T.pair + 2 * (n00 + off), lo, hi);
+        q[m] = lerp4(lo, hi, T.ts.f);
+    }
+    const float4 x00 = lerp4(q[0], q[1], a), x10 = lerp4(q[2], q[3], a);
+    const float4 x01 = lerp4(q[4], q[5], a), x11 = lerp4(q[6], q[7], a);
+    const float4 y0 = lerp4(x00, x10, b), y1 = lerp4(x01, x11, b);
+    const float4 r = lerp4(y0, y1, c);
+    // d/dx: x-differences blended in y and z; d/dy: y-differences blended in z
+    float4 dx0 = lerp4(make_float4(q[1].x - q[0].x, q[1].y - q[0].y, q[1].z - q[0].z, q[1].w - q[0].w),
+                       make_float4(q[3].x - q[2].x, q[3].y - q[2].y, q[3].z - q[2].z, q[3].w - q[2].w), b);
+    float4 dx1 = lerp4(make_float4(q[5].x - q[4].x, q[5].y - q[4].y, q[5].z - q[4].z, q[5].w - q[4].w),
+                       make_float4(q[7].x - q[6].x, q[7].y - q[6].y, q[7].z - q[6].z, q[7].w - q[6].w), b);
+    const float4 ddx = lerp4(dx0, dx1, c);
+    const float4 ddy = lerp4(make_float4(x10.x - x00.x, x10.y - x00.y, x10.z - x00.z, x10.w - x00.w),
+                             make_float4(x11.x - x01.x, x11.y - x01.y, x11.z - x01.z, x11.w - x01.w), c);
+    const float4 ddz = make_float4(y1.x - y0.x, y1.y - y0.y, y1.z - y0.z, y1.w - y0.w);
+    val[0] = r.x; val[1] = r.y; val[2] = r.z; val[3] = r.w;
+    g[0][0] = ddx.x * gx; g[0][1] = ddy.x * gy; g[0][2] = ddz.x * gz;
+    g[1][0] = ddx.y * gx; g[1][1] = ddy.y * gy; g[1][2] = ddz.y * gz;
+    g[2][0] = ddx.z * gx; g[2][1] = ddy.z * gy; g[2][2] = ddz.z * gz;
+    g[3][0] = ddx.w * gx; g[3][1] = ddy.w * gy; g[3][2] = ddz.w * gz;
+    if (!(val[3] > 0.0f)) {
+        val[3] = 0.0f;
+        g[3][0] = g[3][1] = g[3][2] = 0.0f;
+    }
+    if (T.khp) {
+        float e[8];
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+            const int off = (mm & 1) + ((mm >> 1) & 1) * nx + ((mm >> 2) & 1) * nxny;
+            const float2 v = __ldg(T.khp + n00 + off);
+            e[mm] = fmaf(T.ts.f, v.y - v.x, v.x);
+        }
+        const float ex0 = fmaf(a, e[1] - e[0], e[0]), ex1 = fmaf(a, e[3] - e[2], e[2]);
+        const float ex2 = fmaf(a, e[5] - e[4], e[4]), ex3 = fmaf(a, e[7] - e[6], e[6]);
+        const float ey0 = fmaf(b, ex1 - ex0, ex0), ey1 = fmaf(b, ex3 - ex2, ex2);
+        val[4] = fmaf(c, ey1 - ey0, ey0);
+        const float l01 = fmaf(b, (e[3] - e[2]) - (e[1] - e[0]), e[1] - e[0]);
+        const float l23 = fmaf(b, (e[7] - e[6]) - (e[5] - e[4]), e[5] - e[4]);
+        g[4][0] = fmaf(c, l23 - l01, l01) * gx;
+        g[4][1] = fmaf(c, (ex3 - ex2) - (ex1 - ex0), ex1 - ex0) * gy;
+        g[4][2] = (ey1 - ey0) * gz;
+        if (!(val[4] > 0.0f)) {
+            val[4] = 0.0f;
+            g[4][0] = g[4][1] = g[4][2] = 0.0f;
+        }
+    } else {
+        val[4] = fmaxf(P.kh_uniform, 0.0f);
+        g[4][0] = g[4][1] = g[4][2] = 0.0f;
+    }
+    (void)sig_h_uniform;
+}
+
+__device__ __forceinline__ long long release_step_of(const ScenDev &sc, long long slot)
+{
+    const long long p = sc.part_first + (slot - sc.first_slot);
+    return sc.rel_first + (p * (long long)(sc.rel_last - sc.rel_first)) / sc.n_total;
+}
+
+__device__ __forceinline__ float4 pack_state(float x, float y, float z, uint32_t st, int sp)
+{
+    return make_float4(x, y, z, __uint_as_float((st << TAG_SHIFT) | ((uint32_t)sp & TAG_STEP)));
+}
+
+// ---------------------------------------------------------------------------------
+// Forward: receptor concentrations and checkpoints.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(ADJ_BLOCK)
+adj_forward_kernel(const StepParams P, const AdjParams A)
+{
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
+    __shared__ float4 s_rec[MAX_REC];
+    __shared__ double s_C[MAX_REC];
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
+        s_rec[r] = A.rec[r];
+        s_C[r] = 0.0;
+    }
+    __syncthreads();
+    const Tile tile = A.tiles[blockIdx.x];
+    const ScenDev sc = P.scen[tile.scen];
+    const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
+    if ((int)threadIdx.x < tile.count) {
+        const long long slot = tile.first + threadIdx.x;
+        const unsigned long long gid = (unsigned long long)(sc.id0 + (slot - sc.first_slot));
+        const int sp = (int)release_step_of(sc, slot);
+        const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
+        float x = sc.src_x, y = sc.src_y, z = sc.src_z;
+        for (int c = 0; c < A.n_ck && c * CK <= sp; ++c)
+            A.ckpt[(long long)c * A.n_slots + slot] = pack_state(x, y, z, ST_UNRELEASED, sp);
+        uint32_t st = ST_ACTIVE;
+        for (int k = sp; k < A.n_steps; ++k) {
+            if (k > sp && k % CK == 0)
+                A.ckpt[(long long)(k / CK) * A.n_slots + slot] = pack_state(x, y, z, ST_ACTIVE, sp);
+            const StepTime T = step_time(P, sc, k);
+            st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp, sig_h_uniform, x, y, z, nullptr);
+            if (st != ST_ACTIVE) {
+                for (int c = k / CK + 1; c < A.n_ck; ++c)
+                    A.ckpt[(long long)c * A.n_slots + slot] = pack_state(x, y, z, st, sp);
+                break;
+            }
+            if ((k + 1) % A.every == 0) {
+                const float m = m0 * expf(-P.lambda * (float)(k + 1 - sp) * P.dt) * A.inv_ns;
+                for (int r = 0; r < A.R; ++r) {
+                    const float4 q = s_rec[r];
+                    const float dx = x - q.x, dy = y - q.y, dz = z - q.z, dzi = z + q.z;
+                    const float h2 = dx * dx + dy * dy;
+                    const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
+                    if (d1 > A.cut2 && d2 > A.cut2) continue;
+                    const float G = A.norm * (expf(-d1 * A.inv2s2) + expf(-d2 * A.inv2s2));
+                    atomicAdd(&s_C[r], (double)(m * G));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK)
+        if (s_C[r] != 0.0) atomicAdd(A.C + (long long)tile.scen * A.R + r, s_C[r]);
+}
+
+// ---------------------------------------------------------------------------------
+// Backward: segment recomputation and reverse sweep.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(ADJ_BLOCK)
+adj_backward_kernel(const StepParams P, const AdjParams A)
+{
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
+    __shared__ float4 s_rec[MAX_REC];
+    __shared__ float s_w[MAX_REC];
+    __shared__ double s_g[6];
+    __shared__ double s_gq[MAX_NQ];
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    const Tile tile = A.tiles[blockIdx.x];
+    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
+        s_rec[r] = A.rec[r];
+        s_w[r] = (float)(A.w[(long long)tile.scen * A.R + r] * (double)A.inv_ns);
+    }
+    for (int i = threadIdx.x; i < MAX_NQ; i += ADJ_BLOCK) s_gq[i] = 0.0;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = 0.0;
+    __syncthreads();
+    const ScenDev sc = P.scen[tile.scen];
+    const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
+    const float sq2dt = sqrtf(2.0f * P.k_scale * P.dt);
+    float mu0 = 0.f, mu1 = 0.f, mu2 = 0.f;
+    float gsk = 0.f, gbu = 0.f, gbv = 0.f, gq = 0.f;
+    int qidx = 0;
+    if ((int)threadIdx.x < tile.count) {
+        const long long slot = tile.first + threadIdx.x;
+        const unsigned long long gid = (unsigned long long)(sc.id0 + (slot - sc.first_slot));
+        const int sp = (int)release_step_of(sc, slot);
+        const int tix = sc.m0_off + (sp - sc.rel_first);
+        const float m0 = __ldg(P.m0 + tix);
+        const float mq = __ldg(A.mq + tix);
+        qidx = __ldg(A.qi + tix);
+        float4 seg[CK + 1];
+        signed char sfold[CK];
+        for (int c = A.n_ck - 1; c >= 0; --c) {
+            const int k_lo = c * CK, k_hi = min(A.n_steps, k_lo + CK);
+            if (sp >= k_hi) continue;
+            const float4 s0 = A.ckpt[(long long)c * A.n_slots + slot];
+            const uint32_t st0 = __float_as_uint(s0.w) >> TAG_SHIFT;
+            if (st0 != ST_ACTIVE && st0 != ST_UNRELEASED) continue;   // event before k_lo
+            float x = s0.x, y = s0.y, z = s0.z;
+            const int kstart = max(k_lo, sp);
+            if (st0 == ST_UNRELEASED) { x = sc.src_x; y = sc.src_y; z = sc.src_z; }
+            // recompute the segment
+            int n = 0;
+            bool ev = false;
+            for (int k = kstart; k < k_hi; ++k) {
+                seg[n] = make_float4(x, y, z, 0.f);
+                const StepTime T = step_time(P, sc, k);
+                float fs;
+                const uint32_t st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp,
+                                                         sig_h_uniform, x, y, z, &fs);
+                sfold[n] = (signed char)fs;
+                ++n;
+                if (st != ST_ACTIVE) { ev = true; break; }
+            }
+            seg[n] = make_float4(x, y, z, 0.f);
+            // reverse sweep
+            for (int i = n - 1; i >= 0; --i) {
+                const int k = kstart + i;
+                if ((k + 1) % A.every == 0 && !(ev && i == n - 1)) {
+                    const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
+                    const float m = m0 * decay;
+                    const float4 X = seg[i + 1];
+                    for (int r = 0; r < A.R; ++r) {
+                        const float4 q = s_rec[r];
+                        const float dx = X.x - q.x, dy = X.y - q.y, dz = X.z - q.z, dzi = X.z + q.z;
+                        const float h2 = dx * dx + dy * dy;
+                        const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
+                        if (d1 > A.cut2 && d2 > A.cut2) continue;
+                        const float e1 = A.norm * expf(-d1 * A.inv2s2);
+                        const float e2 = A.norm * expf(-d2 * A.inv2s2);
+                        const float wr = s_w[r];
+                        const float c1 = -wr * m * A.inv_s2;
+                        mu0 += c1 * (e1 + e2) * dx;
+                        mu1 += c1 * (e1 + e2) * dy;
+                        mu2 += c1 * (e1 * dz + e2 * dzi);
+                        gq += wr * mq * decay * (e1 + e2);
+                    }
+                }
+                // undo step k at the state before it
+                const float4 X = seg[i];
+                const StepTime T = step_time(P, sc, k);
+                float val[5], g[5][3];
+                sample_met_grad(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
+                const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
+                                           P.seed_lo, P.seed_hi);
+                float n0, n1, n2;
+                normals3(w, n0, n1, n2);
+                const float fold = (float)sfold[i];
+                const float kh = P.k_scale * val[4], kz = P.k_scale * val[3];
+                const float sig_h = sqrtf(2.0f * kh * P.dt), sig_z = sqrtf(2.0f * kz * P.dt);
+                const float ch = val[4] > 0.0f ? sq2dt / (2.0f * sqrtf(val[4])) : 0.0f;
+                const float cz = val[3] > 0.0f ? sq2dt / (2.0f * sqrtf(val[3])) : 0.0f;
+                // parameter partials: s_K, b_u, b_v
+                const float inv2sk = 0.5f / P.k_scale;
+                gsk += (mu0 * n0 * sig_h + mu1 * n1 * sig_h + mu2 * fold * n2 * sig_z) * inv2sk;
+                gbu += mu0 * P.dt;
+                gbv += mu1 * P.dt;
+                // mu <- J^T mu
+                const float mz = mu2 * fold;
+                float nm[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float jx = P.dt * g[0][d] + n0 * ch * g[4][d];
+                    const float jy = P.dt * g[1][d] + n1 * ch * g[4][d];
+                    const float jz = P.dt * g[2][d] + n2 * cz * g[3][d];
+                    nm[d] = mu0 * jx + mu1 * jy + mz * jz;
+                }
+                mu0 += nm[0];
+                mu1 += nm[1];
+                mu2 = mz + nm[2];
+            }
+        }
+    }
+    // block reductions (FP64) and one atomic per parameter per block
+    for (int o = 16; o > 0; o >>= 1) {
+        mu0 += __shfl_xor_sync(0xffffffffu, mu0, o);
+        mu1 += __shfl_xor_sync(0xffffffffu, mu1, o);
+        mu2 += __shfl_xor_sync(0xffffffffu, mu2, o);
+        gsk += __shfl_xor_sync(0xffffffffu, gsk, o);
+        gbu += __shfl_xor_sync(0xffffffffu, gbu, o);
+        gbv += __shfl_xor_sync(0xffffffffu, gbv, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_g[0], (double)mu0);
+        atomicAdd(&s_g[1], (double)mu1);
+        atomicAdd(&s_g[2], (double)mu2);
+        atomicAdd(&s_g[3], (double)gsk);
+        atomicAdd(&s_g[4], (double)gbu);
+        atomicAdd(&s_g[5], (double)gbv);
+    }
+    if (gq != 0.f) atomicAdd(&s_gq[qidx], (double)gq);
+    __syncthreads();
+    double *G = A.grad + (long long)tile.scen * A.ng;
+    if (threadIdx.x < 3) atomicAdd(G + threadIdx.x, s_g[threadIdx.x]);
+    else if (threadIdx.x < 6) atomicAdd(G + 3 + A.nq + (threadIdx.x - 3), s_g[threadIdx.x]);
+    for (int i = threadIdx.x; i < A.nq; i += ADJ_BLOCK)
+        if (s_gq[i] != 0.0) atomicAdd(G + 3 + i, s_gq[i]);
+}
+
+cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    adj_forward_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    adj_backward_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+    return cudaGetLastError();
+}
+
+}  // namespace lpm

@@ -1,0 +1,35 @@
+// lpm_adjoint.h - parameters of the receptor / adjoint kernels (shared with the C ABI).
+#pragma once
+
+#include "lpm_device.cuh"
+
+namespace lpm {
+
+constexpr int CK = 64;                // checkpoint interval (steps)
+constexpr int ADJ_BLOCK = 128;
+constexpr int MAX_REC = 256;
+constexpr int MAX_NQ = 64;
+
+struct AdjParams {
+    const float4 *rec;                // [R] receptor (x, y, z, 0)
+    int R;
+    float inv2s2;                     // 1 / (2 sigma^2)
+    float norm;                       // (2 pi sigma^2)^(-3/2)
+    float inv_s2;                     // 1 / sigma^2
+    float cut2;                       // squared distance beyond which a kernel term is dropped
+    int every;
+    float inv_ns;                     // 1 / number of samples
+    int n_steps;
+    int n_ck;
+    float4 *ckpt;                     // [n_ck][n_slots]
+    long long n_slots;
+    const Tile *tiles;
+    double *C;                        // [n_scen][R]
+    const double *w;                  // [n_scen][R] dL/dC
+    double *grad;                     // [n_scen][ng]
+    int ng, nq;                       // ng = 3 + nq + 3
+    const float *mq;                  // dt / n_s per release step (mass per unit emission rate)
+    const short *qi;                  // emission-series index of each release step
+};
+
+}  // namespace lpm

@@ -99,6 +99,115 @@ __device__ __forceinline__ float mass_at(const StepParams &P, const ScenDev &sc,
     return m0 * expf(-P.lambda * age);
 }
 
+// Per-step quantities shared by every particle of a tile.
+struct StepTime {
+    int k;
+    float tk;                        // t_k
+    TimeSlab ts;
+    const float4 *pair;              // time pair of the step
+    const float2 *khp;               // K_h time pair or nullptr
+    float du, dv;                    // wind offset of the scenario + bias
+};
+
+__device__ __forceinline__ StepTime step_time(const StepParams &P, const ScenDev &sc, int k)
+{
+    StepTime T;
+    T.k = k;
+    T.tk = (float)k * P.dt;
+    T.ts = time_slab(P, T.tk);
+    T.pair = P.pair + (long long)T.ts.h0 * P.slab * 2;
+    T.khp = P.khpair ? P.khpair + (long long)T.ts.h0 * P.slab : nullptr;
+    T.du = P.bias_u;
+    T.dv = P.bias_v;
+    if (sc.wind_offset) {
+        const float2 o0 = __ldg(sc.wind_offset + T.ts.h0);
+        const float2 o1 = __ldg(sc.wind_offset + T.ts.h1);
+        T.du += fmaf(T.ts.f, o1.x - o0.x, o0.x);
+        T.dv += fmaf(T.ts.f, o1.y - o0.y, o0.y);
+    }
+    return T;
+}
+
+// One step of one active particle (Sec. 3.2 main loop: weather at the old position, K,
+// wind then random walk by Eq. 1-2, reflection, lateral exit, dry then wet deposition).
+// Updates (x, y, z) and returns the new status. With GRIDS, deposition and exit add
+// their mass to the scenario's grids and counters; *fold receives dz/dz_pre (+-1, 0 when
+// clamped).
+template <bool GRIDS>
+__device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Levels &LV,
+                                                  const StepTime &T, const ScenDev &sc,
+                                                  const ScenDev *scg, unsigned long long gid,
+                                                  int sp, float sig_h_uniform, float &x, float &y,
+                                                  float &z, float *fold)
+{
+    const int k = T.k;
+    // 1. weather at the old position and t_k; 2. diffusivities
+    const Met m = sample_met_pair(P, LV, T.pair, T.khp, T.ts.f, x, y, z);
+    const float sig_h = T.khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
+    const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
+    // 3. N(0,1) draws
+    const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u, P.seed_lo,
+                               P.seed_hi);
+    float n0, n1, n2;
+    normals3(w, n0, n1, n2);
+    // 4. Eq. (1)-(2): wind then turbulent displacement
+    const float xn = x + (m.u + T.du) * P.dt + n0 * sig_h;
+    const float yn = y + (m.v + T.dv) * P.dt + n1 * sig_h;
+    float zn = z + m.w * P.dt + n2 * sig_z;
+    if (P.drift) zn += P.k_scale * m.dkz * P.dt;
+    // 5. reflection, at most 4 folds, then clamp
+    float fs = 1.0f;
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+        if (P.reflect_ground && zn < 0.0f) { zn = -zn; fs = -fs; }
+        else if (P.reflect_top && zn > P.z_top) { zn = 2.0f * P.z_top - zn; fs = -fs; }
+        else break;
+    }
+    if (P.reflect_ground && zn < 0.0f) { zn = 0.0f; fs = 0.0f; }
+    if (P.reflect_top && zn > P.z_top) { zn = P.z_top; fs = 0.0f; }
+    if (fold) *fold = fs;
+    x = xn; y = yn; z = zn;
+    if (!isfinite(xn + yn + zn)) {
+        atomicOr(P.err, ERR_NAN);
+        return ST_EXITED;
+    }
+    // lateral boundary
+    if (P.lateral_exit && (xn < P.x_lo || xn > P.x_hi || yn < P.y_lo || yn > P.y_hi)) {
+        if (GRIDS)
+            atomicAdd(scg->ctr + C_EXITED * P.ctr_stride, to_fixed(mass_at(P, sc, sp, k), sc.scale));
+        return ST_EXITED;
+    }
+    if (!(P.t_dry | P.t_wet)) return ST_ACTIVE;
+    // 6. dry deposition below the mixing height, then wet where it rains
+    const U4 d = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 1u, P.seed_lo,
+                               P.seed_hi);
+    int kind = -1;
+    if (d.a < P.t_dry && zn < P.h_mix) kind = 0;
+    if (kind < 0 && d.b < P.t_wet && P.rain) {
+        int ir = (int)floorf((xn - P.x0) * P.inv_dx + 0.5f);
+        int jr = (int)floorf((yn - P.y0) * P.inv_dy + 0.5f);
+        ir = min(max(ir, 0), P.nx - 1);
+        jr = min(max(jr, 0), P.ny - 1);
+        int hr = (int)floorf(__fdiv_rn(T.tk - P.met_t0, P.met_dt));
+        hr = min(max(hr, 0), P.n_t - 1);
+        if (__ldg(P.rain + ((long long)hr * P.ny + jr) * P.nx + ir)) kind = 1;
+    }
+    if (kind < 0) return ST_ACTIVE;
+    if (GRIDS) {
+        const unsigned long long v = to_fixed(mass_at(P, sc, sp, k), sc.scale);
+        const int ix = (int)floorf((xn - P.cx0) * P.inv_cdx);
+        const int iy = (int)floorf((yn - P.cy0) * P.inv_cdy);
+        if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy) {
+            const long long cell = ((long long)kind * P.cy + iy) * P.cx + ix;
+            atomicAdd(scg->dep + cell, v);
+        } else {
+            atomicAdd(scg->ctr + (C_DEP_OUT_DRY + kind) * P.ctr_stride, v);
+        }
+        atomicAdd(scg->ctr + (C_DEP_DRY + kind) * P.ctr_stride, v);
+    }
+    return kind == 0 ? ST_DEP_DRY : ST_DEP_WET;
+}
+
 // Occupancy variants: the register budget per thread is 128 (OCC 0), 80 (OCC 1) or 64
 // (OCC 2), i.e. 16, 24 or 32 resident warps per SM.
 template <int BLOCK, int OCC>
@@ -123,7 +232,6 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     unsigned long long *s_warp = s_acc + (threadIdx.x & ~31);
     const long long n_cells = (long long)P.cx * P.cy * P.cz;
-    const long long n_dep = (long long)P.cx * P.cy;
     constexpr int TILE = BLOCK * PPT;
     // the uniform horizontal diffusivity gives one displacement scale for the run
     const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
@@ -179,17 +287,7 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
         unsigned long long steps = 0;
 #pragma unroll 1
         for (int k = k0; k < k1 && live > 0; ++k) {
-            const float tk = (float)k * P.dt;
-            const TimeSlab ts = time_slab(P, tk);
-            const float4 *pair = P.pair + (long long)ts.h0 * P.slab * 2;
-            const float2 *khp = P.khpair ? P.khpair + (long long)ts.h0 * P.slab : nullptr;
-            float du = P.bias_u, dv = P.bias_v;
-            if (sc.wind_offset) {
-                const float2 o0 = __ldg(sc.wind_offset + ts.h0);
-                const float2 o1 = __ldg(sc.wind_offset + ts.h1);
-                du += fmaf(ts.f, o1.x - o0.x, o0.x);
-                dv += fmaf(ts.f, o1.y - o0.y, o0.y);
-            }
+            const StepTime T = step_time(P, sc, k);
             live = 0;
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
@@ -205,69 +303,8 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
                 }
                 ++steps;
                 const unsigned long long gid = (unsigned long long)(gid0 + j * BLOCK);
-                // 1. weather at the old position and t_k; 2. diffusivities
-                const Met m = sample_met_pair(P, LV, pair, khp, ts.f, x[j], y[j], z[j]);
-                const float sig_h = khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
-                const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
-                // 3. N(0,1) draws
-                const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
-                                           P.seed_lo, P.seed_hi);
-                float n0, n1, n2;
-                normals3(w, n0, n1, n2);
-                // 4. Eq. (1)-(2): wind then turbulent displacement
-                const float xn = x[j] + (m.u + du) * P.dt + n0 * sig_h;
-                const float yn = y[j] + (m.v + dv) * P.dt + n1 * sig_h;
-                float zn = z[j] + m.w * P.dt + n2 * sig_z;
-                if (P.drift) zn += P.k_scale * m.dkz * P.dt;
-                // 5. reflection, at most 4 folds, then clamp
-#pragma unroll 1
-                for (int it = 0; it < 4; ++it) {
-                    if (P.reflect_ground && zn < 0.0f) zn = -zn;
-                    else if (P.reflect_top && zn > P.z_top) zn = 2.0f * P.z_top - zn;
-                    else break;
-                }
-                if (P.reflect_ground && zn < 0.0f) zn = 0.0f;
-                if (P.reflect_top && zn > P.z_top) zn = P.z_top;
-                x[j] = xn; y[j] = yn; z[j] = zn;
-                if (!isfinite(xn + yn + zn)) {
-                    atomicOr(P.err, ERR_NAN);
-                    tag[j] = (ST_EXITED << TAG_SHIFT) | (uint32_t)sp;
-                    continue;
-                }
-                // lateral boundary
-                if (P.lateral_exit && (xn < P.x_lo || xn > P.x_hi || yn < P.y_lo || yn > P.y_hi)) {
-                    st = ST_EXITED;
-                    atomicAdd(scg.ctr + C_EXITED * P.ctr_stride,
-                              to_fixed(mass_at(P, sc, sp, k), sc.scale));
-                } else if (P.t_dry | P.t_wet) {
-                    // 6. dry deposition below the mixing height, then wet where it rains
-                    const U4 d = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 1u,
-                                               P.seed_lo, P.seed_hi);
-                    int kind = -1;
-                    if (d.a < P.t_dry && zn < P.h_mix) kind = 0;
-                    if (kind < 0 && d.b < P.t_wet && P.rain) {
-                        int ir = (int)floorf((xn - P.x0) * P.inv_dx + 0.5f);
-                        int jr = (int)floorf((yn - P.y0) * P.inv_dy + 0.5f);
-                        ir = min(max(ir, 0), P.nx - 1);
-                        jr = min(max(jr, 0), P.ny - 1);
-                        int hr = (int)floorf(__fdiv_rn(tk - P.met_t0, P.met_dt));
-                        hr = min(max(hr, 0), P.n_t - 1);
-                        if (__ldg(P.rain + ((long long)hr * P.ny + jr) * P.nx + ir)) kind = 1;
-                    }
-                    if (kind >= 0) {
-                        st = kind == 0 ? ST_DEP_DRY : ST_DEP_WET;
-                        const unsigned long long v = to_fixed(mass_at(P, sc, sp, k), sc.scale);
-                        const int ix = (int)floorf((xn - P.cx0) * P.inv_cdx);
-                        const int iy = (int)floorf((yn - P.cy0) * P.inv_cdy);
-                        if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy) {
-                            const long long cell = ((long long)kind * P.cy + iy) * P.cx + ix;
-                            if (cell < 2 * n_dep) atomicAdd(scg.dep + cell, v);
-                        } else {
-                            atomicAdd(scg.ctr + (C_DEP_OUT_DRY + kind) * P.ctr_stride, v);
-                        }
-                        atomicAdd(scg.ctr + (C_DEP_DRY + kind) * P.ctr_stride, v);
-                    }
-                }
+                st = particle_step<true>(P, LV, T, sc, &scg, gid, sp, sig_h_uniform, x[j], y[j],
+                                         z[j], nullptr);
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;
             }

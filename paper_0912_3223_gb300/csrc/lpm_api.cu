@@ -13,6 +13,7 @@
 
 #include "../../include/lpm.h"
 #include "lpm_launch.h"
+#include "lpm_adjoint.h"
 
 using namespace lpm;
 
@@ -88,6 +89,22 @@ struct lpm_ctx {
     long long k = 0;                        // steps taken
     long long n_bins = 0;                   // snapshots taken
     int block = 256, ppt = 1, occ = 2;
+
+    // differentiable parameters (adjoint form): diffusivity scale and wind bias
+    double k_scale = 1.0, bias_u = 0.0, bias_v = 0.0;
+    // receptor / adjoint state
+    float *d_mq = nullptr;                  // dt / n_s per release step
+    short *d_qi = nullptr;                  // emission-series index per release step
+    float4 *d_ckpt = nullptr;
+    size_t d_ckpt_cap = 0;
+    float4 *d_rec = nullptr;
+    double *d_rC = nullptr, *d_rw = nullptr, *d_rgrad = nullptr;
+    size_t d_rbuf_cap = 0;
+    Tile *d_adj_tiles = nullptr;
+    std::vector<Tile> adj_tiles;
+    bool adj_tiles_valid = false;
+    std::vector<double> adj_sig;            // signature of the forward whose checkpoints are held
+    long long params_version = 0;
 
     // batched form: one CUDA graph per segment (memsets + the persistent launch)
     struct Graph {
@@ -197,8 +214,9 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     for (int k = 0; k < g.nz; ++k) P.zlev[k] = (float)c->zlev[k];
     P.dt = (float)g.dt;
     P.kh_uniform = (float)g.kh_uniform;
-    P.k_scale = 1.0f;
-    P.bias_u = P.bias_v = 0.0f;
+    P.k_scale = (float)c->k_scale;
+    P.bias_u = (float)c->bias_u;
+    P.bias_v = (float)c->bias_v;
     P.lambda = g.half_life_s > 0 ? (float)(std::log(2.0) / g.half_life_s) : 0.0f;
     P.h_mix = (float)g.h_mix;
     P.z_top = (float)g.z_top;
@@ -273,18 +291,40 @@ lpm_status upload_tables(lpm_ctx *c)
         d.part_first = h.part_first;
     }
     if (m0.empty()) m0.push_back(0.f);
+    std::vector<float> mq;
+    std::vector<short> qi;
+    for (size_t s = 0; s < c->scen.size(); ++s) {
+        const ScenHost &h = c->scen[s];
+        for (long long st = h.rel_first; st < h.rel_last; ++st) {
+            const long long cnt = release_count(h.n_total, h.rel_first, h.rel_last, st);
+            mq.push_back(cnt > 0 ? (float)(c->cfg.dt / (double)cnt) : 0.f);
+            long long idx = (long long)std::floor((double)st * c->cfg.dt / h.q_dt);
+            idx = std::max(0LL, std::min(idx, (long long)h.q.size() - 1));
+            qi.push_back((short)idx);
+        }
+    }
+    if (mq.empty()) { mq.push_back(0.f); qi.push_back(0); }
     if (m0.size() > c->d_m0_cap) {
-        if (c->d_m0) cudaFree(c->d_m0);
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (void *p : {(void *)c->d_m0, (void *)c->d_mq, (void *)c->d_qi})
+            if (p) cudaFree(p);
         c->d_m0 = nullptr;
+        c->d_mq = nullptr;
+        c->d_qi = nullptr;
         LPM_CUDA(c, cudaMalloc(&c->d_m0, m0.size() * sizeof(float)));
+        LPM_CUDA(c, cudaMalloc(&c->d_mq, m0.size() * sizeof(float)));
+        LPM_CUDA(c, cudaMalloc(&c->d_qi, m0.size() * sizeof(short)));
         c->d_m0_cap = m0.size();
     }
     // the stream may still read the old tables: order the copies on it
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     LPM_CUDA(c, cudaMemcpy(c->d_m0, m0.data(), m0.size() * sizeof(float), cudaMemcpyHostToDevice));
+    LPM_CUDA(c, cudaMemcpy(c->d_mq, mq.data(), mq.size() * sizeof(float), cudaMemcpyHostToDevice));
+    LPM_CUDA(c, cudaMemcpy(c->d_qi, qi.data(), qi.size() * sizeof(short), cudaMemcpyHostToDevice));
     LPM_CUDA(c, cudaMemcpy(c->d_scen, sd.data(), sd.size() * sizeof(ScenDev), cudaMemcpyHostToDevice));
     LPM_CUDA(c, cudaMemcpy(c->d_woff, woff.data(), woff.size() * sizeof(float2), cudaMemcpyHostToDevice));
     c->tables_dirty = false;
+    c->params_version++;
     drop_graphs(c);
     return LPM_OK;
 }
@@ -297,6 +337,27 @@ lpm_status check_device_error(lpm_ctx *c)
     if (e & ERR_NAN) return fail(c, LPM_E_NUMERIC, "a particle position became non-finite");
     if (e & ERR_INDEX) return fail(c, LPM_E_CUDA, "a grid index fell outside its array");
     if (e & ERR_TIMEOUT) return fail(c, LPM_E_TIMEOUT, "a bounded device loop hit its limit");
+    return LPM_OK;
+}
+
+// Initial mass per release step from the emission series (Sec. 3.2: masses assigned a
+// priori from the emission profile and the particle budget) and the fixed-point scale.
+lpm_status assign_masses(lpm_ctx *c, ScenHost &h)
+{
+    h.m0.assign((size_t)(h.rel_last - h.rel_first), 0.0);
+    h.total_mass = 0.0;
+    for (long long s = h.rel_first; s < h.rel_last; ++s) {
+        const long long cnt = release_count(h.n_total, h.rel_first, h.rel_last, s);
+        if (cnt <= 0) continue;
+        const double rate = emission_rate(h, c->cfg.dt, s);
+        h.m0[(size_t)(s - h.rel_first)] = rate * c->cfg.dt / (double)cnt;
+        h.total_mass += rate * c->cfg.dt;
+    }
+    int e = 0;
+    if (h.total_mass > 0) std::frexp(h.total_mass, &e);
+    h.shift = h.total_mass > 0 ? 61 - e : 0;
+    if (h.shift > 120 || h.shift < -120)
+        return fail(c, LPM_E_INVALID, "total mass %g outside the fixed-point range", h.total_mass);
     return LPM_OK;
 }
 
@@ -491,7 +552,8 @@ void lpm_destroy(lpm_ctx *c)
     cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->d_uvwk, c->d_kh, c->d_pair, c->d_khpair, c->d_rain, c->d_state, c->d_conc, c->d_dep, c->d_ctr,
                     c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles,
-                    c->d_zlut};
+                    c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
+                    c->d_rgrad, c->d_adj_tiles};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -557,14 +619,15 @@ lpm_status lpm_set_source(lpm_ctx *c, int scenario, double x, double y, double z
     if (!is_finite(x) || !is_finite(y) || !is_finite(z))
         return fail(c, LPM_E_INVALID, "source must be finite");
     ScenHost &h = c->scen[(size_t)scenario];
-    h.src_x = x; h.src_y = y; h.src_z = z;
+    std::vector<float> wo;
     if (wind_offset) {
-        h.wind_offset.assign(wind_offset, wind_offset + 2 * (size_t)c->cfg.n_met_t);
-        for (float v : h.wind_offset)
+        wo.assign(wind_offset, wind_offset + 2 * (size_t)c->cfg.n_met_t);
+        for (float v : wo)
             if (!std::isfinite(v)) return fail(c, LPM_E_INVALID, "wind offset not finite");
-    } else {
-        h.wind_offset.clear();
     }
+    if (h.src_x == x && h.src_y == y && h.src_z == z && h.wind_offset == wo) return LPM_OK;
+    h.src_x = x; h.src_y = y; h.src_z = z;
+    h.wind_offset = wo;
     c->tables_dirty = true;
     return LPM_OK;
 }
@@ -602,20 +665,8 @@ lpm_status lpm_release_range(lpm_ctx *c, int scenario, int64_t n_total, int64_t 
     h.rel_last = last;
     h.q.assign(q, q + n_q);
     h.q_dt = q_dt;
-    h.m0.assign((size_t)(last - first), 0.0);
-    h.total_mass = 0.0;
-    for (long long s = first; s < last; ++s) {
-        const long long cnt = release_count(n_total, first, last, s);
-        if (cnt <= 0) continue;
-        const double rate = emission_rate(h, c->cfg.dt, s);
-        h.m0[(size_t)(s - first)] = rate * c->cfg.dt / (double)cnt;
-        h.total_mass += rate * c->cfg.dt;
-    }
-    int e = 0;
-    if (h.total_mass > 0) std::frexp(h.total_mass, &e);
-    h.shift = h.total_mass > 0 ? 61 - e : 0;
-    if (h.shift > 120 || h.shift < -120)
-        return fail(c, LPM_E_INVALID, "total mass %g outside the fixed-point range", h.total_mass);
+    lpm_status mst = assign_masses(c, h);
+    if (mst != LPM_OK) return mst;
     h.released = true;
     c->n_slots_used += count;
     c->n_ids_used = std::max<long long>(c->n_ids_used, id_base + n_total);
@@ -967,6 +1018,208 @@ lpm_status lpm_fixed_state(lpm_ctx *c, int scenario, uint64_t *conc, size_t n_co
         counters[C_N_BINS] = c->n_bins;
     }
     if (shift) *shift = c->scen[(size_t)scenario].shift;
+    return LPM_OK;
+}
+
+lpm_status lpm_set_params(lpm_ctx *c, double k_scale, double bias_u, double bias_v)
+{
+    if (!c) return LPM_E_INVALID;
+    if (!(k_scale > 0) || !is_finite(k_scale) || !is_finite(bias_u) || !is_finite(bias_v))
+        return fail(c, LPM_E_INVALID, "k_scale must be > 0 and the bias finite");
+    if (c->k_scale == k_scale && c->bias_u == bias_u && c->bias_v == bias_v) return LPM_OK;
+    c->k_scale = k_scale;
+    c->bias_u = bias_u;
+    c->bias_v = bias_v;
+    c->params_version++;
+    drop_graphs(c);
+    return LPM_OK;
+}
+
+lpm_status lpm_set_emission(lpm_ctx *c, int scenario, const double *q, int n_q)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->n_released)
+        return fail(c, LPM_E_STATE, "scenario %d has not been released", scenario);
+    if (c->k != 0) return fail(c, LPM_E_STATE, "emission can change only at step 0 (after lpm_reset)");
+    if (!q || n_q < 1 || n_q > MAX_NQ) return fail(c, LPM_E_INVALID, "need 1 <= n_q <= %d", MAX_NQ);
+    for (int i = 0; i < n_q; ++i)
+        if (!is_finite(q[i]) || q[i] < 0) return fail(c, LPM_E_INVALID, "emission rates must be >= 0");
+    ScenHost &h = c->scen[(size_t)scenario];
+    if (h.q.size() == (size_t)n_q && std::equal(h.q.begin(), h.q.end(), q)) return LPM_OK;
+    h.q.assign(q, q + n_q);
+    lpm_status st = assign_masses(c, h);
+    if (st != LPM_OK) return st;
+    c->tables_dirty = true;
+    return LPM_OK;
+}
+
+namespace {
+
+int adj_nq(const lpm_ctx *c)
+{
+    size_t nq = 1;
+    for (const ScenHost &h : c->scen) nq = std::max(nq, h.q.size());
+    return (int)nq;
+}
+
+lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, int every,
+                       AdjParams &A, StepParams &P)
+{
+    const lpm_config &g = c->cfg;
+    if (R < 1 || R > MAX_REC || !rec) return fail(c, LPM_E_INVALID, "need 1 <= R <= %d receptors", MAX_REC);
+    if (!(bandwidth > 0) || every < 1) return fail(c, LPM_E_INVALID, "bandwidth > 0 and every >= 1");
+    if (g.drift_correction) return fail(c, LPM_E_INVALID, "the adjoint does not support drift_correction");
+    if (c->n_released != g.n_scenarios)
+        return fail(c, LPM_E_STATE, "%d of %d scenarios released", c->n_released, g.n_scenarios);
+    if (adj_nq(c) > MAX_NQ) return fail(c, LPM_E_INVALID, "emission series longer than %d", MAX_NQ);
+    for (int t = 0; t < g.n_met_t; ++t)
+        if (!c->met_set[(size_t)t]) return fail(c, LPM_E_STATE, "met slab %d not set", t);
+    const int n_samp = (int)(g.n_steps / every);
+    if (n_samp < 1) return fail(c, LPM_E_INVALID, "no sample step in the run");
+    lpm_status st = upload_tables(c);
+    if (st != LPM_OK) return st;
+    fill_params(c, P);
+    // tiles of ADJ_BLOCK particles over every held particle
+    if (!c->adj_tiles_valid) {
+        c->adj_tiles.clear();
+        for (size_t s = 0; s < c->scen.size(); ++s)
+            for (long long p = 0; p < c->scen[s].n; p += ADJ_BLOCK) {
+                Tile t;
+                t.scen = (int)s;
+                t.first = c->scen[s].first_slot + p;
+                t.count = (int)std::min<long long>(ADJ_BLOCK, c->scen[s].n - p);
+                c->adj_tiles.push_back(t);
+            }
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->d_adj_tiles) cudaFree(c->d_adj_tiles);
+        c->d_adj_tiles = nullptr;
+        LPM_CUDA(c, cudaMalloc(&c->d_adj_tiles, std::max<size_t>(1, c->adj_tiles.size()) * sizeof(Tile)));
+        LPM_CUDA(c, cudaMemcpy(c->d_adj_tiles, c->adj_tiles.data(), c->adj_tiles.size() * sizeof(Tile),
+                               cudaMemcpyHostToDevice));
+        c->adj_tiles_valid = true;
+    }
+    const int n_ck = (int)((g.n_steps + CK - 1) / CK);
+    const size_t need_ck = (size_t)n_ck * (size_t)c->n_slots_used;
+    if (need_ck > c->d_ckpt_cap) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->d_ckpt) cudaFree(c->d_ckpt);
+        c->d_ckpt = nullptr;
+        LPM_CUDA(c, cudaMalloc(&c->d_ckpt, need_ck * sizeof(float4)));
+        c->d_ckpt_cap = need_ck;
+    }
+    const size_t ns = (size_t)g.n_scenarios;
+    const int nq = adj_nq(c), ng = 3 + nq + 3;
+    const size_t need_buf = std::max((size_t)MAX_REC * ns, (size_t)ng * ns);
+    if (!c->d_rec) LPM_CUDA(c, cudaMalloc(&c->d_rec, MAX_REC * sizeof(float4)));
+    if (need_buf > c->d_rbuf_cap) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (double *p : {c->d_rC, c->d_rw, c->d_rgrad})
+            if (p) cudaFree(p);
+        c->d_rC = c->d_rw = c->d_rgrad = nullptr;
+        LPM_CUDA(c, cudaMalloc(&c->d_rC, need_buf * sizeof(double)));
+        LPM_CUDA(c, cudaMalloc(&c->d_rw, need_buf * sizeof(double)));
+        LPM_CUDA(c, cudaMalloc(&c->d_rgrad, need_buf * sizeof(double)));
+        c->d_rbuf_cap = need_buf;
+    }
+    std::vector<float4> hr((size_t)R);
+    for (int r = 0; r < R; ++r) {
+        if (!is_finite(rec[3 * r]) || !is_finite(rec[3 * r + 1]) || !is_finite(rec[3 * r + 2]))
+            return fail(c, LPM_E_INVALID, "receptor %d not finite", r);
+        hr[(size_t)r] = make_float4((float)rec[3 * r], (float)rec[3 * r + 1], (float)rec[3 * r + 2], 0.f);
+    }
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_rec, hr.data(), hr.size() * sizeof(float4),
+                                cudaMemcpyHostToDevice, c->stream));
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::memset(&A, 0, sizeof A);
+    const double s2 = bandwidth * bandwidth;
+    A.rec = c->d_rec;
+    A.R = R;
+    A.inv2s2 = (float)(1.0 / (2.0 * s2));
+    A.norm = (float)std::pow(2.0 * 3.14159265358979323846 * s2, -1.5);
+    A.inv_s2 = (float)(1.0 / s2);
+    A.cut2 = (float)(36.0 * s2);
+    A.every = every;
+    A.inv_ns = (float)(1.0 / n_samp);
+    A.n_steps = (int)g.n_steps;
+    A.n_ck = n_ck;
+    A.ckpt = c->d_ckpt;
+    A.n_slots = c->n_slots_used;
+    A.tiles = c->d_adj_tiles;
+    A.C = c->d_rC;
+    A.w = c->d_rw;
+    A.grad = c->d_rgrad;
+    A.ng = ng;
+    A.nq = nq;
+    A.mq = c->d_mq;
+    A.qi = c->d_qi;
+    return LPM_OK;
+}
+
+std::vector<double> adj_signature(const lpm_ctx *c, const double *rec, int R, double bandwidth,
+                                  int every)
+{
+    std::vector<double> sig(rec, rec + 3 * (size_t)R);
+    sig.push_back(bandwidth);
+    sig.push_back(every);
+    sig.push_back((double)c->params_version);
+    return sig;
+}
+
+lpm_status adj_forward(lpm_ctx *c, const double *rec, int R, double bandwidth, int every,
+                       AdjParams &A, StepParams &P)
+{
+    lpm_status st = adj_prepare(c, rec, R, bandwidth, every, A, P);
+    if (st != LPM_OK) return st;
+    LPM_CUDA(c, cudaMemsetAsync(c->d_rC, 0, (size_t)c->cfg.n_scenarios * R * sizeof(double), c->stream));
+    LPM_CUDA(c, launch_adj_forward(c->stream, P, A, (int)c->adj_tiles.size()));
+    c->n_launches++;
+    st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    c->adj_sig = adj_signature(c, rec, R, bandwidth, every);
+    return LPM_OK;
+}
+
+}  // namespace
+
+lpm_status lpm_receptors(lpm_ctx *c, const double *rec, int R, double bandwidth, int sample_every,
+                         double *C)
+{
+    if (!c) return LPM_E_INVALID;
+    if (!C) return fail(c, LPM_E_INVALID, "C is NULL");
+    AdjParams A;
+    StepParams P;
+    lpm_status st = adj_forward(c, rec, R, bandwidth, sample_every, A, P);
+    if (st != LPM_OK) return st;
+    LPM_CUDA(c, cudaMemcpy(C, c->d_rC, (size_t)c->cfg.n_scenarios * R * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+    return LPM_OK;
+}
+
+lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, int sample_every,
+                       const double *dL_dC, double *grad)
+{
+    if (!c) return LPM_E_INVALID;
+    if (!dL_dC || !grad) return fail(c, LPM_E_INVALID, "dL_dC and grad are required");
+    AdjParams A;
+    StepParams P;
+    lpm_status st;
+    if (c->adj_sig != adj_signature(c, rec, R, bandwidth, sample_every)) {
+        st = adj_forward(c, rec, R, bandwidth, sample_every, A, P);   // checkpoints
+    } else {
+        st = adj_prepare(c, rec, R, bandwidth, sample_every, A, P);
+    }
+    if (st != LPM_OK) return st;
+    const size_t ns = (size_t)c->cfg.n_scenarios;
+    for (size_t i = 0; i < ns * (size_t)R; ++i)
+        if (!is_finite(dL_dC[i])) return fail(c, LPM_E_INVALID, "dL_dC not finite");
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_rw, dL_dC, ns * R * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_rgrad, 0, ns * A.ng * sizeof(double), c->stream));
+    LPM_CUDA(c, launch_adj_backward(c->stream, P, A, (int)c->adj_tiles.size()));
+    c->n_launches++;
+    st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    LPM_CUDA(c, cudaMemcpy(grad, c->d_rgrad, ns * A.ng * sizeof(double), cudaMemcpyDeviceToHost));
     return LPM_OK;
 }
 

@@ -27,7 +27,8 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_release", "lpm_step", "lpm_current_step", "lpm_concentration",
            "lpm_deposition", "lpm_budget", "lpm_particles", "lpm_fixed_state",
            "lpm_set_launch", "lpm_sync", "lpm_draws", "lpm_release_range", "lpm_reset",
-           "lpm_set_profiling", "lpm_stats"]
+           "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
+           "lpm_receptors", "lpm_adjoint"]
 
 
 class LpmError(RuntimeError):
@@ -93,13 +94,18 @@ def load() -> C.CDLL:
     L.lpm_reset.argtypes = [vp]
     L.lpm_set_profiling.argtypes = [vp, C.c_int]
     L.lpm_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), dp]
+    L.lpm_set_params.argtypes = [vp, C.c_double, C.c_double, C.c_double]
+    L.lpm_set_emission.argtypes = [vp, C.c_int, dp, C.c_int]
+    L.lpm_receptors.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp]
+    L.lpm_adjoint.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp, dp]
     L.lpm_draws.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
                             C.c_uint32, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
     for name in ("lpm_create", "lpm_set_met", "lpm_set_source", "lpm_release", "lpm_step",
                  "lpm_current_step", "lpm_concentration", "lpm_deposition", "lpm_budget",
                  "lpm_particles", "lpm_fixed_state", "lpm_set_launch", "lpm_sync",
                  "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
-                 "lpm_stats"):
+                 "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
+                 "lpm_adjoint"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -209,6 +215,38 @@ def lpm_stats(ctx):
     a, b, ms = C.c_int64(), C.c_int64(), C.c_double()
     _check(ctx, load().lpm_stats(C.c_void_p(ctx), C.byref(a), C.byref(b), C.byref(ms)))
     return int(a.value), int(b.value), float(ms.value)
+
+
+def lpm_set_params(ctx, k_scale: float = 1.0, bias_u: float = 0.0, bias_v: float = 0.0) -> None:
+    _check(ctx, load().lpm_set_params(C.c_void_p(ctx), float(k_scale), float(bias_u),
+                                      float(bias_v)))
+
+
+def lpm_set_emission(ctx, scenario: int, q) -> None:
+    qa = np.ascontiguousarray(q, dtype=np.float64)
+    _check(ctx, load().lpm_set_emission(C.c_void_p(ctx), int(scenario), _ptr(qa, C.c_double),
+                                        int(qa.size)))
+
+
+def lpm_receptors(ctx, n_scenarios: int, receptors, bandwidth: float, sample_every: int):
+    """Receptor concentrations [n_scenarios][R]."""
+    rec = np.ascontiguousarray(receptors, dtype=np.float64).reshape(-1, 3)
+    out = np.empty((n_scenarios, rec.shape[0]), dtype=np.float64)
+    _check(ctx, load().lpm_receptors(C.c_void_p(ctx), _ptr(rec, C.c_double), rec.shape[0],
+                                     float(bandwidth), int(sample_every), _ptr(out, C.c_double)))
+    return out
+
+
+def lpm_adjoint(ctx, receptors, bandwidth: float, sample_every: int, dL_dC, n_q: int):
+    """Gradient [n_scenarios][3 + n_q + 3] of sum(dL_dC * C)."""
+    rec = np.ascontiguousarray(receptors, dtype=np.float64).reshape(-1, 3)
+    w = np.ascontiguousarray(dL_dC, dtype=np.float64)
+    w = w.reshape(-1, rec.shape[0])
+    out = np.empty((w.shape[0], 3 + n_q + 3), dtype=np.float64)
+    _check(ctx, load().lpm_adjoint(C.c_void_p(ctx), _ptr(rec, C.c_double), rec.shape[0],
+                                   float(bandwidth), int(sample_every), _ptr(w, C.c_double),
+                                   _ptr(out, C.c_double)))
+    return out
 
 
 def lpm_step(ctx, n: int) -> None:

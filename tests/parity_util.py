@@ -94,15 +94,22 @@ def cell_index(cfg, pos, horizontal=False):
 
 
 def compare(cfg, g, o, pos_tol=POS_TOL_M, grid_tol=GRID_REL_L1, check_grid=True,
-            max_excluded_frac=0.01):
+            max_excluded_frac=0.01, sens=None, max_chaotic_frac=0.01):
     """Element-wise comparison of a GPU run ``g`` with an oracle run ``o`` over the same
-    particles (all of the release). Returns a report dict; asserts the bars."""
+    particles (all of the release). ``sens`` (the oracle's perturbation growth per
+    particle) marks chaotic paths, which are reported and excluded like ambiguous ones.
+    Returns a report dict; asserts the bars."""
     rep = {}
     assert np.array_equal(g["release"], o["release"]), "release steps differ"
     released = o["status"] != li.STATUS_UNRELEASED
     assert np.array_equal(g["status"] == li.STATUS_UNRELEASED, ~released)
     # particles that took a decision within pos_tol of its boundary may branch either way
     ambiguous = (o["margin"] < pos_tol) & released
+    if sens is not None:
+        ch = oracle.chaotic(cfg, sens, o["pos"], pos_tol) & released & ~ambiguous
+        rep["chaotic"] = int(ch.sum())
+        assert ch.mean() <= max_chaotic_frac, rep
+        ambiguous = ambiguous | ch
     rep["ambiguous"] = int(ambiguous.sum())
     assert ambiguous.mean() <= max_excluded_frac, rep
     ok = ~ambiguous & released

@@ -54,12 +54,13 @@ def test_batched_matches_oracle_per_scenario(small_ensemble):
     for s, sc in enumerate(cfg.scenarios):
         n = sc.release.n_particles
         o = oracle.run(cfg, scenario=s)
+        sens = oracle.sensitivity(cfg, scenario=s)
         g = dict(pos=xyz[off:off + n].astype(np.float64), tag=tag[off:off + n],
                  status=(tag[off:off + n] >> 28).astype(np.int32),
                  release=(tag[off:off + n] & 0x0FFFFFFF).astype(np.int64),
                  conc_mass=scen[s]["conc"] * vol,
                  dep_mass=np.stack(scen[s]["dep"]) * area)
-        rep = compare(cfg, g, o)
+        rep = compare(cfg, g, o, sens=sens)
         print(f"scenario {s}: {rep}")
         c = scen[s]["counters"]
         assert int(c[4]) == o["active_steps"]

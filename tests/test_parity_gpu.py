@@ -86,7 +86,8 @@ def test_cfg1_parity_360_steps(cfg1_small):
     deposition, lateral exit), all 20000 particles after 360 steps."""
     g = run_gpu(cfg1_small, n_run=360)
     o = oracle.run(cfg1_small, n_run=360)
-    rep = compare(cfg1_small, g, o, check_grid=False)
+    sens = oracle.sensitivity(cfg1_small, n_run=360)
+    rep = compare(cfg1_small, g, o, check_grid=False, sens=sens)
     print("cfg1 360 steps:", rep)
     # budget after 360 steps (not a bin step: compare the airborne + event totals)
     np.testing.assert_allclose(g["budget"][0], o["budget"][0], rtol=1e-6)
@@ -97,7 +98,7 @@ def test_cfg1_parity_bin_step(cfg1_small):
     """Same inputs stepped to the first hourly snapshot: grids and deposition compared."""
     g = run_gpu(cfg1_small, n_run=120)
     o = oracle.run(cfg1_small, n_run=120)
-    rep = compare(cfg1_small, g, o)
+    rep = compare(cfg1_small, g, o, sens=oracle.sensitivity(cfg1_small, n_run=120))
     print("cfg1 120 steps:", rep)
     _integer_identity(g)
     assert int(g["counters"][4]) == o["active_steps"]
@@ -132,7 +133,10 @@ def test_cfg1_full_size_sampled():
         b = sim.budget()
         cfix2, _, ctr2, _ = sim.fixed_state()
     o360 = oracle.run(cfg, sel=sel, n_run=360)
-    ok = (o360["margin"] >= POS_TOL_M) & (o360["status"] != li.STATUS_UNRELEASED)
+    sens = oracle.sensitivity(cfg, sel=sel, n_run=360)
+    ch = oracle.chaotic(cfg, sens, o360["pos"], POS_TOL_M)
+    ok = (o360["margin"] >= POS_TOL_M) & (o360["status"] != li.STATUS_UNRELEASED) & ~ch
+    assert ch.mean() <= 0.01
     st = (g360["tag"] >> 28).astype(np.int32)
     assert np.array_equal(st[ok], o360["status"][ok])
     d = np.linalg.norm(g360["pos"][ok] - o360["pos"][ok], axis=1)
@@ -178,7 +182,7 @@ def test_ragged_and_sparse_releases(n, first, last):
                                                  first, last))
     g = run_gpu(cfg)
     o = oracle.run(cfg)
-    compare(cfg, g, o)
+    compare(cfg, g, o, sens=oracle.sensitivity(cfg))
     _integer_identity(g)
 
 
