@@ -403,12 +403,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms")
+    ap.add_argument("--only", choices=["batched", "adjoint"], default=None,
+                    help="run one form alone and print its measurement (profiling aid)")
     ap.add_argument("--batched-block", type=int, default=256)
     ap.add_argument("--batched-ppt", type=int, default=1)
     ap.add_argument("--batched-occ", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        from paper_0912_3223_gb300 import build as pkg_build
+        pkg_build.build()
+        stream = torch.cuda.Stream()
+        fn = measure_batched if args.only == "batched" else measure_adjoint
+        print(json.dumps({"form": args.only, **fn(args, stream)}), flush=True)
+        return 0
     return run_gpu(args)
 
 
