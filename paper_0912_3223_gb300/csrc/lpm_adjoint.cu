@@ -182,97 +182,110 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
     float mu0 = 0.f, mu1 = 0.f, mu2 = 0.f;
     float gsk = 0.f, gbu = 0.f, gbv = 0.f, gq = 0.f;
     int qidx = 0;
-    if ((int)threadIdx.x < tile.count) {
-        const long long slot = tile.first + threadIdx.x;
-        const unsigned long long gid = (unsigned long long)(sc.id0 + (slot - sc.first_slot));
-        const int sp = (int)release_step_of(sc, slot);
-        const int tix = sc.m0_off + (sp - sc.rel_first);
-        const float m0 = __ldg(P.m0 + tix);
-        const float mq = __ldg(A.mq + tix);
-        qidx = __ldg(A.qi + tix);
-        float4 seg[CK + 1];
-        signed char sfold[CK];
-        for (int c = A.n_ck - 1; c >= 0; --c) {
-            const int k_lo = c * CK, k_hi = min(A.n_steps, k_lo + CK);
-            if (sp >= k_hi) continue;
+    // Loops run over warp-uniform step ranges with per-lane predicates, so the lanes of a
+    // warp (consecutive particles of one release step) stay converged through the
+    // recomputation and the reverse sweep.
+    const bool valid = (int)threadIdx.x < tile.count;
+    const long long slot = tile.first + (valid ? threadIdx.x : 0);
+    const unsigned long long gid = (unsigned long long)(sc.id0 + (slot - sc.first_slot));
+    const int sp = (int)release_step_of(sc, slot);
+    const int tix = sc.m0_off + (sp - sc.rel_first);
+    const float m0 = __ldg(P.m0 + tix);
+    const float mq = __ldg(A.mq + tix);
+    qidx = __ldg(A.qi + tix);
+    float4 seg[CK + 1];
+    signed char sfold[CK];
+    for (int c = A.n_ck - 1; c >= 0; --c) {
+        const int k_lo = c * CK, k_hi = min(A.n_steps, k_lo + CK);
+        bool run = valid && sp < k_hi;
+        float x = 0.f, y = 0.f, z = 0.f;
+        if (run) {
             const float4 s0 = A.ckpt[(long long)c * A.n_slots + slot];
             const uint32_t st0 = __float_as_uint(s0.w) >> TAG_SHIFT;
-            if (st0 != ST_ACTIVE && st0 != ST_UNRELEASED) continue;   // event before k_lo
-            float x = s0.x, y = s0.y, z = s0.z;
-            const int kstart = max(k_lo, sp);
+            run = st0 == ST_ACTIVE || st0 == ST_UNRELEASED;        // else: event before k_lo
+            x = s0.x; y = s0.y; z = s0.z;
             if (st0 == ST_UNRELEASED) { x = sc.src_x; y = sc.src_y; z = sc.src_z; }
-            // recompute the segment
-            int n = 0;
-            bool ev = false;
-            for (int k = kstart; k < k_hi; ++k) {
-                seg[n] = make_float4(x, y, z, 0.f);
+        }
+        if (!__any_sync(0xffffffffu, run)) continue;
+        const int kstart = max(k_lo, sp);
+        // recompute the segment: seg[k - k_lo] = state before step k
+        bool alive = run;
+        int klast = k_lo - 1;                // last step this lane took
+        bool ev = false;
+        for (int k = k_lo; k < k_hi; ++k) {
+            if (alive && k >= kstart) {
+                seg[k - k_lo] = make_float4(x, y, z, 0.f);
                 const StepTime T = step_time(P, sc, k);
                 float fs;
                 const uint32_t st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp,
                                                          sig_h_uniform, x, y, z, &fs);
-                sfold[n] = (signed char)fs;
-                ++n;
-                if (st != ST_ACTIVE) { ev = true; break; }
-            }
-            seg[n] = make_float4(x, y, z, 0.f);
-            // reverse sweep
-            for (int i = n - 1; i >= 0; --i) {
-                const int k = kstart + i;
-                if ((k + 1) % A.every == 0 && !(ev && i == n - 1)) {
-                    const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
-                    const float m = m0 * decay;
-                    const float4 X = seg[i + 1];
-                    for (int r = 0; r < A.R; ++r) {
-                        const float4 q = s_rec[r];
-                        const float dx = X.x - q.x, dy = X.y - q.y, dz = X.z - q.z, dzi = X.z + q.z;
-                        const float h2 = dx * dx + dy * dy;
-                        const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
-                        if (d1 > A.cut2 && d2 > A.cut2) continue;
-                        const float e1 = A.norm * expf(-d1 * A.inv2s2);
-                        const float e2 = A.norm * expf(-d2 * A.inv2s2);
-                        const float wr = s_w[r];
-                        const float c1 = -wr * m * A.inv_s2;
-                        mu0 += c1 * (e1 + e2) * dx;
-                        mu1 += c1 * (e1 + e2) * dy;
-                        mu2 += c1 * (e1 * dz + e2 * dzi);
-                        gq += wr * mq * decay * (e1 + e2);
-                    }
-                }
-                // undo step k at the state before it
-                const float4 X = seg[i];
-                const StepTime T = step_time(P, sc, k);
-                float val[5], g[5][3];
-                sample_met_grad(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
-                const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
-                                           P.seed_lo, P.seed_hi);
-                float n0, n1, n2;
-                normals3(w, n0, n1, n2);
-                const float fold = (float)sfold[i];
-                const float kh = P.k_scale * val[4], kz = P.k_scale * val[3];
-                const float sig_h = sqrtf(2.0f * kh * P.dt), sig_z = sqrtf(2.0f * kz * P.dt);
-                const float ch = val[4] > 0.0f ? sq2dt / (2.0f * sqrtf(val[4])) : 0.0f;
-                const float cz = val[3] > 0.0f ? sq2dt / (2.0f * sqrtf(val[3])) : 0.0f;
-                // parameter partials: s_K, b_u, b_v
-                const float inv2sk = 0.5f / P.k_scale;
-                gsk += (mu0 * n0 * sig_h + mu1 * n1 * sig_h + mu2 * fold * n2 * sig_z) * inv2sk;
-                gbu += mu0 * P.dt;
-                gbv += mu1 * P.dt;
-                // mu <- J^T mu
-                const float mz = mu2 * fold;
-                float nm[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float jx = P.dt * g[0][d] + n0 * ch * g[4][d];
-                    const float jy = P.dt * g[1][d] + n1 * ch * g[4][d];
-                    const float jz = P.dt * g[2][d] + n2 * cz * g[3][d];
-                    nm[d] = mu0 * jx + mu1 * jy + mz * jz;
-                }
-                mu0 += nm[0];
-                mu1 += nm[1];
-                mu2 = mz + nm[2];
+                sfold[k - k_lo] = (signed char)fs;
+                klast = k;
+                if (st != ST_ACTIVE) { alive = false; ev = true; }
             }
         }
+        if (run) seg[klast + 1 - k_lo] = make_float4(x, y, z, 0.f);
+        __syncwarp();
+        // reverse sweep over the steps this lane took
+        for (int k = k_hi - 1; k >= k_lo; --k) {
+            if (!(run && k >= kstart && k <= klast)) continue;
+            const int i = k - k_lo;
+            if ((k + 1) % A.every == 0 && !(ev && k == klast)) {
+                const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
+                const float m = m0 * decay;
+                const float4 X = seg[i + 1];
+                for (int r = 0; r < A.R; ++r) {
+                    const float4 q = s_rec[r];
+                    const float dx = X.x - q.x, dy = X.y - q.y, dz = X.z - q.z, dzi = X.z + q.z;
+                    const float h2 = dx * dx + dy * dy;
+                    const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
+                    if (d1 > A.cut2 && d2 > A.cut2) continue;
+                    const float e1 = A.norm * expf(-d1 * A.inv2s2);
+                    const float e2 = A.norm * expf(-d2 * A.inv2s2);
+                    const float wr = s_w[r];
+                    const float c1 = -wr * m * A.inv_s2;
+                    mu0 += c1 * (e1 + e2) * dx;
+                    mu1 += c1 * (e1 + e2) * dy;
+                    mu2 += c1 * (e1 * dz + e2 * dzi);
+                    gq += wr * mq * decay * (e1 + e2);
+                }
+            }
+            // undo step k at the state before it
+            const float4 X = seg[i];
+            const StepTime T = step_time(P, sc, k);
+            float val[5], g[5][3];
+            sample_met_grad(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
+            const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
+                                       P.seed_lo, P.seed_hi);
+            float n0, n1, n2;
+            normals3(w, n0, n1, n2);
+            const float fold = (float)sfold[i];
+            const float kh = P.k_scale * val[4], kz = P.k_scale * val[3];
+            const float sig_h = sqrtf(2.0f * kh * P.dt), sig_z = sqrtf(2.0f * kz * P.dt);
+            const float ch = val[4] > 0.0f ? sq2dt / (2.0f * sqrtf(val[4])) : 0.0f;
+            const float cz = val[3] > 0.0f ? sq2dt / (2.0f * sqrtf(val[3])) : 0.0f;
+            // parameter partials: s_K, b_u, b_v
+            const float inv2sk = 0.5f / P.k_scale;
+            gsk += (mu0 * n0 * sig_h + mu1 * n1 * sig_h + mu2 * fold * n2 * sig_z) * inv2sk;
+            gbu += mu0 * P.dt;
+            gbv += mu1 * P.dt;
+            // mu <- J^T mu
+            const float mz = mu2 * fold;
+            float nm[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float jx = P.dt * g[0][d] + n0 * ch * g[4][d];
+                const float jy = P.dt * g[1][d] + n1 * ch * g[4][d];
+                const float jz = P.dt * g[2][d] + n2 * cz * g[3][d];
+                nm[d] = mu0 * jx + mu1 * jy + mz * jz;
+            }
+            mu0 += nm[0];
+            mu1 += nm[1];
+            mu2 = mz + nm[2];
+        }
+        __syncwarp();
     }
+    if (!valid) { mu0 = mu1 = mu2 = gsk = gbu = gbv = gq = 0.f; }
     // block reductions (FP64) and one atomic per parameter per block
     for (int o = 16; o > 0; o >>= 1) {
         mu0 += __shfl_xor_sync(0xffffffffu, mu0, o);
