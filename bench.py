@@ -38,6 +38,11 @@ WORKLOAD = ("plain method, realistic: 1e7 particles, 24 h at dt=30 s (2880 steps
 # deposition streams) 2 x 98, uniforms 12, Box-Muller 11, 4D gather index and weight math
 # 30, 16-corner lerps of 4 components 120, move 18, reflection/exit 8, deposition test 4.
 OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
+# DRAM traffic per advance launch from the ncu capture summarised in
+# profiles/advance_kernel_plain_1e7x2880.md (mean of two mid-run launches, read + write),
+# valid while the kernel sources hash to the values recorded there.
+ADVANCE_TRAFFIC_BYTES = 0.5 * ((119.247616 + 58.066688) + (126.788096 + 65.928192)) * 1e6
+ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "5f935d70", "lpm_device.cuh": "5db607d1"}
 SM_COUNT = 152
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
 SM_MAX_MHZ = 2070.0
@@ -48,6 +53,17 @@ def _env_int(name, default):
         return int(os.environ.get(name, default))
     except ValueError:
         return default
+
+
+def advance_traffic():
+    """The captured per-launch DRAM traffic, or None once the kernel sources changed."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_0912_3223_gb300", "csrc")
+    for name, digest in ADVANCE_TRAFFIC_SOURCES.items():
+        with open(os.path.join(csrc, name), "rb") as f:
+            if not hashlib.sha1(f.read()).hexdigest().startswith(digest):
+                return None
+    return ADVANCE_TRAFFIC_BYTES
 
 
 def read_peaks():
@@ -351,7 +367,8 @@ def run_gpu(args):
         "bound": "alu", "kernel": "advance_kernel",
         "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
         "frac": achieved / alu_peak if achieved else None,
-        "traffic": None,
+        "traffic": advance_traffic(),
+        "traffic_unit": "bytes per advance launch (ncu capture, mid-run launches)",
         "peak_source": (f"derived: {SM_COUNT} SMs x {LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz "
                         "(one 32-bit op per lane per clock)"),
         "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
