@@ -268,6 +268,27 @@ lpm_status lpm_adjoint(lpm_ctx *ctx, const double *receptors, int R, double band
 lpm_status lpm_draws(uint64_t seed, const uint64_t *pid, const uint32_t *step, uint32_t stream,
                      int64_t n, uint32_t *words, float *normals);
 
+/* Largest n lpm_draws_static accepts. */
+#define LPM_DRAWS_STATIC_MAX 65536
+
+/*
+ * lpm_draws without device allocation (the paper has no counterpart: this is an
+ * interface for callers that must not allocate device memory, e.g. applications whose
+ * device memory is owned by their own pool or capped by a fixed budget). Same arguments
+ * and results as lpm_draws; 0 <= n <= LPM_DRAWS_STATIC_MAX, larger n is rejected with
+ * LPM_E_INVALID. Inputs and outputs are staged through one fixed device array in the
+ * library (about 2.6 MB, held by every GPU that loads the library until the process
+ * exits); the call makes no cudaMalloc, cudaFree or other allocating call. The first
+ * call on each device does a one-time set-up: it looks up that array's device address
+ * with the device current. Make that first call before any stream capture begins.
+ * Synchronous on the legacy default stream. Every call shares the one array, which keeps
+ * the last call's contents (each call overwrites what it uses); calls that overlap on the
+ * same GPU, e.g. from several host threads, race with each other.
+ * Errors: lpm_last_error(NULL).
+ */
+lpm_status lpm_draws_static(uint64_t seed, const uint64_t *pid, const uint32_t *step,
+                            uint32_t stream, int64_t n, uint32_t *words, float *normals);
+
 #ifdef __cplusplus
 }
 #endif

@@ -454,6 +454,11 @@ void drop_graphs(lpm_ctx *c)
 
 }  // namespace
 
+namespace lpm {
+// Records the text lpm_last_error(NULL) returns (entry points without a context).
+void set_global_error(const char *msg) { g_create_error = msg; }
+}  // namespace lpm
+
 // =====================================================================================
 // C ABI
 // =====================================================================================

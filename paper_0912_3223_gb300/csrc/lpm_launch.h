@@ -38,6 +38,8 @@ cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned
 cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *state, int scen,
                           long long n, int k_now);
 
+void set_global_error(const char *msg);
+
 struct AdjParams;
 cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles);
 cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles);

@@ -28,7 +28,7 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_deposition", "lpm_budget", "lpm_particles", "lpm_fixed_state",
            "lpm_set_launch", "lpm_sync", "lpm_draws", "lpm_release_range", "lpm_reset",
            "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
-           "lpm_receptors", "lpm_adjoint"]
+           "lpm_receptors", "lpm_adjoint", "lpm_draws_static"]
 
 
 class LpmError(RuntimeError):
@@ -98,6 +98,8 @@ def load() -> C.CDLL:
     L.lpm_set_emission.argtypes = [vp, C.c_int, dp, C.c_int]
     L.lpm_receptors.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp]
     L.lpm_adjoint.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp, dp]
+    L.lpm_draws_static.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
+                                   C.c_uint32, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
     L.lpm_draws.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
                             C.c_uint32, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
     for name in ("lpm_create", "lpm_set_met", "lpm_set_source", "lpm_release", "lpm_step",
@@ -105,7 +107,7 @@ def load() -> C.CDLL:
                  "lpm_particles", "lpm_fixed_state", "lpm_set_launch", "lpm_sync",
                  "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
                  "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
-                 "lpm_adjoint"):
+                 "lpm_adjoint", "lpm_draws_static"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -317,6 +319,22 @@ def lpm_draws(seed: int, pid, step, stream: int = 0):
     _check(None, load().lpm_draws(int(seed), _ptr(pid, C.c_uint64), _ptr(step, C.c_uint32),
                                   int(stream), pid.size, _ptr(words, C.c_uint32),
                                   _ptr(nrm, C.c_float)))
+    return words, nrm
+
+
+DRAWS_STATIC_MAX = 65536
+
+
+def lpm_draws_static(seed: int, pid, step, stream: int = 0):
+    """As ``lpm_draws``, without device allocation (staged through the library's fixed
+    device array; at most DRAWS_STATIC_MAX draws per call)."""
+    pid = np.ascontiguousarray(pid, dtype=np.uint64)
+    step = np.ascontiguousarray(np.broadcast_to(step, pid.shape), dtype=np.uint32)
+    words = np.empty((pid.size, 4), dtype=np.uint32)
+    nrm = np.empty((pid.size, 3), dtype=np.float32)
+    _check(None, load().lpm_draws_static(int(seed), _ptr(pid, C.c_uint64), _ptr(step, C.c_uint32),
+                                         int(stream), pid.size, _ptr(words, C.c_uint32),
+                                         _ptr(nrm, C.c_float)))
     return words, nrm
 
 
