@@ -267,6 +267,74 @@ def measure_adjoint(args, stream):
             "active_particle_steps": active, "checkpoint_every": 64}
 
 
+def measure_inversion(args, stream):
+    """Batched source inversion: 64 candidate sources x 1e5 particles on the adjoint
+    workload, 20 Adam iterations (one receptor forward + one adjoint launch for all
+    candidates per iteration) against observations of a hidden source."""
+    import numpy as np
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim
+    from paper_0912_3223_gb300.inversion import invert, observe
+    cand, obs, hidden = li.make_cfg4()
+    rec = li.make_receptors()
+    with torch.cuda.stream(stream):
+        with Sim(obs, stream=stream) as so:
+            c_obs = observe(so, rec, 200.0, 18)
+        sim = Sim(cand, stream=stream)
+    try:
+        sim.reset()
+        sim.step(cand.n_steps)
+        active = sum(int(sim.fixed_state(s)[2][4]) for s in range(cand.n_scenarios))
+        t0 = time.perf_counter()
+        res = invert(sim, rec, c_obs, n_iter=20)
+        t = time.perf_counter() - t0
+    finally:
+        sim.close()
+    h = np.array(hidden)
+    d0 = np.linalg.norm(res.sources[0, :, :2] - h[:2], axis=1).min()
+    d1 = float(np.linalg.norm(res.sources[-1, res.best, :2] - h[:2]))
+    return {"value": 20 * active / t, "unit": UNIT,
+            "note": "20 x (forward + adjoint) active particle-steps / wall time of the inversion",
+            "candidates": cand.n_scenarios, "particles": cand.n_particles,
+            "ms_per_iteration": 1e3 * t / 20,
+            "ms_forward_total": 1e3 * res.timings["forward"],
+            "ms_adjoint_total": 1e3 * res.timings["adjoint"],
+            "best_loss_start": float(res.loss[0].min()), "best_loss_end": float(res.loss[-1].min()),
+            "best_distance_start_m": float(d0), "best_distance_end_m": d1}
+
+
+def measure_stress(args, stream):
+    """Forward-only stress case: 1e8 particles, 48 h at dt = 30 s, 512x512x32 weather."""
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_stress()
+    with torch.cuda.stream(stream):
+        sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt, args.occ))
+    cfg.uvwk = None                                   # the host copy is no longer needed
+    try:
+        sim.reset()
+        sim.step(cfg.n_steps)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.reset()
+        sim.step(cfg.n_steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        active = int(sim.fixed_state()[2][4])
+    finally:
+        sim.close()
+    return {"value": active / (ms / 1e3), "unit": UNIT, "ms_per_run": ms,
+            "particles": cfg.n_particles, "steps_per_run": cfg.n_steps,
+            "met": [cfg.n_met_t, cfg.nz, cfg.ny, cfg.nx], "active_particle_steps": active}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -394,7 +462,10 @@ def run_gpu(args):
     }
     if not args.no_forms:
         forms = {"batched": measure_batched(args, stream),
-                 "adjoint": measure_adjoint(args, stream)}
+                 "adjoint": measure_adjoint(args, stream),
+                 "inversion": measure_inversion(args, stream)}
+        if not args.no_stress:
+            forms["stress"] = measure_stress(args, stream)
         for f in forms.values():
             f["vs_plain"] = f["value"] / value
         line["forms"] = forms
@@ -420,7 +491,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms")
-    ap.add_argument("--only", choices=["batched", "adjoint"], default=None,
+    ap.add_argument("--no-stress", action="store_true", help="skip the 1e8-particle stress case")
+    ap.add_argument("--only", choices=["batched", "adjoint", "inversion", "stress"], default=None,
                     help="run one form alone and print its measurement (profiling aid)")
     ap.add_argument("--batched-block", type=int, default=256)
     ap.add_argument("--batched-ppt", type=int, default=1)
@@ -433,7 +505,8 @@ def main():
         from paper_0912_3223_gb300 import build as pkg_build
         pkg_build.build()
         stream = torch.cuda.Stream()
-        fn = measure_batched if args.only == "batched" else measure_adjoint
+        fn = {"batched": measure_batched, "adjoint": measure_adjoint,
+              "inversion": measure_inversion, "stress": measure_stress}[args.only]
         print(json.dumps({"form": args.only, **fn(args, stream)}), flush=True)
         return 0
     return run_gpu(args)

@@ -22,7 +22,7 @@ import numpy as np
 
 __all__ = [
     "LpmConfig", "Release", "Scenario",
-    "make_cfg0", "make_cfg1", "make_cfg2", "make_cfg3", "make_cfg4",
+    "make_cfg0", "make_cfg1", "make_cfg2", "make_cfg3", "make_cfg4", "make_stress",
     "make_artificial_weather", "make_receptors", "z_levels_stretched",
     "STATUS_ACTIVE", "STATUS_UNRELEASED", "STATUS_DEP_DRY", "STATUS_DEP_WET",
     "STATUS_EXITED",
@@ -341,14 +341,48 @@ def make_cfg3(n_particles: int = 1_000_000, n_steps: int = 1080,
 
 
 def make_cfg4(n_candidates: int = 64, n_per: int = 100_000, n_steps: int = 1080,
-              seed: int = SEED_HIDDEN):
-    """Batched source inversion: ``n_candidates`` candidate sources of ``n_per``
-    particles, plus a hidden seeded source that generates the observations."""
+              seed: int = SEED_HIDDEN, n_obs: int = 1_000_000):
+    """Batched source inversion on the adjoint workload's weather and receptors:
+    returns (candidates, observation) configurations and the hidden source. The
+    candidates are ``n_candidates`` scenarios of ``n_per`` particles with seeded starting
+    sources; the observation is a plain release of ``n_obs`` particles from the hidden
+    seeded source with another key, so its noise is independent of the candidates'."""
     base = make_cfg3(n_particles=n_per, n_steps=n_steps)
     rng = np.random.default_rng(seed)
-    hidden = (rng.uniform(3000.0, 8000.0), rng.uniform(20000.0, 30000.0),
-              rng.uniform(20.0, 150.0))
+    hidden = (float(rng.uniform(3000.0, 8000.0)), float(rng.uniform(20000.0, 30000.0)),
+              float(rng.uniform(20.0, 150.0)))
     cands = np.stack([rng.uniform(2000.0, 10000.0, n_candidates),
                       rng.uniform(18000.0, 32000.0, n_candidates),
                       rng.uniform(10.0, 300.0, n_candidates)], axis=1)
-    return base, hidden, cands
+    rel = base.release
+    scen = [Scenario(float(c[0]), float(c[1]), float(c[2]),
+                     Release(n_per, rel.q, rel.q_dt, 0, n_steps)) for c in cands]
+    cand_cfg = dataclasses.replace(base, n_scenarios=n_candidates, scenarios=scen,
+                                   name="batched source inversion (candidates)")
+    obs_cfg = dataclasses.replace(base, src_x=hidden[0], src_y=hidden[1], src_z=hidden[2],
+                                  seed=base.seed + 1000,
+                                  release=Release(n_obs, rel.q, rel.q_dt, 0, n_steps),
+                                  name="batched source inversion (observation)")
+    return cand_cfg, obs_cfg, hidden
+
+
+def make_stress(n_particles: int = 100_000_000, n_steps: int = 5760, seed: int = SEED_PARTICLES):
+    """Forward-only throughput stress case: 1e8 particles released continuously over 48 h at
+    dt = 30 s on a 512x512x32 hourly weather grid (250 m spacing, 128 km domain, levels to
+    3 km), source (10 km, 64 km, 50 m); the realistic physics; 512x512x20 concentration grid
+    of 250 m x 250 m x 50 m cells, hourly snapshots."""
+    n_hours = int(math.ceil(n_steps * 30.0 / 3600.0)) + 1
+    uvwk, z_levels = make_met_realistic(nx=512, ny=512, nz=32, n_t=n_hours)
+    rain = make_rain(nx=512, ny=512, n_t=n_hours)
+    return LpmConfig(
+        nx=512, ny=512, nz=32, x0=0.0, y0=0.0, dx=250.0, dy=250.0,
+        z_levels=z_levels, n_met_t=n_hours, met_t0=0.0, met_dt=3600.0,
+        cx=512, cy=512, cz=20, cx0=0.0, cy0=0.0, cz0=0.0, cdx=250.0, cdy=250.0, cdz=50.0,
+        src_x=10000.0, src_y=64000.0, src_z=50.0,
+        dt=30.0, n_steps=n_steps, seed=seed, bin_every=120,
+        half_life_s=8 * 86400.0, vd_dry=0.002, h_mix=1000.0, wet_lambda=1e-4,
+        kh_uniform=100.0, reflect_ground=1, reflect_top=1, z_top=3000.0, lateral_exit=1,
+        drift_correction=0, n_scenarios=1,
+        release=Release(n_particles=n_particles, q=np.array([1.0]), q_dt=3600.0,
+                        first_step=0, last_step=n_steps),
+        uvwk=uvwk, kh=None, rain=rain, name="stress 1e8 x 48 h")
