@@ -360,7 +360,8 @@ def run_gpu(args):
         cfg = dataclasses.replace(cfg, seed=cfg.seed + rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt, args.occ))
+        sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt, args.occ),
+                  sort_every=args.sort_every)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
 
     def one_run():
@@ -450,7 +451,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": cfg.n_particles, "steps_per_run": cfg.n_steps,
                    "dt_s": cfg.dt, "met": [cfg.n_met_t, cfg.nz, cfg.ny, cfg.nx],
-                   "launch": [args.block, args.ppt, args.occ],
+                   "launch": [args.block, args.ppt, args.occ], "sort_every": args.sort_every,
                    "l2": "flushed (256 MB write) between timed steps",
                    "active_particle_steps_per_run": sum(active) // max(1, len(active)),
                    "slot_steps_per_run": cfg.n_particles * cfg.n_steps},
@@ -487,6 +488,8 @@ def main():
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--ppt", type=int, default=1)
     ap.add_argument("--occ", type=int, default=2)
+    ap.add_argument("--sort-every", type=int, default=0,
+                    help="re-order the particles by weather cell every N steps (0 = off)")
     ap.add_argument("--ref-stride", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblpm.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["lpm_api.cu", "lpm_kernels.cu", "lpm_advance_b128.cu", "lpm_advance_b256.cu",
-           "lpm_advance_b512.cu", "lpm_adjoint.cu", "lpm_noalloc.cu"]
+           "lpm_advance_b512.cu", "lpm_adjoint.cu", "lpm_noalloc.cu", "lpm_sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

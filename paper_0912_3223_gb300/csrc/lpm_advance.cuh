@@ -222,7 +222,7 @@ struct MinBlocks {
 template <int BLOCK, int PPT, int OCC>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__restrict__ tiles,
-               int n_tiles, unsigned int *queue, long long plain_n, int k0, int k1, int do_bin)
+               int n_tiles, unsigned int *queue, const PlainRanges R, int k0, int k1, int do_bin)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
@@ -252,26 +252,38 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
         ++iter;
         if (t >= n_tiles) break;
         Tile tile;
+        bool sorted = false;
         if (tiles) {
             tile = tiles[t];
         } else {
             tile.scen = 0;
-            tile.first = (long long)t * TILE;
-            tile.count = (int)min((long long)TILE, plain_n - tile.first);
+            if (t < R.tiles_a) {
+                const long long n_a = R.a_live ? (long long)*R.a_live : R.a_cap;
+                tile.first = (long long)t * TILE;
+                tile.count = (int)max(0LL, min((long long)TILE, n_a - tile.first));
+                sorted = R.pidx != nullptr;
+            } else {
+                tile.first = R.b_base + (long long)(t - R.tiles_a) * TILE;
+                tile.count = (int)min((long long)TILE, R.b_base + R.b_n - tile.first);
+            }
+            if (tile.count <= 0) continue;              // the whole block skips
         }
         const ScenDev &scg = P.scen[tile.scen];
         const ScenDev sc = scg;
-        const long long gid0 = sc.id0 + (tile.first - sc.first_slot) + threadIdx.x;
 
         // ---- load particles ---------------------------------------------------------
         float x[PPT], y[PPT], z[PPT];
         uint32_t tag[PPT];
+        unsigned long long gid[PPT];
         int live = 0;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int local = j * BLOCK + threadIdx.x;
+            const long long slot = tile.first + local;
+            gid[j] = (unsigned long long)(sc.id0 + (sorted ? (long long)__ldg(R.pidx + (local < tile.count ? slot : tile.first))
+                                                            : slot - sc.first_slot));
             if (local < tile.count) {
-                const float4 s = state[tile.first + local];
+                const float4 s = state[slot];
                 x[j] = s.x; y[j] = s.y; z[j] = s.z;
                 tag[j] = __float_as_uint(s.w);
                 const uint32_t st = tag[j] >> TAG_SHIFT;
@@ -302,8 +314,7 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
                     continue;
                 }
                 ++steps;
-                const unsigned long long gid = (unsigned long long)(gid0 + j * BLOCK);
-                st = particle_step<true>(P, LV, T, sc, &scg, gid, sp, sig_h_uniform, x[j], y[j],
+                st = particle_step<true>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform, x[j], y[j],
                                          z[j], nullptr);
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;
@@ -354,7 +365,7 @@ template <int BLOCK, int PPT, int OCC>
 cudaError_t launch_adv(const AdvanceLaunch &L)
 {
     advance_kernel<BLOCK, PPT, OCC><<<L.grid, BLOCK, 0, L.stream>>>(
-        *L.params, L.state, L.tiles, L.n_tiles, L.queue, L.plain_n, L.k0, L.k1, L.do_bin);
+        *L.params, L.state, L.tiles, L.n_tiles, L.queue, L.ranges, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();
 }
 

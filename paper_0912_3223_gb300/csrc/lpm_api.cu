@@ -90,6 +90,14 @@ struct lpm_ctx {
     long long n_bins = 0;                   // snapshots taken
     int block = 256, ppt = 1, occ = 2;
 
+    // plain form: periodic sort of the released particles by weather cell
+    int sort_every = 0;                     // steps between sorts; 0 = off
+    long long last_sort = 0;
+    long long n_sorted = 0;                 // slots [0, n_sorted) hold a sorted permutation
+    float4 *d_state2 = nullptr;
+    unsigned int *d_pidx = nullptr, *d_pidx2 = nullptr, *d_slot_of = nullptr, *d_keys = nullptr;
+    unsigned int *d_hist = nullptr, *d_bsums = nullptr, *d_live = nullptr;
+
     // differentiable parameters (adjoint form): diffusivity scale and wind bias
     double k_scale = 1.0, bias_u = 0.0, bias_v = 0.0;
     // receptor / adjoint state
@@ -413,6 +421,23 @@ lpm_status build_tiles(lpm_ctx *c)
     return LPM_OK;
 }
 
+lpm_status ensure_sort_buffers(lpm_ctx *c)
+{
+    if (c->d_state2) return LPM_OK;
+    const size_t n = (size_t)c->cfg.max_particles;
+    const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
+    const size_t ntiles = (nb + 1023) / 1024;
+    LPM_CUDA(c, cudaMalloc(&c->d_state2, n * sizeof(float4)));
+    LPM_CUDA(c, cudaMalloc(&c->d_pidx, n * sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_pidx2, n * sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_slot_of, n * sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_keys, n * sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_hist, nb * sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_bsums, ntiles * sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_live, sizeof(unsigned int)));
+    return LPM_OK;
+}
+
 cudaEvent_t next_event(lpm_ctx *c)
 {
     if (c->ev_used == c->ev_pool.size()) {
@@ -558,7 +583,8 @@ void lpm_destroy(lpm_ctx *c)
     void *ptrs[] = {c->d_uvwk, c->d_kh, c->d_pair, c->d_khpair, c->d_rain, c->d_state, c->d_conc, c->d_dep, c->d_ctr,
                     c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles,
                     c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
-                    c->d_rgrad, c->d_adj_tiles};
+                    c->d_rgrad, c->d_adj_tiles, c->d_state2, c->d_pidx, c->d_pidx2,
+                    c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -707,6 +733,8 @@ lpm_status lpm_reset(lpm_ctx *c)
     LPM_CUDA(c, launch_release_all(c->stream, P, c->d_state, c->n_slots_used));
     c->n_launches++;
     c->k = 0;
+    c->n_sorted = 0;
+    c->last_sort = 0;
     c->n_bins = 0;
     return LPM_OK;
 }
@@ -782,6 +810,8 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
     while (k < k_end) {
         long long next_bin = (k / g.bin_every + 1) * (long long)g.bin_every;
         long long e = std::min(k_end, std::min(next_bin, (long long)g.n_steps));
+        const bool sorting = !batched && c->sort_every > 0;
+        if (sorting) e = std::min(e, c->last_sort + c->sort_every > k ? c->last_sort + c->sort_every : k + c->sort_every);
         const bool do_bin = (e % g.bin_every == 0) || e == g.n_steps;
         AdvanceLaunch L{};
         L.stream = c->stream;
@@ -807,10 +837,30 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
                 LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + C_BIN_OUT, 0, sizeof(unsigned long long),
                                             c->stream));
             }
+            if (sorting && k > 0 && k - c->last_sort >= c->sort_every) {
+                // sort every particle released before step k by its weather cell
+                st = ensure_sort_buffers(c);
+                if (st != LPM_OK) return st;
+                const long long n_pre = released_before(c->scen[0], k);
+                LPM_CUDA(c, launch_sort(c->stream, P, c->d_state, c->d_pidx, c->n_sorted, n_pre,
+                                        c->d_state2, c->d_pidx2, c->d_slot_of, c->d_keys,
+                                        c->d_hist, c->d_bsums, c->d_live));
+                std::swap(c->d_state, c->d_state2);
+                std::swap(c->d_pidx, c->d_pidx2);
+                c->n_sorted = n_pre;
+                c->last_sort = k;
+                c->n_launches += 7;
+            }
             const long long n_rel = released_before(c->scen[0], e);
             L.tiles = nullptr;
-            L.plain_n = n_rel;
-            L.n_tiles = (int)((n_rel + T - 1) / T);
+            L.state = c->d_state;
+            L.ranges.a_cap = c->n_sorted;
+            L.ranges.a_live = c->n_sorted > 0 ? c->d_live : nullptr;
+            L.ranges.pidx = c->n_sorted > 0 ? c->d_pidx : nullptr;
+            L.ranges.b_base = c->n_sorted;
+            L.ranges.b_n = std::max(0LL, n_rel - c->n_sorted);
+            L.ranges.tiles_a = (int)((c->n_sorted + T - 1) / T);
+            L.n_tiles = L.ranges.tiles_a + (int)((L.ranges.b_n + T - 1) / T);
             L.queue = c->d_queue;
             L.grid = (unsigned)std::max(1, L.n_tiles);
             if (L.n_tiles > 0) {
@@ -833,6 +883,7 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
             if (!exec) {
                 // the segment as one graph: snapshot reset, queue reset, persistent launch
                 L.tiles = c->d_tiles;
+                L.ranges = PlainRanges{};
                 L.n_tiles = (int)(std::lower_bound(c->tile_sp.begin(), c->tile_sp.end(), e) -
                                   c->tile_sp.begin());
                 L.queue = c->d_queue;
@@ -983,8 +1034,17 @@ lpm_status lpm_particles(lpm_ctx *c, int64_t first, int64_t count, float *xyz, u
     if (st != LPM_OK) return st;
     if (count == 0) return LPM_OK;
     std::vector<float4> h((size_t)count);
-    LPM_CUDA(c, cudaMemcpy(h.data(), c->d_state + first, h.size() * sizeof(float4),
-                           cudaMemcpyDeviceToHost));
+    if (c->n_sorted > 0) {
+        // particle order: gather through the inverse permutation into the spare buffer
+        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_slot_of, c->n_sorted, first, count,
+                                  c->d_state2));
+        LPM_CUDA(c, cudaMemcpyAsync(h.data(), c->d_state2, h.size() * sizeof(float4),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    } else {
+        LPM_CUDA(c, cudaMemcpy(h.data(), c->d_state + first, h.size() * sizeof(float4),
+                               cudaMemcpyDeviceToHost));
+    }
     for (size_t i = 0; i < h.size(); ++i) {
         if (xyz) {
             xyz[3 * i] = h[i].x;
@@ -1023,6 +1083,14 @@ lpm_status lpm_fixed_state(lpm_ctx *c, int scenario, uint64_t *conc, size_t n_co
         counters[C_N_BINS] = c->n_bins;
     }
     if (shift) *shift = c->scen[(size_t)scenario].shift;
+    return LPM_OK;
+}
+
+lpm_status lpm_set_sort(lpm_ctx *c, int every_steps)
+{
+    if (!c) return LPM_E_INVALID;
+    if (every_steps < 0) return fail(c, LPM_E_INVALID, "every_steps must be >= 0");
+    c->sort_every = every_steps;
     return LPM_OK;
 }
 

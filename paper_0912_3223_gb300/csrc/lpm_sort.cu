@@ -1,0 +1,214 @@
+// lpm_sort.cu - counting sort of the released particles by weather cell.
+//
+// Particles of one release step leave the source together and drift apart, so after an
+// hour the 32 lanes of a warp gather weather from 32 unrelated places. Sorting the
+// released particles by the cell they sit in puts neighbours into the same warp: their
+// gathers share cache lines. The order of particles in memory has no effect on any
+// result (each particle keeps its index, hence its random numbers; the grids are integer
+// sums), so the sort is a pure layout change. Dead particles (deposited, exited) sort to
+// the end and the next launches skip them.
+#include "lpm_advance.cuh"
+
+namespace lpm {
+
+constexpr unsigned int KEY_NONE_U = 0xffffffffu;
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Key = weather cell (level, row, column) of an active particle; dead_key for the rest.
+__global__ void sort_keys_kernel(const StepParams P, const float4 *__restrict__ state, long long n,
+                                 unsigned int *__restrict__ keys, unsigned int *__restrict__ hist,
+                                 unsigned int dead_key)
+{
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // the whole warp walks the slots together (match_any needs every lane)
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const long long slot = base + lane;
+        unsigned int key = KEY_NONE_U;
+        if (slot < n) {
+            const float4 s = state[slot];
+            if ((__float_as_uint(s.w) >> TAG_SHIFT) == ST_ACTIVE) {
+                int i, j, k;
+                float a, b, c;
+                axis(s.x, P.x0, P.inv_dx, P.nx, i, a);
+                axis(s.y, P.y0, P.inv_dy, P.ny, j, b);
+                level(LV, s.z, k, c);
+                key = ((unsigned int)k * P.ny + j) * P.nx + i;
+            } else {
+                key = dead_key;
+            }
+            keys[slot] = key;
+        }
+        const unsigned int peers = __match_any_sync(0xffffffffu, key);
+        if (key != KEY_NONE_U && lane == __ffs(peers) - 1) atomicAdd(hist + key, __popc(peers));
+    }
+}
+
+__global__ void live_count_kernel(const unsigned int *hist, unsigned int dead_key, long long n,
+                                  unsigned int *live)
+{
+    *live = (unsigned int)(n - (long long)hist[dead_key]);
+}
+
+// Exclusive scan of data[0, nb): per-tile scan, scan of the tile sums, add-back.
+__device__ __forceinline__ unsigned int block_exclusive_scan(unsigned int v, unsigned int *s_warp,
+                                                             unsigned int &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned int w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = w;
+    }
+    __syncthreads();
+    total = s_warp[(blockDim.x >> 5) - 1];
+    const unsigned int before = wid ? s_warp[wid - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_tiles_kernel(unsigned int *data, long long nb, unsigned int *tile_sums)
+{
+    __shared__ unsigned int s_warp[32];
+    const long long base = (long long)blockIdx.x * SCAN_TILE + (long long)threadIdx.x * SCAN_ITEMS;
+    unsigned int v[SCAN_ITEMS], sum = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = base + i < nb ? data[base + i] : 0u;
+        sum += v[i];
+    }
+    unsigned int total;
+    unsigned int run = block_exclusive_scan(sum, s_warp, total);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < nb) data[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_sums_kernel(unsigned int *sums, int n)
+{
+    __shared__ unsigned int s_warp[32];
+    unsigned int carry = 0;
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        const unsigned int v = i < n ? sums[i] : 0u;
+        unsigned int total;
+        const unsigned int ex = block_exclusive_scan(v, s_warp, total);
+        if (i < n) sums[i] = carry + ex;
+        carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+scan_add_kernel(unsigned int *data, long long nb, const unsigned int *tile_sums)
+{
+    const unsigned int add = tile_sums[blockIdx.x];
+    const long long base = (long long)blockIdx.x * SCAN_TILE;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS)
+        if (base + i < nb) data[base + i] += add;
+}
+
+// Scatter: lanes with the same key take consecutive places from one atomic per group.
+__global__ void sort_scatter_kernel(const float4 *__restrict__ state_in,
+                                    const unsigned int *__restrict__ pidx_in, long long n_sorted_old,
+                                    long long n, const unsigned int *__restrict__ keys,
+                                    unsigned int *__restrict__ offsets, float4 *__restrict__ state_out,
+                                    unsigned int *__restrict__ pidx_out,
+                                    unsigned int *__restrict__ slot_of)
+{
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const long long slot = base + lane;
+        const unsigned int key = slot < n ? keys[slot] : KEY_NONE_U;
+        const unsigned int peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        unsigned int first = 0u;
+        if (key != KEY_NONE_U && lane == leader) first = atomicAdd(offsets + key, __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (key != KEY_NONE_U) {
+            const unsigned int dst = first + __popc(peers & ((1u << lane) - 1u));
+            const unsigned int p = slot < n_sorted_old ? pidx_in[slot] : (unsigned int)slot;
+            state_out[dst] = state_in[slot];
+            pidx_out[dst] = p;
+            slot_of[p] = dst;
+        }
+    }
+}
+
+__global__ void gather_kernel(const float4 *__restrict__ state, const unsigned int *__restrict__ slot_of,
+                              long long n_sorted, long long first, long long count,
+                              float4 *__restrict__ out)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const long long p = first + i;
+        const long long slot = p < n_sorted ? (long long)slot_of[p] : p;
+        out[i] = state[slot];
+    }
+}
+
+static unsigned int grid_for(long long n, int block)
+{
+    long long g = (n + block - 1) / block;
+    if (g > 152 * 32) g = 152 * 32;
+    return (unsigned int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const float4 *state_in,
+                        const unsigned int *pidx_in, long long n_sorted_old, long long n,
+                        float4 *state_out, unsigned int *pidx_out, unsigned int *slot_of,
+                        unsigned int *keys, unsigned int *hist, unsigned int *block_sums,
+                        unsigned int *live)
+{
+    const unsigned int dead_key = (unsigned int)((long long)P.nx * P.ny * P.nz);
+    const long long nb = (long long)dead_key + 1;
+    cudaError_t e = cudaMemsetAsync(hist, 0, nb * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        sort_keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(P, state_in, n, keys, hist, dead_key);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    live_count_kernel<<<1, 1, 0, s>>>(hist, dead_key, n, live);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (n == 0) return cudaSuccess;
+    const int n_tiles = (int)((nb + SCAN_TILE - 1) / SCAN_TILE);
+    scan_tiles_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(hist, nb, block_sums);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(block_sums, n_tiles);
+    scan_add_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(hist, nb, block_sums);
+    sort_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(state_in, pidx_in, n_sorted_old, n, keys,
+                                                         hist, state_out, pidx_out, slot_of);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(cudaStream_t s, const float4 *state, const unsigned int *slot_of,
+                          long long n_sorted, long long first, long long count, float4 *out)
+{
+    if (count <= 0) return cudaSuccess;
+    gather_kernel<<<grid_for(count, 256), 256, 0, s>>>(state, slot_of, n_sorted, first, count, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lpm

@@ -28,7 +28,7 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_deposition", "lpm_budget", "lpm_particles", "lpm_fixed_state",
            "lpm_set_launch", "lpm_sync", "lpm_draws", "lpm_release_range", "lpm_reset",
            "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
-           "lpm_receptors", "lpm_adjoint", "lpm_draws_static"]
+           "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort"]
 
 
 class LpmError(RuntimeError):
@@ -95,6 +95,7 @@ def load() -> C.CDLL:
     L.lpm_set_profiling.argtypes = [vp, C.c_int]
     L.lpm_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), dp]
     L.lpm_set_params.argtypes = [vp, C.c_double, C.c_double, C.c_double]
+    L.lpm_set_sort.argtypes = [vp, C.c_int]
     L.lpm_set_emission.argtypes = [vp, C.c_int, dp, C.c_int]
     L.lpm_receptors.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp]
     L.lpm_adjoint.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp, dp]
@@ -107,7 +108,7 @@ def load() -> C.CDLL:
                  "lpm_particles", "lpm_fixed_state", "lpm_set_launch", "lpm_sync",
                  "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
                  "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
-                 "lpm_adjoint", "lpm_draws_static"):
+                 "lpm_adjoint", "lpm_draws_static", "lpm_set_sort"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -217,6 +218,10 @@ def lpm_stats(ctx):
     a, b, ms = C.c_int64(), C.c_int64(), C.c_double()
     _check(ctx, load().lpm_stats(C.c_void_p(ctx), C.byref(a), C.byref(b), C.byref(ms)))
     return int(a.value), int(b.value), float(ms.value)
+
+
+def lpm_set_sort(ctx, every_steps: int) -> None:
+    _check(ctx, load().lpm_set_sort(C.c_void_p(ctx), int(every_steps)))
 
 
 def lpm_set_params(ctx, k_scale: float = 1.0, bias_u: float = 0.0, bias_v: float = 0.0) -> None:
@@ -346,7 +351,7 @@ class Sim:
     releases declared. ``stream`` is a torch.cuda.Stream (default: current stream)."""
 
     def __init__(self, cfg, stream=None, met_on_device: bool = False, launch=None,
-                 part=None):
+                 part=None, sort_every: Optional[int] = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the particle model runs on a CUDA GPU; none is available")
@@ -358,6 +363,8 @@ class Sim:
         try:
             if launch is not None:
                 lpm_set_launch(self.ctx, *launch)
+            if sort_every is not None:
+                lpm_set_sort(self.ctx, sort_every)
             self._set_met(met_on_device)
             if cfg.scenarios:
                 for i, sc in enumerate(cfg.scenarios):

@@ -275,3 +275,22 @@ def test_partitioned_contexts_sum_to_single_run():
     assert np.array_equal(dep, full["dep_fixed"])
     assert np.array_equal(ctr[[0, 1, 2, 3, 4]], full["counters"][[0, 1, 2, 3, 4]])
     assert np.array_equal(np.concatenate(pos).astype(np.float64), full["pos"])
+
+
+@pytest.mark.parametrize("every", [7, 60])
+def test_sorting_particles_by_cell_changes_nothing(every):
+    """Re-ordering the released particles by weather cell is a layout change only: the
+    particles (read back in index order), grids and counters are bit-identical."""
+    cfg = li.make_cfg1(n_particles=7001, n_steps=300, n_hours=4)
+    from paper_0912_3223_gb300 import Sim
+    ref = run_gpu(cfg)
+    with Sim(cfg, sort_every=every) as sim:
+        sim.step(137)
+        sim.step(cfg.n_steps - 137)
+        xyz, tag = sim.particles()
+        part = sim.particles(1234, 99)
+        cfix, dfix, ctr, _ = sim.fixed_state()
+    assert np.array_equal(xyz.astype(np.float64), ref["pos"]) and np.array_equal(tag, ref["tag"])
+    assert np.array_equal(part[0], xyz[1234:1333]) and np.array_equal(part[1], tag[1234:1333])
+    assert np.array_equal(cfix, ref["conc_fixed"]) and np.array_equal(dfix, ref["dep_fixed"])
+    assert np.array_equal(ctr[:6], ref["counters"][:6])
