@@ -435,6 +435,10 @@ lpm_status ensure_sort_buffers(lpm_ctx *c)
     LPM_CUDA(c, cudaMalloc(&c->d_hist, nb * sizeof(unsigned int)));
     LPM_CUDA(c, cudaMalloc(&c->d_bsums, ntiles * sizeof(unsigned int)));
     LPM_CUDA(c, cudaMalloc(&c->d_live, sizeof(unsigned int)));
+    // A particle's state is constant until its release, and a sort moves only the released
+    // prefix: the second buffer needs the unreleased tail once, here and at every reset.
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_state2, c->d_state, (size_t)c->n_slots_used * sizeof(float4),
+                                cudaMemcpyDeviceToDevice, c->stream));
     return LPM_OK;
 }
 
@@ -732,6 +736,10 @@ lpm_status lpm_reset(lpm_ctx *c)
     fill_params(c, P);
     LPM_CUDA(c, launch_release_all(c->stream, P, c->d_state, c->n_slots_used));
     c->n_launches++;
+    if (c->d_state2) {
+        LPM_CUDA(c, launch_release_all(c->stream, P, c->d_state2, c->n_slots_used));
+        c->n_launches++;
+    }
     c->k = 0;
     c->n_sorted = 0;
     c->last_sort = 0;
