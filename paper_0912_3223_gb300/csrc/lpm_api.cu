@@ -96,7 +96,9 @@ struct lpm_ctx {
     long long n_sorted = 0;                 // slots [0, n_sorted) hold a sorted permutation
     float4 *d_state2 = nullptr;
     unsigned int *d_pidx = nullptr, *d_pidx2 = nullptr, *d_slot_of = nullptr, *d_keys = nullptr;
-    unsigned int *d_hist = nullptr, *d_bsums = nullptr, *d_live = nullptr;
+    unsigned int *d_hist = nullptr, *d_bsums = nullptr, *d_live = nullptr;   // d_live = meta[4]
+    float4 *d_grave = nullptr;              // particles found dead at a sort (read-back only)
+    unsigned int *d_grave_n = nullptr;
 
     // differentiable parameters (adjoint form): diffusivity scale and wind bias
     double k_scale = 1.0, bias_u = 0.0, bias_v = 0.0;
@@ -434,7 +436,11 @@ lpm_status ensure_sort_buffers(lpm_ctx *c)
     LPM_CUDA(c, cudaMalloc(&c->d_keys, n * sizeof(unsigned int)));
     LPM_CUDA(c, cudaMalloc(&c->d_hist, nb * sizeof(unsigned int)));
     LPM_CUDA(c, cudaMalloc(&c->d_bsums, ntiles * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_live, sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_live, 4 * sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMalloc(&c->d_grave, n * sizeof(float4)));
+    LPM_CUDA(c, cudaMalloc(&c->d_grave_n, sizeof(unsigned int)));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
     // A particle's state is constant until its release, and a sort moves only the released
     // prefix: the second buffer needs the unreleased tail once, here and at every reset.
     LPM_CUDA(c, cudaMemcpyAsync(c->d_state2, c->d_state, (size_t)c->n_slots_used * sizeof(float4),
@@ -588,7 +594,8 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles,
                     c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
                     c->d_rgrad, c->d_adj_tiles, c->d_state2, c->d_pidx, c->d_pidx2,
-                    c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live};
+                    c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live, c->d_grave,
+                    c->d_grave_n};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -738,6 +745,8 @@ lpm_status lpm_reset(lpm_ctx *c)
     c->n_launches++;
     if (c->d_state2) {
         LPM_CUDA(c, launch_release_all(c->stream, P, c->d_state2, c->n_slots_used));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
         c->n_launches++;
     }
     c->k = 0;
@@ -852,12 +861,13 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
                 const long long n_pre = released_before(c->scen[0], k);
                 LPM_CUDA(c, launch_sort(c->stream, P, c->d_state, c->d_pidx, c->n_sorted, n_pre,
                                         c->d_state2, c->d_pidx2, c->d_slot_of, c->d_keys,
-                                        c->d_hist, c->d_bsums, c->d_live));
+                                        c->d_hist, c->d_bsums, c->d_live, c->d_grave,
+                                        c->d_grave_n));
                 std::swap(c->d_state, c->d_state2);
                 std::swap(c->d_pidx, c->d_pidx2);
                 c->n_sorted = n_pre;
                 c->last_sort = k;
-                c->n_launches += 7;
+                c->n_launches += 8;
             }
             const long long n_rel = released_before(c->scen[0], e);
             L.tiles = nullptr;
@@ -1004,7 +1014,8 @@ lpm_status lpm_budget(lpm_ctx *c, int scenario, double out[8])
                                     c->stream));
     StepParams P;
     fill_params(c, P);
-    LPM_CUDA(c, launch_budget(c->stream, P, c->d_state, scenario, h.n, (int)c->k));
+    LPM_CUDA(c, launch_budget(c->stream, P, c->d_state, scenario, h.n, (int)c->k,
+                              c->n_sorted > 0 ? c->d_live : nullptr, c->n_sorted));
     c->n_launches++;
     st = check_device_error(c);
     if (st != LPM_OK) return st;
@@ -1044,8 +1055,8 @@ lpm_status lpm_particles(lpm_ctx *c, int64_t first, int64_t count, float *xyz, u
     std::vector<float4> h((size_t)count);
     if (c->n_sorted > 0) {
         // particle order: gather through the inverse permutation into the spare buffer
-        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_slot_of, c->n_sorted, first, count,
-                                  c->d_state2));
+        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_slot_of, c->d_grave, c->n_sorted,
+                                  first, count, c->d_state2));
         LPM_CUDA(c, cudaMemcpyAsync(h.data(), c->d_state2, h.size() * sizeof(float4),
                                     cudaMemcpyDeviceToHost, c->stream));
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));

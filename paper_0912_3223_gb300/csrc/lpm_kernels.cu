@@ -71,12 +71,15 @@ __global__ void pack_kernel(const float4 *__restrict__ a, const float4 *__restri
 // split into inside/outside the concentration grid, plus the active count.
 // ---------------------------------------------------------------------------------
 __global__ void budget_kernel(const StepParams P, const float4 *__restrict__ state, int scen,
-                              int k_now)
+                              int k_now, const unsigned int *live, long long hole_end)
 {
     const ScenDev sc = P.scen[scen];
+    // slots [live, hole_end) are unused after a sort (their particles moved elsewhere)
+    const long long hole_lo = live ? (long long)*live : 0, hole_hi = live ? hole_end : 0;
     unsigned long long in = 0, out = 0, cnt = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < sc.n; p += stride) {
+        if (p >= hole_lo && p < hole_hi) continue;
         const float4 s = state[sc.first_slot + p];
         const uint32_t tag = __float_as_uint(s.w);
         if ((tag >> TAG_SHIFT) != ST_ACTIVE) continue;
@@ -191,13 +194,13 @@ cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned
 }
 
 cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *state, int scen,
-                          long long n, int k_now)
+                          long long n, int k_now, const unsigned int *live, long long hole_end)
 {
     const int block = 256;
     long long blocks = (n + block - 1) / block;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    budget_kernel<<<(unsigned)blocks, block, 0, s>>>(P, state, scen, k_now);
+    budget_kernel<<<(unsigned)blocks, block, 0, s>>>(P, state, scen, k_now, live, hole_end);
     return cudaGetLastError();
 }
 

@@ -44,17 +44,18 @@ int occupancy_b512(int ppt, int occ);
 cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
                         const float *kb, float4 *pair, float2 *khpair, long long nodes);
 cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const float4 *state_in,
-                        const unsigned int *pidx_in, long long n_sorted_old, long long n,
+                        const unsigned int *pidx_in, long long n_sorted_old, long long n_pre,
                         float4 *state_out, unsigned int *pidx_out, unsigned int *slot_of,
                         unsigned int *keys, unsigned int *hist, unsigned int *block_sums,
-                        unsigned int *live);
+                        unsigned int *meta, float4 *grave, unsigned int *grave_count);
 cudaError_t launch_gather(cudaStream_t s, const float4 *state, const unsigned int *slot_of,
-                          long long n_sorted, long long first, long long count, float4 *out);
+                          const float4 *grave, long long n_sorted, long long first,
+                          long long count, float4 *out);
 cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned long long *pid,
                          const unsigned int *step, unsigned int stream, long long n, uint4 *words,
                          float *nrm);
 cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *state, int scen,
-                          long long n, int k_now);
+                          long long n, int k_now, const unsigned int *live, long long hole_end);
 
 void set_global_error(const char *msg);
 

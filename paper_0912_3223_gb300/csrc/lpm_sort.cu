@@ -5,8 +5,9 @@
 // released particles by the cell they sit in puts neighbours into the same warp: their
 // gathers share cache lines. The order of particles in memory has no effect on any
 // result (each particle keeps its index, hence its random numbers; the grids are integer
-// sums), so the sort is a pure layout change. Dead particles (deposited, exited) sort to
-// the end and the next launches skip them.
+// sums), so the sort is a pure layout change. A sort takes the live sorted particles and
+// the particles released since the previous sort; particles found deposited or exited
+// move once to an append-only array kept only for read-back.
 #include "lpm_advance.cuh"
 
 namespace lpm {
@@ -16,45 +17,65 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
+constexpr unsigned int GRAVE = 0x80000000u;   // slot_of flag: index into the dead-particle array
+
+// meta[0] live count after the last sort, meta[1] input size of this sort, meta[2] the
+// live count before it. Input i maps to slot i (i < live before) or to the newly
+// released slot n_sorted_old + (i - live before).
+__global__ void sort_begin_kernel(unsigned int *meta, long long n_sorted_old, long long n_pre)
+{
+    const unsigned int live_old = n_sorted_old > 0 ? meta[0] : 0u;
+    meta[2] = live_old;
+    meta[1] = live_old + (unsigned int)(n_pre - n_sorted_old);
+}
+
+__device__ __forceinline__ long long input_slot(long long i, unsigned int live_old,
+                                                long long n_sorted_old)
+{
+    return i < (long long)live_old ? i : n_sorted_old + (i - (long long)live_old);
+}
+
 // Key = weather cell (level, row, column) of an active particle; dead_key for the rest.
-__global__ void sort_keys_kernel(const StepParams P, const float4 *__restrict__ state, long long n,
-                                 unsigned int *__restrict__ keys, unsigned int *__restrict__ hist,
-                                 unsigned int dead_key)
+__global__ void sort_keys_kernel(const StepParams P, const float4 *__restrict__ state,
+                                 const unsigned int *__restrict__ meta, long long n_sorted_old,
+                                 long long n_max, unsigned int *__restrict__ keys,
+                                 unsigned int *__restrict__ hist, unsigned int dead_key)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     __syncthreads();
+    const long long n = meta[1];
+    const unsigned int live_old = meta[2];
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    // the whole warp walks the slots together (match_any needs every lane)
+    // the whole warp walks the inputs together (match_any needs every lane)
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
          base += stride) {
-        const long long slot = base + lane;
+        const long long i = base + lane;
         unsigned int key = KEY_NONE_U;
-        if (slot < n) {
-            const float4 s = state[slot];
+        if (i < n && i < n_max) {
+            const float4 s = state[input_slot(i, live_old, n_sorted_old)];
             if ((__float_as_uint(s.w) >> TAG_SHIFT) == ST_ACTIVE) {
-                int i, j, k;
+                int ix, jy, kz;
                 float a, b, c;
-                axis(s.x, P.x0, P.inv_dx, P.nx, i, a);
-                axis(s.y, P.y0, P.inv_dy, P.ny, j, b);
-                level(LV, s.z, k, c);
-                key = ((unsigned int)k * P.ny + j) * P.nx + i;
+                axis(s.x, P.x0, P.inv_dx, P.nx, ix, a);
+                axis(s.y, P.y0, P.inv_dy, P.ny, jy, b);
+                level(LV, s.z, kz, c);
+                key = ((unsigned int)kz * P.ny + jy) * P.nx + ix;
             } else {
                 key = dead_key;
             }
-            keys[slot] = key;
+            keys[i] = key;
         }
         const unsigned int peers = __match_any_sync(0xffffffffu, key);
         if (key != KEY_NONE_U && lane == __ffs(peers) - 1) atomicAdd(hist + key, __popc(peers));
     }
 }
 
-__global__ void live_count_kernel(const unsigned int *hist, unsigned int dead_key, long long n,
-                                  unsigned int *live)
+__global__ void live_count_kernel(const unsigned int *hist, unsigned int dead_key, unsigned int *meta)
 {
-    *live = (unsigned int)(n - (long long)hist[dead_key]);
+    meta[0] = meta[1] - hist[dead_key];
 }
 
 // Exclusive scan of data[0, nb): per-tile scan, scan of the tile sums, add-back.
@@ -129,44 +150,61 @@ scan_add_kernel(unsigned int *data, long long nb, const unsigned int *tile_sums)
         if (base + i < nb) data[base + i] += add;
 }
 
-// Scatter: lanes with the same key take consecutive places from one atomic per group.
+// Scatter: live particles to their sorted places (one atomic per group of lanes with the
+// same key), dead ones appended to the dead-particle array.
 __global__ void sort_scatter_kernel(const float4 *__restrict__ state_in,
-                                    const unsigned int *__restrict__ pidx_in, long long n_sorted_old,
-                                    long long n, const unsigned int *__restrict__ keys,
-                                    unsigned int *__restrict__ offsets, float4 *__restrict__ state_out,
-                                    unsigned int *__restrict__ pidx_out,
-                                    unsigned int *__restrict__ slot_of)
+                                    const unsigned int *__restrict__ pidx_in,
+                                    const unsigned int *__restrict__ meta, long long n_sorted_old,
+                                    long long n_max, const unsigned int *__restrict__ keys,
+                                    unsigned int dead_key, unsigned int *__restrict__ offsets,
+                                    float4 *__restrict__ state_out, unsigned int *__restrict__ pidx_out,
+                                    unsigned int *__restrict__ slot_of, float4 *__restrict__ grave,
+                                    unsigned int *__restrict__ grave_count)
 {
+    const long long n = meta[1];
+    const unsigned int live_old = meta[2];
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
          base += stride) {
-        const long long slot = base + lane;
-        const unsigned int key = slot < n ? keys[slot] : KEY_NONE_U;
+        const long long i = base + lane;
+        const bool valid = i < n && i < n_max;
+        const unsigned int key = valid ? keys[i] : KEY_NONE_U;
         const unsigned int peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
         unsigned int first = 0u;
-        if (key != KEY_NONE_U && lane == leader) first = atomicAdd(offsets + key, __popc(peers));
+        if (key != KEY_NONE_U && lane == leader)
+            first = atomicAdd(key == dead_key ? grave_count : offsets + key, __popc(peers));
         first = __shfl_sync(0xffffffffu, first, leader);
-        if (key != KEY_NONE_U) {
+        if (valid) {
+            const long long slot = input_slot(i, live_old, n_sorted_old);
             const unsigned int dst = first + __popc(peers & ((1u << lane) - 1u));
-            const unsigned int p = slot < n_sorted_old ? pidx_in[slot] : (unsigned int)slot;
-            state_out[dst] = state_in[slot];
-            pidx_out[dst] = p;
-            slot_of[p] = dst;
+            const unsigned int p = i < (long long)live_old ? pidx_in[slot] : (unsigned int)slot;
+            if (key == dead_key) {
+                grave[dst] = state_in[slot];
+                slot_of[p] = GRAVE | dst;
+            } else {
+                state_out[dst] = state_in[slot];
+                pidx_out[dst] = p;
+                slot_of[p] = dst;
+            }
         }
     }
 }
 
 __global__ void gather_kernel(const float4 *__restrict__ state, const unsigned int *__restrict__ slot_of,
-                              long long n_sorted, long long first, long long count,
-                              float4 *__restrict__ out)
+                              const float4 *__restrict__ grave, long long n_sorted, long long first,
+                              long long count, float4 *__restrict__ out)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
         const long long p = first + i;
-        const long long slot = p < n_sorted ? (long long)slot_of[p] : p;
-        out[i] = state[slot];
+        if (p < n_sorted) {
+            const unsigned int s = slot_of[p];
+            out[i] = (s & GRAVE) ? grave[s & ~GRAVE] : state[s];
+        } else {
+            out[i] = state[p];
+        }
     }
 }
 
@@ -178,36 +216,40 @@ static unsigned int grid_for(long long n, int block)
 }
 
 cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const float4 *state_in,
-                        const unsigned int *pidx_in, long long n_sorted_old, long long n,
+                        const unsigned int *pidx_in, long long n_sorted_old, long long n_pre,
                         float4 *state_out, unsigned int *pidx_out, unsigned int *slot_of,
                         unsigned int *keys, unsigned int *hist, unsigned int *block_sums,
-                        unsigned int *live)
+                        unsigned int *meta, float4 *grave, unsigned int *grave_count)
 {
     const unsigned int dead_key = (unsigned int)((long long)P.nx * P.ny * P.nz);
     const long long nb = (long long)dead_key + 1;
     cudaError_t e = cudaMemsetAsync(hist, 0, nb * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    if (n > 0) {
-        sort_keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(P, state_in, n, keys, hist, dead_key);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    live_count_kernel<<<1, 1, 0, s>>>(hist, dead_key, n, live);
+    sort_begin_kernel<<<1, 1, 0, s>>>(meta, n_sorted_old, n_pre);
+    const long long n_max = n_pre;                  // bound of the input size (sizes the grids)
+    if (n_max > 0)
+        sort_keys_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(P, state_in, meta, n_sorted_old, n_max,
+                                                              keys, hist, dead_key);
+    live_count_kernel<<<1, 1, 0, s>>>(hist, dead_key, meta);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n == 0) return cudaSuccess;
+    if (n_max == 0) return cudaSuccess;
     const int n_tiles = (int)((nb + SCAN_TILE - 1) / SCAN_TILE);
     scan_tiles_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(hist, nb, block_sums);
     scan_sums_kernel<<<1, 1024, 0, s>>>(block_sums, n_tiles);
     scan_add_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(hist, nb, block_sums);
-    sort_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(state_in, pidx_in, n_sorted_old, n, keys,
-                                                         hist, state_out, pidx_out, slot_of);
+    sort_scatter_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(state_in, pidx_in, meta, n_sorted_old,
+                                                             n_max, keys, dead_key, hist, state_out,
+                                                             pidx_out, slot_of, grave, grave_count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather(cudaStream_t s, const float4 *state, const unsigned int *slot_of,
-                          long long n_sorted, long long first, long long count, float4 *out)
+                          const float4 *grave, long long n_sorted, long long first,
+                          long long count, float4 *out)
 {
     if (count <= 0) return cudaSuccess;
-    gather_kernel<<<grid_for(count, 256), 256, 0, s>>>(state, slot_of, n_sorted, first, count, out);
+    gather_kernel<<<grid_for(count, 256), 256, 0, s>>>(state, slot_of, grave, n_sorted, first,
+                                                       count, out);
     return cudaGetLastError();
 }
 
