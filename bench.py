@@ -488,7 +488,7 @@ def main():
     ap.add_argument("--block", type=int, default=256)
     ap.add_argument("--ppt", type=int, default=1)
     ap.add_argument("--occ", type=int, default=2)
-    ap.add_argument("--sort-every", type=int, default=0,
+    ap.add_argument("--sort-every", type=int, default=60,
                     help="re-order the particles by weather cell every N steps (0 = off)")
     ap.add_argument("--ref-stride", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")

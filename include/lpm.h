@@ -212,8 +212,8 @@ lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int
 /* Plain form only (ignored for ensembles): every every_steps steps, re-order the released
  * particles in memory by the weather cell they occupy, so that the threads of a warp
  * gather from neighbouring cells (a layout change only: every particle keeps its index,
- * hence its random numbers, and all results are identical). 0 turns it off (default).
- * Needs 32 bytes of extra device memory per particle slot, allocated at the first sort. */
+ * hence its random numbers, and all results are identical). 0 turns it off; default 60.
+ * Needs 52 bytes of extra device memory per particle slot, allocated at the first sort. */
 lpm_status lpm_set_sort(lpm_ctx *ctx, int every_steps);
 
 /* Synchronises the context stream and reports device-side errors. */

@@ -91,7 +91,7 @@ struct lpm_ctx {
     int block = 256, ppt = 1, occ = 2;
 
     // plain form: periodic sort of the released particles by weather cell
-    int sort_every = 0;                     // steps between sorts; 0 = off
+    int sort_every = 60;                    // steps between sorts; 0 = off
     long long last_sort = 0;
     long long n_sorted = 0;                 // slots [0, n_sorted) hold a sorted permutation
     float4 *d_state2 = nullptr;

@@ -48,10 +48,10 @@ def artificial_weather_cfg(n_particles=2160, n_steps=2160, nz=25):
     return cfg
 
 
-def run_gpu(cfg, n_run=None, launch=None, pieces=None, met_on_device=False):
+def run_gpu(cfg, n_run=None, launch=None, pieces=None, met_on_device=False, sort_every=None):
     from paper_0912_3223_gb300 import Sim
     n_run = cfg.n_steps if n_run is None else n_run
-    sim = Sim(cfg, launch=launch, met_on_device=met_on_device)
+    sim = Sim(cfg, launch=launch, met_on_device=met_on_device, sort_every=sort_every)
     try:
         if pieces:
             for n in pieces:

@@ -283,7 +283,7 @@ def test_sorting_particles_by_cell_changes_nothing(every):
     particles (read back in index order), grids and counters are bit-identical."""
     cfg = li.make_cfg1(n_particles=7001, n_steps=300, n_hours=4)
     from paper_0912_3223_gb300 import Sim
-    ref = run_gpu(cfg)
+    ref = run_gpu(cfg, sort_every=0)
     with Sim(cfg, sort_every=every) as sim:
         sim.step(137)
         sim.step(cfg.n_steps - 137)
