@@ -39,10 +39,10 @@ WORKLOAD = ("plain method, realistic: 1e7 particles, 24 h at dt=30 s (2880 steps
 # 30, 16-corner lerps of 4 components 120, move 18, reflection/exit 8, deposition test 4.
 OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
 # DRAM traffic per advance launch from the ncu capture summarised in
-# profiles/advance_kernel_plain_1e7x2880.md (mean of two mid-run launches, read + write),
-# valid while the kernel sources hash to the values recorded there.
-ADVANCE_TRAFFIC_BYTES = 0.5 * ((119.247616 + 58.066688) + (126.788096 + 65.928192)) * 1e6
-ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "5f935d70", "lpm_device.cuh": "5db607d1"}
+# profiles/advance_kernel_plain_1e7x2880.md (mean of the two captured 60-step launches of
+# hours 6-7, read + write), valid while the kernel sources hash to the values recorded there.
+ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.086912 + 0.00128) + (23.575040 + 0.003584)) * 1e6
+ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "87ac7ea6", "lpm_device.cuh": "5db607d1"}
 SM_COUNT = 152
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
 SM_MAX_MHZ = 2070.0
