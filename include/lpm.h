@@ -216,6 +216,17 @@ lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int
  * Needs 52 bytes of extra device memory per particle slot, allocated at the first sort. */
 lpm_status lpm_set_sort(lpm_ctx *ctx, int every_steps);
 
+/*
+ * Checkpoint / resume of a run (no paper counterpart; the counter-based draws make the
+ * run state small: step index, particles, grids, counters). lpm_save with buf = NULL sets
+ * *n to the size needed; otherwise writes the state into the caller's host buffer of *n
+ * bytes (synchronises). lpm_load restores it into a context created with the same
+ * configuration, weather, sources and releases (checked as far as the sizes go);
+ * continuing from a loaded state gives bit-identical results to the uninterrupted run.
+ */
+lpm_status lpm_save(lpm_ctx *ctx, void *buf, size_t *n);
+lpm_status lpm_load(lpm_ctx *ctx, const void *buf, size_t n);
+
 /* Synchronises the context stream and reports device-side errors. */
 lpm_status lpm_sync(lpm_ctx *ctx);
 

@@ -1054,10 +1054,11 @@ lpm_status lpm_particles(lpm_ctx *c, int64_t first, int64_t count, float *xyz, u
     if (count == 0) return LPM_OK;
     std::vector<float4> h((size_t)count);
     if (c->n_sorted > 0) {
-        // particle order: gather through the inverse permutation into the spare buffer
+        // particle order: gather through the inverse permutation into the spare buffer,
+        // particle p at its index p (the spare buffer's unreleased tail stays valid)
         LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_slot_of, c->d_grave, c->n_sorted,
-                                  first, count, c->d_state2));
-        LPM_CUDA(c, cudaMemcpyAsync(h.data(), c->d_state2, h.size() * sizeof(float4),
+                                  first, count, c->d_state2 + first));
+        LPM_CUDA(c, cudaMemcpyAsync(h.data(), c->d_state2 + first, h.size() * sizeof(float4),
                                     cudaMemcpyDeviceToHost, c->stream));
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     } else {
@@ -1312,6 +1313,102 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     st = check_device_error(c);
     if (st != LPM_OK) return st;
     LPM_CUDA(c, cudaMemcpy(grad, c->d_rgrad, ns * A.ng * sizeof(double), cudaMemcpyDeviceToHost));
+    return LPM_OK;
+}
+
+// ---- checkpoint / resume --------------------------------------------------------
+namespace {
+struct SaveHeader {
+    char magic[8];               // "LPMSAVE1"
+    long long k, n_bins, n_slots, n_scen, ncell, ndep, n_ctr;
+};
+}  // namespace
+
+lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
+{
+    if (!c || !n) return LPM_E_INVALID;
+    const size_t ns = (size_t)c->cfg.n_scenarios;
+    const size_t bytes = sizeof(SaveHeader) + (size_t)c->n_slots_used * sizeof(float4) +
+                         ns * (c->ncell() + c->ndep()) * sizeof(unsigned long long) +
+                         (size_t)N_COUNTERS * ns * sizeof(unsigned long long);
+    if (!buf) {
+        *n = bytes;
+        return LPM_OK;
+    }
+    if (*n < bytes) return fail(c, LPM_E_INVALID, "buffer holds %zu bytes, %zu needed", *n, bytes);
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    SaveHeader h;
+    std::memcpy(h.magic, "LPMSAVE1", 8);
+    h.k = c->k;
+    h.n_bins = c->n_bins;
+    h.n_slots = c->n_slots_used;
+    h.n_scen = (long long)ns;
+    h.ncell = (long long)c->ncell();
+    h.ndep = (long long)c->ndep();
+    h.n_ctr = N_COUNTERS;
+    char *o = static_cast<char *>(buf);
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    // particles in index order (the sorted layout is not part of the state)
+    const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
+    if (c->n_sorted > 0) {
+        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_slot_of, c->d_grave, c->n_sorted, 0,
+                                  c->n_slots_used, c->d_state2));
+        LPM_CUDA(c, cudaMemcpyAsync(o, c->d_state2, sb, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        LPM_CUDA(c, cudaMemcpyAsync(o, c->d_state, sb, cudaMemcpyDeviceToHost, c->stream));
+    }
+    o += sb;
+    LPM_CUDA(c, cudaMemcpyAsync(o, c->d_conc, ns * c->ncell() * 8, cudaMemcpyDeviceToHost, c->stream));
+    o += ns * c->ncell() * 8;
+    LPM_CUDA(c, cudaMemcpyAsync(o, c->d_dep, ns * c->ndep() * 8, cudaMemcpyDeviceToHost, c->stream));
+    o += ns * c->ndep() * 8;
+    LPM_CUDA(c, cudaMemcpyAsync(o, c->d_ctr, ns * N_COUNTERS * 8, cudaMemcpyDeviceToHost, c->stream));
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    *n = bytes;
+    return LPM_OK;
+}
+
+lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
+{
+    if (!c || !buf) return LPM_E_INVALID;
+    if (c->n_released != c->cfg.n_scenarios)
+        return fail(c, LPM_E_STATE, "release every scenario before loading a saved run");
+    SaveHeader h;
+    if (n < sizeof h) return fail(c, LPM_E_INVALID, "buffer too small for a saved run");
+    std::memcpy(&h, buf, sizeof h);
+    const size_t ns = (size_t)c->cfg.n_scenarios;
+    if (std::memcmp(h.magic, "LPMSAVE1", 8) != 0 || h.n_slots != c->n_slots_used ||
+        h.n_scen != (long long)ns || h.ncell != (long long)c->ncell() ||
+        h.ndep != (long long)c->ndep() || h.n_ctr != N_COUNTERS || h.k < 0 ||
+        h.k > c->cfg.n_steps)
+        return fail(c, LPM_E_INVALID, "saved run does not match this context");
+    const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
+    const size_t need = sizeof h + sb + ns * (c->ncell() + c->ndep() + N_COUNTERS) * 8;
+    if (n < need) return fail(c, LPM_E_INVALID, "saved run truncated (%zu of %zu bytes)", n, need);
+    lpm_status st = upload_tables(c);
+    if (st != LPM_OK) return st;
+    const char *i = static_cast<const char *>(buf) + sizeof h;
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_state, i, sb, cudaMemcpyHostToDevice, c->stream));
+    if (c->d_state2)        // the spare buffer's unreleased tail must match (see ensure_sort_buffers)
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_state2, i, sb, cudaMemcpyHostToDevice, c->stream));
+    i += sb;
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_conc, i, ns * c->ncell() * 8, cudaMemcpyHostToDevice, c->stream));
+    i += ns * c->ncell() * 8;
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_dep, i, ns * c->ndep() * 8, cudaMemcpyHostToDevice, c->stream));
+    i += ns * c->ndep() * 8;
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_ctr, i, ns * N_COUNTERS * 8, cudaMemcpyHostToDevice, c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
+    if (c->d_live) {
+        LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
+    }
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->k = h.k;
+    c->n_bins = h.n_bins;
+    c->n_sorted = 0;
+    c->last_sort = h.k;
     return LPM_OK;
 }
 

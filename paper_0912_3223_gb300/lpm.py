@@ -28,7 +28,8 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_deposition", "lpm_budget", "lpm_particles", "lpm_fixed_state",
            "lpm_set_launch", "lpm_sync", "lpm_draws", "lpm_release_range", "lpm_reset",
            "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
-           "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort"]
+           "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save",
+           "lpm_load"]
 
 
 class LpmError(RuntimeError):
@@ -96,6 +97,8 @@ def load() -> C.CDLL:
     L.lpm_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), dp]
     L.lpm_set_params.argtypes = [vp, C.c_double, C.c_double, C.c_double]
     L.lpm_set_sort.argtypes = [vp, C.c_int]
+    L.lpm_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    L.lpm_load.argtypes = [vp, vp, C.c_size_t]
     L.lpm_set_emission.argtypes = [vp, C.c_int, dp, C.c_int]
     L.lpm_receptors.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp]
     L.lpm_adjoint.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp, dp]
@@ -108,7 +111,7 @@ def load() -> C.CDLL:
                  "lpm_particles", "lpm_fixed_state", "lpm_set_launch", "lpm_sync",
                  "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
                  "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
-                 "lpm_adjoint", "lpm_draws_static", "lpm_set_sort"):
+                 "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -218,6 +221,20 @@ def lpm_stats(ctx):
     a, b, ms = C.c_int64(), C.c_int64(), C.c_double()
     _check(ctx, load().lpm_stats(C.c_void_p(ctx), C.byref(a), C.byref(b), C.byref(ms)))
     return int(a.value), int(b.value), float(ms.value)
+
+
+def lpm_save(ctx) -> bytes:
+    """The run state as bytes (step, particles in index order, grids, counters)."""
+    n = C.c_size_t(0)
+    _check(ctx, load().lpm_save(C.c_void_p(ctx), None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, load().lpm_save(C.c_void_p(ctx), C.cast(buf, C.c_void_p), C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def lpm_load(ctx, state: bytes) -> None:
+    buf = C.create_string_buffer(state, len(state))
+    _check(ctx, load().lpm_load(C.c_void_p(ctx), C.cast(buf, C.c_void_p), len(state)))
 
 
 def lpm_set_sort(ctx, every_steps: int) -> None:

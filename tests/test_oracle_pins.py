@@ -384,3 +384,28 @@ def test_binning_brute_force_and_integer_identity():
     sh = oracle.fixed_shift(cfg)
     fixed = np.array([int(np.rint(np.ldexp(v, sh))) for v in m], dtype=np.int64)
     assert int(r["conc_fixed"].sum()) + int(r["counters"][0]) == int(fixed.sum())
+
+
+def test_drift_correction_well_mixed_condition():
+    """K_z = K0 + K1 z in a reflecting column, no wind: the random walk of Eq. 2 (no drift)
+    relaxes to the stationary law of dz = sqrt(2K) dW with zero-flux walls, density
+    proportional to 1/K(z); adding (dK_z/dz) dt (drift_correction) gives the uniform,
+    well-mixed state. KS tests pin both (catches a wrong sign, factor or missing drift)."""
+    H, nz, K0, K1 = 100.0, 11, 10.0, 0.1
+    z_levels = np.linspace(0.0, H, nz)
+    uvwk = np.zeros((2, nz, 2, 2, 4), np.float32)
+    uvwk[..., 3] = (K0 + K1 * z_levels)[None, :, None, None]
+    res = {}
+    for drift in (1, 0):
+        cfg = li.make_cfg0(n_particles=8000, n_steps=2000, kh=0.0, kz=0.0, u=0.0,
+                           src=(0.0, 0.0, 50.0))
+        cfg = dataclasses.replace(cfg, uvwk=uvwk, z_levels=z_levels, nz=nz, dt=2.0,
+                                  reflect_top=1, z_top=H, drift_correction=drift,
+                                  release=li.Release(8000, np.array([1.0]), 3600.0, 0, 10))
+        z = oracle.run(cfg)["pos"][:, 2]
+        uniform = stats.kstest(z / H, "uniform").pvalue
+        inv_k = stats.kstest(np.log((K0 + K1 * z) / K0) / np.log((K0 + K1 * H) / K0),
+                             "uniform").pvalue
+        res[drift] = (uniform, inv_k)
+    assert res[1][0] > 1e-3 and res[1][1] < 1e-6, res
+    assert res[0][1] > 1e-3 and res[0][0] < 1e-6, res

@@ -294,3 +294,41 @@ def test_sorting_particles_by_cell_changes_nothing(every):
     assert np.array_equal(part[0], xyz[1234:1333]) and np.array_equal(part[1], tag[1234:1333])
     assert np.array_equal(cfix, ref["conc_fixed"]) and np.array_equal(dfix, ref["dep_fixed"])
     assert np.array_equal(ctr[:6], ref["counters"][:6])
+
+
+@pytest.mark.parametrize("sort_every", [0, 60])
+def test_save_and_resume_is_bit_identical(sort_every):
+    """Checkpoint after 150 steps, resume in a fresh context: the continued run equals the
+    uninterrupted one bit for bit (particles, grids, counters)."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = li.make_cfg1(n_particles=6007, n_steps=330, n_hours=4)
+    with Sim(cfg, sort_every=sort_every) as a:
+        a.step(150)
+        saved = lpm.lpm_save(a.ctx)
+        a.step(cfg.n_steps - 150)
+        ref_xyz, ref_tag = a.particles()
+        ref = a.fixed_state()
+    with Sim(cfg, sort_every=sort_every) as b:
+        lpm.lpm_load(b.ctx, saved)
+        assert b.k == 150
+        b.step(cfg.n_steps - 150)
+        xyz, tag = b.particles()
+        got = b.fixed_state()
+    assert np.array_equal(xyz, ref_xyz) and np.array_equal(tag, ref_tag)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    assert np.array_equal(got[2][:6], ref[2][:6])
+    with Sim(li.make_cfg1(n_particles=100, n_steps=330, n_hours=4)) as other:
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_load(other.ctx, saved)
+        assert e.value.status == lpm.LPM_E_INVALID
+
+
+def test_allocation_failure_is_reported():
+    """A context too large for the device fails cleanly with LPM_E_OOM."""
+    from paper_0912_3223_gb300 import lpm
+    cfg = li.make_cfg0(n_particles=10, n_steps=10)
+    with pytest.raises(lpm.LpmError) as e:
+        lpm.lpm_create(cfg, max_particles=1 << 40)
+    assert e.value.status == lpm.LPM_E_OOM
+    ctx = lpm.lpm_create(cfg)           # the device is still usable
+    lpm.lpm_destroy(ctx)
