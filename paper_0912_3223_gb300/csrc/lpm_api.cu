@@ -149,12 +149,16 @@ lpm_status fail(lpm_ctx *c, lpm_status s, const char *fmt, ...)
     return s;
 }
 
+// On failure the CUDA error is reported through the status and consumed, so that it
+// does not resurface at a later, unrelated launch check.
 #define LPM_CUDA(c, call)                                                                  \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess)                                                             \
+        if (e_ != cudaSuccess) {                                                           \
+            (void)cudaGetLastError();                                                      \
             return fail((c), e_ == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA,     \
                         "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+        }                                                                                  \
     } while (0)
 
 bool is_finite(double v) { return std::isfinite(v); }
@@ -525,6 +529,7 @@ lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
         if (e_ != cudaSuccess) {                                                           \
+            (void)cudaGetLastError();                                                      \
             fail(c, e_ == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA, "%s: %s",   \
                  #call, cudaGetErrorString(e_));                                           \
             return bail(e_ == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA);         \
@@ -1433,9 +1438,11 @@ lpm_status lpm_draws(uint64_t seed, const uint64_t *pid, const uint32_t *step, u
     if (e == cudaSuccess) e = launch_draws(nullptr, seed, d_pid, d_step, stream, n, d_w, d_n);
     if (e == cudaSuccess) e = cudaMemcpy(words, d_w, n * sizeof(uint4), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(normals, d_n, n * 3 * sizeof(float), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess)
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
         st = fail(nullptr, e == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA, "lpm_draws: %s",
                   cudaGetErrorString(e));
+    }
     cudaFree(d_pid);
     cudaFree(d_step);
     cudaFree(d_w);

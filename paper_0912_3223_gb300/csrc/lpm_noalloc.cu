@@ -39,6 +39,7 @@ lpm_status fail(lpm_status s, const char *msg)
 
 lpm_status fail_cuda(const char *what, cudaError_t e)
 {
+    (void)cudaGetLastError();    // reported through the status; do not let it linger
     char buf[256];
     std::snprintf(buf, sizeof buf, "lpm_draws_static: %s: %s", what, cudaGetErrorString(e));
     return fail(e == cudaErrorMemoryAllocation ? LPM_E_OOM : LPM_E_CUDA, buf);
