@@ -223,6 +223,7 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.dx = (float)g.dx; P.dy = (float)g.dy;
     P.inv_dx = (float)(1.0 / g.dx); P.inv_dy = (float)(1.0 / g.dy);
     P.met_t0 = (float)g.met_t0; P.met_dt = (float)g.met_dt;
+    P.inv_met_dt = (float)(1.0 / g.met_dt);
     P.x_lo = (float)g.x0; P.x_hi = (float)(g.x0 + (g.nx - 1) * g.dx);
     P.y_lo = (float)g.y0; P.y_hi = (float)(g.y0 + (g.ny - 1) * g.dy);
     for (int k = 0; k < g.nz; ++k) P.zlev[k] = (float)c->zlev[k];

@@ -65,7 +65,7 @@ struct StepParams {
     int nx, ny, nz, n_t;
     long long slab;                  // nodes per slab
     float x0, y0, inv_dx, inv_dy, dx, dy;
-    float met_t0, met_dt;
+    float met_t0, met_dt, inv_met_dt;
     float x_lo, x_hi, y_lo, y_hi;
     float zlev[MAX_LEVELS];
     const unsigned char *zlut;       // level at the start of each uniform z bin, or nullptr
@@ -104,8 +104,11 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
     constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
-        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        // one 32x32 -> 64-bit product per multiplier: both halves from one wide multiply
+        const unsigned long long p0 = (unsigned long long)M0 * c0;
+        const unsigned long long p1 = (unsigned long long)M1 * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
         const uint32_t n0 = hi1 ^ c1 ^ k0;
         const uint32_t n2 = hi0 ^ c3 ^ k1;
         c0 = n0;
@@ -166,8 +169,9 @@ __device__ __forceinline__ TimeSlab time_slab(const StepParams &P, float t)
         s.h0 = 0; s.h1 = 0; s.f = 0.0f;
         return s;
     }
-    // correctly rounded division: exact at slab boundaries (t_k on an hour mark)
-    const float ft = __fdiv_rn(t - P.met_t0, P.met_dt);
+    // the interpolant is continuous across slab boundaries, so the reciprocal is enough
+    // here (the rain hour, a discrete choice, uses the exact division)
+    const float ft = (t - P.met_t0) * P.inv_met_dt;
     int h = (int)floorf(ft);
     h = min(max(h, 0), P.n_t - 2);
     s.h0 = h;
