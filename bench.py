@@ -188,7 +188,8 @@ def run_reference(args):
 def measure_batched(args, stream, cfg=None):
     """The batched ensemble form: 256 scenarios (log-uniform 1e4..1e6 particles, own
     source, release height, 24-value emission series and wind offset), 12 h at dt = 30 s,
-    one persistent launch per run replayed from a CUDA graph."""
+    particles of all scenarios sorted by cell every `sort_every` steps; the whole run (sorts
+    and persistent launches) is one CUDA graph launch."""
     import torch
 
     import lpm_inputs as li
@@ -196,7 +197,8 @@ def measure_batched(args, stream, cfg=None):
     cfg = cfg or li.make_cfg2()
     with torch.cuda.stream(stream):
         sim = Sim(cfg, stream=stream, launch=(args.batched_block, args.batched_ppt,
-                                              args.batched_occ))
+                                              args.batched_occ),
+                  sort_every=args.batched_sort_every)
     try:
         for _ in range(max(1, args.warmup)):
             sim.reset()
@@ -223,7 +225,8 @@ def measure_batched(args, stream, cfg=None):
             "scenarios": cfg.n_scenarios, "particles": cfg.n_particles,
             "steps_per_run": cfg.n_steps, "graph_launches_per_run": adv // max(1, args.steps),
             "kernel_launches_per_run": launches / max(1, args.steps),
-            "launch": [args.batched_block, args.batched_ppt, args.batched_occ]}
+            "launch": [args.batched_block, args.batched_ppt, args.batched_occ],
+            "sort_every": args.batched_sort_every}
 
 
 def measure_adjoint(args, stream):
@@ -500,6 +503,8 @@ def main():
     ap.add_argument("--batched-block", type=int, default=256)
     ap.add_argument("--batched-ppt", type=int, default=1)
     ap.add_argument("--batched-occ", type=int, default=2)
+    ap.add_argument("--batched-sort-every", type=int, default=60,
+                    help="steps between sorts by cell in the batched form (0: off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -129,8 +129,9 @@ adj_forward_kernel(const StepParams P, const AdjParams A)
         for (int k = sp; k < A.n_steps; ++k) {
             if (k > sp && k % CK == 0)
                 A.ckpt[(long long)(k / CK) * A.n_slots + slot] = pack_state(x, y, z, ST_ACTIVE, sp);
-            const StepTime T = step_time(P, sc, k);
-            st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp, sig_h_uniform, x, y, z, nullptr);
+            const StepTime T = step_time(P, sc.wind_offset, k);
+            st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp, sig_h_uniform, T.du, T.dv,
+                                      x, y, z, nullptr);
             if (st != ST_ACTIVE) {
                 for (int c = k / CK + 1; c < A.n_ck; ++c)
                     A.ckpt[(long long)c * A.n_slots + slot] = pack_state(x, y, z, st, sp);
@@ -215,10 +216,11 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
         for (int k = k_lo; k < k_hi; ++k) {
             if (alive && k >= kstart) {
                 seg[k - k_lo] = make_float4(x, y, z, 0.f);
-                const StepTime T = step_time(P, sc, k);
+                const StepTime T = step_time(P, sc.wind_offset, k);
                 float fs;
                 const uint32_t st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp,
-                                                         sig_h_uniform, x, y, z, &fs);
+                                                         sig_h_uniform, T.du, T.dv, x, y, z,
+                                                         &fs);
                 sfold[k - k_lo] = (signed char)fs;
                 klast = k;
                 if (st != ST_ACTIVE) { alive = false; ev = true; }
@@ -252,7 +254,7 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
             }
             // undo step k at the state before it
             const float4 X = seg[i];
-            const StepTime T = step_time(P, sc, k);
+            const StepTime T = step_time(P, sc.wind_offset, k);
             float val[5], g[5][3];
             sample_met_grad(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
             const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,

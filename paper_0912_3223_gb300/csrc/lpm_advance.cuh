@@ -40,6 +40,56 @@ __device__ __forceinline__ void warp_accumulate(int key, unsigned long long v,
     __syncwarp();
 }
 
+// The same over the grids of all scenarios: key = scenario * n_cells + cell, or
+// -2 - scenario for that scenario's out-of-grid counter (-1: nothing).
+__device__ __forceinline__ void warp_accumulate_scen(long long key, unsigned long long v,
+                                                     const StepParams &P,
+                                                     unsigned long long *s_warp, long long n_cells)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    s_warp[lane] = v;
+    __syncwarp();
+    if (key != -1 && lane == __ffs(peers) - 1) {
+        unsigned long long sum = 0;
+        unsigned m = peers;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            sum += s_warp[b];
+            m &= m - 1;
+        }
+        if (key >= 0) {
+            if (key < n_cells * P.n_scen) atomicAdd(P.conc_all + key, sum);
+            else atomicOr(P.err, ERR_INDEX);
+        } else {
+            atomicAdd(P.ctr_all + (long long)C_BIN_OUT * P.ctr_stride + (-2 - key), sum);
+        }
+    }
+    __syncwarp();
+}
+
+// Adds v to counter `which` of scenario s (s < 0: nothing), one atomic per scenario present
+// in the warp. Every lane of the warp must call it.
+__device__ __forceinline__ void warp_count_scen(int s, unsigned long long v, int which,
+                                                const StepParams &P, unsigned long long *s_warp)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, s);
+    s_warp[lane] = v;
+    __syncwarp();
+    if (s >= 0 && lane == __ffs(peers) - 1) {
+        unsigned long long sum = 0;
+        unsigned m = peers;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            sum += s_warp[b];
+            m &= m - 1;
+        }
+        if (sum) atomicAdd(P.ctr_all + (long long)which * P.ctr_stride + s, sum);
+    }
+    __syncwarp();
+}
+
 // Weather at a point from the time-paired records: 8 spatial corners, each one 32-byte
 // load of (slab h, slab h+1), blended in time, then in x, y and z.
 __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels &L,
@@ -109,7 +159,7 @@ struct StepTime {
     float du, dv;                    // wind offset of the scenario + bias
 };
 
-__device__ __forceinline__ StepTime step_time(const StepParams &P, const ScenDev &sc, int k)
+__device__ __forceinline__ StepTime step_time(const StepParams &P, const float2 *wind_offset, int k)
 {
     StepTime T;
     T.k = k;
@@ -119,9 +169,9 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const ScenDev
     T.khp = P.khpair ? P.khpair + (long long)T.ts.h0 * P.slab : nullptr;
     T.du = P.bias_u;
     T.dv = P.bias_v;
-    if (sc.wind_offset) {
-        const float2 o0 = __ldg(sc.wind_offset + T.ts.h0);
-        const float2 o1 = __ldg(sc.wind_offset + T.ts.h1);
+    if (wind_offset) {
+        const float2 o0 = __ldg(wind_offset + T.ts.h0);
+        const float2 o1 = __ldg(wind_offset + T.ts.h1);
         T.du += fmaf(T.ts.f, o1.x - o0.x, o0.x);
         T.dv += fmaf(T.ts.f, o1.y - o0.y, o0.y);
     }
@@ -130,15 +180,15 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const ScenDev
 
 // One step of one active particle (Sec. 3.2 main loop: weather at the old position, K,
 // wind then random walk by Eq. 1-2, reflection, lateral exit, dry then wet deposition).
-// Updates (x, y, z) and returns the new status. With GRIDS, deposition and exit add
-// their mass to the scenario's grids and counters; *fold receives dz/dz_pre (+-1, 0 when
-// clamped).
+// Updates (x, y, z) and returns the new status. (du, dv) is the wind offset of the
+// particle's scenario plus the bias at t_k. With GRIDS, deposition and exit add their mass
+// to the scenario's grids and counters; *fold receives dz/dz_pre (+-1, 0 when clamped).
 template <bool GRIDS>
 __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Levels &LV,
                                                   const StepTime &T, const ScenDev &sc,
                                                   const ScenDev *scg, unsigned long long gid,
-                                                  int sp, float sig_h_uniform, float &x, float &y,
-                                                  float &z, float *fold)
+                                                  int sp, float sig_h_uniform, float du, float dv,
+                                                  float &x, float &y, float &z, float *fold)
 {
     const int k = T.k;
     // 1. weather at the old position and t_k; 2. diffusivities
@@ -151,8 +201,8 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
     float n0, n1, n2;
     normals3(w, n0, n1, n2);
     // 4. Eq. (1)-(2): wind then turbulent displacement
-    const float xn = x + (m.u + T.du) * P.dt + n0 * sig_h;
-    const float yn = y + (m.v + T.dv) * P.dt + n1 * sig_h;
+    const float xn = x + (m.u + du) * P.dt + n0 * sig_h;
+    const float yn = y + (m.v + dv) * P.dt + n1 * sig_h;
     float zn = z + m.w * P.dt + n2 * sig_z;
     if (P.drift) zn += P.k_scale * m.dkz * P.dt;
     // 5. reflection, at most 4 folds, then clamp
@@ -216,13 +266,16 @@ struct MinBlocks {
     static constexpr int value = per_sm_threads / BLOCK > 0 ? per_sm_threads / BLOCK : 1;
 };
 
-// Advance: each thread keeps PPT particles in registers and runs steps [k0, k1). Tiles
-// are implicit (plain form: tile t = slots [t*T, t*T+T) of scenario 0) or taken from a
-// table through an atomic queue by a persistent grid (batched form).
-template <int BLOCK, int PPT, int OCC>
+// Advance: each thread keeps PPT particles in registers and runs steps [k0, k1) over the
+// launch's tiles (Ranges): sorted tiles of A and release-ordered tiles of B, handed out by
+// block index (grid over all tiles) or by an atomic queue (persistent grid). With MIXED the
+// lanes of a tile may belong to different scenarios (the sorted particles of a batched
+// context): each lane finds its scenario from its home slot and carries its own wind
+// offset; the results are bit-identical to the per-scenario path.
+template <int BLOCK, int PPT, int OCC, bool MIXED>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
-advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__restrict__ tiles,
-               int n_tiles, unsigned int *queue, const PlainRanges R, int k0, int k1, int do_bin)
+advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
+               int k1, int do_bin)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
@@ -241,48 +294,54 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
         // ---- fetch a tile -----------------------------------------------------------
         __syncthreads();
         if (threadIdx.x == 0) {
-            int t;
-            if (tiles) t = (int)atomicAdd(queue, 1u);
-            else t = blockIdx.x + iter * gridDim.x;
-            s_tile = t;
+            s_tile = queue ? (int)atomicAdd(queue, 1u) : (int)blockIdx.x + iter * (int)gridDim.x;
             s_steps = 0ull;
         }
         __syncthreads();
         const int t = s_tile;
         ++iter;
         if (t >= n_tiles) break;
-        Tile tile;
-        bool sorted = false;
-        if (tiles) {
-            tile = tiles[t];
+        const bool in_a = t < R.tiles_a;
+        float4 *state;
+        long long first;
+        int count, tscen;
+        if (in_a) {
+            state = R.state_a;
+            first = (long long)t * TILE;
+            count = (int)max(0LL, min((long long)TILE, (long long)*R.a_live - first));
+            tscen = 0;
         } else {
-            tile.scen = 0;
-            if (t < R.tiles_a) {
-                const long long n_a = R.a_live ? (long long)*R.a_live : R.a_cap;
-                tile.first = (long long)t * TILE;
-                tile.count = (int)max(0LL, min((long long)TILE, n_a - tile.first));
-                sorted = R.pidx != nullptr;
-            } else {
-                tile.first = R.b_base + (long long)(t - R.tiles_a) * TILE;
-                tile.count = (int)min((long long)TILE, R.b_base + R.b_n - tile.first);
-            }
-            if (tile.count <= 0) continue;              // the whole block skips
+            const Tile tl = R.b_tiles[R.b_first + (t - R.tiles_a)];
+            state = R.state_b;
+            first = tl.first;
+            count = tl.count;
+            tscen = tl.scen;
         }
-        const ScenDev &scg = P.scen[tile.scen];
-        const ScenDev sc = scg;
+        if (count <= 0) continue;                       // the whole block skips
+        const ScenDev &scg = P.scen[tscen];
+        const ScenDev sc = scg;                         // (unused when MIXED)
 
         // ---- load particles ---------------------------------------------------------
         float x[PPT], y[PPT], z[PPT];
         uint32_t tag[PPT];
         unsigned long long gid[PPT];
+        int sj[PPT];                                    // scenario of each particle (MIXED)
         int live = 0;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int local = j * BLOCK + threadIdx.x;
-            const long long slot = tile.first + local;
-            gid[j] = (unsigned long long)(sc.id0 + (sorted ? (long long)__ldg(R.pidx + (local < tile.count ? slot : tile.first))
-                                                            : slot - sc.first_slot));
-            if (local < tile.count) {
+            const long long slot = first + local;
+            sj[j] = tscen;
+            gid[j] = 0ull;
+            if (local < count) {
+                const long long home = in_a ? (long long)__ldg(R.pidx + slot) : slot;
+                if (MIXED) {
+                    if (in_a) sj[j] = scen_of(P, home);
+                    const ScenDev &q = P.scen[sj[j]];
+                    gid[j] = (unsigned long long)(__ldg(&q.id0) + (home - __ldg(&q.first_slot)));
+                } else {
+                    gid[j] = (unsigned long long)(sc.id0 + (home - sc.first_slot));
+                }
                 const float4 s = state[slot];
                 x[j] = s.x; y[j] = s.y; z[j] = s.z;
                 tag[j] = __float_as_uint(s.w);
@@ -297,9 +356,26 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
 
         // ---- time loop --------------------------------------------------------------
         unsigned long long steps = 0;
+        unsigned int nst[PPT];                          // active steps per particle (MIXED)
+        float2 o0[PPT], o1[PPT];                        // lane wind offsets at h0, h1 (MIXED)
+        int cur_h = -1;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            nst[j] = 0u;
+            o0[j] = o1[j] = make_float2(0.0f, 0.0f);
+        }
 #pragma unroll 1
         for (int k = k0; k < k1 && live > 0; ++k) {
-            const StepTime T = step_time(P, sc, k);
+            const StepTime T = step_time(P, MIXED ? nullptr : sc.wind_offset, k);
+            if (MIXED && P.woff && T.ts.h0 != cur_h) {
+                cur_h = T.ts.h0;
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const float2 *w = P.woff + (long long)sj[j] * P.n_t;
+                    o0[j] = __ldg(w + T.ts.h0);
+                    o1[j] = __ldg(w + T.ts.h1);
+                }
+            }
             live = 0;
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
@@ -307,15 +383,32 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
                 const int sp = (int)(tag[j] & TAG_STEP);
                 if (st == ST_UNRELEASED && sp == k) {
                     st = ST_ACTIVE;
-                    x[j] = sc.src_x; y[j] = sc.src_y; z[j] = sc.src_z;
+                    if (MIXED) {
+                        const ScenDev &q = P.scen[sj[j]];
+                        x[j] = __ldg(&q.src_x); y[j] = __ldg(&q.src_y); z[j] = __ldg(&q.src_z);
+                    } else {
+                        x[j] = sc.src_x; y[j] = sc.src_y; z[j] = sc.src_z;
+                    }
                 }
                 if (st != ST_ACTIVE) {
                     if (st == ST_UNRELEASED && sp < k1) ++live;
                     continue;
                 }
-                ++steps;
-                st = particle_step<true>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform, x[j], y[j],
-                                         z[j], nullptr);
+                if (MIXED) {
+                    ++nst[j];
+                    float du = T.du, dv = T.dv;
+                    if (P.woff) {
+                        // the same expression as step_time's, so sorting changes no bit
+                        du = P.bias_u + fmaf(T.ts.f, o1[j].x - o0[j].x, o0[j].x);
+                        dv = P.bias_v + fmaf(T.ts.f, o1[j].y - o0[j].y, o0[j].y);
+                    }
+                    st = particle_step<true>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j], sp,
+                                             sig_h_uniform, du, dv, x[j], y[j], z[j], nullptr);
+                } else {
+                    ++steps;
+                    st = particle_step<true>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform, T.du,
+                                             T.dv, x[j], y[j], z[j], nullptr);
+                }
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;
             }
@@ -325,8 +418,8 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int local = j * BLOCK + threadIdx.x;
-            if (local < tile.count)
-                state[tile.first + local] = make_float4(x[j], y[j], z[j], __uint_as_float(tag[j]));
+            if (local < count)
+                state[first + local] = make_float4(x[j], y[j], z[j], __uint_as_float(tag[j]));
         }
 
         // ---- end-of-segment concentration snapshot (every n-th step, Sec. 3.2) --------
@@ -334,70 +427,100 @@ advance_kernel(const StepParams P, float4 *__restrict__ state, const Tile *__res
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
                 const int local = j * BLOCK + threadIdx.x;
-                int key = KEY_NONE;
-                unsigned long long v = 0ull;
                 const uint32_t st = tag[j] >> TAG_SHIFT;
-                if (local < tile.count && st == ST_ACTIVE) {
+                const bool on = local < count && st == ST_ACTIVE;
+                int cell = KEY_NONE;
+                unsigned long long v = 0ull;
+                if (on) {
                     const int sp = (int)(tag[j] & TAG_STEP);
-                    v = to_fixed(mass_at(P, sc, sp, k1 - 1), sc.scale);
+                    if (MIXED) {
+                        const ScenDev &q = P.scen[sj[j]];
+                        v = to_fixed(mass_at(P, q, sp, k1 - 1), __ldg(&q.scale));
+                    } else {
+                        v = to_fixed(mass_at(P, sc, sp, k1 - 1), sc.scale);
+                    }
                     const int ix = (int)floorf((x[j] - P.cx0) * P.inv_cdx);
                     const int iy = (int)floorf((y[j] - P.cy0) * P.inv_cdy);
                     const int iz = (int)floorf((z[j] - P.cz0) * P.inv_cdz);
                     if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz)
-                        key = (iz * P.cy + iy) * P.cx + ix;
+                        cell = (iz * P.cy + iy) * P.cx + ix;
                     else
-                        key = KEY_OUT;
+                        cell = KEY_OUT;
                 }
-                warp_accumulate(key, v, scg.conc, scg.ctr + C_BIN_OUT * P.ctr_stride, s_warp,
-                                n_cells, P.err);
+                if (MIXED) {
+                    long long key = -1;
+                    if (on) key = cell >= 0 ? (long long)sj[j] * n_cells + cell : -2LL - sj[j];
+                    warp_accumulate_scen(key, v, P, s_warp, n_cells);
+                } else {
+                    warp_accumulate(cell, v, scg.conc, scg.ctr + C_BIN_OUT * P.ctr_stride, s_warp,
+                                    n_cells, P.err);
+                }
             }
         }
 
         // ---- active particle-steps of the tile -----------------------------------------
-        for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
-        if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&s_steps, steps);
-        __syncthreads();
-        if (threadIdx.x == 0 && s_steps) atomicAdd(scg.ctr + C_ACTIVE_STEPS * P.ctr_stride, s_steps);
+        if (MIXED) {
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int local = j * BLOCK + threadIdx.x;
+                warp_count_scen(local < count ? sj[j] : -1, nst[j], C_ACTIVE_STEPS, P, s_warp);
+            }
+        } else {
+            for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+            if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&s_steps, steps);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_steps)
+                atomicAdd(scg.ctr + C_ACTIVE_STEPS * P.ctr_stride, s_steps);
+        }
     }
 }
 
-template <int BLOCK, int PPT, int OCC>
+template <int BLOCK, int PPT, int OCC, bool MIXED>
 cudaError_t launch_adv(const AdvanceLaunch &L)
 {
-    advance_kernel<BLOCK, PPT, OCC><<<L.grid, BLOCK, 0, L.stream>>>(
-        *L.params, L.state, L.tiles, L.n_tiles, L.queue, L.ranges, L.k0, L.k1, L.do_bin);
+    advance_kernel<BLOCK, PPT, OCC, MIXED><<<L.grid, BLOCK, 0, L.stream>>>(
+        *L.params, L.ranges, L.n_tiles(), L.queue, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int PPT, int OCC>
+template <int BLOCK, int PPT, int OCC, bool MIXED>
 int occ_adv()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC, MIXED>, BLOCK,
+                                                  0);
     return n;
 }
 
-// (particles per thread, occupancy variant) -> instantiation, for one block size
+// (particles per thread, occupancy variant, mixed scenarios) -> instantiation, for one
+// block size
+#define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, ...)                                    \
+    case PPT * 100 + OCC * 10 + MIX: return FN<BLOCK, PPT, OCC, (MIX != 0)>(__VA_ARGS__);
+#define LPM_ADV_CASES2(FN, BLOCK, PPT, OCC, ...)                                       \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, __VA_ARGS__)                                  \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, __VA_ARGS__)
 #define LPM_ADV_CASES(FN, BLOCK, ...)                                                  \
-    case 10: return FN<BLOCK, 1, 0>(__VA_ARGS__);                                      \
-    case 11: return FN<BLOCK, 1, 1>(__VA_ARGS__);                                      \
-    case 12: return FN<BLOCK, 1, 2>(__VA_ARGS__);                                      \
-    case 20: return FN<BLOCK, 2, 0>(__VA_ARGS__);                                      \
-    case 21: return FN<BLOCK, 2, 1>(__VA_ARGS__);                                      \
-    case 22: return FN<BLOCK, 2, 2>(__VA_ARGS__);                                      \
-    case 40: return FN<BLOCK, 4, 0>(__VA_ARGS__);                                      \
-    case 41: return FN<BLOCK, 4, 1>(__VA_ARGS__);                                      \
-    case 42: return FN<BLOCK, 4, 2>(__VA_ARGS__);
+    LPM_ADV_CASES2(FN, BLOCK, 1, 0, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 1, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 2, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 2, 0, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 2, 1, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 2, 2, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 4, 0, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 4, 1, __VA_ARGS__)                                       \
+    LPM_ADV_CASES2(FN, BLOCK, 4, 2, __VA_ARGS__)
 
 #define LPM_ADVANCE_TU(BLOCK)                                                          \
     cudaError_t launch_advance_b##BLOCK(const AdvanceLaunch &L)                         \
     {                                                                                  \
-        switch (L.ppt * 10 + L.occ) { LPM_ADV_CASES(launch_adv, BLOCK, L) }            \
+        switch (L.ppt * 100 + L.occ * 10 + (L.mixed ? 1 : 0)) {                        \
+            LPM_ADV_CASES(launch_adv, BLOCK, L)                                        \
+        }                                                                              \
         return cudaErrorInvalidValue;                                                  \
     }                                                                                  \
-    int occupancy_b##BLOCK(int ppt, int occ)                                           \
+    int occupancy_b##BLOCK(int ppt, int occ, bool mixed)                               \
     {                                                                                  \
-        switch (ppt * 10 + occ) { LPM_ADV_CASES(occ_adv, BLOCK) }                      \
+        switch (ppt * 100 + occ * 10 + (mixed ? 1 : 0)) { LPM_ADV_CASES(occ_adv, BLOCK) } \
         return 0;                                                                      \
     }
 

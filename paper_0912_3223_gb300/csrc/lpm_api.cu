@@ -72,6 +72,7 @@ struct lpm_ctx {
     float lut_z0 = 0.f, lut_inv_h = 0.f;
     ScenDev *d_scen = nullptr;
     float2 *d_woff = nullptr;               // [n_scen][n_met_t]
+    bool any_woff = false;                  // some scenario has a wind offset
     Tile *d_tiles = nullptr;
     size_t d_tiles_cap = 0;
 
@@ -90,12 +91,17 @@ struct lpm_ctx {
     long long n_bins = 0;                   // snapshots taken
     int block = 256, ppt = 1, occ = 2;
 
-    // plain form: periodic sort of the released particles by weather cell
+    // sorting by weather cell (both forms) at the multiples of sort_every: d_state is the
+    // home buffer (slot order of the API); the live particles released before sorted_upto
+    // sit ordered by cell in d_sorted[cur], the dead ones in d_grave
     int sort_every = 60;                    // steps between sorts; 0 = off
-    long long last_sort = 0;
-    long long n_sorted = 0;                 // slots [0, n_sorted) hold a sorted permutation
-    float4 *d_state2 = nullptr;
-    unsigned int *d_pidx = nullptr, *d_pidx2 = nullptr, *d_slot_of = nullptr, *d_keys = nullptr;
+    long long sorted_upto = 0;
+    int cur = 0;
+    float4 *d_sorted[2] = {nullptr, nullptr};
+    unsigned int *d_pidx[2] = {nullptr, nullptr};   // home slot of each sorted slot
+    unsigned int *d_slot_of = nullptr;      // per home slot: sorted slot, grave index or home
+    unsigned int *d_keys = nullptr;
+    size_t keys_cap = 0;
     unsigned int *d_hist = nullptr, *d_bsums = nullptr, *d_live = nullptr;   // d_live = meta[4]
     float4 *d_grave = nullptr;              // particles found dead at a sort (read-back only)
     unsigned int *d_grave_n = nullptr;
@@ -116,16 +122,25 @@ struct lpm_ctx {
     std::vector<double> adj_sig;            // signature of the forward whose checkpoints are held
     long long params_version = 0;
 
-    // batched form: one CUDA graph per segment (memsets + the persistent launch)
+    // batched form: one CUDA graph per lpm_step call (sorts, memsets, persistent launches),
+    // keyed by the steps and the sort state it starts from
     struct Graph {
-        long long k0, k1;
+        long long k0, k1, upto0;
+        int cur0;
+        long long upto1;
+        int cur1;
+        long long kernels;
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
 
-    // batched tile schedule
+    // tile table: runs of at most block*ppt particles of one scenario, grouped by the sort
+    // interval [j*E, (j+1)*E) their particles leave in (one interval when sorting is off),
+    // ordered by the release step of their first particle within an interval
     std::vector<Tile> tiles;
     std::vector<long long> tile_sp;         // release step of each tile's first particle
+    std::vector<int> int_lo;                // first tile of each interval (+ the end)
+    long long tiles_E = 1;                  // interval length of the table
     bool tiles_valid = false;
 
     size_t ncell() const { return (size_t)cfg.cx * cfg.cy * cfg.cz; }
@@ -195,7 +210,8 @@ lpm_status validate(const lpm_config *c)
     if (c->reflect_top && !(c->z_top > 0))
         return fail(nullptr, LPM_E_INVALID, "top reflection needs z_top > 0");
     if (c->n_scenarios < 1) return fail(nullptr, LPM_E_INVALID, "n_scenarios must be >= 1");
-    if (c->max_particles < 1) return fail(nullptr, LPM_E_INVALID, "max_particles must be >= 1");
+    if (c->max_particles < 1 || c->max_particles > 0x7ffffffeLL)
+        return fail(nullptr, LPM_E_INVALID, "max_particles must be in [1, 2^31 - 2]");
     return LPM_OK;
 }
 
@@ -257,6 +273,9 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.scen = c->d_scen;
     P.n_scen = g.n_scenarios;
     P.ctr_stride = g.n_scenarios;
+    P.woff = c->any_woff ? c->d_woff : nullptr;
+    P.conc_all = c->d_conc;
+    P.ctr_all = c->d_ctr;
     P.err = c->d_err;
 }
 
@@ -281,6 +300,7 @@ lpm_status upload_tables(lpm_ctx *c)
     std::vector<ScenDev> sd(c->scen.size());
     const size_t nt = (size_t)c->cfg.n_met_t;
     std::vector<float2> woff(c->scen.size() * nt, make_float2(0.f, 0.f));
+    c->any_woff = false;
     for (size_t s = 0; s < c->scen.size(); ++s) {
         const ScenHost &h = c->scen[s];
         ScenDev &d = sd[s];
@@ -298,6 +318,7 @@ lpm_status upload_tables(lpm_ctx *c)
             for (size_t t = 0; t < nt; ++t)
                 woff[s * nt + t] = make_float2(h.wind_offset[2 * t], h.wind_offset[2 * t + 1]);
             d.wind_offset = c->d_woff + s * nt;
+            c->any_woff = true;
         }
         d.conc = c->d_conc + s * c->ncell();
         d.dep = c->d_dep + s * c->ndep();
@@ -387,69 +408,129 @@ long long released_before(const ScenHost &h, long long k1)
     return std::max(0LL, std::min(upto - h.part_first, h.n));
 }
 
-// Batched schedule: tiles of BLOCK*PPT consecutive particles of one scenario, ordered by
-// the release step of their first particle (longest-running first). A segment ending at
-// step k1 runs the prefix of tiles whose first particle leaves before k1.
+// Tile table (see lpm_ctx::tiles). A segment [k, e) after the sort at sorted_upto runs
+// the tiles from the interval of sorted_upto up to the last tile whose first particle
+// leaves before e; a sort at a multiple of E takes the tiles of the intervals since the
+// previous sort. Tiles never straddle an interval, so no particle is in both sets.
 lpm_status build_tiles(lpm_ctx *c)
 {
     const int T = c->block * c->ppt;
-    std::vector<std::pair<long long, Tile>> items;
-    for (size_t s = 0; s < c->scen.size(); ++s) {
-        const ScenHost &h = c->scen[s];
-        const long long S = h.rel_last - h.rel_first;
-        for (long long p = 0; p < h.n; p += T) {
-            Tile t;
-            t.scen = (int)s;
-            t.first = h.first_slot + p;
-            t.count = (int)std::min<long long>(T, h.n - p);
-            const long long sp = h.rel_first + ((h.part_first + p) * S) / h.n_total;
-            items.push_back({sp, t});
-        }
-    }
-    std::stable_sort(items.begin(), items.end(),
-                     [](const auto &a, const auto &b) { return a.first < b.first; });
+    const long long NS = std::max<long long>(1, c->cfg.n_steps);
+    const long long E = c->sort_every > 0 ? c->sort_every : NS;
+    const long long n_int = (NS + E - 1) / E;
     c->tiles.clear();
     c->tile_sp.clear();
-    for (auto &it : items) {
-        c->tiles.push_back(it.second);
-        c->tile_sp.push_back(it.first);
+    c->int_lo.assign((size_t)n_int + 1, 0);
+    std::vector<std::pair<long long, Tile>> items;
+    for (long long j = 0; j < n_int; ++j) {
+        c->int_lo[(size_t)j] = (int)c->tiles.size();
+        items.clear();
+        for (size_t s = 0; s < c->scen.size(); ++s) {
+            const ScenHost &h = c->scen[s];
+            const long long S = h.rel_last - h.rel_first;
+            const long long a = released_before(h, j * E), b = released_before(h, (j + 1) * E);
+            for (long long p = a; p < b; p += T) {
+                Tile t;
+                t.scen = (int)s;
+                t.first = h.first_slot + p;
+                t.count = (int)std::min<long long>(T, b - p);
+                const long long sp = h.rel_first + ((h.part_first + p) * S) / h.n_total;
+                items.push_back({sp, t});
+            }
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const auto &x, const auto &y) { return x.first < y.first; });
+        for (auto &it : items) {
+            c->tiles.push_back(it.second);
+            c->tile_sp.push_back(it.first);
+        }
     }
+    c->int_lo[(size_t)n_int] = (int)c->tiles.size();
+    c->tiles_E = E;
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (c->tiles.size() > c->d_tiles_cap) {
+    if (c->tiles.size() > c->d_tiles_cap || !c->d_tiles) {
         if (c->d_tiles) cudaFree(c->d_tiles);
         c->d_tiles = nullptr;
         LPM_CUDA(c, cudaMalloc(&c->d_tiles, std::max<size_t>(1, c->tiles.size()) * sizeof(Tile)));
-        c->d_tiles_cap = c->tiles.size();
+        c->d_tiles_cap = std::max<size_t>(1, c->tiles.size());
     }
     if (!c->tiles.empty())
         LPM_CUDA(c, cudaMemcpy(c->d_tiles, c->tiles.data(), c->tiles.size() * sizeof(Tile),
                                cudaMemcpyHostToDevice));
     c->tiles_valid = true;
+    drop_graphs(c);
     return LPM_OK;
 }
 
-lpm_status ensure_sort_buffers(lpm_ctx *c)
+// Index of the first tile whose first particle leaves at or after step e.
+int tiles_before(const lpm_ctx *c, long long e)
 {
-    if (c->d_state2) return LPM_OK;
-    const size_t n = (size_t)c->cfg.max_particles;
-    const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
-    const size_t ntiles = (nb + 1023) / 1024;
-    LPM_CUDA(c, cudaMalloc(&c->d_state2, n * sizeof(float4)));
-    LPM_CUDA(c, cudaMalloc(&c->d_pidx, n * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_pidx2, n * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_slot_of, n * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_keys, n * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_hist, nb * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_bsums, ntiles * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_live, 4 * sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMalloc(&c->d_grave, n * sizeof(float4)));
-    LPM_CUDA(c, cudaMalloc(&c->d_grave_n, sizeof(unsigned int)));
-    LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
-    LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
-    // A particle's state is constant until its release, and a sort moves only the released
-    // prefix: the second buffer needs the unreleased tail once, here and at every reset.
-    LPM_CUDA(c, cudaMemcpyAsync(c->d_state2, c->d_state, (size_t)c->n_slots_used * sizeof(float4),
-                                cudaMemcpyDeviceToDevice, c->stream));
+    if (e <= 0 || c->tiles.empty()) return 0;
+    const long long n_int = (long long)c->int_lo.size() - 1;
+    const long long j = std::min((e - 1) / c->tiles_E, n_int - 1);
+    const auto lo = c->tile_sp.begin() + c->int_lo[(size_t)j];
+    const auto hi = c->tile_sp.begin() + c->int_lo[(size_t)j + 1];
+    return (int)(std::lower_bound(lo, hi, e) - c->tile_sp.begin());
+}
+
+// Held particles (all scenarios) that leave before step k.
+long long released_total(const lpm_ctx *c, long long k)
+{
+    long long n = 0;
+    for (const ScenHost &h : c->scen) n += released_before(h, k);
+    return n;
+}
+
+lpm_status ensure_sort_buffers(lpm_ctx *c, size_t keys_need)
+{
+    if (!c->d_sorted[0]) {
+        drop_graphs(c);                      // graphs hold the buffers' addresses
+        const size_t n = (size_t)c->cfg.max_particles;
+        const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
+        const size_t ntiles = (nb + 1023) / 1024;
+        for (int b = 0; b < 2; ++b) {
+            LPM_CUDA(c, cudaMalloc(&c->d_sorted[b], n * sizeof(float4)));
+            LPM_CUDA(c, cudaMalloc(&c->d_pidx[b], n * sizeof(unsigned int)));
+        }
+        LPM_CUDA(c, cudaMalloc(&c->d_slot_of, n * sizeof(unsigned int)));
+        LPM_CUDA(c, cudaMalloc(&c->d_hist, nb * sizeof(unsigned int)));
+        LPM_CUDA(c, cudaMalloc(&c->d_bsums, ntiles * sizeof(unsigned int)));
+        LPM_CUDA(c, cudaMalloc(&c->d_live, 4 * sizeof(unsigned int)));
+        LPM_CUDA(c, cudaMalloc(&c->d_grave, n * sizeof(float4)));
+        LPM_CUDA(c, cudaMalloc(&c->d_grave_n, sizeof(unsigned int)));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_slot_of, 0xff, n * sizeof(unsigned int), c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
+    }
+    if (keys_need > c->keys_cap) {
+        drop_graphs(c);
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->d_keys) cudaFree(c->d_keys);
+        c->d_keys = nullptr;
+        c->keys_cap = 0;
+        LPM_CUDA(c, cudaMalloc(&c->d_keys, keys_need * sizeof(unsigned int)));
+        c->keys_cap = keys_need;
+    }
+    return LPM_OK;
+}
+
+// Empties the sorted set: every particle back to its home slot.
+lpm_status clear_sort_state(lpm_ctx *c, bool move_back)
+{
+    if (c->d_sorted[0]) {
+        if (move_back && c->sorted_upto > 0)
+            LPM_CUDA(c, launch_unsort(c->stream, c->d_state, c->d_sorted[c->cur], c->d_slot_of,
+                                      c->d_grave, c->n_slots_used));
+        else
+            LPM_CUDA(c, cudaMemsetAsync(c->d_slot_of, 0xff,
+                                        (size_t)c->cfg.max_particles * sizeof(unsigned int),
+                                        c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
+        c->n_launches++;
+    }
+    c->sorted_upto = 0;
+    c->cur = 0;
     return LPM_OK;
 }
 
@@ -599,9 +680,9 @@ void lpm_destroy(lpm_ctx *c)
     void *ptrs[] = {c->d_uvwk, c->d_kh, c->d_pair, c->d_khpair, c->d_rain, c->d_state, c->d_conc, c->d_dep, c->d_ctr,
                     c->d_err, c->d_queue, c->d_m0, c->d_scen, c->d_woff, c->d_tiles,
                     c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
-                    c->d_rgrad, c->d_adj_tiles, c->d_state2, c->d_pidx, c->d_pidx2,
-                    c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live, c->d_grave,
-                    c->d_grave_n};
+                    c->d_rgrad, c->d_adj_tiles, c->d_sorted[0], c->d_sorted[1], c->d_pidx[0],
+                    c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
+                    c->d_grave, c->d_grave_n};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -749,15 +830,9 @@ lpm_status lpm_reset(lpm_ctx *c)
     fill_params(c, P);
     LPM_CUDA(c, launch_release_all(c->stream, P, c->d_state, c->n_slots_used));
     c->n_launches++;
-    if (c->d_state2) {
-        LPM_CUDA(c, launch_release_all(c->stream, P, c->d_state2, c->n_slots_used));
-        LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
-        LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
-        c->n_launches++;
-    }
+    st = clear_sort_state(c, false);
+    if (st != LPM_OK) return st;
     c->k = 0;
-    c->n_sorted = 0;
-    c->last_sort = 0;
     c->n_bins = 0;
     return LPM_OK;
 }
@@ -801,6 +876,108 @@ lpm_status lpm_set_launch(lpm_ctx *c, int block, int ppt, int occupancy)
     return LPM_OK;
 }
 
+namespace {
+
+// One segment [k, e) of an lpm_step call: an optional sort at k, then one advance launch.
+struct Segment {
+    long long k, e;
+    bool do_bin, sort, sort_has_a;
+    long long sort_a_bound;            // live-count bound of the sorted set before the sort
+    int sort_b_lo, sort_b_hi;          // tiles whose particles join the sorted set
+    long long a_bound;                 // live-count bound of the sorted set during the launch
+    int b_lo, b_hi;                    // tiles run from their home slots
+};
+
+// Issues the segments on stream s, starting from sort state (upto, cur); returns the
+// kernels launched and leaves the final sort state in (upto, cur). `direct`: launched now
+// (not captured), so advance launches are counted and, with profiling, timed.
+lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segment> &plan,
+                        cudaStream_t s, long long &upto, int &cur, long long &kernels,
+                        bool direct, int occ_blocks)
+{
+    const lpm_config &g = c->cfg;
+    const bool batched = g.n_scenarios > 1;
+    const int T = c->block * c->ppt;
+    const size_t ns = (size_t)g.n_scenarios;
+    for (const Segment &sg : plan) {
+        if (sg.do_bin) {
+            LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0, ns * c->ncell() * sizeof(unsigned long long), s));
+            LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + (size_t)C_BIN_OUT * ns, 0,
+                                        ns * sizeof(unsigned long long), s));
+        }
+        if (sg.sort) {
+            SortSource in{};
+            in.state_a = c->d_sorted[cur];
+            in.pidx_a = c->d_pidx[cur];
+            in.has_a = sg.sort_has_a;
+            in.a_bound = sg.sort_a_bound;
+            in.state_b = c->d_state;
+            in.tiles = c->d_tiles;
+            in.b_first = sg.sort_b_lo;
+            in.n_b = sg.sort_b_hi - sg.sort_b_lo;
+            in.T = T;
+            SortBuffers out{};
+            out.state_out = c->d_sorted[1 - cur];
+            out.pidx_out = c->d_pidx[1 - cur];
+            out.slot_of = c->d_slot_of;
+            out.keys = c->d_keys;
+            out.hist = c->d_hist;
+            out.block_sums = c->d_bsums;
+            out.meta = c->d_live;
+            out.grave = c->d_grave;
+            out.grave_count = c->d_grave_n;
+            LPM_CUDA(c, launch_sort(s, P, in, out));
+            cur = 1 - cur;
+            upto = sg.k;
+            kernels += 7;
+        }
+        AdvanceLaunch L{};
+        L.stream = s;
+        L.params = &P;
+        L.ranges.state_a = c->d_sorted[cur];
+        L.ranges.a_live = c->d_live;
+        L.ranges.pidx = c->d_pidx[cur];
+        L.ranges.tiles_a = (int)((sg.a_bound + T - 1) / T);
+        L.ranges.state_b = c->d_state;
+        L.ranges.b_tiles = c->d_tiles;
+        L.ranges.b_first = sg.b_lo;
+        L.ranges.n_b = sg.b_hi - sg.b_lo;
+        L.k0 = (int)sg.k;
+        L.k1 = (int)sg.e;
+        L.do_bin = sg.do_bin ? 1 : 0;
+        L.block = c->block;
+        L.ppt = c->ppt;
+        L.occ = c->occ;
+        L.mixed = batched;
+        const int n_tiles = L.n_tiles();
+        if (n_tiles <= 0) continue;
+        if (batched) {
+            // persistent grid over an atomic tile queue
+            LPM_CUDA(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), s));
+            L.queue = c->d_queue;
+            L.grid = (unsigned)std::max(1, std::min(n_tiles, occ_blocks * c->sm_count));
+        } else {
+            L.queue = nullptr;
+            L.grid = (unsigned)n_tiles;
+        }
+        const bool timed = direct && c->profiling;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            e0 = next_event(c);
+            e1 = next_event(c);
+            if (!e0 || !e1) return fail(c, LPM_E_CUDA, "cudaEventCreate failed");
+            LPM_CUDA(c, cudaEventRecord(e0, s));
+        }
+        LPM_CUDA(c, launch_advance(L));
+        if (timed) LPM_CUDA(c, cudaEventRecord(e1, s));
+        if (direct) c->n_adv_launches++;
+        kernels++;
+    }
+    return LPM_OK;
+}
+
+}  // namespace
+
 lpm_status lpm_step(lpm_ctx *c, int64_t n)
 {
     if (!c) return LPM_E_INVALID;
@@ -825,134 +1002,111 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
     }
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
+    if (!c->tiles_valid) {
+        st = build_tiles(c);
+        if (st != LPM_OK) return st;
+    }
     StepParams P;
     fill_params(c, P);
     const bool batched = g.n_scenarios > 1;
-    long long k = c->k;
+    const int T = c->block * c->ppt;
+    const long long E = c->sort_every, Et = c->tiles_E;
     const long long k_end = c->k + n;
-    while (k < k_end) {
-        long long next_bin = (k / g.bin_every + 1) * (long long)g.bin_every;
+
+    // ---- plan: segments end at snapshot steps and at multiples of E (sort points) ----------
+    std::vector<Segment> plan;
+    size_t keys_need = 0;
+    long long upto = c->sorted_upto;
+    for (long long k = c->k; k < k_end;) {
+        Segment sg{};
+        const long long next_bin = (k / g.bin_every + 1) * (long long)g.bin_every;
         long long e = std::min(k_end, std::min(next_bin, (long long)g.n_steps));
-        const bool sorting = !batched && c->sort_every > 0;
-        if (sorting) e = std::min(e, c->last_sort + c->sort_every > k ? c->last_sort + c->sort_every : k + c->sort_every);
-        const bool do_bin = (e % g.bin_every == 0) || e == g.n_steps;
-        AdvanceLaunch L{};
-        L.stream = c->stream;
-        L.params = &P;
-        L.state = c->d_state;
-        L.k0 = (int)k;
-        L.k1 = (int)e;
-        L.do_bin = do_bin ? 1 : 0;
-        L.block = c->block;
-        L.ppt = c->ppt;
-        L.occ = c->occ;
-        const int T = c->block * c->ppt;
+        if (E > 0) e = std::min(e, (k / E + 1) * E);
+        sg.k = k;
+        sg.e = e;
+        sg.do_bin = (e % g.bin_every == 0) || e == g.n_steps;
+        if (E > 0 && k > 0 && k % E == 0 && upto < k) {
+            sg.sort = true;
+            sg.sort_has_a = upto > 0;
+            sg.sort_a_bound = upto > 0 ? released_total(c, upto) : 0;
+            sg.sort_b_lo = c->int_lo[(size_t)(upto / Et)];
+            sg.sort_b_hi = c->int_lo[(size_t)(k / Et)];
+            keys_need = std::max(keys_need, (size_t)(sg.sort_a_bound +
+                                                     (long long)(sg.sort_b_hi - sg.sort_b_lo) * T));
+            upto = k;
+        }
+        sg.a_bound = upto > 0 ? released_total(c, upto) : 0;
+        sg.b_lo = c->int_lo[(size_t)(upto / Et)];
+        sg.b_hi = std::max(sg.b_lo, tiles_before(c, e));
+        plan.push_back(sg);
+        k = e;
+    }
+    if (upto > 0) {
+        st = ensure_sort_buffers(c, std::max<size_t>(keys_need, 1));
+        if (st != LPM_OK) return st;
+    }
+
+    // ---- run ------------------------------------------------------------------------------
+    if (!batched) {
+        long long kernels = 0;
+        st = run_segments(c, P, plan, c->stream, c->sorted_upto, c->cur, kernels, true, 1);
+        c->n_launches += kernels;
+        if (st != LPM_OK) return st;
+    } else {
+        // the whole call as one graph, captured once per (steps, starting sort state) on a
+        // private stream (the caller's may be the legacy stream, which cannot be captured)
+        // and launched on the caller's stream
+        lpm_ctx::Graph *gr = nullptr;
+        for (auto &x : c->graphs)
+            if (x.k0 == c->k && x.k1 == k_end && x.upto0 == c->sorted_upto && x.cur0 == c->cur)
+                gr = &x;
+        if (!gr) {
+            if (!c->cap_stream)
+                LPM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+            const cudaStream_t cs = c->cap_stream;
+            const int occ_blocks = std::max(1, advance_occupancy(c->block, c->ppt, c->occ, true));
+            lpm_ctx::Graph ng{};
+            ng.k0 = c->k;
+            ng.k1 = k_end;
+            ng.upto0 = ng.upto1 = c->sorted_upto;
+            ng.cur0 = ng.cur1 = c->cur;
+            LPM_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            lpm_status rs = run_segments(c, P, plan, cs, ng.upto1, ng.cur1, ng.kernels, false,
+                                         occ_blocks);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+            if (rs != LPM_OK || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                (void)cudaGetLastError();
+                if (rs != LPM_OK) return rs;
+                return fail(c, LPM_E_CUDA, "capturing the batched step failed: %s",
+                            cudaGetErrorString(ce));
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&ng.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(c, LPM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+            }
+            c->graphs.push_back(ng);
+            gr = &c->graphs.back();
+        }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (c->profiling) {
             e0 = next_event(c);
             e1 = next_event(c);
             if (!e0 || !e1) return fail(c, LPM_E_CUDA, "cudaEventCreate failed");
+            LPM_CUDA(c, cudaEventRecord(e0, c->stream));
         }
-        if (!batched) {
-            if (do_bin) {
-                LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0, c->ncell() * sizeof(unsigned long long),
-                                            c->stream));
-                LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + C_BIN_OUT, 0, sizeof(unsigned long long),
-                                            c->stream));
-            }
-            if (sorting && k > 0 && k - c->last_sort >= c->sort_every) {
-                // sort every particle released before step k by its weather cell
-                st = ensure_sort_buffers(c);
-                if (st != LPM_OK) return st;
-                const long long n_pre = released_before(c->scen[0], k);
-                LPM_CUDA(c, launch_sort(c->stream, P, c->d_state, c->d_pidx, c->n_sorted, n_pre,
-                                        c->d_state2, c->d_pidx2, c->d_slot_of, c->d_keys,
-                                        c->d_hist, c->d_bsums, c->d_live, c->d_grave,
-                                        c->d_grave_n));
-                std::swap(c->d_state, c->d_state2);
-                std::swap(c->d_pidx, c->d_pidx2);
-                c->n_sorted = n_pre;
-                c->last_sort = k;
-                c->n_launches += 8;
-            }
-            const long long n_rel = released_before(c->scen[0], e);
-            L.tiles = nullptr;
-            L.state = c->d_state;
-            L.ranges.a_cap = c->n_sorted;
-            L.ranges.a_live = c->n_sorted > 0 ? c->d_live : nullptr;
-            L.ranges.pidx = c->n_sorted > 0 ? c->d_pidx : nullptr;
-            L.ranges.b_base = c->n_sorted;
-            L.ranges.b_n = std::max(0LL, n_rel - c->n_sorted);
-            L.ranges.tiles_a = (int)((c->n_sorted + T - 1) / T);
-            L.n_tiles = L.ranges.tiles_a + (int)((L.ranges.b_n + T - 1) / T);
-            L.queue = c->d_queue;
-            L.grid = (unsigned)std::max(1, L.n_tiles);
-            if (L.n_tiles > 0) {
-                if (e0) LPM_CUDA(c, cudaEventRecord(e0, c->stream));
-                LPM_CUDA(c, launch_advance(L));
-                if (e1) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
-                c->n_launches++;
-                c->n_adv_launches++;
-            } else if (e0) {
-                c->ev_used -= 2;
-            }
-        } else {
-            if (!c->tiles_valid) {
-                st = build_tiles(c);
-                if (st != LPM_OK) return st;
-            }
-            cudaGraphExec_t exec = nullptr;
-            for (auto &gr : c->graphs)
-                if (gr.k0 == k && gr.k1 == e) exec = gr.exec;
-            if (!exec) {
-                // the segment as one graph: snapshot reset, queue reset, persistent launch
-                L.tiles = c->d_tiles;
-                L.ranges = PlainRanges{};
-                L.n_tiles = (int)(std::lower_bound(c->tile_sp.begin(), c->tile_sp.end(), e) -
-                                  c->tile_sp.begin());
-                L.queue = c->d_queue;
-                const int occ = std::max(1, advance_occupancy(c->block, c->ppt, c->occ));
-                L.grid = (unsigned)std::max(1, std::min(std::max(1, L.n_tiles), occ * c->sm_count));
-                // captured on a private stream (the caller's may be the legacy stream,
-                // which cannot be captured); the graph is launched on the caller's stream
-                if (!c->cap_stream)
-                    LPM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-                const cudaStream_t cs = c->cap_stream;
-                L.stream = cs;
-                LPM_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-                cudaError_t ce = cudaSuccess;
-                if (do_bin) {
-                    ce = cudaMemsetAsync(c->d_conc, 0, (size_t)g.n_scenarios * c->ncell() *
-                                                           sizeof(unsigned long long), cs);
-                    if (ce == cudaSuccess)
-                        ce = cudaMemsetAsync(c->d_ctr + (size_t)C_BIN_OUT * g.n_scenarios, 0,
-                                             (size_t)g.n_scenarios * sizeof(unsigned long long),
-                                             cs);
-                }
-                if (ce == cudaSuccess) ce = cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), cs);
-                if (ce == cudaSuccess && L.n_tiles > 0) ce = launch_advance(L);
-                cudaGraph_t graph = nullptr;
-                cudaError_t ce2 = cudaStreamEndCapture(cs, &graph);
-                if (ce != cudaSuccess || ce2 != cudaSuccess) {
-                    if (graph) cudaGraphDestroy(graph);
-                    return fail(c, LPM_E_CUDA, "capturing the batched segment failed: %s",
-                                cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
-                }
-                ce = cudaGraphInstantiate(&exec, graph, 0);
-                cudaGraphDestroy(graph);
-                if (ce != cudaSuccess)
-                    return fail(c, LPM_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ce));
-                c->graphs.push_back({k, e, exec});
-            }
-            if (e0) LPM_CUDA(c, cudaEventRecord(e0, c->stream));
-            LPM_CUDA(c, cudaGraphLaunch(exec, c->stream));
-            if (e1) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
-            c->n_launches++;
-            c->n_adv_launches++;
-        }
-        if (do_bin) c->n_bins++;
-        k = e;
+        LPM_CUDA(c, cudaGraphLaunch(gr->exec, c->stream));
+        if (e1) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
+        c->n_launches += gr->kernels;
+        c->n_adv_launches++;
+        c->sorted_upto = gr->upto1;
+        c->cur = gr->cur1;
     }
+    for (const Segment &sg : plan)
+        if (sg.do_bin) c->n_bins++;
     c->k = k_end;
     return LPM_OK;
 }
@@ -1016,12 +1170,14 @@ lpm_status lpm_budget(lpm_ctx *c, int scenario, double out[8])
     if (st != LPM_OK) return st;
     const size_t ns = (size_t)c->cfg.n_scenarios;
     for (int i : {(int)C_AIR_IN, (int)C_AIR_OUT, (int)C_N_ACTIVE})
-        LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + i * ns + scenario, 0, sizeof(unsigned long long),
+        LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + i * ns, 0, ns * sizeof(unsigned long long),
                                     c->stream));
     StepParams P;
     fill_params(c, P);
-    LPM_CUDA(c, launch_budget(c->stream, P, c->d_state, scenario, h.n, (int)c->k,
-                              c->n_sorted > 0 ? c->d_live : nullptr, c->n_sorted));
+    const bool sorted = c->sorted_upto > 0;
+    LPM_CUDA(c, launch_budget(c->stream, P, c->d_state, c->n_slots_used, c->d_slot_of,
+                              c->d_sorted[c->cur], c->d_pidx[c->cur], sorted ? c->d_live : nullptr,
+                              sorted ? released_total(c, c->sorted_upto) : 0, (int)c->k));
     c->n_launches++;
     st = check_device_error(c);
     if (st != LPM_OK) return st;
@@ -1059,14 +1215,16 @@ lpm_status lpm_particles(lpm_ctx *c, int64_t first, int64_t count, float *xyz, u
     if (st != LPM_OK) return st;
     if (count == 0) return LPM_OK;
     std::vector<float4> h((size_t)count);
-    if (c->n_sorted > 0) {
-        // particle order: gather through the inverse permutation into the spare buffer,
-        // particle p at its index p (the spare buffer's unreleased tail stays valid)
-        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_slot_of, c->d_grave, c->n_sorted,
-                                  first, count, c->d_state2 + first));
-        LPM_CUDA(c, cudaMemcpyAsync(h.data(), c->d_state2 + first, h.size() * sizeof(float4),
+    if (c->d_sorted[0]) {
+        // slot order: gather from the home slots, the sorted set and the dead array into
+        // the spare sorted buffer (free until the next sort)
+        float4 *tmp = c->d_sorted[1 - c->cur];
+        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_sorted[c->cur], c->d_slot_of,
+                                  c->d_grave, first, count, tmp));
+        LPM_CUDA(c, cudaMemcpyAsync(h.data(), tmp, h.size() * sizeof(float4),
                                     cudaMemcpyDeviceToHost, c->stream));
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->n_launches++;
     } else {
         LPM_CUDA(c, cudaMemcpy(h.data(), c->d_state + first, h.size() * sizeof(float4),
                                cudaMemcpyDeviceToHost));
@@ -1116,7 +1274,13 @@ lpm_status lpm_set_sort(lpm_ctx *c, int every_steps)
 {
     if (!c) return LPM_E_INVALID;
     if (every_steps < 0) return fail(c, LPM_E_INVALID, "every_steps must be >= 0");
+    if (every_steps == c->sort_every) return LPM_OK;
+    // the sort points move: every particle returns home, the next sort starts afresh
+    lpm_status st = clear_sort_state(c, true);
+    if (st != LPM_OK) return st;
     c->sort_every = every_steps;
+    c->tiles_valid = false;
+    drop_graphs(c);
     return LPM_OK;
 }
 
@@ -1356,12 +1520,14 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     char *o = static_cast<char *>(buf);
     std::memcpy(o, &h, sizeof h);
     o += sizeof h;
-    // particles in index order (the sorted layout is not part of the state)
+    // particles in slot order (the sorted layout is not part of the state)
     const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
-    if (c->n_sorted > 0) {
-        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_slot_of, c->d_grave, c->n_sorted, 0,
-                                  c->n_slots_used, c->d_state2));
-        LPM_CUDA(c, cudaMemcpyAsync(o, c->d_state2, sb, cudaMemcpyDeviceToHost, c->stream));
+    if (c->d_sorted[0]) {
+        float4 *tmp = c->d_sorted[1 - c->cur];
+        LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_sorted[c->cur], c->d_slot_of,
+                                  c->d_grave, 0, c->n_slots_used, tmp));
+        LPM_CUDA(c, cudaMemcpyAsync(o, tmp, sb, cudaMemcpyDeviceToHost, c->stream));
+        c->n_launches++;
     } else {
         LPM_CUDA(c, cudaMemcpyAsync(o, c->d_state, sb, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -1397,8 +1563,6 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     if (st != LPM_OK) return st;
     const char *i = static_cast<const char *>(buf) + sizeof h;
     LPM_CUDA(c, cudaMemcpyAsync(c->d_state, i, sb, cudaMemcpyHostToDevice, c->stream));
-    if (c->d_state2)        // the spare buffer's unreleased tail must match (see ensure_sort_buffers)
-        LPM_CUDA(c, cudaMemcpyAsync(c->d_state2, i, sb, cudaMemcpyHostToDevice, c->stream));
     i += sb;
     LPM_CUDA(c, cudaMemcpyAsync(c->d_conc, i, ns * c->ncell() * 8, cudaMemcpyHostToDevice, c->stream));
     i += ns * c->ncell() * 8;
@@ -1406,15 +1570,11 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     i += ns * c->ndep() * 8;
     LPM_CUDA(c, cudaMemcpyAsync(c->d_ctr, i, ns * N_COUNTERS * 8, cudaMemcpyHostToDevice, c->stream));
     LPM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
-    if (c->d_live) {
-        LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
-        LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
-    }
+    st = clear_sort_state(c, false);     // every particle at its home slot
+    if (st != LPM_OK) return st;
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->k = h.k;
     c->n_bins = h.n_bins;
-    c->n_sorted = 0;
-    c->last_sort = h.k;
     return LPM_OK;
 }
 

@@ -86,8 +86,23 @@ struct StepParams {
     const ScenDev *scen;
     int n_scen;
     int ctr_stride;                  // counters are laid out [N_COUNTERS][n_scen]
+    const float2 *woff;              // [n_scen][n_t] wind offsets of every scenario, or nullptr
+    unsigned long long *conc_all;    // [n_scen][cz][cy][cx]
+    unsigned long long *ctr_all;     // [N_COUNTERS][n_scen]
     unsigned int *err;
 };
+
+// Scenario holding state slot `slot` (bisection over the scenarios' first slots).
+__device__ __forceinline__ int scen_of(const StepParams &P, long long slot)
+{
+    int lo = 0, hi = P.n_scen;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&P.scen[mid].first_slot) <= slot) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 // ---------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 multiplies with

@@ -1,6 +1,6 @@
-// lpm_kernels.cu - particle kernels: release, advance (the step of Sec. 3.2, fused over
-// many steps, with in-kernel deposition and end-of-segment binning) and the budget
-// reduction.
+// lpm_kernels.cu - particle kernels around the step: release, weather time pairing, the
+// budget reduction, the generator check, and the advance dispatch over the instantiations
+// (lpm_advance_b*.cu).
 #include "lpm_device.cuh"
 #include "lpm_launch.h"
 #include "lpm_advance.cuh"
@@ -33,13 +33,7 @@ __global__ void release_all_kernel(const StepParams P, float4 *__restrict__ stat
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x; slot < n_slots;
          slot += stride) {
-        int lo = 0, hi = P.n_scen;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (P.scen[mid].first_slot <= slot) lo = mid;
-            else hi = mid;
-        }
-        const ScenDev sc = P.scen[lo];
+        const ScenDev sc = P.scen[scen_of(P, slot)];
         const long long i = slot - sc.first_slot;
         if (i < 0 || i >= sc.n) continue;
         const long long pr = sc.part_first + i;
@@ -67,40 +61,59 @@ __global__ void pack_kernel(const float4 *__restrict__ a, const float4 *__restri
 }
 
 // ---------------------------------------------------------------------------------
-// Budget: decayed mass of every active particle of a scenario at the current time,
-// split into inside/outside the concentration grid, plus the active count.
+// Budget: decayed mass of every active particle at the current time, split into
+// inside/outside the concentration grid, plus the active count, for every scenario at
+// once. Visits the sorted live particles [0, live) and the particles at their home slots.
 // ---------------------------------------------------------------------------------
-__global__ void budget_kernel(const StepParams P, const float4 *__restrict__ state, int scen,
-                              int k_now, const unsigned int *live, long long hole_end)
+constexpr int BUDGET_BLOCK = 256;
+
+__global__ void __launch_bounds__(BUDGET_BLOCK)
+budget_kernel(const StepParams P, const float4 *__restrict__ home, long long n_home,
+              const unsigned int *__restrict__ slot_of, const float4 *__restrict__ sorted,
+              const unsigned int *__restrict__ pidx, const unsigned int *live, int k_now)
 {
-    const ScenDev sc = P.scen[scen];
-    // slots [live, hole_end) are unused after a sort (their particles moved elsewhere)
-    const long long hole_lo = live ? (long long)*live : 0, hole_hi = live ? hole_end : 0;
-    unsigned long long in = 0, out = 0, cnt = 0;
+    __shared__ unsigned long long s_acc[BUDGET_BLOCK];
+    unsigned long long *s_warp = s_acc + (threadIdx.x & ~31);
+    const long long n_a = live ? (long long)*live : 0;
+    const long long n = n_a + n_home;
+    const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < sc.n; p += stride) {
-        if (p >= hole_lo && p < hole_hi) continue;
-        const float4 s = state[sc.first_slot + p];
-        const uint32_t tag = __float_as_uint(s.w);
-        if ((tag >> TAG_SHIFT) != ST_ACTIVE) continue;
-        const int sp = (int)(tag & TAG_STEP);
-        const unsigned long long v = to_fixed(mass_at(P, sc, sp, k_now - 1), sc.scale);
-        const int ix = (int)floorf((s.x - P.cx0) * P.inv_cdx);
-        const int iy = (int)floorf((s.y - P.cy0) * P.inv_cdy);
-        const int iz = (int)floorf((s.z - P.cz0) * P.inv_cdz);
-        if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz) in += v;
-        else out += v;
-        ++cnt;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        in += __shfl_xor_sync(0xffffffffu, in, o);
-        out += __shfl_xor_sync(0xffffffffu, out, o);
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (in) atomicAdd(sc.ctr + C_AIR_IN * P.ctr_stride, in);
-        if (out) atomicAdd(sc.ctr + C_AIR_OUT * P.ctr_stride, out);
-        if (cnt) atomicAdd(sc.ctr + C_N_ACTIVE * P.ctr_stride, cnt);
+    // the whole warp walks the particles together (match_any needs every lane)
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += stride) {
+        const long long i = base + lane;
+        int scen = -1;
+        unsigned long long in = 0, out = 0, cnt = 0;
+        if (i < n) {
+            float4 st = make_float4(0.f, 0.f, 0.f, 0.f);
+            long long h;
+            bool here;
+            if (i < n_a) {
+                st = sorted[i];
+                h = pidx[i];
+                here = true;
+            } else {
+                h = i - n_a;
+                here = !slot_of || slot_of[h] == SLOT_HOME;
+                if (here) st = home[h];
+            }
+            const uint32_t tag = __float_as_uint(st.w);
+            if (here && (tag >> TAG_SHIFT) == ST_ACTIVE) {
+                scen = P.n_scen > 1 ? scen_of(P, h) : 0;
+                const ScenDev &q = P.scen[scen];
+                const unsigned long long v =
+                    to_fixed(mass_at(P, q, (int)(tag & TAG_STEP), k_now - 1), __ldg(&q.scale));
+                const int ix = (int)floorf((st.x - P.cx0) * P.inv_cdx);
+                const int iy = (int)floorf((st.y - P.cy0) * P.inv_cdy);
+                const int iz = (int)floorf((st.z - P.cz0) * P.inv_cdz);
+                if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz) in = v;
+                else out = v;
+                cnt = 1;
+            }
+        }
+        warp_count_scen(scen, in, C_AIR_IN, P, s_warp);
+        warp_count_scen(scen, out, C_AIR_OUT, P, s_warp);
+        warp_count_scen(scen, cnt, C_N_ACTIVE, P, s_warp);
     }
 }
 
@@ -161,12 +174,12 @@ cudaError_t launch_advance(const AdvanceLaunch &L)
     return cudaErrorInvalidValue;
 }
 
-int advance_occupancy(int block, int ppt, int occ)
+int advance_occupancy(int block, int ppt, int occ, bool mixed)
 {
     switch (block) {
-    case 128: return occupancy_b128(ppt, occ);
-    case 256: return occupancy_b256(ppt, occ);
-    case 512: return occupancy_b512(ppt, occ);
+    case 128: return occupancy_b128(ppt, occ, mixed);
+    case 256: return occupancy_b256(ppt, occ, mixed);
+    case 512: return occupancy_b512(ppt, occ, mixed);
     }
     return 0;
 }
@@ -193,14 +206,16 @@ cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned
     return cudaGetLastError();
 }
 
-cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *state, int scen,
-                          long long n, int k_now, const unsigned int *live, long long hole_end)
+cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *home, long long n_home,
+                          const unsigned int *slot_of, const float4 *sorted,
+                          const unsigned int *pidx, const unsigned int *live, long long a_bound,
+                          int k_now)
 {
-    const int block = 256;
-    long long blocks = (n + block - 1) / block;
+    long long blocks = (n_home + a_bound + BUDGET_BLOCK - 1) / BUDGET_BLOCK;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    budget_kernel<<<(unsigned)blocks, block, 0, s>>>(P, state, scen, k_now, live, hole_end);
+    budget_kernel<<<(unsigned)blocks, BUDGET_BLOCK, 0, s>>>(P, home, n_home, slot_of, sorted, pidx,
+                                                            live, k_now);
     return cudaGetLastError();
 }
 

@@ -5,57 +5,86 @@
 
 namespace lpm {
 
-// Particle ranges of a plain-form launch: A = the sorted prefix [0, live) (live count on
-// the device when sorting is on; particle index of slot s in pidx[s]), B = the unsorted
-// tail [b_base, b_base + b_n) (slot order = particle order).
-struct PlainRanges {
-    long long a_cap;              // upper bound of the sorted live count (sizes the grid)
-    const unsigned int *a_live;   // device live count, or nullptr (then a_cap is exact)
-    const unsigned int *pidx;     // [a_cap] particle index per sorted slot, or nullptr
-    long long b_base, b_n;
-    int tiles_a;
+// The particles of an advance launch. A = the sorted live particles [0, live) of state_a
+// (live count on the device; home slot of sorted slot i in pidx[i]; any scenario);
+// B = tiles [b_first, b_first + n_b) of the tile table, each a run of one scenario's
+// particles at their home slots in state_b. Launch tile t < tiles_a is slots
+// [t*T, t*T + T) of A, tile tiles_a + u is B tile b_first + u.
+struct Ranges {
+    float4 *state_a;
+    const unsigned int *a_live;
+    const unsigned int *pidx;
+    int tiles_a;                  // tiles covering an upper bound of the live count
+    float4 *state_b;
+    const Tile *b_tiles;
+    int b_first, n_b;
 };
 
 struct AdvanceLaunch {
     cudaStream_t stream;
     const StepParams *params;
-    float4 *state;
-    const Tile *tiles;        // nullptr: implicit tiles of scenario 0
-    int n_tiles;
-    unsigned int *queue;      // work-queue counter (zeroed before the launch)
-    PlainRanges ranges;       // implicit tiles (plain form)
+    Ranges ranges;
+    unsigned int *queue;      // work-queue counter (zeroed before the launch), or nullptr:
+                              // then block b takes tiles b, b + grid, ...
     int k0, k1, do_bin;
     int block, ppt, occ;
+    bool mixed;               // lanes of one tile may belong to different scenarios
     unsigned int grid;
+    int n_tiles() const { return ranges.tiles_a + ranges.n_b; }
 };
+
+// Inputs of a sort: the live sorted particles of state_a (when has_a) followed by the B
+// tiles [b_first, b_first + n_b) of the table at their home slots in state_b, T lanes each.
+struct SortSource {
+    const float4 *state_a;
+    const unsigned int *pidx_a;
+    bool has_a;
+    long long a_bound;            // upper bound of the live count
+    const float4 *state_b;
+    const Tile *tiles;
+    int b_first, n_b, T;
+};
+
+struct SortBuffers {
+    float4 *state_out;
+    unsigned int *pidx_out;
+    unsigned int *slot_of;        // per home slot: sorted slot, GRAVE | index, or SLOT_HOME
+    unsigned int *keys, *hist, *block_sums, *meta;
+    float4 *grave;
+    unsigned int *grave_count;
+};
+
+constexpr unsigned int SLOT_HOME = 0xffffffffu;   // slot_of: the particle is at its home slot
+constexpr unsigned int SLOT_GRAVE = 0x80000000u;  // slot_of flag: index into the dead array
 
 cudaError_t launch_release(cudaStream_t s, float4 *state, long long first_slot, long long count,
                            long long part_first, long long n_total, int rel_first, int rel_len,
                            float sx, float sy, float sz);
 cudaError_t launch_release_all(cudaStream_t s, const StepParams &P, float4 *state, long long n_slots);
 cudaError_t launch_advance(const AdvanceLaunch &L);
-int advance_occupancy(int block, int ppt, int occ);
+int advance_occupancy(int block, int ppt, int occ, bool mixed);
 cudaError_t launch_advance_b128(const AdvanceLaunch &L);
 cudaError_t launch_advance_b256(const AdvanceLaunch &L);
 cudaError_t launch_advance_b512(const AdvanceLaunch &L);
-int occupancy_b128(int ppt, int occ);
-int occupancy_b256(int ppt, int occ);
-int occupancy_b512(int ppt, int occ);
+int occupancy_b128(int ppt, int occ, bool mixed);
+int occupancy_b256(int ppt, int occ, bool mixed);
+int occupancy_b512(int ppt, int occ, bool mixed);
 cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
                         const float *kb, float4 *pair, float2 *khpair, long long nodes);
-cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const float4 *state_in,
-                        const unsigned int *pidx_in, long long n_sorted_old, long long n_pre,
-                        float4 *state_out, unsigned int *pidx_out, unsigned int *slot_of,
-                        unsigned int *keys, unsigned int *hist, unsigned int *block_sums,
-                        unsigned int *meta, float4 *grave, unsigned int *grave_count);
-cudaError_t launch_gather(cudaStream_t s, const float4 *state, const unsigned int *slot_of,
-                          const float4 *grave, long long n_sorted, long long first,
+cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &in,
+                        const SortBuffers &out);
+cudaError_t launch_gather(cudaStream_t s, const float4 *home, const float4 *sorted,
+                          const unsigned int *slot_of, const float4 *grave, long long first,
                           long long count, float4 *out);
+cudaError_t launch_unsort(cudaStream_t s, float4 *home, const float4 *sorted,
+                          unsigned int *slot_of, const float4 *grave, long long n);
 cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned long long *pid,
                          const unsigned int *step, unsigned int stream, long long n, uint4 *words,
                          float *nrm);
-cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *state, int scen,
-                          long long n, int k_now, const unsigned int *live, long long hole_end);
+cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *home, long long n_home,
+                          const unsigned int *slot_of, const float4 *sorted,
+                          const unsigned int *pidx, const unsigned int *live, long long a_bound,
+                          int k_now);
 
 void set_global_error(const char *msg);
 

@@ -4,10 +4,11 @@
 // hour the 32 lanes of a warp gather weather from 32 unrelated places. Sorting the
 // released particles by the cell they sit in puts neighbours into the same warp: their
 // gathers share cache lines. The order of particles in memory has no effect on any
-// result (each particle keeps its index, hence its random numbers; the grids are integer
+// result (each particle keeps its id, hence its random numbers; the grids are integer
 // sums), so the sort is a pure layout change. A sort takes the live sorted particles and
-// the particles released since the previous sort; particles found deposited or exited
-// move once to an append-only array kept only for read-back.
+// the particles released since the previous sort (still at their home slots) and writes
+// the live ones, ordered by cell, into the other sorted buffer; particles found deposited
+// or exited move once to an append-only array kept only for read-back.
 #include "lpm_advance.cuh"
 
 namespace lpm {
@@ -17,29 +18,42 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
-constexpr unsigned int GRAVE = 0x80000000u;   // slot_of flag: index into the dead-particle array
-
 // meta[0] live count after the last sort, meta[1] input size of this sort, meta[2] the
-// live count before it. Input i maps to slot i (i < live before) or to the newly
-// released slot n_sorted_old + (i - live before).
-__global__ void sort_begin_kernel(unsigned int *meta, long long n_sorted_old, long long n_pre)
+// live count before it (the number of inputs taken from the sorted buffer).
+__global__ void sort_begin_kernel(unsigned int *meta, int has_a, long long n_b_inputs)
 {
-    const unsigned int live_old = n_sorted_old > 0 ? meta[0] : 0u;
+    const unsigned int live_old = has_a ? meta[0] : 0u;
     meta[2] = live_old;
-    meta[1] = live_old + (unsigned int)(n_pre - n_sorted_old);
+    meta[1] = live_old + (unsigned int)n_b_inputs;
 }
 
-__device__ __forceinline__ long long input_slot(long long i, unsigned int live_old,
-                                                long long n_sorted_old)
+// Input i of a sort: sorted slot i of state_a (i < live_old), else lane (i - live_old) % T
+// of B tile (i - live_old) / T at its home slot. False for the empty lanes of a B tile.
+__device__ __forceinline__ bool sort_input(const SortSource &S, long long i, unsigned int live_old,
+                                           const float4 *&src, long long &slot, unsigned int &home)
 {
-    return i < (long long)live_old ? i : n_sorted_old + (i - (long long)live_old);
+    if (i < (long long)live_old) {
+        src = S.state_a;
+        slot = i;
+        home = S.pidx_a[i];
+        return true;
+    }
+    const long long j = i - (long long)live_old;
+    const long long u = j / S.T;
+    const int lane = (int)(j - u * S.T);
+    const Tile t = S.tiles[S.b_first + u];
+    if (lane >= t.count) return false;
+    src = S.state_b;
+    slot = t.first + lane;
+    home = (unsigned int)slot;
+    return true;
 }
 
 // Key = weather cell (level, row, column) of an active particle; dead_key for the rest.
-__global__ void sort_keys_kernel(const StepParams P, const float4 *__restrict__ state,
-                                 const unsigned int *__restrict__ meta, long long n_sorted_old,
-                                 long long n_max, unsigned int *__restrict__ keys,
-                                 unsigned int *__restrict__ hist, unsigned int dead_key)
+__global__ void sort_keys_kernel(const StepParams P, const SortSource S,
+                                 const unsigned int *__restrict__ meta, long long n_max,
+                                 unsigned int *__restrict__ keys, unsigned int *__restrict__ hist,
+                                 unsigned int dead_key)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
@@ -55,16 +69,21 @@ __global__ void sort_keys_kernel(const StepParams P, const float4 *__restrict__ 
         const long long i = base + lane;
         unsigned int key = KEY_NONE_U;
         if (i < n && i < n_max) {
-            const float4 s = state[input_slot(i, live_old, n_sorted_old)];
-            if ((__float_as_uint(s.w) >> TAG_SHIFT) == ST_ACTIVE) {
-                int ix, jy, kz;
-                float a, b, c;
-                axis(s.x, P.x0, P.inv_dx, P.nx, ix, a);
-                axis(s.y, P.y0, P.inv_dy, P.ny, jy, b);
-                level(LV, s.z, kz, c);
-                key = ((unsigned int)kz * P.ny + jy) * P.nx + ix;
-            } else {
-                key = dead_key;
+            const float4 *src;
+            long long slot;
+            unsigned int home;
+            if (sort_input(S, i, live_old, src, slot, home)) {
+                const float4 s = src[slot];
+                if ((__float_as_uint(s.w) >> TAG_SHIFT) == ST_ACTIVE) {
+                    int ix, jy, kz;
+                    float a, b, c;
+                    axis(s.x, P.x0, P.inv_dx, P.nx, ix, a);
+                    axis(s.y, P.y0, P.inv_dy, P.ny, jy, b);
+                    level(LV, s.z, kz, c);
+                    key = ((unsigned int)kz * P.ny + jy) * P.nx + ix;
+                } else {
+                    key = dead_key;
+                }
             }
             keys[i] = key;
         }
@@ -73,9 +92,10 @@ __global__ void sort_keys_kernel(const StepParams P, const float4 *__restrict__ 
     }
 }
 
+// After the exclusive scan, the offset of the dead key is the number of live inputs.
 __global__ void live_count_kernel(const unsigned int *hist, unsigned int dead_key, unsigned int *meta)
 {
-    meta[0] = meta[1] - hist[dead_key];
+    meta[0] = hist[dead_key];
 }
 
 // Exclusive scan of data[0, nb): per-tile scan, scan of the tile sums, add-back.
@@ -152,14 +172,10 @@ scan_add_kernel(unsigned int *data, long long nb, const unsigned int *tile_sums)
 
 // Scatter: live particles to their sorted places (one atomic per group of lanes with the
 // same key), dead ones appended to the dead-particle array.
-__global__ void sort_scatter_kernel(const float4 *__restrict__ state_in,
-                                    const unsigned int *__restrict__ pidx_in,
-                                    const unsigned int *__restrict__ meta, long long n_sorted_old,
+__global__ void sort_scatter_kernel(const SortSource S, const unsigned int *__restrict__ meta,
                                     long long n_max, const unsigned int *__restrict__ keys,
                                     unsigned int dead_key, unsigned int *__restrict__ offsets,
-                                    float4 *__restrict__ state_out, unsigned int *__restrict__ pidx_out,
-                                    unsigned int *__restrict__ slot_of, float4 *__restrict__ grave,
-                                    unsigned int *__restrict__ grave_count)
+                                    const SortBuffers B)
 {
     const long long n = meta[1];
     const unsigned int live_old = meta[2];
@@ -168,43 +184,62 @@ __global__ void sort_scatter_kernel(const float4 *__restrict__ state_in,
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
          base += stride) {
         const long long i = base + lane;
-        const bool valid = i < n && i < n_max;
-        const unsigned int key = valid ? keys[i] : KEY_NONE_U;
+        const unsigned int key = (i < n && i < n_max) ? keys[i] : KEY_NONE_U;
         const unsigned int peers = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(peers) - 1;
         unsigned int first = 0u;
         if (key != KEY_NONE_U && lane == leader)
-            first = atomicAdd(key == dead_key ? grave_count : offsets + key, __popc(peers));
+            first = atomicAdd(key == dead_key ? B.grave_count : offsets + key, __popc(peers));
         first = __shfl_sync(0xffffffffu, first, leader);
-        if (valid) {
-            const long long slot = input_slot(i, live_old, n_sorted_old);
+        if (key != KEY_NONE_U) {
+            const float4 *src;
+            long long slot;
+            unsigned int home;
+            sort_input(S, i, live_old, src, slot, home);
             const unsigned int dst = first + __popc(peers & ((1u << lane) - 1u));
-            const unsigned int p = i < (long long)live_old ? pidx_in[slot] : (unsigned int)slot;
             if (key == dead_key) {
-                grave[dst] = state_in[slot];
-                slot_of[p] = GRAVE | dst;
+                B.grave[dst] = src[slot];
+                B.slot_of[home] = SLOT_GRAVE | dst;
             } else {
-                state_out[dst] = state_in[slot];
-                pidx_out[dst] = p;
-                slot_of[p] = dst;
+                B.state_out[dst] = src[slot];
+                B.pidx_out[dst] = home;
+                B.slot_of[home] = dst;
             }
         }
     }
 }
 
-__global__ void gather_kernel(const float4 *__restrict__ state, const unsigned int *__restrict__ slot_of,
-                              const float4 *__restrict__ grave, long long n_sorted, long long first,
-                              long long count, float4 *__restrict__ out)
+__device__ __forceinline__ float4 locate(const float4 *home, const float4 *sorted,
+                                         const unsigned int *slot_of, const float4 *grave,
+                                         long long p)
+{
+    const unsigned int s = slot_of ? slot_of[p] : SLOT_HOME;
+    if (s == SLOT_HOME) return home[p];
+    return (s & SLOT_GRAVE) ? grave[s & ~SLOT_GRAVE] : sorted[s];
+}
+
+// Particles [first, first + count) in home order, wherever they are.
+__global__ void gather_kernel(const float4 *__restrict__ home, const float4 *__restrict__ sorted,
+                              const unsigned int *__restrict__ slot_of,
+                              const float4 *__restrict__ grave, long long first, long long count,
+                              float4 *__restrict__ out)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-        const long long p = first + i;
-        if (p < n_sorted) {
-            const unsigned int s = slot_of[p];
-            out[i] = (s & GRAVE) ? grave[s & ~GRAVE] : state[s];
-        } else {
-            out[i] = state[p];
-        }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        out[i] = locate(home, sorted, slot_of, grave, first + i);
+}
+
+// Every particle back to its home slot (the sorted set becomes empty).
+__global__ void unsort_kernel(float4 *__restrict__ home, const float4 *__restrict__ sorted,
+                              unsigned int *__restrict__ slot_of, const float4 *__restrict__ grave,
+                              long long n)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const unsigned int s = slot_of[p];
+        if (s == SLOT_HOME) continue;
+        home[p] = (s & SLOT_GRAVE) ? grave[s & ~SLOT_GRAVE] : sorted[s];
+        slot_of[p] = SLOT_HOME;
     }
 }
 
@@ -215,41 +250,47 @@ static unsigned int grid_for(long long n, int block)
     return (unsigned int)(g < 1 ? 1 : g);
 }
 
-cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const float4 *state_in,
-                        const unsigned int *pidx_in, long long n_sorted_old, long long n_pre,
-                        float4 *state_out, unsigned int *pidx_out, unsigned int *slot_of,
-                        unsigned int *keys, unsigned int *hist, unsigned int *block_sums,
-                        unsigned int *meta, float4 *grave, unsigned int *grave_count)
+cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &in,
+                        const SortBuffers &B)
 {
+    // keys 0..dead_key-1 are cells, dead_key the dead particles
     const unsigned int dead_key = (unsigned int)((long long)P.nx * P.ny * P.nz);
     const long long nb = (long long)dead_key + 1;
-    cudaError_t e = cudaMemsetAsync(hist, 0, nb * sizeof(unsigned int), s);
+    cudaError_t e = cudaMemsetAsync(B.hist, 0, nb * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    sort_begin_kernel<<<1, 1, 0, s>>>(meta, n_sorted_old, n_pre);
-    const long long n_max = n_pre;                  // bound of the input size (sizes the grids)
+    const long long n_b_inputs = (long long)in.n_b * in.T;
+    sort_begin_kernel<<<1, 1, 0, s>>>(B.meta, in.has_a ? 1 : 0, n_b_inputs);
+    const long long n_max = (in.has_a ? in.a_bound : 0) + n_b_inputs;   // bound of the input size
     if (n_max > 0)
-        sort_keys_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(P, state_in, meta, n_sorted_old, n_max,
-                                                              keys, hist, dead_key);
-    live_count_kernel<<<1, 1, 0, s>>>(hist, dead_key, meta);
+        sort_keys_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(P, in, B.meta, n_max, B.keys, B.hist,
+                                                              dead_key);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (n_max == 0) return cudaSuccess;
     const int n_tiles = (int)((nb + SCAN_TILE - 1) / SCAN_TILE);
-    scan_tiles_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(hist, nb, block_sums);
-    scan_sums_kernel<<<1, 1024, 0, s>>>(block_sums, n_tiles);
-    scan_add_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(hist, nb, block_sums);
-    sort_scatter_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(state_in, pidx_in, meta, n_sorted_old,
-                                                             n_max, keys, dead_key, hist, state_out,
-                                                             pidx_out, slot_of, grave, grave_count);
+    scan_tiles_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(B.hist, nb, B.block_sums);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(B.block_sums, n_tiles);
+    scan_add_kernel<<<n_tiles, SCAN_THREADS, 0, s>>>(B.hist, nb, B.block_sums);
+    live_count_kernel<<<1, 1, 0, s>>>(B.hist, dead_key, B.meta);
+    if (n_max > 0)
+        sort_scatter_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(in, B.meta, n_max, B.keys,
+                                                                 dead_key, B.hist, B);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(cudaStream_t s, const float4 *state, const unsigned int *slot_of,
-                          const float4 *grave, long long n_sorted, long long first,
+cudaError_t launch_gather(cudaStream_t s, const float4 *home, const float4 *sorted,
+                          const unsigned int *slot_of, const float4 *grave, long long first,
                           long long count, float4 *out)
 {
     if (count <= 0) return cudaSuccess;
-    gather_kernel<<<grid_for(count, 256), 256, 0, s>>>(state, slot_of, grave, n_sorted, first,
-                                                       count, out);
+    gather_kernel<<<grid_for(count, 256), 256, 0, s>>>(home, sorted, slot_of, grave, first, count,
+                                                       out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsort(cudaStream_t s, float4 *home, const float4 *sorted,
+                          unsigned int *slot_of, const float4 *grave, long long n)
+{
+    if (n <= 0) return cudaSuccess;
+    unsort_kernel<<<grid_for(n, 256), 256, 0, s>>>(home, sorted, slot_of, grave, n);
     return cudaGetLastError();
 }
 

@@ -28,13 +28,17 @@ def small_ensemble():
     return li.make_cfg2(n_scenarios=6, n_steps=240, n_min=500, n_max=3000)
 
 
-def _run(cfg, launch=None, repeat=1):
+def _run(cfg, launch=None, repeat=1, sort_every=None, pieces=None):
     from paper_0912_3223_gb300 import Sim
     out = []
-    with Sim(cfg, launch=launch) as sim:
+    with Sim(cfg, launch=launch, sort_every=sort_every) as sim:
         for _ in range(repeat):
             sim.reset()
-            sim.step(cfg.n_steps)
+            if pieces:
+                for n in pieces:
+                    sim.step(n)
+            else:
+                sim.step(cfg.n_steps)
             xyz, tag = sim.particles()
             scen = []
             for s in range(cfg.n_scenarios):
@@ -120,3 +124,55 @@ def test_autotuner_keeps_results(small_ensemble, tmp_path, monkeypatch):
         again = autotune(sim)                        # served from the cache
         assert again == shape
     assert np.array_equal(xyz, ref[0]) and np.array_equal(tag, ref[1])
+
+
+def _same(a, b):
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for sa, sb in zip(a[2], b[2]):
+        assert np.array_equal(sa["conc_fixed"], sb["conc_fixed"])
+        assert np.array_equal(sa["dep_fixed"], sb["dep_fixed"])
+        assert np.array_equal(sa["counters"], sb["counters"])
+        assert np.array_equal(sa["budget"], sb["budget"])
+
+
+@pytest.mark.parametrize("every", [1, 37, 60])
+def test_sorting_mixes_scenarios_without_changing_results(small_ensemble, every):
+    """Sorting by cell puts particles of different scenarios into one warp (each lane with
+    its own scenario's wind offset, masses and grids): every bit stays the same."""
+    ref = _run(small_ensemble, sort_every=0)[0]
+    got = _run(small_ensemble, sort_every=every)[0]
+    _same(ref, got)
+
+
+def test_sorted_batched_in_pieces_and_replayed(small_ensemble):
+    ref = _run(small_ensemble, sort_every=0)[0]
+    a, b = _run(small_ensemble, sort_every=30, repeat=2, pieces=[45, 15, 100, 80])
+    _same(ref, a)
+    _same(ref, b)
+
+
+def test_sorted_batched_save_resume_and_resort(small_ensemble):
+    """Checkpoint in the middle of a sorted batched run, resume in a fresh context, and
+    change the sort interval on the way (the sorted set goes home first)."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = small_ensemble
+    ref = _run(cfg, sort_every=0)[0]
+    with Sim(cfg, sort_every=40) as sim:
+        sim.reset()
+        sim.step(100)
+        blob = lpm.lpm_save(sim.ctx)
+    with Sim(cfg, sort_every=25) as sim:
+        sim.reset()
+        lpm.lpm_load(sim.ctx, blob)
+        sim.step(50)
+        lpm.lpm_set_sort(sim.ctx, 0)
+        sim.step(30)
+        lpm.lpm_set_sort(sim.ctx, 20)
+        sim.step(cfg.n_steps - 180)
+        xyz, tag = sim.particles()
+        assert np.array_equal(xyz, ref[0]) and np.array_equal(tag, ref[1])
+        for s in range(cfg.n_scenarios):
+            c, d, k, _ = sim.fixed_state(s)
+            assert np.array_equal(c, ref[2][s]["conc_fixed"])
+            assert np.array_equal(d, ref[2][s]["dep_fixed"])
+            assert np.array_equal(sim.budget(s), ref[2][s]["budget"])

@@ -327,8 +327,13 @@ def test_allocation_failure_is_reported():
     """A context too large for the device fails cleanly with LPM_E_OOM."""
     from paper_0912_3223_gb300 import lpm
     cfg = li.make_cfg0(n_particles=10, n_steps=10)
+    # 32 scenarios of a 2e9-cell concentration grid: 512 GB of 64-bit counters
+    huge = dataclasses.replace(cfg, cx=2000, cy=2000, cz=500, n_scenarios=32)
     with pytest.raises(lpm.LpmError) as e:
-        lpm.lpm_create(cfg, max_particles=1 << 40)
+        lpm.lpm_create(huge)
     assert e.value.status == lpm.LPM_E_OOM
+    with pytest.raises(lpm.LpmError) as e:          # beyond the 31-bit slot indices
+        lpm.lpm_create(cfg, max_particles=1 << 40)
+    assert e.value.status == lpm.LPM_E_INVALID
     ctx = lpm.lpm_create(cfg)           # the device is still usable
     lpm.lpm_destroy(ctx)
