@@ -27,15 +27,14 @@ __device__ __forceinline__ void sample_met_grad(const StepParams &P, const Level
     const float gx = (fx >= 0.0f && fx <= (float)(P.nx - 1)) ? P.inv_dx : 0.0f;
     const float gy = (fy >= 0.0f && fy <= (float)(P.ny - 1)) ? P.inv_dy : 0.0f;
     const float gz = (z >= L.z[0] && z <= L.z[P.nz - 1]) ? L.inv[k] : 0.0f;
-    const int nx = P.nx, nxny = P.nx * P.ny;
-    const int n00 = (k * P.ny + j) * nx + i;
+    const int n00 = col_node(P, i, j, k);
     float4 q[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int off = (m & 1) + ((m >> 1) & 1) * nx + ((m >> 2) & 1) * nxny;
-        float4 lo, hi;
-        ld_pair(T.pair + 2 * (n00 + off), lo, hi);
-        q[m] = lerp4(lo, hi, T.ts.f);
+        const int off = corner_off(P, m);
+        float4 lo, dt;
+        ld_pair(T.pair + 2 * (n00 + off), lo, dt);
+        q[m] = tlerp4(lo, dt, T.ts.f);
     }
     const float4 x00 = lerp4(q[0], q[1], a), x10 = lerp4(q[2], q[3], a);
     const float4 x01 = lerp4(q[4], q[5], a), x11 = lerp4(q[6], q[7], a);
@@ -63,9 +62,9 @@ __device__ __forceinline__ void sample_met_grad(const StepParams &P, const Level
         float e[8];
 #pragma unroll
         for (int mm = 0; mm < 8; ++mm) {
-            const int off = (mm & 1) + ((mm >> 1) & 1) * nx + ((mm >> 2) & 1) * nxny;
+            const int off = corner_off(P, mm);
             const float2 v = __ldg(T.khp + n00 + off);
-            e[mm] = fmaf(T.ts.f, v.y - v.x, v.x);
+            e[mm] = fmaf(T.ts.f, v.y, v.x);
         }
         const float ex0 = fmaf(a, e[1] - e[0], e[0]), ex1 = fmaf(a, e[3] - e[2], e[2]);
         const float ex2 = fmaf(a, e[5] - e[4], e[4]), ex3 = fmaf(a, e[7] - e[6], e[6]);

@@ -91,7 +91,7 @@ __device__ __forceinline__ void warp_count_scen(int s, unsigned long long v, int
 }
 
 // Weather at a point from the time-paired records: 8 spatial corners, each one 32-byte
-// load of (slab h, slab h+1), blended in time, then in x, y and z.
+// load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z.
 __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels &L,
                                                const float4 *__restrict__ pair,
                                                const float2 *__restrict__ khp, float f,
@@ -102,15 +102,14 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
     axis(x, P.x0, P.inv_dx, P.nx, i, a);
     axis(y, P.y0, P.inv_dy, P.ny, j, b);
     level(L, z, k, c);
-    const int nx = P.nx, nxny = P.nx * P.ny;
-    const int n00 = (k * P.ny + j) * nx + i;
+    const int n00 = col_node(P, i, j, k);
     float4 q[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-        const int off = (m & 1) + ((m >> 1) & 1) * nx + ((m >> 2) & 1) * nxny;
-        float4 lo, hi;
-        ld_pair(pair + 2 * (n00 + off), lo, hi);
-        q[m] = lerp4(lo, hi, f);
+        const int off = corner_off(P, m);
+        float4 lo, dt;
+        ld_pair(pair + 2 * (n00 + off), lo, dt);
+        q[m] = tlerp4(lo, dt, f);
     }
     const float4 x00 = lerp4(q[0], q[1], a), x10 = lerp4(q[2], q[3], a);
     const float4 x01 = lerp4(q[4], q[5], a), x11 = lerp4(q[6], q[7], a);
@@ -127,9 +126,9 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
         float e[8];
 #pragma unroll
         for (int mm = 0; mm < 8; ++mm) {
-            const int off = (mm & 1) + ((mm >> 1) & 1) * nx + ((mm >> 2) & 1) * nxny;
+            const int off = corner_off(P, mm);
             const float2 v = __ldg(khp + n00 + off);
-            e[mm] = fmaf(f, v.y - v.x, v.x);
+            e[mm] = fmaf(f, v.y, v.x);
         }
         const float ex0 = fmaf(a, e[1] - e[0], e[0]), ex1 = fmaf(a, e[3] - e[2], e[2]);
         const float ex2 = fmaf(a, e[5] - e[4], e[4]), ex3 = fmaf(a, e[7] - e[6], e[6]);

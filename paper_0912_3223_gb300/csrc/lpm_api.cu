@@ -185,6 +185,8 @@ lpm_status validate(const lpm_config *c)
         return fail(nullptr, LPM_E_INVALID, "met grid needs at least 2 nodes per axis");
     if (c->nz > MAX_LEVELS)
         return fail(nullptr, LPM_E_INVALID, "nz=%d exceeds %d levels", c->nz, MAX_LEVELS);
+    if ((double)c->nx * c->ny * c->nz > 1073741824.0)
+        return fail(nullptr, LPM_E_INVALID, "met grid exceeds 2^30 nodes");
     if (!c->z_levels) return fail(nullptr, LPM_E_INVALID, "z_levels is NULL");
     for (int k = 0; k < c->nz; ++k) {
         if (!is_finite(c->z_levels[k])) return fail(nullptr, LPM_E_INVALID, "z_levels not finite");
@@ -643,14 +645,15 @@ lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
     CREATE_CUDA(cudaMemsetAsync(c->d_ctr, 0, ns * N_COUNTERS * sizeof(unsigned long long), c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
     {
-        // vertical lookup table: bins of at most half the smallest level spacing, in the
-        // FP32 arithmetic the kernel uses to pick a bin
+        // vertical lookup table: bins of at most a third of the smallest level spacing (the
+        // kernel then corrects the tabled cell by at most one), in the FP32 arithmetic the
+        // kernel uses to pick a bin
         std::vector<float> zf(cfg->nz);
         for (int k = 0; k < cfg->nz; ++k) zf[k] = (float)cfg->z_levels[k];
         double min_sp = 1e300;
         for (int k = 0; k + 1 < cfg->nz; ++k) min_sp = std::min(min_sp, (double)zf[k + 1] - zf[k]);
         const double span = (double)zf[cfg->nz - 1] - zf[0];
-        const double n_need = min_sp > 0 ? std::ceil(span / (0.5 * min_sp)) + 1 : 1e300;
+        const double n_need = min_sp > 0 ? std::ceil(span / (min_sp / 3.0)) + 1 : 1e300;
         if (n_need <= MAX_LUT) {
             c->n_lut = (int)n_need;
             c->lut_z0 = zf[0];
@@ -731,7 +734,7 @@ lpm_status lpm_set_met(lpm_ctx *c, int t_index, const float *uvwk, const float *
                                 c->d_kh ? c->d_kh + nodes * h : nullptr,
                                 c->d_kh ? c->d_kh + nodes * h1 : nullptr,
                                 c->d_pair + nodes * 2 * h, c->d_khpair ? c->d_khpair + nodes * h : nullptr,
-                                (long long)nodes));
+                                g.nx, g.ny, g.nz));
         c->n_launches++;
     }
     // host sources must be consumed before returning (the caller owns them)

@@ -58,9 +58,10 @@ struct Tile {
 };
 
 struct StepParams {
-    // weather, time-paired: pair[h][node] = (slab h, slab h+1) as two float4 (32 B aligned)
+    // weather, time-paired: pair[h][node] = (slab h, slab h+1 - slab h) as two float4
+    // (32 B aligned), nodes in slab order (see col_node)
     const float4 *pair;              // [n_pair][nz][ny][nx][2], n_pair = max(1, n_t - 1)
-    const float2 *khpair;            // [n_pair][nz][ny][nx] (K_h at h, h+1) or nullptr
+    const float2 *khpair;            // [n_pair][nz][ny][nx] (K_h at h, difference) or nullptr
     const uint8_t *rain;             // [n_t][ny][nx] or nullptr
     int nx, ny, nz, n_t;
     long long slab;                  // nodes per slab
@@ -91,6 +92,20 @@ struct StepParams {
     unsigned long long *ctr_all;     // [N_COUNTERS][n_scen]
     unsigned int *err;
 };
+
+// Node of the paired weather records, in the order of the slabs ([z][y][x]): the two
+// x-neighbours of a corner share a cache line. (Column order, z fastest, measured 6 %
+// slower on the realistic workload.)
+__device__ __forceinline__ int col_node(const StepParams &P, int i, int j, int k)
+{
+    return (k * P.ny + j) * P.nx + i;
+}
+
+// Offset of corner m (bit 0: x + 1, bit 1: y + 1, bit 2: z + 1) from corner 0.
+__device__ __forceinline__ int corner_off(const StepParams &P, int m)
+{
+    return (m & 1) + ((m >> 1) & 1) * P.nx + ((m >> 2) & 1) * P.nx * P.ny;
+}
 
 // Scenario holding state slot `slot` (bisection over the scenarios' first slots).
 __device__ __forceinline__ int scen_of(const StepParams &P, long long slot)
@@ -215,6 +230,10 @@ struct Levels {
     float z0, inv_h;
 };
 
+// Vertical cell k (last level <= z, clamped to [0, nz-2]) and fraction c in [0, 1]. The
+// table gives the cell at the lower edge of z's uniform bin (bins of at most a third of
+// the smallest level spacing); a level inside the bin, or bin arithmetic that rounded
+// across an edge, moves it by one.
 __device__ __forceinline__ void level(const Levels &L, float z, int &k, float &c)
 {
     int kk;
@@ -261,6 +280,12 @@ __device__ __forceinline__ Levels load_levels(const StepParams &P, float *s_z, f
 struct Met {
     float u, v, w, kz, kh, dkz;
 };
+
+// Time blend of a paired record: a + t * d with d the stored difference.
+__device__ __forceinline__ float4 tlerp4(const float4 a, const float4 d, float t)
+{
+    return make_float4(fmaf(t, d.x, a.x), fmaf(t, d.y, a.y), fmaf(t, d.z, a.z), fmaf(t, d.w, a.w));
+}
 
 __device__ __forceinline__ float4 lerp4(const float4 a, const float4 b, float t)
 {

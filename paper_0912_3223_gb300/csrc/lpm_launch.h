@@ -70,7 +70,7 @@ int occupancy_b128(int ppt, int occ, bool mixed);
 int occupancy_b256(int ppt, int occ, bool mixed);
 int occupancy_b512(int ppt, int occ, bool mixed);
 cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
-                        const float *kb, float4 *pair, float2 *khpair, long long nodes);
+                        const float *kb, float4 *pair, float2 *khpair, int nx, int ny, int nz);
 cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &in,
                         const SortBuffers &out);
 cudaError_t launch_gather(cudaStream_t s, const float4 *home, const float4 *sorted,

@@ -49,7 +49,8 @@ __device__ __forceinline__ bool sort_input(const SortSource &S, long long i, uns
     return true;
 }
 
-// Key = weather cell (level, row, column) of an active particle; dead_key for the rest.
+// Key = weather cell (in the order of the paired weather records) of an active particle;
+// dead_key for the rest.
 __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                                  const unsigned int *__restrict__ meta, long long n_max,
                                  unsigned int *__restrict__ keys, unsigned int *__restrict__ hist,
@@ -80,7 +81,7 @@ __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                     axis(s.x, P.x0, P.inv_dx, P.nx, ix, a);
                     axis(s.y, P.y0, P.inv_dy, P.ny, jy, b);
                     level(LV, s.z, kz, c);
-                    key = ((unsigned int)kz * P.ny + jy) * P.nx + ix;
+                    key = (unsigned int)col_node(P, ix, jy, kz);
                 } else {
                     key = dead_key;
                 }
