@@ -55,6 +55,7 @@ class OCfg(C.Structure):
         ("q_dt", C.c_double), ("first_step", C.c_int64), ("last_step", C.c_int64),
         ("pid_offset", C.c_int64),
         ("k_scale", C.c_double), ("bias_u", C.c_double), ("bias_v", C.c_double),
+        ("dose_every", C.c_int),
     ]
 
 
@@ -65,6 +66,8 @@ class OOut(C.Structure):
         ("conc", C.POINTER(C.c_double)), ("conc_fixed", C.POINTER(C.c_int64)),
         ("dep", C.POINTER(C.c_double)), ("dep_fixed", C.POINTER(C.c_int64)),
         ("budget", C.POINTER(C.c_double)), ("counters", C.POINTER(C.c_int64)),
+        ("dose", C.POINTER(C.c_double)), ("dose_fixed", C.POINTER(C.c_int64)),
+        ("dose_ctr", C.POINTER(C.c_int64)),
     ]
 
 
@@ -133,10 +136,11 @@ class _Pinned:
 
 
 def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
-              bias=(0.0, 0.0), src=None, q=None):
+              bias=(0.0, 0.0), src=None, q=None, dose_every: int = 0):
     """Build the C record for one release of ``cfg`` (an ``lpm_inputs.LpmConfig``).
     ``scenario`` selects a member of a batched ensemble (its source, release, global id
-    offset and wind offset). ``src``/``q`` override the source and emission series."""
+    offset and wind offset). ``src``/``q`` override the source and emission series;
+    ``dose_every`` > 0 samples the time-integrated dosage every that many steps."""
     pin = _Pinned()
     o = OCfg()
     for name in ("nx", "ny", "nz", "n_met_t", "cx", "cy", "cz", "bin_every",
@@ -174,6 +178,7 @@ def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
     o.pid_offset = offset
     o.k_scale = float(k_scale)
     o.bias_u, o.bias_v = float(bias[0]), float(bias[1])
+    o.dose_every = int(dose_every)
     o._pin = pin  # keep arrays alive with the record
     return o
 
@@ -251,7 +256,9 @@ def run(cfg, sel=None, n_run: Optional[int] = None, **kw) -> dict:
     """Run the oracle for steps [0, n_run) on the particles ``sel`` (local indices of the
     release; None = all). Returns positions, status, release steps, decision margins,
     the last concentration snapshot (FP64 and fixed point), the deposition grids, the
-    budget and the fixed-point counters."""
+    budget and the fixed-point counters; with ``dose_every`` the dosage sums (dose,
+    dose_fixed: summed mass per cell over the samples; dose_out: fixed-point mass outside
+    the grid; dose_samples)."""
     o = make_ocfg(cfg, **kw)
     if n_run is None:
         n_run = int(cfg.n_steps)
@@ -266,17 +273,23 @@ def run(cfg, sel=None, n_run: Optional[int] = None, **kw) -> dict:
         margin=np.zeros(n), conc=np.zeros((cfg.cz, cfg.cy, cfg.cx)),
         conc_fixed=np.zeros((cfg.cz, cfg.cy, cfg.cx), np.int64),
         dep=np.zeros((2, cfg.cy, cfg.cx)), dep_fixed=np.zeros((2, cfg.cy, cfg.cx), np.int64),
-        budget=np.zeros(8), counters=np.zeros(6, np.int64))
+        budget=np.zeros(8), counters=np.zeros(6, np.int64),
+        dose=np.zeros((cfg.cz, cfg.cy, cfg.cx)),
+        dose_fixed=np.zeros((cfg.cz, cfg.cy, cfg.cx), np.int64), dose_ctr=np.zeros(2, np.int64))
     oo = OOut(_ptr(out["pos"], C.c_double), _ptr(out["status"], C.c_int32),
               _ptr(out["release"], C.c_int64), _ptr(out["margin"], C.c_double),
               _ptr(out["conc"], C.c_double), _ptr(out["conc_fixed"], C.c_int64),
               _ptr(out["dep"], C.c_double), _ptr(out["dep_fixed"], C.c_int64),
-              _ptr(out["budget"], C.c_double), _ptr(out["counters"], C.c_int64))
+              _ptr(out["budget"], C.c_double), _ptr(out["counters"], C.c_int64),
+              _ptr(out["dose"], C.c_double), _ptr(out["dose_fixed"], C.c_int64),
+              _ptr(out["dose_ctr"], C.c_int64))
     assert ncell == out["conc"].size
     rc = lib().oracle_run(C.byref(o), _ptr(sel, C.c_int64), n, int(n_run), C.byref(oo))
     if rc != 0:
         raise ValueError(f"oracle_run rejected the configuration (code {rc})")
     out["active_steps"] = int(out["counters"][4])
+    out["dose_out"] = int(out["dose_ctr"][0])
+    out["dose_samples"] = int(out["dose_ctr"][1])
     return out
 
 

@@ -131,6 +131,8 @@ typedef struct {
     int64_t pid_offset;              /* global id of this release's particle 0 */
     /* differentiable parameters of the adjoint form: K scale and wind bias */
     double k_scale, bias_u, bias_v;
+    /* time-integrated dosage: sample every dose_every steps (0: off) */
+    int dose_every;
 } ocfg;
 
 /* ---------------------------------------------------------------------------------
@@ -341,6 +343,9 @@ typedef struct {
     int64_t *dep_fixed;   /* [2][cy][cx] */
     double *budget;       /* [8] released, air_in, air_out, dry, wet, exited, decayed, n_active */
     int64_t *counters;    /* [6] fixed: bin_out, dep_out_dry, dep_out_wet, exited, steps, bins */
+    double *dose;         /* [cz][cy][cx] sum over the dosage samples of the mass per cell */
+    int64_t *dose_fixed;  /* [cz][cy][cx] the same in fixed point */
+    int64_t *dose_ctr;    /* [2] fixed-point mass outside the grid, number of samples */
 } oout;
 
 static int64_t fixed_of(double m, int shift)
@@ -467,6 +472,21 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
     memset(o->dep, 0, sizeof(double) * ndep);
     memset(o->dep_fixed, 0, sizeof(int64_t) * ndep);
     for (int m = 0; m < 6; ++m) o->counters[m] = 0;
+    const int dosing = c->dose_every > 0 && o->dose && o->dose_fixed && o->dose_ctr;
+    /* the dosage sums up to floor(S / n) samples of at most the total mass: its fixed point
+     * gives up b = ceil(log2(samples)) bits so that no sum passes 2^61 units */
+    int dshift = shift;
+    if (dosing) {
+        int64_t most = c->n_steps / c->dose_every;
+        int b = 0;
+        while (b < 62 && ((int64_t)1 << b) < most) ++b;
+        dshift = shift - b;
+    }
+    if (dosing) {
+        memset(o->dose, 0, sizeof(double) * ncell);
+        memset(o->dose_fixed, 0, sizeof(int64_t) * ncell);
+        o->dose_ctr[0] = o->dose_ctr[1] = 0;
+    }
     double dep_out[2] = {0.0, 0.0}, exited = 0.0, bin_out = 0.0;
     int64_t steps = 0;
 
@@ -507,6 +527,27 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
                         dep_out[kind] += m;
                         o->counters[1 + kind] += fixed_of(m, shift);
                     }
+                }
+            }
+        }
+        /* time-integrated dosage (the post-processing of Sec. 3.2, done in the run): every
+         * dose_every-th step the decayed masses at t_{k+1} are added on the grid; the dose
+         * of a cell is this sum times dose_every * dt over the cell volume */
+        if (dosing && (k + 1) % c->dose_every == 0) {
+            o->dose_ctr[1] += 1;
+            for (int64_t q = 0; q < n; ++q) {
+                if (st[q] != OR_ACTIVE) continue;
+                double *X = P + 3 * q;
+                double m = oracle_mass_at(c, sp[q], k);
+                long ix = (long)floor((X[0] - c->cx0) / c->cdx);
+                long iy = (long)floor((X[1] - c->cy0) / c->cdy);
+                long iz = (long)floor((X[2] - c->cz0) / c->cdz);
+                if (ix >= 0 && ix < c->cx && iy >= 0 && iy < c->cy && iz >= 0 && iz < c->cz) {
+                    size_t cell = ((size_t)iz * c->cy + iy) * c->cx + ix;
+                    o->dose[cell] += m;
+                    o->dose_fixed[cell] += fixed_of(m, dshift);
+                } else {
+                    o->dose_ctr[0] += fixed_of(m, dshift);
                 }
             }
         }

@@ -409,3 +409,58 @@ def test_drift_correction_well_mixed_condition():
         res[drift] = (uniform, inv_k)
     assert res[1][0] > 1e-3 and res[1][1] < 1e-6, res
     assert res[0][1] > 1e-3 and res[0][0] < 1e-6, res
+
+
+# ------------------------------------------------------------------------------------
+# Time-integrated dosage (the post-processing of the n-th-step summations, Sec. 3.2)
+# ------------------------------------------------------------------------------------
+def test_dosage_total_closed_form():
+    """In uniform weather with no lateral boundary, no deposition and a reflecting ground,
+    every particle released at s_p <= k is airborne after step k, so the dosage summed
+    over all cells plus the out-of-grid part is sum over the samples (k+1) % n == 0 of
+    sum_{s_p <= k} round(m0(s_p) exp(-lambda (k+1-s_p) dt) 2^shift), with s_p and m0 from
+    the release reading. Catches a sample taken at the wrong step, a missed sample, the
+    mass of the wrong time, or a dropped out-of-grid part."""
+    n_p, steps, every = 700, 90, 4
+    cfg = dataclasses.replace(li.make_cfg0(n_particles=n_p, n_steps=steps), half_life_s=1800.0)
+    r = oracle.run(cfg, dose_every=every)
+    # fixed point of the dosage: the snapshot's shift less ceil(log2(S // n)) bits
+    shift = oracle.fixed_shift(cfg) - math.ceil(math.log2(steps // every))
+    lam = math.log(2.0) / 1800.0
+    sp = (np.arange(n_p) * steps) // n_p                      # s_p = floor(p S / N)
+    counts = np.bincount(sp, minlength=steps)
+    want, samples = 0, 0
+    for k in range(steps):
+        if (k + 1) % every:
+            continue
+        samples += 1
+        for s in sp[sp <= k]:
+            m = (1.0 * cfg.dt / counts[s]) * math.exp(-lam * ((k + 1 - s) * cfg.dt))
+            want += int(np.rint(math.ldexp(m, shift)))
+    got = int(r["dose_fixed"].sum()) + r["dose_out"]
+    assert r["dose_samples"] == samples == steps // every
+    assert got == want < 2 ** 61
+
+
+def test_dosage_is_the_sum_of_the_snapshots():
+    """The dosage grid equals, cell by cell, the sum of the concentration snapshots taken
+    at the same steps (each snapshot pinned separately against the plume law), and its
+    out-of-grid part the sum of theirs. Catches a wrong cell index or a sample whose
+    positions are not those of the snapshot at the same time."""
+    every, steps = 5, 40                      # 8 samples: the dosage drops b = 3 bits
+    base = dataclasses.replace(li.make_cfg0(n_particles=400, n_steps=steps), half_life_s=3600.0,
+                               bin_every=every, cx=15)        # the plume leaves x > 500 m
+    whole = oracle.run(base, dose_every=every)
+    total = np.zeros_like(whole["dose"])
+    out = 0.0
+    for end in range(every, steps + 1, every):
+        r = oracle.run(base, n_run=end)             # its last snapshot is at step end - 1
+        total += r["conc"]
+        out += r["budget"][2]                       # airborne mass outside the grid
+    np.testing.assert_allclose(whole["dose"], total, rtol=1e-12, atol=0.0)
+    # the fixed-point sums are the snapshots' on a scale 2^3 coarser
+    shift = oracle.fixed_shift(base) - 3
+    ulp = 2.0 ** -shift                             # each of <= 3200 terms rounds by <= ulp/2
+    np.testing.assert_allclose(whole["dose_fixed"] * ulp, total, rtol=0.0, atol=1600 * ulp)
+    assert out > 0
+    assert whole["dose_out"] * ulp == pytest.approx(out, rel=0, abs=1600 * ulp)
