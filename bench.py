@@ -338,6 +338,42 @@ def measure_stress(args, stream):
             "met": [cfg.n_met_t, cfg.nz, cfg.ny, cfg.nx], "active_particle_steps": active}
 
 
+def measure_dosage(args, stream):
+    """The plain realistic run with the time-integrated dosage sampled every 4 steps (the
+    paper's smallest summation interval, Sec. 3.2) in the step kernel."""
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_cfg1()
+    every = 4
+    with torch.cuda.stream(stream):
+        sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt, args.occ),
+                  sort_every=args.sort_every)
+    try:
+        times = []
+        for i in range(max(1, args.warmup) + 2):
+            sim.reset()
+            sim.set_dosage(every)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(cfg.n_steps)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= max(1, args.warmup):
+                times.append(e0.elapsed_time(e1))
+        active = int(sim.fixed_state()[2][4])
+        samples = sim.dosage()[2]
+    finally:
+        sim.close()
+    ms = statistics.mean(times)
+    return {"value": active / (ms / 1e3), "unit": UNIT, "ms_per_run": ms,
+            "dose_every": every, "samples_per_run": samples, "particles": cfg.n_particles,
+            "steps_per_run": cfg.n_steps}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -467,7 +503,8 @@ def run_gpu(args):
     if not args.no_forms:
         forms = {"batched": measure_batched(args, stream),
                  "adjoint": measure_adjoint(args, stream),
-                 "inversion": measure_inversion(args, stream)}
+                 "inversion": measure_inversion(args, stream),
+                 "dosage": measure_dosage(args, stream)}
         if not args.no_stress:
             forms["stress"] = measure_stress(args, stream)
         for f in forms.values():
@@ -498,7 +535,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms")
     ap.add_argument("--no-stress", action="store_true", help="skip the 1e8-particle stress case")
-    ap.add_argument("--only", choices=["batched", "adjoint", "inversion", "stress"], default=None,
+    ap.add_argument("--only", choices=["batched", "adjoint", "inversion", "stress", "dosage"],
+                    default=None,
                     help="run one form alone and print its measurement (profiling aid)")
     ap.add_argument("--batched-block", type=int, default=256)
     ap.add_argument("--batched-ppt", type=int, default=1)
@@ -514,7 +552,8 @@ def main():
         pkg_build.build()
         stream = torch.cuda.Stream()
         fn = {"batched": measure_batched, "adjoint": measure_adjoint,
-              "inversion": measure_inversion, "stress": measure_stress}[args.only]
+              "inversion": measure_inversion, "stress": measure_stress,
+              "dosage": measure_dosage}[args.only]
         print(json.dumps({"form": args.only, **fn(args, stream)}), flush=True)
         return 0
     return run_gpu(args)

@@ -197,7 +197,7 @@ lpm_status lpm_particles(lpm_ctx *ctx, int64_t first, int64_t count, float *xyz,
  * mass, below 2^61 units). conc: [cz][cy][cx], dep: [2][cy][cx] (either NULL);
  * counters[16] (may be NULL) = { bin_out, dep_out_dry, dep_out_wet, exited,
  * active_steps, n_bins, air_in, air_out, n_active, dep_total_dry, dep_total_wet,
- * 0, 0, 0, 0, 0 }, air_* and n_active as of the last lpm_budget. *shift may be NULL.
+ * dose_out, 0, 0, 0, 0 }, air_* and n_active as of the last lpm_budget. *shift may be NULL.
  */
 lpm_status lpm_fixed_state(lpm_ctx *ctx, int scenario, uint64_t *conc, size_t n_conc,
                            uint64_t *dep, size_t n_dep, int64_t counters[16], int *shift);
@@ -209,12 +209,37 @@ lpm_status lpm_fixed_state(lpm_ctx *ctx, int scenario, uint64_t *conc, size_t n_
  * occupancy calculator (Sec. 3.2); here the autotuner picks among these shapes. */
 lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int occupancy);
 
-/* Plain form only (ignored for ensembles): every every_steps steps, re-order the released
- * particles in memory by the weather cell they occupy, so that the threads of a warp
- * gather from neighbouring cells (a layout change only: every particle keeps its index,
- * hence its random numbers, and all results are identical). 0 turns it off; default 60.
- * Needs 52 bytes of extra device memory per particle slot, allocated at the first sort. */
+/* Every every_steps steps (at the multiples of every_steps), re-order the released
+ * particles of all scenarios in device memory by the weather cell they occupy, so that
+ * the threads of a warp gather from neighbouring cells (a layout change only: every
+ * particle keeps its id, hence its random numbers, and all results are bit-identical).
+ * 0 turns it off; default 60. A change moves every particle back to its home slot first.
+ * Needs about 56 bytes of extra device memory per particle slot, allocated at the first
+ * sort. */
 lpm_status lpm_set_sort(lpm_ctx *ctx, int every_steps);
+
+/*
+ * Time-integrated concentration ("dosage"): the paper sums the decayed masses on the grid
+ * every n-th step, n >= 4, and integrates the snapshots in time as a post-processing
+ * (Sec. 3.2), which it notes the GPU could do in a separate kernel (Sec. 4.2). Here the
+ * step kernel does it: with every_steps = n > 0, at t_{k+1} for every step k with
+ * (k + 1) % n == 0, the decayed mass of each active particle is added, in the same
+ * fixed point as the snapshots, to a per-scenario grid of the concentration grid's shape.
+ * lpm_set_dosage (re)starts the dosage from the current step: the grid and the
+ * out-of-grid counter (dose_out, counter 11 of lpm_fixed_state) are zeroed, and n = 0
+ * turns sampling off. lpm_reset zeroes them too. Allocates 8 bytes per cell and scenario
+ * at the first call with n > 0.
+ *
+ * lpm_dosage: out[cz][cy][cx] (n_out = cz*cy*cx) = sum over the samples of the
+ * concentration at the sample times times n*dt, i.e. mass * s / m^3; fixed (may be NULL)
+ * receives the raw sums of round(m * 2^(shift - b)), shift that of lpm_fixed_state and
+ * b = ceil(log2(floor(n_steps / n))) (so that no sum passes 2^61 units); *n_samples (may
+ * be NULL) the number of samples taken. LPM_E_STATE if dosage was never enabled.
+ * Synchronises.
+ */
+lpm_status lpm_set_dosage(lpm_ctx *ctx, int every_steps);
+lpm_status lpm_dosage(lpm_ctx *ctx, int scenario, double *out, size_t n_out, uint64_t *fixed,
+                      int64_t *n_samples);
 
 /*
  * Checkpoint / resume of a run (no paper counterpart; the counter-based draws make the

@@ -40,10 +40,11 @@ __device__ __forceinline__ void warp_accumulate(int key, unsigned long long v,
     __syncwarp();
 }
 
-// The same over the grids of all scenarios: key = scenario * n_cells + cell, or
-// -2 - scenario for that scenario's out-of-grid counter (-1: nothing).
+// The same over the grids of all scenarios (grid_all [n_scen][cells]): key = scenario *
+// n_cells + cell, or -2 - scenario for that scenario's counter `out` (-1: nothing).
 __device__ __forceinline__ void warp_accumulate_scen(long long key, unsigned long long v,
                                                      const StepParams &P,
+                                                     unsigned long long *grid_all, int out,
                                                      unsigned long long *s_warp, long long n_cells)
 {
     const int lane = threadIdx.x & 31;
@@ -59,10 +60,10 @@ __device__ __forceinline__ void warp_accumulate_scen(long long key, unsigned lon
             m &= m - 1;
         }
         if (key >= 0) {
-            if (key < n_cells * P.n_scen) atomicAdd(P.conc_all + key, sum);
+            if (key < n_cells * P.n_scen) atomicAdd(grid_all + key, sum);
             else atomicOr(P.err, ERR_INDEX);
         } else {
-            atomicAdd(P.ctr_all + (long long)C_BIN_OUT * P.ctr_stride + (-2 - key), sum);
+            atomicAdd(P.ctr_all + (long long)out * P.ctr_stride + (-2 - key), sum);
         }
     }
     __syncwarp();
@@ -138,6 +139,17 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
         m.kh = 0.0f;
     }
     return m;
+}
+
+// Concentration-grid cell of a position, or KEY_OUT outside the grid.
+__device__ __forceinline__ int grid_cell(const StepParams &P, float x, float y, float z)
+{
+    const int ix = (int)floorf((x - P.cx0) * P.inv_cdx);
+    const int iy = (int)floorf((y - P.cy0) * P.inv_cdy);
+    const int iz = (int)floorf((z - P.cz0) * P.inv_cdz);
+    if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz)
+        return (iz * P.cy + iy) * P.cx + ix;
+    return KEY_OUT;
 }
 
 __device__ __forceinline__ float mass_at(const StepParams &P, const ScenDev &sc, int sp, int k_end)
@@ -270,8 +282,9 @@ struct MinBlocks {
 // block index (grid over all tiles) or by an atomic queue (persistent grid). With MIXED the
 // lanes of a tile may belong to different scenarios (the sorted particles of a batched
 // context): each lane finds its scenario from its home slot and carries its own wind
-// offset; the results are bit-identical to the per-scenario path.
-template <int BLOCK, int PPT, int OCC, bool MIXED>
+// offset; the results are bit-identical to the per-scenario path. DOSE adds the dosage
+// samples (every P.dose_every steps) inside the time loop.
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
                int k1, int do_bin)
@@ -364,7 +377,13 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
             o0[j] = o1[j] = make_float2(0.0f, 0.0f);
         }
 #pragma unroll 1
-        for (int k = k0; k < k1 && live > 0; ++k) {
+        for (int k = k0; k < k1; ++k) {
+            // with dosage sampling the warp stays together (the samples are warp-collective)
+            if (DOSE) {
+                if (!__any_sync(0xffffffffu, live > 0)) break;
+            } else if (live <= 0) {
+                break;
+            }
             const StepTime T = step_time(P, MIXED ? nullptr : sc.wind_offset, k);
             if (MIXED && P.woff && T.ts.h0 != cur_h) {
                 cur_h = T.ts.h0;
@@ -411,6 +430,34 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;
             }
+            // time-integrated dosage: every dose_every-th step, the decayed masses at t_{k+1}
+            if (DOSE && (k + 1) % P.dose_every == 0) {
+#pragma unroll
+                for (int j = 0; j < PPT; ++j) {
+                    const int local = j * BLOCK + threadIdx.x;
+                    const bool on = local < count && (tag[j] >> TAG_SHIFT) == ST_ACTIVE;
+                    const int sp = (int)(tag[j] & TAG_STEP);
+                    const int cell = on ? grid_cell(P, x[j], y[j], z[j]) : KEY_NONE;
+                    unsigned long long v = 0ull;
+                    if (on) {
+                        if (MIXED) {
+                            const ScenDev &q = P.scen[sj[j]];
+                            v = to_fixed(mass_at(P, q, sp, k), __ldg(&q.scale) * P.dose_mul);
+                        } else {
+                            v = to_fixed(mass_at(P, sc, sp, k), sc.scale * P.dose_mul);
+                        }
+                    }
+                    if (MIXED) {
+                        long long key = -1;
+                        if (on) key = cell >= 0 ? (long long)sj[j] * n_cells + cell : -2LL - sj[j];
+                        warp_accumulate_scen(key, v, P, P.dose_all, C_DOSE_OUT, s_warp, n_cells);
+                    } else {
+                        warp_accumulate(cell, v, P.dose_all + (long long)tscen * n_cells,
+                                        scg.ctr + C_DOSE_OUT * P.ctr_stride, s_warp, n_cells,
+                                        P.err);
+                    }
+                }
+            }
         }
 
         // ---- store ------------------------------------------------------------------
@@ -438,18 +485,12 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                     } else {
                         v = to_fixed(mass_at(P, sc, sp, k1 - 1), sc.scale);
                     }
-                    const int ix = (int)floorf((x[j] - P.cx0) * P.inv_cdx);
-                    const int iy = (int)floorf((y[j] - P.cy0) * P.inv_cdy);
-                    const int iz = (int)floorf((z[j] - P.cz0) * P.inv_cdz);
-                    if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz)
-                        cell = (iz * P.cy + iy) * P.cx + ix;
-                    else
-                        cell = KEY_OUT;
+                    cell = grid_cell(P, x[j], y[j], z[j]);
                 }
                 if (MIXED) {
                     long long key = -1;
                     if (on) key = cell >= 0 ? (long long)sj[j] * n_cells + cell : -2LL - sj[j];
-                    warp_accumulate_scen(key, v, P, s_warp, n_cells);
+                    warp_accumulate_scen(key, v, P, P.conc_all, C_BIN_OUT, s_warp, n_cells);
                 } else {
                     warp_accumulate(cell, v, scg.conc, scg.ctr + C_BIN_OUT * P.ctr_stride, s_warp,
                                     n_cells, P.err);
@@ -474,30 +515,33 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
     }
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE>
 cudaError_t launch_adv(const AdvanceLaunch &L)
 {
-    advance_kernel<BLOCK, PPT, OCC, MIXED><<<L.grid, BLOCK, 0, L.stream>>>(
+    advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE><<<L.grid, BLOCK, 0, L.stream>>>(
         *L.params, L.ranges, L.n_tiles(), L.queue, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE>
 int occ_adv()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC, MIXED>, BLOCK,
-                                                  0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE>,
+                                                  BLOCK, 0);
     return n;
 }
 
-// (particles per thread, occupancy variant, mixed scenarios) -> instantiation, for one
-// block size
-#define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, ...)                                    \
-    case PPT * 100 + OCC * 10 + MIX: return FN<BLOCK, PPT, OCC, (MIX != 0)>(__VA_ARGS__);
+// (particles per thread, occupancy variant, mixed scenarios, dosage) -> instantiation, for
+// one block size
+#define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, DOS, ...)                               \
+    case PPT * 1000 + OCC * 100 + MIX * 10 + DOS:                                      \
+        return FN<BLOCK, PPT, OCC, (MIX != 0), (DOS != 0)>(__VA_ARGS__);
 #define LPM_ADV_CASES2(FN, BLOCK, PPT, OCC, ...)                                       \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, __VA_ARGS__)                                  \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, __VA_ARGS__)
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 0, __VA_ARGS__)                               \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 0, __VA_ARGS__)                               \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 1, __VA_ARGS__)                               \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 1, __VA_ARGS__)
 #define LPM_ADV_CASES(FN, BLOCK, ...)                                                  \
     LPM_ADV_CASES2(FN, BLOCK, 1, 0, __VA_ARGS__)                                       \
     LPM_ADV_CASES2(FN, BLOCK, 1, 1, __VA_ARGS__)                                       \
@@ -512,14 +556,16 @@ int occ_adv()
 #define LPM_ADVANCE_TU(BLOCK)                                                          \
     cudaError_t launch_advance_b##BLOCK(const AdvanceLaunch &L)                         \
     {                                                                                  \
-        switch (L.ppt * 100 + L.occ * 10 + (L.mixed ? 1 : 0)) {                        \
+        switch (L.ppt * 1000 + L.occ * 100 + (L.mixed ? 10 : 0) + (L.dose ? 1 : 0)) {  \
             LPM_ADV_CASES(launch_adv, BLOCK, L)                                        \
         }                                                                              \
         return cudaErrorInvalidValue;                                                  \
     }                                                                                  \
     int occupancy_b##BLOCK(int ppt, int occ, bool mixed)                               \
     {                                                                                  \
-        switch (ppt * 100 + occ * 10 + (mixed ? 1 : 0)) { LPM_ADV_CASES(occ_adv, BLOCK) } \
+        switch (ppt * 1000 + occ * 100 + (mixed ? 10 : 0)) {                           \
+            LPM_ADV_CASES(occ_adv, BLOCK)                                              \
+        }                                                                              \
         return 0;                                                                      \
     }
 

@@ -106,6 +106,12 @@ struct lpm_ctx {
     float4 *d_grave = nullptr;              // particles found dead at a sort (read-back only)
     unsigned int *d_grave_n = nullptr;
 
+    // time-integrated dosage
+    unsigned long long *d_dose = nullptr;   // [n_scen][cz*cy*cx]
+    int dose_every = 0;
+    int dose_bits = 0;                      // ceil(log2(floor(n_steps / dose_every)))
+    long long n_dose = 0;                   // samples taken since the last (re)start
+
     // differentiable parameters (adjoint form): diffusivity scale and wind bias
     double k_scale = 1.0, bias_u = 0.0, bias_v = 0.0;
     // receptor / adjoint state
@@ -278,6 +284,9 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.woff = c->any_woff ? c->d_woff : nullptr;
     P.conc_all = c->d_conc;
     P.ctr_all = c->d_ctr;
+    P.dose_all = c->d_dose;
+    P.dose_every = c->d_dose ? c->dose_every : 0;
+    P.dose_mul = std::ldexp(1.0f, -c->dose_bits);
     P.err = c->d_err;
 }
 
@@ -685,7 +694,7 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
                     c->d_rgrad, c->d_adj_tiles, c->d_sorted[0], c->d_sorted[1], c->d_pidx[0],
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
-                    c->d_grave, c->d_grave_n};
+                    c->d_grave, c->d_grave_n, c->d_dose};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -835,8 +844,12 @@ lpm_status lpm_reset(lpm_ctx *c)
     c->n_launches++;
     st = clear_sort_state(c, false);
     if (st != LPM_OK) return st;
+    if (c->d_dose)
+        LPM_CUDA(c, cudaMemsetAsync(c->d_dose, 0, ns * c->ncell() * sizeof(unsigned long long),
+                                    c->stream));
     c->k = 0;
     c->n_bins = 0;
+    c->n_dose = 0;
     return LPM_OK;
 }
 
@@ -952,6 +965,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.ppt = c->ppt;
         L.occ = c->occ;
         L.mixed = batched;
+        L.dose = P.dose_every > 0;
         const int n_tiles = L.n_tiles();
         if (n_tiles <= 0) continue;
         if (batched) {
@@ -1110,6 +1124,7 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
     }
     for (const Segment &sg : plan)
         if (sg.do_bin) c->n_bins++;
+    if (P.dose_every > 0) c->n_dose += k_end / P.dose_every - c->k / P.dose_every;
     c->k = k_end;
     return LPM_OK;
 }
@@ -1284,6 +1299,58 @@ lpm_status lpm_set_sort(lpm_ctx *c, int every_steps)
     c->sort_every = every_steps;
     c->tiles_valid = false;
     drop_graphs(c);
+    return LPM_OK;
+}
+
+lpm_status lpm_set_dosage(lpm_ctx *c, int every_steps)
+{
+    if (!c) return LPM_E_INVALID;
+    if (every_steps < 0) return fail(c, LPM_E_INVALID, "every_steps must be >= 0");
+    const size_t ns = (size_t)c->cfg.n_scenarios;
+    if (every_steps > 0 && !c->d_dose) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        LPM_CUDA(c, cudaMalloc(&c->d_dose, ns * c->ncell() * sizeof(unsigned long long)));
+    }
+    if (c->d_dose)
+        LPM_CUDA(c, cudaMemsetAsync(c->d_dose, 0, ns * c->ncell() * sizeof(unsigned long long),
+                                    c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + (size_t)C_DOSE_OUT * ns, 0,
+                                ns * sizeof(unsigned long long), c->stream));
+    c->dose_every = every_steps;
+    c->dose_bits = 0;
+    if (every_steps > 0) {
+        // up to floor(S / n) samples of at most the total mass: b bits fewer than the
+        // snapshots keep every sum below 2^61 units
+        const long long most = c->cfg.n_steps / every_steps;
+        while (c->dose_bits < 62 && (1LL << c->dose_bits) < most) ++c->dose_bits;
+    }
+    c->n_dose = 0;
+    drop_graphs(c);                          // the graphs hold the step parameters
+    return LPM_OK;
+}
+
+lpm_status lpm_dosage(lpm_ctx *c, int scenario, double *out, size_t n_out, uint64_t *fixed,
+                      int64_t *n_samples)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "bad scenario");
+    if (!c->d_dose) return fail(c, LPM_E_STATE, "dosage was never enabled (lpm_set_dosage)");
+    if ((out || fixed) && n_out != c->ncell())
+        return fail(c, LPM_E_INVALID, "n_out must be cz*cy*cx = %zu", c->ncell());
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    if (n_samples) *n_samples = c->n_dose;
+    if (!out && !fixed) return LPM_OK;
+    std::vector<unsigned long long> h(c->ncell());
+    LPM_CUDA(c, cudaMemcpy(h.data(), c->d_dose + (size_t)scenario * c->ncell(),
+                           h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    if (fixed) std::memcpy(fixed, h.data(), h.size() * sizeof(uint64_t));
+    if (out) {
+        const lpm_config &g = c->cfg;
+        const double f = std::ldexp(1.0, c->dose_bits - c->scen[(size_t)scenario].shift) *
+                         ((double)c->dose_every * g.dt) / (g.cdx * g.cdy * g.cdz);
+        for (size_t i = 0; i < h.size(); ++i) out[i] = (double)h[i] * f;
+    }
     return LPM_OK;
 }
 
@@ -1492,8 +1559,9 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
 // ---- checkpoint / resume --------------------------------------------------------
 namespace {
 struct SaveHeader {
-    char magic[8];               // "LPMSAVE1"
+    char magic[8];               // "LPMSAVE2"
     long long k, n_bins, n_slots, n_scen, ncell, ndep, n_ctr;
+    long long dose_every, n_dose; // dosage interval (0: none saved) and samples taken
 };
 }  // namespace
 
@@ -1501,9 +1569,11 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
 {
     if (!c || !n) return LPM_E_INVALID;
     const size_t ns = (size_t)c->cfg.n_scenarios;
+    const bool dose = c->d_dose && c->dose_every > 0;
     const size_t bytes = sizeof(SaveHeader) + (size_t)c->n_slots_used * sizeof(float4) +
                          ns * (c->ncell() + c->ndep()) * sizeof(unsigned long long) +
-                         (size_t)N_COUNTERS * ns * sizeof(unsigned long long);
+                         (size_t)N_COUNTERS * ns * sizeof(unsigned long long) +
+                         (dose ? ns * c->ncell() * sizeof(unsigned long long) : 0);
     if (!buf) {
         *n = bytes;
         return LPM_OK;
@@ -1512,7 +1582,7 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     lpm_status st = check_device_error(c);
     if (st != LPM_OK) return st;
     SaveHeader h;
-    std::memcpy(h.magic, "LPMSAVE1", 8);
+    std::memcpy(h.magic, "LPMSAVE2", 8);
     h.k = c->k;
     h.n_bins = c->n_bins;
     h.n_slots = c->n_slots_used;
@@ -1520,6 +1590,8 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     h.ncell = (long long)c->ncell();
     h.ndep = (long long)c->ndep();
     h.n_ctr = N_COUNTERS;
+    h.dose_every = dose ? c->dose_every : 0;
+    h.n_dose = dose ? c->n_dose : 0;
     char *o = static_cast<char *>(buf);
     std::memcpy(o, &h, sizeof h);
     o += sizeof h;
@@ -1540,6 +1612,10 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     LPM_CUDA(c, cudaMemcpyAsync(o, c->d_dep, ns * c->ndep() * 8, cudaMemcpyDeviceToHost, c->stream));
     o += ns * c->ndep() * 8;
     LPM_CUDA(c, cudaMemcpyAsync(o, c->d_ctr, ns * N_COUNTERS * 8, cudaMemcpyDeviceToHost, c->stream));
+    o += ns * N_COUNTERS * 8;
+    if (dose)
+        LPM_CUDA(c, cudaMemcpyAsync(o, c->d_dose, ns * c->ncell() * 8, cudaMemcpyDeviceToHost,
+                                    c->stream));
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     *n = bytes;
     return LPM_OK;
@@ -1554,13 +1630,14 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     if (n < sizeof h) return fail(c, LPM_E_INVALID, "buffer too small for a saved run");
     std::memcpy(&h, buf, sizeof h);
     const size_t ns = (size_t)c->cfg.n_scenarios;
-    if (std::memcmp(h.magic, "LPMSAVE1", 8) != 0 || h.n_slots != c->n_slots_used ||
+    if (std::memcmp(h.magic, "LPMSAVE2", 8) != 0 || h.n_slots != c->n_slots_used ||
         h.n_scen != (long long)ns || h.ncell != (long long)c->ncell() ||
         h.ndep != (long long)c->ndep() || h.n_ctr != N_COUNTERS || h.k < 0 ||
-        h.k > c->cfg.n_steps)
+        h.k > c->cfg.n_steps || h.dose_every < 0 || h.dose_every > 0x7fffffffLL)
         return fail(c, LPM_E_INVALID, "saved run does not match this context");
     const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
-    const size_t need = sizeof h + sb + ns * (c->ncell() + c->ndep() + N_COUNTERS) * 8;
+    const size_t need = sizeof h + sb + ns * (c->ncell() + c->ndep() + N_COUNTERS) * 8 +
+                        (h.dose_every > 0 ? ns * c->ncell() * 8 : 0);
     if (n < need) return fail(c, LPM_E_INVALID, "saved run truncated (%zu of %zu bytes)", n, need);
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
@@ -1572,6 +1649,21 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     LPM_CUDA(c, cudaMemcpyAsync(c->d_dep, i, ns * c->ndep() * 8, cudaMemcpyHostToDevice, c->stream));
     i += ns * c->ndep() * 8;
     LPM_CUDA(c, cudaMemcpyAsync(c->d_ctr, i, ns * N_COUNTERS * 8, cudaMemcpyHostToDevice, c->stream));
+    i += ns * N_COUNTERS * 8;
+    if (h.dose_every > 0) {
+        st = lpm_set_dosage(c, (int)h.dose_every);   // allocates and zeroes the dose_out row
+        if (st != LPM_OK) return st;
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_dose, i, ns * c->ncell() * 8, cudaMemcpyHostToDevice,
+                                    c->stream));
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_ctr + (size_t)C_DOSE_OUT * ns,
+                                    static_cast<const char *>(buf) + sizeof h + sb +
+                                        ns * (c->ncell() + c->ndep()) * 8 + (size_t)C_DOSE_OUT * ns * 8,
+                                    ns * 8, cudaMemcpyHostToDevice, c->stream));
+        c->n_dose = h.n_dose;
+    } else if (c->d_dose) {
+        st = lpm_set_dosage(c, 0);
+        if (st != LPM_OK) return st;
+    }
     LPM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
     st = clear_sort_state(c, false);     // every particle at its home slot
     if (st != LPM_OK) return st;

@@ -27,7 +27,7 @@ constexpr int MAX_LUT = 4096;          // entries of the vertical level lookup t
 enum {
     C_BIN_OUT = 0, C_DEP_OUT_DRY = 1, C_DEP_OUT_WET = 2, C_EXITED = 3,
     C_ACTIVE_STEPS = 4 /* count */, C_N_BINS = 5 /* count */, C_AIR_IN = 6, C_AIR_OUT = 7,
-    C_N_ACTIVE = 8 /* count */, C_DEP_DRY = 9, C_DEP_WET = 10, N_COUNTERS = 16
+    C_N_ACTIVE = 8 /* count */, C_DEP_DRY = 9, C_DEP_WET = 10, C_DOSE_OUT = 11, N_COUNTERS = 16
 };
 
 // Device error word bits.
@@ -90,6 +90,9 @@ struct StepParams {
     const float2 *woff;              // [n_scen][n_t] wind offsets of every scenario, or nullptr
     unsigned long long *conc_all;    // [n_scen][cz][cy][cx]
     unsigned long long *ctr_all;     // [N_COUNTERS][n_scen]
+    unsigned long long *dose_all;    // [n_scen][cz][cy][cx] dosage sums, or nullptr
+    int dose_every;                  // dosage sample every dose_every steps (0: off)
+    float dose_mul;                  // 2^-b: dosage fixed point = snapshot fixed point / 2^b
     unsigned int *err;
 };
 

@@ -29,6 +29,7 @@ struct AdvanceLaunch {
     int k0, k1, do_bin;
     int block, ppt, occ;
     bool mixed;               // lanes of one tile may belong to different scenarios
+    bool dose;                // dosage samples inside the time loop (params->dose_every)
     unsigned int grid;
     int n_tiles() const { return ranges.tiles_a + ranges.n_b; }
 };

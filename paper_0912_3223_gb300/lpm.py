@@ -29,7 +29,7 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_set_launch", "lpm_sync", "lpm_draws", "lpm_release_range", "lpm_reset",
            "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
            "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save",
-           "lpm_load"]
+           "lpm_load", "lpm_set_dosage", "lpm_dosage"]
 
 
 class LpmError(RuntimeError):
@@ -97,6 +97,8 @@ def load() -> C.CDLL:
     L.lpm_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), dp]
     L.lpm_set_params.argtypes = [vp, C.c_double, C.c_double, C.c_double]
     L.lpm_set_sort.argtypes = [vp, C.c_int]
+    L.lpm_set_dosage.argtypes = [vp, C.c_int]
+    L.lpm_dosage.argtypes = [vp, C.c_int, dp, C.c_size_t, C.POINTER(C.c_uint64), C.POINTER(i64)]
     L.lpm_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
     L.lpm_load.argtypes = [vp, vp, C.c_size_t]
     L.lpm_set_emission.argtypes = [vp, C.c_int, dp, C.c_int]
@@ -111,7 +113,8 @@ def load() -> C.CDLL:
                  "lpm_particles", "lpm_fixed_state", "lpm_set_launch", "lpm_sync",
                  "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
                  "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
-                 "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load"):
+                 "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load",
+                 "lpm_set_dosage", "lpm_dosage"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -323,6 +326,20 @@ def lpm_fixed_state(ctx, scenario: int, conc_shape, dep_shape):
     return conc, dep, ctr, int(sh.value)
 
 
+def lpm_set_dosage(ctx, every_steps: int) -> None:
+    _check(ctx, load().lpm_set_dosage(C.c_void_p(ctx), int(every_steps)))
+
+
+def lpm_dosage(ctx, scenario: int, shape):
+    """(dosage [mass s / m^3], raw fixed-point sums, number of samples) of a scenario."""
+    out = np.empty(shape, dtype=np.float64)
+    fixed = np.empty(shape, dtype=np.uint64)
+    n = C.c_int64()
+    _check(ctx, load().lpm_dosage(C.c_void_p(ctx), int(scenario), _ptr(out, C.c_double), out.size,
+                                  _ptr(fixed, C.c_uint64), C.byref(n)))
+    return out, fixed, int(n.value)
+
+
 def lpm_set_launch(ctx, block: int, particles_per_thread: int, occupancy: int = 1) -> None:
     _check(ctx, load().lpm_set_launch(C.c_void_p(ctx), int(block), int(particles_per_thread),
                                       int(occupancy)))
@@ -452,6 +469,15 @@ class Sim:
     def fixed_state(self, scenario: int = 0):
         c = self.cfg
         return lpm_fixed_state(self.ctx, scenario, (c.cz, c.cy, c.cx), (2, c.cy, c.cx))
+
+    def set_dosage(self, every_steps: int):
+        lpm_set_dosage(self.ctx, every_steps)
+        return self
+
+    def dosage(self, scenario: int = 0):
+        """(dosage [mass s / m^3], fixed-point sums, samples) of a scenario."""
+        c = self.cfg
+        return lpm_dosage(self.ctx, scenario, (c.cz, c.cy, c.cx))
 
     def sync(self):
         lpm_sync(self.ctx)

@@ -303,20 +303,26 @@ def test_save_and_resume_is_bit_identical(sort_every):
     from paper_0912_3223_gb300 import Sim, lpm
     cfg = li.make_cfg1(n_particles=6007, n_steps=330, n_hours=4)
     with Sim(cfg, sort_every=sort_every) as a:
+        if sort_every:
+            a.set_dosage(8)                  # the dosage state travels with the checkpoint
         a.step(150)
         saved = lpm.lpm_save(a.ctx)
         a.step(cfg.n_steps - 150)
         ref_xyz, ref_tag = a.particles()
         ref = a.fixed_state()
+        ref_dose = a.dosage() if sort_every else None
     with Sim(cfg, sort_every=sort_every) as b:
         lpm.lpm_load(b.ctx, saved)
         assert b.k == 150
         b.step(cfg.n_steps - 150)
         xyz, tag = b.particles()
         got = b.fixed_state()
+        if sort_every:
+            dose = b.dosage()
+            assert np.array_equal(dose[1], ref_dose[1]) and dose[2] == ref_dose[2] == 330 // 8
     assert np.array_equal(xyz, ref_xyz) and np.array_equal(tag, ref_tag)
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
-    assert np.array_equal(got[2][:6], ref[2][:6])
+    assert np.array_equal(got[2][:6], ref[2][:6]) and got[2][11] == ref[2][11]
     with Sim(li.make_cfg1(n_particles=100, n_steps=330, n_hours=4)) as other:
         with pytest.raises(lpm.LpmError) as e:
             lpm.lpm_load(other.ctx, saved)
