@@ -41,6 +41,7 @@ SEED_RAIN = 12
 SEED_SCENARIOS = 13
 SEED_HIDDEN = 14
 SEED_RECEPTORS = 15
+SEED_BOUNDARY_LAYER = 16
 
 
 @dataclasses.dataclass
@@ -117,6 +118,10 @@ class LpmConfig:
     kh: Optional[np.ndarray] = None     # float32 [n_met_t][nz][ny][nx]
     rain: Optional[np.ndarray] = None   # uint8  [n_met_t][ny][nx]
     scenarios: List[Scenario] = dataclasses.field(default_factory=list)
+    # K_z model: 0 = the gridded K_z of uvwk, 1 = Eq. 3 from the boundary-layer columns
+    kz_model: int = 0
+    kz_min: float = 0.1
+    bl: Optional[np.ndarray] = None     # float32 [n_met_t][ny][nx][4] = (u*, 1/L, H_z, 0)
     name: str = ""
 
     @property
@@ -232,6 +237,38 @@ def make_met_realistic(nx: int = 200, ny: int = 200, nz: int = 30, n_t: int = 25
     return uvwk, z_levels
 
 
+def make_boundary_layer(nx: int = 200, ny: int = 200, n_t: int = 25, dx: float = 250.0,
+                        dy: float = 250.0, seed: int = SEED_BOUNDARY_LAYER) -> np.ndarray:
+    """Hourly boundary-layer columns for Eq. 3, float32 [n_t][ny][nx][4] = (u*, 1/L, H_z, 0):
+    a diurnal cycle starting at 06 h (stable night to unstable day: 1/L from +0.01 to
+    -0.03 1/m, H_z from 400 m to 1600 m) modulated by seeded smooth fields (4 Fourier modes,
+    wavelengths 10..40 km): u* = 0.4 (1 + 0.25 g1) m/s, 1/L + 0.004 g2, H_z (1 + 0.15 g3)."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) * dx
+    y = np.arange(ny) * dy
+    X, Y = np.meshgrid(x, y)
+
+    def smooth():
+        g = np.zeros((ny, nx))
+        for _ in range(4):
+            lam = rng.uniform(10000.0, 40000.0)
+            th = rng.uniform(0.0, 2 * np.pi)
+            ph = rng.uniform(0.0, 2 * np.pi)
+            g += np.sin(2 * np.pi / lam * (np.cos(th) * X + np.sin(th) * Y) + ph)
+        return g / 2.0                       # roughly in [-1, 1]
+
+    g1, g2, g3 = smooth(), smooth(), smooth()
+    out = np.zeros((n_t, ny, nx, 4), dtype=np.float32)
+    for h in range(n_t):
+        day = math.sin(2 * np.pi * (h - 6) / 24.0)        # > 0 by day
+        inv_l = (0.01 - 0.02 * (day + 1.0)) if day > 0 else 0.01 * (1.0 + day)
+        hz = 1000.0 + 600.0 * day
+        out[h, :, :, 0] = np.clip(0.4 * (1.0 + 0.25 * g1), 0.1, 0.8)
+        out[h, :, :, 1] = inv_l + 0.004 * g2
+        out[h, :, :, 2] = np.clip(hz * (1.0 + 0.15 * g3), 200.0, 2500.0)
+    return out
+
+
 def make_rain(nx: int = 200, ny: int = 200, n_t: int = 25, dx: float = 250.0,
               dy: float = 250.0, n_discs: int = 8, u_adv: float = None,
               seed: int = SEED_RAIN) -> np.ndarray:
@@ -259,12 +296,14 @@ def make_rain(nx: int = 200, ny: int = 200, n_t: int = 25, dx: float = 250.0,
 
 
 def make_cfg1(n_particles: int = 10_000_000, n_steps: int = 2880, n_hours: int = None,
-              seed: int = SEED_PARTICLES, with_rain: bool = True) -> LpmConfig:
+              seed: int = SEED_PARTICLES, with_rain: bool = True,
+              kz_eq3: bool = False) -> LpmConfig:
     """Plain method, realistic: 24 h at dt = 30 s on a 200x200x30 hourly met grid
     (250 m spacing, stretched levels to 3 km), 8-day half-life, dry deposition velocity
     0.002 m/s below a 1000 m mixing layer, wet scavenging 1e-4 1/s inside the rain mask,
     400x400x20 concentration grid (125 m x 125 m x 50 m) plus a 400x400 deposition grid.
-    ``n_hours`` limits the generated met slabs (default: enough for ``n_steps``)."""
+    ``n_hours`` limits the generated met slabs (default: enough for ``n_steps``).
+    ``kz_eq3`` takes K_z from Eq. 3 on seeded boundary-layer columns instead of the grid."""
     dt = 30.0
     if n_hours is None:
         n_hours = int(math.ceil(n_steps * dt / 3600.0)) + 1
@@ -283,7 +322,9 @@ def make_cfg1(n_particles: int = 10_000_000, n_steps: int = 2880, n_hours: int =
         n_scenarios=1,
         release=Release(n_particles=n_particles, q=np.array([1.0]), q_dt=3600.0,
                         first_step=0, last_step=n_steps),
-        uvwk=uvwk, kh=None, rain=rain, name="cfg1 plain realistic")
+        uvwk=uvwk, kh=None, rain=rain, name="cfg1 plain realistic",
+        kz_model=1 if kz_eq3 else 0,
+        bl=make_boundary_layer(n_t=n_hours) if kz_eq3 else None)
 
 
 def make_cfg2(n_scenarios: int = 256, n_steps: int = 1440, n_min: float = 1e4,

@@ -56,6 +56,7 @@ class OCfg(C.Structure):
         ("pid_offset", C.c_int64),
         ("k_scale", C.c_double), ("bias_u", C.c_double), ("bias_v", C.c_double),
         ("dose_every", C.c_int),
+        ("kz_model", C.c_int), ("kz_min", C.c_double), ("bl", C.POINTER(C.c_float)),
     ]
 
 
@@ -97,6 +98,7 @@ def lib():
         L.oracle_fixed_shift.restype = C.c_int
         L.oracle_initial_mass.argtypes = [C.POINTER(OCfg), C.c_int64]
         L.oracle_initial_mass.restype = C.c_double
+        L.oracle_kz_eq3.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
         L.oracle_threshold.argtypes = [C.c_double]
         L.oracle_threshold.restype = C.c_uint32
         L.oracle_run.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_int64), C.c_int64, C.c_int64,
@@ -179,6 +181,9 @@ def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
     o.k_scale = float(k_scale)
     o.bias_u, o.bias_v = float(bias[0]), float(bias[1])
     o.dose_every = int(dose_every)
+    o.kz_model = int(getattr(cfg, "kz_model", 0))
+    o.kz_min = float(getattr(cfg, "kz_min", 0.1))
+    o.bl = _ptr(pin.arr(getattr(cfg, "bl", None), np.float32), C.c_float)
     o._pin = pin  # keep arrays alive with the record
     return o
 
@@ -236,6 +241,13 @@ def release_steps(n: int, first: int, last: int, p) -> np.ndarray:
 
 def release_count(n: int, first: int, last: int, step: int) -> int:
     return int(lib().oracle_release_count(n, first, last, step))
+
+
+def kz_eq3(ustar: float, inv_l: float, hz: float, kz_min: float, z: float):
+    """(K_z, dK_z/dz) of Eq. 3 at height z."""
+    out = (C.c_double * 2)()
+    lib().oracle_kz_eq3(float(ustar), float(inv_l), float(hz), float(kz_min), float(z), out)
+    return float(out[0]), float(out[1])
 
 
 def threshold(p: float) -> int:

@@ -133,6 +133,10 @@ typedef struct {
     double k_scale, bias_u, bias_v;
     /* time-integrated dosage: sample every dose_every steps (0: off) */
     int dose_every;
+    /* K_z model: 0 = the gridded K_z of uvwk; 1 = Eq. 3 from the boundary-layer columns */
+    int kz_model;
+    double kz_min;                   /* floor of the Eq. 3 diffusivity (m^2/s) */
+    const float *bl;                 /* [n_met_t][ny][nx][4] (u*, 1/L, H_z, unused) or NULL */
 } ocfg;
 
 /* ---------------------------------------------------------------------------------
@@ -257,8 +261,70 @@ static void axis_time(const ocfg *c, double t, int *h0, int *h1, double *f)
     *h1 = h + 1;
 }
 
+/* Similarity function for heat of Eq. 3, Phi_h(zeta) with zeta = z/L, and its derivative
+ * in zeta. The paper leaves its form open; these are the Businger-Dyer forms:
+ * 1 + 5 zeta for stable stratification (zeta >= 0), (1 - 16 zeta)^(-1/2) for unstable. */
+static double phi_h(double zeta)
+{
+    return zeta >= 0.0 ? 1.0 + 5.0 * zeta : 1.0 / sqrt(1.0 - 16.0 * zeta);
+}
+
+static double dphi_h(double zeta)
+{
+    return zeta >= 0.0 ? 5.0 : 8.0 * pow(1.0 - 16.0 * zeta, -1.5);
+}
+
+/* Eq. 3: K_z(z) = k u* z (1 - z/H_z)^2 / Phi_h(z/L) with k = 0.4 for 0 < z < H_z and 0
+ * elsewhere (the squared factor would grow again above H_z), then floored at kz_min.
+ * out = (K_z, dK_z/dz), the derivative 0 where the floor holds.
+ * Parity: pinned by the neutral closed form (maximum 4 k u* H_z / 27 at H_z / 3), the
+ * stable and unstable factors, and the derivative against central differences. */
+void oracle_kz_eq3(double ustar, double inv_l, double hz, double kz_min, double z, double out[2])
+{
+    const double k = 0.4;
+    double kz = 0.0, dkz = 0.0;
+    if (z > 0.0 && z < hz && ustar > 0.0) {
+        double s = 1.0 - z / hz;
+        double zeta = z * inv_l;
+        double ph = phi_h(zeta);
+        kz = k * ustar * z * s * s / ph;
+        dkz = k * ustar * (s * s - 2.0 * z * s / hz) / ph - kz * dphi_h(zeta) * inv_l / ph;
+    }
+    if (kz < kz_min) {
+        kz = kz_min;
+        dkz = 0.0;
+    }
+    out[0] = kz;
+    out[1] = dkz;
+}
+
+/* Boundary-layer columns at (x, y, t): u*, 1/L and H_z, each bilinear in x, y and linear
+ * in t with the weather's cell rules (1/L rather than L, so that the field passes through
+ * neutral smoothly). */
+static void bl_interp(const ocfg *c, double x, double y, double t, double v[3])
+{
+    int i, j, h0, h1;
+    double a, b, f;
+    axis_uniform(x, c->x0, c->dx, c->nx, &i, &a);
+    axis_uniform(y, c->y0, c->dy, c->ny, &j, &b);
+    axis_time(c, t, &h0, &h1, &f);
+    v[0] = v[1] = v[2] = 0.0;
+    for (int dh = 0; dh < 2; ++dh) {
+        double wt = dh ? f : 1.0 - f;
+        for (int dj = 0; dj < 2; ++dj) {
+            double wy = dj ? b : 1.0 - b;
+            for (int di = 0; di < 2; ++di) {
+                double wx = di ? a : 1.0 - a;
+                size_t col = ((size_t)(dh ? h1 : h0) * c->ny + (j + dj)) * c->nx + (i + di);
+                for (int q = 0; q < 3; ++q) v[q] += wt * wy * wx * (double)c->bl[4 * col + q];
+            }
+        }
+    }
+}
+
 /* Weather at (x, y, z, t): out = (u, v, w, K_z, K_h, dK_z/dz). K values clamped >= 0.
- * dK_z/dz is the z-derivative of the multilinear K_z (0 outside the level range). */
+ * dK_z/dz is the z-derivative of the multilinear K_z (0 outside the level range); with
+ * kz_model 1, K_z and its derivative come from Eq. 3 on the interpolated columns. */
 void oracle_interp(const ocfg *c, double x, double y, double z, double t, double out[6])
 {
     int i, j, k, h0, h1;
@@ -303,6 +369,13 @@ void oracle_interp(const ocfg *c, double x, double y, double z, double t, double
     out[3] = acc[3] > 0.0 ? acc[3] : 0.0;
     out[4] = c->kh ? (kh > 0.0 ? kh : 0.0) : (c->kh_uniform > 0.0 ? c->kh_uniform : 0.0);
     out[5] = inside ? (kz_hi - kz_lo) / dz : 0.0;
+    if (c->kz_model == 1 && c->bl) {
+        double col[3], kz[2];
+        bl_interp(c, x, y, t, col);
+        oracle_kz_eq3(col[0], col[1], col[2], c->kz_min, z, kz);
+        out[3] = kz[0];
+        out[5] = kz[1];
+    }
 }
 
 /* Deposition thresholds: the probability of an event in one step, as a 32-bit integer

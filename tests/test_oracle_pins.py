@@ -464,3 +464,96 @@ def test_dosage_is_the_sum_of_the_snapshots():
     np.testing.assert_allclose(whole["dose_fixed"] * ulp, total, rtol=0.0, atol=1600 * ulp)
     assert out > 0
     assert whole["dose_out"] * ulp == pytest.approx(out, rel=0, abs=1600 * ulp)
+
+
+# ------------------------------------------------------------------------------------
+# K_z from Eq. 3 in the step (k u* z (1 - z/H_z)^2 / Phi_h(z/L), Sec. 2)
+# ------------------------------------------------------------------------------------
+def test_kz_eq3_closed_forms():
+    """Neutral (1/L = 0): K_z = k u* z (1 - z/H)^2 with its maximum 4 k u* H / 27 at
+    z = H/3; stable and unstable layers scale it by 1/(1 + 5 z/L) and (1 - 16 z/L)^(1/2);
+    zero (then the floor) at and above H_z and at the ground. Catches a wrong von Karman
+    constant, exponent, sign of the stability correction or a missing cut at H_z."""
+    k, u, H, kmin = 0.4, 0.37, 900.0, 1e-3
+    kz, dkz = oracle.kz_eq3(u, 0.0, H, kmin, H / 3.0)
+    assert kz == pytest.approx(4.0 * k * u * H / 27.0, rel=1e-12)
+    assert abs(dkz) < 1e-9
+    rng = np.random.default_rng(5)
+    for z in rng.uniform(1.0, H - 1.0, 20):
+        neutral = k * u * z * (1.0 - z / H) ** 2
+        assert oracle.kz_eq3(u, 0.0, H, kmin, z)[0] == pytest.approx(max(kmin, neutral),
+                                                                      rel=1e-12)
+        for inv_l in (0.004, 0.02):
+            assert oracle.kz_eq3(u, inv_l, H, kmin, z)[0] == pytest.approx(
+                max(kmin, neutral / (1.0 + 5.0 * z * inv_l)), rel=1e-12)
+            assert oracle.kz_eq3(u, -inv_l, H, kmin, z)[0] == pytest.approx(
+                max(kmin, neutral * math.sqrt(1.0 + 16.0 * z * inv_l)), rel=1e-12)
+    for z in (H, H + 50.0, 0.0):
+        assert oracle.kz_eq3(u, 0.0, H, 0.25, z) == (0.25, 0.0)
+
+
+def test_kz_eq3_derivative_against_differences():
+    """dK_z/dz (the drift term) against central differences of K_z, in stable, neutral
+    and unstable layers. Catches a dropped product-rule term or a wrong Phi_h derivative."""
+    rng = np.random.default_rng(6)
+    for _ in range(60):
+        u = rng.uniform(0.1, 0.8)
+        inv_l = rng.uniform(-0.04, 0.04)
+        H = rng.uniform(300.0, 2000.0)
+        z = rng.uniform(0.02, 0.98) * H
+        if abs(z * inv_l) < 1e-6:
+            continue
+        h = 1e-4 * H
+        fd = (oracle.kz_eq3(u, inv_l, H, 0.0, z + h)[0] -
+              oracle.kz_eq3(u, inv_l, H, 0.0, z - h)[0]) / (2 * h)
+        # central-difference truncation ~ h^2 K'''/6 ~ 1e-8 k u*
+        assert oracle.kz_eq3(u, inv_l, H, 0.0, z)[1] == pytest.approx(fd, rel=1e-6,
+                                                                       abs=1e-7 * 0.4 * u)
+
+
+def _bl_column(u, inv_l, H, n_t=2, nx=2, ny=2):
+    bl = np.zeros((n_t, ny, nx, 4), np.float32)
+    bl[..., 0], bl[..., 1], bl[..., 2] = u, inv_l, H
+    return bl
+
+
+def test_kz_eq3_columns_interpolated_like_the_weather():
+    """With 1/L = 0, K_z is linear in u*: a u* field linear in x, y and t must give
+    K_z = k u*(x, y, t) z (1 - z/H)^2 exactly (bilinear-in-space, linear-in-time
+    interpolation of the columns)."""
+    cfg = li.make_cfg0(n_particles=10, n_steps=10)
+    bl = _bl_column(0.0, 0.0, 800.0)
+    a0, ax, ay, at = 0.3, 1e-5, -2e-5, 3e-6
+    for h in range(2):
+        for j in range(2):
+            for i in range(2):
+                bl[h, j, i, 0] = a0 + ax * (cfg.x0 + i * cfg.dx) + ay * (cfg.y0 + j * cfg.dy) \
+                    + at * (cfg.met_t0 + h * cfg.met_dt)
+    cfg = dataclasses.replace(cfg, kz_model=1, kz_min=0.0, bl=bl)
+    rng = np.random.default_rng(7)
+    pts = np.stack([rng.uniform(cfg.x0, cfg.x0 + cfg.dx, 50), rng.uniform(cfg.y0, cfg.y0 + cfg.dy, 50),
+                    rng.uniform(1.0, 799.0, 50), rng.uniform(0.0, cfg.met_dt, 50)], axis=1)
+    got = oracle.interp(cfg, pts)
+    ustar = (a0 + ax * pts[:, 0] + ay * pts[:, 1] + at * pts[:, 3]).astype(np.float32)
+    # the columns hold float32 values; compare with the float32-rounded field tolerance
+    want = 0.4 * ustar.astype(np.float64) * pts[:, 2] * (1.0 - pts[:, 2] / 800.0) ** 2
+    np.testing.assert_allclose(got[:, 3], want, rtol=2e-6)
+
+
+@pytest.mark.parametrize("inv_l", [0.0, 0.02, -0.02])
+def test_kz_eq3_drift_keeps_a_column_well_mixed(inv_l):
+    """A reflecting 100 m column under Eq. 3 (K_z from ~0 at the ground): with the drift
+    term the uniform state is stationary (KS uniform); in the neutral case the walk
+    without it piles particles up where K_z is small (rejected)."""
+    H = 100.0
+    cfg = li.make_cfg0(n_particles=8000, n_steps=2000, kh=0.0, kz=0.0, u=0.0, src=(0.0, 0.0, 50.0))
+    cfg = dataclasses.replace(cfg, dt=2.0, reflect_top=1, z_top=H, kz_model=1, kz_min=0.1,
+                              bl=_bl_column(0.5, inv_l, 1000.0),
+                              release=li.Release(8000, np.array([1.0]), 3600.0, 0, 10))
+    for drift in ((1, 0) if inv_l == 0.0 else (1,)):
+        z = oracle.run(dataclasses.replace(cfg, drift_correction=drift))["pos"][:, 2]
+        p = stats.kstest(z / H, "uniform").pvalue
+        if drift:
+            assert p > 1e-3, p
+        else:
+            assert p < 1e-6, p
