@@ -99,6 +99,9 @@ def lib():
         L.oracle_initial_mass.argtypes = [C.POINTER(OCfg), C.c_int64]
         L.oracle_initial_mass.restype = C.c_double
         L.oracle_kz_eq3.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
+        L.oracle_kz_eq3_partials.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
+        L.oracle_interp_grad_many.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_double), C.c_int64,
+                                              C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.oracle_threshold.argtypes = [C.c_double]
         L.oracle_threshold.restype = C.c_uint32
         L.oracle_run.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_int64), C.c_int64, C.c_int64,
@@ -232,6 +235,18 @@ def interp(cfg, xyzt, **kw) -> np.ndarray:
     return out
 
 
+def interp_grad(cfg, xyzt, **kw):
+    """(values [N][5] = (u, v, w, K_z, K_h), gradients [N][5][3] in x, y, z) of the
+    interpolated weather, as the tangent-linear model uses them."""
+    o = make_ocfg(cfg, **kw)
+    pts = np.ascontiguousarray(xyzt, dtype=np.float64).reshape(-1, 4)
+    val = np.empty((pts.shape[0], 5))
+    grad = np.empty((pts.shape[0], 5, 3))
+    lib().oracle_interp_grad_many(C.byref(o), _ptr(pts, C.c_double), pts.shape[0],
+                                  _ptr(val, C.c_double), _ptr(grad, C.c_double))
+    return val, grad
+
+
 def release_steps(n: int, first: int, last: int, p) -> np.ndarray:
     p = np.ascontiguousarray(p, dtype=np.int64)
     out = np.empty_like(p)
@@ -248,6 +263,14 @@ def kz_eq3(ustar: float, inv_l: float, hz: float, kz_min: float, z: float):
     out = (C.c_double * 2)()
     lib().oracle_kz_eq3(float(ustar), float(inv_l), float(hz), float(kz_min), float(z), out)
     return float(out[0]), float(out[1])
+
+
+def kz_eq3_partials(ustar: float, inv_l: float, hz: float, kz_min: float, z: float):
+    """(K_z, dK/dz, dK/du*, dK/d(1/L), dK/dH_z, d2K/dz2) of Eq. 3 at height z."""
+    out = (C.c_double * 6)()
+    lib().oracle_kz_eq3_partials(float(ustar), float(inv_l), float(hz), float(kz_min), float(z),
+                                 out)
+    return tuple(float(v) for v in out)
 
 
 def threshold(p: float) -> int:
@@ -342,13 +365,14 @@ def adjoint(cfg, rec, sigma: float, every: int, w, sel=None, n_run: Optional[int
 
 
 def sensitivity(cfg, sel=None, n_run: Optional[int] = None, **kw) -> np.ndarray:
-    """Per particle [n][2]: the largest norms of d X_end / d (x_k, y_k) and of
-    d X_end / d z_k over its steps k (finite-time perturbation growth)."""
+    """Per particle [n][4]: the largest norms of d X_end / d (x_k, y_k) and of
+    d X_end / d z_k over its steps k (finite-time perturbation growth), then the sums over
+    k of their squares."""
     o = make_ocfg(cfg, **kw)
     n_run = cfg.n_steps if n_run is None else n_run
     sel_a = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     n = int(o.n_particles) if sel_a is None else sel_a.size
-    out = np.zeros((n, 2))
+    out = np.zeros((n, 4))
     rc = lib().oracle_sensitivity(C.byref(o), _ptr(sel_a, C.c_int64), 0 if sel_a is None else n,
                                   int(n_run), _ptr(out, C.c_double))
     if rc:
@@ -357,10 +381,11 @@ def sensitivity(cfg, sel=None, n_run: Optional[int] = None, **kw) -> np.ndarray:
 
 
 def chaotic(cfg, sens: np.ndarray, pos: np.ndarray, pos_tol: float) -> np.ndarray:
-    """Paths on which a single FP32 rounding of the state (2^-24 of its magnitude) can grow
-    past the position tolerance by the end of the run: their FP32 and FP64 realisations
-    are not expected to stay within the tolerance."""
+    """Paths on which the FP32 roundings of the state (2^-24 of its magnitude, one per
+    step, independent) grown to the end of the run add up, as a random walk, past the
+    position tolerance: their FP32 and FP64 realisations are not expected to stay within
+    it. Needs the summed squared growths of ``sensitivity``."""
     eps = 2.0 ** -24
     rh = np.maximum(np.abs(pos[:, 0]), np.abs(pos[:, 1]))
     rz = np.maximum(pos[:, 2], 1.0)
-    return eps * (sens[:, 0] * rh + sens[:, 1] * rz) > pos_tol
+    return eps * np.sqrt(sens[:, 2] * rh ** 2 + sens[:, 3] * rz ** 2) > pos_tol

@@ -298,28 +298,75 @@ void oracle_kz_eq3(double ustar, double inv_l, double hz, double kz_min, double 
     out[1] = dkz;
 }
 
+/* Partial derivatives of Eq. 3 at height z: out = (K_z, dK/dz, dK/du*, dK/d(1/L),
+ * dK/dH_z, d2K/dz2), all but K_z zero where the floor holds (for the tangent-linear
+ * model). With N = k u* z s^2 (s = 1 - z/H_z) and Phi(z) = Phi_h(z/L):
+ * K'' = N''/Phi - 2 N' Phi'/Phi^2 - N Phi''/Phi^2 + 2 N Phi'^2/Phi^3. */
+void oracle_kz_eq3_partials(double ustar, double inv_l, double hz, double kz_min, double z,
+                            double out[6])
+{
+    double kz[2];
+    oracle_kz_eq3(ustar, inv_l, hz, kz_min, z, kz);
+    out[0] = kz[0];
+    out[1] = kz[1];
+    out[2] = out[3] = out[4] = out[5] = 0.0;
+    if (z > 0.0 && z < hz && ustar > 0.0) {
+        double s = 1.0 - z / hz, zeta = z * inv_l, ph = phi_h(zeta);
+        double a = 0.4 * ustar;
+        double raw = a * z * s * s / ph;
+        if (raw >= kz_min) {
+            out[2] = raw / ustar;
+            out[3] = -raw * z * dphi_h(zeta) / ph;
+            out[4] = 2.0 * a * z * z * s / (hz * hz * ph);
+            double n0 = a * z * s * s, n1 = a * (s * s - 2.0 * z * s / hz);
+            double n2 = a * (-4.0 * s / hz + 2.0 * z / (hz * hz));
+            double p1 = inv_l * dphi_h(zeta);
+            double p2 = zeta >= 0.0 ? 0.0 : inv_l * inv_l * 192.0 * pow(ph, 5.0);
+            out[5] = n2 / ph - 2.0 * n1 * p1 / (ph * ph) - n0 * p2 / (ph * ph) +
+                     2.0 * n0 * p1 * p1 / (ph * ph * ph);
+        }
+    }
+}
+
 /* Boundary-layer columns at (x, y, t): u*, 1/L and H_z, each bilinear in x, y and linear
  * in t with the weather's cell rules (1/L rather than L, so that the field passes through
- * neutral smoothly). */
-static void bl_interp(const ocfg *c, double x, double y, double t, double v[3])
+ * neutral smoothly); g (may be NULL) receives d/dx and d/dy of each. */
+static void bl_interp_grad(const ocfg *c, double x, double y, double t, double v[3],
+                           double g[3][2])
 {
     int i, j, h0, h1;
     double a, b, f;
     axis_uniform(x, c->x0, c->dx, c->nx, &i, &a);
     axis_uniform(y, c->y0, c->dy, c->ny, &j, &b);
     axis_time(c, t, &h0, &h1, &f);
+    double fx = (x - c->x0) / c->dx, fy = (y - c->y0) / c->dy;
+    int in_x = fx >= 0.0 && fx <= (double)(c->nx - 1);
+    int in_y = fy >= 0.0 && fy <= (double)(c->ny - 1);
     v[0] = v[1] = v[2] = 0.0;
+    if (g) memset(g, 0, sizeof(double) * 6);
     for (int dh = 0; dh < 2; ++dh) {
         double wt = dh ? f : 1.0 - f;
         for (int dj = 0; dj < 2; ++dj) {
-            double wy = dj ? b : 1.0 - b;
+            double wy = dj ? b : 1.0 - b, gy = in_y ? (dj ? 1.0 : -1.0) / c->dy : 0.0;
             for (int di = 0; di < 2; ++di) {
-                double wx = di ? a : 1.0 - a;
+                double wx = di ? a : 1.0 - a, gx = in_x ? (di ? 1.0 : -1.0) / c->dx : 0.0;
                 size_t col = ((size_t)(dh ? h1 : h0) * c->ny + (j + dj)) * c->nx + (i + di);
-                for (int q = 0; q < 3; ++q) v[q] += wt * wy * wx * (double)c->bl[4 * col + q];
+                for (int q = 0; q < 3; ++q) {
+                    double val = (double)c->bl[4 * col + q];
+                    v[q] += wt * wy * wx * val;
+                    if (g) {
+                        g[q][0] += wt * wy * gx * val;
+                        g[q][1] += wt * gy * wx * val;
+                    }
+                }
             }
         }
     }
+}
+
+static void bl_interp(const ocfg *c, double x, double y, double t, double v[3])
+{
+    bl_interp_grad(c, x, y, t, v, NULL);
 }
 
 /* Weather at (x, y, z, t): out = (u, v, w, K_z, K_h, dK_z/dz). K values clamped >= 0.
@@ -800,10 +847,28 @@ static void interp_grad(const ocfg *c, double x, double y, double z, double t, d
             acc[q] = 0.0;
             g[q][0] = g[q][1] = g[q][2] = 0.0;
         }
+    if (c->kz_model == 1 && c->bl) {
+        /* K_z from Eq. 3: chain rule through the interpolated columns */
+        double col[3], gc[3][2], pk[6];
+        bl_interp_grad(c, x, y, t, col, gc);
+        oracle_kz_eq3_partials(col[0], col[1], col[2], c->kz_min, z, pk);
+        acc[3] = pk[0];
+        g[3][2] = pk[1];
+        for (int d = 0; d < 2; ++d) g[3][d] = pk[2] * gc[0][d] + pk[3] * gc[1][d] + pk[4] * gc[2][d];
+    }
     for (int q = 0; q < 5; ++q) {
         val[q] = acc[q];
         for (int d = 0; d < 3; ++d) grad[q][d] = g[q][d];
     }
+}
+
+/* interp_grad at n points (x, y, z, t): val [n][5], grad [n][5][3] (for the pins). */
+void oracle_interp_grad_many(const ocfg *c, const double *xyzt, int64_t n, double *val,
+                             double *grad)
+{
+    for (int64_t i = 0; i < n; ++i)
+        interp_grad(c, xyzt[4 * i], xyzt[4 * i + 1], xyzt[4 * i + 2], xyzt[4 * i + 3], val + 5 * i,
+                    (double(*)[3])(grad + 15 * i));
 }
 
 /* Derivatives of one step X_old -> X_new: J[r][d] = dX_new[r] / dX_old[d] and
@@ -824,6 +889,14 @@ static void step_jacobian(const ocfg *c, const double X[3], int64_t k, const dou
         J[0][d] = (d == 0 ? 1.0 : 0.0) + dt * g[0][d] + nrm[0] * dsh[d];
         J[1][d] = (d == 1 ? 1.0 : 0.0) + dt * g[1][d] + nrm[1] * dsh[d];
         J[2][d] = fold * ((d == 2 ? 1.0 : 0.0) + dt * g[2][d] + nrm[2] * dsz[d]);
+    }
+    if (c->drift_correction && c->kz_model == 1 && c->bl) {
+        /* the drift term s_K K_z'(z) dt: its vertical derivative (the gridded K_z is
+         * piecewise linear in z, so there it vanishes inside the cells) */
+        double col[3], pk[6];
+        bl_interp(c, X[0], X[1], (double)k * c->dt, col);
+        oracle_kz_eq3_partials(col[0], col[1], col[2], c->kz_min, X[2], pk);
+        J[2][2] += fold * sk * dt * pk[5];
     }
     T[0][0] = nrm[0] * sig_h / (2.0 * sk);
     T[1][0] = nrm[1] * sig_h / (2.0 * sk);
@@ -990,24 +1063,27 @@ int oracle_adjoint(const ocfg *c, const double *rec, int R, double sigma, int ev
 }
 
 /* Finite-time growth of perturbations along each particle's path up to step n_run:
- * out[2q] = max over steps k of the Frobenius norm of d X_end / d (x_k, y_k) and
- * out[2q+1] = max over k of the norm of d X_end / d z_k (reverse products of the step
- * Jacobians). A one-ulp difference in the state at step k can reach these factors times
- * the ulp at the end; the parity tests use them to recognise chaotic paths. */
+ * out[4q] = max over steps k of the Frobenius norm of d X_end / d (x_k, y_k),
+ * out[4q+1] = max over k of the norm of d X_end / d z_k (reverse products of the step
+ * Jacobians), out[4q+2], out[4q+3] = the sums over k of their squares. A one-ulp
+ * difference in the state at step k can reach these factors times the ulp at the end;
+ * independent roundings at every step add up like a random walk, sqrt of the sums. The
+ * parity tests use them to recognise chaotic paths. */
 int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, double *out)
 {
-    if (c->drift_correction) return 1;
     const ostep K = step_constants(c);
     int64_t n = sel ? n_sel : c->n_particles;
     for (int64_t q = 0; q < n; ++q) {
         int64_t p = sel ? sel[q] : q;
         opath o;
         if (trace_particle(c, &K, p, n_run, &o)) return 2;
-        out[2 * q] = 1.0;
-        out[2 * q + 1] = 1.0;
+        out[4 * q] = 1.0;
+        out[4 * q + 1] = 1.0;
+        out[4 * q + 2] = 0.0;
+        out[4 * q + 3] = 0.0;
         if (o.status == OR_UNRELEASED) continue;
         double M[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-        double best_h = 1.4142135623730951, best_z = 1.0;
+        double best_h = 1.4142135623730951, best_z = 1.0, sum_h = 0.0, sum_z = 0.0;
         for (int64_t k = o.kend; k >= o.sp; --k) {
             const size_t s = (size_t)(k - o.sp);
             double J[3][3], T[3][3], N[3][3];
@@ -1025,9 +1101,13 @@ int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t
             }
             if (sqrt(fh) > best_h) best_h = sqrt(fh);
             if (sqrt(fz) > best_z) best_z = sqrt(fz);
+            sum_h += fh;
+            sum_z += fz;
         }
-        out[2 * q] = best_h;
-        out[2 * q + 1] = best_z;
+        out[4 * q] = best_h;
+        out[4 * q + 1] = best_z;
+        out[4 * q + 2] = sum_h;
+        out[4 * q + 3] = sum_z;
         free_path(&o);
     }
     return 0;

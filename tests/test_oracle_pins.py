@@ -557,3 +557,44 @@ def test_kz_eq3_drift_keeps_a_column_well_mixed(inv_l):
             assert p > 1e-3, p
         else:
             assert p < 1e-6, p
+
+
+def test_kz_eq3_gradient_of_the_tangent_linear_model():
+    """The x, y, z gradient of K_z that the tangent-linear model (adjoint, sensitivity)
+    uses, against central differences of the interpolated Eq. 3 K_z on the realistic
+    boundary-layer columns. Catches a missing chain-rule term through u*, 1/L or H_z."""
+    cfg = li.make_cfg1(n_particles=10, n_steps=240, n_hours=3, kz_eq3=True)
+    cfg = dataclasses.replace(cfg, kz_min=0.0)
+    rng = np.random.default_rng(8)
+    n = 200
+    pts = np.stack([rng.uniform(1000.0, 48000.0, n), rng.uniform(1000.0, 48000.0, n),
+                    rng.uniform(5.0, 300.0, n), rng.uniform(0.0, 7000.0, n)], axis=1)
+    val, grad = oracle.interp_grad(cfg, pts)
+    np.testing.assert_allclose(val[:, 3], oracle.interp(cfg, pts)[:, 3], rtol=1e-12)
+    for d, h in enumerate((1e-2, 1e-2, 1e-3)):
+        e = np.zeros(4)
+        e[d] = h
+        fd = (oracle.interp(cfg, pts + e)[:, 3] - oracle.interp(cfg, pts - e)[:, 3]) / (2 * h)
+        # cell faces (kinks of the bilinear columns) within h are skipped
+        f = (pts[:, d] - (0.0 if d < 2 else 0.0)) / 250.0
+        ok = np.abs(f - np.round(f)) * 250.0 > 2 * h if d < 2 else np.ones(n, bool)
+        np.testing.assert_allclose(grad[ok, 3, d], fd[ok], rtol=1e-5, atol=1e-9)
+
+
+def test_kz_eq3_second_derivative_and_partials():
+    """d2K_z/dz2 (the drift term's derivative in the tangent-linear model) and the
+    partials in u*, 1/L, H_z against central differences of Eq. 3."""
+    rng = np.random.default_rng(10)
+    for _ in range(60):
+        u, inv_l, H = rng.uniform(0.1, 0.8), rng.uniform(-0.04, 0.04), rng.uniform(300.0, 2000.0)
+        z = rng.uniform(0.05, 0.95) * H
+        p = oracle.kz_eq3_partials(u, inv_l, H, 0.0, z)
+        h = 1e-4 * H
+        fd2 = (oracle.kz_eq3(u, inv_l, H, 0.0, z + h)[1] -
+               oracle.kz_eq3(u, inv_l, H, 0.0, z - h)[1]) / (2 * h)
+        assert p[5] == pytest.approx(fd2, rel=1e-5, abs=1e-7 * 0.4 * u / H)
+        for idx, (du, args) in enumerate([(1e-6, lambda e: (u + e, inv_l, H)),
+                                          (1e-7, lambda e: (u, inv_l + e, H)),
+                                          (1e-3, lambda e: (u, inv_l, H + e))]):
+            fd = (oracle.kz_eq3(*args(du), 0.0, z)[0] - oracle.kz_eq3(*args(-du), 0.0, z)[0]) / (2 * du)
+            assert p[2 + idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
