@@ -374,6 +374,39 @@ def measure_dosage(args, stream):
             "steps_per_run": cfg.n_steps}
 
 
+def measure_kz_eq3(args, stream):
+    """The plain realistic run with K_z computed in the step from Eq. 3 on hourly
+    boundary-layer columns (u*, 1/L, H_z) instead of read from the gridded field."""
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_cfg1(kz_eq3=True)
+    with torch.cuda.stream(stream):
+        sim = Sim(cfg, stream=stream, launch=(args.block, 1, args.occ),
+                  sort_every=args.sort_every)
+    try:
+        times = []
+        for i in range(max(1, args.warmup) + 2):
+            sim.reset()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(cfg.n_steps)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= max(1, args.warmup):
+                times.append(e0.elapsed_time(e1))
+        active = int(sim.fixed_state()[2][4])
+    finally:
+        sim.close()
+    ms = statistics.mean(times)
+    return {"value": active / (ms / 1e3), "unit": UNIT, "ms_per_run": ms,
+            "kz": "Eq. 3 in the step (Businger-Dyer Phi_h), hourly u*, 1/L, H_z columns",
+            "particles": cfg.n_particles, "steps_per_run": cfg.n_steps}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -504,7 +537,8 @@ def run_gpu(args):
         forms = {"batched": measure_batched(args, stream),
                  "adjoint": measure_adjoint(args, stream),
                  "inversion": measure_inversion(args, stream),
-                 "dosage": measure_dosage(args, stream)}
+                 "dosage": measure_dosage(args, stream),
+                 "kz_eq3": measure_kz_eq3(args, stream)}
         if not args.no_stress:
             forms["stress"] = measure_stress(args, stream)
         for f in forms.values():
@@ -535,7 +569,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms")
     ap.add_argument("--no-stress", action="store_true", help="skip the 1e8-particle stress case")
-    ap.add_argument("--only", choices=["batched", "adjoint", "inversion", "stress", "dosage"],
+    ap.add_argument("--only", choices=["batched", "adjoint", "inversion", "stress", "dosage",
+                                       "kz_eq3"],
                     default=None,
                     help="run one form alone and print its measurement (profiling aid)")
     ap.add_argument("--batched-block", type=int, default=256)
@@ -553,7 +588,7 @@ def main():
         stream = torch.cuda.Stream()
         fn = {"batched": measure_batched, "adjoint": measure_adjoint,
               "inversion": measure_inversion, "stress": measure_stress,
-              "dosage": measure_dosage}[args.only]
+              "dosage": measure_dosage, "kz_eq3": measure_kz_eq3}[args.only]
         print(json.dumps({"form": args.only, **fn(args, stream)}), flush=True)
         return 0
     return run_gpu(args)

@@ -219,6 +219,26 @@ lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int
 lpm_status lpm_set_sort(lpm_ctx *ctx, int every_steps);
 
 /*
+ * K_z inside the step from Eq. 3 (Sec. 2): K_z(z) = k u* z (1 - z/H_z)^2 / Phi_h(z/L),
+ * k = 0.4, for 0 < z < H_z and 0 elsewhere, floored at kz_min (m^2/s). The paper leaves
+ * Phi_h open: the Businger-Dyer forms 1 + 5 z/L (stable) and (1 - 16 z/L)^(-1/2)
+ * (unstable) are used. u*, 1/L and H_z are hourly column fields on the met grid's (y, x)
+ * nodes, interpolated like the weather (bilinear in x, y, linear in t); with
+ * drift_correction the drift term is the analytic dK_z/dz. The K_z component of the
+ * weather records is then ignored.
+ *
+ * lpm_set_kz_model: model 0 = the gridded K_z of lpm_set_met (default), 1 = Eq. 3
+ * (allocates the column buffers: 48 bytes per column and hour). Model 1 runs with one
+ * particle per thread and is not supported by lpm_adjoint (LPM_E_INVALID).
+ * lpm_set_boundary_layer: hour t_index of the columns, bl [ny][nx][4] float =
+ * (u* (m/s) >= 0, 1/L (1/m), H_z (m) > 0, unused), host memory (validated, copied before
+ * return) or device memory (on_device != 0, read on the context stream, not validated).
+ * Every hour a step touches must be set (LPM_E_STATE otherwise).
+ */
+lpm_status lpm_set_kz_model(lpm_ctx *ctx, int model, double kz_min);
+lpm_status lpm_set_boundary_layer(lpm_ctx *ctx, int t_index, const float *bl, int on_device);
+
+/*
  * Time-integrated concentration ("dosage"): the paper sums the decayed masses on the grid
  * every n-th step, n >= 4, and integrates the snapshots in time as a post-processing
  * (Sec. 3.2), which it notes the GPU could do in a separate kernel (Sec. 4.2). Here the

@@ -92,10 +92,14 @@ __device__ __forceinline__ void warp_count_scen(int s, unsigned long long v, int
 }
 
 // Weather at a point from the time-paired records: 8 spatial corners, each one 32-byte
-// load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z.
+// load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z. With KZ3, K_z
+// and its derivative come from Eq. 3 on the boundary-layer columns (4 more 32-byte loads
+// of the time-paired (u*, 1/L, H_z) at the cell's corner columns, bilinear in x, y).
+template <bool KZ3>
 __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels &L,
                                                const float4 *__restrict__ pair,
-                                               const float2 *__restrict__ khp, float f,
+                                               const float2 *__restrict__ khp,
+                                               const float4 *__restrict__ blp, float f,
                                                float x, float y, float z)
 {
     int i, j, k;
@@ -120,9 +124,22 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
     m.u = r.x;
     m.v = r.y;
     m.w = r.z;
-    m.kz = fmaxf(r.w, 0.0f);
-    const bool inside = z >= L.z[0] && z <= L.z[P.nz - 1];
-    m.dkz = inside ? (y1.w - y0.w) * L.inv[k] : 0.0f;
+    if (KZ3) {
+        float4 cq[4];
+#pragma unroll
+        for (int mm = 0; mm < 4; ++mm) {
+            float4 lo, dt;
+            ld_pair(blp + 2 * ((j + ((mm >> 1) & 1)) * P.nx + i + (mm & 1)), lo, dt);
+            cq[mm] = tlerp4(lo, dt, f);
+        }
+        const float4 c0 = lerp4(cq[0], cq[1], a), c1 = lerp4(cq[2], cq[3], a);
+        const float4 col = lerp4(c0, c1, b);
+        kz_eq3(col.x, col.y, col.z, P.kz_min, z, m.kz, m.dkz);
+    } else {
+        m.kz = fmaxf(r.w, 0.0f);
+        const bool inside = z >= L.z[0] && z <= L.z[P.nz - 1];
+        m.dkz = inside ? (y1.w - y0.w) * L.inv[k] : 0.0f;
+    }
     if (khp) {
         float e[8];
 #pragma unroll
@@ -167,6 +184,7 @@ struct StepTime {
     TimeSlab ts;
     const float4 *pair;              // time pair of the step
     const float2 *khp;               // K_h time pair or nullptr
+    const float4 *blp;               // boundary-layer column pair or nullptr
     float du, dv;                    // wind offset of the scenario + bias
 };
 
@@ -178,6 +196,7 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const float2 
     T.ts = time_slab(P, T.tk);
     T.pair = P.pair + (long long)T.ts.h0 * P.slab * 2;
     T.khp = P.khpair ? P.khpair + (long long)T.ts.h0 * P.slab : nullptr;
+    T.blp = P.blpair ? P.blpair + (long long)T.ts.h0 * P.nx * P.ny * 2 : nullptr;
     T.du = P.bias_u;
     T.dv = P.bias_v;
     if (wind_offset) {
@@ -194,7 +213,7 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const float2 
 // Updates (x, y, z) and returns the new status. (du, dv) is the wind offset of the
 // particle's scenario plus the bias at t_k. With GRIDS, deposition and exit add their mass
 // to the scenario's grids and counters; *fold receives dz/dz_pre (+-1, 0 when clamped).
-template <bool GRIDS>
+template <bool GRIDS, bool KZ3 = false>
 __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Levels &LV,
                                                   const StepTime &T, const ScenDev &sc,
                                                   const ScenDev *scg, unsigned long long gid,
@@ -203,7 +222,7 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
 {
     const int k = T.k;
     // 1. weather at the old position and t_k; 2. diffusivities
-    const Met m = sample_met_pair(P, LV, T.pair, T.khp, T.ts.f, x, y, z);
+    const Met m = sample_met_pair<KZ3>(P, LV, T.pair, T.khp, T.blp, T.ts.f, x, y, z);
     const float sig_h = T.khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
     const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
     // 3. N(0,1) draws
@@ -283,8 +302,8 @@ struct MinBlocks {
 // lanes of a tile may belong to different scenarios (the sorted particles of a batched
 // context): each lane finds its scenario from its home slot and carries its own wind
 // offset; the results are bit-identical to the per-scenario path. DOSE adds the dosage
-// samples (every P.dose_every steps) inside the time loop.
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE>
+// samples (every P.dose_every steps) inside the time loop; KZ3 takes K_z from Eq. 3.
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE, bool KZ3>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
                int k1, int do_bin)
@@ -420,12 +439,13 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                         du = P.bias_u + fmaf(T.ts.f, o1[j].x - o0[j].x, o0[j].x);
                         dv = P.bias_v + fmaf(T.ts.f, o1[j].y - o0[j].y, o0[j].y);
                     }
-                    st = particle_step<true>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j], sp,
-                                             sig_h_uniform, du, dv, x[j], y[j], z[j], nullptr);
+                    st = particle_step<true, KZ3>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
+                                                  sp, sig_h_uniform, du, dv, x[j], y[j], z[j],
+                                                  nullptr);
                 } else {
                     ++steps;
-                    st = particle_step<true>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform, T.du,
-                                             T.dv, x[j], y[j], z[j], nullptr);
+                    st = particle_step<true, KZ3>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
+                                                  T.du, T.dv, x[j], y[j], z[j], nullptr);
                 }
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;
@@ -515,55 +535,59 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
     }
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE, bool KZ3>
 cudaError_t launch_adv(const AdvanceLaunch &L)
 {
-    advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE><<<L.grid, BLOCK, 0, L.stream>>>(
+    advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE, KZ3><<<L.grid, BLOCK, 0, L.stream>>>(
         *L.params, L.ranges, L.n_tiles(), L.queue, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE, bool KZ3>
 int occ_adv()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE>,
-                                                  BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE, KZ3>, BLOCK, 0);
     return n;
 }
 
-// (particles per thread, occupancy variant, mixed scenarios, dosage) -> instantiation, for
-// one block size
-#define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, DOS, ...)                               \
-    case PPT * 1000 + OCC * 100 + MIX * 10 + DOS:                                      \
-        return FN<BLOCK, PPT, OCC, (MIX != 0), (DOS != 0)>(__VA_ARGS__);
-#define LPM_ADV_CASES2(FN, BLOCK, PPT, OCC, ...)                                       \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 0, __VA_ARGS__)                               \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 0, __VA_ARGS__)                               \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 1, __VA_ARGS__)                               \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 1, __VA_ARGS__)
+// (particles per thread, occupancy variant, mixed scenarios, dosage, Eq. 3 K_z) ->
+// instantiation, for one block size; Eq. 3 K_z is instantiated for 1 particle per thread
+#define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, DOS, KZ, ...)                           \
+    case PPT * 10000 + OCC * 1000 + MIX * 100 + DOS * 10 + KZ:                         \
+        return FN<BLOCK, PPT, OCC, (MIX != 0), (DOS != 0), (KZ != 0)>(__VA_ARGS__);
+#define LPM_ADV_CASES4(FN, BLOCK, PPT, OCC, KZ, ...)                                   \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 0, KZ, __VA_ARGS__)                           \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 0, KZ, __VA_ARGS__)                           \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 1, KZ, __VA_ARGS__)                           \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 1, KZ, __VA_ARGS__)
 #define LPM_ADV_CASES(FN, BLOCK, ...)                                                  \
-    LPM_ADV_CASES2(FN, BLOCK, 1, 0, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 1, 1, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 1, 2, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 2, 0, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 2, 1, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 2, 2, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 4, 0, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 4, 1, __VA_ARGS__)                                       \
-    LPM_ADV_CASES2(FN, BLOCK, 4, 2, __VA_ARGS__)
+    LPM_ADV_CASES4(FN, BLOCK, 1, 0, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 1, 1, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 1, 2, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 2, 0, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 2, 1, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 2, 2, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 4, 0, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 4, 1, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 4, 2, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 1, 0, 1, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 1, 1, 1, __VA_ARGS__)                                    \
+    LPM_ADV_CASES4(FN, BLOCK, 1, 2, 1, __VA_ARGS__)
 
 #define LPM_ADVANCE_TU(BLOCK)                                                          \
     cudaError_t launch_advance_b##BLOCK(const AdvanceLaunch &L)                         \
     {                                                                                  \
-        switch (L.ppt * 1000 + L.occ * 100 + (L.mixed ? 10 : 0) + (L.dose ? 1 : 0)) {  \
+        switch (L.ppt * 10000 + L.occ * 1000 + (L.mixed ? 100 : 0) + (L.dose ? 10 : 0) + \
+                (L.kz3 ? 1 : 0)) {                                                     \
             LPM_ADV_CASES(launch_adv, BLOCK, L)                                        \
         }                                                                              \
         return cudaErrorInvalidValue;                                                  \
     }                                                                                  \
     int occupancy_b##BLOCK(int ppt, int occ, bool mixed)                               \
     {                                                                                  \
-        switch (ppt * 1000 + occ * 100 + (mixed ? 10 : 0)) {                           \
+        switch (ppt * 10000 + occ * 1000 + (mixed ? 100 : 0)) {                        \
             LPM_ADV_CASES(occ_adv, BLOCK)                                              \
         }                                                                              \
         return 0;                                                                      \

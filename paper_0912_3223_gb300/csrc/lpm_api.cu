@@ -57,6 +57,12 @@ struct lpm_ctx {
     uint8_t *d_rain = nullptr;
     std::vector<char> met_set;
     bool any_rain = false;
+    // boundary-layer columns for K_z from Eq. 3
+    int kz_model = 0;                       // 0: gridded K_z, 1: Eq. 3
+    double kz_min = 0.1;
+    float4 *d_bl = nullptr;                 // [n_t][ny][nx] (u*, 1/L, H_z, 0) as given
+    float4 *d_blpair = nullptr;             // [n_pair][ny][nx][2] value + difference
+    std::vector<char> bl_set;
 
     // particles and outputs
     float4 *d_state = nullptr;
@@ -287,6 +293,8 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.dose_all = c->d_dose;
     P.dose_every = c->d_dose ? c->dose_every : 0;
     P.dose_mul = std::ldexp(1.0f, -c->dose_bits);
+    P.blpair = c->kz_model == 1 ? c->d_blpair : nullptr;
+    P.kz_min = (float)c->kz_min;
     P.err = c->d_err;
 }
 
@@ -694,7 +702,7 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
                     c->d_rgrad, c->d_adj_tiles, c->d_sorted[0], c->d_sorted[1], c->d_pidx[0],
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
-                    c->d_grave, c->d_grave_n, c->d_dose};
+                    c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -966,6 +974,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.occ = c->occ;
         L.mixed = batched;
         L.dose = P.dose_every > 0;
+        L.kz3 = P.blpair != nullptr;
         const int n_tiles = L.n_tiles();
         if (n_tiles <= 0) continue;
         if (batched) {
@@ -1013,10 +1022,15 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
         long long h_b = (long long)std::floor((t_b - g.met_t0) / g.met_dt) + 1;
         h_a = std::max(0LL, std::min(h_a, (long long)g.n_met_t - 1));
         h_b = std::max(0LL, std::min(h_b, (long long)g.n_met_t - 1));
-        for (long long h = h_a; h <= h_b; ++h)
+        for (long long h = h_a; h <= h_b; ++h) {
             if (!c->met_set[(size_t)h])
                 return fail(c, LPM_E_STATE, "met slab %lld not set", h);
+            if (c->kz_model == 1 && !c->bl_set[(size_t)h])
+                return fail(c, LPM_E_STATE, "boundary-layer slab %lld not set", h);
+        }
     }
+    if (c->kz_model == 1 && c->ppt != 1)
+        return fail(c, LPM_E_INVALID, "K_z from Eq. 3 runs with 1 particle per thread");
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
     if (!c->tiles_valid) {
@@ -1302,6 +1316,60 @@ lpm_status lpm_set_sort(lpm_ctx *c, int every_steps)
     return LPM_OK;
 }
 
+lpm_status lpm_set_kz_model(lpm_ctx *c, int model, double kz_min)
+{
+    if (!c) return LPM_E_INVALID;
+    if (model < 0 || model > 1) return fail(c, LPM_E_INVALID, "K_z model must be 0 or 1");
+    if (!is_finite(kz_min) || kz_min < 0) return fail(c, LPM_E_INVALID, "kz_min must be >= 0");
+    const lpm_config &g = c->cfg;
+    if (model == 1 && !c->d_bl) {
+        const size_t cols = (size_t)g.nx * g.ny;
+        const size_t n_pair = (size_t)std::max(1, g.n_met_t - 1);
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        LPM_CUDA(c, cudaMalloc(&c->d_bl, cols * g.n_met_t * sizeof(float4)));
+        LPM_CUDA(c, cudaMalloc(&c->d_blpair, cols * n_pair * 2 * sizeof(float4)));
+        c->bl_set.assign((size_t)g.n_met_t, 0);
+    }
+    c->kz_model = model;
+    c->kz_min = kz_min;
+    drop_graphs(c);                          // the graphs hold the step parameters
+    return LPM_OK;
+}
+
+lpm_status lpm_set_boundary_layer(lpm_ctx *c, int t_index, const float *bl, int on_device)
+{
+    if (!c) return LPM_E_INVALID;
+    const lpm_config &g = c->cfg;
+    if (!c->d_bl) return fail(c, LPM_E_STATE, "select K_z model 1 (lpm_set_kz_model) first");
+    if (t_index < 0 || t_index >= g.n_met_t)
+        return fail(c, LPM_E_INVALID, "t_index %d outside [0, %d)", t_index, g.n_met_t);
+    if (!bl) return fail(c, LPM_E_INVALID, "bl is NULL");
+    const size_t cols = (size_t)g.nx * g.ny;
+    if (!on_device) {
+        for (size_t i = 0; i < cols; ++i) {
+            const float *v = bl + 4 * i;
+            if (!std::isfinite(v[0]) || !std::isfinite(v[1]) || !std::isfinite(v[2]) ||
+                v[0] < 0.0f || !(v[2] > 0.0f))
+                return fail(c, LPM_E_INVALID, "column %zu: need u* >= 0, finite 1/L, H_z > 0", i);
+        }
+    }
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_bl + cols * t_index, bl, cols * sizeof(float4),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream));
+    c->bl_set[(size_t)t_index] = 1;
+    // time pairs (h, h+1) that this slab completes
+    for (int h = t_index - 1; h <= t_index; ++h) {
+        const int h1 = g.n_met_t > 1 ? h + 1 : h;
+        if (h < 0 || h1 > g.n_met_t - 1 || (g.n_met_t > 1 && h > g.n_met_t - 2)) continue;
+        if (!c->bl_set[(size_t)h] || !c->bl_set[(size_t)h1]) continue;
+        LPM_CUDA(c, launch_pack(c->stream, c->d_bl + cols * h, c->d_bl + cols * h1, nullptr,
+                                nullptr, c->d_blpair + cols * 2 * h, nullptr, g.nx, g.ny, 1));
+        c->n_launches++;
+    }
+    if (!on_device) LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LPM_OK;
+}
+
 lpm_status lpm_set_dosage(lpm_ctx *c, int every_steps)
 {
     if (!c) return LPM_E_INVALID;
@@ -1402,6 +1470,7 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     if (R < 1 || R > MAX_REC || !rec) return fail(c, LPM_E_INVALID, "need 1 <= R <= %d receptors", MAX_REC);
     if (!(bandwidth > 0) || every < 1) return fail(c, LPM_E_INVALID, "bandwidth > 0 and every >= 1");
     if (g.drift_correction) return fail(c, LPM_E_INVALID, "the adjoint does not support drift_correction");
+    if (c->kz_model != 0) return fail(c, LPM_E_INVALID, "the adjoint does not support K_z from Eq. 3");
     if (c->n_released != g.n_scenarios)
         return fail(c, LPM_E_STATE, "%d of %d scenarios released", c->n_released, g.n_scenarios);
     if (adj_nq(c) > MAX_NQ) return fail(c, LPM_E_INVALID, "emission series longer than %d", MAX_NQ);

@@ -62,6 +62,10 @@ struct StepParams {
     // (32 B aligned), nodes in slab order (see col_node)
     const float4 *pair;              // [n_pair][nz][ny][nx][2], n_pair = max(1, n_t - 1)
     const float2 *khpair;            // [n_pair][nz][ny][nx] (K_h at h, difference) or nullptr
+    // boundary-layer columns for K_z from Eq. 3: [n_pair][ny][nx][2] (u*, 1/L, H_z, 0) as
+    // value + difference, or nullptr (K_z from the gridded field)
+    const float4 *blpair;
+    float kz_min;
     const uint8_t *rain;             // [n_t][ny][nx] or nullptr
     int nx, ny, nz, n_t;
     long long slab;                  // nodes per slab
@@ -283,6 +287,36 @@ __device__ __forceinline__ Levels load_levels(const StepParams &P, float *s_z, f
 struct Met {
     float u, v, w, kz, kh, dkz;
 };
+
+// Eq. 3 (Sec. 2): K_z = k u* z (1 - z/H_z)^2 / Phi_h(z/L), k = 0.4, for 0 < z < H_z and
+// 0 elsewhere, floored at kz_min; Phi_h = 1 + 5 z/L (stable) or (1 - 16 z/L)^(-1/2)
+// (unstable). dkz = dK_z/dz (0 where the floor holds) for the drift term.
+__device__ __forceinline__ void kz_eq3(float ustar, float inv_l, float hz, float kz_min, float z,
+                                       float &kz, float &dkz)
+{
+    kz = 0.0f;
+    dkz = 0.0f;
+    if (z > 0.0f && z < hz && ustar > 0.0f) {
+        const float s = 1.0f - z / hz;
+        const float zeta = z * inv_l;
+        float ph, dph;
+        if (zeta >= 0.0f) {
+            ph = 1.0f + 5.0f * zeta;
+            dph = 5.0f;
+        } else {
+            const float r = 1.0f / sqrtf(1.0f - 16.0f * zeta);
+            ph = r;
+            dph = 8.0f * r * r * r;
+        }
+        const float ku = 0.4f * ustar;
+        kz = ku * z * s * s / ph;
+        dkz = (ku * (s * s - 2.0f * z * s / hz) - kz * dph * inv_l) / ph;
+    }
+    if (kz < kz_min) {
+        kz = kz_min;
+        dkz = 0.0f;
+    }
+}
 
 // Time blend of a paired record: a + t * d with d the stored difference.
 __device__ __forceinline__ float4 tlerp4(const float4 a, const float4 d, float t)

@@ -30,6 +30,7 @@ struct AdvanceLaunch {
     int block, ppt, occ;
     bool mixed;               // lanes of one tile may belong to different scenarios
     bool dose;                // dosage samples inside the time loop (params->dose_every)
+    bool kz3;                 // K_z from Eq. 3 (params->blpair), 1 particle per thread
     unsigned int grid;
     int n_tiles() const { return ranges.tiles_a + ranges.n_b; }
 };

@@ -29,7 +29,8 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_set_launch", "lpm_sync", "lpm_draws", "lpm_release_range", "lpm_reset",
            "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
            "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save",
-           "lpm_load", "lpm_set_dosage", "lpm_dosage"]
+           "lpm_load", "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model",
+           "lpm_set_boundary_layer"]
 
 
 class LpmError(RuntimeError):
@@ -98,6 +99,8 @@ def load() -> C.CDLL:
     L.lpm_set_params.argtypes = [vp, C.c_double, C.c_double, C.c_double]
     L.lpm_set_sort.argtypes = [vp, C.c_int]
     L.lpm_set_dosage.argtypes = [vp, C.c_int]
+    L.lpm_set_kz_model.argtypes = [vp, C.c_int, C.c_double]
+    L.lpm_set_boundary_layer.argtypes = [vp, C.c_int, vp, C.c_int]
     L.lpm_dosage.argtypes = [vp, C.c_int, dp, C.c_size_t, C.POINTER(C.c_uint64), C.POINTER(i64)]
     L.lpm_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
     L.lpm_load.argtypes = [vp, vp, C.c_size_t]
@@ -114,7 +117,7 @@ def load() -> C.CDLL:
                  "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
                  "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
                  "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load",
-                 "lpm_set_dosage", "lpm_dosage"):
+                 "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model", "lpm_set_boundary_layer"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -326,6 +329,19 @@ def lpm_fixed_state(ctx, scenario: int, conc_shape, dep_shape):
     return conc, dep, ctr, int(sh.value)
 
 
+def lpm_set_kz_model(ctx, model: int, kz_min: float = 0.1) -> None:
+    _check(ctx, load().lpm_set_kz_model(C.c_void_p(ctx), int(model), float(kz_min)))
+
+
+def lpm_set_boundary_layer(ctx, t_index: int, bl) -> None:
+    """Hour t_index of the (u*, 1/L, H_z, unused) columns, [ny][nx][4] float32 (numpy
+    array or CUDA tensor)."""
+    if not hasattr(bl, "data_ptr"):
+        bl = np.ascontiguousarray(bl, dtype=np.float32)
+    a, dev = _addr(bl)
+    _check(ctx, load().lpm_set_boundary_layer(C.c_void_p(ctx), int(t_index), a, dev))
+
+
 def lpm_set_dosage(ctx, every_steps: int) -> None:
     _check(ctx, load().lpm_set_dosage(C.c_void_p(ctx), int(every_steps)))
 
@@ -400,6 +416,10 @@ class Sim:
             if sort_every is not None:
                 lpm_set_sort(self.ctx, sort_every)
             self._set_met(met_on_device)
+            if getattr(cfg, "kz_model", 0):
+                lpm_set_kz_model(self.ctx, cfg.kz_model, cfg.kz_min)
+                for t in range(cfg.n_met_t):
+                    lpm_set_boundary_layer(self.ctx, t, cfg.bl[t])
             if cfg.scenarios:
                 for i, sc in enumerate(cfg.scenarios):
                     lpm_set_source(self.ctx, i, sc.src_x, sc.src_y, sc.src_z, sc.wind_offset)

@@ -1,0 +1,85 @@
+"""GPU parity of K_z computed in the step from Eq. 3 (boundary-layer columns u*, 1/L, H_z)
+against the FP64 oracle, with and without the drift term, and its invariance under the
+particle order and scenario mixing."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import lpm_inputs as li
+import oracle
+from parity_util import compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0912_3223_gb300 import build
+    build.build()
+    oracle.build()
+
+
+@pytest.fixture(scope="module")
+def cfg_eq3():
+    return li.make_cfg1(n_particles=20_000, n_steps=2880, n_hours=25, kz_eq3=True)
+
+
+@pytest.mark.parametrize("drift", [0, 1])
+def test_eq3_parity_360_steps(cfg_eq3, drift):
+    """All 20000 particles after 360 steps in the realistic weather with K_z from Eq. 3
+    (diurnal stability, per-column u*, 1/L, H_z), with and without the drift term."""
+    cfg = dataclasses.replace(cfg_eq3, drift_correction=drift)
+    g = run_gpu(cfg, n_run=360)
+    o = oracle.run(cfg, n_run=360)
+    sens = oracle.sensitivity(cfg, n_run=360)
+    rep = compare(cfg, g, o, check_grid=False, sens=sens)
+    print(f"Eq. 3 K_z, drift {drift}:", rep)
+    np.testing.assert_allclose(g["budget"][0], o["budget"][0], rtol=1e-6)
+
+
+def test_eq3_parity_bin_step(cfg_eq3):
+    """Stepped to the first hourly snapshot: concentration and deposition grids."""
+    g = run_gpu(cfg_eq3, n_run=120)
+    o = oracle.run(cfg_eq3, n_run=120)
+    sens = oracle.sensitivity(cfg_eq3, n_run=120)
+    rep = compare(cfg_eq3, g, o, sens=sens)
+    print("Eq. 3 K_z at the first snapshot:", rep)
+
+
+def test_eq3_sorting_and_mixed_scenarios_change_nothing():
+    """Plain: sorted by cell or not, bit-identical. Batched: the sorted (mixed-scenario)
+    run equals the unsorted one bit for bit."""
+    cfg = li.make_cfg1(n_particles=4001, n_steps=300, n_hours=6, kz_eq3=True)
+    a = run_gpu(cfg, sort_every=0)
+    b = run_gpu(cfg, sort_every=30)
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["tag"], b["tag"])
+    assert np.array_equal(a["conc_fixed"], b["conc_fixed"])
+    from paper_0912_3223_gb300 import Sim
+    ens = li.make_cfg2(n_scenarios=4, n_steps=200, n_min=500, n_max=1500,
+                       base=li.make_cfg1(n_particles=1, n_steps=200, kz_eq3=True))
+    out = []
+    for se in (0, 20):
+        with Sim(ens, sort_every=se) as sim:
+            sim.step(ens.n_steps)
+            out.append(sim.particles())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_eq3_limits_are_reported():
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = li.make_cfg1(n_particles=1000, n_steps=60, n_hours=2, kz_eq3=True)
+    with Sim(cfg, launch=(256, 2, 2)) as sim:
+        with pytest.raises(lpm.LpmError) as e:
+            sim.step(10)
+        assert e.value.status == lpm.LPM_E_INVALID
+    with Sim(cfg) as sim:
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_receptors(sim.ctx, 1, li.make_receptors(), 200.0, 6)
+        assert e.value.status == lpm.LPM_E_INVALID
+        with pytest.raises(lpm.LpmError) as e:
+            lpm.lpm_set_boundary_layer(sim.ctx, 0, np.full((cfg.ny, cfg.nx, 4), -1.0, np.float32))
+        assert e.value.status == lpm.LPM_E_INVALID
