@@ -122,6 +122,9 @@ class LpmConfig:
     kz_model: int = 0
     kz_min: float = 0.1
     bl: Optional[np.ndarray] = None     # float32 [n_met_t][ny][nx][4] = (u*, 1/L, H_z, 0)
+    # decay chain: half-lives (s) of parent -> daughter -> ..., the first = half_life_s,
+    # 0 = stable (last only); None: one species
+    chain_half_lives: Optional[np.ndarray] = None
     name: str = ""
 
     @property

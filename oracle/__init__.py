@@ -57,6 +57,7 @@ class OCfg(C.Structure):
         ("k_scale", C.c_double), ("bias_u", C.c_double), ("bias_v", C.c_double),
         ("dose_every", C.c_int),
         ("kz_model", C.c_int), ("kz_min", C.c_double), ("bl", C.POINTER(C.c_float)),
+        ("n_species", C.c_int), ("chain_half_life", C.POINTER(C.c_double)),
     ]
 
 
@@ -69,6 +70,8 @@ class OOut(C.Structure):
         ("budget", C.POINTER(C.c_double)), ("counters", C.POINTER(C.c_int64)),
         ("dose", C.POINTER(C.c_double)), ("dose_fixed", C.POINTER(C.c_int64)),
         ("dose_ctr", C.POINTER(C.c_int64)),
+        ("sp_conc", C.POINTER(C.c_double)), ("sp_conc_fixed", C.POINTER(C.c_int64)),
+        ("sp_dep", C.POINTER(C.c_double)), ("sp_dep_fixed", C.POINTER(C.c_int64)),
     ]
 
 
@@ -102,6 +105,8 @@ def lib():
         L.oracle_kz_eq3_partials.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
         L.oracle_interp_grad_many.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_double), C.c_int64,
                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.oracle_chain_amount.argtypes = [C.POINTER(OCfg), C.c_int, C.c_double]
+        L.oracle_chain_amount.restype = C.c_double
         L.oracle_threshold.argtypes = [C.c_double]
         L.oracle_threshold.restype = C.c_uint32
         L.oracle_run.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_int64), C.c_int64, C.c_int64,
@@ -187,6 +192,9 @@ def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
     o.kz_model = int(getattr(cfg, "kz_model", 0))
     o.kz_min = float(getattr(cfg, "kz_min", 0.1))
     o.bl = _ptr(pin.arr(getattr(cfg, "bl", None), np.float32), C.c_float)
+    chain = getattr(cfg, "chain_half_lives", None)
+    o.n_species = 0 if chain is None else len(chain)
+    o.chain_half_life = _ptr(pin.arr(chain, np.float64), C.c_double)
     o._pin = pin  # keep arrays alive with the record
     return o
 
@@ -273,6 +281,12 @@ def kz_eq3_partials(ustar: float, inv_l: float, hz: float, kz_min: float, z: flo
     return tuple(float(v) for v in out)
 
 
+def chain_amount(cfg, species: int, age: float) -> float:
+    """Amount of ``species`` per unit of emitted parent after ``age`` seconds."""
+    o = make_ocfg(cfg)
+    return float(lib().oracle_chain_amount(C.byref(o), int(species), float(age)))
+
+
 def threshold(p: float) -> int:
     return int(lib().oracle_threshold(float(p)))
 
@@ -311,13 +325,21 @@ def run(cfg, sel=None, n_run: Optional[int] = None, **kw) -> dict:
         budget=np.zeros(8), counters=np.zeros(6, np.int64),
         dose=np.zeros((cfg.cz, cfg.cy, cfg.cx)),
         dose_fixed=np.zeros((cfg.cz, cfg.cy, cfg.cx), np.int64), dose_ctr=np.zeros(2, np.int64))
+    n_sp = int(o.n_species)
+    if n_sp > 1:
+        out.update(sp_conc=np.zeros((n_sp, cfg.cz, cfg.cy, cfg.cx)),
+                   sp_conc_fixed=np.zeros((n_sp, cfg.cz, cfg.cy, cfg.cx), np.int64),
+                   sp_dep=np.zeros((n_sp, 2, cfg.cy, cfg.cx)),
+                   sp_dep_fixed=np.zeros((n_sp, 2, cfg.cy, cfg.cx), np.int64))
     oo = OOut(_ptr(out["pos"], C.c_double), _ptr(out["status"], C.c_int32),
               _ptr(out["release"], C.c_int64), _ptr(out["margin"], C.c_double),
               _ptr(out["conc"], C.c_double), _ptr(out["conc_fixed"], C.c_int64),
               _ptr(out["dep"], C.c_double), _ptr(out["dep_fixed"], C.c_int64),
               _ptr(out["budget"], C.c_double), _ptr(out["counters"], C.c_int64),
               _ptr(out["dose"], C.c_double), _ptr(out["dose_fixed"], C.c_int64),
-              _ptr(out["dose_ctr"], C.c_int64))
+              _ptr(out["dose_ctr"], C.c_int64),
+              _ptr(out.get("sp_conc"), C.c_double), _ptr(out.get("sp_conc_fixed"), C.c_int64),
+              _ptr(out.get("sp_dep"), C.c_double), _ptr(out.get("sp_dep_fixed"), C.c_int64))
     assert ncell == out["conc"].size
     rc = lib().oracle_run(C.byref(o), _ptr(sel, C.c_int64), n, int(n_run), C.byref(oo))
     if rc != 0:

@@ -137,6 +137,10 @@ typedef struct {
     int kz_model;
     double kz_min;                   /* floor of the Eq. 3 diffusivity (m^2/s) */
     const float *bl;                 /* [n_met_t][ny][nx][4] (u*, 1/L, H_z, unused) or NULL */
+    /* decay chain parent -> daughter -> ...: n_species >= 2 half-lives (s, 0 = stable,
+     * only for the last), the first equal to half_life_s; n_species <= 1: one species */
+    int n_species;
+    const double *chain_half_life;
 } ocfg;
 
 /* ---------------------------------------------------------------------------------
@@ -202,6 +206,38 @@ int oracle_fixed_shift(double total_mass)
 static double decay_rate(const ocfg *c)
 {
     return c->half_life_s > 0.0 ? log(2.0) / c->half_life_s : 0.0;
+}
+
+/* Decay chain (Sec. 2: particles transform to other species by radioactive decay): the
+ * amount of species j per unit of initially emitted parent after a time `age`, from the
+ * closed-form solution of dN_1/dt = -l_1 N_1, dN_j/dt = l_{j-1} N_{j-1} - l_j N_j with
+ * N_1(0) = 1 (Bateman): N_j = (prod_{k<j} l_k) sum_{i<=j} exp(-l_i age) /
+ * prod_{k<=j, k!=i} (l_k - l_i). The decay rates must be distinct.
+ * Parity: pinned against a numerical integration of the rate equations and by
+ * conservation of the total amount when the chain ends in a stable species. */
+double oracle_chain_amount(const ocfg *c, int j, double age)
+{
+    if (c->n_species <= 1 || !c->chain_half_life) return j == 0 ? exp(-decay_rate(c) * age) : 0.0;
+    double lam[8];
+    for (int i = 0; i <= j; ++i)
+        lam[i] = c->chain_half_life[i] > 0.0 ? log(2.0) / c->chain_half_life[i] : 0.0;
+    double pre = 1.0;
+    for (int k = 0; k < j; ++k) pre *= lam[k];
+    double sum = 0.0;
+    for (int i = 0; i <= j; ++i) {
+        double den = 1.0;
+        for (int k = 0; k <= j; ++k)
+            if (k != i) den *= lam[k] - lam[i];
+        sum += exp(-lam[i] * age) / den;
+    }
+    return pre * sum;
+}
+
+/* Amount of species j of a particle released at step s, at the end of step k. */
+static double species_mass_at(const ocfg *c, int j, int64_t s, int64_t k)
+{
+    double age = (double)(k + 1 - s) * c->dt;
+    return oracle_initial_mass(c, s) * oracle_chain_amount(c, j, age);
 }
 
 /* Mass of a particle released at step s, at the end of step k (age (k+1-s)*dt):
@@ -466,6 +502,11 @@ typedef struct {
     double *dose;         /* [cz][cy][cx] sum over the dosage samples of the mass per cell */
     int64_t *dose_fixed;  /* [cz][cy][cx] the same in fixed point */
     int64_t *dose_ctr;    /* [2] fixed-point mass outside the grid, number of samples */
+    /* decay chain: per species (species 0 = the parent, as conc / dep), or NULL */
+    double *sp_conc;      /* [n_species][cz][cy][cx] (last snapshot) */
+    int64_t *sp_conc_fixed;
+    double *sp_dep;       /* [n_species][2][cy][cx] */
+    int64_t *sp_dep_fixed;
 } oout;
 
 static int64_t fixed_of(double m, int shift)
@@ -593,6 +634,16 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
     memset(o->dep_fixed, 0, sizeof(int64_t) * ndep);
     for (int m = 0; m < 6; ++m) o->counters[m] = 0;
     const int dosing = c->dose_every > 0 && o->dose && o->dose_fixed && o->dose_ctr;
+    const int n_sp = (c->n_species > 1 && c->chain_half_life && o->sp_conc && o->sp_conc_fixed &&
+                      o->sp_dep && o->sp_dep_fixed) ? c->n_species : 0;
+    if (n_sp) {
+        if (n_sp > 8 || fabs(c->chain_half_life[0] - c->half_life_s) > 1e-9 * c->half_life_s)
+            return 1;
+        memset(o->sp_conc, 0, sizeof(double) * ncell * n_sp);
+        memset(o->sp_conc_fixed, 0, sizeof(int64_t) * ncell * n_sp);
+        memset(o->sp_dep, 0, sizeof(double) * ndep * n_sp);
+        memset(o->sp_dep_fixed, 0, sizeof(int64_t) * ndep * n_sp);
+    }
     /* the dosage sums up to floor(S / n) samples of at most the total mass: its fixed point
      * gives up b = ceil(log2(samples)) bits so that no sum passes 2^61 units */
     int dshift = shift;
@@ -643,6 +694,11 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
                         size_t cell = ((size_t)kind * c->cy + iy) * c->cx + ix;
                         o->dep[cell] += m;
                         o->dep_fixed[cell] += fixed_of(m, shift);
+                        for (int j = 0; j < n_sp; ++j) {
+                            double mj = species_mass_at(c, j, sp[q], k);
+                            o->sp_dep[j * ndep + cell] += mj;
+                            o->sp_dep_fixed[j * ndep + cell] += fixed_of(mj, shift);
+                        }
                     } else {
                         dep_out[kind] += m;
                         o->counters[1 + kind] += fixed_of(m, shift);
@@ -675,6 +731,10 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
         if ((k + 1) % c->bin_every == 0 || k == c->n_steps - 1) {
             memset(o->conc, 0, sizeof(double) * ncell);
             memset(o->conc_fixed, 0, sizeof(int64_t) * ncell);
+            if (n_sp) {
+                memset(o->sp_conc, 0, sizeof(double) * ncell * n_sp);
+                memset(o->sp_conc_fixed, 0, sizeof(int64_t) * ncell * n_sp);
+            }
             bin_out = 0.0;
             o->counters[0] = 0;
             o->counters[5] += 1;
@@ -689,6 +749,11 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
                     size_t cell = ((size_t)iz * c->cy + iy) * c->cx + ix;
                     o->conc[cell] += m;
                     o->conc_fixed[cell] += fixed_of(m, shift);
+                    for (int j = 0; j < n_sp; ++j) {
+                        double mj = species_mass_at(c, j, sp[q], k);
+                        o->sp_conc[j * ncell + cell] += mj;
+                        o->sp_conc_fixed[j * ncell + cell] += fixed_of(mj, shift);
+                    }
                 } else {
                     bin_out += m;
                     o->counters[0] += fixed_of(m, shift);

@@ -598,3 +598,68 @@ def test_kz_eq3_second_derivative_and_partials():
                                           (1e-3, lambda e: (u, inv_l, H + e))]):
             fd = (oracle.kz_eq3(*args(du), 0.0, z)[0] - oracle.kz_eq3(*args(-du), 0.0, z)[0]) / (2 * du)
             assert p[2 + idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+# ------------------------------------------------------------------------------------
+# Decay chains (Sec. 2: particles transform to other species by radioactive decay)
+# ------------------------------------------------------------------------------------
+def _chain_cfg(half_lives, n_particles=300, n_steps=60):
+    cfg = li.make_cfg0(n_particles=n_particles, n_steps=n_steps)
+    return dataclasses.replace(cfg, half_life_s=float(half_lives[0]),
+                               chain_half_lives=np.asarray(half_lives, dtype=np.float64))
+
+
+@pytest.mark.parametrize("half_lives", [(3600.0, 1200.0, 0.0), (900.0, 5400.0, 300.0, 0.0),
+                                        (7200.0, 600.0)])
+def test_chain_amounts_solve_the_rate_equations(half_lives):
+    """The closed-form amounts against a numerical integration of dN_1/dt = -l_1 N_1,
+    dN_j/dt = l_{j-1} N_{j-1} - l_j N_j (N_1(0) = 1); with a stable last species the total
+    stays 1, otherwise it decays. Catches a wrong product, sign or index in the formula."""
+    from scipy.integrate import solve_ivp
+    cfg = _chain_cfg(half_lives)
+    lam = np.array([math.log(2.0) / h if h > 0 else 0.0 for h in half_lives])
+    n = len(lam)
+
+    def rhs(t, y):
+        d = -lam * y
+        d[1:] += lam[:-1] * y[:-1]
+        return d
+
+    ages = np.array([0.0, 120.0, 1800.0, 7200.0, 30000.0])
+    sol = solve_ivp(rhs, (0.0, ages[-1]), np.eye(n)[0], t_eval=ages, rtol=1e-12, atol=1e-15,
+                    method="DOP853")
+    for a_i, age in enumerate(ages):
+        got = np.array([oracle.chain_amount(cfg, j, age) for j in range(n)])
+        np.testing.assert_allclose(got, sol.y[:, a_i], rtol=1e-8, atol=1e-12)
+        if lam[-1] == 0.0:
+            assert got.sum() == pytest.approx(1.0, abs=1e-12)
+
+
+def test_chain_grids_per_species():
+    """Uniform weather, every particle inside the grid: species 0 is the single-species
+    snapshot exactly, and each species' grid total is the sum over the airborne particles
+    of m0 N_j(age) with N_j from the numerically integrated rate equations."""
+    from scipy.integrate import solve_ivp
+    half_lives = (1800.0, 600.0, 0.0)
+    n_p, steps = 300, 60
+    cfg = dataclasses.replace(_chain_cfg(half_lives, n_p, steps), cx0=-1000.0, cx=100)
+    r = oracle.run(cfg)
+    assert np.array_equal(r["sp_conc_fixed"][0], r["conc_fixed"])
+    np.testing.assert_allclose(r["sp_conc"][0], r["conc"], rtol=0, atol=0)
+    assert r["counters"][0] == 0                       # nothing outside the grid
+    lam = np.array([math.log(2.0) / h if h > 0 else 0.0 for h in half_lives])
+
+    def rhs(t, y):
+        d = -lam * y
+        d[1:] += lam[:-1] * y[:-1]
+        return d
+
+    sp = (np.arange(n_p) * steps) // n_p
+    ages = (steps - sp) * cfg.dt                        # the snapshot after the last step
+    sol = solve_ivp(rhs, (0.0, ages.max()), [1.0, 0.0, 0.0], t_eval=np.unique(ages),
+                    rtol=1e-12, atol=1e-15, method="DOP853")
+    amount = {a: sol.y[:, i] for i, a in enumerate(np.unique(ages))}
+    counts = np.bincount(sp, minlength=steps)
+    for j in range(3):
+        want = sum((1.0 * cfg.dt / counts[s]) * amount[a][j] for s, a in zip(sp, ages))
+        assert r["sp_conc"][j].sum() == pytest.approx(want, rel=1e-9)
