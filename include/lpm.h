@@ -197,7 +197,8 @@ lpm_status lpm_particles(lpm_ctx *ctx, int64_t first, int64_t count, float *xyz,
  * mass, below 2^61 units). conc: [cz][cy][cx], dep: [2][cy][cx] (either NULL);
  * counters[16] (may be NULL) = { bin_out, dep_out_dry, dep_out_wet, exited,
  * active_steps, n_bins, air_in, air_out, n_active, dep_total_dry, dep_total_wet,
- * dose_out, 0, 0, 0, 0 }, air_* and n_active as of the last lpm_budget. *shift may be NULL.
+ * dose_out, species_1_out, species_2_out, species_3_out, 0 }, air_* and n_active as of
+ * the last lpm_budget. *shift may be NULL.
  */
 lpm_status lpm_fixed_state(lpm_ctx *ctx, int scenario, uint64_t *conc, size_t n_conc,
                            uint64_t *dep, size_t n_dep, int64_t counters[16], int *shift);
@@ -217,6 +218,31 @@ lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int
  * Needs about 56 bytes of extra device memory per particle slot, allocated at the first
  * sort. */
 lpm_status lpm_set_sort(lpm_ctx *ctx, int every_steps);
+
+/*
+ * Decay chain (Sec. 2: released particles "can transform to other species" by
+ * radioactive decay, deterministic from the half-lives). The emitted parent (species 0,
+ * the configured half_life_s) decays into species 1, which decays into species 2, ...:
+ * each particle's amount of species j per unit of emitted parent after a time a is the
+ * closed-form solution of the linear rate equations (Bateman), sum_i c_ji exp(-l_i a).
+ * The snapshots (every bin_every steps) and the deposition events then also add each
+ * daughter's amount to grids of its own; species 0 stays in the usual grids, and the
+ * budget, receptors and dosage refer to species 0.
+ *
+ * lpm_set_decay_chain: n_species in [1, 4] half-lives (s); half_lives[0] must equal the
+ * configured half_life_s, 0 (stable) is allowed for the last species only, and the decay
+ * rates must be distinct. Call before the first step or after lpm_reset (LPM_E_STATE
+ * otherwise); n_species = 1 removes the chain. Allocates 8 bytes per cell, deposition cell
+ * and scenario for each daughter.
+ * lpm_species: species' concentration [cz][cy][cx] (mass/m^3), dry and wet deposition
+ * [cy][cx] (mass/m^2) of the last snapshot / the run so far, and the raw fixed-point grids
+ * (same shift as lpm_fixed_state); any pointer may be NULL. Species 0 gives the usual
+ * grids. Daughter mass outside the concentration grid at the snapshot is counter 12 + j - 1
+ * of lpm_fixed_state. Synchronises.
+ */
+lpm_status lpm_set_decay_chain(lpm_ctx *ctx, int n_species, const double *half_lives);
+lpm_status lpm_species(lpm_ctx *ctx, int scenario, int species, double *conc, double *dry,
+                       double *wet, uint64_t *conc_fixed, uint64_t *dep_fixed);
 
 /*
  * K_z inside the step from Eq. 3 (Sec. 2): K_z(z) = k u* z (1 - z/H_z)^2 / Phi_h(z/L),

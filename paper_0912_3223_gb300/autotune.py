@@ -34,7 +34,8 @@ def signature(cfg) -> str:
     parts = [cfg.nx, cfg.ny, cfg.nz, cfg.n_met_t, cfg.cx, cfg.cy, cfg.cz, cfg.n_steps,
              cfg.bin_every, cfg.n_particles, cfg.n_scenarios, cfg.kh is None,
              cfg.rain is None, cfg.vd_dry > 0, cfg.wet_lambda > 0, cfg.lateral_exit,
-             cfg.reflect_top, cfg.drift_correction, round(cfg.dt, 6)]
+             cfg.reflect_top, cfg.drift_correction, round(cfg.dt, 6),
+             getattr(cfg, "kz_model", 0), getattr(cfg, "chain_half_lives", None) is not None]
     return hashlib.sha1(repr(parts).encode()).hexdigest()[:16]
 
 
@@ -89,7 +90,15 @@ def autotune(sim, shapes: Optional[Iterable[Tuple[int, int, int]]] = None, use_c
     shapes = [tuple(v) for v in shapes] if shapes is not None else DEFAULT_SHAPES
     results = {}
     for shape in shapes:
-        results["x".join(map(str, shape))] = time_shape(sim, shape, reps)
+        try:
+            results["x".join(map(str, shape))] = time_shape(sim, shape, reps)
+        except lpm.LpmError as e:
+            # shapes the context's options do not run with (e.g. dosage, Eq. 3 K_z or a
+            # decay chain need one particle per thread)
+            if e.status != lpm.LPM_E_INVALID:
+                raise
+    if not results:
+        raise RuntimeError("no launch shape runs with this context's options")
     best = min(results, key=results.get)
     shape = tuple(int(v) for v in best.split("x"))
     lpm.lpm_set_launch(sim.ctx, *shape)

@@ -94,8 +94,9 @@ __device__ __forceinline__ void warp_count_scen(int s, unsigned long long v, int
 // Weather at a point from the time-paired records: 8 spatial corners, each one 32-byte
 // load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z. With KZ3, K_z
 // and its derivative come from Eq. 3 on the boundary-layer columns (4 more 32-byte loads
-// of the time-paired (u*, 1/L, H_z) at the cell's corner columns, bilinear in x, y).
-template <bool KZ3>
+// of the time-paired (u*, 1/L, H_z) at the cell's corner columns, bilinear in x, y);
+// only the EXT instantiations carry that code.
+template <bool EXT>
 __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels &L,
                                                const float4 *__restrict__ pair,
                                                const float2 *__restrict__ khp,
@@ -124,7 +125,7 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
     m.u = r.x;
     m.v = r.y;
     m.w = r.z;
-    if (KZ3) {
+    if (EXT && blp) {
         float4 cq[4];
 #pragma unroll
         for (int mm = 0; mm < 4; ++mm) {
@@ -177,6 +178,19 @@ __device__ __forceinline__ float mass_at(const StepParams &P, const ScenDev &sc,
     return m0 * expf(-P.lambda * age);
 }
 
+// Daughters of a decay chain deposited with their parent at step k (cell of the 2D grid).
+static __device__ __noinline__ void deposit_species(const StepParams &P, const ScenDev &sc, int scen,
+                                             int sp, int k, int kind, int cell2)
+{
+    const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
+    const float age = (float)(k + 1 - sp) * P.dt;
+    const long long plane = (long long)P.cx * P.cy;
+    for (int j = 1; j < P.n_species; ++j) {
+        const unsigned long long v = to_fixed(m0 * chain_amount(P, j, age), sc.scale);
+        atomicAdd(P.sp_dep_all + (((long long)(j - 1) * P.n_scen + scen) * 2 + kind) * plane + cell2, v);
+    }
+}
+
 // Per-step quantities shared by every particle of a tile.
 struct StepTime {
     int k;
@@ -213,7 +227,7 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const float2 
 // Updates (x, y, z) and returns the new status. (du, dv) is the wind offset of the
 // particle's scenario plus the bias at t_k. With GRIDS, deposition and exit add their mass
 // to the scenario's grids and counters; *fold receives dz/dz_pre (+-1, 0 when clamped).
-template <bool GRIDS, bool KZ3 = false>
+template <bool GRIDS, bool EXT = false>
 __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Levels &LV,
                                                   const StepTime &T, const ScenDev &sc,
                                                   const ScenDev *scg, unsigned long long gid,
@@ -222,7 +236,7 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
 {
     const int k = T.k;
     // 1. weather at the old position and t_k; 2. diffusivities
-    const Met m = sample_met_pair<KZ3>(P, LV, T.pair, T.khp, T.blp, T.ts.f, x, y, z);
+    const Met m = sample_met_pair<EXT>(P, LV, T.pair, T.khp, T.blp, T.ts.f, x, y, z);
     const float sig_h = T.khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
     const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
     // 3. N(0,1) draws
@@ -284,6 +298,8 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
             atomicAdd(scg->ctr + (C_DEP_OUT_DRY + kind) * P.ctr_stride, v);
         }
         atomicAdd(scg->ctr + (C_DEP_DRY + kind) * P.ctr_stride, v);
+        if (EXT && P.n_species > 1 && ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy)
+            deposit_species(P, sc, (int)(scg - P.scen), sp, k, kind, iy * P.cx + ix);
     }
     return kind == 0 ? ST_DEP_DRY : ST_DEP_WET;
 }
@@ -301,9 +317,11 @@ struct MinBlocks {
 // block index (grid over all tiles) or by an atomic queue (persistent grid). With MIXED the
 // lanes of a tile may belong to different scenarios (the sorted particles of a batched
 // context): each lane finds its scenario from its home slot and carries its own wind
-// offset; the results are bit-identical to the per-scenario path. DOSE adds the dosage
-// samples (every P.dose_every steps) inside the time loop; KZ3 takes K_z from Eq. 3.
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE, bool KZ3>
+// offset; the results are bit-identical to the per-scenario path. EXT adds, as uniform
+// run-time options, the dosage samples (every P.dose_every steps) inside the time loop,
+// K_z from Eq. 3 (P.blpair) and the daughters of a decay chain (P.n_species > 1); the
+// default instantiations carry none of that code.
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
                int k1, int do_bin)
@@ -398,7 +416,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
 #pragma unroll 1
         for (int k = k0; k < k1; ++k) {
             // with dosage sampling the warp stays together (the samples are warp-collective)
-            if (DOSE) {
+            if (EXT && P.dose_every) {
                 if (!__any_sync(0xffffffffu, live > 0)) break;
             } else if (live <= 0) {
                 break;
@@ -439,19 +457,19 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                         du = P.bias_u + fmaf(T.ts.f, o1[j].x - o0[j].x, o0[j].x);
                         dv = P.bias_v + fmaf(T.ts.f, o1[j].y - o0[j].y, o0[j].y);
                     }
-                    st = particle_step<true, KZ3>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
+                    st = particle_step<true, EXT>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
                                                   sp, sig_h_uniform, du, dv, x[j], y[j], z[j],
                                                   nullptr);
                 } else {
                     ++steps;
-                    st = particle_step<true, KZ3>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
+                    st = particle_step<true, EXT>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
                                                   T.du, T.dv, x[j], y[j], z[j], nullptr);
                 }
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;
             }
             // time-integrated dosage: every dose_every-th step, the decayed masses at t_{k+1}
-            if (DOSE && (k + 1) % P.dose_every == 0) {
+            if (EXT && P.dose_every && (k + 1) % P.dose_every == 0) {
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
                     const int local = j * BLOCK + threadIdx.x;
@@ -515,6 +533,27 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                     warp_accumulate(cell, v, scg.conc, scg.ctr + C_BIN_OUT * P.ctr_stride, s_warp,
                                     n_cells, P.err);
                 }
+                // daughters of a decay chain, species by species (the same cells)
+                for (int d = 1; EXT && d < P.n_species; ++d) {
+                    unsigned long long vd = 0ull;
+                    if (on) {
+                        const int sp = (int)(tag[j] & TAG_STEP);
+                        const ScenDev &q = MIXED ? P.scen[sj[j]] : scg;
+                        const float m0 = __ldg(P.m0 + q.m0_off + (sp - q.rel_first));
+                        vd = to_fixed(m0 * chain_amount(P, d, (float)(k1 - sp) * P.dt),
+                                      __ldg(&q.scale));
+                    }
+                    unsigned long long *base = P.sp_conc_all + (long long)(d - 1) * P.n_scen * n_cells;
+                    if (MIXED) {
+                        long long key = -1;
+                        if (on) key = cell >= 0 ? (long long)sj[j] * n_cells + cell : -2LL - sj[j];
+                        warp_accumulate_scen(key, vd, P, base, C_SP_OUT + d - 1, s_warp, n_cells);
+                    } else {
+                        warp_accumulate(cell, vd, base + (long long)tscen * n_cells,
+                                        scg.ctr + (C_SP_OUT + d - 1) * P.ctr_stride, s_warp,
+                                        n_cells, P.err);
+                    }
+                }
             }
         }
 
@@ -535,59 +574,56 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
     }
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE, bool KZ3>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
 cudaError_t launch_adv(const AdvanceLaunch &L)
 {
-    advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE, KZ3><<<L.grid, BLOCK, 0, L.stream>>>(
+    advance_kernel<BLOCK, PPT, OCC, MIXED, EXT><<<L.grid, BLOCK, 0, L.stream>>>(
         *L.params, L.ranges, L.n_tiles(), L.queue, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool DOSE, bool KZ3>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
 int occ_adv()
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, advance_kernel<BLOCK, PPT, OCC, MIXED, DOSE, KZ3>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC, MIXED, EXT>,
+                                                  BLOCK, 0);
     return n;
 }
 
-// (particles per thread, occupancy variant, mixed scenarios, dosage, Eq. 3 K_z) ->
-// instantiation, for one block size; Eq. 3 K_z is instantiated for 1 particle per thread
-#define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, DOS, KZ, ...)                           \
-    case PPT * 10000 + OCC * 1000 + MIX * 100 + DOS * 10 + KZ:                         \
-        return FN<BLOCK, PPT, OCC, (MIX != 0), (DOS != 0), (KZ != 0)>(__VA_ARGS__);
-#define LPM_ADV_CASES4(FN, BLOCK, PPT, OCC, KZ, ...)                                   \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 0, KZ, __VA_ARGS__)                           \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 0, KZ, __VA_ARGS__)                           \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, 1, KZ, __VA_ARGS__)                           \
-    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, 1, KZ, __VA_ARGS__)
+// (particles per thread, occupancy variant, mixed scenarios, extended options) ->
+// instantiation, for one block size; the extended options run with 1 particle per thread
+#define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, EX, ...)                                \
+    case PPT * 1000 + OCC * 100 + MIX * 10 + EX:                                       \
+        return FN<BLOCK, PPT, OCC, (MIX != 0), (EX != 0)>(__VA_ARGS__);
+#define LPM_ADV_CASES2(FN, BLOCK, PPT, OCC, EX, ...)                                   \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, EX, __VA_ARGS__)                              \
+    LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, EX, __VA_ARGS__)
 #define LPM_ADV_CASES(FN, BLOCK, ...)                                                  \
-    LPM_ADV_CASES4(FN, BLOCK, 1, 0, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 1, 1, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 1, 2, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 2, 0, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 2, 1, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 2, 2, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 4, 0, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 4, 1, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 4, 2, 0, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 1, 0, 1, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 1, 1, 1, __VA_ARGS__)                                    \
-    LPM_ADV_CASES4(FN, BLOCK, 1, 2, 1, __VA_ARGS__)
+    LPM_ADV_CASES2(FN, BLOCK, 1, 0, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 1, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 2, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 2, 0, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 2, 1, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 2, 2, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 4, 0, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 4, 1, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 4, 2, 0, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 0, 1, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 1, 1, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 2, 1, __VA_ARGS__)
 
 #define LPM_ADVANCE_TU(BLOCK)                                                          \
     cudaError_t launch_advance_b##BLOCK(const AdvanceLaunch &L)                         \
     {                                                                                  \
-        switch (L.ppt * 10000 + L.occ * 1000 + (L.mixed ? 100 : 0) + (L.dose ? 10 : 0) + \
-                (L.kz3 ? 1 : 0)) {                                                     \
+        switch (L.ppt * 1000 + L.occ * 100 + (L.mixed ? 10 : 0) + (L.ext ? 1 : 0)) {   \
             LPM_ADV_CASES(launch_adv, BLOCK, L)                                        \
         }                                                                              \
         return cudaErrorInvalidValue;                                                  \
     }                                                                                  \
-    int occupancy_b##BLOCK(int ppt, int occ, bool mixed)                               \
+    int occupancy_b##BLOCK(int ppt, int occ, bool mixed, bool ext)                     \
     {                                                                                  \
-        switch (ppt * 10000 + occ * 1000 + (mixed ? 100 : 0)) {                        \
+        switch (ppt * 1000 + occ * 100 + (mixed ? 10 : 0) + (ext ? 1 : 0)) {           \
             LPM_ADV_CASES(occ_adv, BLOCK)                                              \
         }                                                                              \
         return 0;                                                                      \

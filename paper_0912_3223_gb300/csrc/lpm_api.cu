@@ -112,6 +112,13 @@ struct lpm_ctx {
     float4 *d_grave = nullptr;              // particles found dead at a sort (read-back only)
     unsigned int *d_grave_n = nullptr;
 
+    // decay chain (species 1..: daughters)
+    int n_species = 1;
+    double chain_c[MAX_SPECIES][MAX_SPECIES] = {};
+    double chain_l[MAX_SPECIES] = {};
+    unsigned long long *d_sp_conc = nullptr;  // [n_species-1][n_scen][cz*cy*cx]
+    unsigned long long *d_sp_dep = nullptr;   // [n_species-1][n_scen][2*cy*cx]
+
     // time-integrated dosage
     unsigned long long *d_dose = nullptr;   // [n_scen][cz*cy*cx]
     int dose_every = 0;
@@ -294,6 +301,13 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.dose_every = c->d_dose ? c->dose_every : 0;
     P.dose_mul = std::ldexp(1.0f, -c->dose_bits);
     P.blpair = c->kz_model == 1 ? c->d_blpair : nullptr;
+    P.n_species = c->n_species;
+    for (int j = 0; j < MAX_SPECIES; ++j) {
+        P.chain_l[j] = (float)c->chain_l[j];
+        for (int i = 0; i < MAX_SPECIES; ++i) P.chain_c[j][i] = (float)c->chain_c[j][i];
+    }
+    P.sp_conc_all = c->d_sp_conc;
+    P.sp_dep_all = c->d_sp_dep;
     P.kz_min = (float)c->kz_min;
     P.err = c->d_err;
 }
@@ -702,7 +716,8 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
                     c->d_rgrad, c->d_adj_tiles, c->d_sorted[0], c->d_sorted[1], c->d_pidx[0],
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
-                    c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair};
+                    c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair,
+                    c->d_sp_conc, c->d_sp_dep};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -855,6 +870,11 @@ lpm_status lpm_reset(lpm_ctx *c)
     if (c->d_dose)
         LPM_CUDA(c, cudaMemsetAsync(c->d_dose, 0, ns * c->ncell() * sizeof(unsigned long long),
                                     c->stream));
+    if (c->n_species > 1) {
+        const size_t nd = (size_t)(c->n_species - 1) * ns;
+        LPM_CUDA(c, cudaMemsetAsync(c->d_sp_conc, 0, nd * c->ncell() * 8, c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_sp_dep, 0, nd * c->ndep() * 8, c->stream));
+    }
     c->k = 0;
     c->n_bins = 0;
     c->n_dose = 0;
@@ -928,6 +948,12 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0, ns * c->ncell() * sizeof(unsigned long long), s));
             LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + (size_t)C_BIN_OUT * ns, 0,
                                         ns * sizeof(unsigned long long), s));
+            if (c->n_species > 1) {
+                LPM_CUDA(c, cudaMemsetAsync(c->d_sp_conc, 0, (size_t)(c->n_species - 1) * ns *
+                                                                 c->ncell() * 8, s));
+                LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + (size_t)C_SP_OUT * ns, 0,
+                                            (size_t)(c->n_species - 1) * ns * 8, s));
+            }
         }
         if (sg.sort) {
             SortSource in{};
@@ -973,8 +999,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.ppt = c->ppt;
         L.occ = c->occ;
         L.mixed = batched;
-        L.dose = P.dose_every > 0;
-        L.kz3 = P.blpair != nullptr;
+        L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1;
         const int n_tiles = L.n_tiles();
         if (n_tiles <= 0) continue;
         if (batched) {
@@ -1029,8 +1054,10 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
                 return fail(c, LPM_E_STATE, "boundary-layer slab %lld not set", h);
         }
     }
-    if (c->kz_model == 1 && c->ppt != 1)
-        return fail(c, LPM_E_INVALID, "K_z from Eq. 3 runs with 1 particle per thread");
+    const bool ext = (c->d_dose && c->dose_every > 0) || c->kz_model == 1 || c->n_species > 1;
+    if (ext && c->ppt != 1)
+        return fail(c, LPM_E_INVALID,
+                    "dosage, K_z from Eq. 3 and decay chains run with 1 particle per thread");
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
     if (!c->tiles_valid) {
@@ -1095,7 +1122,8 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
             if (!c->cap_stream)
                 LPM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
             const cudaStream_t cs = c->cap_stream;
-            const int occ_blocks = std::max(1, advance_occupancy(c->block, c->ppt, c->occ, true));
+            const int occ_blocks = std::max(1, advance_occupancy(c->block, c->ppt, c->occ, true,
+                                                                 ext));
             lpm_ctx::Graph ng{};
             ng.k0 = c->k;
             ng.k1 = k_end;
@@ -1313,6 +1341,100 @@ lpm_status lpm_set_sort(lpm_ctx *c, int every_steps)
     c->sort_every = every_steps;
     c->tiles_valid = false;
     drop_graphs(c);
+    return LPM_OK;
+}
+
+lpm_status lpm_set_decay_chain(lpm_ctx *c, int n_species, const double *half_lives)
+{
+    if (!c) return LPM_E_INVALID;
+    if (c->k != 0) return fail(c, LPM_E_STATE, "set the decay chain before stepping (or after lpm_reset)");
+    if (n_species < 1 || n_species > MAX_SPECIES || (n_species > 1 && !half_lives))
+        return fail(c, LPM_E_INVALID, "a chain has 1 to %d species", MAX_SPECIES);
+    const lpm_config &g = c->cfg;
+    double lam[MAX_SPECIES] = {};
+    if (n_species > 1) {
+        if (!is_finite(half_lives[0]) ||
+            std::fabs(half_lives[0] - g.half_life_s) > 1e-9 * std::fabs(g.half_life_s) ||
+            !(half_lives[0] > 0))
+            return fail(c, LPM_E_INVALID, "the first half-life must be the configured one (%g s)",
+                        g.half_life_s);
+        for (int j = 0; j < n_species; ++j) {
+            if (!is_finite(half_lives[j]) || half_lives[j] < 0 ||
+                (half_lives[j] == 0 && j != n_species - 1))
+                return fail(c, LPM_E_INVALID, "half-lives must be > 0 (0 = stable, last only)");
+            lam[j] = half_lives[j] > 0 ? std::log(2.0) / half_lives[j] : 0.0;
+            for (int i = 0; i < j; ++i)
+                if (std::fabs(lam[j] - lam[i]) <= 1e-9 * std::max(lam[j], lam[i]))
+                    return fail(c, LPM_E_INVALID, "decay rates of a chain must be distinct");
+        }
+    }
+    // closed-form amounts of the rate equations: c[j][i] = prod_{k<j} l_k / prod_{k<=j,k!=i} (l_k - l_i)
+    std::memset(c->chain_c, 0, sizeof c->chain_c);
+    std::memset(c->chain_l, 0, sizeof c->chain_l);
+    for (int j = 0; j < n_species && n_species > 1; ++j) {
+        double pre = 1.0;
+        for (int k = 0; k < j; ++k) pre *= lam[k];
+        for (int i = 0; i <= j; ++i) {
+            double den = 1.0;
+            for (int k = 0; k <= j; ++k)
+                if (k != i) den *= lam[k] - lam[i];
+            c->chain_c[j][i] = pre / den;
+        }
+        c->chain_l[j] = lam[j];
+    }
+    const size_t ns = (size_t)g.n_scenarios;
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (unsigned long long **p : {&c->d_sp_conc, &c->d_sp_dep})
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    c->n_species = 1;
+    if (n_species > 1) {
+        const size_t nd = (size_t)(n_species - 1) * ns;
+        LPM_CUDA(c, cudaMalloc(&c->d_sp_conc, nd * c->ncell() * 8));
+        LPM_CUDA(c, cudaMalloc(&c->d_sp_dep, nd * c->ndep() * 8));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_sp_conc, 0, nd * c->ncell() * 8, c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_sp_dep, 0, nd * c->ndep() * 8, c->stream));
+    }
+    c->n_species = n_species;
+    drop_graphs(c);                          // the graphs hold the step parameters
+    return LPM_OK;
+}
+
+lpm_status lpm_species(lpm_ctx *c, int scenario, int species, double *conc, double *dry,
+                       double *wet, uint64_t *conc_fixed, uint64_t *dep_fixed)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "bad scenario");
+    if (species < 0 || species >= c->n_species)
+        return fail(c, LPM_E_INVALID, "species %d outside the chain of %d", species, c->n_species);
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    const size_t ns = (size_t)c->cfg.n_scenarios, plane = (size_t)c->cfg.cx * c->cfg.cy;
+    const unsigned long long *dc, *dd;
+    if (species == 0) {
+        dc = c->d_conc + (size_t)scenario * c->ncell();
+        dd = c->d_dep + (size_t)scenario * c->ndep();
+    } else {
+        dc = c->d_sp_conc + ((size_t)(species - 1) * ns + scenario) * c->ncell();
+        dd = c->d_sp_dep + ((size_t)(species - 1) * ns + scenario) * c->ndep();
+    }
+    std::vector<unsigned long long> hc(c->ncell()), hd(c->ndep());
+    LPM_CUDA(c, cudaMemcpy(hc.data(), dc, hc.size() * 8, cudaMemcpyDeviceToHost));
+    LPM_CUDA(c, cudaMemcpy(hd.data(), dd, hd.size() * 8, cudaMemcpyDeviceToHost));
+    if (conc_fixed) std::memcpy(conc_fixed, hc.data(), hc.size() * 8);
+    if (dep_fixed) std::memcpy(dep_fixed, hd.data(), hd.size() * 8);
+    const lpm_config &g = c->cfg;
+    const double unit = std::ldexp(1.0, -c->scen[(size_t)scenario].shift);
+    if (conc)
+        for (size_t i = 0; i < hc.size(); ++i) conc[i] = (double)hc[i] * unit / (g.cdx * g.cdy * g.cdz);
+    for (int kind = 0; kind < 2; ++kind) {
+        double *out = kind ? wet : dry;
+        if (!out) continue;
+        for (size_t i = 0; i < plane; ++i)
+            out[i] = (double)hd[kind * plane + i] * unit / (g.cdx * g.cdy);
+    }
     return LPM_OK;
 }
 
@@ -1628,9 +1750,10 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
 // ---- checkpoint / resume --------------------------------------------------------
 namespace {
 struct SaveHeader {
-    char magic[8];               // "LPMSAVE2"
+    char magic[8];               // "LPMSAVE3"
     long long k, n_bins, n_slots, n_scen, ncell, ndep, n_ctr;
     long long dose_every, n_dose; // dosage interval (0: none saved) and samples taken
+    long long n_species;          // decay-chain species (daughters' grids saved when > 1)
 };
 }  // namespace
 
@@ -1642,7 +1765,8 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     const size_t bytes = sizeof(SaveHeader) + (size_t)c->n_slots_used * sizeof(float4) +
                          ns * (c->ncell() + c->ndep()) * sizeof(unsigned long long) +
                          (size_t)N_COUNTERS * ns * sizeof(unsigned long long) +
-                         (dose ? ns * c->ncell() * sizeof(unsigned long long) : 0);
+                         (dose ? ns * c->ncell() * sizeof(unsigned long long) : 0) +
+                         (size_t)(c->n_species - 1) * ns * (c->ncell() + c->ndep()) * 8;
     if (!buf) {
         *n = bytes;
         return LPM_OK;
@@ -1651,7 +1775,7 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     lpm_status st = check_device_error(c);
     if (st != LPM_OK) return st;
     SaveHeader h;
-    std::memcpy(h.magic, "LPMSAVE2", 8);
+    std::memcpy(h.magic, "LPMSAVE3", 8);
     h.k = c->k;
     h.n_bins = c->n_bins;
     h.n_slots = c->n_slots_used;
@@ -1661,6 +1785,7 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     h.n_ctr = N_COUNTERS;
     h.dose_every = dose ? c->dose_every : 0;
     h.n_dose = dose ? c->n_dose : 0;
+    h.n_species = c->n_species;
     char *o = static_cast<char *>(buf);
     std::memcpy(o, &h, sizeof h);
     o += sizeof h;
@@ -1682,9 +1807,19 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     o += ns * c->ndep() * 8;
     LPM_CUDA(c, cudaMemcpyAsync(o, c->d_ctr, ns * N_COUNTERS * 8, cudaMemcpyDeviceToHost, c->stream));
     o += ns * N_COUNTERS * 8;
-    if (dose)
+    if (dose) {
         LPM_CUDA(c, cudaMemcpyAsync(o, c->d_dose, ns * c->ncell() * 8, cudaMemcpyDeviceToHost,
                                     c->stream));
+        o += ns * c->ncell() * 8;
+    }
+    if (c->n_species > 1) {
+        const size_t nd = (size_t)(c->n_species - 1) * ns;
+        LPM_CUDA(c, cudaMemcpyAsync(o, c->d_sp_conc, nd * c->ncell() * 8, cudaMemcpyDeviceToHost,
+                                    c->stream));
+        o += nd * c->ncell() * 8;
+        LPM_CUDA(c, cudaMemcpyAsync(o, c->d_sp_dep, nd * c->ndep() * 8, cudaMemcpyDeviceToHost,
+                                    c->stream));
+    }
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     *n = bytes;
     return LPM_OK;
@@ -1699,14 +1834,16 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     if (n < sizeof h) return fail(c, LPM_E_INVALID, "buffer too small for a saved run");
     std::memcpy(&h, buf, sizeof h);
     const size_t ns = (size_t)c->cfg.n_scenarios;
-    if (std::memcmp(h.magic, "LPMSAVE2", 8) != 0 || h.n_slots != c->n_slots_used ||
+    if (std::memcmp(h.magic, "LPMSAVE3", 8) != 0 || h.n_slots != c->n_slots_used ||
+        h.n_species != c->n_species ||
         h.n_scen != (long long)ns || h.ncell != (long long)c->ncell() ||
         h.ndep != (long long)c->ndep() || h.n_ctr != N_COUNTERS || h.k < 0 ||
         h.k > c->cfg.n_steps || h.dose_every < 0 || h.dose_every > 0x7fffffffLL)
         return fail(c, LPM_E_INVALID, "saved run does not match this context");
     const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
     const size_t need = sizeof h + sb + ns * (c->ncell() + c->ndep() + N_COUNTERS) * 8 +
-                        (h.dose_every > 0 ? ns * c->ncell() * 8 : 0);
+                        (h.dose_every > 0 ? ns * c->ncell() * 8 : 0) +
+                        (size_t)(c->n_species - 1) * ns * (c->ncell() + c->ndep()) * 8;
     if (n < need) return fail(c, LPM_E_INVALID, "saved run truncated (%zu of %zu bytes)", n, need);
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
@@ -1729,9 +1866,18 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
                                         ns * (c->ncell() + c->ndep()) * 8 + (size_t)C_DOSE_OUT * ns * 8,
                                     ns * 8, cudaMemcpyHostToDevice, c->stream));
         c->n_dose = h.n_dose;
+        i += ns * c->ncell() * 8;
     } else if (c->d_dose) {
         st = lpm_set_dosage(c, 0);
         if (st != LPM_OK) return st;
+    }
+    if (c->n_species > 1) {
+        const size_t nd = (size_t)(c->n_species - 1) * ns;
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_sp_conc, i, nd * c->ncell() * 8, cudaMemcpyHostToDevice,
+                                    c->stream));
+        i += nd * c->ncell() * 8;
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_sp_dep, i, nd * c->ndep() * 8, cudaMemcpyHostToDevice,
+                                    c->stream));
     }
     LPM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
     st = clear_sort_state(c, false);     // every particle at its home slot

@@ -22,12 +22,14 @@ constexpr int TAG_SHIFT = 28;
 constexpr uint32_t TAG_STEP = 0x0FFFFFFFu;
 constexpr int MAX_LEVELS = 64;
 constexpr int MAX_LUT = 4096;          // entries of the vertical level lookup table
+constexpr int MAX_SPECIES = 4;         // decay chain: parent and up to 3 daughters
 
 // Per-scenario counters (64-bit, fixed point unless noted).
 enum {
     C_BIN_OUT = 0, C_DEP_OUT_DRY = 1, C_DEP_OUT_WET = 2, C_EXITED = 3,
     C_ACTIVE_STEPS = 4 /* count */, C_N_BINS = 5 /* count */, C_AIR_IN = 6, C_AIR_OUT = 7,
-    C_N_ACTIVE = 8 /* count */, C_DEP_DRY = 9, C_DEP_WET = 10, C_DOSE_OUT = 11, N_COUNTERS = 16
+    C_N_ACTIVE = 8 /* count */, C_DEP_DRY = 9, C_DEP_WET = 10, C_DOSE_OUT = 11,
+    C_SP_OUT = 12 /* 12..14: species 1..3 outside the grid at the snapshot */, N_COUNTERS = 16
 };
 
 // Device error word bits.
@@ -97,6 +99,13 @@ struct StepParams {
     unsigned long long *dose_all;    // [n_scen][cz][cy][cx] dosage sums, or nullptr
     int dose_every;                  // dosage sample every dose_every steps (0: off)
     float dose_mul;                  // 2^-b: dosage fixed point = snapshot fixed point / 2^b
+    // decay chain: species j's amount per unit of emitted parent after a time a is
+    // sum_{i<=j} chain_c[j][i] exp(-chain_l[i] a); species 0 is the binned mass itself
+    int n_species;                   // 1: one species
+    float chain_c[MAX_SPECIES][MAX_SPECIES];
+    float chain_l[MAX_SPECIES];
+    unsigned long long *sp_conc_all; // [n_species-1][n_scen][cz][cy][cx] species 1..
+    unsigned long long *sp_dep_all;  // [n_species-1][n_scen][2][cy][cx]
     unsigned int *err;
 };
 
@@ -112,6 +121,14 @@ __device__ __forceinline__ int col_node(const StepParams &P, int i, int j, int k
 __device__ __forceinline__ int corner_off(const StepParams &P, int m)
 {
     return (m & 1) + ((m >> 1) & 1) * P.nx + ((m >> 2) & 1) * P.nx * P.ny;
+}
+
+// Amount of chain species j per unit of emitted parent after `age` seconds.
+__device__ __forceinline__ float chain_amount(const StepParams &P, int j, float age)
+{
+    float s = 0.0f;
+    for (int i = 0; i <= j; ++i) s = fmaf(P.chain_c[j][i], expf(-P.chain_l[i] * age), s);
+    return s;
 }
 
 // Scenario holding state slot `slot` (bisection over the scenarios' first slots).

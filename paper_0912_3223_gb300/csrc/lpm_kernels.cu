@@ -176,12 +176,12 @@ cudaError_t launch_advance(const AdvanceLaunch &L)
     return cudaErrorInvalidValue;
 }
 
-int advance_occupancy(int block, int ppt, int occ, bool mixed)
+int advance_occupancy(int block, int ppt, int occ, bool mixed, bool ext)
 {
     switch (block) {
-    case 128: return occupancy_b128(ppt, occ, mixed);
-    case 256: return occupancy_b256(ppt, occ, mixed);
-    case 512: return occupancy_b512(ppt, occ, mixed);
+    case 128: return occupancy_b128(ppt, occ, mixed, ext);
+    case 256: return occupancy_b256(ppt, occ, mixed, ext);
+    case 512: return occupancy_b512(ppt, occ, mixed, ext);
     }
     return 0;
 }

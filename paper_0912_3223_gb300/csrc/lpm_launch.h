@@ -29,8 +29,7 @@ struct AdvanceLaunch {
     int k0, k1, do_bin;
     int block, ppt, occ;
     bool mixed;               // lanes of one tile may belong to different scenarios
-    bool dose;                // dosage samples inside the time loop (params->dose_every)
-    bool kz3;                 // K_z from Eq. 3 (params->blpair), 1 particle per thread
+    bool ext;                 // dosage, Eq. 3 K_z or a decay chain is on (1 particle/thread)
     unsigned int grid;
     int n_tiles() const { return ranges.tiles_a + ranges.n_b; }
 };
@@ -64,13 +63,13 @@ cudaError_t launch_release(cudaStream_t s, float4 *state, long long first_slot, 
                            float sx, float sy, float sz);
 cudaError_t launch_release_all(cudaStream_t s, const StepParams &P, float4 *state, long long n_slots);
 cudaError_t launch_advance(const AdvanceLaunch &L);
-int advance_occupancy(int block, int ppt, int occ, bool mixed);
+int advance_occupancy(int block, int ppt, int occ, bool mixed, bool ext);
 cudaError_t launch_advance_b128(const AdvanceLaunch &L);
 cudaError_t launch_advance_b256(const AdvanceLaunch &L);
 cudaError_t launch_advance_b512(const AdvanceLaunch &L);
-int occupancy_b128(int ppt, int occ, bool mixed);
-int occupancy_b256(int ppt, int occ, bool mixed);
-int occupancy_b512(int ppt, int occ, bool mixed);
+int occupancy_b128(int ppt, int occ, bool mixed, bool ext);
+int occupancy_b256(int ppt, int occ, bool mixed, bool ext);
+int occupancy_b512(int ppt, int occ, bool mixed, bool ext);
 cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
                         const float *kb, float4 *pair, float2 *khpair, int nx, int ny, int nz);
 cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &in,

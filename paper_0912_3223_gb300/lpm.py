@@ -30,7 +30,7 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
            "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save",
            "lpm_load", "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model",
-           "lpm_set_boundary_layer"]
+           "lpm_set_boundary_layer", "lpm_set_decay_chain", "lpm_species"]
 
 
 class LpmError(RuntimeError):
@@ -100,6 +100,9 @@ def load() -> C.CDLL:
     L.lpm_set_sort.argtypes = [vp, C.c_int]
     L.lpm_set_dosage.argtypes = [vp, C.c_int]
     L.lpm_set_kz_model.argtypes = [vp, C.c_int, C.c_double]
+    L.lpm_set_decay_chain.argtypes = [vp, C.c_int, dp]
+    L.lpm_species.argtypes = [vp, C.c_int, C.c_int, dp, dp, dp, C.POINTER(C.c_uint64),
+                              C.POINTER(C.c_uint64)]
     L.lpm_set_boundary_layer.argtypes = [vp, C.c_int, vp, C.c_int]
     L.lpm_dosage.argtypes = [vp, C.c_int, dp, C.c_size_t, C.POINTER(C.c_uint64), C.POINTER(i64)]
     L.lpm_save.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
@@ -117,7 +120,8 @@ def load() -> C.CDLL:
                  "lpm_draws", "lpm_release_range", "lpm_reset", "lpm_set_profiling",
                  "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
                  "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load",
-                 "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model", "lpm_set_boundary_layer"):
+                 "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model", "lpm_set_boundary_layer",
+                 "lpm_set_decay_chain", "lpm_species"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -329,6 +333,25 @@ def lpm_fixed_state(ctx, scenario: int, conc_shape, dep_shape):
     return conc, dep, ctr, int(sh.value)
 
 
+def lpm_set_decay_chain(ctx, half_lives) -> None:
+    hl = np.ascontiguousarray(half_lives, dtype=np.float64)
+    _check(ctx, load().lpm_set_decay_chain(C.c_void_p(ctx), int(hl.size), _ptr(hl, C.c_double)))
+
+
+def lpm_species(ctx, scenario: int, species: int, conc_shape, dep_shape):
+    """(conc, dry, wet, conc_fixed, dep_fixed) of one species of the decay chain."""
+    conc = np.empty(conc_shape, dtype=np.float64)
+    dry = np.empty(dep_shape, dtype=np.float64)
+    wet = np.empty(dep_shape, dtype=np.float64)
+    cf = np.empty(conc_shape, dtype=np.uint64)
+    df = np.empty((2,) + tuple(dep_shape), dtype=np.uint64)
+    _check(ctx, load().lpm_species(C.c_void_p(ctx), int(scenario), int(species),
+                                   _ptr(conc, C.c_double), _ptr(dry, C.c_double),
+                                   _ptr(wet, C.c_double), _ptr(cf, C.c_uint64),
+                                   _ptr(df, C.c_uint64)))
+    return conc, dry, wet, cf, df
+
+
 def lpm_set_kz_model(ctx, model: int, kz_min: float = 0.1) -> None:
     _check(ctx, load().lpm_set_kz_model(C.c_void_p(ctx), int(model), float(kz_min)))
 
@@ -416,6 +439,8 @@ class Sim:
             if sort_every is not None:
                 lpm_set_sort(self.ctx, sort_every)
             self._set_met(met_on_device)
+            if getattr(cfg, "chain_half_lives", None) is not None:
+                lpm_set_decay_chain(self.ctx, cfg.chain_half_lives)
             if getattr(cfg, "kz_model", 0):
                 lpm_set_kz_model(self.ctx, cfg.kz_model, cfg.kz_min)
                 for t in range(cfg.n_met_t):
@@ -489,6 +514,11 @@ class Sim:
     def fixed_state(self, scenario: int = 0):
         c = self.cfg
         return lpm_fixed_state(self.ctx, scenario, (c.cz, c.cy, c.cx), (2, c.cy, c.cx))
+
+    def species(self, species: int, scenario: int = 0):
+        """(conc, dry, wet, conc_fixed, dep_fixed) of a decay-chain species."""
+        c = self.cfg
+        return lpm_species(self.ctx, scenario, species, (c.cz, c.cy, c.cx), (c.cy, c.cx))
 
     def set_dosage(self, every_steps: int):
         lpm_set_dosage(self.ctx, every_steps)
