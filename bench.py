@@ -41,8 +41,8 @@ OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
 # DRAM traffic per advance launch from the ncu capture summarised in
 # profiles/advance_kernel_plain_1e7x2880.md (mean of the two captured 60-step launches of
 # hours 6-7, read + write), valid while the kernel sources hash to the values recorded there.
-ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.100992 + 0.000256) + (23.585536 + 0.002048)) * 1e6
-ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "81e6400f", "lpm_device.cuh": "0e18b73b"}
+ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.098688 + 0.0) + (23.586560 + 0.001024)) * 1e6
+ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "532964cf", "lpm_device.cuh": "c40026dc"}
 SM_COUNT = 152
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
 SM_MAX_MHZ = 2070.0
