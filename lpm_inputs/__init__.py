@@ -125,6 +125,9 @@ class LpmConfig:
     # decay chain: half-lives (s) of parent -> daughter -> ..., the first = half_life_s,
     # 0 = stable (last only); None: one species
     chain_half_lives: Optional[np.ndarray] = None
+    # vertical Langevin variant (velocity memory over the Lagrangian time scale t_lagr, s)
+    langevin: int = 0
+    t_lagr: float = 100.0
     name: str = ""
 
     @property

@@ -58,6 +58,7 @@ class OCfg(C.Structure):
         ("dose_every", C.c_int),
         ("kz_model", C.c_int), ("kz_min", C.c_double), ("bl", C.POINTER(C.c_float)),
         ("n_species", C.c_int), ("chain_half_life", C.POINTER(C.c_double)),
+        ("langevin", C.c_int), ("t_lagr", C.c_double),
     ]
 
 
@@ -72,6 +73,7 @@ class OOut(C.Structure):
         ("dose_ctr", C.POINTER(C.c_int64)),
         ("sp_conc", C.POINTER(C.c_double)), ("sp_conc_fixed", C.POINTER(C.c_int64)),
         ("sp_dep", C.POINTER(C.c_double)), ("sp_dep_fixed", C.POINTER(C.c_int64)),
+        ("wvel", C.POINTER(C.c_double)),
     ]
 
 
@@ -195,6 +197,8 @@ def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
     chain = getattr(cfg, "chain_half_lives", None)
     o.n_species = 0 if chain is None else len(chain)
     o.chain_half_life = _ptr(pin.arr(chain, np.float64), C.c_double)
+    o.langevin = int(getattr(cfg, "langevin", 0))
+    o.t_lagr = float(getattr(cfg, "t_lagr", 0.0))
     o._pin = pin  # keep arrays alive with the record
     return o
 
@@ -322,7 +326,7 @@ def run(cfg, sel=None, n_run: Optional[int] = None, **kw) -> dict:
         margin=np.zeros(n), conc=np.zeros((cfg.cz, cfg.cy, cfg.cx)),
         conc_fixed=np.zeros((cfg.cz, cfg.cy, cfg.cx), np.int64),
         dep=np.zeros((2, cfg.cy, cfg.cx)), dep_fixed=np.zeros((2, cfg.cy, cfg.cx), np.int64),
-        budget=np.zeros(8), counters=np.zeros(6, np.int64),
+        budget=np.zeros(8), counters=np.zeros(6, np.int64), wvel=np.zeros(n),
         dose=np.zeros((cfg.cz, cfg.cy, cfg.cx)),
         dose_fixed=np.zeros((cfg.cz, cfg.cy, cfg.cx), np.int64), dose_ctr=np.zeros(2, np.int64))
     n_sp = int(o.n_species)
@@ -339,7 +343,8 @@ def run(cfg, sel=None, n_run: Optional[int] = None, **kw) -> dict:
               _ptr(out["dose"], C.c_double), _ptr(out["dose_fixed"], C.c_int64),
               _ptr(out["dose_ctr"], C.c_int64),
               _ptr(out.get("sp_conc"), C.c_double), _ptr(out.get("sp_conc_fixed"), C.c_int64),
-              _ptr(out.get("sp_dep"), C.c_double), _ptr(out.get("sp_dep_fixed"), C.c_int64))
+              _ptr(out.get("sp_dep"), C.c_double), _ptr(out.get("sp_dep_fixed"), C.c_int64),
+              _ptr(out["wvel"], C.c_double))
     assert ncell == out["conc"].size
     rc = lib().oracle_run(C.byref(o), _ptr(sel, C.c_int64), n, int(n_run), C.byref(oo))
     if rc != 0:

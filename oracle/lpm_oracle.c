@@ -141,7 +141,20 @@ typedef struct {
      * only for the last), the first equal to half_life_s; n_species <= 1: one species */
     int n_species;
     const double *chain_half_life;
+    /* vertical Langevin (velocity-memory) variant: 0 = the random walk of Eq. 2 */
+    int langevin;
+    double t_lagr;                   /* Lagrangian time scale T_L (s) */
 } ocfg;
+
+/* The normal of stream 2 at (particle, step): the vertical turbulent velocity a particle
+ * of the Langevin variant starts with at its release step (Box-Muller on words 0, 1). */
+static double release_normal(uint64_t seed, uint64_t pid, uint32_t step)
+{
+    uint32_t w[4];
+    oracle_draw(seed, pid, step, 2u, w);
+    return sqrt(-2.0 * log(oracle_uniform(w[0]))) * cos(6.283185307179586476925286766559 *
+                                                         oracle_uniform(w[1]));
+}
 
 /* ---------------------------------------------------------------------------------
  * Release schedule (Sec. 3.2: a priori assignment of masses from the emission profile
@@ -507,6 +520,7 @@ typedef struct {
     int64_t *sp_conc_fixed;
     double *sp_dep;       /* [n_species][2][cy][cx] */
     int64_t *sp_dep_fixed;
+    double *wvel;         /* [n_sel] turbulent vertical velocity (Langevin variant), or NULL */
 } oout;
 
 static int64_t fixed_of(double m, int shift)
@@ -539,8 +553,11 @@ static ostep step_constants(const ocfg *c)
  * the particle from any decision boundary it met this step. Also returns, for the
  * adjoint, the sign of dz/dz_pre from the folds (+1/-1, 0 if clamped), the normals and
  * the weather sample. */
+#define LANGEVIN_SIG2_MIN 1e-6   /* floor of sigma_w^2 (m^2/s^2) */
+
 static int particle_step(const ocfg *c, const ostep *K, uint64_t gid, int64_t k, double X[3],
-                         double *margin, double *fold, double nrm[3], double met[6])
+                         double *margin, double *fold, double nrm[3], double met[6],
+                         double *wv, int released)
 {
     const double t = (double)k * c->dt;
     /* 1. sample the weather at the old position and the step's start time */
@@ -553,8 +570,24 @@ static int particle_step(const ocfg *c, const ostep *K, uint64_t gid, int64_t k,
     double u = met[0] + c->bias_u, v = met[1] + c->bias_v, w = met[2];
     X[0] = X[0] + u * c->dt + nrm[0] * sqrt(2.0 * kh * c->dt);
     X[1] = X[1] + v * c->dt + nrm[1] * sqrt(2.0 * kh * c->dt);
-    X[2] = X[2] + w * c->dt + nrm[2] * sqrt(2.0 * kz * c->dt);
-    if (c->drift_correction) X[2] += c->k_scale * met[5] * c->dt;
+    if (wv) {
+        /* vertical Langevin variant (Thomson's well-mixed model for Gaussian turbulence of
+         * variance sigma_w^2(z) = K_z / T_L): the turbulent velocity w' relaxes over T_L,
+         * is kicked by sqrt(2 sigma_w^2 dt / T_L) n, and drifts by
+         * (1 + w'^2 / sigma_w^2) d(sigma_w^2)/dz dt / 2; the position follows w + w'. A
+         * particle starts with w' = sigma_w n' (n' from stream 2 at its release step). */
+        double s2 = kz / c->t_lagr, ds2 = c->k_scale * met[5] / c->t_lagr;
+        if (s2 < LANGEVIN_SIG2_MIN) { s2 = LANGEVIN_SIG2_MIN; ds2 = 0.0; }
+        if (released) *wv = sqrt(s2) * release_normal(c->seed, gid, (uint32_t)k);
+        double wp = *wv;
+        wp = wp - wp / c->t_lagr * c->dt + 0.5 * (1.0 + wp * wp / s2) * ds2 * c->dt +
+             sqrt(2.0 * s2 * c->dt / c->t_lagr) * nrm[2];
+        *wv = wp;
+        X[2] = X[2] + (w + wp) * c->dt;
+    } else {
+        X[2] = X[2] + w * c->dt + nrm[2] * sqrt(2.0 * kz * c->dt);
+        if (c->drift_correction) X[2] += c->k_scale * met[5] * c->dt;
+    }
     /* 5. reflection at the ground and the top, folded at most 4 times, then clamped */
     *fold = 1.0;
     for (int it = 0; it < 4; ++it) {
@@ -564,6 +597,7 @@ static int particle_step(const ocfg *c, const ostep *K, uint64_t gid, int64_t k,
     }
     if (c->reflect_ground && X[2] < 0.0) { X[2] = 0.0; *fold = 0.0; }
     if (c->reflect_top && X[2] > c->z_top) { X[2] = c->z_top; *fold = 0.0; }
+    if (wv) *wv *= *fold;                /* a reflection reverses the turbulent velocity */
     /* leaving the horizontal domain inactivates the particle */
     if (c->lateral_exit) {
         double d = fmin(fmin(fabs(X[0] - K->x_lo), fabs(X[0] - K->x_hi)),
@@ -619,7 +653,12 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
     int64_t *sp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int64_t *tev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     double *mg = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    if (!P || !st || !sp || !tev || !mg) { free(P); free(st); free(sp); free(tev); free(mg); return 2; }
+    double *W = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!P || !st || !sp || !tev || !mg || !W) {
+        free(P); free(st); free(sp); free(tev); free(mg); free(W);
+        return 2;
+    }
+    if (c->langevin && !(c->t_lagr > 0.0)) { free(P); free(st); free(sp); free(tev); free(mg); free(W); return 1; }
     for (int64_t q = 0; q < n; ++q) {
         int64_t p = sel ? sel[q] : q;
         sp[q] = oracle_release_step(c->n_particles, c->first_step, c->last_step, p);
@@ -674,7 +713,8 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
             if (st[q] != OR_ACTIVE) continue;
             ++steps;
             double fold, nrm[3], met[6];
-            int ns = particle_step(c, &K, gid, k, X, &mg[q], &fold, nrm, met);
+            int ns = particle_step(c, &K, gid, k, X, &mg[q], &fold, nrm, met,
+                                   c->langevin ? &W[q] : NULL, sp[q] == k);
             if (ns == OR_EXITED) {
                 st[q] = OR_EXITED;
                 tev[q] = k;
@@ -806,8 +846,9 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
         o->status[q] = st[q];
         o->release[q] = sp[q];
         o->margin[q] = mg[q];
+        if (o->wvel) o->wvel[q] = W[q];
     }
-    free(P); free(st); free(sp); free(tev); free(mg);
+    free(P); free(st); free(sp); free(tev); free(mg); free(W);
     return 0;
 }
 
@@ -1001,7 +1042,8 @@ static int trace_particle(const ocfg *c, const ostep *K, int64_t p, int64_t n_ru
         size_t s = (size_t)(k - o->sp);
         memcpy(o->X + 3 * s, X, sizeof X);
         double met[6];
-        int st = particle_step(c, K, gid, k, X, &o->margin, &o->fold[s], o->nrm + 3 * s, met);
+        int st = particle_step(c, K, gid, k, X, &o->margin, &o->fold[s], o->nrm + 3 * s, met,
+                               NULL, 0);
         o->kend = k;
         if (st != OR_ACTIVE) {
             o->status = st;
@@ -1044,6 +1086,7 @@ static double kernel_g(const double X[3], const double r[3], double sigma, doubl
 int oracle_receptors(const ocfg *c, const double *rec, int R, double sigma, int every,
                      const int64_t *sel, int64_t n_sel, int64_t n_run, double *C)
 {
+    if (c->langevin) return 1;      /* the traced paths follow Eq. 2 only */
     if (R < 0 || !(sigma > 0.0) || every < 1) return 1;
     const ostep K = step_constants(c);
     const int ns = n_samples(n_run, every);
@@ -1075,6 +1118,7 @@ int oracle_receptors(const ocfg *c, const double *rec, int R, double sigma, int 
 int oracle_adjoint(const ocfg *c, const double *rec, int R, double sigma, int every,
                    const double *w, const int64_t *sel, int64_t n_sel, int64_t n_run, double *grad)
 {
+    if (c->langevin) return 1;      /* the traced paths follow Eq. 2 only */
     if (R < 0 || !(sigma > 0.0) || every < 1 || c->drift_correction) return 1;
     const ostep K = step_constants(c);
     const int ns = n_samples(n_run, every);
@@ -1136,6 +1180,7 @@ int oracle_adjoint(const ocfg *c, const double *rec, int R, double sigma, int ev
  * parity tests use them to recognise chaotic paths. */
 int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, double *out)
 {
+    if (c->langevin) return 1;      /* the traced paths follow Eq. 2 only */
     const ostep K = step_constants(c);
     int64_t n = sel ? n_sel : c->n_particles;
     for (int64_t q = 0; q < n; ++q) {

@@ -663,3 +663,57 @@ def test_chain_grids_per_species():
     for j in range(3):
         want = sum((1.0 * cfg.dt / counts[s]) * amount[a][j] for s, a in zip(sp, ages))
         assert r["sp_conc"][j].sum() == pytest.approx(want, rel=1e-9)
+
+
+# ------------------------------------------------------------------------------------
+# Vertical Langevin (velocity-memory) variant of the random walk
+# ------------------------------------------------------------------------------------
+def _langevin_column(K_of_z, H, n, steps, dt, t_lagr, src_z, reflect=True, nz=21):
+    z_levels = np.linspace(0.0, H, nz)
+    uvwk = np.zeros((2, nz, 2, 2, 4), np.float32)
+    uvwk[..., 3] = K_of_z(z_levels)[None, :, None, None]
+    cfg = li.make_cfg0(n_particles=n, n_steps=steps, kh=0.0, kz=0.0, u=0.0, src=(0.0, 0.0, src_z))
+    return dataclasses.replace(cfg, uvwk=uvwk, z_levels=z_levels, nz=nz, dt=dt,
+                               reflect_ground=int(reflect), reflect_top=int(reflect), z_top=H,
+                               langevin=1, t_lagr=t_lagr,
+                               release=li.Release(n, np.array([1.0]), 3600.0, 0, 1))
+
+
+def test_langevin_discrete_laws_in_homogeneous_turbulence():
+    """Constant K_z far from the walls: w' and z after m steps are jointly Gaussian with the
+    covariance of the linear update w <- (1 - dt/T_L) w + sqrt(2 s2 dt / T_L) n,
+    z <- z + dt w (w starting as sqrt(s2) n' at release, s2 = K_z / T_L), propagated here
+    exactly; KS tests on w' and z. Catches a wrong relaxation, kick or initial variance,
+    or the position following the old velocity."""
+    K, T, dt, m, n = 20.0, 50.0, 2.0, 60, 6000
+    cfg = _langevin_column(lambda z: np.full_like(z, K), 20000.0, n, m, dt, T, 10000.0,
+                           reflect=False)
+    r = oracle.run(cfg)
+    s2 = K / T
+    a, b = 1.0 - dt / T, math.sqrt(2.0 * s2 * dt / T)
+    A = np.array([[a, 0.0], [dt * a, 1.0]])
+    B = np.array([[b], [dt * b]])
+    C = np.array([[s2, 0.0], [0.0, 0.0]])              # (w', z) at release, before the step
+    for _ in range(m):
+        C = A @ C @ A.T + B @ B.T
+    assert stats.kstest(r["wvel"] / math.sqrt(C[0, 0]), "norm").pvalue > 1e-3
+    assert stats.kstest((r["pos"][:, 2] - 10000.0) / math.sqrt(C[1, 1]), "norm").pvalue > 1e-3
+    # and the velocity keeps its memory: lag-m correlation a^m against the release draw
+    assert np.corrcoef(r["wvel"], r["pos"][:, 2])[0, 1] == pytest.approx(
+        C[0, 1] / math.sqrt(C[0, 0] * C[1, 1]), abs=0.05)
+
+
+def test_langevin_well_mixed_in_an_inhomogeneous_column():
+    """K_z = K0 + K1 z in a reflecting column: with the drift term of the well-mixed model
+    a uniform state stays uniform and the turbulent velocity at height z has variance
+    K_z(z) / T_L. Catches a missing or mis-signed drift term and a wrong reflection."""
+    H, K0, K1, T, dt = 100.0, 2.0, 0.3, 20.0, 1.0
+    n, steps = 8000, 3000
+    cfg = _langevin_column(lambda z: K0 + K1 * z, H, n, steps, dt, T, 50.0)
+    r = oracle.run(cfg)
+    z, w = r["pos"][:, 2], r["wvel"]
+    assert stats.kstest(z / H, "uniform").pvalue > 1e-3
+    for lo in (0.0, 40.0, 80.0):
+        sel = (z >= lo) & (z < lo + 20.0)
+        want = (K0 + K1 * (lo + 10.0)) / T
+        assert np.var(w[sel]) == pytest.approx(want, rel=0.12)
