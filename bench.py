@@ -445,6 +445,40 @@ def measure_decay_chain(args, stream):
             "steps_per_run": cfg.n_steps}
 
 
+def measure_langevin(args, stream):
+    """The plain realistic run with the vertical Langevin (velocity-memory) variant,
+    T_L = 100 s."""
+    import dataclasses
+
+    import torch
+
+    import lpm_inputs as li
+    from paper_0912_3223_gb300 import Sim
+    cfg = dataclasses.replace(li.make_cfg1(), langevin=1, t_lagr=100.0)
+    with torch.cuda.stream(stream):
+        sim = Sim(cfg, stream=stream, launch=(args.block, 1, args.occ),
+                  sort_every=args.sort_every)
+    try:
+        times = []
+        for i in range(max(1, args.warmup) + 2):
+            sim.reset()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(cfg.n_steps)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= max(1, args.warmup):
+                times.append(e0.elapsed_time(e1))
+        active = int(sim.fixed_state()[2][4])
+    finally:
+        sim.close()
+    ms = statistics.mean(times)
+    return {"value": active / (ms / 1e3), "unit": UNIT, "ms_per_run": ms, "t_lagr_s": cfg.t_lagr,
+            "particles": cfg.n_particles, "steps_per_run": cfg.n_steps}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -577,7 +611,8 @@ def run_gpu(args):
                  "inversion": measure_inversion(args, stream),
                  "dosage": measure_dosage(args, stream),
                  "kz_eq3": measure_kz_eq3(args, stream),
-                 "decay_chain": measure_decay_chain(args, stream)}
+                 "decay_chain": measure_decay_chain(args, stream),
+                 "langevin": measure_langevin(args, stream)}
         if not args.no_stress:
             forms["stress"] = measure_stress(args, stream)
         for f in forms.values():
@@ -609,7 +644,7 @@ def main():
                     help="skip the batched and adjoint forms")
     ap.add_argument("--no-stress", action="store_true", help="skip the 1e8-particle stress case")
     ap.add_argument("--only", choices=["batched", "adjoint", "inversion", "stress", "dosage",
-                                       "kz_eq3", "decay_chain"],
+                                       "kz_eq3", "decay_chain", "langevin"],
                     default=None,
                     help="run one form alone and print its measurement (profiling aid)")
     ap.add_argument("--batched-block", type=int, default=256)
@@ -628,7 +663,7 @@ def main():
         fn = {"batched": measure_batched, "adjoint": measure_adjoint,
               "inversion": measure_inversion, "stress": measure_stress,
               "dosage": measure_dosage, "kz_eq3": measure_kz_eq3,
-              "decay_chain": measure_decay_chain}[args.only]
+              "decay_chain": measure_decay_chain, "langevin": measure_langevin}[args.only]
         print(json.dumps({"form": args.only, **fn(args, stream)}), flush=True)
         return 0
     return run_gpu(args)

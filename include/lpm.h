@@ -220,6 +220,26 @@ lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int
 lpm_status lpm_set_sort(lpm_ctx *ctx, int every_steps);
 
 /*
+ * Vertical Langevin (velocity-memory) variant of the random walk of Eq. 2 (no paper
+ * counterpart: the paper moves particles by Eq. 1-2 only). Each particle carries a
+ * turbulent vertical velocity w', updated every step by Thomson's well-mixed model for
+ * Gaussian turbulence with sigma_w^2 = K_z / T_L: w' <- w' - w' dt / T_L
+ * + (1 + w'^2 / sigma_w^2) d(sigma_w^2)/dz dt / 2 + sqrt(2 sigma_w^2 dt / T_L) n; then
+ * z <- z + (w + w') dt. Reflections reverse w'; a particle starts with sigma_w n' at its
+ * release step (n' from Philox stream 2, words 0 and 1, Box-Muller). The horizontal motion
+ * stays Eq. 2; drift_correction is ignored (the model carries its own drift term). For
+ * dt >> T_L the model reduces to the random walk with the same K_z.
+ *
+ * lpm_set_langevin: on (0/1) and T_L (s, > 0); before the first step or after lpm_reset
+ * (LPM_E_STATE otherwise). Allocates 12 bytes per particle slot. Runs with one particle
+ * per thread; not supported by lpm_adjoint (LPM_E_INVALID).
+ * lpm_particle_velocity: w' (m/s) of slots [first, first+count) to host (0 for deposited or
+ * exited particles). Synchronises.
+ */
+lpm_status lpm_set_langevin(lpm_ctx *ctx, int on, double t_lagr);
+lpm_status lpm_particle_velocity(lpm_ctx *ctx, int64_t first, int64_t count, float *w);
+
+/*
  * Decay chain (Sec. 2: released particles "can transform to other species" by
  * radioactive decay, deterministic from the half-lives). The emitted parent (species 0,
  * the configured half_life_s) decays into species 1, which decays into species 2, ...:

@@ -232,7 +232,8 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
                                                   const StepTime &T, const ScenDev &sc,
                                                   const ScenDev *scg, unsigned long long gid,
                                                   int sp, float sig_h_uniform, float du, float dv,
-                                                  float &x, float &y, float &z, float *fold)
+                                                  float &x, float &y, float &z, float *fold,
+                                                  float *wv = nullptr)
 {
     const int k = T.k;
     // 1. weather at the old position and t_k; 2. diffusivities
@@ -247,8 +248,32 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
     // 4. Eq. (1)-(2): wind then turbulent displacement
     const float xn = x + (m.u + du) * P.dt + n0 * sig_h;
     const float yn = y + (m.v + dv) * P.dt + n1 * sig_h;
-    float zn = z + m.w * P.dt + n2 * sig_z;
-    if (P.drift) zn += P.k_scale * m.dkz * P.dt;
+    float zn;
+    if (EXT && wv) {
+        // vertical Langevin variant (well-mixed for Gaussian turbulence of variance
+        // sigma_w^2 = K_z / T_L): w' relaxes over T_L, is kicked by sqrt(2 sigma^2 dt / T_L) n
+        // and drifts by (1 + w'^2 / sigma^2) d(sigma^2)/dz dt / 2; z follows w + w'. At its
+        // release step a particle starts with sigma_w n' (n' from stream 2).
+        float s2 = P.k_scale * m.kz / P.t_lagr, ds2 = P.k_scale * m.dkz / P.t_lagr;
+        if (s2 < 1e-6f) {
+            s2 = 1e-6f;
+            ds2 = 0.0f;
+        }
+        if (sp == k) {
+            const U4 r = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 2u,
+                                       P.seed_lo, P.seed_hi);
+            *wv = sqrtf(s2) * sqrtf(-2.0f * logf(unit_uniform(r.a))) *
+                  cospif(2.0f * unit_uniform(r.b));
+        }
+        float wp = *wv;
+        wp = wp - wp / P.t_lagr * P.dt + 0.5f * (1.0f + wp * wp / s2) * ds2 * P.dt +
+             sqrtf(2.0f * s2 * P.dt / P.t_lagr) * n2;
+        *wv = wp;
+        zn = z + (m.w + wp) * P.dt;
+    } else {
+        zn = z + m.w * P.dt + n2 * sig_z;
+        if (P.drift) zn += P.k_scale * m.dkz * P.dt;
+    }
     // 5. reflection, at most 4 folds, then clamp
     float fs = 1.0f;
 #pragma unroll 1
@@ -260,6 +285,7 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
     if (P.reflect_ground && zn < 0.0f) { zn = 0.0f; fs = 0.0f; }
     if (P.reflect_top && zn > P.z_top) { zn = P.z_top; fs = 0.0f; }
     if (fold) *fold = fs;
+    if (EXT && wv) *wv *= fs;            // a reflection reverses the turbulent velocity
     x = xn; y = yn; z = zn;
     if (!isfinite(xn + yn + zn)) {
         atomicOr(P.err, ERR_NAN);
@@ -375,6 +401,9 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         uint32_t tag[PPT];
         unsigned long long gid[PPT];
         int sj[PPT];                                    // scenario of each particle (MIXED)
+        float wv[PPT];                                  // Langevin w' (EXT)
+        float *wsrc = in_a ? R.w_a : R.w_b;
+        const bool lang = EXT && P.langevin && wsrc;
         int live = 0;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
@@ -394,12 +423,14 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                 const float4 s = state[slot];
                 x[j] = s.x; y[j] = s.y; z[j] = s.z;
                 tag[j] = __float_as_uint(s.w);
+                wv[j] = lang ? wsrc[slot] : 0.0f;
                 const uint32_t st = tag[j] >> TAG_SHIFT;
                 const int sp = (int)(tag[j] & TAG_STEP);
                 if (st == ST_ACTIVE || (st == ST_UNRELEASED && sp < k1)) ++live;
             } else {
                 x[j] = y[j] = z[j] = 0.0f;
                 tag[j] = ST_EXITED << TAG_SHIFT;
+                wv[j] = 0.0f;
             }
         }
 
@@ -459,11 +490,12 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                     }
                     st = particle_step<true, EXT>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
                                                   sp, sig_h_uniform, du, dv, x[j], y[j], z[j],
-                                                  nullptr);
+                                                  nullptr, lang ? &wv[j] : nullptr);
                 } else {
                     ++steps;
                     st = particle_step<true, EXT>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
-                                                  T.du, T.dv, x[j], y[j], z[j], nullptr);
+                                                  T.du, T.dv, x[j], y[j], z[j], nullptr,
+                                                  lang ? &wv[j] : nullptr);
                 }
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;
@@ -502,8 +534,12 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             const int local = j * BLOCK + threadIdx.x;
-            if (local < count)
+            if (local < count) {
                 state[first + local] = make_float4(x[j], y[j], z[j], __uint_as_float(tag[j]));
+                // only a moving particle has a turbulent velocity (0 once deposited or
+                // exited, and before its release)
+                if (lang) wsrc[first + local] = (tag[j] >> TAG_SHIFT) == ST_ACTIVE ? wv[j] : 0.0f;
+            }
         }
 
         // ---- end-of-segment concentration snapshot (every n-th step, Sec. 3.2) --------

@@ -119,6 +119,12 @@ struct lpm_ctx {
     unsigned long long *d_sp_conc = nullptr;  // [n_species-1][n_scen][cz*cy*cx]
     unsigned long long *d_sp_dep = nullptr;   // [n_species-1][n_scen][2*cy*cx]
 
+    // vertical Langevin variant: turbulent velocity per particle (home and sorted slots)
+    int langevin = 0;
+    double t_lagr = 100.0;
+    float *d_w_home = nullptr;
+    float *d_w_sorted[2] = {nullptr, nullptr};
+
     // time-integrated dosage
     unsigned long long *d_dose = nullptr;   // [n_scen][cz*cy*cx]
     int dose_every = 0;
@@ -308,6 +314,8 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     }
     P.sp_conc_all = c->d_sp_conc;
     P.sp_dep_all = c->d_sp_dep;
+    P.langevin = c->langevin;
+    P.t_lagr = (float)c->t_lagr;
     P.kz_min = (float)c->kz_min;
     P.err = c->d_err;
 }
@@ -553,7 +561,9 @@ lpm_status clear_sort_state(lpm_ctx *c, bool move_back)
     if (c->d_sorted[0]) {
         if (move_back && c->sorted_upto > 0)
             LPM_CUDA(c, launch_unsort(c->stream, c->d_state, c->d_sorted[c->cur], c->d_slot_of,
-                                      c->d_grave, c->n_slots_used));
+                                      c->d_grave, c->n_slots_used,
+                                      c->langevin ? c->d_w_home : nullptr,
+                                      c->langevin ? c->d_w_sorted[c->cur] : nullptr));
         else
             LPM_CUDA(c, cudaMemsetAsync(c->d_slot_of, 0xff,
                                         (size_t)c->cfg.max_particles * sizeof(unsigned int),
@@ -717,7 +727,8 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_rgrad, c->d_adj_tiles, c->d_sorted[0], c->d_sorted[1], c->d_pidx[0],
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
                     c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair,
-                    c->d_sp_conc, c->d_sp_dep};
+                    c->d_sp_conc, c->d_sp_dep, c->d_w_home, c->d_w_sorted[0],
+                    c->d_w_sorted[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -875,6 +886,9 @@ lpm_status lpm_reset(lpm_ctx *c)
         LPM_CUDA(c, cudaMemsetAsync(c->d_sp_conc, 0, nd * c->ncell() * 8, c->stream));
         LPM_CUDA(c, cudaMemsetAsync(c->d_sp_dep, 0, nd * c->ndep() * 8, c->stream));
     }
+    if (c->d_w_home)
+        LPM_CUDA(c, cudaMemsetAsync(c->d_w_home, 0, (size_t)c->cfg.max_particles * sizeof(float),
+                                    c->stream));
     c->k = 0;
     c->n_bins = 0;
     c->n_dose = 0;
@@ -966,6 +980,8 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             in.b_first = sg.sort_b_lo;
             in.n_b = sg.sort_b_hi - sg.sort_b_lo;
             in.T = T;
+            in.w_a = c->langevin ? c->d_w_sorted[cur] : nullptr;
+            in.w_b = c->langevin ? c->d_w_home : nullptr;
             SortBuffers out{};
             out.state_out = c->d_sorted[1 - cur];
             out.pidx_out = c->d_pidx[1 - cur];
@@ -976,6 +992,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             out.meta = c->d_live;
             out.grave = c->d_grave;
             out.grave_count = c->d_grave_n;
+            out.w_out = c->langevin ? c->d_w_sorted[1 - cur] : nullptr;
             LPM_CUDA(c, launch_sort(s, P, in, out));
             cur = 1 - cur;
             upto = sg.k;
@@ -992,6 +1009,8 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.ranges.b_tiles = c->d_tiles;
         L.ranges.b_first = sg.b_lo;
         L.ranges.n_b = sg.b_hi - sg.b_lo;
+        L.ranges.w_a = c->langevin ? c->d_w_sorted[cur] : nullptr;
+        L.ranges.w_b = c->langevin ? c->d_w_home : nullptr;
         L.k0 = (int)sg.k;
         L.k1 = (int)sg.e;
         L.do_bin = sg.do_bin ? 1 : 0;
@@ -999,7 +1018,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.ppt = c->ppt;
         L.occ = c->occ;
         L.mixed = batched;
-        L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1;
+        L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 || P.langevin;
         const int n_tiles = L.n_tiles();
         if (n_tiles <= 0) continue;
         if (batched) {
@@ -1054,10 +1073,11 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
                 return fail(c, LPM_E_STATE, "boundary-layer slab %lld not set", h);
         }
     }
-    const bool ext = (c->d_dose && c->dose_every > 0) || c->kz_model == 1 || c->n_species > 1;
+    const bool ext = (c->d_dose && c->dose_every > 0) || c->kz_model == 1 || c->n_species > 1 ||
+                     c->langevin;
     if (ext && c->ppt != 1)
-        return fail(c, LPM_E_INVALID,
-                    "dosage, K_z from Eq. 3 and decay chains run with 1 particle per thread");
+        return fail(c, LPM_E_INVALID, "dosage, K_z from Eq. 3, decay chains and the Langevin "
+                                      "variant run with 1 particle per thread");
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
     if (!c->tiles_valid) {
@@ -1344,6 +1364,45 @@ lpm_status lpm_set_sort(lpm_ctx *c, int every_steps)
     return LPM_OK;
 }
 
+lpm_status lpm_set_langevin(lpm_ctx *c, int on, double t_lagr)
+{
+    if (!c) return LPM_E_INVALID;
+    if (c->k != 0) return fail(c, LPM_E_STATE, "choose the Langevin variant before stepping (or after lpm_reset)");
+    if (on && (!is_finite(t_lagr) || !(t_lagr > 0)))
+        return fail(c, LPM_E_INVALID, "the Lagrangian time scale must be > 0");
+    if (on && !c->d_w_home) {
+        const size_t n = (size_t)c->cfg.max_particles;
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        LPM_CUDA(c, cudaMalloc(&c->d_w_home, n * sizeof(float)));
+        for (int b = 0; b < 2; ++b) LPM_CUDA(c, cudaMalloc(&c->d_w_sorted[b], n * sizeof(float)));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_w_home, 0, n * sizeof(float), c->stream));
+    }
+    c->langevin = on ? 1 : 0;
+    if (on) c->t_lagr = t_lagr;
+    drop_graphs(c);                          // the graphs hold the step parameters
+    return LPM_OK;
+}
+
+lpm_status lpm_particle_velocity(lpm_ctx *c, int64_t first, int64_t count, float *w)
+{
+    if (!c || !w) return LPM_E_INVALID;
+    if (!c->langevin) return fail(c, LPM_E_STATE, "the Langevin variant is off");
+    if (first < 0 || count < 0 || first + count > c->n_slots_used)
+        return fail(c, LPM_E_INVALID, "slots [%lld, %lld) outside the %lld released",
+                    (long long)first, (long long)(first + count), c->n_slots_used);
+    lpm_status st = check_device_error(c);
+    if (st != LPM_OK) return st;
+    if (count == 0) return LPM_OK;
+    float *tmp = c->d_w_sorted[1 - c->cur];  // free until the next sort
+    LPM_CUDA(c, launch_gather_w(c->stream, c->d_w_home, c->d_w_sorted[c->cur], c->d_slot_of,
+                                first, count, tmp));
+    LPM_CUDA(c, cudaMemcpyAsync(w, tmp, (size_t)count * sizeof(float), cudaMemcpyDeviceToHost,
+                                c->stream));
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->n_launches++;
+    return LPM_OK;
+}
+
 lpm_status lpm_set_decay_chain(lpm_ctx *c, int n_species, const double *half_lives)
 {
     if (!c) return LPM_E_INVALID;
@@ -1593,6 +1652,7 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     if (!(bandwidth > 0) || every < 1) return fail(c, LPM_E_INVALID, "bandwidth > 0 and every >= 1");
     if (g.drift_correction) return fail(c, LPM_E_INVALID, "the adjoint does not support drift_correction");
     if (c->kz_model != 0) return fail(c, LPM_E_INVALID, "the adjoint does not support K_z from Eq. 3");
+    if (c->langevin) return fail(c, LPM_E_INVALID, "the adjoint does not support the Langevin variant");
     if (c->n_released != g.n_scenarios)
         return fail(c, LPM_E_STATE, "%d of %d scenarios released", c->n_released, g.n_scenarios);
     if (adj_nq(c) > MAX_NQ) return fail(c, LPM_E_INVALID, "emission series longer than %d", MAX_NQ);
@@ -1750,10 +1810,11 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
 // ---- checkpoint / resume --------------------------------------------------------
 namespace {
 struct SaveHeader {
-    char magic[8];               // "LPMSAVE3"
+    char magic[8];               // "LPMSAVE4"
     long long k, n_bins, n_slots, n_scen, ncell, ndep, n_ctr;
     long long dose_every, n_dose; // dosage interval (0: none saved) and samples taken
     long long n_species;          // decay-chain species (daughters' grids saved when > 1)
+    long long langevin;           // the Langevin w' of every slot follows when 1
 };
 }  // namespace
 
@@ -1766,7 +1827,8 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
                          ns * (c->ncell() + c->ndep()) * sizeof(unsigned long long) +
                          (size_t)N_COUNTERS * ns * sizeof(unsigned long long) +
                          (dose ? ns * c->ncell() * sizeof(unsigned long long) : 0) +
-                         (size_t)(c->n_species - 1) * ns * (c->ncell() + c->ndep()) * 8;
+                         (size_t)(c->n_species - 1) * ns * (c->ncell() + c->ndep()) * 8 +
+                         (c->langevin ? (size_t)c->n_slots_used * sizeof(float) : 0);
     if (!buf) {
         *n = bytes;
         return LPM_OK;
@@ -1775,7 +1837,7 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     lpm_status st = check_device_error(c);
     if (st != LPM_OK) return st;
     SaveHeader h;
-    std::memcpy(h.magic, "LPMSAVE3", 8);
+    std::memcpy(h.magic, "LPMSAVE4", 8);
     h.k = c->k;
     h.n_bins = c->n_bins;
     h.n_slots = c->n_slots_used;
@@ -1786,6 +1848,7 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     h.dose_every = dose ? c->dose_every : 0;
     h.n_dose = dose ? c->n_dose : 0;
     h.n_species = c->n_species;
+    h.langevin = c->langevin;
     char *o = static_cast<char *>(buf);
     std::memcpy(o, &h, sizeof h);
     o += sizeof h;
@@ -1819,6 +1882,16 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
         o += nd * c->ncell() * 8;
         LPM_CUDA(c, cudaMemcpyAsync(o, c->d_sp_dep, nd * c->ndep() * 8, cudaMemcpyDeviceToHost,
                                     c->stream));
+        o += nd * c->ndep() * 8;
+    }
+    if (c->langevin) {
+        // the spare sorted-w buffer is free here (the gather of the particles above used
+        // the spare state buffer)
+        float *tmp = c->d_w_sorted[1 - c->cur];
+        LPM_CUDA(c, launch_gather_w(c->stream, c->d_w_home, c->d_w_sorted[c->cur], c->d_slot_of, 0,
+                                    c->n_slots_used, tmp));
+        LPM_CUDA(c, cudaMemcpyAsync(o, tmp, (size_t)c->n_slots_used * sizeof(float),
+                                    cudaMemcpyDeviceToHost, c->stream));
     }
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     *n = bytes;
@@ -1834,8 +1907,8 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     if (n < sizeof h) return fail(c, LPM_E_INVALID, "buffer too small for a saved run");
     std::memcpy(&h, buf, sizeof h);
     const size_t ns = (size_t)c->cfg.n_scenarios;
-    if (std::memcmp(h.magic, "LPMSAVE3", 8) != 0 || h.n_slots != c->n_slots_used ||
-        h.n_species != c->n_species ||
+    if (std::memcmp(h.magic, "LPMSAVE4", 8) != 0 || h.n_slots != c->n_slots_used ||
+        h.n_species != c->n_species || h.langevin != c->langevin ||
         h.n_scen != (long long)ns || h.ncell != (long long)c->ncell() ||
         h.ndep != (long long)c->ndep() || h.n_ctr != N_COUNTERS || h.k < 0 ||
         h.k > c->cfg.n_steps || h.dose_every < 0 || h.dose_every > 0x7fffffffLL)
@@ -1843,7 +1916,8 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
     const size_t need = sizeof h + sb + ns * (c->ncell() + c->ndep() + N_COUNTERS) * 8 +
                         (h.dose_every > 0 ? ns * c->ncell() * 8 : 0) +
-                        (size_t)(c->n_species - 1) * ns * (c->ncell() + c->ndep()) * 8;
+                        (size_t)(c->n_species - 1) * ns * (c->ncell() + c->ndep()) * 8 +
+                        (c->langevin ? (size_t)c->n_slots_used * sizeof(float) : 0);
     if (n < need) return fail(c, LPM_E_INVALID, "saved run truncated (%zu of %zu bytes)", n, need);
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
@@ -1878,7 +1952,11 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
         i += nd * c->ncell() * 8;
         LPM_CUDA(c, cudaMemcpyAsync(c->d_sp_dep, i, nd * c->ndep() * 8, cudaMemcpyHostToDevice,
                                     c->stream));
+        i += nd * c->ndep() * 8;
     }
+    if (c->langevin)
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_w_home, i, (size_t)c->n_slots_used * sizeof(float),
+                                    cudaMemcpyHostToDevice, c->stream));
     LPM_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
     st = clear_sort_state(c, false);     // every particle at its home slot
     if (st != LPM_OK) return st;

@@ -106,6 +106,9 @@ struct StepParams {
     float chain_l[MAX_SPECIES];
     unsigned long long *sp_conc_all; // [n_species-1][n_scen][cz][cy][cx] species 1..
     unsigned long long *sp_dep_all;  // [n_species-1][n_scen][2][cy][cx]
+    // vertical Langevin variant: turbulent velocity w' per particle (in the Ranges)
+    int langevin;
+    float t_lagr;                    // Lagrangian time scale T_L (s)
     unsigned int *err;
 };
 

@@ -18,6 +18,7 @@ struct Ranges {
     float4 *state_b;
     const Tile *b_tiles;
     int b_first, n_b;
+    float *w_a, *w_b;             // Langevin w' of A (sorted) and B (home) slots, or nullptr
 };
 
 struct AdvanceLaunch {
@@ -44,6 +45,7 @@ struct SortSource {
     const float4 *state_b;
     const Tile *tiles;
     int b_first, n_b, T;
+    const float *w_a, *w_b;       // Langevin w' (moved with the particles), or nullptr
 };
 
 struct SortBuffers {
@@ -53,6 +55,7 @@ struct SortBuffers {
     unsigned int *keys, *hist, *block_sums, *meta;
     float4 *grave;
     unsigned int *grave_count;
+    float *w_out;                 // Langevin w' of the sorted particles, or nullptr
 };
 
 constexpr unsigned int SLOT_HOME = 0xffffffffu;   // slot_of: the particle is at its home slot
@@ -77,8 +80,12 @@ cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &i
 cudaError_t launch_gather(cudaStream_t s, const float4 *home, const float4 *sorted,
                           const unsigned int *slot_of, const float4 *grave, long long first,
                           long long count, float4 *out);
+cudaError_t launch_gather_w(cudaStream_t s, const float *home, const float *sorted,
+                            const unsigned int *slot_of, long long first, long long count,
+                            float *out);
 cudaError_t launch_unsort(cudaStream_t s, float4 *home, const float4 *sorted,
-                          unsigned int *slot_of, const float4 *grave, long long n);
+                          unsigned int *slot_of, const float4 *grave, long long n, float *w_home,
+                          const float *w_sorted);
 cudaError_t launch_draws(cudaStream_t s, unsigned long long seed, const unsigned long long *pid,
                          const unsigned int *step, unsigned int stream, long long n, uint4 *words,
                          float *nrm);

@@ -205,6 +205,7 @@ __global__ void sort_scatter_kernel(const SortSource S, const unsigned int *__re
                 B.state_out[dst] = src[slot];
                 B.pidx_out[dst] = home;
                 B.slot_of[home] = dst;
+                if (B.w_out) B.w_out[dst] = (i < (long long)live_old ? S.w_a : S.w_b)[slot];
             }
         }
     }
@@ -230,16 +231,31 @@ __global__ void gather_kernel(const float4 *__restrict__ home, const float4 *__r
         out[i] = locate(home, sorted, slot_of, grave, first + i);
 }
 
+// Langevin w' of particles [first, first + count) in home order (0 for dead ones).
+__global__ void gather_w_kernel(const float *__restrict__ home, const float *__restrict__ sorted,
+                                const unsigned int *__restrict__ slot_of, long long first,
+                                long long count, float *__restrict__ out)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const long long p = first + i;
+        const unsigned int s = slot_of ? slot_of[p] : SLOT_HOME;
+        out[i] = s == SLOT_HOME ? home[p] : ((s & SLOT_GRAVE) ? 0.0f : sorted[s]);
+    }
+}
+
 // Every particle back to its home slot (the sorted set becomes empty).
 __global__ void unsort_kernel(float4 *__restrict__ home, const float4 *__restrict__ sorted,
                               unsigned int *__restrict__ slot_of, const float4 *__restrict__ grave,
-                              long long n)
+                              long long n, float *__restrict__ w_home,
+                              const float *__restrict__ w_sorted)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
         const unsigned int s = slot_of[p];
         if (s == SLOT_HOME) continue;
         home[p] = (s & SLOT_GRAVE) ? grave[s & ~SLOT_GRAVE] : sorted[s];
+        if (w_home) w_home[p] = (s & SLOT_GRAVE) ? 0.0f : w_sorted[s];
         slot_of[p] = SLOT_HOME;
     }
 }
@@ -287,11 +303,22 @@ cudaError_t launch_gather(cudaStream_t s, const float4 *home, const float4 *sort
     return cudaGetLastError();
 }
 
+cudaError_t launch_gather_w(cudaStream_t s, const float *home, const float *sorted,
+                            const unsigned int *slot_of, long long first, long long count,
+                            float *out)
+{
+    if (count <= 0) return cudaSuccess;
+    gather_w_kernel<<<grid_for(count, 256), 256, 0, s>>>(home, sorted, slot_of, first, count, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unsort(cudaStream_t s, float4 *home, const float4 *sorted,
-                          unsigned int *slot_of, const float4 *grave, long long n)
+                          unsigned int *slot_of, const float4 *grave, long long n, float *w_home,
+                          const float *w_sorted)
 {
     if (n <= 0) return cudaSuccess;
-    unsort_kernel<<<grid_for(n, 256), 256, 0, s>>>(home, sorted, slot_of, grave, n);
+    unsort_kernel<<<grid_for(n, 256), 256, 0, s>>>(home, sorted, slot_of, grave, n, w_home,
+                                                   w_sorted);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,8 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_set_profiling", "lpm_stats", "lpm_set_params", "lpm_set_emission",
            "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save",
            "lpm_load", "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model",
-           "lpm_set_boundary_layer", "lpm_set_decay_chain", "lpm_species"]
+           "lpm_set_boundary_layer", "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
+           "lpm_particle_velocity"]
 
 
 class LpmError(RuntimeError):
@@ -101,6 +102,8 @@ def load() -> C.CDLL:
     L.lpm_set_dosage.argtypes = [vp, C.c_int]
     L.lpm_set_kz_model.argtypes = [vp, C.c_int, C.c_double]
     L.lpm_set_decay_chain.argtypes = [vp, C.c_int, dp]
+    L.lpm_set_langevin.argtypes = [vp, C.c_int, C.c_double]
+    L.lpm_particle_velocity.argtypes = [vp, i64, i64, C.POINTER(C.c_float)]
     L.lpm_species.argtypes = [vp, C.c_int, C.c_int, dp, dp, dp, C.POINTER(C.c_uint64),
                               C.POINTER(C.c_uint64)]
     L.lpm_set_boundary_layer.argtypes = [vp, C.c_int, vp, C.c_int]
@@ -121,7 +124,8 @@ def load() -> C.CDLL:
                  "lpm_stats", "lpm_set_params", "lpm_set_emission", "lpm_receptors",
                  "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load",
                  "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model", "lpm_set_boundary_layer",
-                 "lpm_set_decay_chain", "lpm_species"):
+                 "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
+                 "lpm_particle_velocity"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -333,6 +337,18 @@ def lpm_fixed_state(ctx, scenario: int, conc_shape, dep_shape):
     return conc, dep, ctr, int(sh.value)
 
 
+def lpm_set_langevin(ctx, on: bool, t_lagr: float = 100.0) -> None:
+    _check(ctx, load().lpm_set_langevin(C.c_void_p(ctx), int(bool(on)), float(t_lagr)))
+
+
+def lpm_particle_velocity(ctx, first: int, count: int) -> np.ndarray:
+    """Turbulent vertical velocity w' (m/s) of slots [first, first + count)."""
+    w = np.empty(int(count), dtype=np.float32)
+    _check(ctx, load().lpm_particle_velocity(C.c_void_p(ctx), int(first), int(count),
+                                             _ptr(w, C.c_float)))
+    return w
+
+
 def lpm_set_decay_chain(ctx, half_lives) -> None:
     hl = np.ascontiguousarray(half_lives, dtype=np.float64)
     _check(ctx, load().lpm_set_decay_chain(C.c_void_p(ctx), int(hl.size), _ptr(hl, C.c_double)))
@@ -439,6 +455,8 @@ class Sim:
             if sort_every is not None:
                 lpm_set_sort(self.ctx, sort_every)
             self._set_met(met_on_device)
+            if getattr(cfg, "langevin", 0):
+                lpm_set_langevin(self.ctx, True, cfg.t_lagr)
             if getattr(cfg, "chain_half_lives", None) is not None:
                 lpm_set_decay_chain(self.ctx, cfg.chain_half_lives)
             if getattr(cfg, "kz_model", 0):
@@ -514,6 +532,13 @@ class Sim:
     def fixed_state(self, scenario: int = 0):
         c = self.cfg
         return lpm_fixed_state(self.ctx, scenario, (c.cz, c.cy, c.cx), (2, c.cy, c.cx))
+
+    def velocity(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        """Langevin w' of the held particles."""
+        if count is None:
+            held = self.part[1] if self.part is not None else self.cfg.n_particles
+            count = held - first
+        return lpm_particle_velocity(self.ctx, first, count)
 
     def species(self, species: int, scenario: int = 0):
         """(conc, dry, wet, conc_fixed, dep_fixed) of a decay-chain species."""
