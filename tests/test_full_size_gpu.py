@@ -1,0 +1,122 @@
+"""Parity at the full sizes of the benchmark workloads, in the benchmark's launch
+configuration (256 threads x 1 particle, 64 registers, sorted by cell every 60 steps):
+deterministic samples of particles recomputed one by one by the oracle, and properties
+that hold at any size where the output sums over every particle."""
+import numpy as np
+import pytest
+
+import lpm_inputs as li
+import oracle
+from parity_util import POS_TOL_M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0912_3223_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def _check_sample(cfg, g_pos, g_tag, sel, n_run, label, **kw):
+    o = oracle.run(cfg, sel=sel, n_run=n_run, **kw)
+    sens = oracle.sensitivity(cfg, sel=sel, n_run=n_run, **kw)
+    ch = oracle.chaotic(cfg, sens, o["pos"], POS_TOL_M)
+    released = o["status"] != li.STATUS_UNRELEASED
+    ok = (o["margin"] >= POS_TOL_M) & released & ~ch
+    assert ch.mean() <= 0.01
+    assert np.array_equal((g_tag >> 28).astype(np.int32) == li.STATUS_UNRELEASED, ~released)
+    assert np.array_equal((g_tag >> 28).astype(np.int32)[ok], o["status"][ok])
+    d = np.linalg.norm(g_pos.astype(np.float64)[ok] - o["pos"][ok], axis=1)
+    print(f"{label}: {ok.sum()} particles, max {d.max() if d.size else 0:.3g} m, "
+          f"chaotic {int(ch.sum())}")
+    assert d.size == 0 or d.max() <= POS_TOL_M
+    return int(ok.sum())
+
+
+def test_batched_full_size_sampled():
+    """256 scenarios, 5.38e7 particles, 1440 x 30 s, in one graph with sorting: after 360
+    steps every 16th scenario sampled at ~400 particles (~100 of them released) against the
+    oracle; at the
+    end, each sampled scenario's fixed-point identities and released mass."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_cfg2()
+    n = [sc.release.n_particles for sc in cfg.scenarios]
+    first = np.concatenate([[0], np.cumsum(n)[:-1]])
+    picked = list(range(0, cfg.n_scenarios, 16))
+    checked = 0
+    with Sim(cfg) as sim:
+        sim.step(360)
+        for s in picked:
+            sel = np.arange(0, n[s], max(1, n[s] // 400), dtype=np.int64)   # 1/4 released
+            xyz, tag = sim.particles(int(first[s]), n[s])
+            checked += _check_sample(cfg, xyz[sel], tag[sel], sel, 360, f"scenario {s}",
+                                     scenario=s)
+        sim.step(cfg.n_steps - 360)
+        for s in picked:
+            b = sim.budget(s)
+            cfix, _, ctr, _ = sim.fixed_state(s)
+            assert int(cfix.sum()) + int(ctr[0]) == int(ctr[6]) + int(ctr[7])
+            assert b[0] - b[6] == pytest.approx(b[1] + b[2] + b[3] + b[4] + b[5], rel=1e-12)
+            assert b[0] == pytest.approx(oracle.total_mass(cfg, scenario=s), rel=1e-9)
+    assert checked > 1000
+
+
+def test_stress_full_size_sampled():
+    """1e8 particles, 512x512x32 hourly weather: after 360 steps ~1000 of the particles
+    released so far (ids in release order) against the oracle; at the end of the 48 h run
+    the fixed-point identity and the released mass."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_stress()
+    n_rel = cfg.n_particles * 360 // cfg.n_steps
+    sel = np.arange(0, n_rel, n_rel // 1000, dtype=np.int64)
+    with Sim(cfg) as sim:
+        sim.step(360)
+        xyz, tag = sim.particles(0, n_rel)
+        assert _check_sample(cfg, xyz[sel], tag[sel], sel, 360, "stress 1e8") > 900
+        sim.step(cfg.n_steps - 360)
+        b = sim.budget()
+        cfix, _, ctr, _ = sim.fixed_state()
+    assert int(cfix.sum()) + int(ctr[0]) == int(ctr[6]) + int(ctr[7])
+    assert b[0] - b[6] == pytest.approx(b[1] + b[2] + b[3] + b[4] + b[5], rel=1e-12)
+    assert b[0] == pytest.approx(oracle.total_mass(cfg), rel=1e-9)
+
+
+def test_adjoint_full_size_properties():
+    """The adjoint workload at full size (1e6 particles, 1080 x 20 s, 64 receptors): the
+    receptor loss is linear in the emission series, so sum_j q_j dL/dq_j = L exactly (up to
+    rounding); the horizontal source gradient matches central differences of the same GPU
+    forward with common random numbers. (The release-height gradient is not compared this
+    way: near the ground some paths amplify a perturbation 1e5-fold, so a finite
+    difference over any resolvable step leaves the linear regime; it is compared with the
+    oracle's pathwise adjoint at reduced size instead.)"""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = li.make_cfg3()
+    rec = li.make_receptors()
+    rng = np.random.default_rng(3)
+    w = rng.normal(size=(1, rec.shape[0]))
+    q = np.asarray(cfg.release.q, dtype=np.float64)
+    with Sim(cfg) as sim:
+        def L():
+            return float(w[0] @ lpm.lpm_receptors(sim.ctx, 1, rec, 200.0, 18)[0])
+        g = lpm.lpm_adjoint(sim.ctx, rec, 200.0, 18, w, q.size)[0]
+        L0 = L()
+        assert float(q @ g[3:3 + q.size]) == pytest.approx(L0, rel=1e-4)
+        fd = []
+        for d, h in enumerate((5.0, 5.0)):
+            base = [cfg.src_x, cfg.src_y, cfg.src_z]
+            p = list(base); p[d] += h
+            m = list(base); m[d] -= h
+            lpm.lpm_set_source(sim.ctx, 0, *p)
+            lp = L()
+            lpm.lpm_set_source(sim.ctx, 0, *m)
+            lm = L()
+            fd.append((lp - lm) / (2 * h))
+        lpm.lpm_set_source(sim.ctx, 0, cfg.src_x, cfg.src_y, cfg.src_z)
+    fd = np.array(fd)
+    print("full-size adjoint source gradient", g[:2], "central differences", fd)
+    np.testing.assert_allclose(g[:2], fd, atol=2e-2 * np.abs(fd).max(), rtol=5e-2)
