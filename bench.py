@@ -554,7 +554,7 @@ def run_gpu(args):
     # snapshots, deposition and budget out, every step
     pinned_uvwk = torch.from_numpy(cfg.uvwk).pin_memory()
     pinned_rain = torch.from_numpy(cfg.rain).pin_memory()
-    conc = np.empty((cfg.cz, cfg.cy, cfg.cx))
+    conc = torch.empty((cfg.cz, cfg.cy, cfg.cx), dtype=torch.float64, pin_memory=True).numpy()
     h2d = pinned_uvwk.numel() * 4 + pinned_rain.numel()
     d2h = conc.nbytes + 2 * cfg.cy * cfg.cx * 8 + 8 * 8
     e2e_t, e2e_p = 0.0, 0
@@ -564,7 +564,7 @@ def run_gpu(args):
         for t in range(cfg.n_met_t):
             lpm.lpm_set_met(sim.ctx, t, pinned_uvwk[t], None, pinned_rain[t])
         one_run()
-        c = sim.concentration()
+        sim.concentration(out=conc)
         dry, wet = sim.deposition()
         b = sim.budget()
         e2e_t += time.perf_counter() - t0

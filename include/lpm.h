@@ -116,8 +116,13 @@ const char *lpm_last_error(const lpm_ctx *ctx);
  *   kh:   [nz][ny][nx] float K_h, required iff kh_uniform < 0, else must be NULL.
  *   rain: [ny][nx] uint8, nonzero where it precipitates; NULL = no rain in this slab.
  * on_device = 1: the pointers are device pointers (copied on the context stream, the
- * caller keeps them valid until the stream reaches the copy); 0: host pointers (copied
- * before the call returns).
+ * caller keeps them valid until the stream reaches the copy); 0: host pointers. Pageable
+ * host memory is copied before the call returns. Page-locked host memory (cudaMallocHost,
+ * cudaHostRegister, a pinned tensor; all given pointers) is copied asynchronously on a copy
+ * stream of the context, after the work already enqueued on the context stream, so that
+ * later hours arrive while earlier ones are computed: the caller keeps those buffers
+ * unchanged until the next lpm_sync (or read-back call) returns; lpm_step waits for the
+ * hours its steps use.
  */
 lpm_status lpm_set_met(lpm_ctx *ctx, int t_index, const float *uvwk, const float *kh,
                        const uint8_t *rain, int on_device);

@@ -57,6 +57,11 @@ struct lpm_ctx {
     uint8_t *d_rain = nullptr;
     std::vector<char> met_set;
     bool any_rain = false;
+    // asynchronous weather uploads from page-locked host memory
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_main = nullptr;          // orders a copy after the context stream's work
+    std::vector<cudaEvent_t> ev_pair;       // time pair h packed (copy stream)
+    std::vector<char> pair_pending;
     // boundary-layer columns for K_z from Eq. 3
     int kz_model = 0;                       // 0: gridded K_z, 1: Eq. 3
     double kz_min = 0.1;
@@ -410,6 +415,7 @@ lpm_status check_device_error(lpm_ctx *c)
 {
     unsigned int e = 0;
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->copy_stream) LPM_CUDA(c, cudaStreamSynchronize(c->copy_stream));
     LPM_CUDA(c, cudaMemcpy(&e, c->d_err, sizeof e, cudaMemcpyDeviceToHost));
     if (e & ERR_NAN) return fail(c, LPM_E_NUMERIC, "a particle position became non-finite");
     if (e & ERR_INDEX) return fail(c, LPM_E_CUDA, "a grid index fell outside its array");
@@ -731,7 +737,12 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_w_sorted[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_pair)
+        if (e) cudaEventDestroy(e);
+    if (c->ev_main) cudaEventDestroy(c->ev_main);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -741,6 +752,21 @@ const char *lpm_last_error(const lpm_ctx *c)
 {
     return c ? c->err.c_str() : g_create_error.c_str();
 }
+
+namespace {
+
+bool is_pinned_host(const void *p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
 
 lpm_status lpm_set_met(lpm_ctx *c, int t_index, const float *uvwk, const float *kh,
                        const uint8_t *rain, int on_device)
@@ -754,18 +780,34 @@ lpm_status lpm_set_met(lpm_ctx *c, int t_index, const float *uvwk, const float *
         return fail(c, LPM_E_INVALID, "kh must be given iff kh_uniform < 0");
     const size_t nodes = (size_t)g.nx * g.ny * g.nz;
     const size_t cols = (size_t)g.nx * g.ny;
+    const bool async = !on_device && is_pinned_host(uvwk) && is_pinned_host(kh) &&
+                       is_pinned_host(rain);
+    cudaStream_t s = c->stream;
+    if (async) {
+        // copy after everything already enqueued (earlier runs may still read the slabs)
+        if (!c->copy_stream)
+            LPM_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        if (!c->ev_main) LPM_CUDA(c, cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming));
+        if (c->ev_pair.empty()) {
+            c->ev_pair.assign((size_t)std::max(1, g.n_met_t - 1), nullptr);
+            c->pair_pending.assign(c->ev_pair.size(), 0);
+        }
+        LPM_CUDA(c, cudaEventRecord(c->ev_main, c->stream));
+        LPM_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->ev_main, 0));
+        s = c->copy_stream;
+    } else if (c->copy_stream) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->copy_stream));   // no copy of ours in flight
+    }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    LPM_CUDA(c, cudaMemcpyAsync(c->d_uvwk + nodes * t_index, uvwk, nodes * sizeof(float4), kind,
-                                c->stream));
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_uvwk + nodes * t_index, uvwk, nodes * sizeof(float4), kind, s));
     if (kh)
-        LPM_CUDA(c, cudaMemcpyAsync(c->d_kh + nodes * t_index, kh, nodes * sizeof(float), kind,
-                                    c->stream));
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_kh + nodes * t_index, kh, nodes * sizeof(float), kind, s));
     if (rain) {
-        LPM_CUDA(c, cudaMemcpyAsync(c->d_rain + cols * t_index, rain, cols, kind, c->stream));
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_rain + cols * t_index, rain, cols, kind, s));
         if (!c->any_rain) drop_graphs(c);    // captured launches baked in "no rain"
         c->any_rain = true;
     } else {
-        LPM_CUDA(c, cudaMemsetAsync(c->d_rain + cols * t_index, 0, cols, c->stream));
+        LPM_CUDA(c, cudaMemsetAsync(c->d_rain + cols * t_index, 0, cols, s));
     }
     c->met_set[(size_t)t_index] = 1;
     // time pairs (h, h+1) that this slab completes
@@ -773,15 +815,21 @@ lpm_status lpm_set_met(lpm_ctx *c, int t_index, const float *uvwk, const float *
         const int h1 = g.n_met_t > 1 ? h + 1 : h;
         if (h < 0 || h1 > g.n_met_t - 1 || (g.n_met_t > 1 && h > g.n_met_t - 2)) continue;
         if (!c->met_set[(size_t)h] || !c->met_set[(size_t)h1]) continue;
-        LPM_CUDA(c, launch_pack(c->stream, c->d_uvwk + nodes * h, c->d_uvwk + nodes * h1,
+        LPM_CUDA(c, launch_pack(s, c->d_uvwk + nodes * h, c->d_uvwk + nodes * h1,
                                 c->d_kh ? c->d_kh + nodes * h : nullptr,
                                 c->d_kh ? c->d_kh + nodes * h1 : nullptr,
                                 c->d_pair + nodes * 2 * h, c->d_khpair ? c->d_khpair + nodes * h : nullptr,
                                 g.nx, g.ny, g.nz));
         c->n_launches++;
+        if (async) {
+            if (!c->ev_pair[(size_t)h])
+                LPM_CUDA(c, cudaEventCreateWithFlags(&c->ev_pair[(size_t)h], cudaEventDisableTiming));
+            LPM_CUDA(c, cudaEventRecord(c->ev_pair[(size_t)h], c->copy_stream));
+            c->pair_pending[(size_t)h] = 1;
+        }
     }
-    // host sources must be consumed before returning (the caller owns them)
-    if (!on_device) LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    // pageable host sources must be consumed before returning (the caller owns them)
+    if (!on_device && !async) LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     return LPM_OK;
 }
 
@@ -936,6 +984,22 @@ lpm_status lpm_set_launch(lpm_ctx *c, int block, int ppt, int occupancy)
 
 namespace {
 
+// Makes stream s wait for the weather pairs that steps [k0, k1) read and that a
+// page-locked upload may still be writing.
+lpm_status wait_met_pairs(lpm_ctx *c, cudaStream_t s, long long k0, long long k1)
+{
+    if (!c->copy_stream || k1 <= k0) return LPM_OK;
+    const lpm_config &g = c->cfg;
+    const long long n_pair = (long long)c->pair_pending.size();
+    long long h_a = (long long)std::floor(((double)k0 * g.dt - g.met_t0) / g.met_dt);
+    long long h_b = (long long)std::floor(((double)(k1 - 1) * g.dt - g.met_t0) / g.met_dt);
+    h_a = std::max(0LL, std::min(h_a, n_pair - 1));
+    h_b = std::max(0LL, std::min(h_b, n_pair - 1));
+    for (long long h = h_a; h <= h_b; ++h)
+        if (c->pair_pending[(size_t)h]) LPM_CUDA(c, cudaStreamWaitEvent(s, c->ev_pair[(size_t)h], 0));
+    return LPM_OK;
+}
+
 // One segment [k, e) of an lpm_step call: an optional sort at k, then one advance launch.
 struct Segment {
     long long k, e;
@@ -958,6 +1022,10 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
     const int T = c->block * c->ppt;
     const size_t ns = (size_t)g.n_scenarios;
     for (const Segment &sg : plan) {
+        if (direct) {
+            lpm_status ws = wait_met_pairs(c, s, sg.k, sg.e);
+            if (ws != LPM_OK) return ws;
+        }
         if (sg.do_bin) {
             LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0, ns * c->ncell() * sizeof(unsigned long long), s));
             LPM_CUDA(c, cudaMemsetAsync(c->d_ctr + (size_t)C_BIN_OUT * ns, 0,
@@ -1073,12 +1141,19 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
                 return fail(c, LPM_E_STATE, "boundary-layer slab %lld not set", h);
         }
     }
+    lpm_status st = LPM_OK;
+    if (c->copy_stream && g.n_scenarios > 1) {
+        // weather pairs still in flight from page-locked uploads: the graph of the call
+        // waits for all those it reads (the plain form waits segment by segment)
+        st = wait_met_pairs(c, c->stream, c->k, c->k + n);
+        if (st != LPM_OK) return st;
+    }
     const bool ext = (c->d_dose && c->dose_every > 0) || c->kz_model == 1 || c->n_species > 1 ||
                      c->langevin;
     if (ext && c->ppt != 1)
         return fail(c, LPM_E_INVALID, "dosage, K_z from Eq. 3, decay chains and the Langevin "
                                       "variant run with 1 particle per thread");
-    lpm_status st = upload_tables(c);
+    st = upload_tables(c);
     if (st != LPM_OK) return st;
     if (!c->tiles_valid) {
         st = build_tiles(c);
@@ -1212,12 +1287,16 @@ lpm_status lpm_concentration(lpm_ctx *c, int scenario, double *out, size_t n_out
         return fail(c, LPM_E_INVALID, "out must hold cz*cy*cx = %zu doubles", c->ncell());
     lpm_status st = check_device_error(c);
     if (st != LPM_OK) return st;
-    std::vector<unsigned long long> h(c->ncell());
-    LPM_CUDA(c, cudaMemcpy(h.data(), c->d_conc + (size_t)scenario * c->ncell(),
-                           h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    // the 64-bit sums land in the caller's buffer and are converted in place (same size)
+    LPM_CUDA(c, cudaMemcpy(out, c->d_conc + (size_t)scenario * c->ncell(),
+                           c->ncell() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     const lpm_config &g = c->cfg;
     const double f = std::ldexp(1.0, -c->scen[(size_t)scenario].shift) / (g.cdx * g.cdy * g.cdz);
-    for (size_t i = 0; i < h.size(); ++i) out[i] = (double)h[i] * f;
+    for (size_t i = 0; i < c->ncell(); ++i) {
+        unsigned long long v;
+        std::memcpy(&v, out + i, sizeof v);
+        out[i] = (double)v * f;
+    }
     return LPM_OK;
 }
 
@@ -1663,6 +1742,8 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     lpm_status st = upload_tables(c);
     if (st != LPM_OK) return st;
     fill_params(c, P);
+    for (size_t h = 0; h < c->pair_pending.size(); ++h)      // weather still being uploaded
+        if (c->pair_pending[h]) LPM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_pair[h], 0));
     // tiles of ADJ_BLOCK particles over every held particle
     if (!c->adj_tiles_valid) {
         c->adj_tiles.clear();

@@ -297,8 +297,13 @@ def lpm_current_step(ctx) -> int:
     return int(k.value)
 
 
-def lpm_concentration(ctx, scenario: int, shape) -> np.ndarray:
-    out = np.empty(shape, dtype=np.float64)
+def lpm_concentration(ctx, scenario: int, shape, out=None) -> np.ndarray:
+    """Concentration [cz][cy][cx]; ``out`` (a C-contiguous float64 array of that shape,
+    e.g. over page-locked memory) receives it instead of a new array."""
+    if out is None:
+        out = np.empty(shape, dtype=np.float64)
+    elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size != int(np.prod(shape)):
+        raise ValueError("out must be a C-contiguous float64 array of the grid's size")
     _check(ctx, load().lpm_concentration(C.c_void_p(ctx), int(scenario), _ptr(out, C.c_double),
                                          out.size))
     return out
@@ -512,9 +517,9 @@ class Sim:
     def k(self) -> int:
         return lpm_current_step(self.ctx)
 
-    def concentration(self, scenario: int = 0) -> np.ndarray:
+    def concentration(self, scenario: int = 0, out=None) -> np.ndarray:
         c = self.cfg
-        return lpm_concentration(self.ctx, scenario, (c.cz, c.cy, c.cx))
+        return lpm_concentration(self.ctx, scenario, (c.cz, c.cy, c.cx), out=out)
 
     def deposition(self, scenario: int = 0):
         c = self.cfg

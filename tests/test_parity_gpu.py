@@ -343,3 +343,23 @@ def test_allocation_failure_is_reported():
     assert e.value.status == lpm.LPM_E_INVALID
     ctx = lpm.lpm_create(cfg)           # the device is still usable
     lpm.lpm_destroy(ctx)
+
+
+def test_met_from_pinned_host_memory_overlaps_and_matches():
+    """Weather from page-locked host memory is uploaded asynchronously (hours arrive while
+    earlier ones are computed); the results equal those of pageable uploads bit for bit,
+    also when the same context re-uploads between runs."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = li.make_cfg1(n_particles=5003, n_steps=480, n_hours=5)
+    ref = run_gpu(cfg)
+    uvwk = torch.from_numpy(cfg.uvwk).pin_memory()
+    rain = torch.from_numpy(cfg.rain).pin_memory()
+    with Sim(cfg) as sim:
+        for rep in range(2):
+            sim.reset()
+            for t in range(cfg.n_met_t):
+                lpm.lpm_set_met(sim.ctx, t, uvwk[t], None, rain[t])
+            sim.step(cfg.n_steps)
+            xyz, tag = sim.particles()
+            assert np.array_equal(xyz.astype(np.float64), ref["pos"]) and np.array_equal(tag, ref["tag"])
+            assert np.array_equal(sim.fixed_state()[0], ref["conc_fixed"])
