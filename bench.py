@@ -43,6 +43,10 @@ OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
 # hours 6-7, read + write), valid while the kernel sources hash to the values recorded there.
 ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.098688 + 0.0) + (23.586560 + 0.001024)) * 1e6
 ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "532964cf", "lpm_device.cuh": "c40026dc"}
+# Busiest hardware units of the same capture (% of peak, mean of the two launches): the
+# L1 data pipe carrying the weather gathers, and the warp-instruction issue slots.
+ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (79.13 + 80.43) / 100.0,
+                         "issue_slots": 0.5 * (72.32 + 72.26) / 100.0}
 SM_COUNT = 152
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
 SM_MAX_MHZ = 2070.0
@@ -55,15 +59,20 @@ def _env_int(name, default):
         return default
 
 
-def advance_traffic():
-    """The captured per-launch DRAM traffic, or None once the kernel sources changed."""
+def capture_current():
+    """Whether the kernel sources still hash to those of the committed ncu capture."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_0912_3223_gb300", "csrc")
     for name, digest in ADVANCE_TRAFFIC_SOURCES.items():
         with open(os.path.join(csrc, name), "rb") as f:
             if not hashlib.sha1(f.read()).hexdigest().startswith(digest):
-                return None
-    return ADVANCE_TRAFFIC_BYTES
+                return False
+    return True
+
+
+def advance_traffic():
+    """The captured per-launch DRAM traffic, or None once the kernel sources changed."""
+    return ADVANCE_TRAFFIC_BYTES if capture_current() else None
 
 
 def read_peaks():
@@ -585,6 +594,10 @@ def run_gpu(args):
         "peak_source": (f"derived: {SM_COUNT} SMs x {LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz "
                         "(one 32-bit op per lane per clock)"),
         "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
+        # the hardware view of the same kernel (ncu capture, % of each unit's peak): what
+        # bounds it is the L1 data pipe and the issue slots, not DRAM
+        "busiest_units": dict(ADVANCE_BUSIEST_UNITS, source="ncu capture, profiles/"
+                              "advance_kernel_plain_1e7x2880.md") if capture_current() else None,
         "advance_share_of_step": (adv_ms / 1e3) / (sum(times) / 1e3) if times else None,
         "hbm_gbs_measured_peak": peaks.get("hbm_gbs"),
     }
