@@ -92,10 +92,10 @@ __device__ __forceinline__ void warp_count_scen(int s, unsigned long long v, int
 }
 
 // Weather at a point from the time-paired records: 8 spatial corners, each one 32-byte
-// load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z. With KZ3, K_z
-// and its derivative come from Eq. 3 on the boundary-layer columns (4 more 32-byte loads
-// of the time-paired (u*, 1/L, H_z) at the cell's corner columns, bilinear in x, y);
-// only the EXT instantiations carry that code.
+// load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z. With the
+// boundary-layer columns (EXT and blp), K_z and its derivative come from Eq. 3 instead
+// (4 more 32-byte loads of the time-paired (u*, 1/L, H_z) at the cell's corner columns,
+// bilinear in x, y); only the EXT instantiations carry that code.
 template <bool EXT>
 __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels &L,
                                                const float4 *__restrict__ pair,

@@ -530,23 +530,32 @@ long long released_total(const lpm_ctx *c, long long k)
 
 lpm_status ensure_sort_buffers(lpm_ctx *c, size_t keys_need)
 {
-    if (!c->d_sorted[0]) {
+    // allocate whatever is still missing (an earlier call may have stopped at a failure)
+    const size_t n = (size_t)c->cfg.max_particles;
+    const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
+    const size_t ntiles = (nb + 1023) / 1024;
+    auto need = [&](auto *&p, size_t bytes) -> cudaError_t {
+        if (p) return cudaSuccess;
         drop_graphs(c);                      // graphs hold the buffers' addresses
-        const size_t n = (size_t)c->cfg.max_particles;
-        const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
-        const size_t ntiles = (nb + 1023) / 1024;
-        for (int b = 0; b < 2; ++b) {
-            LPM_CUDA(c, cudaMalloc(&c->d_sorted[b], n * sizeof(float4)));
-            LPM_CUDA(c, cudaMalloc(&c->d_pidx[b], n * sizeof(unsigned int)));
-        }
-        LPM_CUDA(c, cudaMalloc(&c->d_slot_of, n * sizeof(unsigned int)));
-        LPM_CUDA(c, cudaMalloc(&c->d_hist, nb * sizeof(unsigned int)));
-        LPM_CUDA(c, cudaMalloc(&c->d_bsums, ntiles * sizeof(unsigned int)));
-        LPM_CUDA(c, cudaMalloc(&c->d_live, 4 * sizeof(unsigned int)));
-        LPM_CUDA(c, cudaMalloc(&c->d_grave, n * sizeof(float4)));
-        LPM_CUDA(c, cudaMalloc(&c->d_grave_n, sizeof(unsigned int)));
+        return cudaMalloc(&p, bytes);
+    };
+    for (int b = 0; b < 2; ++b) {
+        LPM_CUDA(c, need(c->d_sorted[b], n * sizeof(float4)));
+        LPM_CUDA(c, need(c->d_pidx[b], n * sizeof(unsigned int)));
+    }
+    if (!c->d_slot_of) {
+        LPM_CUDA(c, need(c->d_slot_of, n * sizeof(unsigned int)));
         LPM_CUDA(c, cudaMemsetAsync(c->d_slot_of, 0xff, n * sizeof(unsigned int), c->stream));
+    }
+    LPM_CUDA(c, need(c->d_hist, nb * sizeof(unsigned int)));
+    LPM_CUDA(c, need(c->d_bsums, ntiles * sizeof(unsigned int)));
+    if (!c->d_live) {
+        LPM_CUDA(c, need(c->d_live, 4 * sizeof(unsigned int)));
         LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
+    }
+    LPM_CUDA(c, need(c->d_grave, n * sizeof(float4)));
+    if (!c->d_grave_n) {
+        LPM_CUDA(c, need(c->d_grave_n, sizeof(unsigned int)));
         LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
     }
     if (keys_need > c->keys_cap) {
@@ -1449,12 +1458,15 @@ lpm_status lpm_set_langevin(lpm_ctx *c, int on, double t_lagr)
     if (c->k != 0) return fail(c, LPM_E_STATE, "choose the Langevin variant before stepping (or after lpm_reset)");
     if (on && (!is_finite(t_lagr) || !(t_lagr > 0)))
         return fail(c, LPM_E_INVALID, "the Lagrangian time scale must be > 0");
-    if (on && !c->d_w_home) {
+    if (on && (!c->d_w_home || !c->d_w_sorted[0] || !c->d_w_sorted[1])) {
         const size_t n = (size_t)c->cfg.max_particles;
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
-        LPM_CUDA(c, cudaMalloc(&c->d_w_home, n * sizeof(float)));
-        for (int b = 0; b < 2; ++b) LPM_CUDA(c, cudaMalloc(&c->d_w_sorted[b], n * sizeof(float)));
-        LPM_CUDA(c, cudaMemsetAsync(c->d_w_home, 0, n * sizeof(float), c->stream));
+        if (!c->d_w_home) {
+            LPM_CUDA(c, cudaMalloc(&c->d_w_home, n * sizeof(float)));
+            LPM_CUDA(c, cudaMemsetAsync(c->d_w_home, 0, n * sizeof(float), c->stream));
+        }
+        for (int b = 0; b < 2; ++b)
+            if (!c->d_w_sorted[b]) LPM_CUDA(c, cudaMalloc(&c->d_w_sorted[b], n * sizeof(float)));
     }
     c->langevin = on ? 1 : 0;
     if (on) c->t_lagr = t_lagr;
@@ -1582,12 +1594,13 @@ lpm_status lpm_set_kz_model(lpm_ctx *c, int model, double kz_min)
     if (model < 0 || model > 1) return fail(c, LPM_E_INVALID, "K_z model must be 0 or 1");
     if (!is_finite(kz_min) || kz_min < 0) return fail(c, LPM_E_INVALID, "kz_min must be >= 0");
     const lpm_config &g = c->cfg;
-    if (model == 1 && !c->d_bl) {
+    if (model == 1 && (!c->d_bl || !c->d_blpair)) {
         const size_t cols = (size_t)g.nx * g.ny;
         const size_t n_pair = (size_t)std::max(1, g.n_met_t - 1);
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
-        LPM_CUDA(c, cudaMalloc(&c->d_bl, cols * g.n_met_t * sizeof(float4)));
-        LPM_CUDA(c, cudaMalloc(&c->d_blpair, cols * n_pair * 2 * sizeof(float4)));
+        if (!c->d_bl) LPM_CUDA(c, cudaMalloc(&c->d_bl, cols * g.n_met_t * sizeof(float4)));
+        if (!c->d_blpair)
+            LPM_CUDA(c, cudaMalloc(&c->d_blpair, cols * n_pair * 2 * sizeof(float4)));
         c->bl_set.assign((size_t)g.n_met_t, 0);
     }
     c->kz_model = model;
@@ -1600,7 +1613,8 @@ lpm_status lpm_set_boundary_layer(lpm_ctx *c, int t_index, const float *bl, int 
 {
     if (!c) return LPM_E_INVALID;
     const lpm_config &g = c->cfg;
-    if (!c->d_bl) return fail(c, LPM_E_STATE, "select K_z model 1 (lpm_set_kz_model) first");
+    if (!c->d_bl || !c->d_blpair || c->bl_set.empty())
+        return fail(c, LPM_E_STATE, "select K_z model 1 (lpm_set_kz_model) first");
     if (t_index < 0 || t_index >= g.n_met_t)
         return fail(c, LPM_E_INVALID, "t_index %d outside [0, %d)", t_index, g.n_met_t);
     if (!bl) return fail(c, LPM_E_INVALID, "bl is NULL");
