@@ -41,12 +41,12 @@ OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
 # DRAM traffic per advance launch from the ncu capture summarised in
 # profiles/advance_kernel_plain_1e7x2880.md (mean of the two captured 60-step launches of
 # hours 6-7, read + write), valid while the kernel sources hash to the values recorded there.
-ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.098688 + 0.0) + (23.586560 + 0.001024)) * 1e6
-ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "532964cf", "lpm_device.cuh": "c40026dc"}
+ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.099968 + 0.000512) + (23.584768 + 0.002304)) * 1e6
+ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "5467001d", "lpm_device.cuh": "9d1c6665"}
 # Busiest hardware units of the same capture (% of peak, mean of the two launches): the
 # L1 data pipe carrying the weather gathers, and the warp-instruction issue slots.
-ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (79.13 + 80.43) / 100.0,
-                         "issue_slots": 0.5 * (72.32 + 72.26) / 100.0}
+ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (79.97 + 80.01) / 100.0,
+                         "issue_slots": 0.5 * (72.33 + 72.25) / 100.0}
 SM_COUNT = 152
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
 SM_MAX_MHZ = 2070.0
@@ -269,6 +269,7 @@ def measure_adjoint(args, stream):
             t2 = time.perf_counter()
             fwd.append(t1 - t0)
             bwd.append(t2 - t1)
+        traj, nbytes = lpm.lpm_adjoint_storage(sim.ctx)
     finally:
         sim.close()
     tf, tb = statistics.mean(fwd), statistics.mean(bwd)
@@ -276,7 +277,9 @@ def measure_adjoint(args, stream):
             "note": "active particle-steps of the run / (forward + backward) wall time",
             "ms_forward": 1e3 * tf, "ms_backward": 1e3 * tb, "particles": cfg.n_particles,
             "steps_per_run": cfg.n_steps, "receptors": int(rec.shape[0]),
-            "active_particle_steps": active, "checkpoint_every": 64}
+            "active_particle_steps": active,
+            "storage": "trajectory" if traj else "checkpoints every 64 steps",
+            "storage_gb": nbytes / 1e9}
 
 
 def measure_inversion(args, stream):
@@ -287,7 +290,7 @@ def measure_inversion(args, stream):
     import torch
 
     import lpm_inputs as li
-    from paper_0912_3223_gb300 import Sim
+    from paper_0912_3223_gb300 import Sim, lpm
     from paper_0912_3223_gb300.inversion import invert, observe
     cand, obs, hidden = li.make_cfg4()
     rec = li.make_receptors()
@@ -302,6 +305,7 @@ def measure_inversion(args, stream):
         t0 = time.perf_counter()
         res = invert(sim, rec, c_obs, n_iter=20)
         t = time.perf_counter() - t0
+        traj, nbytes = lpm.lpm_adjoint_storage(sim.ctx)
     finally:
         sim.close()
     h = np.array(hidden)
@@ -314,7 +318,9 @@ def measure_inversion(args, stream):
             "ms_forward_total": 1e3 * res.timings["forward"],
             "ms_adjoint_total": 1e3 * res.timings["adjoint"],
             "best_loss_start": float(res.loss[0].min()), "best_loss_end": float(res.loss[-1].min()),
-            "best_distance_start_m": float(d0), "best_distance_end_m": d1}
+            "best_distance_start_m": float(d0), "best_distance_end_m": d1,
+            "storage": "trajectory" if traj else "checkpoints every 64 steps",
+            "storage_gb": nbytes / 1e9}
 
 
 def measure_stress(args, stream):

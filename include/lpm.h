@@ -354,7 +354,7 @@ lpm_status lpm_set_emission(lpm_ctx *ctx, int scenario, const double *q, int n_q
  * m_p G(X_p - x_r), G a 3D Gaussian kernel of width `bandwidth` (m) plus its image below
  * the ground (terms beyond 6 bandwidths are dropped), n_s = floor(n_steps / sample_every).
  * receptors: host [R][3] (x, y, z), 1 <= R <= 256; C: host [n_scenarios][R]. Also stores
- * the checkpoints (every 64 steps) that lpm_adjoint uses. Synchronous. Not with
+ * the states that lpm_adjoint uses (see lpm_set_adjoint_storage). Synchronous. Not with
  * drift_correction.
  */
 lpm_status lpm_receptors(lpm_ctx *ctx, const double *receptors, int R, double bandwidth,
@@ -365,12 +365,26 @@ lpm_status lpm_receptors(lpm_ctx *ctx, const double *receptors, int R, double ba
  * step, events frozen, same keyed random numbers): grad [n_scenarios][3 + nq + 3] =
  * (dL/dx_s, dL/dy_s, dL/dh, dL/dq[0..nq-1], dL/dk_scale, dL/dbias_u, dL/dbias_v) per
  * scenario, nq the longest emission series of the context (shorter series leave zeros).
- * Uses the checkpoints of the last lpm_receptors with the same receptors, bandwidth,
- * sample_every and parameters, else runs that forward first. Paths are recomputed from
- * the checkpoints one 64-step segment at a time. Synchronous.
+ * Uses the states stored by the last lpm_receptors with the same receptors, bandwidth,
+ * sample_every and parameters, else runs that forward first. Synchronous.
  */
 lpm_status lpm_adjoint(lpm_ctx *ctx, const double *receptors, int R, double bandwidth,
                        int sample_every, const double *dL_dC, double *grad);
+
+/*
+ * Storage of the receptor forward's states for lpm_adjoint. The forward keeps the whole
+ * trajectory (16 B per particle and step, from the first release step of each block of
+ * 128 particles on, plus 16 B per particle) when that is at most max_bytes and leaves
+ * 8 GiB of device memory free; the backward then reads the states back in reverse.
+ * Otherwise, and always with max_bytes = 0, it keeps a checkpoint every 64 steps (16 B per
+ * particle each) and the backward recomputes each 64-step segment from its checkpoint.
+ * Both give the same gradients up to the order of the FP64 sums. Default 128 GiB. Drops
+ * the held forward. An allocation that fails falls back to checkpoints (no error).
+ * lpm_adjoint_storage: *trajectory = 1 when the last receptor forward kept the trajectory,
+ * *bytes = device bytes held for the adjoint's states (trajectory or checkpoints).
+ */
+lpm_status lpm_set_adjoint_storage(lpm_ctx *ctx, uint64_t max_bytes);
+lpm_status lpm_adjoint_storage(lpm_ctx *ctx, int *trajectory, uint64_t *bytes);
 
 /*
  * The counter-based draws the step consumes (replacing the Mersenne Twister + Box-Muller

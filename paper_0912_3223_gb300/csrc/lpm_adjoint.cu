@@ -98,8 +98,9 @@ __device__ __forceinline__ float4 pack_state(float x, float y, float z, uint32_t
 }
 
 // ---------------------------------------------------------------------------------
-// Forward: receptor concentrations and checkpoints.
+// Forward: receptor concentrations, and checkpoints or the whole trajectory.
 // ---------------------------------------------------------------------------------
+template <bool TRAJ>
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_forward_kernel(const StepParams P, const AdjParams A)
 {
@@ -122,18 +123,33 @@ adj_forward_kernel(const StepParams P, const AdjParams A)
         const int sp = (int)release_step_of(sc, slot);
         const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
         float x = sc.src_x, y = sc.src_y, z = sc.src_z;
-        for (int c = 0; c < A.n_ck && c * CK <= sp; ++c)
-            A.ckpt[(long long)c * A.n_slots + slot] = pack_state(x, y, z, ST_UNRELEASED, sp);
+        float4 *row = nullptr;
+        int k0 = 0;
+        if (TRAJ) {
+            const longlong2 tt = A.traj_tile[blockIdx.x];
+            row = A.traj + tt.x + threadIdx.x;
+            k0 = (int)tt.y;
+        } else {
+            for (int c = 0; c < A.n_ck && c * CK <= sp; ++c)
+                A.ckpt[(long long)c * A.n_slots + slot] = pack_state(x, y, z, ST_UNRELEASED, sp);
+        }
         uint32_t st = ST_ACTIVE;
+        int kn = sp;                              // one past the last step taken
         for (int k = sp; k < A.n_steps; ++k) {
-            if (k > sp && k % CK == 0)
+            if (!TRAJ && k > sp && k % CK == 0)
                 A.ckpt[(long long)(k / CK) * A.n_slots + slot] = pack_state(x, y, z, ST_ACTIVE, sp);
             const StepTime T = step_time(P, sc.wind_offset, k);
+            const float xb = x, yb = y, zb = z;
+            float fs = 1.0f;
             st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp, sig_h_uniform, T.du, T.dv,
-                                      x, y, z, nullptr);
+                                      x, y, z, TRAJ ? &fs : nullptr);
+            if (TRAJ && k >= k0)                  // rows start at the tile's first release
+                __stcs(row + (long long)(k - k0) * ADJ_BLOCK, make_float4(xb, yb, zb, fs));
+            kn = k + 1;
             if (st != ST_ACTIVE) {
-                for (int c = k / CK + 1; c < A.n_ck; ++c)
-                    A.ckpt[(long long)c * A.n_slots + slot] = pack_state(x, y, z, st, sp);
+                if (!TRAJ)
+                    for (int c = k / CK + 1; c < A.n_ck; ++c)
+                        A.ckpt[(long long)c * A.n_slots + slot] = pack_state(x, y, z, st, sp);
                 break;
             }
             if ((k + 1) % A.every == 0) {
@@ -149,6 +165,9 @@ adj_forward_kernel(const StepParams P, const AdjParams A)
                 }
             }
         }
+        if (TRAJ)
+            A.fin[slot] = make_float4(x, y, z, __uint_as_float((uint32_t)kn |
+                                                               (st != ST_ACTIVE ? 0x80000000u : 0u)));
     }
     __syncthreads();
     for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK)
@@ -156,8 +175,120 @@ adj_forward_kernel(const StepParams P, const AdjParams A)
 }
 
 // ---------------------------------------------------------------------------------
-// Backward: segment recomputation and reverse sweep.
+// Backward: reverse sweep.
 // ---------------------------------------------------------------------------------
+struct Adjoint {
+    float mu0, mu1, mu2;                  // dL/dX of the state after the current step
+    float gsk, gbu, gbv, gq;              // partials: s_K, b_u, b_v, emission of the release hour
+};
+
+// One step of the reverse sweep: the receptor term of the state Xa after step k (when k
+// is a sample step and not the step that ended the run), then mu <- J_k^T mu with the
+// Jacobian of step k at the state X before it (fold = the step's reflection sign).
+__device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParams &A,
+                                             const Levels &LV, const ScenDev &sc,
+                                             const float4 *s_rec, const float *s_w,
+                                             unsigned long long gid, int sp, float m0, float mq,
+                                             float sig_h_uniform, float sq2dt, int k, float4 X,
+                                             float fold, float4 Xa, bool sample, Adjoint &J)
+{
+    if (sample) {
+        const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
+        const float m = m0 * decay;
+        for (int r = 0; r < A.R; ++r) {
+            const float4 q = s_rec[r];
+            const float dx = Xa.x - q.x, dy = Xa.y - q.y, dz = Xa.z - q.z, dzi = Xa.z + q.z;
+            const float h2 = dx * dx + dy * dy;
+            const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
+            if (d1 > A.cut2 && d2 > A.cut2) continue;
+            const float e1 = A.norm * expf(-d1 * A.inv2s2);
+            const float e2 = A.norm * expf(-d2 * A.inv2s2);
+            const float wr = s_w[r];
+            const float c1 = -wr * m * A.inv_s2;
+            J.mu0 += c1 * (e1 + e2) * dx;
+            J.mu1 += c1 * (e1 + e2) * dy;
+            J.mu2 += c1 * (e1 * dz + e2 * dzi);
+            J.gq += wr * mq * decay * (e1 + e2);
+        }
+    }
+    const StepTime T = step_time(P, sc.wind_offset, k);
+    float val[5], g[5][3];
+    sample_met_grad(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
+    const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
+                               P.seed_lo, P.seed_hi);
+    float n0, n1, n2;
+    normals3(w, n0, n1, n2);
+    const float kh = P.k_scale * val[4], kz = P.k_scale * val[3];
+    const float sig_h = sqrtf(2.0f * kh * P.dt), sig_z = sqrtf(2.0f * kz * P.dt);
+    const float ch = val[4] > 0.0f ? sq2dt / (2.0f * sqrtf(val[4])) : 0.0f;
+    const float cz = val[3] > 0.0f ? sq2dt / (2.0f * sqrtf(val[3])) : 0.0f;
+    // parameter partials: s_K, b_u, b_v
+    const float inv2sk = 0.5f / P.k_scale;
+    J.gsk += (J.mu0 * n0 * sig_h + J.mu1 * n1 * sig_h + J.mu2 * fold * n2 * sig_z) * inv2sk;
+    J.gbu += J.mu0 * P.dt;
+    J.gbv += J.mu1 * P.dt;
+    // mu <- J^T mu
+    const float mz = J.mu2 * fold;
+    float nm[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float jx = P.dt * g[0][d] + n0 * ch * g[4][d];
+        const float jy = P.dt * g[1][d] + n1 * ch * g[4][d];
+        const float jz = P.dt * g[2][d] + n2 * cz * g[3][d];
+        nm[d] = J.mu0 * jx + J.mu1 * jy + mz * jz;
+    }
+    J.mu0 += nm[0];
+    J.mu1 += nm[1];
+    J.mu2 = mz + nm[2];
+}
+
+// Sums of the block's particles (FP64) and one atomic per parameter per block: the source
+// partials are the sum of mu at release.
+__device__ __forceinline__ void reduce_gradient(const AdjParams &A, const Tile &tile, Adjoint J,
+                                                bool valid, int qidx, double *s_g, double *s_gq)
+{
+    if (!valid) J = Adjoint{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int o = 16; o > 0; o >>= 1) {
+        J.mu0 += __shfl_xor_sync(0xffffffffu, J.mu0, o);
+        J.mu1 += __shfl_xor_sync(0xffffffffu, J.mu1, o);
+        J.mu2 += __shfl_xor_sync(0xffffffffu, J.mu2, o);
+        J.gsk += __shfl_xor_sync(0xffffffffu, J.gsk, o);
+        J.gbu += __shfl_xor_sync(0xffffffffu, J.gbu, o);
+        J.gbv += __shfl_xor_sync(0xffffffffu, J.gbv, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_g[0], (double)J.mu0);
+        atomicAdd(&s_g[1], (double)J.mu1);
+        atomicAdd(&s_g[2], (double)J.mu2);
+        atomicAdd(&s_g[3], (double)J.gsk);
+        atomicAdd(&s_g[4], (double)J.gbu);
+        atomicAdd(&s_g[5], (double)J.gbv);
+    }
+    if (J.gq != 0.f) atomicAdd(&s_gq[qidx], (double)J.gq);
+    __syncthreads();
+    double *G = A.grad + (long long)tile.scen * A.ng;
+    if (threadIdx.x < 3) atomicAdd(G + threadIdx.x, s_g[threadIdx.x]);
+    else if (threadIdx.x < 6) atomicAdd(G + 3 + A.nq + (threadIdx.x - 3), s_g[threadIdx.x]);
+    for (int i = threadIdx.x; i < A.nq; i += ADJ_BLOCK)
+        if (s_gq[i] != 0.0) atomicAdd(G + 3 + i, s_gq[i]);
+}
+
+// Receptors and per-scenario dL/dC (scaled by 1 / samples) into shared memory.
+__device__ __forceinline__ void load_receptors(const AdjParams &A, const Tile &tile, float4 *s_rec,
+                                               float *s_w, double *s_g, double *s_gq)
+{
+    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
+        s_rec[r] = A.rec[r];
+        s_w[r] = (float)(A.w[(long long)tile.scen * A.R + r] * (double)A.inv_ns);
+    }
+    for (int i = threadIdx.x; i < MAX_NQ; i += ADJ_BLOCK) s_gq[i] = 0.0;
+    if (threadIdx.x < 6) s_g[threadIdx.x] = 0.0;
+    __syncthreads();
+}
+
+// Checkpoint form: each thread recomputes its particle's path one CK-step segment at a
+// time from the checkpoint (same keyed draws and FP32 arithmetic, so the same path and
+// events) into a local buffer, then sweeps the segment in reverse.
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_backward_kernel(const StepParams P, const AdjParams A)
 {
@@ -169,19 +300,11 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
     __shared__ double s_gq[MAX_NQ];
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     const Tile tile = A.tiles[blockIdx.x];
-    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
-        s_rec[r] = A.rec[r];
-        s_w[r] = (float)(A.w[(long long)tile.scen * A.R + r] * (double)A.inv_ns);
-    }
-    for (int i = threadIdx.x; i < MAX_NQ; i += ADJ_BLOCK) s_gq[i] = 0.0;
-    if (threadIdx.x < 6) s_g[threadIdx.x] = 0.0;
-    __syncthreads();
+    load_receptors(A, tile, s_rec, s_w, s_g, s_gq);
     const ScenDev sc = P.scen[tile.scen];
     const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
     const float sq2dt = sqrtf(2.0f * P.k_scale * P.dt);
-    float mu0 = 0.f, mu1 = 0.f, mu2 = 0.f;
-    float gsk = 0.f, gbu = 0.f, gbv = 0.f, gq = 0.f;
-    int qidx = 0;
+    Adjoint J{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     // Loops run over warp-uniform step ranges with per-lane predicates, so the lanes of a
     // warp (consecutive particles of one release step) stay converged through the
     // recomputation and the reverse sweep.
@@ -192,7 +315,7 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
     const int tix = sc.m0_off + (sp - sc.rel_first);
     const float m0 = __ldg(P.m0 + tix);
     const float mq = __ldg(A.mq + tix);
-    qidx = __ldg(A.qi + tix);
+    const int qidx = __ldg(A.qi + tix);
     float4 seg[CK + 1];
     signed char sfold[CK];
     for (int c = A.n_ck - 1; c >= 0; --c) {
@@ -231,99 +354,85 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
         for (int k = k_hi - 1; k >= k_lo; --k) {
             if (!(run && k >= kstart && k <= klast)) continue;
             const int i = k - k_lo;
-            if ((k + 1) % A.every == 0 && !(ev && k == klast)) {
-                const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
-                const float m = m0 * decay;
-                const float4 X = seg[i + 1];
-                for (int r = 0; r < A.R; ++r) {
-                    const float4 q = s_rec[r];
-                    const float dx = X.x - q.x, dy = X.y - q.y, dz = X.z - q.z, dzi = X.z + q.z;
-                    const float h2 = dx * dx + dy * dy;
-                    const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
-                    if (d1 > A.cut2 && d2 > A.cut2) continue;
-                    const float e1 = A.norm * expf(-d1 * A.inv2s2);
-                    const float e2 = A.norm * expf(-d2 * A.inv2s2);
-                    const float wr = s_w[r];
-                    const float c1 = -wr * m * A.inv_s2;
-                    mu0 += c1 * (e1 + e2) * dx;
-                    mu1 += c1 * (e1 + e2) * dy;
-                    mu2 += c1 * (e1 * dz + e2 * dzi);
-                    gq += wr * mq * decay * (e1 + e2);
-                }
-            }
-            // undo step k at the state before it
-            const float4 X = seg[i];
-            const StepTime T = step_time(P, sc.wind_offset, k);
-            float val[5], g[5][3];
-            sample_met_grad(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
-            const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
-                                       P.seed_lo, P.seed_hi);
-            float n0, n1, n2;
-            normals3(w, n0, n1, n2);
-            const float fold = (float)sfold[i];
-            const float kh = P.k_scale * val[4], kz = P.k_scale * val[3];
-            const float sig_h = sqrtf(2.0f * kh * P.dt), sig_z = sqrtf(2.0f * kz * P.dt);
-            const float ch = val[4] > 0.0f ? sq2dt / (2.0f * sqrtf(val[4])) : 0.0f;
-            const float cz = val[3] > 0.0f ? sq2dt / (2.0f * sqrtf(val[3])) : 0.0f;
-            // parameter partials: s_K, b_u, b_v
-            const float inv2sk = 0.5f / P.k_scale;
-            gsk += (mu0 * n0 * sig_h + mu1 * n1 * sig_h + mu2 * fold * n2 * sig_z) * inv2sk;
-            gbu += mu0 * P.dt;
-            gbv += mu1 * P.dt;
-            // mu <- J^T mu
-            const float mz = mu2 * fold;
-            float nm[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float jx = P.dt * g[0][d] + n0 * ch * g[4][d];
-                const float jy = P.dt * g[1][d] + n1 * ch * g[4][d];
-                const float jz = P.dt * g[2][d] + n2 * cz * g[3][d];
-                nm[d] = mu0 * jx + mu1 * jy + mz * jz;
-            }
-            mu0 += nm[0];
-            mu1 += nm[1];
-            mu2 = mz + nm[2];
+            const bool sample = (k + 1) % A.every == 0 && !(ev && k == klast);
+            reverse_step(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k,
+                         seg[i], (float)sfold[i], seg[i + 1], sample, J);
         }
         __syncwarp();
     }
-    if (!valid) { mu0 = mu1 = mu2 = gsk = gbu = gbv = gq = 0.f; }
-    // block reductions (FP64) and one atomic per parameter per block
-    for (int o = 16; o > 0; o >>= 1) {
-        mu0 += __shfl_xor_sync(0xffffffffu, mu0, o);
-        mu1 += __shfl_xor_sync(0xffffffffu, mu1, o);
-        mu2 += __shfl_xor_sync(0xffffffffu, mu2, o);
-        gsk += __shfl_xor_sync(0xffffffffu, gsk, o);
-        gbu += __shfl_xor_sync(0xffffffffu, gbu, o);
-        gbv += __shfl_xor_sync(0xffffffffu, gbv, o);
+    reduce_gradient(A, tile, J, valid, qidx, s_g, s_gq);
+}
+
+// Trajectory form: the forward kept every state, so the sweep reads them back (one
+// coalesced 16-B row entry per step, prefetched one step ahead) instead of recomputing.
+__global__ void __launch_bounds__(ADJ_BLOCK)
+adj_backward_traj_kernel(const StepParams P, const AdjParams A)
+{
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
+    __shared__ float4 s_rec[MAX_REC];
+    __shared__ float s_w[MAX_REC];
+    __shared__ double s_g[6];
+    __shared__ double s_gq[MAX_NQ];
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    const Tile tile = A.tiles[blockIdx.x];
+    load_receptors(A, tile, s_rec, s_w, s_g, s_gq);
+    const ScenDev sc = P.scen[tile.scen];
+    const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
+    const float sq2dt = sqrtf(2.0f * P.k_scale * P.dt);
+    Adjoint J{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const bool valid = (int)threadIdx.x < tile.count;
+    const long long slot = tile.first + (valid ? threadIdx.x : 0);
+    const unsigned long long gid = (unsigned long long)(sc.id0 + (slot - sc.first_slot));
+    const int sp = (int)release_step_of(sc, slot);
+    const int tix = sc.m0_off + (sp - sc.rel_first);
+    const float m0 = __ldg(P.m0 + tix);
+    const float mq = __ldg(A.mq + tix);
+    const int qidx = __ldg(A.qi + tix);
+    const longlong2 tt = A.traj_tile[blockIdx.x];
+    const float4 *row = A.traj + tt.x + threadIdx.x;
+    const int k0 = (int)tt.y;
+    float4 Xa = A.fin[slot];                      // state after the last step taken
+    const uint32_t fw = __float_as_uint(Xa.w);
+    const bool ev = (fw >> 31) != 0;
+    // steps [kb, kn) of this lane (empty for padding lanes); rows exist from k0 on
+    const int kn = valid ? (int)(fw & 0x7fffffffu) : 0;
+    const int kb = valid ? max(sp, k0) : 0;
+    // warp-uniform range with per-lane predicates, as in the checkpoint form
+    const int k_top = __reduce_max_sync(0xffffffffu, kn) - 1;
+    const int k_bot = __reduce_min_sync(0xffffffffu, kb < kn ? kb : 0x7fffffff);
+    float4 Xn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k_top >= kb && k_top < kn) Xn = __ldcs(row + (long long)(k_top - k0) * ADJ_BLOCK);
+    for (int k = k_top; k >= k_bot; --k) {
+        const bool act = k >= kb && k < kn;
+        const float4 X = Xn;
+        if (k - 1 >= kb && k - 1 < kn) Xn = __ldcs(row + (long long)(k - 1 - k0) * ADJ_BLOCK);
+        if (!act) continue;
+        const bool sample = (k + 1) % A.every == 0 && !(ev && k == kn - 1);
+        reverse_step(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
+                     X.w, Xa, sample, J);
+        Xa = X;
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&s_g[0], (double)mu0);
-        atomicAdd(&s_g[1], (double)mu1);
-        atomicAdd(&s_g[2], (double)mu2);
-        atomicAdd(&s_g[3], (double)gsk);
-        atomicAdd(&s_g[4], (double)gbu);
-        atomicAdd(&s_g[5], (double)gbv);
-    }
-    if (gq != 0.f) atomicAdd(&s_gq[qidx], (double)gq);
-    __syncthreads();
-    double *G = A.grad + (long long)tile.scen * A.ng;
-    if (threadIdx.x < 3) atomicAdd(G + threadIdx.x, s_g[threadIdx.x]);
-    else if (threadIdx.x < 6) atomicAdd(G + 3 + A.nq + (threadIdx.x - 3), s_g[threadIdx.x]);
-    for (int i = threadIdx.x; i < A.nq; i += ADJ_BLOCK)
-        if (s_gq[i] != 0.0) atomicAdd(G + 3 + i, s_gq[i]);
+    reduce_gradient(A, tile, J, valid, qidx, s_g, s_gq);
 }
 
 cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    adj_forward_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+    if (A.traj)
+        adj_forward_kernel<true><<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+    else
+        adj_forward_kernel<false><<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles)
 {
     if (n_tiles <= 0) return cudaSuccess;
-    adj_backward_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+    if (A.traj)
+        adj_backward_traj_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+    else
+        adj_backward_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,14 @@ struct AdjParams {
     int n_ck;
     float4 *ckpt;                     // [n_ck][n_slots]
     long long n_slots;
+    // Trajectory storage (ckpt unused when traj is set): tile t keeps the state before
+    // each step k >= traj_tile[t].y, with the step's fold in w, as rows of ADJ_BLOCK float4
+    // from traj + traj_tile[t].x + (k - traj_tile[t].y) * ADJ_BLOCK; fin[slot] is the state
+    // after the last step taken, w = that step + 1 (release step if none), bit 31 set when
+    // the run ended by an event.
+    float4 *traj;
+    float4 *fin;
+    const longlong2 *traj_tile;
     const Tile *tiles;
     double *C;                        // [n_scen][R]
     const double *w;                  // [n_scen][R] dL/dC

@@ -143,6 +143,14 @@ struct lpm_ctx {
     short *d_qi = nullptr;                  // emission-series index per release step
     float4 *d_ckpt = nullptr;
     size_t d_ckpt_cap = 0;
+    // trajectory storage (the default when it fits): rows of every tile from its first
+    // release step on, and the state after each particle's last step (float4 elements)
+    float4 *d_traj = nullptr, *d_fin = nullptr;
+    size_t d_traj_cap = 0, d_fin_cap = 0;
+    longlong2 *d_traj_tile = nullptr;
+    size_t traj_need = 0;
+    size_t adj_store_max = (size_t)128 << 30;   // bytes; 0 keeps checkpoints only
+    bool adj_traj = false;                      // storage of the held forward
     float4 *d_rec = nullptr;
     double *d_rC = nullptr, *d_rw = nullptr, *d_rgrad = nullptr;
     size_t d_rbuf_cap = 0;
@@ -743,7 +751,7 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
                     c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair,
                     c->d_sp_conc, c->d_sp_dep, c->d_w_home, c->d_w_sorted[0],
-                    c->d_w_sorted[1]};
+                    c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
@@ -1737,8 +1745,56 @@ int adj_nq(const lpm_ctx *c)
     return (int)nq;
 }
 
+// Storage of the forward's states for the backward: the whole trajectory when it fits in
+// the limit and in free device memory (keeping 8 GiB spare), else checkpoints every CK steps.
+lpm_status adj_storage(lpm_ctx *c)
+{
+    const size_t need_b = (c->traj_need + (size_t)c->n_slots_used) * sizeof(float4);
+    bool traj = need_b <= c->adj_store_max;
+    if (traj && (c->traj_need > c->d_traj_cap || (size_t)c->n_slots_used > c->d_fin_cap)) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        size_t fr = 0, tot = 0;
+        LPM_CUDA(c, cudaMemGetInfo(&fr, &tot));
+        const size_t held = (c->d_traj_cap + c->d_fin_cap + c->d_ckpt_cap) * sizeof(float4);
+        traj = need_b + ((size_t)8 << 30) <= fr + held;
+        if (traj) {
+            for (float4 **p : {&c->d_traj, &c->d_fin, &c->d_ckpt}) {
+                if (*p) cudaFree(*p);
+                *p = nullptr;
+            }
+            c->d_traj_cap = c->d_fin_cap = c->d_ckpt_cap = 0;
+            c->adj_sig.clear();
+            const size_t nt = std::max<size_t>(1, c->traj_need);
+            const size_t nf = std::max<size_t>(1, (size_t)c->n_slots_used);
+            if (cudaMalloc(&c->d_traj, nt * sizeof(float4)) == cudaSuccess &&
+                cudaMalloc(&c->d_fin, nf * sizeof(float4)) == cudaSuccess) {
+                c->d_traj_cap = nt;
+                c->d_fin_cap = nf;
+            } else {
+                (void)cudaGetLastError();             // out of memory: use checkpoints
+                for (float4 **p : {&c->d_traj, &c->d_fin}) {
+                    if (*p) cudaFree(*p);
+                    *p = nullptr;
+                }
+                traj = false;
+            }
+        }
+    }
+    if (!traj && (c->d_traj || c->d_fin)) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        for (float4 **p : {&c->d_traj, &c->d_fin}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        c->d_traj_cap = c->d_fin_cap = 0;
+        c->adj_sig.clear();
+    }
+    c->adj_traj = traj;
+    return LPM_OK;
+}
+
 lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, int every,
-                       AdjParams &A, StepParams &P)
+                       AdjParams &A, StepParams &P, bool reuse = false)
 {
     const lpm_config &g = c->cfg;
     if (R < 1 || R > MAX_REC || !rec) return fail(c, LPM_E_INVALID, "need 1 <= R <= %d receptors", MAX_REC);
@@ -1758,28 +1814,48 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     fill_params(c, P);
     for (size_t h = 0; h < c->pair_pending.size(); ++h)      // weather still being uploaded
         if (c->pair_pending[h]) LPM_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_pair[h], 0));
-    // tiles of ADJ_BLOCK particles over every held particle
+    // tiles of ADJ_BLOCK particles over every held particle; the trajectory rows of a tile
+    // start at its first particle's release step (release steps do not decrease with slot)
     if (!c->adj_tiles_valid) {
         c->adj_tiles.clear();
-        for (size_t s = 0; s < c->scen.size(); ++s)
-            for (long long p = 0; p < c->scen[s].n; p += ADJ_BLOCK) {
+        std::vector<longlong2> tt;
+        size_t rows = 0;
+        for (size_t s = 0; s < c->scen.size(); ++s) {
+            const ScenHost &h = c->scen[s];
+            for (long long p = 0; p < h.n; p += ADJ_BLOCK) {
                 Tile t;
                 t.scen = (int)s;
-                t.first = c->scen[s].first_slot + p;
-                t.count = (int)std::min<long long>(ADJ_BLOCK, c->scen[s].n - p);
+                t.first = h.first_slot + p;
+                t.count = (int)std::min<long long>(ADJ_BLOCK, h.n - p);
                 c->adj_tiles.push_back(t);
+                const long long k0 =
+                    h.rel_first + ((h.part_first + p) * (h.rel_last - h.rel_first)) / h.n_total;
+                tt.push_back(make_longlong2((long long)rows, k0));
+                rows += (size_t)std::max<long long>(0, g.n_steps - k0) * ADJ_BLOCK;
             }
+        }
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
-        if (c->d_adj_tiles) cudaFree(c->d_adj_tiles);
-        c->d_adj_tiles = nullptr;
-        LPM_CUDA(c, cudaMalloc(&c->d_adj_tiles, std::max<size_t>(1, c->adj_tiles.size()) * sizeof(Tile)));
+        for (void **p : {(void **)&c->d_adj_tiles, (void **)&c->d_traj_tile}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        const size_t nt = std::max<size_t>(1, c->adj_tiles.size());
+        LPM_CUDA(c, cudaMalloc(&c->d_adj_tiles, nt * sizeof(Tile)));
+        LPM_CUDA(c, cudaMalloc(&c->d_traj_tile, nt * sizeof(longlong2)));
         LPM_CUDA(c, cudaMemcpy(c->d_adj_tiles, c->adj_tiles.data(), c->adj_tiles.size() * sizeof(Tile),
                                cudaMemcpyHostToDevice));
+        LPM_CUDA(c, cudaMemcpy(c->d_traj_tile, tt.data(), tt.size() * sizeof(longlong2),
+                               cudaMemcpyHostToDevice));
+        c->traj_need = rows;
         c->adj_tiles_valid = true;
+    }
+    if (!reuse) {
+        lpm_status sst = adj_storage(c);
+        if (sst != LPM_OK) return sst;
     }
     const int n_ck = (int)((g.n_steps + CK - 1) / CK);
     const size_t need_ck = (size_t)n_ck * (size_t)c->n_slots_used;
-    if (need_ck > c->d_ckpt_cap) {
+    if (!c->adj_traj && need_ck > c->d_ckpt_cap) {
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
         if (c->d_ckpt) cudaFree(c->d_ckpt);
         c->d_ckpt = nullptr;
@@ -1823,6 +1899,9 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     A.n_ck = n_ck;
     A.ckpt = c->d_ckpt;
     A.n_slots = c->n_slots_used;
+    A.traj = c->adj_traj ? c->d_traj : nullptr;
+    A.fin = c->adj_traj ? c->d_fin : nullptr;
+    A.traj_tile = c->d_traj_tile;
     A.tiles = c->d_adj_tiles;
     A.C = c->d_rC;
     A.w = c->d_rw;
@@ -1841,6 +1920,7 @@ std::vector<double> adj_signature(const lpm_ctx *c, const double *rec, int R, do
     sig.push_back(bandwidth);
     sig.push_back(every);
     sig.push_back((double)c->params_version);
+    sig.push_back(c->adj_traj ? 1.0 : 0.0);
     return sig;
 }
 
@@ -1885,7 +1965,7 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     if (c->adj_sig != adj_signature(c, rec, R, bandwidth, sample_every)) {
         st = adj_forward(c, rec, R, bandwidth, sample_every, A, P);   // checkpoints
     } else {
-        st = adj_prepare(c, rec, R, bandwidth, sample_every, A, P);
+        st = adj_prepare(c, rec, R, bandwidth, sample_every, A, P, true);
     }
     if (st != LPM_OK) return st;
     const size_t ns = (size_t)c->cfg.n_scenarios;
@@ -1899,6 +1979,22 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     st = check_device_error(c);
     if (st != LPM_OK) return st;
     LPM_CUDA(c, cudaMemcpy(grad, c->d_rgrad, ns * A.ng * sizeof(double), cudaMemcpyDeviceToHost));
+    return LPM_OK;
+}
+
+lpm_status lpm_set_adjoint_storage(lpm_ctx *c, uint64_t max_bytes)
+{
+    if (!c) return LPM_E_INVALID;
+    c->adj_store_max = (size_t)max_bytes;
+    c->adj_sig.clear();
+    return LPM_OK;
+}
+
+lpm_status lpm_adjoint_storage(lpm_ctx *c, int *trajectory, uint64_t *bytes)
+{
+    if (!c || !trajectory || !bytes) return LPM_E_INVALID;
+    *trajectory = c->adj_traj ? 1 : 0;
+    *bytes = (uint64_t)((c->d_traj_cap + c->d_fin_cap + c->d_ckpt_cap) * sizeof(float4));
     return LPM_OK;
 }
 

@@ -31,7 +31,7 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save",
            "lpm_load", "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model",
            "lpm_set_boundary_layer", "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
-           "lpm_particle_velocity"]
+           "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage"]
 
 
 class LpmError(RuntimeError):
@@ -113,6 +113,8 @@ def load() -> C.CDLL:
     L.lpm_set_emission.argtypes = [vp, C.c_int, dp, C.c_int]
     L.lpm_receptors.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp]
     L.lpm_adjoint.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp, dp]
+    L.lpm_set_adjoint_storage.argtypes = [vp, C.c_uint64]
+    L.lpm_adjoint_storage.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_uint64)]
     L.lpm_draws_static.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
                                    C.c_uint32, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
     L.lpm_draws.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
@@ -125,7 +127,7 @@ def load() -> C.CDLL:
                  "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load",
                  "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model", "lpm_set_boundary_layer",
                  "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
-                 "lpm_particle_velocity"):
+                 "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -285,6 +287,18 @@ def lpm_adjoint(ctx, receptors, bandwidth: float, sample_every: int, dL_dC, n_q:
                                    float(bandwidth), int(sample_every), _ptr(w, C.c_double),
                                    _ptr(out, C.c_double)))
     return out
+
+
+def lpm_set_adjoint_storage(ctx, max_bytes: int) -> None:
+    """Largest trajectory the receptor forward may keep for the adjoint (0: checkpoints)."""
+    _check(ctx, load().lpm_set_adjoint_storage(C.c_void_p(ctx), int(max_bytes)))
+
+
+def lpm_adjoint_storage(ctx):
+    """(kept the trajectory, device bytes held for the adjoint's states)."""
+    t, b = C.c_int(), C.c_uint64()
+    _check(ctx, load().lpm_adjoint_storage(C.c_void_p(ctx), C.byref(t), C.byref(b)))
+    return bool(t.value), int(b.value)
 
 
 def lpm_step(ctx, n: int) -> None:

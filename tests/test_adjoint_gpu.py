@@ -195,3 +195,31 @@ def test_batched_inversion_reduces_misfit_and_approaches_the_hidden_source():
     d1 = np.linalg.norm(res.sources[-1, :, :2] - h[:2], axis=1)
     print("best candidate distance to the hidden source: start", d0.min(), "end", d1[res.best])
     assert d1[res.best] < d0.min()
+
+
+def test_trajectory_and_checkpoint_storage_agree():
+    """The backward that reads the stored trajectory and the one that recomputes 64-step
+    segments from checkpoints take the same paths and events: receptors and gradients agree
+    to the order of the FP64 sums, for one scenario (deposition, exits) and a batch of
+    candidates; a limit below the trajectory's size selects checkpoints."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg, rec = _realistic(n=5000, steps=400)
+    cand, _, _ = li.make_cfg4(n_candidates=3, n_per=3000, n_steps=300, n_obs=1000)
+    for c, nq in [(cfg, 24), (cand, 24)]:
+        w = np.linspace(-1.0, 1.0, c.n_scenarios * rec.shape[0]).reshape(c.n_scenarios, -1)
+        out = {}
+        for limit in (1 << 37, 0, 1024):
+            with Sim(c) as sim:
+                lpm.lpm_set_adjoint_storage(sim.ctx, limit)
+                C = lpm.lpm_receptors(sim.ctx, c.n_scenarios, rec, SIGMA, 18)
+                g = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, w, nq)
+                traj, nbytes = lpm.lpm_adjoint_storage(sim.ctx)
+            assert traj == (limit == 1 << 37)
+            assert nbytes > 0
+            out[limit] = (C, g)
+        C0, g0 = out[1 << 37]
+        assert np.abs(g0).max() > 0
+        for limit in (0, 1024):
+            C1, g1 = out[limit]
+            np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max())
+            np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
