@@ -247,7 +247,7 @@ def measure_adjoint(args, stream):
 
     import lpm_inputs as li
     from paper_0912_3223_gb300 import Sim, lpm
-    cfg = li.make_cfg3()
+    cfg = li.make_cfg3(n_particles=args.adjoint_particles)
     rec = li.make_receptors()
     w = np.linspace(-1.0, 1.0, rec.shape[0])[None, :]
     with torch.cuda.stream(stream):
@@ -669,6 +669,8 @@ def main():
     ap.add_argument("--batched-block", type=int, default=256)
     ap.add_argument("--batched-ppt", type=int, default=1)
     ap.add_argument("--batched-occ", type=int, default=2)
+    ap.add_argument("--adjoint-particles", type=int, default=1_000_000,
+                    help="particles of the adjoint form (smaller for profiler captures)")
     ap.add_argument("--batched-sort-every", type=int, default=60,
                     help="steps between sorts by cell in the batched form (0: off)")
     args = ap.parse_args()

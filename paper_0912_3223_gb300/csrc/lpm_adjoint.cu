@@ -1,13 +1,18 @@
 // lpm_adjoint.cu - receptor concentrations and their reverse-mode gradient.
 //
-// Forward: every particle runs the whole horizon with the step of the main loop
-// (particle_step), the decayed mass is spread on the receptors with a Gaussian kernel
-// (with the ground image) every `every` steps, and the state at the start of every
-// CK-th step is checkpointed. Backward: each thread recomputes its particle's path one
-// CK-step segment at a time from the checkpoint (same keyed draws, same FP32 arithmetic,
-// so the same path and events), then sweeps the segment in reverse, carrying
-// mu = dL/dX and accumulating the parameter partials. Events (deposition, exit) are
-// frozen; sums over particles are reduced in FP64.
+// Forward: every particle runs the horizon with the step of the main loop (particle_step)
+// and the decayed mass is spread on the receptors with a Gaussian kernel (with the ground
+// image) every `every` steps. Backward: a reverse sweep carrying mu = dL/dX through the
+// transposed Jacobian of each step and accumulating the parameter partials; events
+// (deposition, exit) are frozen; sums over particles are reduced in FP64. The backward
+// needs the forward's states, kept in one of three forms:
+//  - trajectory, cell-sorted (one scenario, sorting on): CK-step segments over the
+//    particles re-sorted by weather cell between segments, every state stored;
+//  - trajectory in release order (several scenarios, or sorting off): every state stored,
+//    one thread per particle over the whole horizon;
+//  - checkpoints every CK steps when the trajectory does not fit: each CK-step segment is
+//    recomputed from its checkpoint (same keyed draws and FP32 arithmetic, so the same
+//    path and events) before it is swept.
 #include "lpm_advance.cuh"
 #include "lpm_adjoint.h"
 
@@ -101,7 +106,7 @@ __device__ __forceinline__ float4 pack_state(float x, float y, float z, uint32_t
 // Forward: receptor concentrations, and checkpoints or the whole trajectory.
 // ---------------------------------------------------------------------------------
 template <bool TRAJ>
-__global__ void __launch_bounds__(ADJ_BLOCK)
+__global__ void __launch_bounds__(ADJ_BLOCK, 8)
 adj_forward_kernel(const StepParams P, const AdjParams A)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
@@ -414,6 +419,170 @@ adj_backward_traj_kernel(const StepParams P, const AdjParams A)
         Xa = X;
     }
     reduce_gradient(A, tile, J, valid, qidx, s_g, s_gq);
+}
+
+// ---------------------------------------------------------------------------------
+// Sorted trajectory form (one scenario): one launch per CK-step segment over the
+// particles alive at its start in weather-cell order, then its releases; between
+// segments the survivors are re-sorted by cell (lpm_sort.cu). The states of a segment are
+// stored row by row in that order; the backward sweeps the segments in reverse and hands
+// dL/dX from one segment to the previous one through G.mu, indexed by home slot.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ bool seg_entry(const AdjSeg &G, const ScenDev &sc, long long e,
+                                          bool from_a, unsigned int live, long long &home)
+{
+    if (from_a) {
+        if (e >= (long long)live) { home = sc.first_slot; return false; }
+        home = G.ord[e];
+        return true;
+    }
+    const Tile t = G.tiles[G.b_first + (blockIdx.x - G.tiles_a)];
+    const bool ok = (int)threadIdx.x < t.count;
+    home = t.first + (ok ? threadIdx.x : 0);
+    return ok;
+}
+
+__global__ void __launch_bounds__(ADJ_BLOCK, 8)
+adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
+{
+    const bool from_a = (int)blockIdx.x < G.tiles_a;
+    const unsigned int live = from_a ? *G.live : 0u;
+    if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
+    __shared__ float4 s_rec[MAX_REC];
+    __shared__ double s_C[MAX_REC];
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
+        s_rec[r] = A.rec[r];
+        s_C[r] = 0.0;
+    }
+    __syncthreads();
+    const ScenDev sc = P.scen[0];
+    const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
+    const long long e = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
+    long long home;
+    if (seg_entry(G, sc, e, from_a, live, home)) {
+        const unsigned long long gid = (unsigned long long)(sc.id0 + (home - sc.first_slot));
+        const int sp = (int)release_step_of(sc, home);
+        const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
+        float x = sc.src_x, y = sc.src_y, z = sc.src_z;
+        if (from_a) {
+            const float4 s0 = G.sorted[e];
+            x = s0.x; y = s0.y; z = s0.z;
+        }
+        uint32_t st = ST_ACTIVE;
+        const int k_first = max(sp, G.k_lo);
+        int kn = k_first;                          // one past the last step taken
+        for (int k = k_first; k < G.k_hi; ++k) {
+            const StepTime T = step_time(P, sc.wind_offset, k);
+            const float xb = x, yb = y, zb = z;
+            float fs = 1.0f;
+            st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp, sig_h_uniform, T.du, T.dv,
+                                      x, y, z, &fs);
+            __stcs(G.traj + (long long)(k - G.k_lo) * G.width + e, make_float4(xb, yb, zb, fs));
+            kn = k + 1;
+            if (st != ST_ACTIVE) break;
+            if ((k + 1) % A.every == 0) {
+                const float m = m0 * expf(-P.lambda * (float)(k + 1 - sp) * P.dt) * A.inv_ns;
+                for (int r = 0; r < A.R; ++r) {
+                    const float4 q = s_rec[r];
+                    const float dx = x - q.x, dy = y - q.y, dz = z - q.z, dzi = z + q.z;
+                    const float h2 = dx * dx + dy * dy;
+                    const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
+                    if (d1 > A.cut2 && d2 > A.cut2) continue;
+                    const float Gk = A.norm * (expf(-d1 * A.inv2s2) + expf(-d2 * A.inv2s2));
+                    atomicAdd(&s_C[r], (double)(m * Gk));
+                }
+            }
+        }
+        G.fin[e] = make_float4(x, y, z, __uint_as_float((uint32_t)kn |
+                                                        (st != ST_ACTIVE ? 0x80000000u : 0u)));
+        const float4 out = pack_state(x, y, z, st, sp);          // what the sort reads
+        if (from_a) G.sorted[e] = out;
+        else G.home[home] = out;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK)
+        if (s_C[r] != 0.0) atomicAdd(A.C + r, s_C[r]);
+}
+
+__global__ void __launch_bounds__(ADJ_BLOCK, 5)
+adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
+{
+    const bool from_a = (int)blockIdx.x < G.tiles_a;
+    const unsigned int live = from_a ? *G.live : 0u;
+    if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
+    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ unsigned char s_lut[MAX_LUT];
+    __shared__ float4 s_rec[MAX_REC];
+    __shared__ float s_w[MAX_REC];
+    __shared__ double s_g[6];
+    __shared__ double s_gq[MAX_NQ];
+    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    const Tile tile0{0, 0, 0};
+    load_receptors(A, tile0, s_rec, s_w, s_g, s_gq);
+    const ScenDev sc = P.scen[0];
+    const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
+    const float sq2dt = sqrtf(2.0f * P.k_scale * P.dt);
+    const long long e = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
+    long long home;
+    const bool valid = seg_entry(G, sc, e, from_a, live, home);
+    const unsigned long long gid = (unsigned long long)(sc.id0 + (home - sc.first_slot));
+    const int sp = (int)release_step_of(sc, home);
+    const int tix = sc.m0_off + (sp - sc.rel_first);
+    const float m0 = __ldg(P.m0 + tix);
+    const float mq = __ldg(A.mq + tix);
+    const int qidx = __ldg(A.qi + tix);
+    float4 Xa = valid ? G.fin[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t fw = __float_as_uint(Xa.w);
+    const bool ev = (fw >> 31) != 0;
+    const int kn = valid ? (int)(fw & 0x7fffffffu) : 0;
+    const int kb = valid ? max(sp, G.k_lo) : 0;
+    Adjoint J{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    // a particle that ran through the segment carries dL/dX from the next one
+    if (valid && !ev && kn == G.k_hi && G.k_hi < A.n_steps) {
+        const float4 m = G.mu[home];
+        J.mu0 = m.x; J.mu1 = m.y; J.mu2 = m.z;
+    }
+    const int k_top = __reduce_max_sync(0xffffffffu, kn) - 1;
+    const int k_bot = __reduce_min_sync(0xffffffffu, kb < kn ? kb : 0x7fffffff);
+    const float4 *row = G.traj + e;
+    float4 Xn = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k_top >= kb && k_top < kn) Xn = __ldcs(row + (long long)(k_top - G.k_lo) * G.width);
+    for (int k = k_top; k >= k_bot; --k) {
+        const bool act = k >= kb && k < kn;
+        const float4 X = Xn;
+        if (k - 1 >= kb && k - 1 < kn) Xn = __ldcs(row + (long long)(k - 1 - G.k_lo) * G.width);
+        if (!act) continue;
+        const bool sample = (k + 1) % A.every == 0 && !(ev && k == kn - 1);
+        reverse_step(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
+                     X.w, Xa, sample, J);
+        Xa = X;
+    }
+    // released earlier: hand mu to the previous segment; released here: mu is the
+    // particle's share of the source partials
+    if (sp < G.k_lo) {
+        if (valid) G.mu[home] = make_float4(J.mu0, J.mu1, J.mu2, 0.f);
+        J.mu0 = J.mu1 = J.mu2 = 0.f;
+    }
+    reduce_gradient(A, tile0, J, valid, qidx, s_g, s_gq);
+}
+
+cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
+                                   const AdjSeg &G, int n_blocks)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    adj_forward_seg_kernel<<<n_blocks, ADJ_BLOCK, 0, s>>>(P, A, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
+                                    const AdjSeg &G, int n_blocks)
+{
+    if (n_blocks <= 0) return cudaSuccess;
+    adj_backward_seg_kernel<<<n_blocks, ADJ_BLOCK, 0, s>>>(P, A, G);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles)

@@ -40,4 +40,26 @@ struct AdjParams {
     const short *qi;                  // emission-series index of each release step
 };
 
+// One CK-step segment [k_lo, k_hi) of the sorted trajectory form (one scenario). Entries
+// [0, tiles_a * ADJ_BLOCK) are the particles alive at k_lo in weather-cell order (the first
+// *live valid: home slot ord[i], state sorted[i]); then come the release tiles
+// tiles[b_first, ...) of the segment at their home slots. Entry e of block b is
+// b * ADJ_BLOCK + lane.
+struct AdjSeg {
+    int k_lo, k_hi;
+    const unsigned int *live;
+    const unsigned int *ord;
+    float4 *sorted;                   // states at k_lo; the forward writes the end states back
+    int tiles_a;                      // blocks over the sorted entries (bound of *live)
+    float4 *home;                     // end states of the segment's releases, by home slot
+    const Tile *tiles;
+    int b_first;
+    long long width;                  // entries = (tiles_a + release tiles) * ADJ_BLOCK
+    float4 *traj;                     // state before step k of entry e at (k - k_lo) * width + e,
+                                      // the step's fold in w
+    float4 *fin;                      // [width] state after the entry's last step in the
+                                      // segment, w = that step + 1 | event bit 31
+    float4 *mu;                       // [slots] dL/dX at the segment's end, by home slot
+};
+
 }  // namespace lpm

@@ -151,6 +151,22 @@ struct lpm_ctx {
     size_t traj_need = 0;
     size_t adj_store_max = (size_t)128 << 30;   // bytes; 0 keeps checkpoints only
     bool adj_traj = false;                      // storage of the held forward
+    // sorted trajectory form (one scenario, sorting on): CK-step segments over the
+    // particles in weather-cell order, with the adjoint's own sort buffers (the run's sort
+    // state is not touched)
+    struct AdjSorted {
+        std::vector<Tile> tiles;                // release tiles grouped by segment
+        std::vector<int> seg_tile;              // [n_seg + 1] first release tile of a segment
+        std::vector<int> tiles_a;               // [n_seg] blocks over its sorted entries
+        std::vector<long long> off, foff;       // [n_seg + 1] trajectory / end-state offsets
+        long long max_width = 0;
+        Tile *d_tiles = nullptr;
+        unsigned int *ord = nullptr, *live = nullptr, *keys = nullptr, *hist = nullptr,
+                     *bsums = nullptr, *meta = nullptr, *slot_of = nullptr, *grave_n = nullptr;
+        float4 *st[2] = {nullptr, nullptr};
+        float4 *home = nullptr, *mu = nullptr, *grave = nullptr;
+    } as;
+    bool adj_sorted = false;                    // the held forward used the sorted form
     float4 *d_rec = nullptr;
     double *d_rC = nullptr, *d_rw = nullptr, *d_rgrad = nullptr;
     size_t d_rbuf_cap = 0;
@@ -754,6 +770,13 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    {
+        lpm_ctx::AdjSorted &S = c->as;
+        void *aps[] = {S.d_tiles, S.ord, S.live, S.keys, S.hist, S.bsums, S.meta, S.slot_of,
+                       S.grave_n, S.st[0], S.st[1], S.home, S.mu, S.grave};
+        for (void *p : aps)
+            if (p) cudaFree(p);
+    }
     if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_pair)
@@ -1745,13 +1768,165 @@ int adj_nq(const lpm_ctx *c)
     return (int)nq;
 }
 
+// Segments of the sorted form (one scenario): segment s covers steps [s CK, (s+1) CK); its
+// entries are blocks over the particles released before s CK (a bound of those alive) and
+// the tiles of the particles released within it; its trajectory rows and end states are
+// laid out back to back.
+lpm_status adj_plan_segments(lpm_ctx *c)
+{
+    lpm_ctx::AdjSorted &S = c->as;
+    const long long NS = c->cfg.n_steps;
+    const int n_seg = (int)((NS + CK - 1) / CK);
+    S.tiles.clear();
+    S.seg_tile.assign((size_t)n_seg + 1, 0);
+    S.tiles_a.assign((size_t)n_seg, 0);
+    S.off.assign((size_t)n_seg + 1, 0);
+    S.foff.assign((size_t)n_seg + 1, 0);
+    S.max_width = 0;
+    const ScenHost &h = c->scen[0];
+    long long off = 0, foff = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        S.seg_tile[(size_t)s] = (int)S.tiles.size();
+        const long long a = released_before(h, (long long)s * CK);
+        const long long b = released_before(h, (long long)(s + 1) * CK);
+        for (long long p = a; p < b; p += ADJ_BLOCK) {
+            Tile t;
+            t.scen = 0;
+            t.first = h.first_slot + p;
+            t.count = (int)std::min<long long>(ADJ_BLOCK, b - p);
+            S.tiles.push_back(t);
+        }
+        S.tiles_a[(size_t)s] = s ? (int)((a + ADJ_BLOCK - 1) / ADJ_BLOCK) : 0;
+        const long long width =
+            (long long)(S.tiles_a[(size_t)s] + (int)S.tiles.size() - S.seg_tile[(size_t)s]) * ADJ_BLOCK;
+        S.off[(size_t)s] = off;
+        S.foff[(size_t)s] = foff;
+        off += std::min<long long>(CK, NS - (long long)s * CK) * width;
+        foff += width;
+        S.max_width = std::max(S.max_width, width);
+    }
+    S.seg_tile[(size_t)n_seg] = (int)S.tiles.size();
+    S.off[(size_t)n_seg] = off;
+    S.foff[(size_t)n_seg] = foff;
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (S.d_tiles) cudaFree(S.d_tiles);
+    S.d_tiles = nullptr;
+    LPM_CUDA(c, cudaMalloc(&S.d_tiles, std::max<size_t>(1, S.tiles.size()) * sizeof(Tile)));
+    if (!S.tiles.empty())
+        LPM_CUDA(c, cudaMemcpy(S.d_tiles, S.tiles.data(), S.tiles.size() * sizeof(Tile),
+                               cudaMemcpyHostToDevice));
+    return LPM_OK;
+}
+
+// The sorted form's own buffers (allocates whatever is still missing).
+lpm_status adj_sorted_buffers(lpm_ctx *c)
+{
+    lpm_ctx::AdjSorted &S = c->as;
+    const size_t ns = std::max<size_t>(1, (size_t)c->n_slots_used);
+    const size_t nseg = S.tiles_a.size();
+    const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
+    auto need = [&](auto *&p, size_t bytes) -> cudaError_t {
+        return p ? cudaSuccess : cudaMalloc(&p, bytes);
+    };
+    LPM_CUDA(c, need(S.ord, std::max<size_t>(1, nseg) * ns * sizeof(unsigned int)));
+    LPM_CUDA(c, need(S.live, std::max<size_t>(1, nseg) * sizeof(unsigned int)));
+    LPM_CUDA(c, need(S.keys, (size_t)std::max<long long>(1, S.max_width) * sizeof(unsigned int)));
+    LPM_CUDA(c, need(S.hist, nb * sizeof(unsigned int)));
+    LPM_CUDA(c, need(S.bsums, ((nb + 1023) / 1024) * sizeof(unsigned int)));
+    LPM_CUDA(c, need(S.meta, 4 * sizeof(unsigned int)));
+    LPM_CUDA(c, need(S.slot_of, ns * sizeof(unsigned int)));
+    LPM_CUDA(c, need(S.grave_n, sizeof(unsigned int)));
+    for (float4 **p : {&S.st[0], &S.st[1], &S.home, &S.mu, &S.grave})
+        LPM_CUDA(c, need(*p, ns * sizeof(float4)));
+    return LPM_OK;
+}
+
+// Segment s of the sorted form, its sorted entries in S.st[cur].
+AdjSeg adj_segment(const lpm_ctx *c, int s, int cur)
+{
+    const lpm_ctx::AdjSorted &S = c->as;
+    AdjSeg G;
+    G.k_lo = s * CK;
+    G.k_hi = (int)std::min<long long>(c->cfg.n_steps, (long long)(s + 1) * CK);
+    G.live = S.live + s;
+    G.ord = S.ord + (size_t)s * std::max<size_t>(1, (size_t)c->n_slots_used);
+    G.sorted = S.st[cur];
+    G.tiles_a = S.tiles_a[(size_t)s];
+    G.home = S.home;
+    G.tiles = S.d_tiles;
+    G.b_first = S.seg_tile[(size_t)s];
+    G.width = (long long)(G.tiles_a + S.seg_tile[(size_t)s + 1] - G.b_first) * ADJ_BLOCK;
+    G.traj = c->d_traj + S.off[(size_t)s];
+    G.fin = c->d_fin + S.foff[(size_t)s];
+    G.mu = S.mu;
+    return G;
+}
+
+// Forward of the sorted form: per segment the advance over its entries, then the sort of
+// the survivors (and the segment's releases) by cell into the other buffer.
+lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &A)
+{
+    lpm_ctx::AdjSorted &S = c->as;
+    const int n_seg = (int)S.tiles_a.size();
+    LPM_CUDA(c, cudaMemsetAsync(S.live, 0, std::max(1, n_seg) * sizeof(unsigned int), c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(S.meta, 0, 4 * sizeof(unsigned int), c->stream));
+    LPM_CUDA(c, cudaMemsetAsync(S.grave_n, 0, sizeof(unsigned int), c->stream));
+    int cur = 0;
+    for (int s = 0; s < n_seg; ++s) {
+        const AdjSeg G = adj_segment(c, s, cur);
+        if (s > 0)
+            LPM_CUDA(c, cudaMemcpyAsync(S.live + s, S.meta, sizeof(unsigned int),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+        LPM_CUDA(c, launch_adj_forward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK)));
+        c->n_launches++;
+        if (s + 1 < n_seg) {
+            SortSource in;
+            in.state_a = G.sorted;
+            in.pidx_a = G.ord;
+            in.has_a = s > 0;
+            in.a_bound = (long long)G.tiles_a * ADJ_BLOCK;
+            in.state_b = S.home;
+            in.tiles = S.d_tiles;
+            in.b_first = G.b_first;
+            in.n_b = S.seg_tile[(size_t)s + 1] - G.b_first;
+            in.T = ADJ_BLOCK;
+            in.w_a = in.w_b = nullptr;
+            SortBuffers out;
+            out.state_out = S.st[cur ^ 1];
+            out.pidx_out = S.ord + (size_t)(s + 1) * std::max<size_t>(1, (size_t)c->n_slots_used);
+            out.slot_of = S.slot_of;
+            out.keys = S.keys;
+            out.hist = S.hist;
+            out.block_sums = S.bsums;
+            out.meta = S.meta;
+            out.grave = S.grave;
+            out.grave_count = S.grave_n;
+            out.w_out = nullptr;
+            LPM_CUDA(c, launch_sort(c->stream, P, in, out));
+            c->n_launches += 7;
+            cur ^= 1;
+        }
+    }
+    return LPM_OK;
+}
+
+lpm_status adj_backward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &A)
+{
+    for (int s = (int)c->as.tiles_a.size() - 1; s >= 0; --s) {
+        const AdjSeg G = adj_segment(c, s, 0);
+        LPM_CUDA(c, launch_adj_backward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK)));
+        c->n_launches++;
+    }
+    return LPM_OK;
+}
+
 // Storage of the forward's states for the backward: the whole trajectory when it fits in
 // the limit and in free device memory (keeping 8 GiB spare), else checkpoints every CK steps.
-lpm_status adj_storage(lpm_ctx *c)
+lpm_status adj_storage(lpm_ctx *c, size_t nt_need, size_t nf_need)
 {
-    const size_t need_b = (c->traj_need + (size_t)c->n_slots_used) * sizeof(float4);
+    const size_t need_b = (nt_need + nf_need) * sizeof(float4);
     bool traj = need_b <= c->adj_store_max;
-    if (traj && (c->traj_need > c->d_traj_cap || (size_t)c->n_slots_used > c->d_fin_cap)) {
+    if (traj && (nt_need > c->d_traj_cap || nf_need > c->d_fin_cap)) {
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
         size_t fr = 0, tot = 0;
         LPM_CUDA(c, cudaMemGetInfo(&fr, &tot));
@@ -1764,8 +1939,8 @@ lpm_status adj_storage(lpm_ctx *c)
             }
             c->d_traj_cap = c->d_fin_cap = c->d_ckpt_cap = 0;
             c->adj_sig.clear();
-            const size_t nt = std::max<size_t>(1, c->traj_need);
-            const size_t nf = std::max<size_t>(1, (size_t)c->n_slots_used);
+            const size_t nt = std::max<size_t>(1, nt_need);
+            const size_t nf = std::max<size_t>(1, nf_need);
             if (cudaMalloc(&c->d_traj, nt * sizeof(float4)) == cudaSuccess &&
                 cudaMalloc(&c->d_fin, nf * sizeof(float4)) == cudaSuccess) {
                 c->d_traj_cap = nt;
@@ -1847,11 +2022,21 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
         LPM_CUDA(c, cudaMemcpy(c->d_traj_tile, tt.data(), tt.size() * sizeof(longlong2),
                                cudaMemcpyHostToDevice));
         c->traj_need = rows;
+        if (g.n_scenarios == 1) {
+            lpm_status pst = adj_plan_segments(c);
+            if (pst != LPM_OK) return pst;
+        }
         c->adj_tiles_valid = true;
     }
     if (!reuse) {
-        lpm_status sst = adj_storage(c);
+        const bool want_sorted = g.n_scenarios == 1 && c->sort_every > 0;
+        const lpm_ctx::AdjSorted &S = c->as;
+        lpm_status sst = want_sorted
+                             ? adj_storage(c, (size_t)S.off.back(), (size_t)S.foff.back())
+                             : adj_storage(c, c->traj_need, (size_t)c->n_slots_used);
         if (sst != LPM_OK) return sst;
+        c->adj_sorted = c->adj_traj && want_sorted;
+        if (c->adj_sorted && (sst = adj_sorted_buffers(c)) != LPM_OK) return sst;
     }
     const int n_ck = (int)((g.n_steps + CK - 1) / CK);
     const size_t need_ck = (size_t)n_ck * (size_t)c->n_slots_used;
@@ -1921,6 +2106,7 @@ std::vector<double> adj_signature(const lpm_ctx *c, const double *rec, int R, do
     sig.push_back(every);
     sig.push_back((double)c->params_version);
     sig.push_back(c->adj_traj ? 1.0 : 0.0);
+    sig.push_back(c->adj_sorted ? 1.0 : 0.0);
     return sig;
 }
 
@@ -1930,8 +2116,13 @@ lpm_status adj_forward(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     lpm_status st = adj_prepare(c, rec, R, bandwidth, every, A, P);
     if (st != LPM_OK) return st;
     LPM_CUDA(c, cudaMemsetAsync(c->d_rC, 0, (size_t)c->cfg.n_scenarios * R * sizeof(double), c->stream));
-    LPM_CUDA(c, launch_adj_forward(c->stream, P, A, (int)c->adj_tiles.size()));
-    c->n_launches++;
+    if (c->adj_sorted) {
+        st = adj_forward_sorted(c, P, A);
+        if (st != LPM_OK) return st;
+    } else {
+        LPM_CUDA(c, launch_adj_forward(c->stream, P, A, (int)c->adj_tiles.size()));
+        c->n_launches++;
+    }
     st = check_device_error(c);
     if (st != LPM_OK) return st;
     c->adj_sig = adj_signature(c, rec, R, bandwidth, every);
@@ -1974,8 +2165,13 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     LPM_CUDA(c, cudaMemcpyAsync(c->d_rw, dL_dC, ns * R * sizeof(double), cudaMemcpyHostToDevice,
                                 c->stream));
     LPM_CUDA(c, cudaMemsetAsync(c->d_rgrad, 0, ns * A.ng * sizeof(double), c->stream));
-    LPM_CUDA(c, launch_adj_backward(c->stream, P, A, (int)c->adj_tiles.size()));
-    c->n_launches++;
+    if (c->adj_sorted) {
+        st = adj_backward_sorted(c, P, A);
+        if (st != LPM_OK) return st;
+    } else {
+        LPM_CUDA(c, launch_adj_backward(c->stream, P, A, (int)c->adj_tiles.size()));
+        c->n_launches++;
+    }
     st = check_device_error(c);
     if (st != LPM_OK) return st;
     LPM_CUDA(c, cudaMemcpy(grad, c->d_rgrad, ns * A.ng * sizeof(double), cudaMemcpyDeviceToHost));

@@ -97,7 +97,12 @@ cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *hom
 void set_global_error(const char *msg);
 
 struct AdjParams;
+struct AdjSeg;
 cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles);
 cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles);
+cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
+                                   const AdjSeg &G, int n_blocks);
+cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
+                                    const AdjSeg &G, int n_blocks);
 
 }  // namespace lpm

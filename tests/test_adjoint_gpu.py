@@ -198,28 +198,45 @@ def test_batched_inversion_reduces_misfit_and_approaches_the_hidden_source():
 
 
 def test_trajectory_and_checkpoint_storage_agree():
-    """The backward that reads the stored trajectory and the one that recomputes 64-step
-    segments from checkpoints take the same paths and events: receptors and gradients agree
-    to the order of the FP64 sums, for one scenario (deposition, exits) and a batch of
-    candidates; a limit below the trajectory's size selects checkpoints."""
+    """The three backward forms take the same paths and events, so receptors and gradients
+    agree to the order of the FP64 sums: the trajectory re-sorted by weather cell every 64
+    steps (one scenario, sorting on), the trajectory in release order (sorting off, or a
+    batch of candidates), and 64-step checkpoints with recomputation (a limit below the
+    trajectory's size). One scenario with deposition and exits, and a batch of three."""
     from paper_0912_3223_gb300 import Sim, lpm
     cfg, rec = _realistic(n=5000, steps=400)
     cand, _, _ = li.make_cfg4(n_candidates=3, n_per=3000, n_steps=300, n_obs=1000)
     for c, nq in [(cfg, 24), (cand, 24)]:
         w = np.linspace(-1.0, 1.0, c.n_scenarios * rec.shape[0]).reshape(c.n_scenarios, -1)
         out = {}
-        for limit in (1 << 37, 0, 1024):
+        for form, limit, sort in [("trajectory", 1 << 37, 60), ("release order", 1 << 37, 0),
+                                  ("checkpoints", 0, 60), ("checkpoints (limit)", 1024, 60)]:
             with Sim(c) as sim:
+                lpm.lpm_set_sort(sim.ctx, sort)
                 lpm.lpm_set_adjoint_storage(sim.ctx, limit)
                 C = lpm.lpm_receptors(sim.ctx, c.n_scenarios, rec, SIGMA, 18)
                 g = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, w, nq)
+                g2 = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, 2.0 * w, nq)   # held forward reused
                 traj, nbytes = lpm.lpm_adjoint_storage(sim.ctx)
             assert traj == (limit == 1 << 37)
             assert nbytes > 0
-            out[limit] = (C, g)
-        C0, g0 = out[1 << 37]
+            np.testing.assert_allclose(g2, 2.0 * g, rtol=1e-12, atol=1e-15 * np.abs(g).max())
+            out[form] = (C, g)
+        # same order of the per-particle FP32 sums: agree to the order of the FP64 sums
+        C0, g0 = out["release order"]
         assert np.abs(g0).max() > 0
-        for limit in (0, 1024):
-            C1, g1 = out[limit]
-            np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max())
-            np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
+        for form in ("checkpoints", "checkpoints (limit)"):
+            C1, g1 = out[form]
+            np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max(),
+                                       err_msg=form)
+            np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max(),
+                                       err_msg=form)
+        # the sorted form carries dL/dX between segments exactly (FP32 values) but restarts
+        # each particle's FP32 parameter sums every 64 steps: source partials to the order
+        # of the FP64 sums, parameter partials to FP32 rounding of the per-particle sums
+        C1, g1 = out["trajectory"]
+        np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max())
+        np.testing.assert_allclose(g1[:, :3], g0[:, :3], rtol=1e-9,
+                                   atol=1e-12 * np.abs(g0[:, :3]).max())
+        np.testing.assert_allclose(g1[:, 3:], g0[:, 3:], rtol=0,
+                                   atol=2e-5 * np.abs(g0[:, 3:]).max())
