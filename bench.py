@@ -573,7 +573,7 @@ def run_gpu(args):
     h2d = pinned_uvwk.numel() * 4 + pinned_rain.numel()
     d2h = conc.nbytes + 2 * cfg.cy * cfg.cx * 8 + 8 * 8
     e2e_t, e2e_p = 0.0, 0
-    for _ in range(args.steps):
+    for i in range(max(1, args.warmup) + args.steps):   # warm-up passes first, untimed
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for t in range(cfg.n_met_t):
@@ -582,6 +582,8 @@ def run_gpu(args):
         sim.concentration(out=conc)
         dry, wet = sim.deposition()
         b = sim.budget()
+        if i < max(1, args.warmup):
+            continue
         e2e_t += time.perf_counter() - t0
         _, _, ctr, _ = sim.fixed_state()
         e2e_p += int(ctr[4])

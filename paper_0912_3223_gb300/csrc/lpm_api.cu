@@ -143,6 +143,8 @@ struct lpm_ctx {
     short *d_qi = nullptr;                  // emission-series index per release step
     float4 *d_ckpt = nullptr;
     size_t d_ckpt_cap = 0;
+    double *d_conv = nullptr;               // read-back of a grid converted on the device
+    size_t d_conv_cap = 0;
     // trajectory storage (the default when it fits): rows of every tile from its first
     // release step on, and the state after each particle's last step (float4 elements)
     float4 *d_traj = nullptr, *d_fin = nullptr;
@@ -767,7 +769,7 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
                     c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair,
                     c->d_sp_conc, c->d_sp_dep, c->d_w_home, c->d_w_sorted[0],
-                    c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile};
+                    c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile, c->d_conv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {
@@ -1319,6 +1321,28 @@ lpm_status lpm_sync(lpm_ctx *c)
     return check_device_error(c);
 }
 
+namespace {
+// Converts n 64-bit fixed-point sums to doubles (x f) on the device and copies them to the
+// host; the conversion and the copy run on the context stream, then it is synchronised.
+lpm_status read_fixed(lpm_ctx *c, const unsigned long long *src, size_t n, double f, double *out)
+{
+    if (n > c->d_conv_cap) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->d_conv) cudaFree(c->d_conv);
+        c->d_conv = nullptr;
+        c->d_conv_cap = 0;
+        LPM_CUDA(c, cudaMalloc(&c->d_conv, n * sizeof(double)));
+        c->d_conv_cap = n;
+    }
+    LPM_CUDA(c, launch_fixed_to_double(c->stream, src, c->d_conv, (long long)n, f));
+    c->n_launches++;
+    LPM_CUDA(c, cudaMemcpyAsync(out, c->d_conv, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LPM_OK;
+}
+}  // namespace
+
 lpm_status lpm_concentration(lpm_ctx *c, int scenario, double *out, size_t n_out)
 {
     if (!c) return LPM_E_INVALID;
@@ -1327,17 +1351,9 @@ lpm_status lpm_concentration(lpm_ctx *c, int scenario, double *out, size_t n_out
         return fail(c, LPM_E_INVALID, "out must hold cz*cy*cx = %zu doubles", c->ncell());
     lpm_status st = check_device_error(c);
     if (st != LPM_OK) return st;
-    // the 64-bit sums land in the caller's buffer and are converted in place (same size)
-    LPM_CUDA(c, cudaMemcpy(out, c->d_conc + (size_t)scenario * c->ncell(),
-                           c->ncell() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     const lpm_config &g = c->cfg;
     const double f = std::ldexp(1.0, -c->scen[(size_t)scenario].shift) / (g.cdx * g.cdy * g.cdz);
-    for (size_t i = 0; i < c->ncell(); ++i) {
-        unsigned long long v;
-        std::memcpy(&v, out + i, sizeof v);
-        out[i] = (double)v * f;
-    }
-    return LPM_OK;
+    return read_fixed(c, c->d_conc + (size_t)scenario * c->ncell(), c->ncell(), f, out);
 }
 
 lpm_status lpm_deposition(lpm_ctx *c, int scenario, double *dry, double *wet, size_t n_out)
@@ -1348,14 +1364,10 @@ lpm_status lpm_deposition(lpm_ctx *c, int scenario, double *dry, double *wet, si
     if (n_out != plane) return fail(c, LPM_E_INVALID, "n_out must be cy*cx = %zu", plane);
     lpm_status st = check_device_error(c);
     if (st != LPM_OK) return st;
-    std::vector<unsigned long long> h(c->ndep());
-    LPM_CUDA(c, cudaMemcpy(h.data(), c->d_dep + (size_t)scenario * c->ndep(),
-                           h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     const double f = std::ldexp(1.0, -c->scen[(size_t)scenario].shift) / (c->cfg.cdx * c->cfg.cdy);
-    for (size_t i = 0; i < plane; ++i) {
-        if (dry) dry[i] = (double)h[i] * f;
-        if (wet) wet[i] = (double)h[plane + i] * f;
-    }
+    const unsigned long long *src = c->d_dep + (size_t)scenario * c->ndep();
+    if (dry && (st = read_fixed(c, src, plane, f, dry)) != LPM_OK) return st;
+    if (wet && (st = read_fixed(c, src + plane, plane, f, wet)) != LPM_OK) return st;
     return LPM_OK;
 }
 

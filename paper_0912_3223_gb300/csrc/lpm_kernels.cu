@@ -186,6 +186,27 @@ int advance_occupancy(int block, int ppt, int occ, bool mixed, bool ext)
     return 0;
 }
 
+// Read-back of a 64-bit fixed-point grid as physical values: out[i] = in[i] * f (the
+// conversion rounds to nearest, as on the host).
+__global__ void fixed_to_double_kernel(const unsigned long long *__restrict__ in,
+                                       double *__restrict__ out, long long n, double f)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = __ull2double_rn(in[i]) * f;
+}
+
+cudaError_t launch_fixed_to_double(cudaStream_t s, const unsigned long long *in, double *out,
+                                   long long n, double f)
+{
+    if (n <= 0) return cudaSuccess;
+    const int block = 256;
+    long long blocks = (n + block - 1) / block;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    fixed_to_double_kernel<<<(unsigned)blocks, block, 0, s>>>(in, out, n, f);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
                         const float *kb, float4 *pair, float2 *khpair, int nx, int ny, int nz)
 {

@@ -94,6 +94,8 @@ cudaError_t launch_budget(cudaStream_t s, const StepParams &P, const float4 *hom
                           const unsigned int *pidx, const unsigned int *live, long long a_bound,
                           int k_now);
 
+cudaError_t launch_fixed_to_double(cudaStream_t s, const unsigned long long *in, double *out,
+                                   long long n, double f);
 void set_global_error(const char *msg);
 
 struct AdjParams;
