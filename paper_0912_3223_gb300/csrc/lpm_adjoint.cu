@@ -111,8 +111,9 @@ adj_forward_kernel(const StepParams P, const AdjParams A)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
-    __shared__ float4 s_rec[MAX_REC];
-    __shared__ double s_C[MAX_REC];
+    extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_forward
+    float4 *s_rec = s_dyn;                        // [R]
+    double *s_C = reinterpret_cast<double *>(s_rec + A.R);    // [R]
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
         s_rec[r] = A.rec[r];
@@ -286,7 +287,7 @@ __device__ __forceinline__ void load_receptors(const AdjParams &A, const Tile &t
         s_rec[r] = A.rec[r];
         s_w[r] = (float)(A.w[(long long)tile.scen * A.R + r] * (double)A.inv_ns);
     }
-    for (int i = threadIdx.x; i < MAX_NQ; i += ADJ_BLOCK) s_gq[i] = 0.0;
+    for (int i = threadIdx.x; i < A.nq; i += ADJ_BLOCK) s_gq[i] = 0.0;
     if (threadIdx.x < 6) s_g[threadIdx.x] = 0.0;
     __syncthreads();
 }
@@ -299,10 +300,11 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
-    __shared__ float4 s_rec[MAX_REC];
-    __shared__ float s_w[MAX_REC];
-    __shared__ double s_g[6];
-    __shared__ double s_gq[MAX_NQ];
+    extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
+    float4 *s_rec = s_dyn;                        // [R]
+    double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
+    double *s_gq = s_g + 6;                       // [nq]
+    float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     const Tile tile = A.tiles[blockIdx.x];
     load_receptors(A, tile, s_rec, s_w, s_g, s_gq);
@@ -375,10 +377,11 @@ adj_backward_traj_kernel(const StepParams P, const AdjParams A)
 {
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
-    __shared__ float4 s_rec[MAX_REC];
-    __shared__ float s_w[MAX_REC];
-    __shared__ double s_g[6];
-    __shared__ double s_gq[MAX_NQ];
+    extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
+    float4 *s_rec = s_dyn;                        // [R]
+    double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
+    double *s_gq = s_g + 6;                       // [nq]
+    float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     const Tile tile = A.tiles[blockIdx.x];
     load_receptors(A, tile, s_rec, s_w, s_g, s_gq);
@@ -421,6 +424,19 @@ adj_backward_traj_kernel(const StepParams P, const AdjParams A)
     reduce_gradient(A, tile, J, valid, qidx, s_g, s_gq);
 }
 
+// Dynamic shared memory of the kernels, sized by the receptors and the emission series
+// (small arrays keep the shared-memory carve-out small and leave the rest of the SM's
+// unified L1 to the weather gathers).
+static size_t adj_smem_forward(const AdjParams &A)
+{
+    return (size_t)A.R * (sizeof(float4) + sizeof(double));
+}
+
+static size_t adj_smem_backward(const AdjParams &A)
+{
+    return (size_t)A.R * (sizeof(float4) + sizeof(float)) + (size_t)(6 + A.nq) * sizeof(double);
+}
+
 // ---------------------------------------------------------------------------------
 // Sorted trajectory form (one scenario): one launch per CK-step segment over the
 // particles alive at its start in weather-cell order, then its releases; between
@@ -450,8 +466,9 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
-    __shared__ float4 s_rec[MAX_REC];
-    __shared__ double s_C[MAX_REC];
+    extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_forward
+    float4 *s_rec = s_dyn;                        // [R]
+    double *s_C = reinterpret_cast<double *>(s_rec + A.R);    // [R]
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
         s_rec[r] = A.rec[r];
@@ -515,10 +532,11 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
     __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
-    __shared__ float4 s_rec[MAX_REC];
-    __shared__ float s_w[MAX_REC];
-    __shared__ double s_g[6];
-    __shared__ double s_gq[MAX_NQ];
+    extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
+    float4 *s_rec = s_dyn;                        // [R]
+    double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
+    double *s_gq = s_g + 6;                       // [nq]
+    float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
     const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
     const Tile tile0{0, 0, 0};
     load_receptors(A, tile0, s_rec, s_w, s_g, s_gq);
@@ -573,7 +591,7 @@ cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const Ad
                                    const AdjSeg &G, int n_blocks)
 {
     if (n_blocks <= 0) return cudaSuccess;
-    adj_forward_seg_kernel<<<n_blocks, ADJ_BLOCK, 0, s>>>(P, A, G);
+    adj_forward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A, G);
     return cudaGetLastError();
 }
 
@@ -581,7 +599,7 @@ cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const A
                                     const AdjSeg &G, int n_blocks)
 {
     if (n_blocks <= 0) return cudaSuccess;
-    adj_backward_seg_kernel<<<n_blocks, ADJ_BLOCK, 0, s>>>(P, A, G);
+    adj_backward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A, G);
     return cudaGetLastError();
 }
 
@@ -589,9 +607,9 @@ cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjPar
 {
     if (n_tiles <= 0) return cudaSuccess;
     if (A.traj)
-        adj_forward_kernel<true><<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+        adj_forward_kernel<true><<<n_tiles, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A);
     else
-        adj_forward_kernel<false><<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+        adj_forward_kernel<false><<<n_tiles, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A);
     return cudaGetLastError();
 }
 
@@ -599,9 +617,9 @@ cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjPa
 {
     if (n_tiles <= 0) return cudaSuccess;
     if (A.traj)
-        adj_backward_traj_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+        adj_backward_traj_kernel<<<n_tiles, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A);
     else
-        adj_backward_kernel<<<n_tiles, ADJ_BLOCK, 0, s>>>(P, A);
+        adj_backward_kernel<<<n_tiles, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A);
     return cudaGetLastError();
 }
 
