@@ -138,8 +138,8 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
         kz_eq3(col.x, col.y, col.z, P.kz_min, z, m.kz, m.dkz);
     } else {
         m.kz = fmaxf(r.w, 0.0f);
-        const bool inside = z >= L.z[0] && z <= L.z[P.nz - 1];
-        m.dkz = inside ? (y1.w - y0.w) * L.inv[k] : 0.0f;
+        const bool inside = z >= L.z_lo && z <= L.z_hi;
+        m.dkz = inside ? (y1.w - y0.w) * L.zi[k].y : 0.0f;
     }
     if (khp) {
         float e[8];
@@ -352,12 +352,12 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
                int k1, int do_bin)
 {
-    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     __shared__ unsigned long long s_acc[BLOCK];
     __shared__ int s_tile;
     __shared__ unsigned long long s_steps;
-    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    const Levels LV = load_levels(P, s_zi, s_lut);
     unsigned long long *s_warp = s_acc + (threadIdx.x & ~31);
     const long long n_cells = (long long)P.cx * P.cy * P.cz;
     constexpr int TILE = BLOCK * PPT;

@@ -727,9 +727,9 @@ lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
     CREATE_CUDA(cudaMemsetAsync(c->d_ctr, 0, ns * N_COUNTERS * sizeof(unsigned long long), c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
     {
-        // vertical lookup table: bins of at most a third of the smallest level spacing (the
-        // kernel then corrects the tabled cell by at most one), in the FP32 arithmetic the
-        // kernel uses to pick a bin
+        // vertical lookup table: bins of at most a third of the smallest level spacing, each
+        // holding the cell 0.05 bin below its lower edge (the kernel then corrects it by at
+        // most one with one comparison), in the FP32 arithmetic the kernel uses to pick a bin
         std::vector<float> zf(cfg->nz);
         for (int k = 0; k < cfg->nz; ++k) zf[k] = (float)cfg->z_levels[k];
         double min_sp = 1e300;
@@ -742,7 +742,7 @@ lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
             c->lut_inv_h = (float)((c->n_lut - 1) / span);
             std::vector<unsigned char> lut((size_t)c->n_lut);
             for (int b = 0; b < c->n_lut; ++b) {
-                const double zb = (double)zf[0] + b / (double)c->lut_inv_h;
+                const double zb = (double)zf[0] + (b - 0.05) / (double)c->lut_inv_h;
                 int k = 0;
                 for (int m = 0; m < cfg->nz; ++m)
                     if ((double)zf[m] <= zb) k = m;

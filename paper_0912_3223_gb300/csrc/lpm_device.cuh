@@ -246,61 +246,63 @@ __device__ __forceinline__ void axis(float coord, float c0, float inv_d, int n, 
     a = fminf(fmaxf(f - (float)ii, 0.0f), 1.0f);
 }
 
-// Vertical cell: last level <= z, clamped to [0, nz-2]. With the lookup table (bins no
-// wider than half the smallest level spacing) one bin holds at most one level boundary,
-// so one step down and two steps up settle the exact answer; without it, bisection.
+// Vertical cell: last level <= z, clamped to [0, nz-2]. With the lookup table, bin b of
+// width h (at most a third of the smallest level spacing) holds the cell at the point
+// 0.05 h below its lower edge; FP32 bin arithmetic errs by far less than that, so the span
+// from that point to the bin's upper edge holds at most one level boundary and one
+// comparison with the next level settles the exact cell. Without it, bisection.
 struct Levels {
-    const float *z;                  // shared-memory copy of z_levels
-    const float *inv;                // 1 / (z[k+1] - z[k])
+    const float2 *zi;                // shared memory: (z_levels[k], 1 / (z[k+1] - z[k]))
     const unsigned char *lut;        // shared-memory copy of the table, or nullptr
     int nz, n_lut;
-    float z0, inv_h;
+    float z0, inv_h;                 // table origin and 1 / bin width
+    float z_lo, z_hi;                // lowest and highest level
 };
 
-// Vertical cell k (last level <= z, clamped to [0, nz-2]) and fraction c in [0, 1]. The
-// table gives the cell at the lower edge of z's uniform bin (bins of at most a third of
-// the smallest level spacing); a level inside the bin, or bin arithmetic that rounded
-// across an edge, moves it by one.
+// Vertical cell k (last level <= z, clamped to [0, nz-2]) and fraction c in [0, 1].
 __device__ __forceinline__ void level(const Levels &L, float z, int &k, float &c)
 {
     int kk;
+    float2 zk;
     if (L.lut) {
         int b = (int)((z - L.z0) * L.inv_h);
         b = min(max(b, 0), L.n_lut - 1);
-        kk = L.lut[b];
-        if (kk > 0 && z < L.z[kk]) --kk;
-        if (kk < L.nz - 2 && z >= L.z[kk + 1]) ++kk;
-        if (kk < L.nz - 2 && z >= L.z[kk + 1]) ++kk;
+        const int k0 = L.lut[b];
+        const float2 lo = L.zi[k0], hi = L.zi[k0 + 1];
+        const bool up = k0 < L.nz - 2 && z >= hi.x;
+        kk = up ? k0 + 1 : k0;
+        zk = up ? hi : lo;
     } else {
         int lo = 0, hi = L.nz - 1;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (L.z[mid] <= z) lo = mid;
+            if (L.zi[mid].x <= z) lo = mid;
             else hi = mid;
         }
         kk = lo;
+        zk = L.zi[kk];
     }
     k = kk;
-    c = fminf(fmaxf((z - L.z[kk]) * L.inv[kk], 0.0f), 1.0f);
+    c = fminf(fmaxf((z - zk.x) * zk.y, 0.0f), 1.0f);
 }
 
 // Fills the shared-memory level tables (call by the whole block, then __syncthreads()).
-__device__ __forceinline__ Levels load_levels(const StepParams &P, float *s_z, float *s_inv,
+__device__ __forceinline__ Levels load_levels(const StepParams &P, float2 *s_zi,
                                               unsigned char *s_lut)
 {
-    for (int i = threadIdx.x; i < P.nz; i += blockDim.x) s_z[i] = P.zlev[i];
-    for (int i = threadIdx.x; i < P.nz - 1; i += blockDim.x)
-        s_inv[i] = 1.0f / (P.zlev[i + 1] - P.zlev[i]);
+    for (int i = threadIdx.x; i < P.nz; i += blockDim.x)
+        s_zi[i] = make_float2(P.zlev[i], i + 1 < P.nz ? 1.0f / (P.zlev[i + 1] - P.zlev[i]) : 0.0f);
     if (P.zlut)
         for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.zlut[i];
     Levels L;
-    L.z = s_z;
-    L.inv = s_inv;
+    L.zi = s_zi;
     L.lut = P.zlut ? s_lut : nullptr;
     L.nz = P.nz;
     L.n_lut = P.n_lut;
     L.z0 = P.lut_z0;
     L.inv_h = P.lut_inv_h;
+    L.z_lo = P.zlev[0];
+    L.z_hi = P.zlev[P.nz - 1];
     return L;
 }
 

@@ -56,9 +56,9 @@ __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                                  unsigned int *__restrict__ keys, unsigned int *__restrict__ hist,
                                  unsigned int dead_key)
 {
-    __shared__ float s_z[MAX_LEVELS], s_zinv[MAX_LEVELS];
+    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
-    const Levels LV = load_levels(P, s_z, s_zinv, s_lut);
+    const Levels LV = load_levels(P, s_zi, s_lut);
     __syncthreads();
     const long long n = meta[1];
     const unsigned int live_old = meta[2];
