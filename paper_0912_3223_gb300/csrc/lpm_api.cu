@@ -243,6 +243,8 @@ lpm_status validate(const lpm_config *c)
         return fail(nullptr, LPM_E_INVALID, "nz=%d exceeds %d levels", c->nz, MAX_LEVELS);
     if ((double)c->nx * c->ny * c->nz > 1073741824.0)
         return fail(nullptr, LPM_E_INVALID, "met grid exceeds 2^30 nodes");
+    if (sort_key_range(c->nx, c->ny, c->nz) >= 0xffffffffLL)
+        return fail(nullptr, LPM_E_INVALID, "met grid too large for 32-bit sort keys");
     if (!c->z_levels) return fail(nullptr, LPM_E_INVALID, "z_levels is NULL");
     for (int k = 0; k < c->nz; ++k) {
         if (!is_finite(c->z_levels[k])) return fail(nullptr, LPM_E_INVALID, "z_levels not finite");
@@ -558,7 +560,7 @@ lpm_status ensure_sort_buffers(lpm_ctx *c, size_t keys_need)
 {
     // allocate whatever is still missing (an earlier call may have stopped at a failure)
     const size_t n = (size_t)c->cfg.max_particles;
-    const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
+    const size_t nb = (size_t)sort_key_range(c->cfg.nx, c->cfg.ny, c->cfg.nz) + 1;
     const size_t ntiles = (nb + 1023) / 1024;
     auto need = [&](auto *&p, size_t bytes) -> cudaError_t {
         if (p) return cudaSuccess;
@@ -1836,7 +1838,7 @@ lpm_status adj_sorted_buffers(lpm_ctx *c)
     lpm_ctx::AdjSorted &S = c->as;
     const size_t ns = std::max<size_t>(1, (size_t)c->n_slots_used);
     const size_t nseg = S.tiles_a.size();
-    const size_t nb = (size_t)c->cfg.nx * c->cfg.ny * c->cfg.nz + 1;
+    const size_t nb = (size_t)sort_key_range(c->cfg.nx, c->cfg.ny, c->cfg.nz) + 1;
     auto need = [&](auto *&p, size_t bytes) -> cudaError_t {
         return p ? cudaSuccess : cudaMalloc(&p, bytes);
     };

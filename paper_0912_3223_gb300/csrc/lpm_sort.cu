@@ -49,7 +49,19 @@ __device__ __forceinline__ bool sort_input(const SortSource &S, long long i, uns
     return true;
 }
 
-// Key = weather cell (in the order of the paired weather records) of an active particle;
+// Key of cell (ix, jy, kz): its tile of columns, then its place in the tile.
+__device__ __forceinline__ unsigned int cell_key(const StepParams &P, int ix, int jy, int kz)
+{
+    constexpr int TB = SORT_TILE_BITS;
+    constexpr int T = 1 << TB;
+    const unsigned int ntx = (unsigned int)((P.nx + T - 1) >> TB);
+    const unsigned int nty = (unsigned int)((P.ny + T - 1) >> TB);
+    const unsigned int tile = ((unsigned int)kz * nty + (unsigned int)(jy >> TB)) * ntx +
+                              (unsigned int)(ix >> TB);
+    return (tile << (2 * TB)) | ((unsigned int)(jy & (T - 1)) << TB) | (unsigned int)(ix & (T - 1));
+}
+
+// Key = weather cell (cell_key order) of an active particle;
 // dead_key for the rest.
 __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                                  const unsigned int *__restrict__ meta, long long n_max,
@@ -81,7 +93,7 @@ __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                     axis(s.x, P.x0, P.inv_dx, P.nx, ix, a);
                     axis(s.y, P.y0, P.inv_dy, P.ny, jy, b);
                     level(LV, s.z, kz, c);
-                    key = (unsigned int)col_node(P, ix, jy, kz);
+                    key = cell_key(P, ix, jy, kz);
                 } else {
                     key = dead_key;
                 }
@@ -271,7 +283,7 @@ cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &i
                         const SortBuffers &B)
 {
     // keys 0..dead_key-1 are cells, dead_key the dead particles
-    const unsigned int dead_key = (unsigned int)((long long)P.nx * P.ny * P.nz);
+    const unsigned int dead_key = (unsigned int)sort_key_range(P.nx, P.ny, P.nz);
     const long long nb = (long long)dead_key + 1;
     cudaError_t e = cudaMemsetAsync(B.hist, 0, nb * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
