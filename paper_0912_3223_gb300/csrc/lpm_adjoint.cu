@@ -587,10 +587,28 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     reduce_gradient(A, tile0, J, valid, qidx, s_g, s_gq);
 }
 
+// The kernels need a few KB of shared memory per block: ask for the smallest carve-out so
+// the rest of the unified L1 serves the weather gathers (once per process).
+static void adj_prefer_l1()
+{
+    static bool done = false;
+    if (done) return;
+    done = true;
+    const int pct = 25;
+    cudaFuncSetAttribute(adj_forward_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_forward_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_traj_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_forward_seg_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_seg_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    (void)cudaGetLastError();
+}
+
 cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
                                    const AdjSeg &G, int n_blocks)
 {
     if (n_blocks <= 0) return cudaSuccess;
+    adj_prefer_l1();
     adj_forward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A, G);
     return cudaGetLastError();
 }
@@ -599,6 +617,7 @@ cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const A
                                     const AdjSeg &G, int n_blocks)
 {
     if (n_blocks <= 0) return cudaSuccess;
+    adj_prefer_l1();
     adj_backward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A, G);
     return cudaGetLastError();
 }
@@ -606,6 +625,7 @@ cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const A
 cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles)
 {
     if (n_tiles <= 0) return cudaSuccess;
+    adj_prefer_l1();
     if (A.traj)
         adj_forward_kernel<true><<<n_tiles, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A);
     else
@@ -616,6 +636,7 @@ cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjPar
 cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles)
 {
     if (n_tiles <= 0) return cudaSuccess;
+    adj_prefer_l1();
     if (A.traj)
         adj_backward_traj_kernel<<<n_tiles, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A);
     else
