@@ -58,14 +58,16 @@ struct SortBuffers {
     float *w_out;                 // Langevin w' of the sorted particles, or nullptr
 };
 
-// Sort keys: cells grouped in tiles of 2^SORT_TILE_BITS x 2^SORT_TILE_BITS columns, tile
-// by tile along x, then y, then level; keys run over [0, sort_key_range).
+// Sort keys: cells grouped in tiles of 2^SORT_TILE_BITS x 2^SORT_TILE_BITS columns by
+// 2^SORT_TILE_ZBITS levels, tile by tile along x, then y, then z; keys run over
+// [0, sort_key_range).
 constexpr int SORT_TILE_BITS = 2;
+constexpr int SORT_TILE_ZBITS = 2;
 
 __host__ __device__ inline long long sort_key_range(int nx, int ny, int nz)
 {
-    const long long t = 1LL << SORT_TILE_BITS;
-    return (long long)nz * ((ny + t - 1) / t) * ((nx + t - 1) / t) * t * t;
+    const long long t = 1LL << SORT_TILE_BITS, tz = 1LL << SORT_TILE_ZBITS;
+    return ((nz + tz - 1) / tz) * tz * ((ny + t - 1) / t) * ((nx + t - 1) / t) * t * t;
 }
 
 constexpr unsigned int SLOT_HOME = 0xffffffffu;   // slot_of: the particle is at its home slot

@@ -49,16 +49,17 @@ __device__ __forceinline__ bool sort_input(const SortSource &S, long long i, uns
     return true;
 }
 
-// Key of cell (ix, jy, kz): its tile of columns, then its place in the tile.
+// Key of cell (ix, jy, kz): its tile, then its place in the tile.
 __device__ __forceinline__ unsigned int cell_key(const StepParams &P, int ix, int jy, int kz)
 {
-    constexpr int TB = SORT_TILE_BITS;
-    constexpr int T = 1 << TB;
+    constexpr int TB = SORT_TILE_BITS, TZ = SORT_TILE_ZBITS;
+    constexpr int T = 1 << TB, TZN = 1 << TZ;
     const unsigned int ntx = (unsigned int)((P.nx + T - 1) >> TB);
     const unsigned int nty = (unsigned int)((P.ny + T - 1) >> TB);
-    const unsigned int tile = ((unsigned int)kz * nty + (unsigned int)(jy >> TB)) * ntx +
+    const unsigned int tile = ((unsigned int)(kz >> TZ) * nty + (unsigned int)(jy >> TB)) * ntx +
                               (unsigned int)(ix >> TB);
-    return (tile << (2 * TB)) | ((unsigned int)(jy & (T - 1)) << TB) | (unsigned int)(ix & (T - 1));
+    return (tile << (2 * TB + TZ)) | ((unsigned int)(kz & (TZN - 1)) << (2 * TB)) |
+           ((unsigned int)(jy & (T - 1)) << TB) | (unsigned int)(ix & (T - 1));
 }
 
 // Key = weather cell (cell_key order) of an active particle;
