@@ -102,6 +102,19 @@ __device__ __forceinline__ float4 pack_state(float x, float y, float z, uint32_t
     return make_float4(x, y, z, __uint_as_float((st << TAG_SHIFT) | ((uint32_t)sp & TAG_STEP)));
 }
 
+// Receptors a particle at (x, y) can be within the cut-off distance of: entries [lo, hi) of
+// the bin lists (empty outside the bins).
+__device__ __forceinline__ void receptors_near(const AdjParams &A, float x, float y, int &lo,
+                                               int &hi)
+{
+    lo = hi = 0;
+    const float fx = (x - A.rbx0) * A.rinv_bin, fy = (y - A.rby0) * A.rinv_bin;
+    if (!(fx >= 0.0f && fy >= 0.0f && fx < (float)A.rnbx && fy < (float)A.rnby)) return;
+    const int b = (int)fy * A.rnbx + (int)fx;
+    lo = __ldg(A.rbin_off + b);
+    hi = __ldg(A.rbin_off + b + 1);
+}
+
 // ---------------------------------------------------------------------------------
 // Forward: receptor concentrations, and checkpoints or the whole trajectory.
 // ---------------------------------------------------------------------------------
@@ -160,7 +173,10 @@ adj_forward_kernel(const StepParams P, const AdjParams A)
             }
             if ((k + 1) % A.every == 0) {
                 const float m = m0 * expf(-P.lambda * (float)(k + 1 - sp) * P.dt) * A.inv_ns;
-                for (int r = 0; r < A.R; ++r) {
+                int lo, hi;
+                receptors_near(A, x, y, lo, hi);
+                for (int t = lo; t < hi; ++t) {
+                    const int r = __ldg(A.rbin_idx + t);
                     const float4 q = s_rec[r];
                     const float dx = x - q.x, dy = y - q.y, dz = z - q.z, dzi = z + q.z;
                     const float h2 = dx * dx + dy * dy;
@@ -201,7 +217,10 @@ __device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParam
     if (sample) {
         const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
         const float m = m0 * decay;
-        for (int r = 0; r < A.R; ++r) {
+        int lo, hi;
+        receptors_near(A, Xa.x, Xa.y, lo, hi);
+        for (int t = lo; t < hi; ++t) {
+            const int r = __ldg(A.rbin_idx + t);
             const float4 q = s_rec[r];
             const float dx = Xa.x - q.x, dy = Xa.y - q.y, dz = Xa.z - q.z, dzi = Xa.z + q.z;
             const float h2 = dx * dx + dy * dy;
@@ -502,7 +521,10 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
             if (st != ST_ACTIVE) break;
             if ((k + 1) % A.every == 0) {
                 const float m = m0 * expf(-P.lambda * (float)(k + 1 - sp) * P.dt) * A.inv_ns;
-                for (int r = 0; r < A.R; ++r) {
+                int lo, hi;
+                receptors_near(A, x, y, lo, hi);
+                for (int t = lo; t < hi; ++t) {
+                    const int r = __ldg(A.rbin_idx + t);
                     const float4 q = s_rec[r];
                     const float dx = x - q.x, dy = y - q.y, dz = z - q.z, dzi = z + q.z;
                     const float h2 = dx * dx + dy * dy;

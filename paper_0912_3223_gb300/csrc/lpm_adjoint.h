@@ -13,6 +13,13 @@ constexpr int MAX_NQ = 64;
 struct AdjParams {
     const float4 *rec;                // [R] receptor (x, y, z, 0)
     int R;
+    // receptors by horizontal bin: rnbx x rnby bins of width 1 / rinv_bin from (rbx0, rby0);
+    // bin b lists in rbin_idx[rbin_off[b], rbin_off[b+1]) the receptors that a particle in it
+    // can be within the cut-off distance of, in increasing order (none outside the bins)
+    const int *rbin_off;
+    const unsigned char *rbin_idx;
+    float rbx0, rby0, rinv_bin;
+    int rnbx, rnby;
     float inv2s2;                     // 1 / (2 sigma^2)
     float norm;                       // (2 pi sigma^2)^(-3/2)
     float inv_s2;                     // 1 / sigma^2

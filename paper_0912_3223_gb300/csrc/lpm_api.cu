@@ -170,6 +170,9 @@ struct lpm_ctx {
     } as;
     bool adj_sorted = false;                    // the held forward used the sorted form
     float4 *d_rec = nullptr;
+    int *d_rbin_off = nullptr;              // receptor bins (AdjParams)
+    unsigned char *d_rbin_idx = nullptr;
+    size_t d_rbin_off_cap = 0, d_rbin_idx_cap = 0;
     double *d_rC = nullptr, *d_rw = nullptr, *d_rgrad = nullptr;
     size_t d_rbuf_cap = 0;
     Tile *d_adj_tiles = nullptr;
@@ -771,7 +774,8 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
                     c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair,
                     c->d_sp_conc, c->d_sp_dep, c->d_w_home, c->d_w_sorted[0],
-                    c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile, c->d_conv};
+                    c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile, c->d_conv,
+                    c->d_rbin_off, c->d_rbin_idx};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {
@@ -2081,10 +2085,71 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
             return fail(c, LPM_E_INVALID, "receptor %d not finite", r);
         hr[(size_t)r] = make_float4((float)rec[3 * r], (float)rec[3 * r + 1], (float)rec[3 * r + 2], 0.f);
     }
+    // receptor bins: the receptors' box widened by the cut-off (6 bandwidths) and a margin
+    // that covers FP32 rounding of positions and bin arithmetic; bins of about the cut-off;
+    // bin b lists, in increasing order, every receptor within cut-off + margin of it
+    const double cut = 6.0 * bandwidth, margin = 1.0 + 1e-3 * cut;
+    double rx0 = 1e300, rx1 = -1e300, ry0 = 1e300, ry1 = -1e300;
+    for (const float4 &q : hr) {
+        rx0 = std::min(rx0, (double)q.x); rx1 = std::max(rx1, (double)q.x);
+        ry0 = std::min(ry0, (double)q.y); ry1 = std::max(ry1, (double)q.y);
+    }
+    const float bx0 = (float)(rx0 - cut - 2.0 * margin), by0 = (float)(ry0 - cut - 2.0 * margin);
+    const double wx = rx1 + cut + 2.0 * margin - (double)bx0, wy = ry1 + cut + 2.0 * margin - (double)by0;
+    double bin = cut;
+    int nbx = std::max(1, (int)std::ceil(wx / bin)), nby = std::max(1, (int)std::ceil(wy / bin));
+    while ((long long)nbx * nby > 4096) {
+        bin *= 1.5;
+        nbx = std::max(1, (int)std::ceil(wx / bin));
+        nby = std::max(1, (int)std::ceil(wy / bin));
+    }
+    const float inv_bin = (float)(1.0 / bin);
+    const double be = 1.0 / (double)inv_bin;          // the width the kernel's arithmetic uses
+    nbx = std::max(1, (int)std::ceil(wx / be));
+    nby = std::max(1, (int)std::ceil(wy / be));
+    std::vector<int> boff((size_t)nbx * nby + 1, 0);
+    std::vector<unsigned char> bidx;
+    const double reach2 = (cut + margin) * (cut + margin);
+    for (int by = 0; by < nby; ++by)
+        for (int bxi = 0; bxi < nbx; ++bxi) {
+            const double xl = (double)bx0 + bxi * be - margin, xh = (double)bx0 + (bxi + 1) * be + margin;
+            const double yl = (double)by0 + by * be - margin, yh = (double)by0 + (by + 1) * be + margin;
+            for (int r = 0; r < R; ++r) {
+                const double qx = hr[(size_t)r].x, qy = hr[(size_t)r].y;
+                const double dx = std::max(0.0, std::max(xl - qx, qx - xh));
+                const double dy = std::max(0.0, std::max(yl - qy, qy - yh));
+                if (dx * dx + dy * dy <= reach2) bidx.push_back((unsigned char)r);
+            }
+            boff[(size_t)by * nbx + bxi + 1] = (int)bidx.size();
+        }
+    if (boff.size() > c->d_rbin_off_cap || std::max<size_t>(1, bidx.size()) > c->d_rbin_idx_cap) {
+        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (c->d_rbin_off) cudaFree(c->d_rbin_off);
+        if (c->d_rbin_idx) cudaFree(c->d_rbin_idx);
+        c->d_rbin_off = nullptr;
+        c->d_rbin_idx = nullptr;
+        c->d_rbin_off_cap = c->d_rbin_idx_cap = 0;
+        LPM_CUDA(c, cudaMalloc(&c->d_rbin_off, boff.size() * sizeof(int)));
+        LPM_CUDA(c, cudaMalloc(&c->d_rbin_idx, std::max<size_t>(1, bidx.size())));
+        c->d_rbin_off_cap = boff.size();
+        c->d_rbin_idx_cap = std::max<size_t>(1, bidx.size());
+    }
     LPM_CUDA(c, cudaMemcpyAsync(c->d_rec, hr.data(), hr.size() * sizeof(float4),
                                 cudaMemcpyHostToDevice, c->stream));
+    LPM_CUDA(c, cudaMemcpyAsync(c->d_rbin_off, boff.data(), boff.size() * sizeof(int),
+                                cudaMemcpyHostToDevice, c->stream));
+    if (!bidx.empty())
+        LPM_CUDA(c, cudaMemcpyAsync(c->d_rbin_idx, bidx.data(), bidx.size(),
+                                    cudaMemcpyHostToDevice, c->stream));
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     std::memset(&A, 0, sizeof A);
+    A.rbin_off = c->d_rbin_off;
+    A.rbin_idx = c->d_rbin_idx;
+    A.rbx0 = bx0;
+    A.rby0 = by0;
+    A.rinv_bin = inv_bin;
+    A.rnbx = nbx;
+    A.rnby = nby;
     const double s2 = bandwidth * bandwidth;
     A.rec = c->d_rec;
     A.R = R;
