@@ -241,8 +241,7 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
     const float sig_h = T.khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
     const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
     // 3. N(0,1) draws
-    const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u, P.seed_lo,
-                               P.seed_hi);
+    const U4 w = philox4x32_10_rk((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u, P.rk);
     float n0, n1, n2;
     normals3(w, n0, n1, n2);
     // 4. Eq. (1)-(2): wind then turbulent displacement
@@ -299,8 +298,7 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Lev
     }
     if (!(P.t_dry | P.t_wet)) return ST_ACTIVE;
     // 6. dry deposition below the mixing height, then wet where it rains
-    const U4 d = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 1u, P.seed_lo,
-                               P.seed_hi);
+    const U4 d = philox4x32_10_rk((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 1u, P.rk);
     int kind = -1;
     if (d.a < P.t_dry && zn < P.h_mix) kind = 0;
     if (kind < 0 && d.b < P.t_wet && P.rain) {

@@ -316,6 +316,10 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.z_top = (float)g.z_top;
     P.seed_lo = (unsigned int)(g.seed & 0xffffffffu);
     P.seed_hi = (unsigned int)(g.seed >> 32);
+    for (int r = 0; r < 10; ++r) {                  // Philox key schedule (Weyl increments)
+        P.rk[2 * r] = P.seed_lo + (unsigned int)r * 0x9E3779B9u;
+        P.rk[2 * r + 1] = P.seed_hi + (unsigned int)r * 0xBB67AE85u;
+    }
     const double p_dry = (g.vd_dry > 0 && g.h_mix > 0) ? 1.0 - std::exp(-g.vd_dry * g.dt / g.h_mix) : 0.0;
     const double p_wet = (g.wet_lambda > 0 && c->any_rain) ? 1.0 - std::exp(-g.wet_lambda * g.dt) : 0.0;
     P.t_dry = threshold(p_dry);

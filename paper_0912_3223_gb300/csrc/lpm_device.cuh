@@ -83,6 +83,7 @@ struct StepParams {
     float lambda;                    // decay rate (1/s)
     float h_mix, z_top;
     unsigned int seed_lo, seed_hi;
+    unsigned int rk[20];             // Philox round keys (seed + r x Weyl constant), r = 0..9
     unsigned int t_dry, t_wet;       // event iff word < threshold
     int reflect_ground, reflect_top, lateral_exit, drift;
     // concentration grid
@@ -174,6 +175,28 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
         c3 = lo0;
         k0 += W0;
         k1 += W1;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// The same generator with the round keys precomputed (rk[2r], rk[2r+1] = the key after r
+// bumps), as the step kernels receive them with their parameters.
+__device__ __forceinline__ U4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                               const unsigned int (&rk)[20])
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)M0 * c0;
+        const unsigned long long p1 = (unsigned long long)M1 * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c1 ^ rk[2 * r];
+        const uint32_t n2 = hi0 ^ c3 ^ rk[2 * r + 1];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
     }
     return U4{c0, c1, c2, c3};
 }
