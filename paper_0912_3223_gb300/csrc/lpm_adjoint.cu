@@ -273,22 +273,14 @@ __device__ __forceinline__ void reduce_gradient(const AdjParams &A, const Tile &
                                                 bool valid, int qidx, double *s_g, double *s_gq)
 {
     if (!valid) J = Adjoint{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int o = 16; o > 0; o >>= 1) {
-        J.mu0 += __shfl_xor_sync(0xffffffffu, J.mu0, o);
-        J.mu1 += __shfl_xor_sync(0xffffffffu, J.mu1, o);
-        J.mu2 += __shfl_xor_sync(0xffffffffu, J.mu2, o);
-        J.gsk += __shfl_xor_sync(0xffffffffu, J.gsk, o);
-        J.gbu += __shfl_xor_sync(0xffffffffu, J.gbu, o);
-        J.gbv += __shfl_xor_sync(0xffffffffu, J.gbv, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&s_g[0], (double)J.mu0);
-        atomicAdd(&s_g[1], (double)J.mu1);
-        atomicAdd(&s_g[2], (double)J.mu2);
-        atomicAdd(&s_g[3], (double)J.gsk);
-        atomicAdd(&s_g[4], (double)J.gbu);
-        atomicAdd(&s_g[5], (double)J.gbv);
-    }
+    // warp sums in FP64, so the totals do not depend on which particles share a warp
+    double d[6] = {J.mu0, J.mu1, J.mu2, J.gsk, J.gbu, J.gbv};
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        for (int o = 16; o > 0; o >>= 1) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) atomicAdd(&s_g[i], d[i]);
     if (J.gq != 0.f) atomicAdd(&s_gq[qidx], (double)J.gq);
     __syncthreads();
     double *G = A.grad + (long long)tile.scen * A.ng;

@@ -231,12 +231,44 @@ def test_trajectory_and_checkpoint_storage_agree():
                                        err_msg=form)
             np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max(),
                                        err_msg=form)
-        # the sorted form carries dL/dX between segments exactly (FP32 values) but restarts
-        # each particle's FP32 parameter sums every 64 steps: source partials to the order
-        # of the FP64 sums, parameter partials to FP32 rounding of the per-particle sums
+        # the sorted form carries dL/dX between segments exactly (FP32 values; sums over
+        # particles are FP64) but restarts each particle's FP32 parameter sums every 64
+        # steps: source partials to the order of the FP64 sums, parameter partials to FP32
+        # rounding of the per-particle sums
         C1, g1 = out["trajectory"]
         np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max())
         np.testing.assert_allclose(g1[:, :3], g0[:, :3], rtol=1e-9,
                                    atol=1e-12 * np.abs(g0[:, :3]).max())
         np.testing.assert_allclose(g1[:, 3:], g0[:, 3:], rtol=0,
                                    atol=2e-5 * np.abs(g0[:, 3:]).max())
+
+
+def test_sorted_trajectory_with_late_release_and_partial_segment_matches_oracle():
+    """Segment edges of the cell-sorted form: a release window [70, 380) that starts and ends
+    inside 64-step segments, in a 401-step run whose last segment holds 17 steps, against
+    the oracle and against the recomputing checkpoint form."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg, rec = _realistic(n=4000, steps=401)
+    cfg = dataclasses.replace(cfg, release=dataclasses.replace(cfg.release, first_step=70,
+                                                               last_step=380))
+    w = np.linspace(-1.0, 1.0, rec.shape[0])
+    out = {}
+    for limit in (1 << 37, 0):
+        with Sim(cfg) as sim:
+            lpm.lpm_set_adjoint_storage(sim.ctx, limit)
+            C = lpm.lpm_receptors(sim.ctx, 1, rec, SIGMA, 18)[0]
+            g = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, w[None, :], 24)[0]
+            assert lpm.lpm_adjoint_storage(sim.ctx)[0] == (limit != 0)
+        out[limit] = (C, g)
+    C, g = out[1 << 37]
+    C1, g1 = out[0]
+    np.testing.assert_allclose(C1, C, rtol=1e-12, atol=1e-15 * np.abs(C).max())
+    np.testing.assert_allclose(g1[:3], g[:3], rtol=1e-9, atol=1e-12 * np.abs(g[:3]).max())
+    np.testing.assert_allclose(g1[3:], g[3:], rtol=0, atol=2e-5 * np.abs(g[3:]).max())
+    ref_C = oracle.receptors(cfg, rec, SIGMA, 18)
+    assert np.abs(ref_C).max() > 0
+    np.testing.assert_allclose(C, ref_C, rtol=1e-3, atol=1e-4 * np.abs(ref_C).max())
+    ref = oracle.adjoint(cfg, rec, SIGMA, 18, w)
+    np.testing.assert_allclose(g[:3], ref[:3], atol=0.01 * np.abs(ref[:3]).max())
+    np.testing.assert_allclose(g[3:27], ref[3:27], rtol=1e-3, atol=1e-6 * np.abs(ref[3:27]).max())
+    np.testing.assert_allclose(g[27:], ref[27:], atol=0.01 * np.abs(ref[27:]).max())
