@@ -27,11 +27,11 @@ __device__ __forceinline__ void sample_met_grad(const StepParams &P, const Level
     float a, b, c;
     axis(x, P.x0, P.inv_dx, P.nx, i, a);
     axis(y, P.y0, P.inv_dy, P.ny, j, b);
-    level(L, z, k, c);
+    level(P, L, z, k, c);
     const float fx = (x - P.x0) * P.inv_dx, fy = (y - P.y0) * P.inv_dy;
     const float gx = (fx >= 0.0f && fx <= (float)(P.nx - 1)) ? P.inv_dx : 0.0f;
     const float gy = (fy >= 0.0f && fy <= (float)(P.ny - 1)) ? P.inv_dy : 0.0f;
-    const float gz = (z >= L.z_lo && z <= L.z_hi) ? L.zi[k].y : 0.0f;
+    const float gz = (z >= L.z_lo && z <= L.z_hi) ? P.zi[k].y : 0.0f;
     const int n00 = col_node(P, i, j, k);
     float4 q[8];
 #pragma unroll
@@ -122,12 +122,11 @@ template <bool TRAJ>
 __global__ void __launch_bounds__(ADJ_BLOCK, 8)
 adj_forward_kernel(const StepParams P, const AdjParams A)
 {
-    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_forward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_C = reinterpret_cast<double *>(s_rec + A.R);    // [R]
-    const Levels LV = load_levels(P, s_zi, s_lut);
+    const Levels LV = load_levels(P, s_lut);
     for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
         s_rec[r] = A.rec[r];
         s_C[r] = 0.0;
@@ -309,14 +308,13 @@ __device__ __forceinline__ void load_receptors(const AdjParams &A, const Tile &t
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_backward_kernel(const StepParams P, const AdjParams A)
 {
-    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
     double *s_gq = s_g + 6;                       // [nq]
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
-    const Levels LV = load_levels(P, s_zi, s_lut);
+    const Levels LV = load_levels(P, s_lut);
     const Tile tile = A.tiles[blockIdx.x];
     load_receptors(A, tile, s_rec, s_w, s_g, s_gq);
     const ScenDev sc = P.scen[tile.scen];
@@ -386,14 +384,13 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_backward_traj_kernel(const StepParams P, const AdjParams A)
 {
-    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
     double *s_gq = s_g + 6;                       // [nq]
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
-    const Levels LV = load_levels(P, s_zi, s_lut);
+    const Levels LV = load_levels(P, s_lut);
     const Tile tile = A.tiles[blockIdx.x];
     load_receptors(A, tile, s_rec, s_w, s_g, s_gq);
     const ScenDev sc = P.scen[tile.scen];
@@ -475,12 +472,11 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     const bool from_a = (int)blockIdx.x < G.tiles_a;
     const unsigned int live = from_a ? *G.live : 0u;
     if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
-    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_forward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_C = reinterpret_cast<double *>(s_rec + A.R);    // [R]
-    const Levels LV = load_levels(P, s_zi, s_lut);
+    const Levels LV = load_levels(P, s_lut);
     for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
         s_rec[r] = A.rec[r];
         s_C[r] = 0.0;
@@ -544,14 +540,13 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     const bool from_a = (int)blockIdx.x < G.tiles_a;
     const unsigned int live = from_a ? *G.live : 0u;
     if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
-    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
     double *s_gq = s_g + 6;                       // [nq]
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
-    const Levels LV = load_levels(P, s_zi, s_lut);
+    const Levels LV = load_levels(P, s_lut);
     const Tile tile0{0, 0, 0};
     load_receptors(A, tile0, s_rec, s_w, s_g, s_gq);
     const ScenDev sc = P.scen[0];

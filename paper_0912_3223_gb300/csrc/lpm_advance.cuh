@@ -107,7 +107,7 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
     float a, b, c;
     axis(x, P.x0, P.inv_dx, P.nx, i, a);
     axis(y, P.y0, P.inv_dy, P.ny, j, b);
-    level(L, z, k, c);
+    level(P, L, z, k, c);
     const int n00 = col_node(P, i, j, k);
     float4 q[8];
 #pragma unroll
@@ -139,7 +139,7 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
     } else {
         m.kz = fmaxf(r.w, 0.0f);
         const bool inside = z >= L.z_lo && z <= L.z_hi;
-        m.dkz = inside ? (y1.w - y0.w) * L.zi[k].y : 0.0f;
+        m.dkz = inside ? (y1.w - y0.w) * P.zi[k].y : 0.0f;
     }
     if (khp) {
         float e[8];
@@ -350,12 +350,11 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
                int k1, int do_bin)
 {
-    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
     __shared__ unsigned long long s_acc[BLOCK];
     __shared__ int s_tile;
     __shared__ unsigned long long s_steps;
-    const Levels LV = load_levels(P, s_zi, s_lut);
+    const Levels LV = load_levels(P, s_lut);
     unsigned long long *s_warp = s_acc + (threadIdx.x & ~31);
     const long long n_cells = (long long)P.cx * P.cy * P.cz;
     constexpr int TILE = BLOCK * PPT;

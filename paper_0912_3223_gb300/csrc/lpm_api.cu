@@ -305,7 +305,11 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.inv_met_dt = (float)(1.0 / g.met_dt);
     P.x_lo = (float)g.x0; P.x_hi = (float)(g.x0 + (g.nx - 1) * g.dx);
     P.y_lo = (float)g.y0; P.y_hi = (float)(g.y0 + (g.ny - 1) * g.dy);
-    for (int k = 0; k < g.nz; ++k) P.zlev[k] = (float)c->zlev[k];
+    for (int k = 0; k < g.nz; ++k) {      // same FP32 arithmetic as a kernel would do
+        const float z0 = (float)c->zlev[k];
+        const float inv = k + 1 < g.nz ? 1.0f / ((float)c->zlev[k + 1] - z0) : 0.0f;
+        P.zi[k] = make_float2(z0, inv);
+    }
     P.dt = (float)g.dt;
     P.kh_uniform = (float)g.kh_uniform;
     P.k_scale = (float)c->k_scale;

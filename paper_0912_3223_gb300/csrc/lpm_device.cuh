@@ -74,7 +74,6 @@ struct StepParams {
     float x0, y0, inv_dx, inv_dy, dx, dy;
     float met_t0, met_dt, inv_met_dt;
     float x_lo, x_hi, y_lo, y_hi;
-    float zlev[MAX_LEVELS];
     const unsigned char *zlut;       // level at the start of each uniform z bin, or nullptr
     int n_lut;
     float lut_z0, lut_inv_h;         // bin b = (z - lut_z0) * lut_inv_h
@@ -84,6 +83,9 @@ struct StepParams {
     float h_mix, z_top;
     unsigned int seed_lo, seed_hi;
     unsigned int rk[20];             // Philox round keys (seed + r x Weyl constant), r = 0..9
+    // (z_levels[k], 1 / (z[k+1] - z[k])) (0 for the top level): read by index from the
+    // kernel parameters, i.e. through the constant cache, off the L1 data pipe
+    float2 zi[MAX_LEVELS];
     unsigned int t_dry, t_wet;       // event iff word < threshold
     int reflect_ground, reflect_top, lateral_exit, drift;
     // concentration grid
@@ -275,7 +277,6 @@ __device__ __forceinline__ void axis(float coord, float c0, float inv_d, int n, 
 // from that point to the bin's upper edge holds at most one level boundary and one
 // comparison with the next level settles the exact cell. Without it, bisection.
 struct Levels {
-    const float2 *zi;                // shared memory: (z_levels[k], 1 / (z[k+1] - z[k]))
     const unsigned char *lut;        // shared-memory copy of the table, or nullptr
     int nz, n_lut;
     float z0, inv_h;                 // table origin and 1 / bin width
@@ -283,7 +284,8 @@ struct Levels {
 };
 
 // Vertical cell k (last level <= z, clamped to [0, nz-2]) and fraction c in [0, 1].
-__device__ __forceinline__ void level(const Levels &L, float z, int &k, float &c)
+__device__ __forceinline__ void level(const StepParams &P, const Levels &L, float z, int &k,
+                                      float &c)
 {
     int kk;
     float2 zk;
@@ -291,7 +293,7 @@ __device__ __forceinline__ void level(const Levels &L, float z, int &k, float &c
         int b = (int)((z - L.z0) * L.inv_h);
         b = min(max(b, 0), L.n_lut - 1);
         const int k0 = L.lut[b];
-        const float2 lo = L.zi[k0], hi = L.zi[k0 + 1];
+        const float2 lo = P.zi[k0], hi = P.zi[k0 + 1];
         const bool up = k0 < L.nz - 2 && z >= hi.x;
         kk = up ? k0 + 1 : k0;
         zk = up ? hi : lo;
@@ -299,33 +301,29 @@ __device__ __forceinline__ void level(const Levels &L, float z, int &k, float &c
         int lo = 0, hi = L.nz - 1;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (L.zi[mid].x <= z) lo = mid;
+            if (P.zi[mid].x <= z) lo = mid;
             else hi = mid;
         }
         kk = lo;
-        zk = L.zi[kk];
+        zk = P.zi[kk];
     }
     k = kk;
     c = fminf(fmaxf((z - zk.x) * zk.y, 0.0f), 1.0f);
 }
 
 // Fills the shared-memory level tables (call by the whole block, then __syncthreads()).
-__device__ __forceinline__ Levels load_levels(const StepParams &P, float2 *s_zi,
-                                              unsigned char *s_lut)
+__device__ __forceinline__ Levels load_levels(const StepParams &P, unsigned char *s_lut)
 {
-    for (int i = threadIdx.x; i < P.nz; i += blockDim.x)
-        s_zi[i] = make_float2(P.zlev[i], i + 1 < P.nz ? 1.0f / (P.zlev[i + 1] - P.zlev[i]) : 0.0f);
     if (P.zlut)
         for (int i = threadIdx.x; i < P.n_lut; i += blockDim.x) s_lut[i] = P.zlut[i];
     Levels L;
-    L.zi = s_zi;
     L.lut = P.zlut ? s_lut : nullptr;
     L.nz = P.nz;
     L.n_lut = P.n_lut;
     L.z0 = P.lut_z0;
     L.inv_h = P.lut_inv_h;
-    L.z_lo = P.zlev[0];
-    L.z_hi = P.zlev[P.nz - 1];
+    L.z_lo = P.zi[0].x;
+    L.z_hi = P.zi[P.nz - 1].x;
     return L;
 }
 

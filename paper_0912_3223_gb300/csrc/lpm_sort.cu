@@ -69,9 +69,8 @@ __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                                  unsigned int *__restrict__ keys, unsigned int *__restrict__ hist,
                                  unsigned int dead_key)
 {
-    __shared__ float2 s_zi[MAX_LEVELS];
     __shared__ unsigned char s_lut[MAX_LUT];
-    const Levels LV = load_levels(P, s_zi, s_lut);
+    const Levels LV = load_levels(P, s_lut);
     __syncthreads();
     const long long n = meta[1];
     const unsigned int live_old = meta[2];
@@ -93,7 +92,7 @@ __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                     float a, b, c;
                     axis(s.x, P.x0, P.inv_dx, P.nx, ix, a);
                     axis(s.y, P.y0, P.inv_dy, P.ny, jy, b);
-                    level(LV, s.z, kz, c);
+                    level(P, LV, s.z, kz, c);
                     key = cell_key(P, ix, jy, kz);
                 } else {
                     key = dead_key;
