@@ -19,6 +19,8 @@
 namespace lpm {
 
 // Weather and its spatial gradient: val = (u, v, w, K_z, K_h), g[q][d] = d val[q] / d x_d.
+// KHG: K_h is a gridded field (else uniform, gradient 0, and none of its code is compiled).
+template <bool KHG>
 __device__ __forceinline__ void sample_met_grad(const StepParams &P, const Levels &L,
                                                 const StepTime &T, float sig_h_uniform, float x,
                                                 float y, float z, float val[5], float g[5][3])
@@ -63,7 +65,7 @@ __device__ __forceinline__ void sample_met_grad(const StepParams &P, const Level
         val[3] = 0.0f;
         g[3][0] = g[3][1] = g[3][2] = 0.0f;
     }
-    if (T.khp) {
+    if (KHG && T.khp) {
         float e[8];
 #pragma unroll
         for (int mm = 0; mm < 8; ++mm) {
@@ -206,6 +208,7 @@ struct Adjoint {
 // One step of the reverse sweep: the receptor term of the state Xa after step k (when k
 // is a sample step and not the step that ended the run), then mu <- J_k^T mu with the
 // Jacobian of step k at the state X before it (fold = the step's reflection sign).
+template <bool KHG>
 __device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParams &A,
                                              const Levels &LV, const ScenDev &sc,
                                              const float4 *s_rec, const float *s_w,
@@ -237,7 +240,7 @@ __device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParam
     }
     const StepTime T = step_time(P, sc.wind_offset, k);
     float val[5], g[5][3];
-    sample_met_grad(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
+    sample_met_grad<KHG>(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
     const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
                                P.seed_lo, P.seed_hi);
     float n0, n1, n2;
@@ -305,6 +308,7 @@ __device__ __forceinline__ void load_receptors(const AdjParams &A, const Tile &t
 // Checkpoint form: each thread recomputes its particle's path one CK-step segment at a
 // time from the checkpoint (same keyed draws and FP32 arithmetic, so the same path and
 // events) into a local buffer, then sweeps the segment in reverse.
+template <bool KHG>
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_backward_kernel(const StepParams P, const AdjParams A)
 {
@@ -371,7 +375,7 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
             if (!(run && k >= kstart && k <= klast)) continue;
             const int i = k - k_lo;
             const bool sample = (k + 1) % A.every == 0 && !(ev && k == klast);
-            reverse_step(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k,
+            reverse_step<KHG>(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k,
                          seg[i], (float)sfold[i], seg[i + 1], sample, J);
         }
         __syncwarp();
@@ -381,6 +385,7 @@ adj_backward_kernel(const StepParams P, const AdjParams A)
 
 // Trajectory form: the forward kept every state, so the sweep reads them back (one
 // coalesced 16-B row entry per step, prefetched one step ahead) instead of recomputing.
+template <bool KHG>
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_backward_traj_kernel(const StepParams P, const AdjParams A)
 {
@@ -425,7 +430,7 @@ adj_backward_traj_kernel(const StepParams P, const AdjParams A)
         if (k - 1 >= kb && k - 1 < kn) Xn = __ldcs(row + (long long)(k - 1 - k0) * ADJ_BLOCK);
         if (!act) continue;
         const bool sample = (k + 1) % A.every == 0 && !(ev && k == kn - 1);
-        reverse_step(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
+        reverse_step<KHG>(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
                      X.w, Xa, sample, J);
         Xa = X;
     }
@@ -534,6 +539,7 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
         if (s_C[r] != 0.0) atomicAdd(A.C + r, s_C[r]);
 }
 
+template <bool KHG>
 __global__ void __launch_bounds__(ADJ_BLOCK, 5)
 adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
 {
@@ -583,7 +589,7 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
         if (k - 1 >= kb && k - 1 < kn) Xn = __ldcs(row + (long long)(k - 1 - G.k_lo) * G.width);
         if (!act) continue;
         const bool sample = (k + 1) % A.every == 0 && !(ev && k == kn - 1);
-        reverse_step(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
+        reverse_step<KHG>(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
                      X.w, Xa, sample, J);
         Xa = X;
     }
@@ -606,10 +612,13 @@ static void adj_prefer_l1()
     const int pct = 25;
     cudaFuncSetAttribute(adj_forward_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_forward_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_backward_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_backward_traj_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_traj_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_traj_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_forward_seg_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_backward_seg_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_seg_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_backward_seg_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     (void)cudaGetLastError();
 }
 
@@ -627,7 +636,10 @@ cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const A
 {
     if (n_blocks <= 0) return cudaSuccess;
     adj_prefer_l1();
-    adj_backward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A, G);
+    if (P.khpair)
+        adj_backward_seg_kernel<true><<<n_blocks, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A, G);
+    else
+        adj_backward_seg_kernel<false><<<n_blocks, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A, G);
     return cudaGetLastError();
 }
 
@@ -646,10 +658,15 @@ cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjPa
 {
     if (n_tiles <= 0) return cudaSuccess;
     adj_prefer_l1();
-    if (A.traj)
-        adj_backward_traj_kernel<<<n_tiles, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A);
+    const size_t sm = adj_smem_backward(A);
+    if (A.traj && P.khpair)
+        adj_backward_traj_kernel<true><<<n_tiles, ADJ_BLOCK, sm, s>>>(P, A);
+    else if (A.traj)
+        adj_backward_traj_kernel<false><<<n_tiles, ADJ_BLOCK, sm, s>>>(P, A);
+    else if (P.khpair)
+        adj_backward_kernel<true><<<n_tiles, ADJ_BLOCK, sm, s>>>(P, A);
     else
-        adj_backward_kernel<<<n_tiles, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A);
+        adj_backward_kernel<false><<<n_tiles, ADJ_BLOCK, sm, s>>>(P, A);
     return cudaGetLastError();
 }
 
