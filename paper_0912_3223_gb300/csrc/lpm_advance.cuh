@@ -96,8 +96,8 @@ __device__ __forceinline__ void warp_count_scen(int s, unsigned long long v, int
 // boundary-layer columns (EXT and blp), K_z and its derivative come from Eq. 3 instead
 // (4 more 32-byte loads of the time-paired (u*, 1/L, H_z) at the cell's corner columns,
 // bilinear in x, y); only the EXT instantiations carry that code.
-template <bool EXT>
-__device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels &L,
+template <bool EXT, class LEV>
+__device__ __forceinline__ Met sample_met_pair(const StepParams &P, const LEV &L,
                                                const float4 *__restrict__ pair,
                                                const float2 *__restrict__ khp,
                                                const float4 *__restrict__ blp, float f,
@@ -139,7 +139,7 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const Levels
     } else {
         m.kz = fmaxf(r.w, 0.0f);
         const bool inside = z >= L.z_lo && z <= L.z_hi;
-        m.dkz = inside ? (y1.w - y0.w) * P.zi[k].y : 0.0f;
+        m.dkz = inside ? (y1.w - y0.w) * level_entry(P, L, k).y : 0.0f;
     }
     if (khp) {
         float e[8];
@@ -227,8 +227,8 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const float2 
 // Updates (x, y, z) and returns the new status. (du, dv) is the wind offset of the
 // particle's scenario plus the bias at t_k. With GRIDS, deposition and exit add their mass
 // to the scenario's grids and counters; *fold receives dz/dz_pre (+-1, 0 when clamped).
-template <bool GRIDS, bool EXT = false>
-__device__ __forceinline__ uint32_t particle_step(const StepParams &P, const Levels &LV,
+template <bool GRIDS, bool EXT = false, class LEV>
+__device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV &LV,
                                                   const StepTime &T, const ScenDev &sc,
                                                   const ScenDev *scg, unsigned long long gid,
                                                   int sp, float sig_h_uniform, float du, float dv,

@@ -283,8 +283,26 @@ struct Levels {
     float z_lo, z_hi;                // lowest and highest level
 };
 
+// The same tables with (z_levels[k], 1 / spacing) from shared memory instead of the kernel
+// parameters: for kernels whose warps hold particles at many different levels (the constant
+// cache serialises a warp's distinct addresses, shared memory serves them in one pass).
+struct LevelsS : Levels {
+    const float2 *zi;
+};
+
+__device__ __forceinline__ float2 level_entry(const StepParams &P, const Levels &, int k)
+{
+    return P.zi[k];
+}
+
+__device__ __forceinline__ float2 level_entry(const StepParams &, const LevelsS &L, int k)
+{
+    return L.zi[k];
+}
+
 // Vertical cell k (last level <= z, clamped to [0, nz-2]) and fraction c in [0, 1].
-__device__ __forceinline__ void level(const StepParams &P, const Levels &L, float z, int &k,
+template <class LEV>
+__device__ __forceinline__ void level(const StepParams &P, const LEV &L, float z, int &k,
                                       float &c)
 {
     int kk;
@@ -293,7 +311,7 @@ __device__ __forceinline__ void level(const StepParams &P, const Levels &L, floa
         int b = (int)((z - L.z0) * L.inv_h);
         b = min(max(b, 0), L.n_lut - 1);
         const int k0 = L.lut[b];
-        const float2 lo = P.zi[k0], hi = P.zi[k0 + 1];
+        const float2 lo = level_entry(P, L, k0), hi = level_entry(P, L, k0 + 1);
         const bool up = k0 < L.nz - 2 && z >= hi.x;
         kk = up ? k0 + 1 : k0;
         zk = up ? hi : lo;
@@ -301,11 +319,11 @@ __device__ __forceinline__ void level(const StepParams &P, const Levels &L, floa
         int lo = 0, hi = L.nz - 1;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (P.zi[mid].x <= z) lo = mid;
+            if (level_entry(P, L, mid).x <= z) lo = mid;
             else hi = mid;
         }
         kk = lo;
-        zk = P.zi[kk];
+        zk = level_entry(P, L, kk);
     }
     k = kk;
     c = fminf(fmaxf((z - zk.x) * zk.y, 0.0f), 1.0f);
@@ -324,6 +342,17 @@ __device__ __forceinline__ Levels load_levels(const StepParams &P, unsigned char
     L.inv_h = P.lut_inv_h;
     L.z_lo = P.zi[0].x;
     L.z_hi = P.zi[P.nz - 1].x;
+    return L;
+}
+
+// LevelsS with the level entries copied to shared memory (whole block, then __syncthreads()).
+__device__ __forceinline__ LevelsS load_levels_smem(const StepParams &P, float2 *s_zi,
+                                                   unsigned char *s_lut)
+{
+    LevelsS L;
+    static_cast<Levels &>(L) = load_levels(P, s_lut);
+    for (int i = threadIdx.x; i < P.nz; i += blockDim.x) s_zi[i] = P.zi[i];
+    L.zi = s_zi;
     return L;
 }
 
