@@ -13,6 +13,8 @@
 //  - checkpoints every CK steps when the trajectory does not fit: each CK-step segment is
 //    recomputed from its checkpoint (same keyed draws and FP32 arithmetic, so the same
 //    path and events) before it is swept.
+#include <mutex>
+
 #include "lpm_advance.cuh"
 #include "lpm_adjoint.h"
 
@@ -607,11 +609,8 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
 
 // The kernels need a few KB of shared memory per block: ask for the smallest carve-out so
 // the rest of the unified L1 serves the weather gathers (once per process).
-static void adj_prefer_l1()
+static void adj_set_carveout()
 {
-    static bool done = false;
-    if (done) return;
-    done = true;
     const int pct = 25;
     cudaFuncSetAttribute(adj_forward_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_forward_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
@@ -622,6 +621,12 @@ static void adj_prefer_l1()
     cudaFuncSetAttribute(adj_backward_seg_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_backward_seg_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     (void)cudaGetLastError();
+}
+
+static void adj_prefer_l1()
+{
+    static std::once_flag once;              // contexts on several host threads may launch
+    std::call_once(once, adj_set_carveout);
 }
 
 cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
