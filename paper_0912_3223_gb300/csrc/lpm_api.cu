@@ -740,15 +740,17 @@ lpm_status lpm_create(const lpm_config *cfg, void *cuda_stream, lpm_ctx **out)
     CREATE_CUDA(cudaMemsetAsync(c->d_ctr, 0, ns * N_COUNTERS * sizeof(unsigned long long), c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));
     {
-        // vertical lookup table: bins of at most a third of the smallest level spacing, each
-        // holding the cell 0.05 bin below its lower edge (the kernel then corrects it by at
-        // most one with one comparison), in the FP32 arithmetic the kernel uses to pick a bin
+        // vertical lookup table: bins of the smallest level spacing / 1.2, each holding the
+        // cell 0.05 bin below its lower edge (the kernel then corrects it by at most one with
+        // one comparison: the 1.05 bins from that point to the bin's top hold at most one
+        // level), in the FP32 arithmetic the kernel uses to pick a bin; fewer, wider bins
+        // spread a warp's lookups over fewer shared-memory words
         std::vector<float> zf(cfg->nz);
         for (int k = 0; k < cfg->nz; ++k) zf[k] = (float)cfg->z_levels[k];
         double min_sp = 1e300;
         for (int k = 0; k + 1 < cfg->nz; ++k) min_sp = std::min(min_sp, (double)zf[k + 1] - zf[k]);
         const double span = (double)zf[cfg->nz - 1] - zf[0];
-        const double n_need = min_sp > 0 ? std::ceil(span / (min_sp / 3.0)) + 1 : 1e300;
+        const double n_need = min_sp > 0 ? std::ceil(span / (min_sp / 1.2)) + 1 : 1e300;
         if (n_need <= MAX_LUT) {
             c->n_lut = (int)n_need;
             c->lut_z0 = zf[0];

@@ -272,10 +272,10 @@ __device__ __forceinline__ void axis(float coord, float c0, float inv_d, int n, 
 }
 
 // Vertical cell: last level <= z, clamped to [0, nz-2]. With the lookup table, bin b of
-// width h (at most a third of the smallest level spacing) holds the cell at the point
-// 0.05 h below its lower edge; FP32 bin arithmetic errs by far less than that, so the span
-// from that point to the bin's upper edge holds at most one level boundary and one
-// comparison with the next level settles the exact cell. Without it, bisection.
+// width h (the smallest level spacing / 1.2) holds the cell at the point 0.05 h below its
+// lower edge; FP32 bin arithmetic errs by far less than that, so the span from that point
+// to the bin's upper edge (1.05 h) holds at most one level boundary and one comparison with
+// the next level settles the exact cell. Without it, bisection.
 struct Levels {
     const unsigned char *lut;        // shared-memory copy of the table, or nullptr
     int nz, n_lut;
