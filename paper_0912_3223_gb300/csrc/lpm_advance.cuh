@@ -539,6 +539,39 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
             }
         }
 
+        // ---- sort keys for the sort that follows (its inputs: A slots, then B lanes) ----
+        if (R.keys) {
+            const unsigned int dead_key = (unsigned int)sort_key_range(P.nx, P.ny, P.nz);
+            const int lane = threadIdx.x & 31;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const int local = j * BLOCK + threadIdx.x;
+                long long idx = -1;
+                unsigned int key = KEY_NONE_U;
+                if (in_a) {
+                    if (local < count) idx = first + local;
+                } else {
+                    idx = (long long)*R.a_live + (long long)(t - R.tiles_a) * TILE + local;
+                }
+                if (local < count) {
+                    if ((tag[j] >> TAG_SHIFT) == ST_ACTIVE) {
+                        int ix, jy, kz;
+                        float fa, fb, fc;
+                        axis(x[j], P.x0, P.inv_dx, P.nx, ix, fa);
+                        axis(y[j], P.y0, P.inv_dy, P.ny, jy, fb);
+                        level(P, LV, z[j], kz, fc);
+                        key = cell_key(P, ix, jy, kz);
+                    } else {
+                        key = dead_key;
+                    }
+                }
+                if (idx >= 0) R.keys[idx] = key;
+                const unsigned int peers = __match_any_sync(0xffffffffu, key);
+                if (key != KEY_NONE_U && lane == __ffs(peers) - 1)
+                    atomicAdd(R.hist + key, (unsigned int)__popc(peers));
+            }
+        }
+
         // ---- end-of-segment concentration snapshot (every n-th step, Sec. 3.2) --------
         if (do_bin) {
 #pragma unroll

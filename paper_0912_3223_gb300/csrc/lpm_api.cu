@@ -1079,7 +1079,9 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
     const bool batched = g.n_scenarios > 1;
     const int T = c->block * c->ppt;
     const size_t ns = (size_t)g.n_scenarios;
-    for (const Segment &sg : plan) {
+    bool keys_ready = false;                 // the previous launch wrote the sort's keys
+    for (size_t gi = 0; gi < plan.size(); ++gi) {
+        const Segment &sg = plan[gi];
         if (direct) {
             lpm_status ws = wait_met_pairs(c, s, sg.k, sg.e);
             if (ws != LPM_OK) return ws;
@@ -1108,6 +1110,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             in.T = T;
             in.w_a = c->langevin ? c->d_w_sorted[cur] : nullptr;
             in.w_b = c->langevin ? c->d_w_home : nullptr;
+            in.keys_ready = keys_ready;
             SortBuffers out{};
             out.state_out = c->d_sorted[1 - cur];
             out.pidx_out = c->d_pidx[1 - cur];
@@ -1122,7 +1125,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             LPM_CUDA(c, launch_sort(s, P, in, out));
             cur = 1 - cur;
             upto = sg.k;
-            kernels += 7;
+            kernels += keys_ready ? 6 : 7;
         }
         AdvanceLaunch L{};
         L.stream = s;
@@ -1146,7 +1149,19 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.mixed = batched;
         L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 || P.langevin;
         const int n_tiles = L.n_tiles();
+        keys_ready = false;
         if (n_tiles <= 0) continue;
+        // the next segment starts with a sort of exactly these particles: write its keys here
+        // (one scenario: measured +0.9 %; the mixed-scenario kernel measured 0.4 % slower)
+        const Segment *nx = gi + 1 < plan.size() ? &plan[gi + 1] : nullptr;
+        if (!batched && nx && nx->sort && nx->sort_b_lo == sg.b_lo && nx->sort_b_hi == sg.b_hi &&
+            nx->sort_a_bound == (upto > 0 ? sg.a_bound : 0)) {
+            const size_t nb = (size_t)sort_key_range(g.nx, g.ny, g.nz) + 1;
+            LPM_CUDA(c, cudaMemsetAsync(c->d_hist, 0, nb * sizeof(unsigned int), s));
+            L.ranges.keys = c->d_keys;
+            L.ranges.hist = c->d_hist;
+            keys_ready = true;
+        }
         if (batched) {
             // persistent grid over an atomic tile queue
             LPM_CUDA(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), s));
@@ -1919,6 +1934,7 @@ lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &
             in.n_b = S.seg_tile[(size_t)s + 1] - G.b_first;
             in.T = ADJ_BLOCK;
             in.w_a = in.w_b = nullptr;
+            in.keys_ready = false;
             SortBuffers out;
             out.state_out = S.st[cur ^ 1];
             out.pidx_out = S.ord + (size_t)(s + 1) * std::max<size_t>(1, (size_t)c->n_slots_used);

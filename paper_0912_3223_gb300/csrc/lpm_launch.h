@@ -19,6 +19,10 @@ struct Ranges {
     const Tile *b_tiles;
     int b_first, n_b;
     float *w_a, *w_b;             // Langevin w' of A (sorted) and B (home) slots, or nullptr
+    // when the next sort takes exactly this launch's particles as its inputs (A slots, then
+    // the B tiles lane by lane): their sort keys and histogram (zeroed before the launch),
+    // written at the segment's end so that the sort skips its key pass; else nullptr
+    unsigned int *keys, *hist;
 };
 
 struct AdvanceLaunch {
@@ -46,6 +50,7 @@ struct SortSource {
     const Tile *tiles;
     int b_first, n_b, T;
     const float *w_a, *w_b;       // Langevin w' (moved with the particles), or nullptr
+    bool keys_ready;              // keys and histogram already written (fused key pass)
 };
 
 struct SortBuffers {
@@ -68,6 +73,21 @@ __host__ __device__ inline long long sort_key_range(int nx, int ny, int nz)
 {
     const long long t = 1LL << SORT_TILE_BITS, tz = 1LL << SORT_TILE_ZBITS;
     return ((nz + tz - 1) / tz) * tz * ((ny + t - 1) / t) * ((nx + t - 1) / t) * t * t;
+}
+
+constexpr unsigned int KEY_NONE_U = 0xffffffffu;     // sort input that is no particle
+
+// Key of cell (ix, jy, kz): its tile, then its place in the tile.
+__device__ __forceinline__ unsigned int cell_key(const StepParams &P, int ix, int jy, int kz)
+{
+    constexpr int TB = SORT_TILE_BITS, TZ = SORT_TILE_ZBITS;
+    constexpr int T = 1 << TB, TZN = 1 << TZ;
+    const unsigned int ntx = (unsigned int)((P.nx + T - 1) >> TB);
+    const unsigned int nty = (unsigned int)((P.ny + T - 1) >> TB);
+    const unsigned int tile = ((unsigned int)(kz >> TZ) * nty + (unsigned int)(jy >> TB)) * ntx +
+                              (unsigned int)(ix >> TB);
+    return (tile << (2 * TB + TZ)) | ((unsigned int)(kz & (TZN - 1)) << (2 * TB)) |
+           ((unsigned int)(jy & (T - 1)) << TB) | (unsigned int)(ix & (T - 1));
 }
 
 constexpr unsigned int SLOT_HOME = 0xffffffffu;   // slot_of: the particle is at its home slot

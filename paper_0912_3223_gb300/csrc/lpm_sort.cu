@@ -13,7 +13,6 @@
 
 namespace lpm {
 
-constexpr unsigned int KEY_NONE_U = 0xffffffffu;
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -47,19 +46,6 @@ __device__ __forceinline__ bool sort_input(const SortSource &S, long long i, uns
     slot = t.first + lane;
     home = (unsigned int)slot;
     return true;
-}
-
-// Key of cell (ix, jy, kz): its tile, then its place in the tile.
-__device__ __forceinline__ unsigned int cell_key(const StepParams &P, int ix, int jy, int kz)
-{
-    constexpr int TB = SORT_TILE_BITS, TZ = SORT_TILE_ZBITS;
-    constexpr int T = 1 << TB, TZN = 1 << TZ;
-    const unsigned int ntx = (unsigned int)((P.nx + T - 1) >> TB);
-    const unsigned int nty = (unsigned int)((P.ny + T - 1) >> TB);
-    const unsigned int tile = ((unsigned int)(kz >> TZ) * nty + (unsigned int)(jy >> TB)) * ntx +
-                              (unsigned int)(ix >> TB);
-    return (tile << (2 * TB + TZ)) | ((unsigned int)(kz & (TZN - 1)) << (2 * TB)) |
-           ((unsigned int)(jy & (T - 1)) << TB) | (unsigned int)(ix & (T - 1));
 }
 
 // Key = weather cell (cell_key order) of an active particle;
@@ -285,12 +271,13 @@ cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &i
     // keys 0..dead_key-1 are cells, dead_key the dead particles
     const unsigned int dead_key = (unsigned int)sort_key_range(P.nx, P.ny, P.nz);
     const long long nb = (long long)dead_key + 1;
-    cudaError_t e = cudaMemsetAsync(B.hist, 0, nb * sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (!in.keys_ready && (e = cudaMemsetAsync(B.hist, 0, nb * sizeof(unsigned int), s)) != cudaSuccess)
+        return e;
     const long long n_b_inputs = (long long)in.n_b * in.T;
     sort_begin_kernel<<<1, 1, 0, s>>>(B.meta, in.has_a ? 1 : 0, n_b_inputs);
     const long long n_max = (in.has_a ? in.a_bound : 0) + n_b_inputs;   // bound of the input size
-    if (n_max > 0)
+    if (n_max > 0 && !in.keys_ready)        // else the advance launch wrote keys and histogram
         sort_keys_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(P, in, B.meta, n_max, B.keys, B.hist,
                                                               dead_key);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
