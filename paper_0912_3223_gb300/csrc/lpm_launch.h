@@ -21,7 +21,8 @@ struct Ranges {
     float *w_a, *w_b;             // Langevin w' of A (sorted) and B (home) slots, or nullptr
     // when the next sort takes exactly this launch's particles as its inputs (A slots, then
     // the B tiles lane by lane): their sort keys and histogram (zeroed before the launch),
-    // written at the segment's end so that the sort skips its key pass; else nullptr
+    // written at the segment's end so that the sort skips its key pass; else nullptr (one
+    // scenario only: the mixed-scenario instantiations carry no key code)
     unsigned int *keys, *hist;
 };
 
