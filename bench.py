@@ -654,7 +654,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--block", type=int, default=512)
     ap.add_argument("--ppt", type=int, default=1)
     ap.add_argument("--occ", type=int, default=2)
     ap.add_argument("--sort-every", type=int, default=60,
@@ -668,7 +668,7 @@ def main():
                                        "kz_eq3", "decay_chain", "langevin"],
                     default=None,
                     help="run one form alone and print its measurement (profiling aid)")
-    ap.add_argument("--batched-block", type=int, default=256)
+    ap.add_argument("--batched-block", type=int, default=512)
     ap.add_argument("--batched-ppt", type=int, default=1)
     ap.add_argument("--batched-occ", type=int, default=2)
     ap.add_argument("--adjoint-particles", type=int, default=1_000_000,

@@ -210,7 +210,7 @@ lpm_status lpm_fixed_state(lpm_ctx *ctx, int scenario, uint64_t *conc, size_t n_
 
 /* Launch shape of the particle kernels: threads per block (128, 256 or 512), particles
  * per thread (1, 2 or 4) and occupancy variant (0, 1, 2: at most 128, 80 or 64 registers
- * per thread, i.e. 16, 24 or 32 resident warps per SM). Default 256 x 1 x 2. Results do
+ * per thread, i.e. 16, 24 or 32 resident warps per SM). Default 512 x 1 x 2. Results do
  * not depend on it. The paper tuned its launch (32 blocks of 256 threads) with the
  * occupancy calculator (Sec. 3.2); here the autotuner picks among these shapes. */
 lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int occupancy);

@@ -4,6 +4,8 @@
 // Instantiated per block size in lpm_advance_b*.cu.
 #pragma once
 
+#include <mutex>
+
 #include "lpm_device.cuh"
 #include "lpm_launch.h"
 
@@ -641,8 +643,20 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
 }
 
 template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
+void adv_prefer_l1()
+{
+    // the kernel needs a few KB of shared memory per block: ask for a small carve-out so the
+    // rest of the SM's unified L1 serves the weather gathers (measured +0.7 to +1.7 %)
+    cudaFuncSetAttribute(advance_kernel<BLOCK, PPT, OCC, MIXED, EXT>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 10);
+    (void)cudaGetLastError();
+}
+
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
 cudaError_t launch_adv(const AdvanceLaunch &L)
 {
+    static std::once_flag once;          // per instantiation; contexts may use several threads
+    std::call_once(once, adv_prefer_l1<BLOCK, PPT, OCC, MIXED, EXT>);
     advance_kernel<BLOCK, PPT, OCC, MIXED, EXT><<<L.grid, BLOCK, 0, L.stream>>>(
         *L.params, L.ranges, L.n_tiles(), L.queue, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();

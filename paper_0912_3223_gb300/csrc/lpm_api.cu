@@ -100,7 +100,7 @@ struct lpm_ctx {
     bool tables_dirty = true;
     long long k = 0;                        // steps taken
     long long n_bins = 0;                   // snapshots taken
-    int block = 256, ppt = 1, occ = 2;
+    int block = 512, ppt = 1, occ = 2;
 
     // sorting by weather cell (both forms) at the multiples of sort_every: d_state is the
     // home buffer (slot order of the API); the live particles released before sorted_upto
