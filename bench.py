@@ -41,12 +41,12 @@ OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
 # DRAM traffic per advance launch from the ncu capture summarised in
 # profiles/advance_kernel_plain_1e7x2880.md (mean of the two captured 60-step launches of
 # hours 6-7, read + write), valid while the kernel sources hash to the values recorded there.
-ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.399232 + 0.000512) + (23.884800 + 0.009984)) * 1e6
-ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "c4344a6f", "lpm_device.cuh": "f5cb88b5"}
+ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.396672 + 0.000512) + (23.878656 + 0.006912)) * 1e6
+ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "23c5cd48", "lpm_device.cuh": "f5cb88b5"}
 # Busiest hardware units of the same capture (% of peak, mean of the two launches): the
 # L1 data pipe carrying the weather gathers, and the warp-instruction issue slots.
-ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (82.82 + 82.20) / 100.0,
-                         "issue_slots": 0.5 * (74.84 + 74.95) / 100.0}
+ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (78.13 + 78.82) / 100.0,
+                         "issue_slots": 0.5 * (76.37 + 76.27) / 100.0}
 SM_COUNT = 152
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
 SM_MAX_MHZ = 2070.0
