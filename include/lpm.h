@@ -375,7 +375,10 @@ lpm_status lpm_adjoint(lpm_ctx *ctx, const double *receptors, int R, double band
  * Storage of the receptor forward's states for lpm_adjoint. The forward keeps the whole
  * trajectory (16 B per particle and step, from the first release step of each block of
  * 128 particles on, plus 16 B per particle) when that is at most max_bytes and leaves
- * 8 GiB of device memory free; the backward then reads the states back in reverse.
+ * 8 GiB of device memory free; the backward then reads the states back in reverse. With
+ * one scenario and sorting on (lpm_set_sort > 0, the default) the trajectory is kept in
+ * 64-step segments over the particles re-sorted by weather cell at each segment start
+ * (about the same size); otherwise in release order.
  * Otherwise, and always with max_bytes = 0, it keeps a checkpoint every 64 steps (16 B per
  * particle each) and the backward recomputes each 64-step segment from its checkpoint.
  * Both give the same gradients up to the order of the FP64 sums. Default 128 GiB. Drops
