@@ -126,10 +126,10 @@ template <bool TRAJ>
 __global__ void __launch_bounds__(ADJ_BLOCK, 8)
 adj_forward_kernel(const StepParams P, const AdjParams A)
 {
-    __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_forward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_C = reinterpret_cast<double *>(s_rec + A.R);    // [R]
+    unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_C + A.R);   // [n_lut]
     __shared__ float2 s_zi[MAX_LEVELS];            // warps span many levels here
     const LevelsS LV = load_levels_smem(P, s_zi, s_lut);
     for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
@@ -315,12 +315,12 @@ template <bool KHG>
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_backward_kernel(const StepParams P, const AdjParams A)
 {
-    __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
     double *s_gq = s_g + 6;                       // [nq]
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
+    unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_w + A.R);   // [n_lut]
     __shared__ float2 s_zi[MAX_LEVELS];            // warps span many levels here
     const LevelsS LV = load_levels_smem(P, s_zi, s_lut);
     const Tile tile = A.tiles[blockIdx.x];
@@ -393,12 +393,12 @@ template <bool KHG>
 __global__ void __launch_bounds__(ADJ_BLOCK)
 adj_backward_traj_kernel(const StepParams P, const AdjParams A)
 {
-    __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
     double *s_gq = s_g + 6;                       // [nq]
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
+    unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_w + A.R);   // [n_lut]
     __shared__ float2 s_zi[MAX_LEVELS];            // warps span many levels here
     const LevelsS LV = load_levels_smem(P, s_zi, s_lut);
     const Tile tile = A.tiles[blockIdx.x];
@@ -442,17 +442,19 @@ adj_backward_traj_kernel(const StepParams P, const AdjParams A)
     reduce_gradient(A, tile, J, valid, qidx, s_g, s_gq);
 }
 
-// Dynamic shared memory of the kernels, sized by the receptors and the emission series
+// Dynamic shared memory of the kernels, sized by the receptors, the emission series and the
+// level table
 // (small arrays keep the shared-memory carve-out small and leave the rest of the SM's
 // unified L1 to the weather gathers).
-static size_t adj_smem_forward(const AdjParams &A)
+static size_t adj_smem_forward(const StepParams &P, const AdjParams &A)
 {
-    return (size_t)A.R * (sizeof(float4) + sizeof(double));
+    return (size_t)A.R * (sizeof(float4) + sizeof(double)) + (size_t)P.n_lut;
 }
 
-static size_t adj_smem_backward(const AdjParams &A)
+static size_t adj_smem_backward(const StepParams &P, const AdjParams &A)
 {
-    return (size_t)A.R * (sizeof(float4) + sizeof(float)) + (size_t)(6 + A.nq) * sizeof(double);
+    return (size_t)A.R * (sizeof(float4) + sizeof(float)) + (size_t)(6 + A.nq) * sizeof(double) +
+           (size_t)P.n_lut;
 }
 
 // ---------------------------------------------------------------------------------
@@ -482,10 +484,10 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     const bool from_a = (int)blockIdx.x < G.tiles_a;
     const unsigned int live = from_a ? *G.live : 0u;
     if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
-    __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_forward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_C = reinterpret_cast<double *>(s_rec + A.R);    // [R]
+    unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_C + A.R);   // [n_lut]
     const Levels LV = load_levels(P, s_lut);
     for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
         s_rec[r] = A.rec[r];
@@ -551,12 +553,12 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     const bool from_a = (int)blockIdx.x < G.tiles_a;
     const unsigned int live = from_a ? *G.live : 0u;
     if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
-    __shared__ unsigned char s_lut[MAX_LUT];
     extern __shared__ float4 s_dyn[];             // sized by the launch: adj_smem_backward
     float4 *s_rec = s_dyn;                        // [R]
     double *s_g = reinterpret_cast<double *>(s_rec + A.R);    // [6]
     double *s_gq = s_g + 6;                       // [nq]
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
+    unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_w + A.R);   // [n_lut]
     const Levels LV = load_levels(P, s_lut);
     const Tile tile0{0, 0, 0};
     load_receptors(A, tile0, s_rec, s_w, s_g, s_gq);
@@ -634,7 +636,7 @@ cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const Ad
 {
     if (n_blocks <= 0) return cudaSuccess;
     adj_prefer_l1();
-    adj_forward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A, G);
+    adj_forward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_forward(P, A), s>>>(P, A, G);
     return cudaGetLastError();
 }
 
@@ -644,9 +646,9 @@ cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const A
     if (n_blocks <= 0) return cudaSuccess;
     adj_prefer_l1();
     if (P.khpair)
-        adj_backward_seg_kernel<true><<<n_blocks, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A, G);
+        adj_backward_seg_kernel<true><<<n_blocks, ADJ_BLOCK, adj_smem_backward(P, A), s>>>(P, A, G);
     else
-        adj_backward_seg_kernel<false><<<n_blocks, ADJ_BLOCK, adj_smem_backward(A), s>>>(P, A, G);
+        adj_backward_seg_kernel<false><<<n_blocks, ADJ_BLOCK, adj_smem_backward(P, A), s>>>(P, A, G);
     return cudaGetLastError();
 }
 
@@ -655,9 +657,9 @@ cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjPar
     if (n_tiles <= 0) return cudaSuccess;
     adj_prefer_l1();
     if (A.traj)
-        adj_forward_kernel<true><<<n_tiles, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A);
+        adj_forward_kernel<true><<<n_tiles, ADJ_BLOCK, adj_smem_forward(P, A), s>>>(P, A);
     else
-        adj_forward_kernel<false><<<n_tiles, ADJ_BLOCK, adj_smem_forward(A), s>>>(P, A);
+        adj_forward_kernel<false><<<n_tiles, ADJ_BLOCK, adj_smem_forward(P, A), s>>>(P, A);
     return cudaGetLastError();
 }
 
@@ -666,7 +668,7 @@ cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjPa
     if (n_tiles <= 0) return cudaSuccess;
     adj_prefer_l1();
     // (the release-order sweep measured faster with the gridded-K_h branch kept at run time)
-    const size_t sm = adj_smem_backward(A);
+    const size_t sm = adj_smem_backward(P, A);
     if (A.traj)
         adj_backward_traj_kernel<true><<<n_tiles, ADJ_BLOCK, sm, s>>>(P, A);
     else if (P.khpair)
