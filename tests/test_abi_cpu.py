@@ -100,3 +100,29 @@ def test_oracle_and_cuda_path_share_no_code():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lpm_oracle" not in text, f
+
+
+def test_context_calls_reject_a_null_context(lib):
+    """Every context call checks its context before touching the device: NULL gives
+    LPM_E_INVALID (here, with no GPU, any CUDA call would fail differently)."""
+    vp = C.c_void_p(None)
+    i64 = C.c_int64
+    calls = [
+        lambda: lib.lpm_step(vp, i64(1)),
+        lambda: lib.lpm_reset(vp),
+        lambda: lib.lpm_sync(vp),
+        lambda: lib.lpm_set_sort(vp, 60),
+        lambda: lib.lpm_set_launch(vp, 512, 1, 2),
+        lambda: lib.lpm_set_params(vp, 1.0, 0.0, 0.0),
+        lambda: lib.lpm_set_profiling(vp, 1),
+        lambda: lib.lpm_set_dosage(vp, 4),
+        lambda: lib.lpm_set_langevin(vp, 1, 100.0),
+        lambda: lib.lpm_set_adjoint_storage(vp, 0),
+        lambda: lib.lpm_adjoint_storage(vp, C.byref(C.c_int()), C.byref(C.c_uint64())),
+        lambda: lib.lpm_concentration(vp, 0, None, 0),
+        lambda: lib.lpm_deposition(vp, 0, None, None, 0),
+        lambda: lib.lpm_budget(vp, 0, (C.c_double * 8)()),
+        lambda: lib.lpm_current_step(vp, C.byref(i64())),
+    ]
+    for call in calls:
+        assert call() == lpm.LPM_E_INVALID
