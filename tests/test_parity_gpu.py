@@ -363,3 +363,19 @@ def test_met_from_pinned_host_memory_overlaps_and_matches():
             xyz, tag = sim.particles()
             assert np.array_equal(xyz.astype(np.float64), ref["pos"]) and np.array_equal(tag, ref["tag"])
             assert np.array_equal(sim.fixed_state()[0], ref["conc_fixed"])
+
+
+def test_level_bisection_path_matches_oracle():
+    """Levels whose smallest spacing would need more than 4096 table bins (a 3 mm first
+    layer) take the bisection path of the vertical cell search; realistic weather, 360
+    steps, against the oracle with the same exclusions as the table path."""
+    cfg = li.make_cfg1(n_particles=5000, n_steps=360)
+    z = np.array(cfg.z_levels, dtype=np.float64)
+    z[1] = 0.003
+    cfg = dataclasses.replace(cfg, z_levels=z)
+    g = run_gpu(cfg, n_run=360)
+    o = oracle.run(cfg, n_run=360)
+    sens = oracle.sensitivity(cfg, n_run=360)
+    rep = compare(cfg, g, o, check_grid=False, sens=sens)
+    print("bisection levels, 360 steps:", rep)
+    np.testing.assert_allclose(g["budget"][0], o["budget"][0], rtol=1e-6)
