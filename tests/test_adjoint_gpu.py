@@ -272,3 +272,26 @@ def test_sorted_trajectory_with_late_release_and_partial_segment_matches_oracle(
     np.testing.assert_allclose(g[:3], ref[:3], atol=0.01 * np.abs(ref[:3]).max())
     np.testing.assert_allclose(g[3:27], ref[3:27], rtol=1e-3, atol=1e-6 * np.abs(ref[3:27]).max())
     np.testing.assert_allclose(g[27:], ref[27:], atol=0.01 * np.abs(ref[27:]).max())
+
+
+def test_adjoint_with_gridded_kh_matches_oracle_in_every_storage_form():
+    """A gridded K_h field brings its spatial gradient into the transposed Jacobian (the
+    sqrt(K_h) derivative of the horizontal displacement): the cell-sorted trajectory, the
+    release-order trajectory and the checkpoint forms against the oracle."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg, rec = _realistic(n=3000, steps=360)
+    rng = np.random.default_rng(21)
+    kh = (60.0 + 80.0 * rng.random(cfg.uvwk.shape[:-1])).astype(np.float32)
+    cfg = dataclasses.replace(cfg, kh=kh, kh_uniform=-1.0)
+    w = np.linspace(-1.0, 1.0, rec.shape[0])
+    ref = oracle.adjoint(cfg, rec, SIGMA, 18, w)
+    assert np.abs(ref[27:28]).max() > 0
+    for limit, sort in ((1 << 37, 60), (1 << 37, 0), (0, 60)):
+        with Sim(cfg) as sim:
+            lpm.lpm_set_sort(sim.ctx, sort)
+            lpm.lpm_set_adjoint_storage(sim.ctx, limit)
+            g = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, w[None, :], 24)[0]
+        np.testing.assert_allclose(g[:3], ref[:3], atol=0.01 * np.abs(ref[:3]).max())
+        np.testing.assert_allclose(g[3:27], ref[3:27], rtol=1e-3,
+                                   atol=1e-6 * np.abs(ref[3:27]).max())
+        np.testing.assert_allclose(g[27:], ref[27:], atol=0.01 * np.abs(ref[27:]).max())
