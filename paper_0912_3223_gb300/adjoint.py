@@ -1,7 +1,8 @@
 """Differentiable receptor concentrations (torch.autograd.Function over the C ABI).
 
 Forward: ``lpm_receptors`` (Gaussian-kernel receptor concentrations of every scenario,
-with 64-step checkpoints). Backward: ``lpm_adjoint`` (hand-written reverse sweep of the
+keeping the states the backward needs: the whole trajectory, or 64-step checkpoints when
+it does not fit). Backward: ``lpm_adjoint`` (hand-written reverse sweep of the
 particle step with common random numbers and frozen events). Parameters per scenario:
 the source (x_s, y_s, h) and the emission series q; shared: the diffusivity scale s_K
 and the wind bias (b_u, b_v).
