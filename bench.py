@@ -240,8 +240,9 @@ def measure_batched(args, stream, cfg=None):
 
 def measure_adjoint(args, stream):
     """The adjoint form: 1e6 particles, 6 h at dt = 20 s on the realistic met, 64 receptors
-    (Gaussian kernel, 200 m), sampled every 18 steps; forward (receptors + checkpoints every
-    64 steps) and backward (segment recomputation + reverse sweep) per run."""
+    (Gaussian kernel, 200 m), sampled every 18 steps; forward (receptors, keeping the states
+    the backward needs: the cell-sorted trajectory by default) and backward (reverse sweep)
+    per run."""
     import numpy as np
     import torch
 

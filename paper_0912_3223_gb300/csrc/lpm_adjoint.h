@@ -5,7 +5,7 @@
 
 namespace lpm {
 
-constexpr int CK = 64;                // checkpoint interval (steps)
+constexpr int CK = 64;                // segment length: checkpoint interval, sorted segments
 constexpr int ADJ_BLOCK = 128;
 constexpr int MAX_REC = 256;
 constexpr int MAX_NQ = 64;

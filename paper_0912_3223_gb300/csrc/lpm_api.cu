@@ -178,7 +178,7 @@ struct lpm_ctx {
     Tile *d_adj_tiles = nullptr;
     std::vector<Tile> adj_tiles;
     bool adj_tiles_valid = false;
-    std::vector<double> adj_sig;            // signature of the forward whose checkpoints are held
+    std::vector<double> adj_sig;            // signature of the forward whose states are held
     long long params_version = 0;
 
     // batched form: one CUDA graph per lpm_step call (sorts, memsets, persistent launches),
@@ -2259,7 +2259,7 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     StepParams P;
     lpm_status st;
     if (c->adj_sig != adj_signature(c, rec, R, bandwidth, sample_every)) {
-        st = adj_forward(c, rec, R, bandwidth, sample_every, A, P);   // checkpoints
+        st = adj_forward(c, rec, R, bandwidth, sample_every, A, P);   // states for the sweep
     } else {
         st = adj_prepare(c, rec, R, bandwidth, sample_every, A, P, true);
     }
