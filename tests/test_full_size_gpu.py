@@ -1,7 +1,9 @@
 """Parity at the full sizes of the benchmark workloads, in the benchmark's launch
-configuration (256 threads x 1 particle, 64 registers, sorted by cell every 60 steps):
+configuration (512 threads x 1 particle, 64 registers, sorted by cell every 60 steps):
 deterministic samples of particles recomputed one by one by the oracle, and properties
 that hold at any size where the output sums over every particle."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -120,3 +122,40 @@ def test_adjoint_full_size_properties():
     fd = np.array(fd)
     print("full-size adjoint source gradient", g[:2], "central differences", fd)
     np.testing.assert_allclose(g[:2], fd, atol=2e-2 * np.abs(fd).max(), rtol=5e-2)
+
+
+def test_kz_eq3_full_size_sampled():
+    """The benchmark's Eq. 3 form (K_z computed in the step from hourly boundary-layer
+    columns) at its full size, 1e7 particles: a sample recomputed by the oracle after 360
+    steps."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_cfg1(kz_eq3=True)
+    sel = np.arange(0, cfg.n_particles, 9973, dtype=np.int64)
+    with Sim(cfg) as sim:
+        sim.step(360)
+        xyz, tag = sim.particles()
+    assert _check_sample(cfg, xyz[sel], tag[sel], sel, 360, "Eq. 3 K_z, 1e7 sample") > 100
+
+
+def test_langevin_full_size_sampled():
+    """The benchmark's vertical Langevin form (T_L = 100 s) at its full size: a sample
+    recomputed by the oracle after 360 steps, positions and turbulent velocities (the
+    velocity memory leaves no path chaotic, so none is excluded as such)."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = dataclasses.replace(li.make_cfg1(), langevin=1, t_lagr=100.0)
+    sel = np.arange(0, cfg.n_particles, 9973, dtype=np.int64)
+    with Sim(cfg) as sim:
+        sim.step(360)
+        xyz, tag = sim.particles()
+        w = sim.velocity()
+    o = oracle.run(cfg, sel=sel, n_run=360)
+    released = o["status"] != li.STATUS_UNRELEASED
+    ok = released & (o["margin"] >= POS_TOL_M)
+    assert ok.sum() > 100
+    st = (tag[sel] >> 28).astype(np.int32)
+    assert np.array_equal(st[ok], o["status"][ok])
+    d = np.linalg.norm(xyz[sel].astype(np.float64)[ok] - o["pos"][ok], axis=1)
+    print(f"Langevin, 1e7 sample: {ok.sum()} particles, max {d.max():.3g} m")
+    assert d.max() <= POS_TOL_M
+    act = ok & (o["status"] == 0)
+    np.testing.assert_allclose(w[sel][act], o["wvel"][act], atol=1e-3)
