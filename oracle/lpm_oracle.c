@@ -13,9 +13,7 @@
  * turbulent diffusion, test dry then wet deposition; every n-th step sum the decayed
  * masses on a rectangular grid.
  *
- * Parity status of each function is stated at the function. Philox4x32-10 carries no
- * published known-answer vector in this tree; it is pinned by statistical and structural
- * properties only (see the philox comment).
+ * Parity status of each function is stated at the function.
  */
 #include <math.h>
 #include <stdint.h>
@@ -36,7 +34,9 @@
  * words and the round key; the key advances by the Weyl constants W0, W1 between rounds.
  * It replaces the paper's Mersenne Twister (Sec. 2, Sec. 3.2) so that a realisation is
  * a pure function of (seed, particle, step).
- * Parity: pinned by properties (uniformity, avalanche, stream independence), no KAT.
+ * Parity: pinned by bit identity with an independent implementation of the same generator
+ * (Triton's tl.philox, run by its CPU interpreter) over edge and random counters and full
+ * 64-bit seeds, and by properties (uniformity, avalanche, stream independence).
  * ------------------------------------------------------------------------------- */
 #define PHILOX_M0 0xD2511F53u
 #define PHILOX_M1 0xCD9E8D57u

@@ -61,6 +61,67 @@ def test_philox_avalanche_counter_and_key():
             assert abs(frac.mean() - 0.5) < 0.01
 
 
+_TRITON_PHILOX = r"""
+import json, sys
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def philox_rows(seed, ctr_ptr, out_ptr, N: tl.constexpr):
+    i = tl.arange(0, N)
+    r0, r1, r2, r3 = tl.philox(seed, tl.load(ctr_ptr + 4 * i), tl.load(ctr_ptr + 4 * i + 1),
+                               tl.load(ctr_ptr + 4 * i + 2), tl.load(ctr_ptr + 4 * i + 3))
+    tl.store(out_ptr + 4 * i, r0)
+    tl.store(out_ptr + 4 * i + 1, r1)
+    tl.store(out_ptr + 4 * i + 2, r2)
+    tl.store(out_ptr + 4 * i + 3, r3)
+
+res = []
+for seed, ctr in json.load(sys.stdin):
+    ctr = np.ascontiguousarray(np.array(ctr, dtype=np.uint32))
+    out = torch.empty(ctr.shape, dtype=torch.int32)
+    philox_rows[(1,)](seed, torch.from_numpy(ctr.view(np.int32)), out, N=ctr.shape[0])
+    res.append(out.numpy().view(np.uint32).tolist())
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_an_independent_library_implementation():
+    """Bit identity with Triton's own Philox4x32-10 (``tl.philox``, 10 rounds, key = the
+    seed's low and high 32-bit halves), run by Triton's CPU interpreter in a child process
+    (the interpreter must be chosen before Triton is imported): a second implementation of
+    the SC'11 generator written by other people. Catches swapped multipliers or Weyl
+    constants, a wrong round count, swapped key halves, a word permutation in the round and
+    a dropped high or low product half, none of which the statistical pins above need to
+    see."""
+    pytest.importorskip("triton")
+    import json
+    import os
+    import subprocess
+    import sys
+
+    n = 64
+    edge = np.array([[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 0, 0, 0], [0, 0, 0, 1]], np.uint32)
+    rand = np.random.default_rng(3).integers(0, 2 ** 32, (n - len(edge), 4), dtype=np.uint64)
+    ctr = np.vstack([edge, rand.astype(np.uint32)])
+    seeds = (0, 1, 7, 0x0123456789ABCDEF, (1 << 63) - 1, (1 << 64) - 1)
+    # the particle draw puts (particle id low, high, step, stream) in the counter
+    pid = np.array([0, 1, 123456789, (1 << 40) + 5], dtype=np.uint64)
+    draw_seed, step, stream = 0x0123456789ABCDEF, 77, 1
+    draw_ctr = np.stack([pid & 0xFFFFFFFF, pid >> 32, np.full(4, step), np.full(4, stream)],
+                        1).astype(np.uint32)
+    jobs = [[s, ctr.tolist()] for s in seeds] + [[draw_seed, draw_ctr.tolist()]]
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    run = subprocess.run([sys.executable, "-c", _TRITON_PHILOX], input=json.dumps(jobs),
+                         capture_output=True, text=True, env=env, timeout=300)
+    assert run.returncode == 0, run.stderr[-2000:]
+    lib = [np.array(r, dtype=np.uint32) for r in json.loads(run.stdout.splitlines()[-1])]
+    for seed, got in zip(seeds, lib):
+        ours = np.array([oracle.philox([seed & 0xFFFFFFFF, seed >> 32], c) for c in ctr],
+                        dtype=np.uint32)
+        np.testing.assert_array_equal(ours, got, err_msg=hex(seed))
+    np.testing.assert_array_equal(oracle.draws(draw_seed, pid, step, stream), lib[-1])
+
+
 def test_philox_no_collisions_and_streams_independent():
     """Distinct counters give distinct outputs (the round is a bijection), and the
     deposition stream is uncorrelated with the displacement stream."""
