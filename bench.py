@@ -102,10 +102,17 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the timed region starts once the sampler has written its first row (bounded wait)
+        t_end = time.monotonic() + 3.0
+        while time.monotonic() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -155,7 +162,7 @@ def oracle_sample(cfg, stride: int):
     return r["active_steps"], dt, sel.size
 
 
-def cpu_baseline(cfg, stride: int = 100):
+def cpu_baseline(cfg, stride: int = 30):
     steps, dt, n = oracle_sample(cfg, stride)
     return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"every {stride}th particle ({n} particles) of the workload, all "
@@ -641,7 +648,7 @@ def run_gpu(args):
             f["vs_plain"] = f["value"] / value
         line["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg, args.ref_stride)
+        line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_stride)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -660,7 +667,11 @@ def main():
     ap.add_argument("--occ", type=int, default=2)
     ap.add_argument("--sort-every", type=int, default=60,
                     help="re-order the particles by weather cell every N steps (0 = off)")
-    ap.add_argument("--ref-stride", type=int, default=100)
+    ap.add_argument("--ref-stride", type=int, default=100,
+                    help="particle sample stride of each --impl reference step")
+    ap.add_argument("--cpu-stride", type=int, default=30,
+                    help="particle sample stride of the cpu_baseline leg (about 10-20 s of oracle "
+                         "work on one core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms")
