@@ -559,6 +559,8 @@ def run_gpu(args):
         _, _, ctr, _ = sim.fixed_state()
         active.append(int(ctr[4]))
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
     launches, adv_launches, adv_ms = lpm.lpm_stats(sim.ctx)
     lpm.lpm_set_profiling(sim.ctx, False)
@@ -583,6 +585,8 @@ def run_gpu(args):
     e2e_t, e2e_p = 0.0, 0
     for i in range(max(1, args.warmup) + args.steps):   # warm-up passes first, untimed
         torch.cuda.synchronize()
+        if world > 1 and i == max(1, args.warmup):
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         for t in range(cfg.n_met_t):
             lpm.lpm_set_met(sim.ctx, t, pinned_uvwk[t], None, pinned_rain[t])
@@ -595,6 +599,13 @@ def run_gpu(args):
         e2e_t += time.perf_counter() - t0
         _, _, ctr, _ = sim.fixed_state()
         e2e_p += int(ctr[4])
+    if world > 1:                                # whole job: max time, summed work
+        import torch.distributed as dist
+        t = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p = torch.tensor([e2e_p], dtype=torch.float64, device="cuda")
+        dist.all_reduce(p)
+        e2e_t, e2e_p = float(t.item()), int(p.item())
     e2e_value = e2e_p / e2e_t
 
     sim.close()
@@ -645,8 +656,10 @@ def run_gpu(args):
         if not args.no_stress:
             forms["stress"] = measure_stress(args, stream)
         for f in forms.values():
-            f["vs_plain"] = f["value"] / value
+            f["vs_plain"] = f["value"] / value * world   # both per GPU
         line["forms"] = forms
+        if world > 1:
+            line["forms_scope"] = "rank 0's GPU"
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_stride)
     if rank == 0:
