@@ -6,6 +6,15 @@ draws the same keyed random numbers as a single run would, and bins with the sca
 the whole release. The only exchange is an integer sum of the fixed-point grids and
 counters, which is associative, so the reduced result is bit-identical to the
 single-context run whatever the rank count or reduction order.
+
+The receptor concentrations and the adjoint's parameter gradients are FP64 sums over
+particles, so a partitioned run adds the ranks' partial sums. They are exchanged in fixed
+point as well: each element is scaled by a power of two fitted to the largest magnitude of
+that element over the ranks (a MAX reduction), rounded to int64, summed as integers and
+scaled back, so the reduced value does not depend on the order in which ranks are added.
+For a loss that is not linear in the concentrations, the receptor sums are reduced first,
+every rank forms the same dL/dC from them, and the gradients taken with it are reduced
+second.
 """
 from __future__ import annotations
 
@@ -38,3 +47,74 @@ def allreduce_fixed(values: np.ndarray, group=None, device=None) -> np.ndarray:
         t = t.to(device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.cpu().numpy().view(a.dtype).reshape(a.shape)
+
+
+FIXED_BITS = 62          # |reduced sum| * 2^scale stays below 2^62 whatever the rank count
+
+
+def fixed_exponents(max_abs: np.ndarray, world: int) -> np.ndarray:
+    """Per-element power-of-two exponent e such that world * max_abs * 2^e <= 2^FIXED_BITS
+    (0 where the element is zero on every rank)."""
+    m = np.asarray(max_abs, dtype=np.float64)
+    if not np.all(np.isfinite(m)):
+        raise ValueError("non-finite value in a fixed-point reduction")
+    bound = m * world
+    e = np.zeros(m.shape, dtype=np.int64)
+    nz = bound > 0
+    e[nz] = FIXED_BITS - np.ceil(np.log2(bound[nz])).astype(np.int64)
+    return e
+
+
+def to_fixed(values: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """round(values * 2^e) as int64 (exact scaling by a power of two, one rounding)."""
+    return np.rint(np.ldexp(np.asarray(values, dtype=np.float64), e)).astype(np.int64)
+
+
+def from_fixed(q: np.ndarray, e: np.ndarray) -> np.ndarray:
+    return np.ldexp(np.asarray(q, dtype=np.int64).astype(np.float64), -e)
+
+
+def sum_float_fixed(parts) -> np.ndarray:
+    """The fixed-point sum of FP64 partial arrays held by one process (one per partition),
+    with the same arithmetic as ``allreduce_float_fixed`` over that many ranks."""
+    parts = [np.asarray(p, dtype=np.float64) for p in parts]
+    e = fixed_exponents(np.max(np.abs(np.stack(parts)), axis=0), len(parts))
+    return from_fixed(np.sum(np.stack([to_fixed(p, e) for p in parts]), axis=0), e)
+
+
+def allreduce_float_fixed(values: np.ndarray, group=None, device=None) -> np.ndarray:
+    """Sum over all ranks of an FP64 array, reduced in fixed point: a MAX reduction of the
+    magnitudes fixes each element's scale, then an int64 SUM reduction adds the rounded
+    values; the result is independent of the reduction order."""
+    import torch
+    import torch.distributed as dist
+    a = np.ascontiguousarray(values, dtype=np.float64)
+    world = dist.get_world_size(group)
+    m = torch.from_numpy(np.abs(a).copy())
+    if device is not None:
+        m = m.to(device)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX, group=group)
+    e = fixed_exponents(m.cpu().numpy(), world)
+    q = torch.from_numpy(to_fixed(a, e))
+    if device is not None:
+        q = q.to(device)
+    dist.all_reduce(q, op=dist.ReduceOp.SUM, group=group)
+    return from_fixed(q.cpu().numpy(), e)
+
+
+def receptors_partitioned(sim, receptors, bandwidth: float, sample_every: int, group=None,
+                          device=None) -> np.ndarray:
+    """Receptor concentrations [n_scenarios][R] of the whole release, from each rank's
+    context holding its particle range."""
+    from . import lpm
+    c = lpm.lpm_receptors(sim.ctx, sim.cfg.n_scenarios, receptors, bandwidth, sample_every)
+    return allreduce_float_fixed(c, group, device)
+
+
+def adjoint_partitioned(sim, receptors, bandwidth: float, sample_every: int, dL_dC, n_q: int,
+                        group=None, device=None) -> np.ndarray:
+    """Gradient [n_scenarios][3 + n_q + 3] of sum(dL_dC * C) for the whole release; dL_dC
+    must be the same on every rank (formed from ``receptors_partitioned``)."""
+    from . import lpm
+    g = lpm.lpm_adjoint(sim.ctx, receptors, bandwidth, sample_every, dL_dC, n_q)
+    return allreduce_float_fixed(g, group, device)

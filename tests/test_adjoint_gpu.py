@@ -320,3 +320,35 @@ def test_batched_adjoint_matches_oracle_per_scenario():
                                    atol=1e-6 * np.abs(ref[3:27]).max())
         np.testing.assert_allclose(g[s, 27:], ref[27:], atol=0.01 * np.abs(ref[27:]).max())
     assert seen >= 1
+
+
+def test_partitioned_receptors_and_adjoint_sum_to_single_context():
+    """Three contexts holding disjoint particle ranges of one release, run one after
+    another on this GPU as the ranks of a partitioned run would: their receptor sums, and
+    their gradients of a misfit whose dL/dC is formed from the summed concentrations, add
+    up in fixed point to the single-context values (the per-particle arithmetic is the
+    same; only the FP64 summation order differs)."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    from paper_0912_3223_gb300.parallel import partition, sum_float_fixed
+    cfg, rec = _realistic(n=3001, steps=360)
+    nq = cfg.release.q.size
+    parts_c = []
+    for r in range(3):
+        with Sim(cfg, part=partition(cfg.n_particles, 3, r)) as sim:
+            parts_c.append(lpm.lpm_receptors(sim.ctx, 1, rec, SIGMA, 18))
+    c = sum_float_fixed(parts_c)
+    w = 2.0 * (c - 0.5 * c)                      # dL/dC of sum (C - C/2)^2
+    parts_g = []
+    for r in range(3):
+        with Sim(cfg, part=partition(cfg.n_particles, 3, r)) as sim:
+            parts_g.append(lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, w, nq))
+    g = sum_float_fixed(parts_g)
+    with Sim(cfg) as sim:
+        c_full = lpm.lpm_receptors(sim.ctx, 1, rec, SIGMA, 18)
+        g_full = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, w, nq)
+    assert np.abs(c_full).max() > 0 and np.abs(g_full).max() > 0
+    dc = np.abs(c - c_full).max() / np.abs(c_full).max()
+    dg = np.abs(g - g_full).max() / np.abs(g_full).max()
+    print(f"partitioned vs single context: receptors {dc:.2e}, gradient {dg:.2e}")
+    np.testing.assert_allclose(c, c_full, rtol=1e-12, atol=1e-14 * np.abs(c_full).max())
+    np.testing.assert_allclose(g, g_full, rtol=1e-12, atol=1e-14 * np.abs(g_full).max())
