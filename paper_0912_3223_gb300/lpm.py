@@ -456,13 +456,32 @@ def lpm_draws_static(seed: int, pid, step, stream: int = 0):
 # ------------------------------------------------------------------------------------
 class Sim:
     """One context set up from an ``lpm_inputs.LpmConfig``: met uploaded, sources set,
-    releases declared. ``stream`` is a torch.cuda.Stream (default: current stream)."""
+    releases declared. ``stream`` is a torch.cuda.Stream (default: current stream).
+    ``part = (first, count)`` holds that particle range of a single release;
+    ``scenarios = (first, count)`` holds that range of an ensemble's scenarios (local
+    scenario i is ensemble scenario first + i) with the ensemble's global particle ids, so
+    each held scenario draws the same random numbers as in the whole ensemble."""
 
     def __init__(self, cfg, stream=None, met_on_device: bool = False, launch=None,
-                 part=None, sort_every: Optional[int] = None):
+                 part=None, sort_every: Optional[int] = None, scenarios=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the particle model runs on a CUDA GPU; none is available")
+        self.id_base = None
+        if scenarios is not None:
+            import dataclasses
+            if not cfg.scenarios or part is not None:
+                raise ValueError("a scenario range needs an ensemble and no particle range")
+            first, count = (int(v) for v in scenarios)
+            if first < 0 or count < 1 or first + count > len(cfg.scenarios):
+                raise ValueError(f"scenario range ({first}, {count}) outside the "
+                                 f"{len(cfg.scenarios)} scenarios")
+            ids = [0]
+            for sc in cfg.scenarios:
+                ids.append(ids[-1] + int(sc.release.n_particles))
+            self.id_base = ids[first:first + count]
+            cfg = dataclasses.replace(cfg, n_scenarios=count,
+                                      scenarios=list(cfg.scenarios[first:first + count]))
         self.cfg = cfg
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.part = part
@@ -487,8 +506,12 @@ class Sim:
                     lpm_set_source(self.ctx, i, sc.src_x, sc.src_y, sc.src_z, sc.wind_offset)
                 for i, sc in enumerate(cfg.scenarios):
                     r = sc.release
-                    lpm_release(self.ctx, i, r.n_particles, r.q, r.q_dt, r.first_step,
-                                r.last_step)
+                    if self.id_base is None:
+                        lpm_release(self.ctx, i, r.n_particles, r.q, r.q_dt, r.first_step,
+                                    r.last_step)
+                    else:
+                        lpm_release_range(self.ctx, i, r.n_particles, 0, r.n_particles, r.q,
+                                          r.q_dt, r.first_step, r.last_step, self.id_base[i])
             elif part is not None:
                 r = cfg.release
                 lpm_release_range(self.ctx, 0, r.n_particles, part[0], part[1], r.q, r.q_dt,

@@ -5,7 +5,10 @@ id ranges, one per rank; each rank's context holds its range (``lpm_release_rang
 draws the same keyed random numbers as a single run would, and bins with the scale of
 the whole release. The only exchange is an integer sum of the fixed-point grids and
 counters, which is associative, so the reduced result is bit-identical to the
-single-context run whatever the rank count or reduction order.
+single-context run whatever the rank count or reduction order. A batched ensemble
+shards by scenario instead: ``partition(n_scenarios, world, rank)`` gives each rank a
+contiguous scenario range (``Sim(cfg, scenarios=...)``, global particle ids kept), whose
+grids are final without any exchange.
 
 The receptor concentrations and the adjoint's parameter gradients are FP64 sums over
 particles, so a partitioned run adds the ranks' partial sums. They are exchanged in fixed
@@ -24,8 +27,8 @@ import numpy as np
 
 
 def partition(n_total: int, world: int, rank: int) -> Tuple[int, int]:
-    """Contiguous range [first, first + count) of ``n_total`` ids held by ``rank``;
-    range sizes differ by at most one."""
+    """Contiguous range [first, first + count) of ``n_total`` ids (particles, or the
+    scenarios of an ensemble) held by ``rank``; range sizes differ by at most one."""
     if world < 1 or not 0 <= rank < world:
         raise ValueError(f"rank {rank} outside world of {world}")
     if n_total < world:
