@@ -159,3 +159,55 @@ def test_langevin_full_size_sampled():
     assert d.max() <= POS_TOL_M
     act = ok & (o["status"] == 0)
     np.testing.assert_allclose(w[sel][act], o["wvel"][act], atol=1e-3)
+
+
+def test_dosage_full_size_sum_of_snapshots_and_sampled():
+    """The benchmark's dosage form at its full size, 1e7 particles sampled every 4 steps,
+    with the concentration snapshot taken on the same steps: after each 4-step piece the
+    integer snapshot is added up on the host. The dosage keeps b = ceil(log2(720)) = 10
+    bits fewer than the snapshots (720 samples in the 2880-step run), so each (sample,
+    particle) term of a cell differs from the snapshots' by at most 2^(b-1) + 1/2 units:
+    after 360 steps the L1 distance between the dosage grid x 2^b and the sum of the
+    snapshots, and the gap between the out-of-grid counters, stay within that many units
+    per term (about 5e-8 of the total; a sample one step off moves the total by 3e-5, a
+    wrong cell index moves whole cells). A particle sample against the oracle."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = dataclasses.replace(li.make_cfg1(), bin_every=4)
+    every, n_run = 4, 360
+    b = int(np.ceil(np.log2(cfg.n_steps // every)))
+    acc = np.zeros((cfg.cz, cfg.cy, cfg.cx), dtype=np.float64)
+    out = 0
+    with Sim(cfg) as sim:
+        sim.set_dosage(every)
+        for _ in range(n_run // every):
+            sim.step(every)
+            c, _, k, _ = sim.fixed_state()
+            acc += c.astype(np.float64)
+            out += int(k[0])
+        _, fixed, samples = sim.dosage()
+        dose_out = int(sim.fixed_state()[2][11])
+        xyz, tag = sim.particles()
+    assert samples == n_run // every
+    bound = samples * cfg.n_particles * (2.0 ** (b - 1) + 0.5)
+    total = acc.sum()
+    l1 = np.abs(fixed.astype(np.float64) * 2.0 ** b - acc).sum()
+    print(f"dosage vs summed snapshots: total {total:.4g}, L1 {l1:.3g}, bound {bound:.3g}; "
+          f"out {dose_out * 2 ** b} / {out}")
+    assert total > 1e5 * bound
+    assert l1 <= bound
+    assert abs(dose_out * 2 ** b - out) <= bound
+    sel = np.arange(0, cfg.n_particles, 9973, dtype=np.int64)
+    assert _check_sample(cfg, xyz[sel], tag[sel], sel, n_run, "dosage form, 1e7 sample") > 100
+
+
+def test_decay_chain_full_size_sampled():
+    """The benchmark's decay-chain form (8-day parent, 12-hour daughter, stable end) at
+    its full size, 1e7 particles: a sample recomputed by the oracle after 360 steps."""
+    from paper_0912_3223_gb300 import Sim
+    base = li.make_cfg1()
+    cfg = dataclasses.replace(base, chain_half_lives=np.array([base.half_life_s, 43200.0, 0.0]))
+    sel = np.arange(0, cfg.n_particles, 9973, dtype=np.int64)
+    with Sim(cfg) as sim:
+        sim.step(360)
+        xyz, tag = sim.particles()
+    assert _check_sample(cfg, xyz[sel], tag[sel], sel, 360, "decay chain, 1e7 sample") > 100
