@@ -148,11 +148,13 @@ class _Pinned:
 
 
 def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
-              bias=(0.0, 0.0), src=None, q=None, dose_every: int = 0):
+              bias=(0.0, 0.0), src=None, q=None, dose_every: int = 0,
+              id_offset: Optional[int] = None):
     """Build the C record for one release of ``cfg`` (an ``lpm_inputs.LpmConfig``).
     ``scenario`` selects a member of a batched ensemble (its source, release, global id
     offset and wind offset). ``src``/``q`` override the source and emission series;
-    ``dose_every`` > 0 samples the time-integrated dosage every that many steps."""
+    ``dose_every`` > 0 samples the time-integrated dosage every that many steps;
+    ``id_offset`` sets the global id (generator counter) of the release's particle 0."""
     pin = _Pinned()
     o = OCfg()
     for name in ("nx", "ny", "nz", "n_met_t", "cx", "cy", "cz", "bin_every",
@@ -187,7 +189,7 @@ def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
     o.q_dt = float(rel.q_dt)
     o.first_step = int(rel.first_step)
     o.last_step = int(rel.last_step)
-    o.pid_offset = offset
+    o.pid_offset = offset if id_offset is None else int(id_offset)
     o.k_scale = float(k_scale)
     o.bias_u, o.bias_v = float(bias[0]), float(bias[1])
     o.dose_every = int(dose_every)

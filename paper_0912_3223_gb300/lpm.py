@@ -457,13 +457,15 @@ def lpm_draws_static(seed: int, pid, step, stream: int = 0):
 class Sim:
     """One context set up from an ``lpm_inputs.LpmConfig``: met uploaded, sources set,
     releases declared. ``stream`` is a torch.cuda.Stream (default: current stream).
-    ``part = (first, count)`` holds that particle range of a single release;
+    ``part = (first, count)`` holds that particle range of a single release, and
+    ``id_base`` sets the global id (generator counter) of its particle 0;
     ``scenarios = (first, count)`` holds that range of an ensemble's scenarios (local
     scenario i is ensemble scenario first + i) with the ensemble's global particle ids, so
     each held scenario draws the same random numbers as in the whole ensemble."""
 
     def __init__(self, cfg, stream=None, met_on_device: bool = False, launch=None,
-                 part=None, sort_every: Optional[int] = None, scenarios=None):
+                 part=None, sort_every: Optional[int] = None, scenarios=None,
+                 id_base: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the particle model runs on a CUDA GPU; none is available")
@@ -512,10 +514,11 @@ class Sim:
                     else:
                         lpm_release_range(self.ctx, i, r.n_particles, 0, r.n_particles, r.q,
                                           r.q_dt, r.first_step, r.last_step, self.id_base[i])
-            elif part is not None:
+            elif part is not None or id_base:
                 r = cfg.release
-                lpm_release_range(self.ctx, 0, r.n_particles, part[0], part[1], r.q, r.q_dt,
-                                  r.first_step, r.last_step, 0)
+                first, count = part if part is not None else (0, r.n_particles)
+                lpm_release_range(self.ctx, 0, r.n_particles, first, count, r.q, r.q_dt,
+                                  r.first_step, r.last_step, int(id_base))
             else:
                 r = cfg.release
                 lpm_release(self.ctx, 0, r.n_particles, r.q, r.q_dt, r.first_step, r.last_step)

@@ -48,10 +48,12 @@ def artificial_weather_cfg(n_particles=2160, n_steps=2160, nz=25):
     return cfg
 
 
-def run_gpu(cfg, n_run=None, launch=None, pieces=None, met_on_device=False, sort_every=None):
+def run_gpu(cfg, n_run=None, launch=None, pieces=None, met_on_device=False, sort_every=None,
+            id_base=0):
     from paper_0912_3223_gb300 import Sim
     n_run = cfg.n_steps if n_run is None else n_run
-    sim = Sim(cfg, launch=launch, met_on_device=met_on_device, sort_every=sort_every)
+    sim = Sim(cfg, launch=launch, met_on_device=met_on_device, sort_every=sort_every,
+              id_base=id_base)
     try:
         if pieces:
             for n in pieces:

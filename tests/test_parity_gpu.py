@@ -186,6 +186,20 @@ def test_ragged_and_sparse_releases(n, first, last):
     _integer_identity(g)
 
 
+@pytest.mark.parametrize("id_base", [(1 << 32) - 1000, (1 << 40) + 7])
+def test_particle_ids_beyond_32_bits(id_base):
+    """Global particle ids past 2^32: the generator counter's high word is non-zero (and,
+    for the first base, the release straddles the boundary), yet the particle path still
+    matches the oracle drawing with the same ids, and differs from the ids-from-0 run."""
+    cfg = li.make_cfg1(n_particles=3000, n_steps=240, n_hours=5)
+    g = run_gpu(cfg, id_base=id_base)
+    o = oracle.run(cfg, id_offset=id_base)
+    rep = compare(cfg, g, o, sens=oracle.sensitivity(cfg, id_offset=id_base))
+    print(f"ids from {id_base:#x}:", rep)
+    _integer_identity(g)
+    assert not np.array_equal(run_gpu(cfg)["pos"], g["pos"])
+
+
 def test_gridded_kh_drift_and_emission_series():
     """Gridded K_h, the drift-corrected variant and a 24-value emission series."""
     base = li.make_cfg1(n_particles=5000, n_steps=240, n_hours=5)
