@@ -352,3 +352,32 @@ def test_partitioned_receptors_and_adjoint_sum_to_single_context():
     print(f"partitioned vs single context: receptors {dc:.2e}, gradient {dg:.2e}")
     np.testing.assert_allclose(c, c_full, rtol=1e-12, atol=1e-14 * np.abs(c_full).max())
     np.testing.assert_allclose(g, g_full, rtol=1e-12, atol=1e-14 * np.abs(g_full).max())
+
+
+def test_adjoint_at_the_maximum_receptors_and_emission_values():
+    """256 receptors and a 64-value emission series, the adjoint's limits: receptor
+    concentrations and the gradient against the oracle, emission values after the run with
+    a zero gradient; one receptor or one emission value more is rejected on the host."""
+    from paper_0912_3223_gb300 import lpm
+    rng = np.random.default_rng(21)
+    q = np.exp(rng.normal(0.0, 0.3, 64))
+    cfg = li.make_cfg0(n_particles=3000, n_steps=120)
+    cfg = dataclasses.replace(cfg, release=dataclasses.replace(cfg.release, q=q, q_dt=20.0))
+    xs, ys = np.meshgrid(np.linspace(300.0, 4800.0, 16), np.linspace(-750.0, 750.0, 16))
+    rec = np.stack([xs.ravel(), ys.ravel(), np.full(256, 10.0)], 1)
+    w = rng.normal(size=256)
+    with _sim(cfg) as sim:
+        C = lpm.lpm_receptors(sim.ctx, 1, rec, SIGMA, 10)[0]
+        g = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 10, w[None, :], 64)[0]
+        for bad in (lambda: lpm.lpm_receptors(sim.ctx, 1, np.vstack([rec, rec[:1]]), SIGMA, 10),
+                    lambda: lpm.lpm_set_emission(sim.ctx, 0, np.ones(65))):
+            with pytest.raises(lpm.LpmError) as e:
+                bad()
+            assert e.value.status == lpm.LPM_E_INVALID
+    ref_c = oracle.receptors(cfg, rec, SIGMA, 10)
+    assert np.count_nonzero(ref_c) > 100
+    np.testing.assert_allclose(C, ref_c, rtol=1e-3, atol=1e-4 * np.abs(ref_c).max())
+    ref = oracle.adjoint(cfg, rec, SIGMA, 10, w)
+    np.testing.assert_allclose(g, ref, rtol=1e-3, atol=1e-4 * np.abs(ref).max())
+    assert np.all(g[3 + 60:3 + 64] == 0.0)     # 20 s emission bins after the 1200 s run
+    assert np.all(g[3:3 + 60] != 0.0)
