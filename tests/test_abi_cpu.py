@@ -69,6 +69,7 @@ def test_config_layout_matches_c_header(tmp_path):
     (dict(bin_every=0), "bin_every"),
     (dict(cx=0), "non-empty"),
     (dict(n_steps=0), "n_steps"),
+    (dict(nz=65), "exceeds 64 levels"),
     (dict(vd_dry=0.01, h_mix=0.0), "h_mix"),
     (dict(reflect_top=1, z_top=0.0), "z_top"),
     (dict(n_scenarios=0), "n_scenarios"),

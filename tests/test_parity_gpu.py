@@ -200,6 +200,20 @@ def test_particle_ids_beyond_32_bits(id_base):
     assert not np.array_equal(run_gpu(cfg)["pos"], g["pos"])
 
 
+def test_maximum_levels_match_oracle():
+    """64 stretched levels, the most the kernel parameters carry (the lowest 0.76 m apart,
+    so the level table would need over 4096 bins and the lookup bisects): the realistic
+    run against the oracle."""
+    base = li.make_cfg1(n_particles=3000, n_steps=240, n_hours=5)
+    uvwk, z = li.make_met_realistic(nz=64, n_t=5)
+    cfg = dataclasses.replace(base, nz=64, z_levels=z, uvwk=uvwk)
+    g = run_gpu(cfg)
+    o = oracle.run(cfg)
+    rep = compare(cfg, g, o, sens=oracle.sensitivity(cfg))
+    print("64 levels:", rep)
+    _integer_identity(g)
+
+
 def test_gridded_kh_drift_and_emission_series():
     """Gridded K_h, the drift-corrected variant and a 24-value emission series."""
     base = li.make_cfg1(n_particles=5000, n_steps=240, n_hours=5)
