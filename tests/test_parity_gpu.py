@@ -214,6 +214,29 @@ def test_maximum_levels_match_oracle():
     _integer_identity(g)
 
 
+def test_degenerate_zero_emission_and_stable_tracer():
+    """Two degenerate cases of the method. An all-zero emission series: the particles still
+    move exactly as the oracle's, every grid and budget entry is zero, and the run reports
+    no error. A stable tracer (no decay) with no deposition and no lateral exit: nothing
+    leaves the air, so the airborne mass equals the released mass up to the FP32 storage of
+    the initial masses, and the fixed-point identity holds."""
+    base = li.make_cfg1(n_particles=2000, n_steps=120, n_hours=3)
+    zero = dataclasses.replace(base, release=li.Release(2000, np.zeros(3), 3600.0, 0, 120))
+    g = run_gpu(zero)
+    o = oracle.run(zero)
+    compare(zero, g, o, check_grid=False, sens=oracle.sensitivity(zero))
+    assert not g["conc_fixed"].any() and not g["dep_fixed"].any()
+    assert not np.any(g["budget"][:7])
+    stable = dataclasses.replace(base, half_life_s=0.0, vd_dry=0.0, wet_lambda=0.0,
+                                 lateral_exit=0)
+    g = run_gpu(stable)
+    _integer_identity(g)
+    b = g["budget"]
+    assert b[0] > 0 and b[3] == b[4] == b[5] == 0.0
+    assert abs(b[1] + b[2] - b[0]) <= 1e-6 * b[0] and abs(b[6]) <= 1e-6 * b[0]
+    assert int(b[7]) == 2000                     # every particle released and still airborne
+
+
 def test_gridded_kh_drift_and_emission_series():
     """Gridded K_h, the drift-corrected variant and a 24-value emission series."""
     base = li.make_cfg1(n_particles=5000, n_steps=240, n_hours=5)
