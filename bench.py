@@ -124,28 +124,37 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
         with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+            lines = f.readlines()
         os.unlink(self.path)
-        if not rows:
-            return out
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in rows:
-            for name, v in zip(names, r[5:9]):
-                if v.lower() in ("active", "1"):
-                    reasons.add(name)
-        loaded = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
-        out.update(sm_mhz=statistics.median(loaded) if loaded else None,
-                   sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
-                   samples=len(rows))
+        return parse_clock_rows(lines)
+
+
+def parse_clock_rows(lines):
+    """Summary of nvidia-smi rows (the ClockSampler fields, csv, no header or units): the
+    median SM clock over the samples under load (above half the maximum), the maximum, and
+    every throttle reason seen active in any sample."""
+    out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) >= 9:
+            rows.append(parts)
+    if not rows:
         return out
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    for r in rows:
+        for name, v in zip(names, r[5:9]):
+            if v.lower() in ("active", "1"):
+                reasons.add(name)
+    loaded = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
+    out.update(sm_mhz=statistics.median(loaded) if loaded else None,
+               sm_max_mhz=max(mx) if mx else None, reasons=sorted(reasons),
+               samples=len(rows))
+    return out
 
 
 # ------------------------------------------------------------------------------------
