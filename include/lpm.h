@@ -155,7 +155,14 @@ lpm_status lpm_release(lpm_ctx *ctx, int scenario, int64_t n_particles, const do
  * masses and the fixed-point scale are those of the whole release, so the integer grids
  * of disjoint ranges add up exactly to the grid of the whole release. lpm_release(...)
  * is lpm_release_range(..., n, 0, n, ..., id_base = sum of earlier releases' n_total).
- * Particles hold their state independently (Sec. 4.2: particles never interact).
+ * Particles hold their state independently (Sec. 4.2: particles never interact). A
+ * scenario of an ensemble held alone (scenario-range partitioning) passes the id_base it
+ * has in the ensemble and draws the same numbers. Global ids are 64-bit: id_base >= 0 and
+ * id_base + n_total may exceed 2^32 (the generator counter takes both 32-bit halves).
+ * Returns LPM_E_INVALID (nothing changed) for n_total < 1, count < 1, a range outside
+ * [0, n_total), id_base < 0, an empty or out-of-run step window, negative or non-finite
+ * rates, or more particles than max_particles; LPM_E_STATE for a scenario released out
+ * of order or twice, or a window that starts before the current step.
  */
 lpm_status lpm_release_range(lpm_ctx *ctx, int scenario, int64_t n_total, int64_t first_particle,
                              int64_t count, const double *q, int n_q, double q_dt,
