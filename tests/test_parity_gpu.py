@@ -237,6 +237,47 @@ def test_degenerate_zero_emission_and_stable_tracer():
     assert int(b[7]) == 2000                     # every particle released and still airborne
 
 
+def _linear_wind(X, Y, Z, T):
+    u = 4.0 + 1e-4 * X - 5e-5 * Y + 2e-3 * Z + 1e-4 * T
+    v = -1.0 + 5e-5 * X + 1e-4 * Y - 1e-3 * Z + 5e-5 * T
+    w = 1e-3 - 1e-6 * Z + 1e-7 * X
+    return u, v, w
+
+
+def test_linear_weather_paths_follow_the_closed_form():
+    """No diffusion and no sinks: every particle follows the Euler map
+    x_{k+1} = x_k + u(x_k, t_k) dt (Eq. 1-2 with K = 0). For weather linear in x, y, z
+    and t the multilinear interpolation is exact, so the GPU paths must follow the map
+    iterated in FP64 on the closed-form field, independently of the oracle, to FP32
+    rounding of the positions (0.1 m after up to 120 steps at x <= 14 km). Catches
+    swapped axes, a wrong weight complement, an off-by-one cell or level and a wrong time
+    fraction, each worth metres per step."""
+    nx, ny, nz, nt = 25, 21, 12, 2
+    z_levels = li.z_levels_stretched(nz, 2000.0)
+    T, Z, Y, X = np.meshgrid(np.arange(nt) * 3600.0, z_levels, 1000.0 * np.arange(ny),
+                             1000.0 * np.arange(nx), indexing="ij")
+    uvwk = np.zeros((nt, nz, ny, nx, 4))
+    uvwk[..., 0], uvwk[..., 1], uvwk[..., 2] = _linear_wind(X, Y, Z, T)
+    n = 120
+    base = li.make_cfg0(n_particles=n, n_steps=n, kh=0.0, kz=0.0)
+    cfg = dataclasses.replace(base, nx=nx, ny=ny, nz=nz, x0=0.0, y0=0.0, dx=1000.0,
+                              dy=1000.0, z_levels=z_levels, n_met_t=nt, met_t0=0.0,
+                              met_dt=3600.0, uvwk=uvwk.astype(np.float32), dt=20.0,
+                              src_x=2000.0, src_y=10000.0, src_z=300.0,
+                              release=li.Release(n, np.array([1.0]), 3600.0, 0, n))
+    want = np.empty((n, 3))
+    for p in range(n):                           # particle p leaves at step p
+        x = np.array([cfg.src_x, cfg.src_y, cfg.src_z])
+        for k in range(p, n):
+            x = x + np.array(_linear_wind(x[0], x[1], x[2], k * cfg.dt)) * cfg.dt
+        want[p] = x
+    g = run_gpu(cfg)
+    assert np.all(g["status"] == 0)
+    d = np.abs(g["pos"] - want).max()
+    print(f"linear weather: max deviation from the closed-form paths {d:.3g} m")
+    assert d < 0.1
+
+
 def test_gridded_kh_drift_and_emission_series():
     """Gridded K_h, the drift-corrected variant and a 24-value emission series."""
     base = li.make_cfg1(n_particles=5000, n_steps=240, n_hours=5)
