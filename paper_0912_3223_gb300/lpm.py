@@ -470,6 +470,9 @@ class Sim:
         if not torch.cuda.is_available():
             raise RuntimeError("the particle model runs on a CUDA GPU; none is available")
         self.id_base = None
+        if id_base and cfg.scenarios:
+            raise ValueError("id_base applies to a single release; an ensemble's scenarios "
+                             "take their ids from their order")
         if scenarios is not None:
             import dataclasses
             if not cfg.scenarios or part is not None:
