@@ -127,3 +127,17 @@ def test_context_calls_reject_a_null_context(lib):
     ]
     for call in calls:
         assert call() == lpm.LPM_E_INVALID
+
+
+def test_product_path_fails_loudly_without_the_library_or_a_gpu(monkeypatch, tmp_path):
+    """No fallback: a missing liblpm.so raises on load, and a simulation without a CUDA
+    device raises instead of running anywhere else."""
+    import torch
+    from paper_0912_3223_gb300 import Sim
+    monkeypatch.setattr(lpm, "LIB_PATH", str(tmp_path / "liblpm.so"))
+    monkeypatch.setattr(lpm, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        lpm.load()
+    if not torch.cuda.is_available():
+        with pytest.raises(RuntimeError, match="CUDA GPU"):
+            Sim(li.make_cfg0(n_particles=10, n_steps=10))
