@@ -113,3 +113,24 @@ def test_batched_dosage_mixed_scenarios():
     fixed, out = runs[1][s]
     tot_g, tot_o = int(fixed.sum()) + out, int(o["dose_fixed"].sum()) + o["dose_out"]
     assert abs(tot_g - tot_o) <= 1e-3 * tot_o
+
+
+def test_dosage_survives_save_and_resume():
+    """A dosage run checkpointed after 150 steps and resumed in a fresh context, which takes
+    the sampling interval, the sums, the out-of-grid counter and the sample count from the
+    checkpoint, ends bit-identical to the uninterrupted run."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = li.make_cfg1(n_particles=5003, n_steps=400, n_hours=7)
+    ref = _gpu(cfg, 7)
+    with Sim(cfg) as a:
+        a.set_dosage(7)
+        a.step(150)
+        blob = lpm.lpm_save(a.ctx)
+    with Sim(cfg) as b:
+        lpm.lpm_load(b.ctx, blob)
+        b.step(cfg.n_steps - 150)
+        dose, fixed, samples = b.dosage()
+        out = int(b.fixed_state()[2][11])
+    assert samples == ref["samples"] == cfg.n_steps // 7
+    assert np.array_equal(fixed, ref["fixed"]) and out == ref["out"]
+    assert np.array_equal(dose, ref["dose"])

@@ -83,3 +83,22 @@ def test_eq3_limits_are_reported():
         with pytest.raises(lpm.LpmError) as e:
             lpm.lpm_set_boundary_layer(sim.ctx, 0, np.full((cfg.ny, cfg.nx, 4), -1.0, np.float32))
         assert e.value.status == lpm.LPM_E_INVALID
+
+
+def test_eq3_survives_save_and_resume():
+    """K_z from Eq. 3 checkpointed after 100 steps and resumed in a fresh context (the
+    boundary-layer columns are inputs, set again from the configuration): positions and
+    grids bit-identical to the uninterrupted run."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cfg = li.make_cfg1(n_particles=4001, n_steps=240, n_hours=5, kz_eq3=True)
+    ref = run_gpu(cfg)
+    with Sim(cfg) as a:
+        a.step(100)
+        blob = lpm.lpm_save(a.ctx)
+    with Sim(cfg) as b:
+        lpm.lpm_load(b.ctx, blob)
+        b.step(cfg.n_steps - 100)
+        xyz, tag = b.particles()
+        c, d, k, _ = b.fixed_state()
+    assert np.array_equal(xyz, ref["pos"].astype(np.float32)) and np.array_equal(tag, ref["tag"])
+    assert np.array_equal(c, ref["conc_fixed"]) and np.array_equal(d, ref["dep_fixed"])
