@@ -41,7 +41,8 @@ typedef enum {
     LPM_E_CUDA = 3,      /* a CUDA runtime call failed */
     LPM_E_STATE = 4,     /* the call is not allowed in the current state */
     LPM_E_NUMERIC = 5,   /* a particle position became non-finite */
-    LPM_E_TIMEOUT = 6    /* a bounded device loop hit its iteration limit */
+    LPM_E_TIMEOUT = 6    /* a bounded device loop hit its iteration limit (reserved: no
+                            kernel waits on another, every loop is bounded by its data) */
 } lpm_status;
 
 /* Particle status, bits 28..31 of the particle tag; bits 0..27 hold the release step. */
