@@ -93,7 +93,9 @@ def allreduce_float_fixed(values: np.ndarray, group=None, device=None) -> np.nda
     import torch.distributed as dist
     a = np.ascontiguousarray(values, dtype=np.float64)
     world = dist.get_world_size(group)
-    m = torch.from_numpy(np.abs(a).copy())
+    mag = np.abs(a)
+    mag[~np.isfinite(mag)] = np.inf              # MAX carries inf to every rank (NaN may not),
+    m = torch.from_numpy(mag)                    # so all ranks raise before the SUM together
     if device is not None:
         m = m.to(device)
     dist.all_reduce(m, op=dist.ReduceOp.MAX, group=group)

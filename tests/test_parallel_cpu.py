@@ -139,3 +139,31 @@ def test_fixed_point_float_sum_is_order_independent_and_exact_to_rounding():
         assert np.array_equal(sum_float_fixed([parts[i] for i in perm]), got)
     with pytest.raises(ValueError):
         sum_float_fixed([np.array([1.0, np.inf])])
+
+
+def _nan_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    vals = np.array([1.0, 2.0, 3.0])
+    if rank == 1:
+        vals[1] = np.nan
+    try:
+        allreduce_float_fixed(vals)
+        outcome = "reduced"
+    except ValueError:
+        outcome = "raised"
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write(outcome)
+    dist.destroy_process_group()
+
+
+def test_gloo_non_finite_value_on_one_rank_raises_on_every_rank(tmp_path):
+    """A NaN held by one rank makes every rank raise before the integer sum, so no rank is
+    left waiting in a collective the others never enter."""
+    world = 3
+    mp.start_processes(_nan_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    for r in range(world):
+        assert (tmp_path / f"rank{r}.txt").read_text() == "raised"
