@@ -38,18 +38,19 @@ WORKLOAD = ("plain method, realistic: 1e7 particles, 24 h at dt=30 s (2880 steps
 # deposition streams) 2 x 98, uniforms 12, Box-Muller 11, 4D gather index and weight math
 # 30, 16-corner lerps of 4 components 120, move 18, reflection/exit 8, deposition test 4.
 OPS_PER_PARTICLE_STEP = 2 * 98 + 12 + 11 + 30 + 120 + 18 + 8 + 4
-# DRAM traffic per advance launch from the ncu capture summarised in
-# profiles/advance_kernel_plain_1e7x2880.md (mean of the two captured 60-step launches of
-# hours 6-7, read + write), valid while the kernel sources hash to the values recorded there.
+# The upper end of the coarser estimate of the same work (250-350 instructions per
+# particle-step), reported beside it.
+OPS_PER_PARTICLE_STEP_LOW = 350
+# DRAM traffic per advance launch from an ncu capture of two mid-run 60-step launches
+# (hours 6-7 of the realistic workload; read + write, mean of the two), valid while the
+# kernel sources hash to the values below.
 ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.396672 + 0.000512) + (23.878656 + 0.006912)) * 1e6
 ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "23c5cd48", "lpm_device.cuh": "f5cb88b5"}
 # Busiest hardware units of the same capture (% of peak, mean of the two launches): the
 # L1 data pipe carrying the weather gathers, and the warp-instruction issue slots.
 ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (78.13 + 78.82) / 100.0,
                          "issue_slots": 0.5 * (76.37 + 76.27) / 100.0}
-SM_COUNT = 152
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
-SM_MAX_MHZ = 2070.0
 
 
 def _env_int(name, default):
@@ -549,6 +550,46 @@ def measure_langevin(args, stream):
             "particles": cfg.n_particles, "steps_per_run": cfg.n_steps}
 
 
+def device_sm_count(index: int) -> int:
+    """Streaming multiprocessors of the device (cudaDeviceProp.multiProcessorCount)."""
+    import torch
+    return int(torch.cuda.get_device_properties(index).multi_processor_count)
+
+
+def alu_roofline(active_steps, adv_ms, step_ms_total, sm_count, clk, peaks):
+    """The advance kernel against its ALU roofline. achieved = algorithmic operations of the
+    timed runs / the advance launches' summed CUDA-event time; peak = the device's SMs x 128
+    lanes x the median SM clock sampled during the timed region (one 32-bit operation per
+    lane per clock), falling back to the device's maximum clock when no sample was taken."""
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or peaks.get("sm_max_mhz")
+    clock_source = "median of the timed region's samples" if clk.get("sm_mhz") else \
+        "maximum SM clock (no samples)"
+    peak = sm_count * LANES_PER_SM * mhz * 1e6 / 1e12 if mhz else None
+    rate = active_steps / (adv_ms / 1e3) if adv_ms > 0 else None
+    achieved = OPS_PER_PARTICLE_STEP * rate / 1e12 if rate else None
+    achieved_low = OPS_PER_PARTICLE_STEP_LOW * rate / 1e12 if rate else None
+    return {
+        "bound": "alu", "kernel": "advance_kernel",
+        "achieved": achieved, "peak": peak, "unit": "Tops/s",
+        "frac": achieved / peak if achieved and peak else None,
+        "traffic": advance_traffic(),
+        "traffic_unit": "bytes per advance launch (ncu capture, mid-run launches)",
+        "peak_source": (f"derived: {sm_count} SMs (queried from the device) x {LANES_PER_SM} "
+                        f"lanes x {mhz:.0f} MHz ({clock_source}); one 32-bit op per lane per "
+                        "clock") if mhz else None,
+        "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
+        "advance_particle_steps_per_s": rate,
+        "frac_at_350_ops": achieved_low / peak if achieved_low and peak else None,
+        # the hardware view of the same kernel (ncu capture, % of each unit's peak): what
+        # bounds it is the L1 data pipe and the issue slots, not DRAM
+        "busiest_units": dict(ADVANCE_BUSIEST_UNITS,
+                              source="ncu capture of the same kernel sources (hashes in "
+                                     "ADVANCE_TRAFFIC_SOURCES)") if capture_current() else None,
+        "advance_share_of_step": (adv_ms / 1e3) / (step_ms_total / 1e3) if step_ms_total else None,
+        "hbm_gbs_measured_peak": peaks.get("hbm_gbs"),
+    }
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -657,24 +698,7 @@ def run_gpu(args):
 
     sim.close()
     peaks = read_peaks()
-    alu_peak = SM_COUNT * LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # Tops/s
-    achieved = OPS_PER_PARTICLE_STEP * sum(active) / (adv_ms / 1e3) / 1e12 if adv_ms > 0 else None
-    roofline = {
-        "bound": "alu", "kernel": "advance_kernel",
-        "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-        "frac": achieved / alu_peak if achieved else None,
-        "traffic": advance_traffic(),
-        "traffic_unit": "bytes per advance launch (ncu capture, mid-run launches)",
-        "peak_source": (f"derived: {SM_COUNT} SMs x {LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz "
-                        "(one 32-bit op per lane per clock)"),
-        "ops_per_particle_step": OPS_PER_PARTICLE_STEP,
-        # the hardware view of the same kernel (ncu capture, % of each unit's peak): what
-        # bounds it is the L1 data pipe and the issue slots, not DRAM
-        "busiest_units": dict(ADVANCE_BUSIEST_UNITS, source="ncu capture, profiles/"
-                              "advance_kernel_plain_1e7x2880.md") if capture_current() else None,
-        "advance_share_of_step": (adv_ms / 1e3) / (sum(times) / 1e3) if times else None,
-        "hbm_gbs_measured_peak": peaks.get("hbm_gbs"),
-    }
+    roofline = alu_roofline(sum(active), adv_ms, sum(times), device_sm_count(local), clk, peaks)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(times),

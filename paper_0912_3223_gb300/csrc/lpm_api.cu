@@ -918,6 +918,7 @@ lpm_status lpm_release_range(lpm_ctx *c, int scenario, int64_t n_total, int64_t 
                              int64_t first, int64_t last, int64_t id_base)
 {
     if (!c) return LPM_E_INVALID;
+    NvtxRange nr("lpm_release");
     if (scenario != c->n_released)
         return fail(c, LPM_E_STATE, "scenarios must be released once each, in order (next is %d)",
                     c->n_released);
@@ -971,6 +972,7 @@ lpm_status lpm_release(lpm_ctx *c, int scenario, int64_t n, const double *q, int
 lpm_status lpm_reset(lpm_ctx *c)
 {
     if (!c) return LPM_E_INVALID;
+    NvtxRange nr("lpm_reset");
     const size_t ns = (size_t)c->cfg.n_scenarios;
     LPM_CUDA(c, cudaMemsetAsync(c->d_conc, 0, ns * c->ncell() * sizeof(unsigned long long), c->stream));
     LPM_CUDA(c, cudaMemsetAsync(c->d_dep, 0, ns * c->ndep() * sizeof(unsigned long long), c->stream));
@@ -1098,6 +1100,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             }
         }
         if (sg.sort) {
+            NvtxRange nr("lpm sort");
             SortSource in{};
             in.state_a = c->d_sorted[cur];
             in.pidx_a = c->d_pidx[cur];
@@ -1179,7 +1182,10 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             if (!e0 || !e1) return fail(c, LPM_E_CUDA, "cudaEventCreate failed");
             LPM_CUDA(c, cudaEventRecord(e0, s));
         }
-        LPM_CUDA(c, launch_advance(L));
+        {
+            NvtxRange nr("lpm advance");
+            LPM_CUDA(c, launch_advance(L));
+        }
         if (timed) LPM_CUDA(c, cudaEventRecord(e1, s));
         if (direct) c->n_adv_launches++;
         kernels++;
@@ -1192,6 +1198,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
 lpm_status lpm_step(lpm_ctx *c, int64_t n)
 {
     if (!c) return LPM_E_INVALID;
+    NvtxRange nr("lpm_step");
     const lpm_config &g = c->cfg;
     if (n < 0) return fail(c, LPM_E_INVALID, "n must be >= 0");
     if (n == 0) return LPM_OK;
@@ -2240,6 +2247,7 @@ lpm_status lpm_receptors(lpm_ctx *c, const double *rec, int R, double bandwidth,
                          double *C)
 {
     if (!c) return LPM_E_INVALID;
+    NvtxRange nr("lpm_receptors (adjoint forward)");
     if (!C) return fail(c, LPM_E_INVALID, "C is NULL");
     AdjParams A;
     StepParams P;
@@ -2254,6 +2262,7 @@ lpm_status lpm_adjoint(lpm_ctx *c, const double *rec, int R, double bandwidth, i
                        const double *dL_dC, double *grad)
 {
     if (!c) return LPM_E_INVALID;
+    NvtxRange nr("lpm_adjoint (reverse sweep)");
     if (!dL_dC || !grad) return fail(c, LPM_E_INVALID, "dL_dC and grad are required");
     AdjParams A;
     StepParams P;
@@ -2405,13 +2414,24 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
         h.ndep != (long long)c->ndep() || h.n_ctr != N_COUNTERS || h.k < 0 ||
         h.k > c->cfg.n_steps || h.dose_every < 0 || h.dose_every > 0x7fffffffLL)
         return fail(c, LPM_E_INVALID, "saved run does not match this context");
+    // a snapshot is taken at most once per step, a dosage sample once per dose_every steps
+    if (h.n_bins < 0 || h.n_bins > h.k || h.n_dose < 0 ||
+        (h.dose_every > 0 ? h.n_dose > h.k / h.dose_every : h.n_dose != 0))
+        return fail(c, LPM_E_INVALID, "saved run has inconsistent snapshot or dosage counts");
     const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
     const size_t need = sizeof h + sb + ns * (c->ncell() + c->ndep() + N_COUNTERS) * 8 +
                         (h.dose_every > 0 ? ns * c->ncell() * 8 : 0) +
                         (size_t)(c->n_species - 1) * ns * (c->ncell() + c->ndep()) * 8 +
                         (c->langevin ? (size_t)c->n_slots_used * sizeof(float) : 0);
     if (n < need) return fail(c, LPM_E_INVALID, "saved run truncated (%zu of %zu bytes)", n, need);
-    lpm_status st = upload_tables(c);
+    lpm_status st;
+    if (h.dose_every > 0) {
+        // the dosage grid may need an allocation: take it before any particle, grid or
+        // counter is overwritten, so that a failed allocation leaves the run as it was
+        st = lpm_set_dosage(c, (int)h.dose_every);
+        if (st != LPM_OK) return st;
+    }
+    st = upload_tables(c);
     if (st != LPM_OK) return st;
     const char *i = static_cast<const char *>(buf) + sizeof h;
     LPM_CUDA(c, cudaMemcpyAsync(c->d_state, i, sb, cudaMemcpyHostToDevice, c->stream));
@@ -2423,14 +2443,9 @@ lpm_status lpm_load(lpm_ctx *c, const void *buf, size_t n)
     LPM_CUDA(c, cudaMemcpyAsync(c->d_ctr, i, ns * N_COUNTERS * 8, cudaMemcpyHostToDevice, c->stream));
     i += ns * N_COUNTERS * 8;
     if (h.dose_every > 0) {
-        st = lpm_set_dosage(c, (int)h.dose_every);   // allocates and zeroes the dose_out row
-        if (st != LPM_OK) return st;
+        // the grid was allocated above; the counters copied above hold the saved dose_out row
         LPM_CUDA(c, cudaMemcpyAsync(c->d_dose, i, ns * c->ncell() * 8, cudaMemcpyHostToDevice,
                                     c->stream));
-        LPM_CUDA(c, cudaMemcpyAsync(c->d_ctr + (size_t)C_DOSE_OUT * ns,
-                                    static_cast<const char *>(buf) + sizeof h + sb +
-                                        ns * (c->ncell() + c->ndep()) * 8 + (size_t)C_DOSE_OUT * ns * 8,
-                                    ns * 8, cudaMemcpyHostToDevice, c->stream));
         c->n_dose = h.n_dose;
         i += ns * c->ncell() * 8;
     } else if (c->d_dose) {

@@ -1,9 +1,21 @@
 // lpm_launch.h - host-side launch interface between the C-ABI layer and the kernels.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lpm_device.cuh"
 
 namespace lpm {
+
+// A named NVTX range over a host scope (the enqueueing of a phase's device work: release,
+// step, sort, advance, the adjoint's passes), for timeline tools; without a tool attached
+// the push and pop return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // The particles of an advance launch. A = the sorted live particles [0, live) of state_a
 // (live count on the device; home slot of sorted slot i in pidx[i]; any scenario);

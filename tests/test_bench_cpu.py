@@ -73,3 +73,21 @@ def test_reference_arm_other_ranks_exit_quietly():
                          capture_output=True, text=True, timeout=120, cwd=root, env=env)
     assert run.returncode == 0, run.stderr[-2000:]
     assert not [ln for ln in run.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_alu_roofline_follows_the_queried_sms_and_the_sampled_clock():
+    """The ALU peak is the device's SM count x 128 lanes x the median SM clock of the timed
+    region; the fraction follows from the algorithmic operations per particle-step."""
+    clk = {"sm_mhz": 1500.0, "sm_max_mhz": 2070.0}
+    r = bench.alu_roofline(active_steps=2e9, adv_ms=100.0, step_ms_total=125.0, sm_count=100,
+                           clk=clk, peaks={})
+    peak = 100 * 128 * 1500e6 / 1e12
+    assert r["peak"] == peak
+    assert abs(r["achieved"] - bench.OPS_PER_PARTICLE_STEP * 2e10 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / peak) < 1e-12
+    assert abs(r["frac_at_350_ops"] - 350 * 2e10 / 1e12 / peak) < 1e-12
+    assert abs(r["advance_share_of_step"] - 0.8) < 1e-12
+    assert "100 SMs" in r["peak_source"] and "1500 MHz" in r["peak_source"]
+    # no clock samples: the device's maximum clock
+    r2 = bench.alu_roofline(2e9, 100.0, 125.0, 100, {"sm_mhz": None, "sm_max_mhz": 2070.0}, {})
+    assert r2["peak"] == 100 * 128 * 2070e6 / 1e12 and "maximum" in r2["peak_source"]

@@ -419,6 +419,24 @@ def test_save_and_resume_is_bit_identical(sort_every):
         with pytest.raises(lpm.LpmError) as e:
             lpm.lpm_load(other.ctx, saved)
         assert e.value.status == lpm.LPM_E_INVALID
+    # headers with impossible snapshot or dosage counts are refused before anything is
+    # loaded: the context keeps its own run (header: 8-byte magic, then int64 k, n_bins,
+    # n_slots, n_scen, ncell, ndep, n_ctr, dose_every, n_dose, ...)
+    import struct
+    bad_fields = [(16, -1), (16, 151)]                 # n_bins < 0, n_bins > k
+    bad_fields += [(72, 150 // 8 + 1), (72, -1)] if sort_every else [(72, 1)]
+    with Sim(cfg, sort_every=sort_every) as c:
+        c.step(10)
+        before = c.fixed_state()
+        for off, val in bad_fields:
+            bad = bytearray(saved)
+            struct.pack_into("<q", bad, off, val)
+            with pytest.raises(lpm.LpmError) as e:
+                lpm.lpm_load(c.ctx, bytes(bad))
+            assert e.value.status == lpm.LPM_E_INVALID
+            assert c.k == 10
+        after = c.fixed_state()
+        assert np.array_equal(before[0], after[0]) and np.array_equal(before[2], after[2])
 
 
 def test_allocation_failure_is_reported():
