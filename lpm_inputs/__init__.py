@@ -42,6 +42,7 @@ SEED_SCENARIOS = 13
 SEED_HIDDEN = 14
 SEED_RECEPTORS = 15
 SEED_BOUNDARY_LAYER = 16
+SEED_MODES = 17
 
 
 @dataclasses.dataclass
@@ -64,6 +65,10 @@ class Scenario:
     release: Release
     # Domain-uniform wind offset (du, dv) per met hour, [n_met_t][2] float32.
     wind_offset: Optional[np.ndarray] = None
+    # The scenario's realisation of the ensemble's perturbation modes (LpmConfig.modes):
+    # phase (cycles) and amplitude (m/s) of each mode, float64 [n_modes].
+    mode_phase: Optional[np.ndarray] = None
+    mode_amp: Optional[np.ndarray] = None
 
 
 @dataclasses.dataclass
@@ -128,6 +133,14 @@ class LpmConfig:
     # vertical Langevin variant (velocity memory over the Lagrangian time scale t_lagr, s)
     langevin: int = 0
     t_lagr: float = 100.0
+    # perturbation modes of the wind (plane waves of a streamfunction), shared by the
+    # scenarios: float64 [n_modes][5] = (fx, fy (cycles/m), omega (cycles/s), eu, ev (unit
+    # velocity direction)) and the height profile [nz] they are scaled by; each scenario
+    # (or, for a plain run, mode_phase / mode_amp here) gives its phases and amplitudes
+    modes: Optional[np.ndarray] = None
+    mode_profile: Optional[np.ndarray] = None
+    mode_phase: Optional[np.ndarray] = None
+    mode_amp: Optional[np.ndarray] = None
     name: str = ""
 
     @property
@@ -333,16 +346,41 @@ def make_cfg1(n_particles: int = 10_000_000, n_steps: int = 2880, n_hours: int =
         bl=make_boundary_layer(n_t=n_hours) if kz_eq3 else None)
 
 
+def make_modes(z_levels: np.ndarray, n_modes: int = 4, ustar: float = 0.4, z0: float = 0.1,
+               seed: int = SEED_MODES):
+    """Perturbation modes shared by an ensemble: ``n_modes`` plane waves of a horizontal
+    streamfunction with wavelengths log-uniform in 5..50 km, seeded directions, phase rates
+    of 0..1/4 cycle per hour, velocity perpendicular to the wavenumber (non-divergent), and
+    the height profile u(z)/u(100 m) of the log wind at the levels. Returns (modes [M][5],
+    profile [nz])."""
+    rng = np.random.default_rng(seed)
+    lam = np.exp(rng.uniform(np.log(5000.0), np.log(50000.0), n_modes))
+    theta = rng.uniform(0.0, 2 * np.pi, n_modes)
+    omega = rng.uniform(0.0, 0.25, n_modes) / 3600.0
+    modes = np.stack([np.cos(theta) / lam, np.sin(theta) / lam, omega, -np.sin(theta),
+                      np.cos(theta)], axis=1)
+    u100 = _log_wind(np.array([100.0]), ustar, z0)[0]
+    profile = _log_wind(np.asarray(z_levels, dtype=np.float64), ustar, z0) / u100
+    return modes, profile
+
+
 def make_cfg2(n_scenarios: int = 256, n_steps: int = 1440, n_min: float = 1e4,
               n_max: float = 1e6, seed: int = SEED_SCENARIOS,
-              base: Optional[LpmConfig] = None) -> LpmConfig:
+              base: Optional[LpmConfig] = None, n_modes: int = 4,
+              mode_rms: float = 1.0) -> LpmConfig:
     """Batched ensemble: ``n_scenarios`` scenarios on the realistic met grid, particle
     counts log-uniform in [n_min, n_max], own source (x, y, release height 10..300 m),
-    24-value hourly emission series and a seeded, domain-uniform hourly wind offset
-    (rms 1.5 m/s per component); 12 h at dt = 30 s; one surface-layer concentration
-    layer (0..50 m) plus dry/wet deposition per scenario."""
+    24-value hourly emission series and perturbed meteorology: a seeded, domain-uniform
+    hourly wind offset (AR(1), rms 1.5 m/s per component) plus the scenario's own
+    realisation of ``n_modes`` shared perturbation modes (seeded phases, amplitudes
+    (0.5..1.5) x mode_rms sqrt(2 / n_modes)); 12 h at dt = 30 s; one surface-layer
+    concentration layer (0..50 m) plus dry/wet deposition per scenario."""
     if base is None:
         base = make_cfg1(n_particles=1, n_steps=n_steps)
+    modes = profile = None
+    mrng = np.random.default_rng(SEED_MODES + 1)
+    if n_modes > 0:
+        modes, profile = make_modes(base.z_levels, n_modes)
     rng = np.random.default_rng(seed)
     scen = []
     for _ in range(n_scenarios):
@@ -356,9 +394,15 @@ def make_cfg2(n_scenarios: int = 256, n_steps: int = 1440, n_min: float = 1e4,
         for h in range(base.n_met_t):
             off[h] = a
             a = 0.8 * a + math.sqrt(1 - 0.64) * rng.normal(0.0, 1.5, 2)
-        scen.append(Scenario(sx, sy, sz, Release(n, q, 3600.0, 0, n_steps), off))
+        sc = Scenario(sx, sy, sz, Release(n, q, 3600.0, 0, n_steps), off)
+        if n_modes > 0:
+            sc.mode_phase = mrng.uniform(0.0, 1.0, n_modes)
+            sc.mode_amp = (mode_rms * math.sqrt(2.0 / n_modes) *
+                           mrng.uniform(0.5, 1.5, n_modes))
+        scen.append(sc)
     cfg = dataclasses.replace(base, n_steps=n_steps, bin_every=n_steps,
                               cz=1, n_scenarios=n_scenarios, scenarios=scen,
+                              modes=modes, mode_profile=profile,
                               name="cfg2 batched ensemble")
     return cfg
 

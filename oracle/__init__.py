@@ -59,6 +59,9 @@ class OCfg(C.Structure):
         ("kz_model", C.c_int), ("kz_min", C.c_double), ("bl", C.POINTER(C.c_float)),
         ("n_species", C.c_int), ("chain_half_life", C.POINTER(C.c_double)),
         ("langevin", C.c_int), ("t_lagr", C.c_double),
+        ("n_modes", C.c_int), ("modes", C.POINTER(C.c_double)),
+        ("mode_profile", C.POINTER(C.c_double)), ("mode_phase", C.POINTER(C.c_double)),
+        ("mode_amp", C.POINTER(C.c_double)),
     ]
 
 
@@ -81,50 +84,55 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        u64p = C.POINTER(C.c_uint64)
-        u32p = C.POINTER(C.c_uint32)
-        L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
-        L.oracle_draw_many.argtypes = [C.c_uint64, u64p, u32p, C.c_uint32, C.c_int64, u32p]
-        L.oracle_normals_many.argtypes = [C.c_uint64, u64p, u32p, C.c_int64,
-                                          C.POINTER(C.c_double)]
-        L.oracle_uniform.argtypes = [C.c_uint32]
-        L.oracle_uniform.restype = C.c_double
-        L.oracle_interp_many.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_double), C.c_int64,
-                                         C.POINTER(C.c_double)]
-        L.oracle_release_many.argtypes = [C.c_int64, C.c_int64, C.c_int64,
-                                          C.POINTER(C.c_int64), C.c_int64,
-                                          C.POINTER(C.c_int64)]
-        L.oracle_release_count.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64]
-        L.oracle_release_count.restype = C.c_int64
-        L.oracle_total_mass.argtypes = [C.POINTER(OCfg)]
-        L.oracle_total_mass.restype = C.c_double
-        L.oracle_fixed_shift.argtypes = [C.c_double]
-        L.oracle_fixed_shift.restype = C.c_int
-        L.oracle_initial_mass.argtypes = [C.POINTER(OCfg), C.c_int64]
-        L.oracle_initial_mass.restype = C.c_double
-        L.oracle_kz_eq3.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
-        L.oracle_kz_eq3_partials.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
-        L.oracle_interp_grad_many.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_double), C.c_int64,
-                                              C.POINTER(C.c_double), C.POINTER(C.c_double)]
-        L.oracle_chain_amount.argtypes = [C.POINTER(OCfg), C.c_int, C.c_double]
-        L.oracle_chain_amount.restype = C.c_double
-        L.oracle_threshold.argtypes = [C.c_double]
-        L.oracle_threshold.restype = C.c_uint32
-        L.oracle_run.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_int64), C.c_int64, C.c_int64,
-                                 C.POINTER(OOut)]
-        L.oracle_run.restype = C.c_int
-        dp = C.POINTER(C.c_double)
-        i64p = C.POINTER(C.c_int64)
-        L.oracle_receptors.argtypes = [C.POINTER(OCfg), dp, C.c_int, C.c_double, C.c_int, i64p,
-                                       C.c_int64, C.c_int64, dp]
-        L.oracle_adjoint.argtypes = [C.POINTER(OCfg), dp, C.c_int, C.c_double, C.c_int, dp, i64p,
-                                     C.c_int64, C.c_int64, dp]
-        L.oracle_sensitivity.argtypes = [C.POINTER(OCfg), i64p, C.c_int64, C.c_int64, dp]
-        for f in (L.oracle_receptors, L.oracle_adjoint, L.oracle_sensitivity):
-            f.restype = C.c_int
-        _lib = L
+        _lib = configure(C.CDLL(_LIB))
     return _lib
+
+
+def configure(L):
+    """Declares the argument and result types of the oracle's exported functions on a
+    loaded copy of the library."""
+    u64p = C.POINTER(C.c_uint64)
+    u32p = C.POINTER(C.c_uint32)
+    L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.oracle_draw_many.argtypes = [C.c_uint64, u64p, u32p, C.c_uint32, C.c_int64, u32p]
+    L.oracle_normals_many.argtypes = [C.c_uint64, u64p, u32p, C.c_int64,
+                                      C.POINTER(C.c_double)]
+    L.oracle_uniform.argtypes = [C.c_uint32]
+    L.oracle_uniform.restype = C.c_double
+    L.oracle_interp_many.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_double), C.c_int64,
+                                     C.POINTER(C.c_double)]
+    L.oracle_release_many.argtypes = [C.c_int64, C.c_int64, C.c_int64,
+                                      C.POINTER(C.c_int64), C.c_int64,
+                                      C.POINTER(C.c_int64)]
+    L.oracle_release_count.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_int64]
+    L.oracle_release_count.restype = C.c_int64
+    L.oracle_total_mass.argtypes = [C.POINTER(OCfg)]
+    L.oracle_total_mass.restype = C.c_double
+    L.oracle_fixed_shift.argtypes = [C.c_double]
+    L.oracle_fixed_shift.restype = C.c_int
+    L.oracle_initial_mass.argtypes = [C.POINTER(OCfg), C.c_int64]
+    L.oracle_initial_mass.restype = C.c_double
+    L.oracle_kz_eq3.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
+    L.oracle_kz_eq3_partials.argtypes = [C.c_double] * 5 + [C.POINTER(C.c_double)]
+    L.oracle_interp_grad_many.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_double), C.c_int64,
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.oracle_chain_amount.argtypes = [C.POINTER(OCfg), C.c_int, C.c_double]
+    L.oracle_chain_amount.restype = C.c_double
+    L.oracle_threshold.argtypes = [C.c_double]
+    L.oracle_threshold.restype = C.c_uint32
+    L.oracle_run.argtypes = [C.POINTER(OCfg), C.POINTER(C.c_int64), C.c_int64, C.c_int64,
+                             C.POINTER(OOut)]
+    L.oracle_run.restype = C.c_int
+    dp = C.POINTER(C.c_double)
+    i64p = C.POINTER(C.c_int64)
+    L.oracle_receptors.argtypes = [C.POINTER(OCfg), dp, C.c_int, C.c_double, C.c_int, i64p,
+                                   C.c_int64, C.c_int64, dp]
+    L.oracle_adjoint.argtypes = [C.POINTER(OCfg), dp, C.c_int, C.c_double, C.c_int, dp, i64p,
+                                 C.c_int64, C.c_int64, dp]
+    L.oracle_sensitivity.argtypes = [C.POINTER(OCfg), i64p, C.c_int64, C.c_int64, dp]
+    for f in (L.oracle_receptors, L.oracle_adjoint, L.oracle_sensitivity):
+        f.restype = C.c_int
+    return L
 
 
 def _ptr(a: Optional[np.ndarray], ct):
@@ -182,6 +190,20 @@ def make_ocfg(cfg, scenario: Optional[int] = None, k_scale: float = 1.0,
     if src is not None:
         o.src_x, o.src_y, o.src_z = (float(v) for v in src)
     o.wind_offset = _ptr(pin.arr(wind_offset, np.float32), C.c_float)
+    # perturbation modes: the ensemble's waves and profile, the scenario's phases and
+    # amplitudes (a plain configuration may carry them as scenario 0's)
+    modes = getattr(cfg, "modes", None)
+    o.n_modes = 0
+    if modes is not None and len(modes):
+        sc_modes = cfg.scenarios[scenario] if scenario is not None else cfg
+        phase = getattr(sc_modes, "mode_phase", None)
+        amp = getattr(sc_modes, "mode_amp", None)
+        if phase is not None and amp is not None:
+            o.n_modes = int(len(modes))
+            o.modes = _ptr(pin.arr(modes, np.float64), C.c_double)
+            o.mode_profile = _ptr(pin.arr(cfg.mode_profile, np.float64), C.c_double)
+            o.mode_phase = _ptr(pin.arr(phase, np.float64), C.c_double)
+            o.mode_amp = _ptr(pin.arr(amp, np.float64), C.c_double)
     qa = pin.arr(rel.q if q is None else q, np.float64)
     o.n_particles = int(rel.n_particles)
     o.q = _ptr(qa, C.c_double)

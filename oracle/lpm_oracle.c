@@ -144,6 +144,17 @@ typedef struct {
     /* vertical Langevin (velocity-memory) variant: 0 = the random walk of Eq. 2 */
     int langevin;
     double t_lagr;                   /* Lagrangian time scale T_L (s) */
+    /* perturbed weather of a scenario: n_modes plane waves of a horizontal streamfunction
+     * added to the wind. Mode m has the wavenumber (fx, fy) (cycles/m), the phase rate
+     * omega (cycles/s) and the unit direction (eu, ev) of its velocity (perpendicular to
+     * (fx, fy) for a non-divergent field); the scenario gives its phase (cycles) and
+     * amplitude (m/s), and every mode is scaled in height by a profile given at the
+     * levels. */
+    int n_modes;
+    const double *modes;             /* [n_modes][5] (fx, fy, omega, eu, ev) */
+    const double *mode_profile;      /* [nz] scale at the levels */
+    const double *mode_phase;        /* [n_modes] this scenario's phases (cycles) */
+    const double *mode_amp;          /* [n_modes] this scenario's amplitudes (m/s) */
 } ocfg;
 
 /* The normal of stream 2 at (particle, step): the vertical turbulent velocity a particle
@@ -418,6 +429,48 @@ static void bl_interp(const ocfg *c, double x, double y, double t, double v[3])
     bl_interp_grad(c, x, y, t, v, NULL);
 }
 
+/* The scenario's wind perturbation at (x, y, z, t):
+ *   (u', v') = p(z) sum_m amp_m (eu_m, ev_m) sin(2 pi (fx_m x + fy_m y + phase_m + omega_m t)),
+ * p(z) linear between the levels with the weather's level rules (constant beyond them).
+ * g (may be NULL) receives d(u', v')/d(x, y, z).
+ * Parity: pinned by closed-form paths (a particle carried along a wave crest moves in a
+ * straight line at the speed of its phase; the Euler sum over a moving phase is the
+ * sum of a sine over an arithmetic progression), zero divergence, the profile at the
+ * levels and the gradient against central differences (tests). */
+static void mode_wind(const ocfg *c, double x, double y, double z, double t, double uv[2],
+                      double g[2][3])
+{
+    uv[0] = uv[1] = 0.0;
+    if (g) memset(g, 0, sizeof(double) * 6);
+    if (c->n_modes <= 0 || !c->modes) return;
+    int k;
+    double cz;
+    axis_levels(z, c->z_levels, c->nz, &k, &cz);
+    const double p = (1.0 - cz) * c->mode_profile[k] + cz * c->mode_profile[k + 1];
+    const int in_z = z >= c->z_levels[0] && z <= c->z_levels[c->nz - 1];
+    const double dp = in_z ? (c->mode_profile[k + 1] - c->mode_profile[k]) /
+                                 (c->z_levels[k + 1] - c->z_levels[k]) : 0.0;
+    const double two_pi = 6.283185307179586476925287;
+    double s_u = 0.0, s_v = 0.0, d_u[2] = {0.0, 0.0}, d_v[2] = {0.0, 0.0};
+    for (int m = 0; m < c->n_modes; ++m) {
+        const double *md = c->modes + 5 * m;
+        const double arg = two_pi * (md[0] * x + md[1] * y + c->mode_phase[m] + md[2] * t);
+        const double sn = sin(arg), cs = cos(arg), a = c->mode_amp[m];
+        s_u += a * md[3] * sn;
+        s_v += a * md[4] * sn;
+        for (int d = 0; d < 2; ++d) {
+            d_u[d] += a * md[3] * cs * two_pi * md[d];
+            d_v[d] += a * md[4] * cs * two_pi * md[d];
+        }
+    }
+    uv[0] = p * s_u;
+    uv[1] = p * s_v;
+    if (g) {
+        g[0][0] = p * d_u[0]; g[0][1] = p * d_u[1]; g[0][2] = dp * s_u;
+        g[1][0] = p * d_v[0]; g[1][1] = p * d_v[1]; g[1][2] = dp * s_v;
+    }
+}
+
 /* Weather at (x, y, z, t): out = (u, v, w, K_z, K_h, dK_z/dz). K values clamped >= 0.
  * dK_z/dz is the z-derivative of the multilinear K_z (0 outside the level range); with
  * kz_model 1, K_z and its derivative come from Eq. 3 on the interpolated columns. */
@@ -456,6 +509,12 @@ void oracle_interp(const ocfg *c, double x, double y, double z, double t, double
         acc[0] += (1.0 - f) * (double)c->wind_offset[2 * h0] + f * (double)c->wind_offset[2 * h1];
         acc[1] += (1.0 - f) * (double)c->wind_offset[2 * h0 + 1]
                   + f * (double)c->wind_offset[2 * h1 + 1];
+    }
+    if (c->n_modes > 0) {
+        double uv[2];
+        mode_wind(c, x, y, z, t, uv, NULL);
+        acc[0] += uv[0];
+        acc[1] += uv[1];
     }
     double dz = c->z_levels[k + 1] - c->z_levels[k];
     int inside = z >= c->z_levels[0] && z <= c->z_levels[c->nz - 1];
@@ -641,6 +700,9 @@ int oracle_run(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, 
 {
     if (c->nx < 2 || c->ny < 2 || c->nz < 2 || c->n_particles <= 0) return 1;
     if (c->last_step <= c->first_step || c->dt <= 0.0 || c->bin_every <= 0) return 1;
+    if (c->n_modes < 0 || (c->n_modes > 0 && (!c->modes || !c->mode_profile || !c->mode_phase ||
+                                              !c->mode_amp)))
+        return 1;
     int64_t n = sel ? n_sel : c->n_particles;
     size_t ncell = (size_t)c->cx * c->cy * c->cz, ndep = (size_t)2 * c->cx * c->cy;
     const int shift = oracle_fixed_shift(oracle_total_mass(c));
@@ -943,6 +1005,14 @@ static void interp_grad(const ocfg *c, double x, double y, double z, double t, d
     if (c->wind_offset) {
         acc[0] += (1.0 - f) * (double)c->wind_offset[2 * h0] + f * (double)c->wind_offset[2 * h1];
         acc[1] += (1.0 - f) * (double)c->wind_offset[2 * h0 + 1] + f * (double)c->wind_offset[2 * h1 + 1];
+    }
+    if (c->n_modes > 0) {
+        double uv[2], gm[2][3];
+        mode_wind(c, x, y, z, t, uv, gm);
+        for (int q = 0; q < 2; ++q) {
+            acc[q] += uv[q];
+            for (int d = 0; d < 3; ++d) g[q][d] += gm[q][d];
+        }
     }
     if (!c->kh) {
         acc[4] = c->kh_uniform;
