@@ -137,6 +137,36 @@ lpm_status lpm_set_met(lpm_ctx *ctx, int t_index, const float *uvwk, const float
 lpm_status lpm_set_source(lpm_ctx *ctx, int scenario, double x, double y, double z,
                           const float *wind_offset);
 
+/* Most perturbation modes lpm_set_modes accepts. */
+#define LPM_MAX_MODES 4
+
+/*
+ * Spatially varying perturbation of the scenarios' weather (the batched ensemble's
+ * perturbed meteorology; the paper's weather varies in x, y, z and t, Sec. 3.2): n_modes
+ * plane waves of a horizontal streamfunction shared by every scenario, each scenario
+ * adding its own realisation (phases and amplitudes, lpm_set_mode_phases) to the wind:
+ *   u += p(z) sum_m amp_m eu_m sin(2 pi (fx_m x + fy_m y + phase_m + omega_m t)),
+ *   v += p(z) sum_m amp_m ev_m sin(...),
+ * with t the step's start time and p linear between the levels like the weather
+ * (constant beyond them). modes: host [n_modes][5] (fx, fy (cycles/m), omega (cycles/s),
+ * eu, ev); the field is non-divergent when (eu, ev) is perpendicular to (fx, fy).
+ * profile: host [nz] scale at the levels. 0 <= n_modes <= LPM_MAX_MODES (0 turns the
+ * modes off); every scenario starts with zero amplitudes. Copied; applies to the next
+ * lpm_step. Runs in the extended step kernel (1 particle per thread); lpm_adjoint and
+ * lpm_receptors reject a context with modes (LPM_E_INVALID). Like the met and the
+ * source, the modes are inputs, not part of lpm_save's state.
+ * Errors: LPM_E_INVALID for n_modes out of range, NULL or non-finite arrays.
+ */
+lpm_status lpm_set_modes(lpm_ctx *ctx, int n_modes, const double *modes, const double *profile);
+
+/*
+ * A scenario's realisation of the modes of lpm_set_modes: phase (cycles) and amplitude
+ * (m/s) of each, host [n_modes] each, copied. Errors: LPM_E_INVALID for a scenario out
+ * of range or NULL / non-finite values.
+ */
+lpm_status lpm_set_mode_phases(lpm_ctx *ctx, int scenario, const double *phase,
+                               const double *amp);
+
 /*
  * Continuous release of a scenario (Sec. 3.2: masses are assigned a priori from the
  * emission profile and the particle budget): n_particles particles over steps

@@ -361,7 +361,12 @@ def make_modes(z_levels: np.ndarray, n_modes: int = 4, ustar: float = 0.4, z0: f
                       np.cos(theta)], axis=1)
     u100 = _log_wind(np.array([100.0]), ustar, z0)[0]
     profile = _log_wind(np.asarray(z_levels, dtype=np.float64), ustar, z0) / u100
-    return modes, profile
+    # values representable in FP32, so that a single-precision consumer reads them exactly
+    return _fp32_exact(modes), _fp32_exact(profile)
+
+
+def _fp32_exact(a: np.ndarray) -> np.ndarray:
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
 def make_cfg2(n_scenarios: int = 256, n_steps: int = 1440, n_min: float = 1e4,
@@ -396,9 +401,9 @@ def make_cfg2(n_scenarios: int = 256, n_steps: int = 1440, n_min: float = 1e4,
             a = 0.8 * a + math.sqrt(1 - 0.64) * rng.normal(0.0, 1.5, 2)
         sc = Scenario(sx, sy, sz, Release(n, q, 3600.0, 0, n_steps), off)
         if n_modes > 0:
-            sc.mode_phase = mrng.uniform(0.0, 1.0, n_modes)
-            sc.mode_amp = (mode_rms * math.sqrt(2.0 / n_modes) *
-                           mrng.uniform(0.5, 1.5, n_modes))
+            sc.mode_phase = _fp32_exact(mrng.uniform(0.0, 1.0, n_modes))
+            sc.mode_amp = _fp32_exact(mode_rms * math.sqrt(2.0 / n_modes) *
+                                      mrng.uniform(0.5, 1.5, n_modes))
         scen.append(sc)
     cfg = dataclasses.replace(base, n_steps=n_steps, bin_every=n_steps,
                               cz=1, n_scenarios=n_scenarios, scenarios=scen,

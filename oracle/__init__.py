@@ -431,12 +431,18 @@ def sensitivity(cfg, sel=None, n_run: Optional[int] = None, **kw) -> np.ndarray:
     return out
 
 
-def chaotic(cfg, sens: np.ndarray, pos: np.ndarray, pos_tol: float) -> np.ndarray:
-    """Paths on which the FP32 roundings of the state (2^-24 of its magnitude, one per
-    step, independent) grown to the end of the run add up, as a random walk, past the
-    position tolerance: their FP32 and FP64 realisations are not expected to stay within
-    it. Needs the summed squared growths of ``sensitivity``."""
+def growth_bound(sens: np.ndarray, pos: np.ndarray) -> np.ndarray:
+    """The expected distance between a path run in FP32 and the same path in FP64: one
+    rounding of the state per step (2^-24 of its magnitude), each grown to the end of the
+    run by that step's growth factor, adding up as a random walk. Needs the summed squared
+    growths of ``sensitivity``."""
     eps = 2.0 ** -24
     rh = np.maximum(np.abs(pos[:, 0]), np.abs(pos[:, 1]))
     rz = np.maximum(pos[:, 2], 1.0)
-    return eps * np.sqrt(sens[:, 2] * rh ** 2 + sens[:, 3] * rz ** 2) > pos_tol
+    return eps * np.sqrt(sens[:, 2] * rh ** 2 + sens[:, 3] * rz ** 2)
+
+
+def chaotic(cfg, sens: np.ndarray, pos: np.ndarray, pos_tol: float) -> np.ndarray:
+    """Paths whose expected FP32-vs-FP64 distance (``growth_bound``) exceeds the position
+    tolerance: their two realisations are not expected to stay within it."""
+    return growth_bound(sens, pos) > pos_tol

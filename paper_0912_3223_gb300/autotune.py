@@ -35,7 +35,8 @@ def signature(cfg) -> str:
              cfg.bin_every, cfg.n_particles, cfg.n_scenarios, cfg.kh is None,
              cfg.rain is None, cfg.vd_dry > 0, cfg.wet_lambda > 0, cfg.lateral_exit,
              cfg.reflect_top, cfg.drift_correction, round(cfg.dt, 6),
-             getattr(cfg, "kz_model", 0), getattr(cfg, "chain_half_lives", None) is not None]
+             getattr(cfg, "kz_model", 0), getattr(cfg, "chain_half_lives", None) is not None,
+             0 if getattr(cfg, "modes", None) is None else len(cfg.modes)]
     return hashlib.sha1(repr(parts).encode()).hexdigest()[:16]
 
 

@@ -93,17 +93,44 @@ __device__ __forceinline__ void warp_count_scen(int s, unsigned long long v, int
     __syncwarp();
 }
 
+// The scenario's perturbation of (u, v) at (x, y, t_k) on level cell k with fraction c:
+// its phases and amplitudes are one 32-byte row msc (see StepParams::mode_sc).
+__device__ __forceinline__ void mode_wind(const StepParams &P, const float *msc, int k, float c,
+                                          float x, float y, float tk, float &du, float &dv)
+{
+    float4 ph, am;
+    ld_pair(reinterpret_cast<const float4 *>(msc), ph, am);
+    const float pa[MAX_MODES] = {ph.x, ph.y, ph.z, ph.w};
+    const float aa[MAX_MODES] = {am.x, am.y, am.z, am.w};
+    float su = 0.0f, sv = 0.0f;
+#pragma unroll
+    for (int m = 0; m < MAX_MODES; ++m) {
+        if (m < P.n_modes) {
+            // phase in cycles; sinpif reduces its argument exactly
+            const float r = fmaf(P.mode_fx[m], x, fmaf(P.mode_fy[m], y, fmaf(P.mode_om[m], tk, pa[m])));
+            const float as = aa[m] * sinpif(2.0f * r);
+            su = fmaf(as, P.mode_eu[m], su);
+            sv = fmaf(as, P.mode_ev[m], sv);
+        }
+    }
+    const float pz = fmaf(c, P.mode_prof[k + 1] - P.mode_prof[k], P.mode_prof[k]);
+    du = pz * su;
+    dv = pz * sv;
+}
+
 // Weather at a point from the time-paired records: 8 spatial corners, each one 32-byte
 // load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z. With the
 // boundary-layer columns (EXT and blp), K_z and its derivative come from Eq. 3 instead
 // (4 more 32-byte loads of the time-paired (u*, 1/L, H_z) at the cell's corner columns,
-// bilinear in x, y); only the EXT instantiations carry that code.
+// bilinear in x, y); with msc (EXT) the scenario's perturbation modes are added to (u, v).
+// Only the EXT instantiations carry that code.
 template <bool EXT, class LEV>
 __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const LEV &L,
                                                const float4 *__restrict__ pair,
                                                const float2 *__restrict__ khp,
                                                const float4 *__restrict__ blp, float f,
-                                               float x, float y, float z)
+                                               float x, float y, float z, float tk = 0.0f,
+                                               const float *msc = nullptr)
 {
     int i, j, k;
     float a, b, c;
@@ -127,6 +154,12 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const LEV &L
     m.u = r.x;
     m.v = r.y;
     m.w = r.z;
+    if (EXT && msc) {
+        float du, dv;
+        mode_wind(P, msc, k, c, x, y, tk, du, dv);
+        m.u += du;
+        m.v += dv;
+    }
     if (EXT && blp) {
         float4 cq[4];
 #pragma unroll
@@ -235,11 +268,12 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV
                                                   const ScenDev *scg, unsigned long long gid,
                                                   int sp, float sig_h_uniform, float du, float dv,
                                                   float &x, float &y, float &z, float *fold,
-                                                  float *wv = nullptr)
+                                                  float *wv = nullptr, const float *msc = nullptr)
 {
     const int k = T.k;
-    // 1. weather at the old position and t_k; 2. diffusivities
-    const Met m = sample_met_pair<EXT>(P, LV, T.pair, T.khp, T.blp, T.ts.f, x, y, z);
+    // 1. weather at the old position and t_k (with the scenario's perturbation modes: msc);
+    // 2. diffusivities
+    const Met m = sample_met_pair<EXT>(P, LV, T.pair, T.khp, T.blp, T.ts.f, x, y, z, T.tk, msc);
     const float sig_h = T.khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
     const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
     // 3. N(0,1) draws
@@ -345,8 +379,9 @@ struct MinBlocks {
 // context): each lane finds its scenario from its home slot and carries its own wind
 // offset; the results are bit-identical to the per-scenario path. EXT adds, as uniform
 // run-time options, the dosage samples (every P.dose_every steps) inside the time loop,
-// K_z from Eq. 3 (P.blpair) and the daughters of a decay chain (P.n_species > 1); the
-// default instantiations carry none of that code.
+// K_z from Eq. 3 (P.blpair), the daughters of a decay chain (P.n_species > 1), the
+// Langevin variant and the scenarios' perturbation modes (P.n_modes > 0); the default
+// instantiations carry none of that code.
 template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
@@ -403,6 +438,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         float wv[PPT];                                  // Langevin w' (EXT)
         float *wsrc = in_a ? R.w_a : R.w_b;
         const bool lang = EXT && P.langevin && wsrc;
+        const bool modes = EXT && P.n_modes > 0 && P.mode_sc;
         int live = 0;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
@@ -489,12 +525,14 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                     }
                     st = particle_step<true, EXT>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
                                                   sp, sig_h_uniform, du, dv, x[j], y[j], z[j],
-                                                  nullptr, lang ? &wv[j] : nullptr);
+                                                  nullptr, lang ? &wv[j] : nullptr,
+                                                  modes ? P.mode_sc + 8 * sj[j] : nullptr);
                 } else {
                     ++steps;
                     st = particle_step<true, EXT>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
                                                   T.du, T.dv, x[j], y[j], z[j], nullptr,
-                                                  lang ? &wv[j] : nullptr);
+                                                  lang ? &wv[j] : nullptr,
+                                                  modes ? P.mode_sc + 8 * tscen : nullptr);
                 }
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;

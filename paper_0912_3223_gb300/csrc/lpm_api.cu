@@ -36,6 +36,8 @@ struct ScenHost {
     double total_mass = 0.0;
     std::vector<double> m0;          // per release step (FP64, host)
     std::vector<float> wind_offset;  // [n_met_t][2] or empty
+    double mode_phase[MAX_MODES] = {};   // this scenario's realisation of the perturbation
+    double mode_amp[MAX_MODES] = {};     // modes (cycles, m/s); amplitude 0 = mode off
 };
 
 }  // namespace
@@ -129,6 +131,13 @@ struct lpm_ctx {
     double t_lagr = 100.0;
     float *d_w_home = nullptr;
     float *d_w_sorted[2] = {nullptr, nullptr};
+
+    // perturbation modes of the scenarios' wind: shared waves and height profile, the
+    // scenarios' phases and amplitudes on the device as 32-byte rows
+    int n_modes = 0;
+    double modes[MAX_MODES][5] = {};        // (fx, fy, omega, eu, ev)
+    std::vector<double> mode_profile;       // [nz]
+    float *d_mode_sc = nullptr;             // [n_scen][8]
 
     // time-integrated dosage
     unsigned long long *d_dose = nullptr;   // [n_scen][cz*cy*cx]
@@ -361,6 +370,16 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.langevin = c->langevin;
     P.t_lagr = (float)c->t_lagr;
     P.kz_min = (float)c->kz_min;
+    P.n_modes = c->d_mode_sc ? c->n_modes : 0;
+    for (int m = 0; m < c->n_modes; ++m) {
+        P.mode_fx[m] = (float)c->modes[m][0];
+        P.mode_fy[m] = (float)c->modes[m][1];
+        P.mode_om[m] = (float)c->modes[m][2];
+        P.mode_eu[m] = (float)c->modes[m][3];
+        P.mode_ev[m] = (float)c->modes[m][4];
+    }
+    for (size_t k = 0; k < c->mode_profile.size(); ++k) P.mode_prof[k] = (float)c->mode_profile[k];
+    P.mode_sc = P.n_modes ? c->d_mode_sc : nullptr;
     P.err = c->d_err;
 }
 
@@ -444,6 +463,18 @@ lpm_status upload_tables(lpm_ctx *c)
     LPM_CUDA(c, cudaMemcpy(c->d_qi, qi.data(), qi.size() * sizeof(short), cudaMemcpyHostToDevice));
     LPM_CUDA(c, cudaMemcpy(c->d_scen, sd.data(), sd.size() * sizeof(ScenDev), cudaMemcpyHostToDevice));
     LPM_CUDA(c, cudaMemcpy(c->d_woff, woff.data(), woff.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    if (c->n_modes > 0) {
+        std::vector<float> rows(c->scen.size() * 8, 0.0f);
+        for (size_t s = 0; s < c->scen.size(); ++s)
+            for (int m = 0; m < c->n_modes; ++m) {
+                rows[s * 8 + (size_t)m] = (float)c->scen[s].mode_phase[m];
+                rows[s * 8 + 4 + (size_t)m] = (float)c->scen[s].mode_amp[m];
+            }
+        if (!c->d_mode_sc)
+            LPM_CUDA(c, cudaMalloc(&c->d_mode_sc, rows.size() * sizeof(float)));
+        LPM_CUDA(c, cudaMemcpy(c->d_mode_sc, rows.data(), rows.size() * sizeof(float),
+                               cudaMemcpyHostToDevice));
+    }
     c->tables_dirty = false;
     c->params_version++;
     drop_graphs(c);
@@ -785,7 +816,7 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair,
                     c->d_sp_conc, c->d_sp_dep, c->d_w_home, c->d_w_sorted[0],
                     c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile, c->d_conv,
-                    c->d_rbin_off, c->d_rbin_idx};
+                    c->d_rbin_off, c->d_rbin_idx, c->d_mode_sc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     {
@@ -910,6 +941,49 @@ lpm_status lpm_set_source(lpm_ctx *c, int scenario, double x, double y, double z
     h.src_x = x; h.src_y = y; h.src_z = z;
     h.wind_offset = wo;
     c->tables_dirty = true;
+    return LPM_OK;
+}
+
+lpm_status lpm_set_modes(lpm_ctx *c, int n_modes, const double *modes, const double *profile)
+{
+    if (!c) return LPM_E_INVALID;
+    if (n_modes < 0 || n_modes > MAX_MODES)
+        return fail(c, LPM_E_INVALID, "n_modes=%d outside [0, %d]", n_modes, MAX_MODES);
+    if (n_modes > 0 && (!modes || !profile))
+        return fail(c, LPM_E_INVALID, "modes and profile are required");
+    for (int i = 0; i < 5 * n_modes; ++i)
+        if (!is_finite(modes[i])) return fail(c, LPM_E_INVALID, "mode parameters not finite");
+    for (int k = 0; n_modes > 0 && k < c->cfg.nz; ++k)
+        if (!is_finite(profile[k])) return fail(c, LPM_E_INVALID, "mode profile not finite");
+    c->n_modes = n_modes;
+    std::memset(c->modes, 0, sizeof c->modes);
+    for (int m = 0; m < n_modes; ++m)
+        for (int q = 0; q < 5; ++q) c->modes[m][q] = modes[5 * m + q];
+    if (n_modes > 0) c->mode_profile.assign(profile, profile + c->cfg.nz);
+    else c->mode_profile.clear();
+    c->tables_dirty = true;
+    c->adj_sig.clear();
+    drop_graphs(c);                          // the graphs hold the step parameters
+    return LPM_OK;
+}
+
+lpm_status lpm_set_mode_phases(lpm_ctx *c, int scenario, const double *phase, const double *amp)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios)
+        return fail(c, LPM_E_INVALID, "scenario %d outside [0, %d)", scenario, c->cfg.n_scenarios);
+    if (c->n_modes > 0 && (!phase || !amp))
+        return fail(c, LPM_E_INVALID, "phase and amp are required");
+    for (int m = 0; m < c->n_modes; ++m)
+        if (!is_finite(phase[m]) || !is_finite(amp[m]))
+            return fail(c, LPM_E_INVALID, "mode phases and amplitudes must be finite");
+    ScenHost &h = c->scen[(size_t)scenario];
+    for (int m = 0; m < MAX_MODES; ++m) {
+        h.mode_phase[m] = m < c->n_modes ? phase[m] : 0.0;
+        h.mode_amp[m] = m < c->n_modes ? amp[m] : 0.0;
+    }
+    c->tables_dirty = true;
+    c->adj_sig.clear();
     return LPM_OK;
 }
 
@@ -1150,7 +1224,8 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.ppt = c->ppt;
         L.occ = c->occ;
         L.mixed = batched;
-        L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 || P.langevin;
+        L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 || P.langevin ||
+                P.n_modes > 0;
         const int n_tiles = L.n_tiles();
         keys_ready = false;
         if (n_tiles <= 0) continue;
@@ -1229,10 +1304,11 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
         if (st != LPM_OK) return st;
     }
     const bool ext = (c->d_dose && c->dose_every > 0) || c->kz_model == 1 || c->n_species > 1 ||
-                     c->langevin;
+                     c->langevin || c->n_modes > 0;
     if (ext && c->ppt != 1)
-        return fail(c, LPM_E_INVALID, "dosage, K_z from Eq. 3, decay chains and the Langevin "
-                                      "variant run with 1 particle per thread");
+        return fail(c, LPM_E_INVALID, "dosage, K_z from Eq. 3, decay chains, the Langevin "
+                                      "variant and perturbation modes run with 1 particle per "
+                                      "thread");
     st = upload_tables(c);
     if (st != LPM_OK) return st;
     if (!c->tiles_valid) {
@@ -2028,6 +2104,8 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     if (g.drift_correction) return fail(c, LPM_E_INVALID, "the adjoint does not support drift_correction");
     if (c->kz_model != 0) return fail(c, LPM_E_INVALID, "the adjoint does not support K_z from Eq. 3");
     if (c->langevin) return fail(c, LPM_E_INVALID, "the adjoint does not support the Langevin variant");
+    if (c->n_modes > 0)
+        return fail(c, LPM_E_INVALID, "the adjoint does not support perturbation modes");
     if (c->n_released != g.n_scenarios)
         return fail(c, LPM_E_STATE, "%d of %d scenarios released", c->n_released, g.n_scenarios);
     if (adj_nq(c) > MAX_NQ) return fail(c, LPM_E_INVALID, "emission series longer than %d", MAX_NQ);

@@ -23,6 +23,7 @@ constexpr uint32_t TAG_STEP = 0x0FFFFFFFu;
 constexpr int MAX_LEVELS = 64;
 constexpr int MAX_LUT = 4096;          // entries of the vertical level lookup table
 constexpr int MAX_SPECIES = 4;         // decay chain: parent and up to 3 daughters
+constexpr int MAX_MODES = 4;           // perturbation modes of a scenario's wind
 
 // Per-scenario counters (64-bit, fixed point unless noted).
 enum {
@@ -112,6 +113,15 @@ struct StepParams {
     // vertical Langevin variant: turbulent velocity w' per particle (in the Ranges)
     int langevin;
     float t_lagr;                    // Lagrangian time scale T_L (s)
+    // perturbed weather of the scenarios: n_modes plane waves of a horizontal
+    // streamfunction, (u', v') = p(z) sum_m amp_sm (eu_m, ev_m)
+    // sin(2 pi (fx_m x + fy_m y + phase_sm + om_m t)); the waves and the profile p (at the
+    // levels) are shared, each scenario s has its own phases and amplitudes
+    int n_modes;                     // 0: off
+    float mode_fx[MAX_MODES], mode_fy[MAX_MODES], mode_om[MAX_MODES];
+    float mode_eu[MAX_MODES], mode_ev[MAX_MODES];
+    float mode_prof[MAX_LEVELS];
+    const float *mode_sc;            // [n_scen][8]: phases (cycles), amplitudes (m/s); 32-B rows
     unsigned int *err;
 };
 

@@ -31,7 +31,8 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_receptors", "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save",
            "lpm_load", "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model",
            "lpm_set_boundary_layer", "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
-           "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage"]
+           "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage",
+           "lpm_set_modes", "lpm_set_mode_phases"]
 
 
 class LpmError(RuntimeError):
@@ -115,6 +116,8 @@ def load() -> C.CDLL:
     L.lpm_adjoint.argtypes = [vp, dp, C.c_int, C.c_double, C.c_int, dp, dp]
     L.lpm_set_adjoint_storage.argtypes = [vp, C.c_uint64]
     L.lpm_adjoint_storage.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_uint64)]
+    L.lpm_set_modes.argtypes = [vp, C.c_int, dp, dp]
+    L.lpm_set_mode_phases.argtypes = [vp, C.c_int, dp, dp]
     L.lpm_draws_static.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
                                    C.c_uint32, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
     L.lpm_draws.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
@@ -127,7 +130,8 @@ def load() -> C.CDLL:
                  "lpm_adjoint", "lpm_draws_static", "lpm_set_sort", "lpm_save", "lpm_load",
                  "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model", "lpm_set_boundary_layer",
                  "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
-                 "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage"):
+                 "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage",
+                 "lpm_set_modes", "lpm_set_mode_phases"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -199,6 +203,27 @@ def lpm_set_met(ctx, t_index: int, uvwk, kh=None, rain=None) -> None:
     b, _ = _addr(kh)
     r, _ = _addr(rain)
     _check(ctx, load().lpm_set_met(C.c_void_p(ctx), int(t_index), a, b, r, dev))
+
+
+MAX_MODES = 4
+
+
+def lpm_set_modes(ctx, modes, profile) -> None:
+    """Perturbation modes shared by the scenarios: ``modes`` [n][5] = (fx, fy, omega, eu,
+    ev), ``profile`` [nz]; an empty ``modes`` turns them off."""
+    m = np.ascontiguousarray(np.zeros((0, 5)) if modes is None else modes,
+                             dtype=np.float64).reshape(-1, 5)
+    prof = None if profile is None else np.ascontiguousarray(profile, dtype=np.float64)
+    _check(ctx, load().lpm_set_modes(C.c_void_p(ctx), m.shape[0], _ptr(m, C.c_double),
+                                     _ptr(prof, C.c_double)))
+
+
+def lpm_set_mode_phases(ctx, scenario: int, phase, amp) -> None:
+    """A scenario's phases (cycles) and amplitudes (m/s) of the modes."""
+    ph = np.ascontiguousarray(phase, dtype=np.float64)
+    am = np.ascontiguousarray(amp, dtype=np.float64)
+    _check(ctx, load().lpm_set_mode_phases(C.c_void_p(ctx), int(scenario), _ptr(ph, C.c_double),
+                                           _ptr(am, C.c_double)))
 
 
 def lpm_set_source(ctx, scenario: int, x: float, y: float, z: float, wind_offset=None) -> None:
@@ -506,6 +531,12 @@ class Sim:
                 lpm_set_kz_model(self.ctx, cfg.kz_model, cfg.kz_min)
                 for t in range(cfg.n_met_t):
                     lpm_set_boundary_layer(self.ctx, t, cfg.bl[t])
+            modes = getattr(cfg, "modes", None)
+            if modes is not None and len(modes):
+                lpm_set_modes(self.ctx, modes, cfg.mode_profile)
+                for i, sc in enumerate(cfg.scenarios or [cfg]):
+                    if getattr(sc, "mode_phase", None) is not None:
+                        lpm_set_mode_phases(self.ctx, i, sc.mode_phase, sc.mode_amp)
             if cfg.scenarios:
                 for i, sc in enumerate(cfg.scenarios):
                     lpm_set_source(self.ctx, i, sc.src_x, sc.src_y, sc.src_z, sc.wind_offset)

@@ -1,4 +1,5 @@
-"""Batched ensemble: many scenarios (own source, release, emission series, wind offset)
+"""Batched ensemble: many scenarios (own source, release, emission series and perturbed
+weather: an hourly wind offset plus the scenario's realisation of the perturbation modes)
 in one persistent launch replayed from a CUDA graph, checked against the oracle scenario
 by scenario, against single-scenario contexts bit for bit, and across graph replays."""
 import dataclasses
@@ -109,7 +110,7 @@ def test_graph_replay_is_identical(small_ensemble):
 
 def test_scenario_equals_single_context(small_ensemble):
     """Scenario s of the ensemble equals a plain context holding the same release with the
-    same global ids (id_base), source and wind offset."""
+    same global ids (id_base), source, wind offset and perturbation modes."""
     from paper_0912_3223_gb300 import lpm
     cfg = small_ensemble
     (xyz, tag, scen), = _run(cfg)
@@ -124,6 +125,9 @@ def test_scenario_equals_single_context(small_ensemble):
         for t in range(one.n_met_t):
             lpm.lpm_set_met(ctx, t, one.uvwk[t], None, one.rain[t])
         lpm.lpm_set_source(ctx, 0, sc.src_x, sc.src_y, sc.src_z, sc.wind_offset)
+        if cfg.modes is not None:
+            lpm.lpm_set_modes(ctx, cfg.modes, cfg.mode_profile)
+            lpm.lpm_set_mode_phases(ctx, 0, sc.mode_phase, sc.mode_amp)
         r = sc.release
         lpm.lpm_release_range(ctx, 0, r.n_particles, 0, r.n_particles, r.q, r.q_dt,
                               r.first_step, r.last_step, off)

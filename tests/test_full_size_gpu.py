@@ -9,7 +9,8 @@ import pytest
 
 import lpm_inputs as li
 import oracle
-from parity_util import POS_TOL_M
+from parity_util import (FACE_EPS_M, POS_TOL_M, _cell_mask, _grid_l1, compare, face_distance,
+                         gpu_state, oracle_sharded)
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -211,3 +212,114 @@ def test_decay_chain_full_size_sampled():
         sim.step(360)
         xyz, tag = sim.particles()
     assert _check_sample(cfg, xyz[sel], tag[sel], sel, 360, "decay chain, 1e7 sample") > 100
+
+
+def _late_grid_report(cfg, g, o):
+    """Late in a run, where chaotic paths have diverged: the status agreement, the grid's
+    relative L1 with only the 1e-3 m face band excluded, and with the cells of diverged
+    particles (other status, or more than 0.5 m apart) and of particles closer to a face
+    than their own distance also excluded."""
+    same = g["status"] == o["status"]
+    dist = np.linalg.norm(g["pos"] - o["pos"], axis=1)
+    diverged = ~same | (dist > POS_TOL_M)
+    fd = face_distance(cfg, o["pos"])
+    l1_band = _grid_l1(cfg, g, o, _cell_mask(cfg, fd < FACE_EPS_M, g, o))
+    mask = _cell_mask(cfg, diverged | (fd < np.maximum(FACE_EPS_M, dist)), g, o)
+    return same, l1_band, _grid_l1(cfg, g, o, mask), int(diverged.sum()), int((~mask).sum())
+
+
+def _released_by(cfg, n_run):
+    """Particles released before step n_run (p < ceil(n_run N / S): release order)."""
+    return -(-n_run * cfg.n_particles // cfg.n_steps)
+
+
+def test_cfg1_full_size_grids_against_the_oracle():
+    """The benchmark's workload in full (1e7 particles, 2880 x 30 s, the benchmark's launch
+    shape and sort interval) against the oracle run over every particle, sharded over the
+    host cores (Sec. 4.1 compares the gridded activities of whole runs): at the first
+    hourly snapshot (step 120) every released particle and the concentration and
+    deposition grids cell by cell (1e-4 relative L1 outside the face-ambiguous cells, and
+    reported with only the 1e-3 m face band excluded); after 360 steps every released
+    particle (0.5 m); at 24 h the grids and distances are reported and the exact
+    identities checked."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_cfg1()
+    n120, n360 = _released_by(cfg, 120), _released_by(cfg, 360)
+    with Sim(cfg) as sim:
+        sim.step(120)
+        g120 = gpu_state(sim, cfg, n120)
+        sim.step(240)
+        g360 = gpu_state(sim, cfg, n360, grids=False)
+        sim.step(cfg.n_steps - 360)
+        g_end = gpu_state(sim, cfg, cfg.n_particles)
+    o = oracle_sharded(cfg, 120, n120)
+    rep = compare(cfg, g120, o, sens=o["sens"])
+    print(f"1e7 particles, step 120 ({n120} released): {rep}")
+    assert int(g120["counters"][4]) == o["active_steps"]
+    ctr = g120["counters"]
+    assert int(g120["conc_fixed"].sum()) + int(ctr[0]) == int(ctr[6]) + int(ctr[7])
+    o = oracle_sharded(cfg, 360, n360)
+    rep = compare(cfg, g360, o, check_grid=False, sens=o["sens"])
+    print(f"1e7 particles, step 360 ({n360} released): {rep}")
+    assert rep["chaotic"] + rep["near_event"] < 0.01 * n360
+    # 24 h: chaotic divergence grows with time (Sec. 4.1 saw tens of metres); report
+    o = oracle_sharded(cfg, cfg.n_steps, cfg.n_particles, with_sens=False)
+    same, l1_band, l1_conv, n_div, n_cells = _late_grid_report(cfg, g_end, o)
+    dist = np.linalg.norm(g_end["pos"] - o["pos"], axis=1)
+    d = dist[same & (o["status"] == li.STATUS_ACTIVE)]
+    print(f"1e7 particles, 24 h: status agrees for {same.mean():.6f} of the particles; "
+          f"airborne distance median {np.median(d):.3g} m, 99th pct {np.percentile(d, 99):.3g} m, "
+          f"max {d.max():.3g} m; grid rel L1 {l1_band:.3g} (face band only), {l1_conv:.3g} "
+          f"(also without the {n_cells} cells of the {n_div} diverged particles)")
+    assert same.mean() > 0.95
+    assert l1_conv <= 1e-4
+    ctr = g_end["counters"]
+    assert int(g_end["conc_fixed"].sum()) + int(ctr[0]) == int(ctr[6]) + int(ctr[7])
+    assert int(g_end["counters"][4]) == pytest.approx(o["active_steps"], rel=1e-3)
+    b = g_end["budget"]
+    assert b[0] == pytest.approx(o["budget"][0], rel=1e-9)
+
+
+def test_batched_full_size_scenarios_against_the_oracle():
+    """Four whole scenarios of the 256-scenario ensemble (5.38e7 particles in one graph,
+    sorted by cell, per-scenario perturbed weather) at their full particle counts against
+    the oracle: every released particle after 360 steps (0.5 m) and, at the end of the
+    12 h run, each scenario's surface-layer and deposition grids (reported with the face
+    band only; gated at 1e-4 outside the cells of particles that diverged)."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_cfg2()
+    n = [sc.release.n_particles for sc in cfg.scenarios]
+    first = np.concatenate([[0], np.cumsum(n)[:-1]])
+    order = np.argsort(n)
+    picked = [int(order[0]), int(order[len(n) // 3]), int(order[2 * len(n) // 3]),
+              int(order[-1])]
+    vol = cfg.cdx * cfg.cdy * cfg.cdz
+    area = cfg.cdx * cfg.cdy
+    g360, g_end = {}, {}
+    with Sim(cfg) as sim:
+        sim.step(360)
+        for s in picked:
+            xyz, tag = sim.particles(int(first[s]), n[s])
+            g360[s] = dict(pos=xyz.astype(np.float64), tag=tag,
+                           status=(tag >> 28).astype(np.int32),
+                           release=(tag & 0x0FFFFFFF).astype(np.int64))
+        sim.step(cfg.n_steps - 360)
+        for s in picked:
+            xyz, tag = sim.particles(int(first[s]), n[s])
+            dry, wet = sim.deposition(s)
+            g_end[s] = dict(pos=xyz.astype(np.float64), tag=tag,
+                            status=(tag >> 28).astype(np.int32),
+                            release=(tag & 0x0FFFFFFF).astype(np.int64),
+                            conc_mass=sim.concentration(s) * vol,
+                            dep_mass=np.stack([dry, wet]) * area)
+    for s in picked:
+        o = oracle_sharded(cfg, 360, n[s], scenario=s)
+        rep = compare(cfg, g360[s], o, check_grid=False, sens=o["sens"])
+        print(f"scenario {s} ({n[s]} particles), step 360: {rep}")
+        o = oracle_sharded(cfg, cfg.n_steps, n[s], with_sens=False, scenario=s)
+        same, l1_band, l1_conv, n_div, n_cells = _late_grid_report(cfg, g_end[s], o)
+        print(f"scenario {s}, 12 h: status agrees for {same.mean():.5f}, grid rel L1 "
+              f"{l1_band:.3g} (face band only), {l1_conv:.3g} (without the {n_cells} cells "
+              f"of the {n_div} diverged particles)")
+        assert same.mean() > 0.95
+        assert l1_conv <= 1e-4
