@@ -595,37 +595,62 @@ def run_gpu(args):
     import torch
 
     import lpm_inputs as li
-    from paper_0912_3223_gb300 import Sim, lpm
+    from paper_0912_3223_gb300 import Sim, lpm, parallel
     from paper_0912_3223_gb300 import build as pkg_build
 
     rank = _env_int("RANK", 0)
     world = _env_int("WORLD_SIZE", 1)
     local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    store = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        store = dist.distributed_c10d._get_default_store()
     pkg_build.build()
     lpm.load()
 
-    cfg = li.make_cfg1()
-    # weak scaling: each rank runs its own realisation (key seed + rank) of the workload
-    if world > 1:
-        import dataclasses
-        cfg = dataclasses.replace(cfg, seed=cfg.seed + rank)
+    # weak scaling: N GPUs run one release of N x 1e7 particles, each rank holding a
+    # contiguous range of 1e7 (the same keyed draws as a single run of the whole release);
+    # at every hourly snapshot the ranks sum their fixed-point grids and counters on the
+    # device (one int64 all-reduce over NCCL), the exchange step of a partitioned run
+    per_rank = 10_000_000                        # the realistic workload's particles
+    cfg = li.make_cfg1(n_particles=per_rank * world)
+    part = parallel.partition(cfg.n_particles, world, rank) if world > 1 else None
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt, args.occ),
-                  sort_every=args.sort_every)
+                  sort_every=args.sort_every, part=part)
+    if args.regroup:
+        lpm.lpm_set_regroup(sim.ctx, args.regroup)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    exchange = parallel.SnapshotExchange(sim) if world > 1 else None
+    ex_events = []
+    runs = [0]
+
+    def timed_exchange():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        exchange()
+        e1.record(stream)
+        ex_events.append((e0, e1))
 
     def one_run():
         sim.reset()
-        sim.step(cfg.n_steps)
+        if exchange is None:
+            sim.step(cfg.n_steps)
+        else:
+            runs[0] += 1
+            for _ in parallel.run_partitioned(sim, cfg.n_steps, cfg.bin_every, timed_exchange,
+                                              store=store, world=world, rank=rank,
+                                              timeout_s=60.0, run_tag=f"run{runs[0]}/"):
+                pass
 
     for _ in range(args.warmup):
         one_run()
     torch.cuda.synchronize()
+    ex_events.clear()
     lpm.lpm_stats(sim.ctx)
     lpm.lpm_set_profiling(sim.ctx, True)
     if world > 1:
@@ -650,6 +675,8 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
+    ex_ms = sum(a.elapsed_time(b) for a, b in ex_events)
+    n_ex = len(ex_events)
     launches, adv_launches, adv_ms = lpm.lpm_stats(sim.ctx)
     lpm.lpm_set_profiling(sim.ctx, False)
     t_total = sum(times) / 1e3
@@ -667,7 +694,13 @@ def run_gpu(args):
     # snapshots, deposition and budget out, every step
     pinned_uvwk = torch.from_numpy(cfg.uvwk).pin_memory()
     pinned_rain = torch.from_numpy(cfg.rain).pin_memory()
-    conc = torch.empty((cfg.cz, cfg.cy, cfg.cx), dtype=torch.float64, pin_memory=True).numpy()
+    conc_t = torch.empty((cfg.cz, cfg.cy, cfg.cx), dtype=torch.float64, pin_memory=True)
+    dep_t = torch.empty((2, cfg.cy, cfg.cx), dtype=torch.float64, pin_memory=True)
+    conc = conc_t.numpy()
+    if exchange is not None:
+        unit = 2.0 ** -int(sim.fixed_state()[3])         # fixed-point unit (mass)
+        conc_f = unit / (cfg.cdx * cfg.cdy * cfg.cdz)
+        dep_f = unit / (cfg.cdx * cfg.cdy)
     h2d = pinned_uvwk.numel() * 4 + pinned_rain.numel()
     d2h = conc.nbytes + 2 * cfg.cy * cfg.cx * 8 + 8 * 8
     e2e_t, e2e_p = 0.0, 0
@@ -679,8 +712,15 @@ def run_gpu(args):
         for t in range(cfg.n_met_t):
             lpm.lpm_set_met(sim.ctx, t, pinned_uvwk[t], None, pinned_rain[t])
         one_run()
-        sim.concentration(out=conc)
-        dry, wet = sim.deposition()
+        if exchange is None:
+            sim.concentration(out=conc)
+            dry, wet = sim.deposition()
+        else:
+            # the whole release's grids, from the last exchange, converted on the device
+            with torch.cuda.stream(stream):
+                conc_t.copy_(exchange.conc.to(torch.float64) * conc_f)
+                dep_t.copy_(exchange.dep.to(torch.float64) * dep_f)
+            stream.synchronize()
         b = sim.budget()
         if i < max(1, args.warmup):
             continue
@@ -707,6 +747,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "particles": cfg.n_particles, "steps_per_run": cfg.n_steps,
                    "dt_s": cfg.dt, "met": [cfg.n_met_t, cfg.nz, cfg.ny, cfg.nx],
                    "launch": [args.block, args.ppt, args.occ], "sort_every": args.sort_every,
+                   "regroup_every": args.regroup,
                    "l2": "flushed (256 MB write) between timed steps",
                    "active_particle_steps_per_run": sum(active) // max(1, len(active)),
                    "slot_steps_per_run": cfg.n_particles * cfg.n_steps},
@@ -716,6 +757,15 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if world > 1:
+        line["config"]["partition"] = (f"one release of {cfg.n_particles} particles, "
+                                       f"{per_rank} per rank (contiguous id ranges)")
+        line["exchange"] = {
+            "what": "int64 all-reduce (NCCL) of the hourly snapshot, deposition grids and "
+                    "counters, on the device",
+            "per_run": n_ex // max(1, args.steps), "bytes_per_rank": exchange.bytes,
+            "ms_per_run": ex_ms / max(1, args.steps),
+            "share_of_step": ex_ms / max(1e-9, sum(times))}
     if not args.no_forms:
         forms = {"batched": measure_batched(args, stream),
                  "adjoint": measure_adjoint(args, stream),
@@ -740,6 +790,19 @@ def run_gpu(args):
     return 0
 
 
+def relaunch_distributed(n: int) -> int:
+    """``--gpus N`` outside a distributed launcher: run this command again as N ranks on
+    this node (torch.distributed.run, rendezvous on 127.0.0.1) and return its status."""
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)]
+    return subprocess.call(cmd + sys.argv[1:])
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -751,6 +814,9 @@ def main():
     ap.add_argument("--occ", type=int, default=2)
     ap.add_argument("--sort-every", type=int, default=60,
                     help="re-order the particles by weather cell every N steps (0 = off)")
+    ap.add_argument("--regroup", type=int, default=0,
+                    help="re-order each block's particles by cell inside the step kernel every "
+                         "N steps (0 = off)")
     ap.add_argument("--ref-stride", type=int, default=100,
                     help="particle sample stride of each --impl reference step")
     ap.add_argument("--cpu-stride", type=int, default=30,
@@ -772,6 +838,12 @@ def main():
     ap.add_argument("--batched-sort-every", type=int, default=60,
                     help="steps between sorts by cell in the batched form (0: off)")
     args = ap.parse_args()
+    world = _env_int("WORLD_SIZE", 0)
+    if args.gpus > 1 and world == 0:
+        return relaunch_distributed(args.gpus)
+    if world and args.gpus != world:
+        print(f"--gpus {args.gpus} does not match WORLD_SIZE={world}", file=sys.stderr)
+        return 2
     if args.impl == "reference":
         return run_reference(args)
     if args.only:

@@ -246,12 +246,39 @@ lpm_status lpm_particles(lpm_ctx *ctx, int64_t first, int64_t count, float *xyz,
 lpm_status lpm_fixed_state(lpm_ctx *ctx, int scenario, uint64_t *conc, size_t n_conc,
                            uint64_t *dep, size_t n_dep, int64_t counters[16], int *shift);
 
+/*
+ * Device addresses of the same fixed-point state, for a partitioned run that sums its
+ * partitions' grids on the device (particles never interact, Sec. 4.2, so the grids of
+ * the whole release are the integer sums of the partitions' grids; see
+ * lpm_release_range). *conc: [cz][cy][cx] uint64 of the last snapshot; *dep: [2][cy][cx]
+ * uint64, cumulative since lpm_reset; counter i of the scenario (the order of
+ * lpm_fixed_state's counters; n_bins is not kept on the device) at
+ * (*counters)[i * *counter_stride]. Any output pointer may be NULL. The memory belongs to
+ * the context until lpm_destroy and must not be written; its contents are those left by
+ * the work enqueued so far on the context stream, so readers order themselves after that
+ * stream (lpm_sync, or work on the same stream). Errors: LPM_E_INVALID for a scenario
+ * out of range.
+ */
+lpm_status lpm_device_state(lpm_ctx *ctx, int scenario, const uint64_t **conc,
+                            const uint64_t **dep, const uint64_t **counters,
+                            int64_t *counter_stride);
+
 /* Launch shape of the particle kernels: threads per block (128, 256 or 512), particles
  * per thread (1, 2 or 4) and occupancy variant (0, 1, 2: at most 128, 80 or 64 registers
  * per thread, i.e. 16, 24 or 32 resident warps per SM). Default 512 x 1 x 2. Results do
  * not depend on it. The paper tuned its launch (32 blocks of 256 threads) with the
  * occupancy calculator (Sec. 3.2); here the autotuner picks among these shapes. */
 lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int occupancy);
+
+/*
+ * In-block regroup of the step kernel (a layout choice, no change to what is computed):
+ * with one particle per thread, every every_steps steps each block re-orders its
+ * particles by weather cell through shared memory, the ones that no longer move last, so
+ * that a warp's lanes share weather records and finished warps idle together. Results
+ * are bit-identical to every_steps = 0 (off). Errors: LPM_E_INVALID for every_steps < 0
+ * or 2^22 scenarios or more.
+ */
+lpm_status lpm_set_regroup(lpm_ctx *ctx, int every_steps);
 
 /* Every every_steps steps (at the multiples of every_steps), re-order the released
  * particles of all scenarios in device memory by the weather cell they occupy, so that

@@ -103,6 +103,7 @@ struct lpm_ctx {
     long long k = 0;                        // steps taken
     long long n_bins = 0;                   // snapshots taken
     int block = 512, ppt = 1, occ = 2;
+    int regroup = 0;                        // in-block regroup interval (steps; 0: off)
 
     // sorting by weather cell (both forms) at the multiples of sort_every: d_state is the
     // home buffer (slot order of the API); the live particles released before sorted_upto
@@ -380,6 +381,7 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     }
     for (size_t k = 0; k < c->mode_profile.size(); ++k) P.mode_prof[k] = (float)c->mode_profile[k];
     P.mode_sc = P.n_modes ? c->d_mode_sc : nullptr;
+    P.regroup = c->ppt == 1 ? c->regroup : 0;
     P.err = c->d_err;
 }
 
@@ -1373,8 +1375,9 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
             if (!c->cap_stream)
                 LPM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
             const cudaStream_t cs = c->cap_stream;
-            const int occ_blocks = std::max(1, advance_occupancy(c->block, c->ppt, c->occ, true,
-                                                                 ext));
+            const int occ_blocks = std::max(1, advance_occupancy(
+                c->block, c->ppt, c->occ, true, ext,
+                adv_dyn_smem(c->block, c->ppt, ext, P.regroup, P.n_lut)));
             lpm_ctx::Graph ng{};
             ng.k0 = c->k;
             ng.k1 = k_end;
@@ -1592,6 +1595,30 @@ lpm_status lpm_fixed_state(lpm_ctx *c, int scenario, uint64_t *conc, size_t n_co
         counters[C_N_BINS] = c->n_bins;
     }
     if (shift) *shift = c->scen[(size_t)scenario].shift;
+    return LPM_OK;
+}
+
+lpm_status lpm_device_state(lpm_ctx *c, int scenario, const uint64_t **conc, const uint64_t **dep,
+                            const uint64_t **counters, int64_t *counter_stride)
+{
+    if (!c) return LPM_E_INVALID;
+    if (scenario < 0 || scenario >= c->cfg.n_scenarios) return fail(c, LPM_E_INVALID, "bad scenario");
+    const size_t s = (size_t)scenario;
+    if (conc) *conc = reinterpret_cast<const uint64_t *>(c->d_conc + s * c->ncell());
+    if (dep) *dep = reinterpret_cast<const uint64_t *>(c->d_dep + s * c->ndep());
+    if (counters) *counters = reinterpret_cast<const uint64_t *>(c->d_ctr + s);
+    if (counter_stride) *counter_stride = c->cfg.n_scenarios;
+    return LPM_OK;
+}
+
+lpm_status lpm_set_regroup(lpm_ctx *c, int every_steps)
+{
+    if (!c) return LPM_E_INVALID;
+    if (every_steps < 0) return fail(c, LPM_E_INVALID, "every_steps must be >= 0");
+    if (every_steps > 0 && c->cfg.n_scenarios >= (1 << 22))
+        return fail(c, LPM_E_INVALID, "the regroup carries scenario indices below 2^22");
+    c->regroup = every_steps;
+    drop_graphs(c);                          // the graphs hold the step parameters
     return LPM_OK;
 }
 

@@ -122,6 +122,9 @@ struct StepParams {
     float mode_eu[MAX_MODES], mode_ev[MAX_MODES];
     float mode_prof[MAX_LEVELS];
     const float *mode_sc;            // [n_scen][8]: phases (cycles), amplitudes (m/s); 32-B rows
+    // the advance launch re-orders each block's particles by weather cell every `regroup`
+    // steps (one particle per thread; 0: never)
+    int regroup;
     unsigned int *err;
 };
 
@@ -221,10 +224,24 @@ __device__ __forceinline__ void ld_pair(const float4 *p, float4 &a, float4 &b)
         : "l"(p));
 }
 
-// Uniform on (0,1): midpoint of one of 2^23 equal bins, exact in FP32.
+// Uniform on (0,1): midpoint of one of 2^23 equal bins, (2 (w >> 9) + 1) 2^-24, exact in
+// FP32. Built from the bits: 1 + (w >> 9) 2^-23 has the 23 bits as its mantissa, and
+// subtracting 1 - 2^-24 (exact: the difference has at most 24 significant bits) leaves
+// the bin midpoint.
 __device__ __forceinline__ float unit_uniform(uint32_t w)
 {
-    return __uint2float_rn(2u * (w >> 9) + 1u) * 5.9604644775390625e-08f;
+    return __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994039535522461f;
+}
+
+// Square root of x in [2^-126, 2^127) from the hardware reciprocal square root and one
+// Newton step for the root (s = x y, s + (x - s^2) y / 2): within one ulp of the correctly
+// rounded root, without the special-case path of the IEEE square root (the Box-Muller
+// radius never meets zero, infinities or subnormals).
+__device__ __forceinline__ float sqrt_normal(float x)
+{
+    const float y = rsqrtf(x);
+    const float s = x * y;
+    return fmaf(fmaf(-s, s, x), 0.5f * y, s);
 }
 
 // Three N(0,1) by the basic Box-Muller transform (Sec. 2): (u0,u1) -> n0, n1;
@@ -233,11 +250,11 @@ __device__ __forceinline__ void normals3(const U4 &w, float &n0, float &n1, floa
 {
     const float u0 = unit_uniform(w.a), u1 = unit_uniform(w.b);
     const float u2 = unit_uniform(w.c), u3 = unit_uniform(w.d);
-    // accurate logarithm, square root and sin/cos of pi*x: the near-ground wind shear
-    // amplifies vertical rounding into horizontal displacement, so the draws stay within
-    // a few ulp of the FP64 values
-    const float r0 = sqrtf(-2.0f * logf(u0));
-    const float r1 = sqrtf(-2.0f * logf(u2));
+    // accurate logarithm and sin/cos of pi*x, a square root within one ulp: the
+    // near-ground wind shear amplifies vertical rounding into horizontal displacement, so
+    // the draws stay within a few ulp of the FP64 values (-2 ln u lies in [1.2e-7, 33.3])
+    const float r0 = sqrt_normal(-2.0f * logf(u0));
+    const float r1 = sqrt_normal(-2.0f * logf(u2));
     float s1, c1;
     sincospif(2.0f * u1, &s1, &c1);
     n0 = r0 * c1;

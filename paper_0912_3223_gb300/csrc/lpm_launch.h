@@ -110,14 +110,24 @@ cudaError_t launch_release(cudaStream_t s, float4 *state, long long first_slot, 
                            long long part_first, long long n_total, int rel_first, int rel_len,
                            float sx, float sy, float sz);
 cudaError_t launch_release_all(cudaStream_t s, const StepParams &P, float4 *state, long long n_slots);
+// Bytes of dynamic shared memory of an advance launch: the in-block regroup's particle
+// exchange (one particle per thread, every `regroup` steps; with the extended options also
+// the Langevin w'), then the vertical level table.
+inline size_t adv_dyn_smem(int block, int ppt, bool ext, int regroup, int n_lut)
+{
+    size_t b = 0;
+    if (ppt == 1 && regroup > 0) b += (size_t)block * (16 + (ext ? 4 : 0));
+    return b + (((size_t)(n_lut > 0 ? n_lut : 0) + 15) & ~(size_t)15);
+}
+
 cudaError_t launch_advance(const AdvanceLaunch &L);
-int advance_occupancy(int block, int ppt, int occ, bool mixed, bool ext);
+int advance_occupancy(int block, int ppt, int occ, bool mixed, bool ext, size_t smem);
 cudaError_t launch_advance_b128(const AdvanceLaunch &L);
 cudaError_t launch_advance_b256(const AdvanceLaunch &L);
 cudaError_t launch_advance_b512(const AdvanceLaunch &L);
-int occupancy_b128(int ppt, int occ, bool mixed, bool ext);
-int occupancy_b256(int ppt, int occ, bool mixed, bool ext);
-int occupancy_b512(int ppt, int occ, bool mixed, bool ext);
+int occupancy_b128(int ppt, int occ, bool mixed, bool ext, size_t smem);
+int occupancy_b256(int ppt, int occ, bool mixed, bool ext, size_t smem);
+int occupancy_b512(int ppt, int occ, bool mixed, bool ext, size_t smem);
 cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
                         const float *kb, float4 *pair, float2 *khpair, int nx, int ny, int nz);
 cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &in,

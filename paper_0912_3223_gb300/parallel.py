@@ -18,10 +18,18 @@ scaled back, so the reduced value does not depend on the order in which ranks ar
 For a loss that is not linear in the concentrations, the receptor sums are reduced first,
 every rank forms the same dL/dC from them, and the gradients taken with it are reduced
 second.
+
+On GPUs the exchange works on the library's device grids directly (``SnapshotExchange``:
+one device copy into a staging buffer and one integer all-reduce, NCCL between GPUs). A
+rank that leaves between steps is detected on the host before the next exchange: every
+rank announces each exchange in the process group's store and waits, for a bounded time,
+for the others' announcements (``check_ranks``), so the survivors raise ``RankLost``
+naming the missing ranks instead of entering a collective that cannot complete.
 """
 from __future__ import annotations
 
-from typing import Tuple
+import time
+from typing import Iterable, List, Tuple
 
 import numpy as np
 
@@ -123,3 +131,106 @@ def adjoint_partitioned(sim, receptors, bandwidth: float, sample_every: int, dL_
     from . import lpm
     g = lpm.lpm_adjoint(sim.ctx, receptors, bandwidth, sample_every, dL_dC, n_q)
     return allreduce_float_fixed(g, group, device)
+
+
+# ------------------------------------------------------------------------------------
+# The exchange on the device, and rank liveness
+# ------------------------------------------------------------------------------------
+N_COUNTERS = 16
+
+
+class _DeviceWords:
+    """A library-owned device array described by the CUDA array interface (no copy; the
+    exchange only reads it)."""
+
+    def __init__(self, ptr: int, n: int, stride: int = 1):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (ptr, False),
+                                         "strides": (8 * stride,), "version": 2}
+
+
+class SnapshotExchange:
+    """The exchange step of a run partitioned by particle ranges, on the device: the
+    context's last snapshot, cumulative deposition grids and counters (scenario 0) are
+    copied, on the context stream, into one staging buffer and summed over the ranks by
+    one int64 all-reduce; the context's own state is left as it is (the deposition grids
+    keep accumulating each rank's own deposits). After ``__call__`` the attributes
+    ``conc``, ``dep`` and ``counters`` hold the whole release's fixed-point state."""
+
+    def __init__(self, sim, group=None):
+        import torch
+        from . import lpm
+        self.sim, self.group = sim, group
+        cfg = sim.cfg
+        conc, dep, ctr, stride = lpm.lpm_device_state(sim.ctx, 0)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.n_conc = cfg.cz * cfg.cy * cfg.cx
+        self.n_dep = 2 * cfg.cy * cfg.cx
+        self._src = [torch.as_tensor(_DeviceWords(conc, self.n_conc), device=dev),
+                     torch.as_tensor(_DeviceWords(dep, self.n_dep), device=dev),
+                     torch.as_tensor(_DeviceWords(ctr, N_COUNTERS, stride), device=dev)]
+        self.buf = torch.empty(self.n_conc + self.n_dep + N_COUNTERS, dtype=torch.int64,
+                               device=dev)
+        self.conc = self.buf[:self.n_conc].view(cfg.cz, cfg.cy, cfg.cx)
+        self.dep = self.buf[self.n_conc:self.n_conc + self.n_dep].view(2, cfg.cy, cfg.cx)
+        self.counters = self.buf[self.n_conc + self.n_dep:]
+
+    @property
+    def bytes(self) -> int:
+        """Bytes each rank contributes to one exchange."""
+        return int(self.buf.numel() * 8)
+
+    def __call__(self):
+        import torch
+        import torch.distributed as dist
+        with torch.cuda.stream(self.sim.stream):
+            torch.cat(self._src, out=self.buf)
+            if dist.is_initialized() and dist.get_world_size(self.group) > 1:
+                dist.all_reduce(self.buf, op=dist.ReduceOp.SUM, group=self.group)
+        return self
+
+
+class RankLost(RuntimeError):
+    """Ranks that did not reach an exchange within the time limit (they left the run)."""
+
+    def __init__(self, missing: List[int], tag: str):
+        self.missing = list(missing)
+        self.tag = tag
+        super().__init__(f"rank(s) {self.missing} did not reach exchange {tag!r}: they left "
+                         "the partitioned run")
+
+
+def check_ranks(store, tag: str, world: int, rank: int, timeout_s: float = 10.0,
+                poll_s: float = 0.01) -> None:
+    """Announces that this rank reached the exchange ``tag`` and waits, at most
+    ``timeout_s``, for every other rank's announcement; raises ``RankLost`` with the ranks
+    still missing. Host only: nothing waits on the device."""
+    store.set(f"lpm/alive/{tag}/{rank}", "1")
+    missing = set(range(world)) - {rank}
+    deadline = time.monotonic() + timeout_s
+    while missing:
+        for r in sorted(missing):
+            if store.check([f"lpm/alive/{tag}/{r}"]):
+                missing.discard(r)
+        if not missing:
+            break
+        if time.monotonic() >= deadline:
+            raise RankLost(sorted(missing), tag)
+        time.sleep(poll_s)
+
+
+def run_partitioned(sim, n_steps: int, exchange_every: int, exchange, store=None,
+                    world: int = 1, rank: int = 0, timeout_s: float = 10.0,
+                    run_tag: str = "") -> Iterable[int]:
+    """Steps ``sim`` through ``n_steps`` in pieces of ``exchange_every`` steps; after each
+    piece the ranks check one another's presence (with a ``store``; ``run_tag`` keeps the
+    announcements of repeated runs apart) and run ``exchange``. Yields the step count
+    after each exchange."""
+    k = sim.k
+    while k < n_steps:
+        n = min(exchange_every - k % exchange_every, n_steps - k)
+        sim.step(n)
+        k += n
+        if store is not None and world > 1:
+            check_ranks(store, f"{run_tag}step{k}", world, rank, timeout_s)
+        exchange()
+        yield k

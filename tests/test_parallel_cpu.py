@@ -167,3 +167,53 @@ def test_gloo_non_finite_value_on_one_rank_raises_on_every_rank(tmp_path):
                        join=True, start_method="spawn")
     for r in range(world):
         assert (tmp_path / f"rank{r}.txt").read_text() == "raised"
+
+
+# ------------------------------------------------------------------------------------
+# A rank that leaves between steps
+# ------------------------------------------------------------------------------------
+def _leaving_worker(rank, world, store_port, out_dir, leaver):
+    import datetime
+
+    import torch.distributed as dist
+    from paper_0912_3223_gb300.parallel import RankLost, check_ranks
+    store = dist.TCPStore("127.0.0.1", store_port, world, rank == 0,
+                          timeout=datetime.timedelta(seconds=60))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=60))
+    cfg = li.make_cfg1(n_particles=300, n_steps=150, n_hours=4)
+    first, count = partition(cfg.n_particles, world, rank)
+    sel = np.arange(first, first + count)
+    log = []
+    try:
+        for k in (50, 100, 150):                 # three exchange steps
+            r = oracle.run(cfg, sel=sel, n_run=k)
+            check_ranks(store, f"step{k}", world, rank, timeout_s=5.0)
+            allreduce_fixed(r["conc_fixed"])
+            log.append(f"exchanged {k}")
+            if rank == leaver and k == 50:
+                log.append("left")               # leaves between steps, nothing in flight
+                break
+    except RankLost as e:
+        log.append(f"lost {e.missing} at {e.tag}")
+    with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+        f.write("\n".join(log))
+    if rank != 0:
+        return                                   # rank 0 keeps the store up for the others
+    import time
+    time.sleep(2.0)
+
+
+def test_gloo_rank_leaving_between_steps_is_reported_by_the_others(tmp_path):
+    """Three CPU ranks exchange after every 50 steps; rank 2 leaves after the first
+    exchange. The others detect it on the host before the next exchange (their store
+    announcements go unanswered within the time limit) and report the missing rank
+    instead of waiting in a collective it will never join."""
+    world, leaver = 3, 2
+    mp.start_processes(_leaving_worker, args=(world, _free_port(), str(tmp_path), leaver),
+                       nprocs=world, join=True, start_method="spawn")
+    logs = {r: (tmp_path / f"rank{r}.txt").read_text().splitlines() for r in range(world)}
+    assert logs[leaver] == ["exchanged 50", "left"]
+    for r in range(world):
+        if r != leaver:
+            assert logs[r] == ["exchanged 50", f"lost [{leaver}] at step100"], logs[r]
