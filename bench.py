@@ -293,11 +293,12 @@ def measure_batched(args, stream, cfg=None):
             "sort_every": args.batched_sort_every}
 
 
-def measure_adjoint(args, stream):
+def measure_adjoint(args, stream, storage="checkpoints"):
     """The adjoint form: 1e6 particles, 6 h at dt = 20 s on the realistic met, 64 receptors
     (Gaussian kernel, 200 m), sampled every 18 steps; forward (receptors, keeping the states
-    the backward needs: the cell-sorted trajectory by default) and backward (reverse sweep)
-    per run."""
+    the backward needs) and backward (reverse sweep) per run. ``storage``: "checkpoints"
+    keeps the state every 64 steps and recomputes each segment in the backward (the form
+    the workload names); "trajectory" keeps every particle-step (9.3 GB) instead."""
     import numpy as np
     import torch
 
@@ -309,6 +310,8 @@ def measure_adjoint(args, stream):
     with torch.cuda.stream(stream):
         sim = Sim(cfg, stream=stream)
     try:
+        if storage == "checkpoints":
+            lpm.lpm_set_adjoint_storage(sim.ctx, 0)
         sim.reset()
         sim.step(cfg.n_steps)
         active = int(sim.fixed_state()[2][4])         # same paths as the receptor run
@@ -621,8 +624,6 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         sim = Sim(cfg, stream=stream, launch=(args.block, args.ppt, args.occ),
                   sort_every=args.sort_every, part=part)
-    if args.regroup:
-        lpm.lpm_set_regroup(sim.ctx, args.regroup)
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
     exchange = parallel.SnapshotExchange(sim) if world > 1 else None
     ex_events = []
@@ -747,7 +748,6 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "particles": cfg.n_particles, "steps_per_run": cfg.n_steps,
                    "dt_s": cfg.dt, "met": [cfg.n_met_t, cfg.nz, cfg.ny, cfg.nx],
                    "launch": [args.block, args.ppt, args.occ], "sort_every": args.sort_every,
-                   "regroup_every": args.regroup,
                    "l2": "flushed (256 MB write) between timed steps",
                    "active_particle_steps_per_run": sum(active) // max(1, len(active)),
                    "slot_steps_per_run": cfg.n_particles * cfg.n_steps},
@@ -768,7 +768,8 @@ def run_gpu(args):
             "share_of_step": ex_ms / max(1e-9, sum(times))}
     if not args.no_forms:
         forms = {"batched": measure_batched(args, stream),
-                 "adjoint": measure_adjoint(args, stream),
+                 "adjoint": measure_adjoint(args, stream, "checkpoints"),
+                 "adjoint_trajectory": measure_adjoint(args, stream, "trajectory"),
                  "inversion": measure_inversion(args, stream),
                  "dosage": measure_dosage(args, stream),
                  "kz_eq3": measure_kz_eq3(args, stream),
@@ -814,9 +815,6 @@ def main():
     ap.add_argument("--occ", type=int, default=2)
     ap.add_argument("--sort-every", type=int, default=60,
                     help="re-order the particles by weather cell every N steps (0 = off)")
-    ap.add_argument("--regroup", type=int, default=0,
-                    help="re-order each block's particles by cell inside the step kernel every "
-                         "N steps (0 = off)")
     ap.add_argument("--ref-stride", type=int, default=100,
                     help="particle sample stride of each --impl reference step")
     ap.add_argument("--cpu-stride", type=int, default=30,
@@ -826,8 +824,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms")
     ap.add_argument("--no-stress", action="store_true", help="skip the 1e8-particle stress case")
-    ap.add_argument("--only", choices=["batched", "adjoint", "inversion", "stress", "dosage",
-                                       "kz_eq3", "decay_chain", "langevin"],
+    ap.add_argument("--only", choices=["batched", "adjoint", "adjoint_trajectory", "inversion",
+                                       "stress", "dosage", "kz_eq3", "decay_chain", "langevin"],
                     default=None,
                     help="run one form alone and print its measurement (profiling aid)")
     ap.add_argument("--batched-block", type=int, default=512)
@@ -852,6 +850,7 @@ def main():
         pkg_build.build()
         stream = torch.cuda.Stream()
         fn = {"batched": measure_batched, "adjoint": measure_adjoint,
+              "adjoint_trajectory": lambda a, st: measure_adjoint(a, st, "trajectory"),
               "inversion": measure_inversion, "stress": measure_stress,
               "dosage": measure_dosage, "kz_eq3": measure_kz_eq3,
               "decay_chain": measure_decay_chain, "langevin": measure_langevin}[args.only]

@@ -270,16 +270,6 @@ lpm_status lpm_device_state(lpm_ctx *ctx, int scenario, const uint64_t **conc,
  * occupancy calculator (Sec. 3.2); here the autotuner picks among these shapes. */
 lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int occupancy);
 
-/*
- * In-block regroup of the step kernel (a layout choice, no change to what is computed):
- * with one particle per thread, every every_steps steps each block re-orders its
- * particles by weather cell through shared memory, the ones that no longer move last, so
- * that a warp's lanes share weather records and finished warps idle together. Results
- * are bit-identical to every_steps = 0 (off). Errors: LPM_E_INVALID for every_steps < 0
- * or 2^22 scenarios or more.
- */
-lpm_status lpm_set_regroup(lpm_ctx *ctx, int every_steps);
-
 /* Every every_steps steps (at the multiples of every_steps), re-order the released
  * particles of all scenarios in device memory by the weather cell they occupy, so that
  * the threads of a warp gather from neighbouring cells (a layout change only: every

@@ -415,15 +415,19 @@ def adjoint(cfg, rec, sigma: float, every: int, w, sel=None, n_run: Optional[int
     return out
 
 
+SENS_FIELDS = 6
+
+
 def sensitivity(cfg, sel=None, n_run: Optional[int] = None, **kw) -> np.ndarray:
-    """Per particle [n][4]: the largest norms of d X_end / d (x_k, y_k) and of
-    d X_end / d z_k over its steps k (finite-time perturbation growth), then the sums over
-    k of their squares."""
+    """Per particle [n][6]: the largest norms of d X_end / d (x_k, y_k) and of
+    d X_end / d z_k over its steps k (finite-time perturbation growth), the sums over k of
+    their squares, and the sums over k of the squared growth from X_{k+1} times the square
+    of step k's horizontal and vertical displacement scale."""
     o = make_ocfg(cfg, **kw)
     n_run = cfg.n_steps if n_run is None else n_run
     sel_a = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     n = int(o.n_particles) if sel_a is None else sel_a.size
-    out = np.zeros((n, 4))
+    out = np.zeros((n, SENS_FIELDS))
     rc = lib().oracle_sensitivity(C.byref(o), _ptr(sel_a, C.c_int64), 0 if sel_a is None else n,
                                   int(n_run), _ptr(out, C.c_double))
     if rc:
@@ -431,15 +435,23 @@ def sensitivity(cfg, sel=None, n_run: Optional[int] = None, **kw) -> np.ndarray:
     return out
 
 
+# Relative error of a displacement computed in FP32 (the interpolated wind, the normals and
+# the diffusion scale each carry a few roundings of about 6e-8; twice their sum, about
+# 5e-7, rounded up to a power of two).
+DISP_REL_ERR = 2.0 ** -20
+
+
 def growth_bound(sens: np.ndarray, pos: np.ndarray) -> np.ndarray:
-    """The expected distance between a path run in FP32 and the same path in FP64: one
-    rounding of the state per step (2^-24 of its magnitude), each grown to the end of the
-    run by that step's growth factor, adding up as a random walk. Needs the summed squared
-    growths of ``sensitivity``."""
+    """The expected distance between a path run in FP32 and the same path in FP64: per
+    step, one rounding of the state (2^-24 of its magnitude) and the error of the computed
+    displacement (DISP_REL_ERR of its scale), each grown to the end of the run by that
+    step's growth factor, adding up as a random walk. Needs ``sensitivity``."""
     eps = 2.0 ** -24
     rh = np.maximum(np.abs(pos[:, 0]), np.abs(pos[:, 1]))
     rz = np.maximum(pos[:, 2], 1.0)
-    return eps * np.sqrt(sens[:, 2] * rh ** 2 + sens[:, 3] * rz ** 2)
+    state = eps ** 2 * (sens[:, 2] * rh ** 2 + sens[:, 3] * rz ** 2)
+    disp = DISP_REL_ERR ** 2 * (sens[:, 4] + sens[:, 5]) if sens.shape[1] > 4 else 0.0
+    return np.sqrt(state + disp)
 
 
 def chaotic(cfg, sens: np.ndarray, pos: np.ndarray, pos_tol: float) -> np.ndarray:

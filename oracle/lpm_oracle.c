@@ -1090,6 +1090,8 @@ typedef struct {
     double *X;                  /* [n_states][3] */
     double *nrm;                /* [n_steps][3] */
     double *fold;               /* [n_steps] */
+    double *err;                /* [n_steps][2] scale of the step's displacement, horizontal
+                                 * and vertical (see oracle_sensitivity) */
     double margin;
 } opath;
 
@@ -1104,7 +1106,8 @@ static int trace_particle(const ocfg *c, const ostep *K, int64_t p, int64_t n_ru
     o->X = (double *)malloc(sizeof(double) * 3 * (cap + 1));
     o->nrm = (double *)malloc(sizeof(double) * 3 * cap);
     o->fold = (double *)malloc(sizeof(double) * cap);
-    if (!o->X || !o->nrm || !o->fold) return 2;
+    o->err = (double *)malloc(sizeof(double) * 2 * cap);
+    if (!o->X || !o->nrm || !o->fold || !o->err) return 2;
     double X[3] = {c->src_x, c->src_y, c->src_z};
     const uint64_t gid = (uint64_t)(c->pid_offset + p);
     o->status = OR_ACTIVE;
@@ -1114,6 +1117,14 @@ static int trace_particle(const ocfg *c, const ostep *K, int64_t p, int64_t n_ru
         double met[6];
         int st = particle_step(c, K, gid, k, X, &o->margin, &o->fold[s], o->nrm + 3 * s, met,
                                NULL, 0);
+        /* the size of the step's displacement: the wind's part plus the random walk's scale
+         * times (|n| + 1) (a normal carries an absolute error of the size of its scale's) */
+        const double *n3 = o->nrm + 3 * s;
+        const double sh = sqrt(2.0 * c->k_scale * met[4] * c->dt);
+        const double sz = sqrt(2.0 * c->k_scale * met[3] * c->dt);
+        o->err[2 * s] = (fabs(met[0] + c->bias_u) + fabs(met[1] + c->bias_v)) * c->dt +
+                        sh * (fabs(n3[0]) + fabs(n3[1]) + 2.0);
+        o->err[2 * s + 1] = fabs(met[2]) * c->dt + sz * (fabs(n3[2]) + 1.0);
         o->kend = k;
         if (st != OR_ACTIVE) {
             o->status = st;
@@ -1130,6 +1141,7 @@ static void free_path(opath *o)
     free(o->X);
     free(o->nrm);
     free(o->fold);
+    free(o->err);
 }
 
 static int n_samples(int64_t n_run, int every)
@@ -1241,13 +1253,19 @@ int oracle_adjoint(const ocfg *c, const double *rec, int R, double sigma, int ev
     return 0;
 }
 
-/* Finite-time growth of perturbations along each particle's path up to step n_run:
- * out[4q] = max over steps k of the Frobenius norm of d X_end / d (x_k, y_k),
- * out[4q+1] = max over k of the norm of d X_end / d z_k (reverse products of the step
- * Jacobians), out[4q+2], out[4q+3] = the sums over k of their squares. A one-ulp
- * difference in the state at step k can reach these factors times the ulp at the end;
- * independent roundings at every step add up like a random walk, sqrt of the sums. The
- * parity tests use them to recognise chaotic paths. */
+/* Finite-time growth of perturbations along each particle's path up to step n_run
+ * (SENS_FIELDS values per particle):
+ * out[6q] = max over steps k of the Frobenius norm of d X_end / d (x_k, y_k),
+ * out[6q+1] = max over k of the norm of d X_end / d z_k (reverse products of the step
+ * Jacobians), out[6q+2], out[6q+3] = the sums over k of their squares;
+ * out[6q+4], out[6q+5] = the sums over k of the squared growth from X_{k+1} times the
+ * square of step k's displacement scale (horizontal: |u| dt + |v| dt + sigma_h (|n0| +
+ * |n1| + 2); vertical: |w| dt + sigma_z (|n2| + 1)).
+ * A one-ulp difference in the state at step k can reach these factors times the ulp at the
+ * end, and an error of the computed displacement, relative to its scale, likewise;
+ * independent errors at every step add up like a random walk, sqrt of the sums. The parity
+ * tests use them to recognise chaotic paths. */
+#define SENS_FIELDS 6
 int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t n_run, double *out)
 {
     if (c->langevin) return 1;      /* the traced paths follow Eq. 2 only */
@@ -1257,37 +1275,49 @@ int oracle_sensitivity(const ocfg *c, const int64_t *sel, int64_t n_sel, int64_t
         int64_t p = sel ? sel[q] : q;
         opath o;
         if (trace_particle(c, &K, p, n_run, &o)) return 2;
-        out[4 * q] = 1.0;
-        out[4 * q + 1] = 1.0;
-        out[4 * q + 2] = 0.0;
-        out[4 * q + 3] = 0.0;
+        double *r = out + SENS_FIELDS * q;
+        r[0] = 1.0;
+        r[1] = 1.0;
+        for (int f = 2; f < SENS_FIELDS; ++f) r[f] = 0.0;
         if (o.status == OR_UNRELEASED) continue;
         double M[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
         double best_h = 1.4142135623730951, best_z = 1.0, sum_h = 0.0, sum_z = 0.0;
+        double sum_eh = 0.0, sum_ez = 0.0;
         for (int64_t k = o.kend; k >= o.sp; --k) {
             const size_t s = (size_t)(k - o.sp);
+            /* a displacement error of step k enters X_{k+1}: it grows by d X_end / d X_{k+1},
+             * the product accumulated so far */
+            double gh = 0.0, gz = 0.0;
+            for (int rr = 0; rr < 3; ++rr) {
+                gh += M[rr][0] * M[rr][0] + M[rr][1] * M[rr][1];
+                gz += M[rr][2] * M[rr][2];
+            }
+            sum_eh += gh * o.err[2 * s] * o.err[2 * s];
+            sum_ez += gz * o.err[2 * s + 1] * o.err[2 * s + 1];
             double J[3][3], T[3][3], N[3][3];
             step_jacobian(c, o.X + 3 * s, k, o.nrm + 3 * s, o.fold[s], J, T);
-            for (int r = 0; r < 3; ++r)
+            for (int rr = 0; rr < 3; ++rr)
                 for (int d = 0; d < 3; ++d) {
-                    N[r][d] = 0.0;
-                    for (int e = 0; e < 3; ++e) N[r][d] += M[r][e] * J[e][d];
+                    N[rr][d] = 0.0;
+                    for (int e = 0; e < 3; ++e) N[rr][d] += M[rr][e] * J[e][d];
                 }
             memcpy(M, N, sizeof M);
             double fh = 0.0, fz = 0.0;
-            for (int r = 0; r < 3; ++r) {
-                fh += M[r][0] * M[r][0] + M[r][1] * M[r][1];
-                fz += M[r][2] * M[r][2];
+            for (int rr = 0; rr < 3; ++rr) {
+                fh += M[rr][0] * M[rr][0] + M[rr][1] * M[rr][1];
+                fz += M[rr][2] * M[rr][2];
             }
             if (sqrt(fh) > best_h) best_h = sqrt(fh);
             if (sqrt(fz) > best_z) best_z = sqrt(fz);
             sum_h += fh;
             sum_z += fz;
         }
-        out[4 * q] = best_h;
-        out[4 * q + 1] = best_z;
-        out[4 * q + 2] = sum_h;
-        out[4 * q + 3] = sum_z;
+        r[0] = best_h;
+        r[1] = best_z;
+        r[2] = sum_h;
+        r[3] = sum_z;
+        r[4] = sum_eh;
+        r[5] = sum_ez;
         free_path(&o);
     }
     return 0;

@@ -208,9 +208,9 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const LEV &L
 // Concentration-grid cell of a position, or KEY_OUT outside the grid.
 __device__ __forceinline__ int grid_cell(const StepParams &P, float x, float y, float z)
 {
-    const int ix = (int)floorf((x - P.cx0) * P.inv_cdx);
-    const int iy = (int)floorf((y - P.cy0) * P.inv_cdy);
-    const int iz = (int)floorf((z - P.cz0) * P.inv_cdz);
+    const int ix = grid_axis(x, P.gx0, P.ginv_dx);
+    const int iy = grid_axis(y, P.gy0, P.ginv_dy);
+    const int iz = grid_axis(z, P.gz0, P.ginv_dz);
     if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz)
         return (iz * P.cy + iy) * P.cx + ix;
     return KEY_OUT;
@@ -360,8 +360,8 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV
     if (kind < 0) return ST_ACTIVE;
     if (GRIDS) {
         const unsigned long long v = to_fixed(mass_at(P, sc, sp, k), sc.scale);
-        const int ix = (int)floorf((xn - P.cx0) * P.inv_cdx);
-        const int iy = (int)floorf((yn - P.cy0) * P.inv_cdy);
+        const int ix = grid_axis(xn, P.gx0, P.ginv_dx);
+        const int iy = grid_axis(yn, P.gy0, P.ginv_dy);
         if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy) {
             const long long cell = ((long long)kind * P.cy + iy) * P.cx + ix;
             atomicAdd(scg->dep + cell, v);
@@ -373,84 +373,6 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV
             deposit_species(P, sc, (int)(scg - P.scen), sp, k, kind, iy * P.cx + ix);
     }
     return kind == 0 ? ST_DEP_DRY : ST_DEP_WET;
-}
-
-// Buckets of the in-block regroup: the low 8 bits of the cell's sort key (its place in a
-// 4x4x4 tile of cells and the tile's x position modulo 4), then one for the particles that
-// no longer move.
-constexpr int RG_BUCKETS = 257;
-constexpr int RG_DEAD = 256;
-
-// Re-orders the block's particles (one per thread) through shared memory by the bucket of
-// their weather cell, the particles that no longer move last: the lanes of a warp then
-// share corner records of the weather (fewer L1 wavefronts per gather) and warps left
-// with finished particles only idle together. Every thread of the block must call it.
-// The order of particles within a bucket follows the shared-memory atomics; no result
-// depends on it (each particle keeps its id, hence its draws; every sum is an integer).
-template <int BLOCK, bool MIXED, class LEV>
-__device__ __forceinline__ void regroup_block(const StepParams &P, const LEV &LV, int k1,
-                                              int count, float &x, float &y, float &z,
-                                              uint32_t &tag, unsigned int &hm, int &loc, int &sj,
-                                              float &wv, bool lang, float4 *s_pay, uint2 *s_aux,
-                                              float *s_wv, unsigned int *s_hist)
-{
-    const int tid = threadIdx.x;
-    const uint32_t st = tag >> TAG_SHIFT;
-    const int sp = (int)(tag & TAG_STEP);
-    const bool alive = loc < count && (st == ST_ACTIVE || (st == ST_UNRELEASED && sp < k1));
-    unsigned int b = RG_DEAD;
-    if (alive) {
-        int ix, jy, kz;
-        float fa, fb, fc;
-        axis(x, P.x0, P.inv_dx, P.nx, ix, fa);
-        axis(y, P.y0, P.inv_dy, P.ny, jy, fb);
-        level(P, LV, z, kz, fc);
-        b = cell_key(P, ix, jy, kz) & 255u;
-    }
-    for (int i = tid; i < RG_BUCKETS; i += BLOCK) s_hist[i] = 0u;
-    __syncthreads();
-    const unsigned int r = atomicAdd(&s_hist[b], 1u);
-    __syncthreads();
-    if (tid < 32) {
-        // exclusive scan of the bucket counts by one warp: 9 buckets per lane, then a
-        // scan of the lanes' totals
-        constexpr int PER = (RG_BUCKETS + 31) / 32;
-        unsigned int v[PER], tot = 0u;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int idx = tid * PER + i;
-            v[i] = idx < RG_BUCKETS ? s_hist[idx] : 0u;
-            tot += v[i];
-        }
-        unsigned int incl = tot;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (tid >= o) incl += t;
-        }
-        unsigned int run = incl - tot;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int idx = tid * PER + i;
-            if (idx < RG_BUCKETS) s_hist[idx] = run;
-            run += v[i];
-        }
-    }
-    __syncthreads();
-    const unsigned int dest = s_hist[b] + r;
-    s_pay[dest] = make_float4(x, y, z, __uint_as_float(tag));
-    s_aux[dest] = make_uint2(hm, (unsigned int)loc | ((unsigned int)sj << 10));
-    if (lang) s_wv[dest] = wv;
-    __syncthreads();
-    const float4 p = s_pay[tid];
-    const uint2 a = s_aux[tid];
-    x = p.x; y = p.y; z = p.z;
-    tag = __float_as_uint(p.w);
-    hm = a.x;
-    loc = (int)(a.y & 1023u);
-    if (MIXED) sj = (int)(a.y >> 10);
-    if (lang) wv = s_wv[tid];
-    __syncthreads();                     // the buffers are free again (s_aux is s_acc)
 }
 
 // Occupancy variants: the register budget per thread is 128 (OCC 0), 80 (OCC 1) or 64
@@ -476,19 +398,11 @@ __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
                int k1, int do_bin)
 {
-    extern __shared__ float4 s_adv_dyn[];            // 16-byte aligned
-    unsigned char *s_dyn = reinterpret_cast<unsigned char *>(s_adv_dyn);
+    extern __shared__ float4 s_adv_dyn[];            // the level table, sized by the launch
     __shared__ unsigned long long s_acc[BLOCK];
     __shared__ int s_tile;
     __shared__ unsigned long long s_steps;
-    __shared__ unsigned int s_hist[PPT == 1 ? RG_BUCKETS : 1];
-    // in-block regroup every P.regroup steps (one particle per thread only)
-    const int RG = PPT == 1 ? P.regroup : 0;
-    const int RGd = RG > 0 ? RG : 1;                // (a divisor for the code under RG > 0)
-    const size_t rg_bytes = RG > 0 ? (size_t)BLOCK * (16 + (EXT ? 4 : 0)) : 0;
-    float4 *s_pay = reinterpret_cast<float4 *>(s_dyn);
-    float *s_wv = reinterpret_cast<float *>(s_dyn + (size_t)BLOCK * 16);
-    const Levels LV = load_levels(P, s_dyn + rg_bytes);
+    const Levels LV = load_levels(P, reinterpret_cast<unsigned char *>(s_adv_dyn));
     unsigned long long *s_warp = s_acc + (threadIdx.x & ~31);
     const long long n_cells = (long long)P.cx * P.cy * P.cz;
     constexpr int TILE = BLOCK * PPT;
@@ -533,8 +447,6 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         unsigned long long gid[PPT];
         int sj[PPT];                                    // scenario of each particle (MIXED)
         float wv[PPT];                                  // Langevin w' (EXT)
-        int loc[PPT];                                   // the particle's index in the tile
-        unsigned int hm[PPT];                           // and its home slot
         float *wsrc = in_a ? R.w_a : R.w_b;
         const bool lang = EXT && P.langevin && wsrc;
         const bool modes = EXT && P.n_modes > 0 && P.mode_sc;
@@ -545,11 +457,8 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
             const long long slot = first + local;
             sj[j] = tscen;
             gid[j] = 0ull;
-            loc[j] = local;
-            hm[j] = 0u;
             if (local < count) {
                 const long long home = in_a ? (long long)__ldg(R.pidx + slot) : slot;
-                hm[j] = (unsigned int)home;
                 if (MIXED) {
                     if (in_a) sj[j] = scen_of(P, home);
                     const ScenDev &q = P.scen[sj[j]];
@@ -583,33 +492,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         }
 #pragma unroll 1
         for (int k = k0; k < k1; ++k) {
-            if (RG > 0) {
-                // the block stays together: it regroups every RG steps and stops when none of
-                // its particles moves any more
-                if (k > k0 && (k - k0) % RGd == 0) {
-                    if (!__syncthreads_or(live > 0)) break;
-                    if (MIXED) {                        // active steps of the lane so far
-                        warp_count_scen(loc[0] < count ? sj[0] : -1, nst[0], C_ACTIVE_STEPS, P,
-                                        s_warp);
-                        nst[0] = 0u;
-                    }
-                    regroup_block<BLOCK, MIXED>(P, LV, k1, count, x[0], y[0], z[0], tag[0], hm[0],
-                                                loc[0], sj[0], wv[0], lang, s_pay,
-                                                reinterpret_cast<uint2 *>(s_acc), s_wv, s_hist);
-                    const ScenDev &q = MIXED ? P.scen[sj[0]] : scg;
-                    gid[0] = (unsigned long long)(__ldg(&q.id0) + ((long long)hm[0] -
-                                                                    __ldg(&q.first_slot)));
-                    const uint32_t st0 = tag[0] >> TAG_SHIFT;
-                    live = loc[0] < count && (st0 == ST_ACTIVE ||
-                                              (st0 == ST_UNRELEASED && (int)(tag[0] & TAG_STEP) < k1));
-                    cur_h = -1;                         // reload the lane's wind offsets
-                }
-                if (live <= 0 && !(EXT && P.dose_every)) {
-                    // nothing to move until the next regroup (or the segment's end)
-                    k = min(k0 + ((k - k0) / RGd + 1) * RGd, k1) - 1;
-                    continue;
-                }
-            } else if (EXT && P.dose_every) {
+            if (EXT && P.dose_every) {
                 // with dosage sampling the warp stays together (the samples are warp-collective)
                 if (!__any_sync(0xffffffffu, live > 0)) break;
             } else if (live <= 0) {
@@ -669,7 +552,8 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
             if (EXT && P.dose_every && (k + 1) % P.dose_every == 0) {
 #pragma unroll
                 for (int j = 0; j < PPT; ++j) {
-                    const bool on = loc[j] < count && (tag[j] >> TAG_SHIFT) == ST_ACTIVE;
+                    const int local = j * BLOCK + threadIdx.x;
+                    const bool on = local < count && (tag[j] >> TAG_SHIFT) == ST_ACTIVE;
                     const int sp = (int)(tag[j] & TAG_STEP);
                     const int cell = on ? grid_cell(P, x[j], y[j], z[j]) : KEY_NONE;
                     unsigned long long v = 0ull;
@@ -697,7 +581,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         // ---- store ------------------------------------------------------------------
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
-            const int local = loc[j];
+            const int local = j * BLOCK + threadIdx.x;
             if (local < count) {
                 state[first + local] = make_float4(x[j], y[j], z[j], __uint_as_float(tag[j]));
                 // only a moving particle has a turbulent velocity (0 once deposited or
@@ -712,7 +596,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
             const int lane = threadIdx.x & 31;
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
-                const int local = loc[j];
+                const int local = j * BLOCK + threadIdx.x;
                 long long idx = -1;
                 unsigned int key = KEY_NONE_U;
                 if (in_a) {
@@ -743,8 +627,9 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         if (do_bin) {
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
+                const int local = j * BLOCK + threadIdx.x;
                 const uint32_t st = tag[j] >> TAG_SHIFT;
-                const bool on = loc[j] < count && st == ST_ACTIVE;
+                const bool on = local < count && st == ST_ACTIVE;
                 int cell = KEY_NONE;
                 unsigned long long v = 0ull;
                 if (on) {
@@ -792,8 +677,10 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         // ---- active particle-steps of the tile -----------------------------------------
         if (MIXED) {
 #pragma unroll
-            for (int j = 0; j < PPT; ++j)
-                warp_count_scen(loc[j] < count ? sj[j] : -1, nst[j], C_ACTIVE_STEPS, P, s_warp);
+            for (int j = 0; j < PPT; ++j) {
+                const int local = j * BLOCK + threadIdx.x;
+                warp_count_scen(local < count ? sj[j] : -1, nst[j], C_ACTIVE_STEPS, P, s_warp);
+            }
         } else {
             for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
             if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&s_steps, steps);
@@ -819,7 +706,7 @@ cudaError_t launch_adv(const AdvanceLaunch &L)
 {
     static std::once_flag once;          // per instantiation; contexts may use several threads
     std::call_once(once, adv_prefer_l1<BLOCK, PPT, OCC, MIXED, EXT>);
-    const size_t smem = adv_dyn_smem(BLOCK, PPT, EXT, L.params->regroup, L.params->n_lut);
+    const size_t smem = adv_dyn_smem(L.params->n_lut);
     advance_kernel<BLOCK, PPT, OCC, MIXED, EXT><<<L.grid, BLOCK, smem, L.stream>>>(
         *L.params, L.ranges, L.n_tiles(), L.queue, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();

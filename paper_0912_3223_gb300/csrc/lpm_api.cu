@@ -103,7 +103,6 @@ struct lpm_ctx {
     long long k = 0;                        // steps taken
     long long n_bins = 0;                   // snapshots taken
     int block = 512, ppt = 1, occ = 2;
-    int regroup = 0;                        // in-block regroup interval (steps; 0: off)
 
     // sorting by weather cell (both forms) at the multiples of sort_every: d_state is the
     // home buffer (slot order of the API); the live particles released before sorted_upto
@@ -343,9 +342,8 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     P.lateral_exit = g.lateral_exit;
     P.drift = g.drift_correction;
     P.cx = g.cx; P.cy = g.cy; P.cz = g.cz;
-    P.cx0 = (float)g.cx0; P.cy0 = (float)g.cy0; P.cz0 = (float)g.cz0;
-    P.inv_cdx = (float)(1.0 / g.cdx); P.inv_cdy = (float)(1.0 / g.cdy);
-    P.inv_cdz = (float)(1.0 / g.cdz);
+    P.gx0 = g.cx0; P.gy0 = g.cy0; P.gz0 = g.cz0;
+    P.ginv_dx = 1.0 / g.cdx; P.ginv_dy = 1.0 / g.cdy; P.ginv_dz = 1.0 / g.cdz;
     P.zlut = c->n_lut > 0 ? c->d_zlut : nullptr;
     P.n_lut = c->n_lut;
     P.lut_z0 = c->lut_z0;
@@ -381,7 +379,6 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     }
     for (size_t k = 0; k < c->mode_profile.size(); ++k) P.mode_prof[k] = (float)c->mode_profile[k];
     P.mode_sc = P.n_modes ? c->d_mode_sc : nullptr;
-    P.regroup = c->ppt == 1 ? c->regroup : 0;
     P.err = c->d_err;
 }
 
@@ -1377,7 +1374,7 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
             const cudaStream_t cs = c->cap_stream;
             const int occ_blocks = std::max(1, advance_occupancy(
                 c->block, c->ppt, c->occ, true, ext,
-                adv_dyn_smem(c->block, c->ppt, ext, P.regroup, P.n_lut)));
+                adv_dyn_smem(P.n_lut)));
             lpm_ctx::Graph ng{};
             ng.k0 = c->k;
             ng.k1 = k_end;
@@ -1608,17 +1605,6 @@ lpm_status lpm_device_state(lpm_ctx *c, int scenario, const uint64_t **conc, con
     if (dep) *dep = reinterpret_cast<const uint64_t *>(c->d_dep + s * c->ndep());
     if (counters) *counters = reinterpret_cast<const uint64_t *>(c->d_ctr + s);
     if (counter_stride) *counter_stride = c->cfg.n_scenarios;
-    return LPM_OK;
-}
-
-lpm_status lpm_set_regroup(lpm_ctx *c, int every_steps)
-{
-    if (!c) return LPM_E_INVALID;
-    if (every_steps < 0) return fail(c, LPM_E_INVALID, "every_steps must be >= 0");
-    if (every_steps > 0 && c->cfg.n_scenarios >= (1 << 22))
-        return fail(c, LPM_E_INVALID, "the regroup carries scenario indices below 2^22");
-    c->regroup = every_steps;
-    drop_graphs(c);                          // the graphs hold the step parameters
     return LPM_OK;
 }
 

@@ -89,9 +89,10 @@ struct StepParams {
     float2 zi[MAX_LEVELS];
     unsigned int t_dry, t_wet;       // event iff word < threshold
     int reflect_ground, reflect_top, lateral_exit, drift;
-    // concentration grid
+    // concentration grid; the cell of a position is taken in FP64 (origin and reciprocal
+    // spacing in FP64: a cell face is resolved far below the FP32 position's own ulp)
     int cx, cy, cz;
-    float cx0, cy0, cz0, inv_cdx, inv_cdy, inv_cdz;
+    double gx0, gy0, gz0, ginv_dx, ginv_dy, ginv_dz;
     // tables
     const float *m0;                 // initial mass per release step (all scenarios)
     const ScenDev *scen;
@@ -122,9 +123,6 @@ struct StepParams {
     float mode_eu[MAX_MODES], mode_ev[MAX_MODES];
     float mode_prof[MAX_LEVELS];
     const float *mode_sc;            // [n_scen][8]: phases (cycles), amplitudes (m/s); 32-B rows
-    // the advance launch re-orders each block's particles by weather cell every `regroup`
-    // steps (one particle per thread; 0: never)
-    int regroup;
     unsigned int *err;
 };
 
@@ -427,6 +425,14 @@ __device__ __forceinline__ float4 lerp4(const float4 a, const float4 b, float t)
 {
     return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y),
                        fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
+}
+
+// Cell index of an FP32 coordinate along one axis of the concentration grid, in FP64: the
+// FP32 product with a rounded reciprocal would misplace positions within about 1e-3 m of a
+// face at 25 km from the origin; in FP64 only positions within 1e-8 m can be.
+__device__ __forceinline__ int grid_axis(float v, double o, double inv_d)
+{
+    return (int)floor(((double)v - o) * inv_d);
 }
 
 // Fixed-point mass: round-to-nearest-even of m * 2^shift (scale is an exact power of 2).

@@ -105,9 +105,9 @@ budget_kernel(const StepParams P, const float4 *__restrict__ home, long long n_h
                 const ScenDev &q = P.scen[scen];
                 const unsigned long long v =
                     to_fixed(mass_at(P, q, (int)(tag & TAG_STEP), k_now - 1), __ldg(&q.scale));
-                const int ix = (int)floorf((st.x - P.cx0) * P.inv_cdx);
-                const int iy = (int)floorf((st.y - P.cy0) * P.inv_cdy);
-                const int iz = (int)floorf((st.z - P.cz0) * P.inv_cdz);
+                const int ix = grid_axis(st.x, P.gx0, P.ginv_dx);
+                const int iy = grid_axis(st.y, P.gy0, P.ginv_dy);
+                const int iz = grid_axis(st.z, P.gz0, P.ginv_dz);
                 if (ix >= 0 && ix < P.cx && iy >= 0 && iy < P.cy && iz >= 0 && iz < P.cz) in = v;
                 else out = v;
                 cnt = 1;

@@ -110,14 +110,10 @@ cudaError_t launch_release(cudaStream_t s, float4 *state, long long first_slot, 
                            long long part_first, long long n_total, int rel_first, int rel_len,
                            float sx, float sy, float sz);
 cudaError_t launch_release_all(cudaStream_t s, const StepParams &P, float4 *state, long long n_slots);
-// Bytes of dynamic shared memory of an advance launch: the in-block regroup's particle
-// exchange (one particle per thread, every `regroup` steps; with the extended options also
-// the Langevin w'), then the vertical level table.
-inline size_t adv_dyn_smem(int block, int ppt, bool ext, int regroup, int n_lut)
+// Bytes of dynamic shared memory of an advance launch: its copy of the vertical level table.
+inline size_t adv_dyn_smem(int n_lut)
 {
-    size_t b = 0;
-    if (ppt == 1 && regroup > 0) b += (size_t)block * (16 + (ext ? 4 : 0));
-    return b + (((size_t)(n_lut > 0 ? n_lut : 0) + 15) & ~(size_t)15);
+    return ((size_t)(n_lut > 0 ? n_lut : 0) + 15) & ~(size_t)15;
 }
 
 cudaError_t launch_advance(const AdvanceLaunch &L);

@@ -32,7 +32,7 @@ SYMBOLS = ["lpm_create", "lpm_destroy", "lpm_last_error", "lpm_set_met", "lpm_se
            "lpm_load", "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model",
            "lpm_set_boundary_layer", "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
            "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage",
-           "lpm_set_modes", "lpm_set_mode_phases", "lpm_device_state", "lpm_set_regroup"]
+           "lpm_set_modes", "lpm_set_mode_phases", "lpm_device_state"]
 
 
 class LpmError(RuntimeError):
@@ -119,7 +119,6 @@ def load() -> C.CDLL:
     L.lpm_device_state.argtypes = [vp, C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(i64)]
     L.lpm_set_modes.argtypes = [vp, C.c_int, dp, dp]
-    L.lpm_set_regroup.argtypes = [vp, C.c_int]
     L.lpm_set_mode_phases.argtypes = [vp, C.c_int, dp, dp]
     L.lpm_draws_static.argtypes = [C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32),
                                    C.c_uint32, i64, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]
@@ -134,8 +133,7 @@ def load() -> C.CDLL:
                  "lpm_set_dosage", "lpm_dosage", "lpm_set_kz_model", "lpm_set_boundary_layer",
                  "lpm_set_decay_chain", "lpm_species", "lpm_set_langevin",
                  "lpm_particle_velocity", "lpm_set_adjoint_storage", "lpm_adjoint_storage",
-                 "lpm_set_modes", "lpm_set_mode_phases", "lpm_device_state",
-                 "lpm_set_regroup"):
+                 "lpm_set_modes", "lpm_set_mode_phases", "lpm_device_state"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -290,12 +288,6 @@ def lpm_save(ctx) -> bytes:
 def lpm_load(ctx, state: bytes) -> None:
     buf = C.create_string_buffer(state, len(state))
     _check(ctx, load().lpm_load(C.c_void_p(ctx), C.cast(buf, C.c_void_p), len(state)))
-
-
-def lpm_set_regroup(ctx, every_steps: int) -> None:
-    """Re-order each block's particles by weather cell every ``every_steps`` steps inside
-    the step kernel (0: off); results do not change."""
-    _check(ctx, load().lpm_set_regroup(C.c_void_p(ctx), int(every_steps)))
 
 
 def lpm_set_sort(ctx, every_steps: int) -> None:

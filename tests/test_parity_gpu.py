@@ -489,40 +489,3 @@ def test_level_bisection_path_matches_oracle():
     rep = compare(cfg, g, o, check_grid=False, sens=sens)
     print("bisection levels, 360 steps:", rep)
     np.testing.assert_allclose(g["budget"][0], o["budget"][0], rtol=1e-6)
-
-
-def _options_cfgs():
-    plain = li.make_cfg1(n_particles=3001, n_steps=240, n_hours=5)
-    ens = li.make_cfg2(n_scenarios=5, n_steps=240, n_min=300, n_max=1500)
-    return {"plain": plain, "ensemble_with_modes": ens,
-            "langevin": dataclasses.replace(plain, langevin=1, t_lagr=100.0),
-            "decay_chain": dataclasses.replace(
-                plain, chain_half_lives=np.array([plain.half_life_s, 3600.0, 0.0]))}
-
-
-@pytest.mark.parametrize("name", ["plain", "ensemble_with_modes", "langevin", "decay_chain"])
-@pytest.mark.parametrize("every", [1, 7, 20])
-def test_regroup_changes_nothing(name, every):
-    """Re-ordering each block's particles by cell inside the step kernel (every 1, 7 or 20
-    steps; sorted and release-ordered tiles, mixed scenarios, the Langevin velocity and
-    decay-chain daughters travelling with their particle) leaves every bit of the run as
-    it is."""
-    from paper_0912_3223_gb300 import Sim, lpm
-    cfg = _options_cfgs()[name]
-
-    def run(rg):
-        with Sim(cfg) as sim:
-            lpm.lpm_set_regroup(sim.ctx, rg)
-            sim.step(cfg.n_steps)
-            xyz, tag = sim.particles()
-            state = [sim.fixed_state(s) for s in range(cfg.n_scenarios)]
-            w = sim.velocity() if getattr(cfg, "langevin", 0) else None
-        return xyz, tag, state, w
-
-    ref, got = run(0), run(every)
-    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1])
-    for a, b in zip(ref[2], got[2]):
-        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
-        assert np.array_equal(a[2], b[2])
-    if ref[3] is not None:
-        assert np.array_equal(ref[3], got[3])
