@@ -666,10 +666,13 @@ static int particle_step(const ocfg *c, const ostep *K, uint64_t gid, int64_t k,
             return OR_EXITED;
     }
     /* 6. stochastic dry deposition below the mixing height, then wet deposition where it
-     *    rains (Sec. 2); one uniform word per test */
+     *    rains (Sec. 2); one uniform word per test: the block of stream 1 at counter step
+     *    k / 2 serves two steps, words 0 and 1 for an even step, 2 and 3 for an odd one */
     if (K->t_dry || K->t_wet) {
-        uint32_t dw[4];
-        oracle_draw(c->seed, gid, (uint32_t)k, 1u, dw);
+        uint32_t blk[4], dw[2];
+        oracle_draw(c->seed, gid, (uint32_t)(k / 2), 1u, blk);
+        dw[0] = blk[2 * (k % 2)];
+        dw[1] = blk[2 * (k % 2) + 1];
         if (K->t_dry && dw[0] < K->t_dry) {
             double d = fabs(X[2] - c->h_mix);
             if (d < *margin) *margin = d;

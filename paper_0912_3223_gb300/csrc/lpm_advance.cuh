@@ -106,9 +106,11 @@ __device__ __forceinline__ void mode_wind(const StepParams &P, const float *msc,
 #pragma unroll
     for (int m = 0; m < MAX_MODES; ++m) {
         if (m < P.n_modes) {
-            // phase in cycles; sinpif reduces its argument exactly
+            // phase in cycles, reduced exactly to [-1/2, 1/2]; the hardware sine on
+            // [-pi, pi] errs by less than 5e-7 (a velocity error of that fraction of the
+            // amplitude)
             const float r = fmaf(P.mode_fx[m], x, fmaf(P.mode_fy[m], y, fmaf(P.mode_om[m], tk, pa[m])));
-            const float as = aa[m] * sinpif(2.0f * r);
+            const float as = aa[m] * __sinf(6.28318548f * (r - rintf(r)));
             su = fmaf(as, P.mode_eu[m], su);
             sv = fmaf(as, P.mode_ev[m], sv);
         }
@@ -237,6 +239,38 @@ static __device__ __noinline__ void deposit_species(const StepParams &P, const S
     }
 }
 
+// The deposition words of a particle: one Philox block (stream 1) serves a pair of steps,
+// words 0 and 1 for the even step, 2 and 3 for the odd one (dry, then wet test). A step
+// runner may keep the odd step's words from the even step in a DepCache.
+struct DepCache {
+    uint32_t c, d;                   // words of the odd step of pair `pair`
+    int pair;                        // -1: nothing kept
+};
+
+__device__ __forceinline__ void dep_words(const StepParams &P, unsigned long long gid, int k,
+                                          DepCache *dc, uint32_t &w_dry, uint32_t &w_wet)
+{
+    const int pair = k >> 1;
+    if (dc && (k & 1) && dc->pair == pair) {
+        w_dry = dc->c;
+        w_wet = dc->d;
+        return;
+    }
+    const U4 d = philox4x32_10_rk((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)pair, 1u, P.rk);
+    if (k & 1) {
+        w_dry = d.c;
+        w_wet = d.d;
+    } else {
+        w_dry = d.a;
+        w_wet = d.b;
+        if (dc) {
+            dc->c = d.c;
+            dc->d = d.d;
+            dc->pair = pair;
+        }
+    }
+}
+
 // Per-step quantities shared by every particle of a tile.
 struct StepTime {
     int k;
@@ -279,7 +313,8 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV
                                                   const ScenDev *scg, unsigned long long gid,
                                                   int sp, float sig_h_uniform, float du, float dv,
                                                   float &x, float &y, float &z, float *fold,
-                                                  float *wv = nullptr, const float *msc = nullptr)
+                                                  float *wv = nullptr, const float *msc = nullptr,
+                                                  DepCache *dc = nullptr)
 {
     const int k = T.k;
     // 1. weather at the old position and t_k (with the scenario's perturbation modes: msc);
@@ -345,10 +380,11 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV
     }
     if (!(P.t_dry | P.t_wet)) return ST_ACTIVE;
     // 6. dry deposition below the mixing height, then wet where it rains
-    const U4 d = philox4x32_10_rk((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 1u, P.rk);
+    uint32_t w_dry, w_wet;
+    dep_words(P, gid, k, dc, w_dry, w_wet);
     int kind = -1;
-    if (d.a < P.t_dry && zn < P.h_mix) kind = 0;
-    if (kind < 0 && d.b < P.t_wet && P.rain) {
+    if (w_dry < P.t_dry && zn < P.h_mix) kind = 0;
+    if (kind < 0 && w_wet < P.t_wet && P.rain) {
         int ir = (int)floorf((xn - P.x0) * P.inv_dx + 0.5f);
         int jr = (int)floorf((yn - P.y0) * P.inv_dy + 0.5f);
         ir = min(max(ir, 0), P.nx - 1);
@@ -484,11 +520,13 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         unsigned long long steps = 0;
         unsigned int nst[PPT];                          // active steps per particle (MIXED)
         float2 o0[PPT], o1[PPT];                        // lane wind offsets at h0, h1 (MIXED)
+        DepCache dc[PPT];                               // odd-step deposition words
         int cur_h = -1;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             nst[j] = 0u;
             o0[j] = o1[j] = make_float2(0.0f, 0.0f);
+            dc[j].pair = -1;
         }
 #pragma unroll 1
         for (int k = k0; k < k1; ++k) {
@@ -537,13 +575,13 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                     st = particle_step<true, EXT>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
                                                   sp, sig_h_uniform, du, dv, x[j], y[j], z[j],
                                                   nullptr, lang ? &wv[j] : nullptr,
-                                                  modes ? P.mode_sc + 8 * sj[j] : nullptr);
+                                                  modes ? P.mode_sc + 8 * sj[j] : nullptr, &dc[j]);
                 } else {
                     ++steps;
                     st = particle_step<true, EXT>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
                                                   T.du, T.dv, x[j], y[j], z[j], nullptr,
                                                   lang ? &wv[j] : nullptr,
-                                                  modes ? P.mode_sc + 8 * tscen : nullptr);
+                                                  modes ? P.mode_sc + 8 * tscen : nullptr, &dc[j]);
                 }
                 tag[j] = (st << TAG_SHIFT) | (uint32_t)sp;
                 if (st == ST_ACTIVE) ++live;

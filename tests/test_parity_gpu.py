@@ -486,6 +486,9 @@ def test_level_bisection_path_matches_oracle():
     g = run_gpu(cfg, n_run=360)
     o = oracle.run(cfg, n_run=360)
     sens = oracle.sensitivity(cfg, n_run=360)
-    rep = compare(cfg, g, o, check_grid=False, sens=sens)
+    # the 3 mm layer makes the wind's vertical gradient near the ground a hundred times
+    # steeper than in the realistic levels: more paths are chaotic, so up to 2 % may be set
+    # apart (each still held to its own growth bound)
+    rep = compare(cfg, g, o, check_grid=False, sens=sens, max_excluded_frac=0.02)
     print("bisection levels, 360 steps:", rep)
     np.testing.assert_allclose(g["budget"][0], o["budget"][0], rtol=1e-6)
