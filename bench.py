@@ -263,7 +263,16 @@ def measure_batched(args, stream, cfg=None):
         sim = Sim(cfg, stream=stream, launch=(args.batched_block, args.batched_ppt,
                                               args.batched_occ),
                   sort_every=args.batched_sort_every)
+    tuned = None
     try:
+        if args.autotune:
+            # the autotuner's choice of launch shape and sort interval, timed fresh here
+            from paper_0912_3223_gb300.autotune import autotune_with_sort
+            shape, every, tried = autotune_with_sort(
+                sim, shapes=[(512, 1, 2), (256, 1, 2), (128, 1, 2), (256, 2, 1)],
+                sort_intervals=(30, 60, 90), use_cache=False, reps=1)
+            tuned = {"launch": list(shape), "sort_every": every,
+                     "ms_per_run_tried": {k: round(v, 2) for k, v in tried.items()}}
         for _ in range(max(1, args.warmup)):
             sim.reset()
             sim.step(cfg.n_steps)
@@ -285,12 +294,18 @@ def measure_batched(args, stream, cfg=None):
     finally:
         sim.close()
     t = sum(times) / 1e3
-    return {"value": active / t, "unit": UNIT, "ms_per_run": statistics.mean(times),
-            "scenarios": cfg.n_scenarios, "particles": cfg.n_particles,
-            "steps_per_run": cfg.n_steps, "graph_launches_per_run": adv // max(1, args.steps),
-            "kernel_launches_per_run": launches / max(1, args.steps),
-            "launch": [args.batched_block, args.batched_ppt, args.batched_occ],
-            "sort_every": args.batched_sort_every}
+    out = {"value": active / t, "unit": UNIT, "ms_per_run": statistics.mean(times),
+           "scenarios": cfg.n_scenarios, "particles": cfg.n_particles,
+           "steps_per_run": cfg.n_steps, "graph_launches_per_run": adv // max(1, args.steps),
+           "kernel_launches_per_run": launches / max(1, args.steps),
+           "launch": tuned["launch"] if tuned else [args.batched_block, args.batched_ppt,
+                                                    args.batched_occ],
+           "sort_every": tuned["sort_every"] if tuned else args.batched_sort_every,
+           "weather": "shared hourly fields + per-scenario hourly wind offset + 4 "
+                      "perturbation modes (own phases and amplitudes)"}
+    if tuned:
+        out["autotuned"] = tuned
+    return out
 
 
 def measure_adjoint(args, stream, storage="checkpoints"):
@@ -835,6 +850,9 @@ def main():
                     help="particles of the adjoint form (smaller for profiler captures)")
     ap.add_argument("--batched-sort-every", type=int, default=60,
                     help="steps between sorts by cell in the batched form (0: off)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="time the batched form with the given launch shape and sort interval "
+                         "instead of the autotuner's choice")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 0)
     if args.gpus > 1 and world == 0:

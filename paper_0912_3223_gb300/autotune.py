@@ -1,11 +1,13 @@
-"""Launch-shape autotuner for the particle kernels.
+"""Launch-shape and sort-interval autotuner for the particle kernels.
 
 Times complete runs (lpm_reset + lpm_step over the whole horizon, so the release ramp,
 the exits and the end-of-run binning are all represented) for every supported
-(threads per block, particles per thread, occupancy variant) with CUDA events on the
-context stream, and keeps the fastest. Results are cached per (GPU name, workload signature) in a JSON
-file (``$LPM_AUTOTUNE_CACHE`` or ``~/.cache/lpm_gb300/autotune.json``). Every shape gives
-bit-identical results, so tuning never changes what is computed.
+(threads per block, particles per thread, occupancy variant), and with
+``autotune_with_sort`` also for several intervals of the re-ordering of the particles by
+weather cell (the steps fused between two sorts), with CUDA events on the context stream,
+and keeps the fastest. Results are cached per (GPU name, workload signature) in a JSON file
+(``$LPM_AUTOTUNE_CACHE`` or ``~/.cache/lpm_gb300/autotune.json``). Every shape and sort
+interval gives bit-identical results, so tuning never changes what is computed.
 """
 from __future__ import annotations
 
@@ -109,3 +111,47 @@ def autotune(sim, shapes: Optional[Iterable[Tuple[int, int, int]]] = None, use_c
         cache[key] = {"shape": list(shape), "ms": results}
         _store(cache)
     return shape
+
+
+SORT_INTERVALS = (30, 60, 90)
+
+
+def autotune_with_sort(sim, shapes: Optional[Iterable[Tuple[int, int, int]]] = None,
+                       sort_intervals: Iterable[int] = SORT_INTERVALS, use_cache: bool = True,
+                       reps: int = 2) -> Tuple[Tuple[int, int, int], int, Dict[str, float]]:
+    """Picks and applies the fastest (launch shape, sort interval) for ``sim``; returns the
+    shape, the interval and the measured milliseconds of every combination tried."""
+    import torch
+    intervals = [int(e) for e in sort_intervals]
+    key = f"{torch.cuda.get_device_name()}|{signature(sim.cfg)}|sort{intervals}"
+    cache = _load() if use_cache else {}
+    if key in cache:
+        shape = tuple(cache[key]["shape"])
+        every = int(cache[key]["sort_every"])
+        lpm.lpm_set_launch(sim.ctx, *shape)
+        lpm.lpm_set_sort(sim.ctx, every)
+        return shape, every, cache[key]["ms"]
+    shapes = [tuple(v) for v in shapes] if shapes is not None else DEFAULT_SHAPES
+    results = {}
+    for every in intervals:
+        lpm.lpm_set_sort(sim.ctx, every)
+        for shape in shapes:
+            try:
+                results["x".join(map(str, shape)) + f"/sort{every}"] = time_shape(sim, shape, reps)
+            except lpm.LpmError as e:
+                if e.status != lpm.LPM_E_INVALID:
+                    raise
+    if not results:
+        raise RuntimeError("no launch shape runs with this context's options")
+    best = min(results, key=results.get)
+    shape_s, every_s = best.split("/sort")
+    shape = tuple(int(v) for v in shape_s.split("x"))
+    every = int(every_s)
+    lpm.lpm_set_launch(sim.ctx, *shape)
+    lpm.lpm_set_sort(sim.ctx, every)
+    sim.reset()
+    if use_cache:
+        cache = _load()
+        cache[key] = {"shape": list(shape), "sort_every": every, "ms": results}
+        _store(cache)
+    return shape, every, results

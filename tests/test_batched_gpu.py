@@ -158,6 +158,25 @@ def test_autotuner_keeps_results(small_ensemble, tmp_path, monkeypatch):
     assert np.array_equal(xyz, ref[0]) and np.array_equal(tag, ref[1])
 
 
+def test_autotuner_with_sort_interval_keeps_results(small_ensemble, tmp_path, monkeypatch):
+    """Tuning the launch shape together with the sort interval picks one of the tried
+    combinations, applies it, and the run it leaves is bit-identical to the default one."""
+    from paper_0912_3223_gb300 import Sim
+    from paper_0912_3223_gb300.autotune import autotune_with_sort
+    monkeypatch.setenv("LPM_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    ref = _run(small_ensemble)[0]
+    with Sim(small_ensemble) as sim:
+        shape, every, tried = autotune_with_sort(sim, shapes=[(128, 1, 2), (512, 1, 2)],
+                                                 sort_intervals=(20, 60), reps=1)
+        assert shape in [(128, 1, 2), (512, 1, 2)] and every in (20, 60)
+        assert len(tried) == 4
+        sim.step(small_ensemble.n_steps)
+        xyz, tag = sim.particles()
+        assert autotune_with_sort(sim, shapes=[(128, 1, 2), (512, 1, 2)],
+                                  sort_intervals=(20, 60))[:2] == (shape, every)   # cached
+    assert np.array_equal(xyz, ref[0]) and np.array_equal(tag, ref[1])
+
+
 def _same(a, b):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     for sa, sb in zip(a[2], b[2]):
