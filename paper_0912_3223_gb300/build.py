@@ -17,6 +17,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblpm.so")
 BUILD = os.path.join(HERE, "_build")
+# The checked build: the same sources with every indexed access of the kernels tested
+# against its array (a failed test sets the device error word; nothing traps), for
+# verification runs in place of a memory checker.
+OUT_CHECKED = os.path.join(HERE, "liblpm_checked.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 SOURCES = ["lpm_api.cu", "lpm_kernels.cu", "lpm_advance_b128.cu", "lpm_advance_b256.cu",
            "lpm_advance_b512.cu", "lpm_adjoint.cu", "lpm_noalloc.cu", "lpm_sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -43,15 +48,19 @@ def _headers():
     return hs + [os.path.join(ROOT, "include", "lpm.h")]
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Builds liblpm.so (or, with ``checked``, liblpm_checked.so) and returns its path."""
+    out_lib, build_dir = (OUT_CHECKED, BUILD_CHECKED) if checked else (OUT, BUILD)
+    if checked:
+        extra = tuple(extra) + ("-DLPM_CHECKED=1",)
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     hdrs = _headers()
     jobs = []
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             cmd = [cc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
@@ -69,13 +78,13 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    if force or jobs or _stale(OUT, objs):
-        tmp = OUT + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(out_lib, objs):
+        tmp = out_lib + f".{os.getpid()}.tmp"
         subprocess.check_call([cc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, OUT)
-    return OUT
+        os.replace(tmp, out_lib)
+    return out_lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(OUT)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -166,7 +166,8 @@ adj_forward_kernel(const StepParams P, const AdjParams A)
             float fs = 1.0f;
             st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp, sig_h_uniform, T.du, T.dv,
                                       x, y, z, TRAJ ? &fs : nullptr);
-            if (TRAJ && k >= k0)                  // rows start at the tile's first release
+            if (TRAJ && k >= k0 &&                // rows start at the tile's first release
+                LPM_IN_BOUNDS(P.err, (row - A.traj) + (long long)(k - k0) * ADJ_BLOCK < A.traj_cap))
                 __stcs(row + (long long)(k - k0) * ADJ_BLOCK, make_float4(xb, yb, zb, fs));
             kn = k + 1;
             if (st != ST_ACTIVE) {
@@ -428,11 +429,16 @@ adj_backward_traj_kernel(const StepParams P, const AdjParams A)
     const int k_top = __reduce_max_sync(0xffffffffu, kn) - 1;
     const int k_bot = __reduce_min_sync(0xffffffffu, kb < kn ? kb : 0x7fffffff);
     float4 Xn = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k_top >= kb && k_top < kn) Xn = __ldcs(row + (long long)(k_top - k0) * ADJ_BLOCK);
+    const long long row0 = row - A.traj;
+    if (k_top >= kb && k_top < kn &&
+        LPM_IN_BOUNDS(P.err, row0 + (long long)(k_top - k0) * ADJ_BLOCK < A.traj_cap))
+        Xn = __ldcs(row + (long long)(k_top - k0) * ADJ_BLOCK);
     for (int k = k_top; k >= k_bot; --k) {
         const bool act = k >= kb && k < kn;
         const float4 X = Xn;
-        if (k - 1 >= kb && k - 1 < kn) Xn = __ldcs(row + (long long)(k - 1 - k0) * ADJ_BLOCK);
+        if (k - 1 >= kb && k - 1 < kn &&
+            LPM_IN_BOUNDS(P.err, row0 + (long long)(k - 1 - k0) * ADJ_BLOCK < A.traj_cap))
+            Xn = __ldcs(row + (long long)(k - 1 - k0) * ADJ_BLOCK);
         if (!act) continue;
         const bool sample = (k + 1) % A.every == 0 && !(ev && k == kn - 1);
         reverse_step<KHG>(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,

@@ -36,6 +36,7 @@ struct AdjParams {
     // after the last step taken, w = that step + 1 (release step if none), bit 31 set when
     // the run ended by an event.
     float4 *traj;
+    long long traj_cap;               // float4 entries of traj (bounds of the checked build)
     float4 *fin;
     const longlong2 *traj_tile;
     const Tile *tiles;

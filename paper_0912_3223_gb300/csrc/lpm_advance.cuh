@@ -139,6 +139,9 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const LEV &L
     axis(x, P.x0, P.inv_dx, P.nx, i, a);
     axis(y, P.y0, P.inv_dy, P.ny, j, b);
     level(P, L, z, k, c);
+    if (!LPM_IN_BOUNDS(P.err, i >= 0 && i <= P.nx - 2 && j >= 0 && j <= P.ny - 2 && k >= 0 &&
+                                  k <= P.nz - 2))
+        i = j = k = 0;
     // the corners as two x-adjacent records at four bases: (y, z), (y+1, z), (y, z+1),
     // (y+1, z+1); the x + 1 record is the next 32 bytes
     const float4 *b00 = pair + 2 * (long long)col_node(P, i, j, k);
@@ -218,10 +221,18 @@ __device__ __forceinline__ int grid_cell(const StepParams &P, float x, float y, 
     return KEY_OUT;
 }
 
+// Initial mass of a particle released at step sp (the scenario's table, Sec. 3.2).
+__device__ __forceinline__ float m0_of(const StepParams &P, const ScenDev &sc, int sp)
+{
+    int ix = sc.m0_off + (sp - sc.rel_first);
+    if (!LPM_IN_BOUNDS(P.err, ix >= 0 && ix < P.n_m0)) ix = 0;
+    return __ldg(P.m0 + ix);
+}
+
 __device__ __forceinline__ float mass_at(const StepParams &P, const ScenDev &sc, int sp, int k_end)
 {
     // decayed mass at the end of step k_end (age (k_end + 1 - s_p) dt), Sec. 2 / Sec. 3.2
-    const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
+    const float m0 = m0_of(P, sc, sp);
     const float age = (float)(k_end + 1 - sp) * P.dt;
     return m0 * expf(-P.lambda * age);
 }
@@ -230,7 +241,7 @@ __device__ __forceinline__ float mass_at(const StepParams &P, const ScenDev &sc,
 static __device__ __noinline__ void deposit_species(const StepParams &P, const ScenDev &sc, int scen,
                                              int sp, int k, int kind, int cell2)
 {
-    const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
+    const float m0 = m0_of(P, sc, sp);
     const float age = (float)(k + 1 - sp) * P.dt;
     const long long plane = (long long)P.cx * P.cy;
     for (int j = 1; j < P.n_species; ++j) {
@@ -288,6 +299,7 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const float2 
     T.k = k;
     T.tk = (float)k * P.dt;
     T.ts = time_slab(P, T.tk);
+    if (!LPM_IN_BOUNDS(P.err, T.ts.h0 >= 0 && T.ts.h0 < P.n_pair)) T.ts.h0 = 0;
     T.pair = P.pair + (long long)T.ts.h0 * P.slab * 2;
     T.khp = P.khpair ? P.khpair + (long long)T.ts.h0 * P.slab : nullptr;
     T.blp = P.blpair ? P.blpair + (long long)T.ts.h0 * P.nx * P.ny * 2 : nullptr;
@@ -472,6 +484,9 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
             first = tl.first;
             count = tl.count;
             tscen = tl.scen;
+            if (!LPM_IN_BOUNDS(P.err, first >= 0 && first + count <= P.slot_cap && tscen >= 0 &&
+                                          tscen < P.n_scen))
+                count = 0;
         }
         if (count <= 0) continue;                       // the whole block skips
         const ScenDev &scg = P.scen[tscen];
@@ -494,9 +509,11 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
             sj[j] = tscen;
             gid[j] = 0ull;
             if (local < count) {
-                const long long home = in_a ? (long long)__ldg(R.pidx + slot) : slot;
+                long long home = in_a ? (long long)__ldg(R.pidx + slot) : slot;
+                if (!LPM_IN_BOUNDS(P.err, home >= 0 && home < P.slot_cap)) home = 0;
                 if (MIXED) {
                     if (in_a) sj[j] = scen_of(P, home);
+                    if (!LPM_IN_BOUNDS(P.err, sj[j] >= 0 && sj[j] < P.n_scen)) sj[j] = 0;
                     const ScenDev &q = P.scen[sj[j]];
                     gid[j] = (unsigned long long)(__ldg(&q.id0) + (home - __ldg(&q.first_slot)));
                 } else {
@@ -694,7 +711,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                     if (on) {
                         const int sp = (int)(tag[j] & TAG_STEP);
                         const ScenDev &q = MIXED ? P.scen[sj[j]] : scg;
-                        const float m0 = __ldg(P.m0 + q.m0_off + (sp - q.rel_first));
+                        const float m0 = m0_of(P, q, sp);
                         vd = to_fixed(m0 * chain_amount(P, d, (float)(k1 - sp) * P.dt),
                                       __ldg(&q.scale));
                     }

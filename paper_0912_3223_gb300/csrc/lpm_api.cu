@@ -379,6 +379,9 @@ void fill_params(const lpm_ctx *c, StepParams &P)
     }
     for (size_t k = 0; k < c->mode_profile.size(); ++k) P.mode_prof[k] = (float)c->mode_profile[k];
     P.mode_sc = P.n_modes ? c->d_mode_sc : nullptr;
+    P.slot_cap = c->cfg.max_particles;
+    P.n_pair = std::max(1, g.n_met_t - 1);
+    P.n_m0 = (int)c->d_m0_cap;
     P.err = c->d_err;
 }
 
@@ -1198,6 +1201,8 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             out.grave = c->d_grave;
             out.grave_count = c->d_grave_n;
             out.w_out = c->langevin ? c->d_w_sorted[1 - cur] : nullptr;
+            out.cap = c->cfg.max_particles;
+            out.err = c->d_err;
             LPM_CUDA(c, launch_sort(s, P, in, out));
             cur = 1 - cur;
             upto = sg.k;
@@ -2042,6 +2047,8 @@ lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &
             out.grave = S.grave;
             out.grave_count = S.grave_n;
             out.w_out = nullptr;
+            out.cap = std::max<long long>(1, c->n_slots_used);
+            out.err = c->d_err;
             LPM_CUDA(c, launch_sort(c->stream, P, in, out));
             c->n_launches += 7;
             cur ^= 1;
@@ -2288,6 +2295,7 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     A.ckpt = c->d_ckpt;
     A.n_slots = c->n_slots_used;
     A.traj = c->adj_traj ? c->d_traj : nullptr;
+    A.traj_cap = (long long)c->d_traj_cap;
     A.fin = c->adj_traj ? c->d_fin : nullptr;
     A.traj_tile = c->d_traj_tile;
     A.tiles = c->d_adj_tiles;

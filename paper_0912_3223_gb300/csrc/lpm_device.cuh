@@ -36,6 +36,24 @@ enum {
 // Device error word bits.
 enum { ERR_NAN = 1u, ERR_INDEX = 2u, ERR_TIMEOUT = 4u };
 
+// The checked build (compiled with -DLPM_CHECKED=1, a separate library): every indexed load
+// and store of the step, sort and adjoint kernels first tests its index against the array
+// it reads or writes; a failed test sets ERR_INDEX in the device error word (reported by
+// the next read-back as LPM_E_CUDA) and the access is clamped or skipped, never trapped.
+// In the default build the tests compile to nothing.
+#ifndef LPM_CHECKED
+#define LPM_CHECKED 0
+#endif
+
+__device__ __forceinline__ bool check_index(unsigned int *err, bool ok)
+{
+    if (!ok) atomicOr(err, ERR_INDEX);
+    return ok;
+}
+
+// True when `cond` holds (always, in the default build); records a failure otherwise.
+#define LPM_IN_BOUNDS(err, cond) (!LPM_CHECKED || ::lpm::check_index((err), (cond)))
+
 struct ScenDev {
     float src_x, src_y, src_z;
     float scale;                     // 2^shift (fixed-point scale), exact power of two
@@ -123,6 +141,9 @@ struct StepParams {
     float mode_eu[MAX_MODES], mode_ev[MAX_MODES];
     float mode_prof[MAX_LEVELS];
     const float *mode_sc;            // [n_scen][8]: phases (cycles), amplitudes (m/s); 32-B rows
+    // array extents for the checked build: home slots, time pairs, initial-mass entries
+    long long slot_cap;
+    int n_pair, n_m0;
     unsigned int *err;
 };
 

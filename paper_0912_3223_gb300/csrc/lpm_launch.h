@@ -74,6 +74,8 @@ struct SortBuffers {
     float4 *grave;
     unsigned int *grave_count;
     float *w_out;                 // Langevin w' of the sorted particles, or nullptr
+    long long cap;                // entries of state_out, pidx_out, slot_of and grave
+    unsigned int *err;            // device error word (bounds of the checked build)
 };
 
 // Sort keys: cells grouped in tiles of 2^SORT_TILE_BITS x 2^SORT_TILE_BITS columns by

@@ -196,6 +196,8 @@ __global__ void sort_scatter_kernel(const SortSource S, const unsigned int *__re
             unsigned int home;
             sort_input(S, i, live_old, src, slot, home);
             const unsigned int dst = first + __popc(peers & ((1u << lane) - 1u));
+            if (!LPM_IN_BOUNDS(B.err, (long long)dst < B.cap && (long long)home < B.cap))
+                continue;
             if (key == dead_key) {
                 B.grave[dst] = src[slot];
                 B.slot_of[home] = SLOT_GRAVE | dst;

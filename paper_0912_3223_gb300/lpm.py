@@ -16,6 +16,13 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblpm.so")
+# The checked build (every kernel index tested against its array; see build.py), loaded
+# instead when the environment sets LPM_CHECKED_BUILD=1 before the first call.
+CHECKED_LIB_PATH = os.path.join(HERE, "liblpm_checked.so")
+
+
+def library_path() -> str:
+    return CHECKED_LIB_PATH if os.environ.get("LPM_CHECKED_BUILD") == "1" else LIB_PATH
 
 LPM_OK, LPM_E_INVALID, LPM_E_OOM, LPM_E_CUDA, LPM_E_STATE, LPM_E_NUMERIC, LPM_E_TIMEOUT = range(7)
 STATUS_NAMES = {0: "LPM_OK", 1: "LPM_E_INVALID", 2: "LPM_E_OOM", 3: "LPM_E_CUDA",
@@ -69,10 +76,13 @@ def load() -> C.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
-                           "`python -c 'import __graft_entry__ as g; g.build()'`")
-    L = C.CDLL(LIB_PATH)
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`"
+                           + (" (the checked build: python paper_0912_3223_gb300/build.py "
+                              "--checked)" if path == CHECKED_LIB_PATH else ""))
+    L = C.CDLL(path)
     vp, i64, dp = C.c_void_p, C.c_int64, C.POINTER(C.c_double)
     L.lpm_create.argtypes = [C.POINTER(lpm_config), vp, C.POINTER(vp)]
     L.lpm_destroy.argtypes = [vp]
