@@ -1,7 +1,7 @@
 """The checked build (every indexed load and store of the kernels tested against its
 array, a failure recorded in the device error word instead of a fault) runs the library's
 kernel families without a single out-of-range index, and gives the default build's
-results bit for bit. It stands in for a memory checker, which this pool does not offer;
+results bit for bit (the adjoint's FP64 atomic sums to rounding). It stands in for a memory checker, which this pool does not offer;
 the checked library is loaded in a child process of its own."""
 import os
 import subprocess
@@ -41,4 +41,9 @@ def test_checked_build_is_clean_and_identical(tmp_path):
     got = np.load(out)
     assert sorted(got.files) == sorted(ref)
     for k, v in ref.items():
-        assert np.array_equal(got[k], v), k
+        if k.startswith("adj_"):
+            # receptor sums and gradients are FP64 atomic sums over particles, whose order
+            # changes from run to run
+            np.testing.assert_allclose(got[k], v, rtol=1e-12, atol=1e-300, err_msg=k)
+        else:
+            assert np.array_equal(got[k], v), k
