@@ -1,8 +1,9 @@
 """The checked build (every indexed load and store of the kernels tested against its
 array, a failure recorded in the device error word instead of a fault) runs the library's
 kernel families without a single out-of-range index, and gives the default build's
-results bit for bit (the adjoint's FP64 atomic sums to rounding). It stands in for a memory checker, which this pool does not offer;
-the checked library is loaded in a child process of its own."""
+results bit for bit (the adjoint's FP64 atomic sums to rounding). It stands in for a
+memory checker, which this pool does not offer; the checked library is loaded in a child
+process of its own."""
 import os
 import subprocess
 import sys
