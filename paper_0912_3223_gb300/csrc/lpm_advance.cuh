@@ -124,9 +124,9 @@ __device__ __forceinline__ void mode_wind(const StepParams &P, const float *msc,
 // load of (slab h, slab h+1 - slab h), blended in time, then in x, y and z. With the
 // boundary-layer columns (EXT and blp), K_z and its derivative come from Eq. 3 instead
 // (4 more 32-byte loads of the time-paired (u*, 1/L, H_z) at the cell's corner columns,
-// bilinear in x, y); with msc (EXT) the scenario's perturbation modes are added to (u, v).
-// Only the EXT instantiations carry that code.
-template <bool EXT, class LEV>
+// bilinear in x, y); with msc (MODES) the scenario's perturbation modes are added to
+// (u, v). Only the EXT or MODES instantiations carry that code.
+template <bool EXT, class LEV, bool MODES = EXT>
 __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const LEV &L,
                                                const float4 *__restrict__ pair,
                                                const float2 *__restrict__ khp,
@@ -164,7 +164,7 @@ __device__ __forceinline__ Met sample_met_pair(const StepParams &P, const LEV &L
     m.u = r.x;
     m.v = r.y;
     m.w = r.z;
-    if (EXT && msc) {
+    if (MODES && msc) {
         float du, dv;
         mode_wind(P, msc, k, c, x, y, tk, du, dv);
         m.u += du;
@@ -319,7 +319,7 @@ __device__ __forceinline__ StepTime step_time(const StepParams &P, const float2 
 // Updates (x, y, z) and returns the new status. (du, dv) is the wind offset of the
 // particle's scenario plus the bias at t_k. With GRIDS, deposition and exit add their mass
 // to the scenario's grids and counters; *fold receives dz/dz_pre (+-1, 0 when clamped).
-template <bool GRIDS, bool EXT = false, class LEV>
+template <bool GRIDS, bool EXT = false, class LEV, bool MODES = EXT>
 __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV &LV,
                                                   const StepTime &T, const ScenDev &sc,
                                                   const ScenDev *scg, unsigned long long gid,
@@ -331,7 +331,8 @@ __device__ __forceinline__ uint32_t particle_step(const StepParams &P, const LEV
     const int k = T.k;
     // 1. weather at the old position and t_k (with the scenario's perturbation modes: msc);
     // 2. diffusivities
-    const Met m = sample_met_pair<EXT>(P, LV, T.pair, T.khp, T.blp, T.ts.f, x, y, z, T.tk, msc);
+    const Met m = sample_met_pair<EXT, LEV, MODES>(P, LV, T.pair, T.khp, T.blp, T.ts.f, x, y, z,
+                                                  T.tk, msc);
     const float sig_h = T.khp ? sqrtf(2.0f * P.k_scale * m.kh * P.dt) : sig_h_uniform;
     const float sig_z = sqrtf(2.0f * P.k_scale * m.kz * P.dt);
     // 3. N(0,1) draws
@@ -439,9 +440,9 @@ struct MinBlocks {
 // offset; the results are bit-identical to the per-scenario path. EXT adds, as uniform
 // run-time options, the dosage samples (every P.dose_every steps) inside the time loop,
 // K_z from Eq. 3 (P.blpair), the daughters of a decay chain (P.n_species > 1), the
-// Langevin variant and the scenarios' perturbation modes (P.n_modes > 0); the default
-// instantiations carry none of that code.
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
+// Langevin variant and the scenarios' perturbation modes (P.n_modes > 0); MODES without
+// EXT carries the modes alone. The default instantiations carry none of that code.
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT, bool MODES>
 __global__ void __launch_bounds__(BLOCK, (MinBlocks<BLOCK, OCC>::value))
 advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *queue, int k0,
                int k1, int do_bin)
@@ -500,7 +501,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         float wv[PPT];                                  // Langevin w' (EXT)
         float *wsrc = in_a ? R.w_a : R.w_b;
         const bool lang = EXT && P.langevin && wsrc;
-        const bool modes = EXT && P.n_modes > 0 && P.mode_sc;
+        const bool modes = MODES && P.n_modes > 0 && P.mode_sc;
         int live = 0;
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
@@ -589,13 +590,13 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
                         du = P.bias_u + fmaf(T.ts.f, o1[j].x - o0[j].x, o0[j].x);
                         dv = P.bias_v + fmaf(T.ts.f, o1[j].y - o0[j].y, o0[j].y);
                     }
-                    st = particle_step<true, EXT>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
+                    st = particle_step<true, EXT, Levels, MODES>(P, LV, T, P.scen[sj[j]], P.scen + sj[j], gid[j],
                                                   sp, sig_h_uniform, du, dv, x[j], y[j], z[j],
                                                   nullptr, lang ? &wv[j] : nullptr,
                                                   modes ? P.mode_sc + 8 * sj[j] : nullptr, &dc[j]);
                 } else {
                     ++steps;
-                    st = particle_step<true, EXT>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
+                    st = particle_step<true, EXT, Levels, MODES>(P, LV, T, sc, &scg, gid[j], sp, sig_h_uniform,
                                                   T.du, T.dv, x[j], y[j], z[j], nullptr,
                                                   lang ? &wv[j] : nullptr,
                                                   modes ? P.mode_sc + 8 * tscen : nullptr, &dc[j]);
@@ -746,41 +747,42 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
     }
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT, bool MODES>
 void adv_prefer_l1()
 {
     // the kernel needs a few KB of shared memory per block: ask for a small carve-out so the
     // rest of the SM's unified L1 serves the weather gathers (measured +0.7 to +1.7 %)
-    cudaFuncSetAttribute(advance_kernel<BLOCK, PPT, OCC, MIXED, EXT>,
+    cudaFuncSetAttribute(advance_kernel<BLOCK, PPT, OCC, MIXED, EXT, MODES>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, 10);
     (void)cudaGetLastError();
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT, bool MODES>
 cudaError_t launch_adv(const AdvanceLaunch &L)
 {
     static std::once_flag once;          // per instantiation; contexts may use several threads
-    std::call_once(once, adv_prefer_l1<BLOCK, PPT, OCC, MIXED, EXT>);
+    std::call_once(once, adv_prefer_l1<BLOCK, PPT, OCC, MIXED, EXT, MODES>);
     const size_t smem = adv_dyn_smem(L.params->n_lut);
-    advance_kernel<BLOCK, PPT, OCC, MIXED, EXT><<<L.grid, BLOCK, smem, L.stream>>>(
+    advance_kernel<BLOCK, PPT, OCC, MIXED, EXT, MODES><<<L.grid, BLOCK, smem, L.stream>>>(
         *L.params, L.ranges, L.n_tiles(), L.queue, L.k0, L.k1, L.do_bin);
     return cudaGetLastError();
 }
 
-template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT>
+template <int BLOCK, int PPT, int OCC, bool MIXED, bool EXT, bool MODES>
 int occ_adv(size_t smem)
 {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, advance_kernel<BLOCK, PPT, OCC, MIXED, EXT>,
-                                                  BLOCK, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, advance_kernel<BLOCK, PPT, OCC, MIXED, EXT, MODES>, BLOCK, smem);
     return n;
 }
 
-// (particles per thread, occupancy variant, mixed scenarios, extended options) ->
-// instantiation, for one block size; the extended options run with 1 particle per thread
+// (particles per thread, occupancy variant, mixed scenarios, options: 0 none, 1 extended,
+// 2 perturbation modes alone) -> instantiation, for one block size; the extended options
+// and the modes run with 1 particle per thread
 #define LPM_ADV_CASE(FN, BLOCK, PPT, OCC, MIX, EX, ...)                                \
     case PPT * 1000 + OCC * 100 + MIX * 10 + EX:                                       \
-        return FN<BLOCK, PPT, OCC, (MIX != 0), (EX != 0)>(__VA_ARGS__);
+        return FN<BLOCK, PPT, OCC, (MIX != 0), (EX == 1), (EX != 0)>(__VA_ARGS__);
 #define LPM_ADV_CASES2(FN, BLOCK, PPT, OCC, EX, ...)                                   \
     LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 0, EX, __VA_ARGS__)                              \
     LPM_ADV_CASE(FN, BLOCK, PPT, OCC, 1, EX, __VA_ARGS__)
@@ -796,19 +798,22 @@ int occ_adv(size_t smem)
     LPM_ADV_CASES2(FN, BLOCK, 4, 2, 0, __VA_ARGS__)                                    \
     LPM_ADV_CASES2(FN, BLOCK, 1, 0, 1, __VA_ARGS__)                                    \
     LPM_ADV_CASES2(FN, BLOCK, 1, 1, 1, __VA_ARGS__)                                    \
-    LPM_ADV_CASES2(FN, BLOCK, 1, 2, 1, __VA_ARGS__)
+    LPM_ADV_CASES2(FN, BLOCK, 1, 2, 1, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 0, 2, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 1, 2, __VA_ARGS__)                                    \
+    LPM_ADV_CASES2(FN, BLOCK, 1, 2, 2, __VA_ARGS__)
 
 #define LPM_ADVANCE_TU(BLOCK)                                                          \
     cudaError_t launch_advance_b##BLOCK(const AdvanceLaunch &L)                         \
     {                                                                                  \
-        switch (L.ppt * 1000 + L.occ * 100 + (L.mixed ? 10 : 0) + (L.ext ? 1 : 0)) {   \
+        switch (L.ppt * 1000 + L.occ * 100 + (L.mixed ? 10 : 0) + L.variant()) {       \
             LPM_ADV_CASES(launch_adv, BLOCK, L)                                        \
         }                                                                              \
         return cudaErrorInvalidValue;                                                  \
     }                                                                                  \
-    int occupancy_b##BLOCK(int ppt, int occ, bool mixed, bool ext, size_t smem)        \
+    int occupancy_b##BLOCK(int ppt, int occ, bool mixed, int variant, size_t smem)     \
     {                                                                                  \
-        switch (ppt * 1000 + occ * 100 + (mixed ? 10 : 0) + (ext ? 1 : 0)) {           \
+        switch (ppt * 1000 + occ * 100 + (mixed ? 10 : 0) + variant) {                 \
             LPM_ADV_CASES(occ_adv, BLOCK, smem)                                        \
         }                                                                              \
         return 0;                                                                      \

@@ -1228,8 +1228,8 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
         L.ppt = c->ppt;
         L.occ = c->occ;
         L.mixed = batched;
-        L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 || P.langevin ||
-                P.n_modes > 0;
+        L.ext = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 || P.langevin;
+        L.modes = P.n_modes > 0;
         const int n_tiles = L.n_tiles();
         keys_ready = false;
         if (n_tiles <= 0) continue;
@@ -1377,8 +1377,10 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
             if (!c->cap_stream)
                 LPM_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
             const cudaStream_t cs = c->cap_stream;
+            const bool ext_opts = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 ||
+                                  P.langevin;
             const int occ_blocks = std::max(1, advance_occupancy(
-                c->block, c->ppt, c->occ, true, ext,
+                c->block, c->ppt, c->occ, true, ext_opts ? 1 : P.n_modes > 0 ? 2 : 0,
                 adv_dyn_smem(P.n_lut)));
             lpm_ctx::Graph ng{};
             ng.k0 = c->k;

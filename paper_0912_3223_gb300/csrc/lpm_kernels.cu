@@ -176,12 +176,12 @@ cudaError_t launch_advance(const AdvanceLaunch &L)
     return cudaErrorInvalidValue;
 }
 
-int advance_occupancy(int block, int ppt, int occ, bool mixed, bool ext, size_t smem)
+int advance_occupancy(int block, int ppt, int occ, bool mixed, int variant, size_t smem)
 {
     switch (block) {
-    case 128: return occupancy_b128(ppt, occ, mixed, ext, smem);
-    case 256: return occupancy_b256(ppt, occ, mixed, ext, smem);
-    case 512: return occupancy_b512(ppt, occ, mixed, ext, smem);
+    case 128: return occupancy_b128(ppt, occ, mixed, variant, smem);
+    case 256: return occupancy_b256(ppt, occ, mixed, variant, smem);
+    case 512: return occupancy_b512(ppt, occ, mixed, variant, smem);
     }
     return 0;
 }

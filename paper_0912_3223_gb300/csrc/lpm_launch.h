@@ -47,9 +47,11 @@ struct AdvanceLaunch {
     int k0, k1, do_bin;
     int block, ppt, occ;
     bool mixed;               // lanes of one tile may belong to different scenarios
-    bool ext;                 // dosage, Eq. 3 K_z or a decay chain is on (1 particle/thread)
+    bool ext;                 // dosage, Eq. 3 K_z, a decay chain or the Langevin variant is on
+    bool modes;               // perturbation modes are on (both: 1 particle per thread)
     unsigned int grid;
     int n_tiles() const { return ranges.tiles_a + ranges.n_b; }
+    int variant() const { return ext ? 1 : modes ? 2 : 0; }   // kernel options, see LPM_ADV_CASES
 };
 
 // Inputs of a sort: the live sorted particles of state_a (when has_a) followed by the B
@@ -119,13 +121,13 @@ inline size_t adv_dyn_smem(int n_lut)
 }
 
 cudaError_t launch_advance(const AdvanceLaunch &L);
-int advance_occupancy(int block, int ppt, int occ, bool mixed, bool ext, size_t smem);
+int advance_occupancy(int block, int ppt, int occ, bool mixed, int variant, size_t smem);
 cudaError_t launch_advance_b128(const AdvanceLaunch &L);
 cudaError_t launch_advance_b256(const AdvanceLaunch &L);
 cudaError_t launch_advance_b512(const AdvanceLaunch &L);
-int occupancy_b128(int ppt, int occ, bool mixed, bool ext, size_t smem);
-int occupancy_b256(int ppt, int occ, bool mixed, bool ext, size_t smem);
-int occupancy_b512(int ppt, int occ, bool mixed, bool ext, size_t smem);
+int occupancy_b128(int ppt, int occ, bool mixed, int variant, size_t smem);
+int occupancy_b256(int ppt, int occ, bool mixed, int variant, size_t smem);
+int occupancy_b512(int ppt, int occ, bool mixed, int variant, size_t smem);
 cudaError_t launch_pack(cudaStream_t s, const float4 *a, const float4 *b, const float *ka,
                         const float *kb, float4 *pair, float2 *khpair, int nx, int ny, int nz);
 cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &in,

@@ -123,3 +123,26 @@ def test_adjoint_refuses_perturbation_modes():
         with pytest.raises(lpm.LpmError) as e:
             lpm.lpm_receptors(sim.ctx, 1, rec, 200.0, 18)
         assert e.value.status == lpm.LPM_E_INVALID and "modes" in str(e.value)
+
+
+def test_modes_alone_and_in_the_extended_kernel_agree():
+    """The perturbation modes run in a kernel of their own, or, with any extended option
+    on (the dosage here, which moves no particle), in the extended kernel: particles and
+    grids are the same bits either way, for mixed-scenario lanes and per-scenario tiles."""
+    from paper_0912_3223_gb300 import Sim
+    cfg = li.make_cfg2(n_scenarios=5, n_steps=240, n_min=300, n_max=1500)
+
+    def run(dose, sort_every):
+        with Sim(cfg, sort_every=sort_every) as sim:
+            if dose:
+                sim.set_dosage(6)
+            sim.step(cfg.n_steps)
+            xyz, tag = sim.particles()
+            grids = [sim.fixed_state(s)[:2] for s in range(cfg.n_scenarios)]
+        return xyz, tag, grids
+
+    for sort_every in (0, 30):
+        a, b = run(False, sort_every), run(True, sort_every)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        for (ca, da), (cb, db) in zip(a[2], b[2]):
+            assert np.array_equal(ca, cb) and np.array_equal(da, db)
