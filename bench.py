@@ -313,7 +313,8 @@ def measure_adjoint(args, stream, storage="checkpoints"):
     (Gaussian kernel, 200 m), sampled every 18 steps; forward (receptors, keeping the states
     the backward needs) and backward (reverse sweep) per run. ``storage``: "checkpoints"
     keeps the state every 64 steps and recomputes each segment in the backward (the form
-    the workload names); "trajectory" keeps every particle-step (9.3 GB) instead."""
+    the workload names; the segments in weather-cell order, one segment's states as
+    scratch); "trajectory" keeps every particle-step (9.3 GB) instead."""
     import numpy as np
     import torch
 

@@ -484,9 +484,12 @@ __device__ __forceinline__ bool seg_entry(const AdjSeg &G, const ScenDev &sc, lo
     return ok;
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(ADJ_BLOCK, 8)
 adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
 {
+    constexpr bool SAMPLE = MODE != SEG_RECOMPUTE;          // receptor sums, sort inputs
+    constexpr bool ROWS = MODE != SEG_CKPT;                 // every state into traj / fin
     const bool from_a = (int)blockIdx.x < G.tiles_a;
     const unsigned int live = from_a ? *G.live : 0u;
     if (from_a && (long long)blockIdx.x * ADJ_BLOCK >= (long long)live) return;
@@ -495,10 +498,11 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     double *s_C = reinterpret_cast<double *>(s_rec + A.R);    // [R]
     unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_C + A.R);   // [n_lut]
     const Levels LV = load_levels(P, s_lut);
-    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
-        s_rec[r] = A.rec[r];
-        s_C[r] = 0.0;
-    }
+    if (SAMPLE)
+        for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK) {
+            s_rec[r] = A.rec[r];
+            s_C[r] = 0.0;
+        }
     __syncthreads();
     const ScenDev sc = P.scen[0];
     const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
@@ -510,7 +514,8 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
         const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
         float x = sc.src_x, y = sc.src_y, z = sc.src_z;
         if (from_a) {
-            const float4 s0 = G.sorted[e];
+            const float4 s0 = MODE == SEG_RECOMPUTE ? G.ck[e] : G.sorted[e];
+            if (MODE == SEG_CKPT) G.ck[e] = s0;
             x = s0.x; y = s0.y; z = s0.z;
         }
         uint32_t st = ST_ACTIVE;
@@ -522,10 +527,11 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
             float fs = 1.0f;
             st = particle_step<false>(P, LV, T, sc, nullptr, gid, sp, sig_h_uniform, T.du, T.dv,
                                       x, y, z, &fs);
-            __stcs(G.traj + (long long)(k - G.k_lo) * G.width + e, make_float4(xb, yb, zb, fs));
+            if (ROWS)
+                __stcs(G.traj + (long long)(k - G.k_lo) * G.width + e, make_float4(xb, yb, zb, fs));
             kn = k + 1;
             if (st != ST_ACTIVE) break;
-            if ((k + 1) % A.every == 0) {
+            if (SAMPLE && (k + 1) % A.every == 0) {
                 const float m = m0 * expf(-P.lambda * (float)(k + 1 - sp) * P.dt) * A.inv_ns;
                 int lo, hi;
                 receptors_near(A, x, y, lo, hi);
@@ -541,15 +547,20 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
                 }
             }
         }
-        G.fin[e] = make_float4(x, y, z, __uint_as_float((uint32_t)kn |
-                                                        (st != ST_ACTIVE ? 0x80000000u : 0u)));
-        const float4 out = pack_state(x, y, z, st, sp);          // what the sort reads
-        if (from_a) G.sorted[e] = out;
-        else G.home[home] = out;
+        if (ROWS)
+            G.fin[e] = make_float4(x, y, z, __uint_as_float((uint32_t)kn |
+                                                            (st != ST_ACTIVE ? 0x80000000u : 0u)));
+        if (SAMPLE) {
+            const float4 out = pack_state(x, y, z, st, sp);      // what the sort reads
+            if (from_a) G.sorted[e] = out;
+            else G.home[home] = out;
+        }
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK)
-        if (s_C[r] != 0.0) atomicAdd(A.C + r, s_C[r]);
+    if (SAMPLE) {
+        __syncthreads();
+        for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK)
+            if (s_C[r] != 0.0) atomicAdd(A.C + r, s_C[r]);
+    }
 }
 
 template <bool KHG>
@@ -625,7 +636,9 @@ static void adj_set_carveout()
     cudaFuncSetAttribute(adj_backward_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_backward_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_backward_traj_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_forward_seg_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_forward_seg_kernel<SEG_STORE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_forward_seg_kernel<SEG_CKPT>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    cudaFuncSetAttribute(adj_forward_seg_kernel<SEG_RECOMPUTE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_backward_seg_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_backward_seg_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     (void)cudaGetLastError();
@@ -638,11 +651,19 @@ static void adj_prefer_l1()
 }
 
 cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
-                                   const AdjSeg &G, int n_blocks)
+                                   const AdjSeg &G, int n_blocks, int mode)
 {
     if (n_blocks <= 0) return cudaSuccess;
     adj_prefer_l1();
-    adj_forward_seg_kernel<<<n_blocks, ADJ_BLOCK, adj_smem_forward(P, A), s>>>(P, A, G);
+    const size_t sm = adj_smem_forward(P, A);
+    switch (mode) {
+    case SEG_STORE: adj_forward_seg_kernel<SEG_STORE><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G); break;
+    case SEG_CKPT: adj_forward_seg_kernel<SEG_CKPT><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G); break;
+    case SEG_RECOMPUTE:
+        adj_forward_seg_kernel<SEG_RECOMPUTE><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

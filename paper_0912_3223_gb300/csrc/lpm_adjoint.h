@@ -68,6 +68,17 @@ struct AdjSeg {
     float4 *fin;                      // [width] state after the entry's last step in the
                                       // segment, w = that step + 1 | event bit 31
     float4 *mu;                       // [slots] dL/dX at the segment's end, by home slot
+    float4 *ck;                       // checkpoint form: [tiles_a * ADJ_BLOCK] the sorted
+                                      // entries' states at k_lo, kept by the receptor forward
+                                      // for the recomputation (traj, fin: one segment's scratch)
 };
+
+// What a launch of the segment forward does (adj_forward_seg_kernel):
+//  SEG_STORE     receptor sums, the sort's end states, and every state into traj / fin;
+//  SEG_CKPT      receptor sums, the sort's end states, and the sorted entries' starting
+//                states into ck (no rows);
+//  SEG_RECOMPUTE the segment again from ck (and the source, for its releases), every state
+//                into traj / fin (the scratch) and nothing else.
+enum SegMode { SEG_STORE = 0, SEG_CKPT = 1, SEG_RECOMPUTE = 2 };
 
 }  // namespace lpm

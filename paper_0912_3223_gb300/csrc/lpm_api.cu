@@ -170,6 +170,7 @@ struct lpm_ctx {
         std::vector<int> seg_tile;              // [n_seg + 1] first release tile of a segment
         std::vector<int> tiles_a;               // [n_seg] blocks over its sorted entries
         std::vector<long long> off, foff;       // [n_seg + 1] trajectory / end-state offsets
+        std::vector<long long> ckoff;           // [n_seg + 1] checkpoint offsets (sorted entries)
         long long max_width = 0;
         Tile *d_tiles = nullptr;
         unsigned int *ord = nullptr, *live = nullptr, *keys = nullptr, *hist = nullptr,
@@ -178,6 +179,8 @@ struct lpm_ctx {
         float4 *home = nullptr, *mu = nullptr, *grave = nullptr;
     } as;
     bool adj_sorted = false;                    // the held forward used the sorted form
+                                                // (with adj_traj false: its checkpoint form,
+                                                // d_traj / d_fin one segment's scratch)
     float4 *d_rec = nullptr;
     int *d_rbin_off = nullptr;              // receptor bins (AdjParams)
     unsigned char *d_rbin_idx = nullptr;
@@ -1928,9 +1931,10 @@ lpm_status adj_plan_segments(lpm_ctx *c)
     S.tiles_a.assign((size_t)n_seg, 0);
     S.off.assign((size_t)n_seg + 1, 0);
     S.foff.assign((size_t)n_seg + 1, 0);
+    S.ckoff.assign((size_t)n_seg + 1, 0);
     S.max_width = 0;
     const ScenHost &h = c->scen[0];
-    long long off = 0, foff = 0;
+    long long off = 0, foff = 0, ckoff = 0;
     for (int s = 0; s < n_seg; ++s) {
         S.seg_tile[(size_t)s] = (int)S.tiles.size();
         const long long a = released_before(h, (long long)s * CK);
@@ -1947,13 +1951,16 @@ lpm_status adj_plan_segments(lpm_ctx *c)
             (long long)(S.tiles_a[(size_t)s] + (int)S.tiles.size() - S.seg_tile[(size_t)s]) * ADJ_BLOCK;
         S.off[(size_t)s] = off;
         S.foff[(size_t)s] = foff;
+        S.ckoff[(size_t)s] = ckoff;
         off += std::min<long long>(CK, NS - (long long)s * CK) * width;
         foff += width;
+        ckoff += (long long)S.tiles_a[(size_t)s] * ADJ_BLOCK;
         S.max_width = std::max(S.max_width, width);
     }
     S.seg_tile[(size_t)n_seg] = (int)S.tiles.size();
     S.off[(size_t)n_seg] = off;
     S.foff[(size_t)n_seg] = foff;
+    S.ckoff[(size_t)n_seg] = ckoff;
     LPM_CUDA(c, cudaStreamSynchronize(c->stream));
     if (S.d_tiles) cudaFree(S.d_tiles);
     S.d_tiles = nullptr;
@@ -1987,7 +1994,9 @@ lpm_status adj_sorted_buffers(lpm_ctx *c)
     return LPM_OK;
 }
 
-// Segment s of the sorted form, its sorted entries in S.st[cur].
+// Segment s of the sorted form, its sorted entries in S.st[cur]. Trajectory form: its rows
+// and end states within the whole trajectory; checkpoint form: its checkpoint, and the
+// scratch for its rows and end states.
 AdjSeg adj_segment(const lpm_ctx *c, int s, int cur)
 {
     const lpm_ctx::AdjSorted &S = c->as;
@@ -2002,9 +2011,10 @@ AdjSeg adj_segment(const lpm_ctx *c, int s, int cur)
     G.tiles = S.d_tiles;
     G.b_first = S.seg_tile[(size_t)s];
     G.width = (long long)(G.tiles_a + S.seg_tile[(size_t)s + 1] - G.b_first) * ADJ_BLOCK;
-    G.traj = c->d_traj + S.off[(size_t)s];
-    G.fin = c->d_fin + S.foff[(size_t)s];
+    G.traj = c->d_traj + (c->adj_traj ? S.off[(size_t)s] : 0);
+    G.fin = c->d_fin + (c->adj_traj ? S.foff[(size_t)s] : 0);
     G.mu = S.mu;
+    G.ck = c->adj_traj ? nullptr : c->d_ckpt + S.ckoff[(size_t)s];
     return G;
 }
 
@@ -2023,7 +2033,8 @@ lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &
         if (s > 0)
             LPM_CUDA(c, cudaMemcpyAsync(S.live + s, S.meta, sizeof(unsigned int),
                                         cudaMemcpyDeviceToDevice, c->stream));
-        LPM_CUDA(c, launch_adj_forward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK)));
+        LPM_CUDA(c, launch_adj_forward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK),
+                                           c->adj_traj ? SEG_STORE : SEG_CKPT));
         c->n_launches++;
         if (s + 1 < n_seg) {
             SortSource in;
@@ -2059,35 +2070,55 @@ lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &
     return LPM_OK;
 }
 
+// Backward of the sorted form, last segment first; the checkpoint form first recomputes
+// each segment from its checkpoint into the scratch (the same keyed draws and FP32
+// arithmetic in the same entry order, so the same states and events as the receptor forward).
 lpm_status adj_backward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &A)
 {
     for (int s = (int)c->as.tiles_a.size() - 1; s >= 0; --s) {
         const AdjSeg G = adj_segment(c, s, 0);
+        if (!c->adj_traj) {
+            LPM_CUDA(c, launch_adj_forward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK),
+                                               SEG_RECOMPUTE));
+            c->n_launches++;
+        }
         LPM_CUDA(c, launch_adj_backward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK)));
         c->n_launches++;
     }
     return LPM_OK;
 }
 
-// Storage of the forward's states for the backward: the whole trajectory when it fits in
-// the limit and in free device memory (keeping 8 GiB spare), else checkpoints every CK steps.
-lpm_status adj_storage(lpm_ctx *c, size_t nt_need, size_t nf_need)
+// Storage of the forward's states for the backward: the whole trajectory (nt_need rows,
+// nf_need end states) when it fits in the limit and in free device memory (keeping 8 GiB
+// spare), else checkpoints every CK steps. For the checkpoint form of the sorted segments
+// the trajectory buffers become one segment's scratch (st_need rows, sf_need end states;
+// `scratch` tells whether it fits in free memory); st_need = 0 frees them.
+lpm_status adj_storage(lpm_ctx *c, size_t nt_need, size_t nf_need, size_t st_need,
+                       size_t sf_need, bool &scratch)
 {
+    scratch = false;
+    const size_t spare = (size_t)8 << 30;
     const size_t need_b = (nt_need + nf_need) * sizeof(float4);
     bool traj = need_b <= c->adj_store_max;
+    auto free_rows = [c]() {
+        for (float4 **p : {&c->d_traj, &c->d_fin}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        c->d_traj_cap = c->d_fin_cap = 0;
+        c->adj_sig.clear();
+    };
     if (traj && (nt_need > c->d_traj_cap || nf_need > c->d_fin_cap)) {
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
         size_t fr = 0, tot = 0;
         LPM_CUDA(c, cudaMemGetInfo(&fr, &tot));
         const size_t held = (c->d_traj_cap + c->d_fin_cap + c->d_ckpt_cap) * sizeof(float4);
-        traj = need_b + ((size_t)8 << 30) <= fr + held;
+        traj = need_b + spare <= fr + held;
         if (traj) {
-            for (float4 **p : {&c->d_traj, &c->d_fin, &c->d_ckpt}) {
-                if (*p) cudaFree(*p);
-                *p = nullptr;
-            }
-            c->d_traj_cap = c->d_fin_cap = c->d_ckpt_cap = 0;
-            c->adj_sig.clear();
+            free_rows();
+            if (c->d_ckpt) cudaFree(c->d_ckpt);
+            c->d_ckpt = nullptr;
+            c->d_ckpt_cap = 0;
             const size_t nt = std::max<size_t>(1, nt_need);
             const size_t nf = std::max<size_t>(1, nf_need);
             if (cudaMalloc(&c->d_traj, nt * sizeof(float4)) == cudaSuccess &&
@@ -2096,22 +2127,37 @@ lpm_status adj_storage(lpm_ctx *c, size_t nt_need, size_t nf_need)
                 c->d_fin_cap = nf;
             } else {
                 (void)cudaGetLastError();             // out of memory: use checkpoints
-                for (float4 **p : {&c->d_traj, &c->d_fin}) {
-                    if (*p) cudaFree(*p);
-                    *p = nullptr;
-                }
+                free_rows();
                 traj = false;
             }
         }
     }
-    if (!traj && (c->d_traj || c->d_fin)) {
-        LPM_CUDA(c, cudaStreamSynchronize(c->stream));
-        for (float4 **p : {&c->d_traj, &c->d_fin}) {
-            if (*p) cudaFree(*p);
-            *p = nullptr;
+    if (!traj) {
+        // keep buffers that hold the scratch without being more than twice its size
+        const bool keep = st_need > 0 && st_need <= c->d_traj_cap && sf_need <= c->d_fin_cap &&
+                          c->d_traj_cap <= 2 * st_need && c->d_fin_cap <= 2 * sf_need;
+        if (keep) {
+            scratch = true;
+        } else {
+            if (c->d_traj || c->d_fin) {
+                LPM_CUDA(c, cudaStreamSynchronize(c->stream));
+                free_rows();
+            }
+            if (st_need > 0) {
+                size_t fr = 0, tot = 0;
+                LPM_CUDA(c, cudaMemGetInfo(&fr, &tot));
+                if ((st_need + sf_need) * sizeof(float4) + spare <= fr &&
+                    cudaMalloc(&c->d_traj, st_need * sizeof(float4)) == cudaSuccess &&
+                    cudaMalloc(&c->d_fin, sf_need * sizeof(float4)) == cudaSuccess) {
+                    c->d_traj_cap = st_need;
+                    c->d_fin_cap = sf_need;
+                    scratch = true;
+                } else {
+                    (void)cudaGetLastError();         // no room: release-order checkpoints
+                    free_rows();
+                }
+            }
         }
-        c->d_traj_cap = c->d_fin_cap = 0;
-        c->adj_sig.clear();
     }
     c->adj_traj = traj;
     return LPM_OK;
@@ -2182,15 +2228,19 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
     if (!reuse) {
         const bool want_sorted = g.n_scenarios == 1 && c->sort_every > 0;
         const lpm_ctx::AdjSorted &S = c->as;
-        lpm_status sst = want_sorted
-                             ? adj_storage(c, (size_t)S.off.back(), (size_t)S.foff.back())
-                             : adj_storage(c, c->traj_need, (size_t)c->n_slots_used);
+        bool scratch = false;
+        lpm_status sst =
+            want_sorted ? adj_storage(c, (size_t)S.off.back(), (size_t)S.foff.back(),
+                                      (size_t)CK * (size_t)S.max_width, (size_t)S.max_width, scratch)
+                        : adj_storage(c, c->traj_need, (size_t)c->n_slots_used, 0, 0, scratch);
         if (sst != LPM_OK) return sst;
-        c->adj_sorted = c->adj_traj && want_sorted;
+        c->adj_sorted = want_sorted && (c->adj_traj || scratch);
         if (c->adj_sorted && (sst = adj_sorted_buffers(c)) != LPM_OK) return sst;
     }
     const int n_ck = (int)((g.n_steps + CK - 1) / CK);
-    const size_t need_ck = (size_t)n_ck * (size_t)c->n_slots_used;
+    // checkpoints: the sorted entries of every segment, or every slot every CK steps
+    const size_t need_ck = c->adj_sorted ? (size_t)std::max<long long>(1, c->as.ckoff.back())
+                                         : (size_t)n_ck * (size_t)c->n_slots_used;
     if (!c->adj_traj && need_ck > c->d_ckpt_cap) {
         LPM_CUDA(c, cudaStreamSynchronize(c->stream));
         if (c->d_ckpt) cudaFree(c->d_ckpt);

@@ -158,7 +158,7 @@ struct AdjSeg;
 cudaError_t launch_adj_forward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles);
 cudaError_t launch_adj_backward(cudaStream_t s, const StepParams &P, const AdjParams &A, int n_tiles);
 cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
-                                   const AdjSeg &G, int n_blocks);
+                                   const AdjSeg &G, int n_blocks, int mode);
 cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const AdjParams &A,
                                     const AdjSeg &G, int n_blocks);
 

@@ -1,6 +1,6 @@
 """Small runs covering every kernel family of the library (plain and sorted advance,
 batched mixed-scenario lanes with perturbation modes, the extended options, the sort, the
-budget, the adjoint's trajectory and checkpoint forms), returning their outputs: the
+budget, the adjoint's trajectory and checkpoint forms, cell-sorted and in release order), returning their outputs: the
 checked-build test runs them once with each library and compares."""
 import dataclasses
 
@@ -35,8 +35,10 @@ def run_cases() -> dict:
     adj = li.make_cfg3(n_particles=3000, n_steps=240)
     rec = li.make_receptors()
     w = np.linspace(-1.0, 1.0, rec.shape[0])[None, :]
-    for name, storage in [("adj_traj", None), ("adj_ckpt", 0)]:
+    for name, storage, sort in [("adj_traj", None, 60), ("adj_ckpt", 0, 60),
+                                ("adj_traj_release", None, 0), ("adj_ckpt_release", 0, 0)]:
         with Sim(adj) as sim:
+            lpm.lpm_set_sort(sim.ctx, sort)
             if storage is not None:
                 lpm.lpm_set_adjoint_storage(sim.ctx, storage)
             out[f"{name}_C"] = lpm.lpm_receptors(sim.ctx, 1, rec, 200.0, 18)

@@ -198,11 +198,12 @@ def test_batched_inversion_reduces_misfit_and_approaches_the_hidden_source():
 
 
 def test_trajectory_and_checkpoint_storage_agree():
-    """The three backward forms take the same paths and events, so receptors and gradients
-    agree to the order of the FP64 sums: the trajectory re-sorted by weather cell every 64
-    steps (one scenario, sorting on), the trajectory in release order (sorting off, or a
-    batch of candidates), and 64-step checkpoints with recomputation (a limit below the
-    trajectory's size). One scenario with deposition and exits, and a batch of three."""
+    """The backward forms take the same paths and events, so receptors and gradients agree
+    to the order of the FP64 sums: the trajectory re-sorted by weather cell every 64 steps
+    (one scenario, sorting on), the trajectory in release order (sorting off, or a batch of
+    candidates), and 64-step checkpoints with recomputation (a limit below the trajectory's
+    size), in cell-sorted segments (one scenario, sorting on) or in release order. One
+    scenario with deposition and exits, and a batch of three."""
     from paper_0912_3223_gb300 import Sim, lpm
     cfg, rec = _realistic(n=5000, steps=400)
     cand, _, _ = li.make_cfg4(n_candidates=3, n_per=3000, n_steps=300, n_obs=1000)
@@ -210,7 +211,8 @@ def test_trajectory_and_checkpoint_storage_agree():
         w = np.linspace(-1.0, 1.0, c.n_scenarios * rec.shape[0]).reshape(c.n_scenarios, -1)
         out = {}
         for form, limit, sort in [("trajectory", 1 << 37, 60), ("release order", 1 << 37, 0),
-                                  ("checkpoints", 0, 60), ("checkpoints (limit)", 1024, 60)]:
+                                  ("checkpoints", 0, 60), ("checkpoints (limit)", 1024, 60),
+                                  ("checkpoints in release order", 0, 0)]:
             with Sim(c) as sim:
                 lpm.lpm_set_sort(sim.ctx, sort)
                 lpm.lpm_set_adjoint_storage(sim.ctx, limit)
@@ -225,11 +227,18 @@ def test_trajectory_and_checkpoint_storage_agree():
         # same order of the per-particle FP32 sums: agree to the order of the FP64 sums
         C0, g0 = out["release order"]
         assert np.abs(g0).max() > 0
-        for form in ("checkpoints", "checkpoints (limit)"):
+        # one scenario: the sorted checkpoint form sweeps the same entries in the same order
+        # as the sorted trajectory; a batch has no sorted form, so both limits give the
+        # release-order checkpoints
+        pairs = [("checkpoints in release order", "release order")]
+        pairs += [(f, "trajectory" if c.n_scenarios == 1 else "release order")
+                  for f in ("checkpoints", "checkpoints (limit)")]
+        for form, base in pairs:
             C1, g1 = out[form]
-            np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max(),
+            Cb, gb = out[base]
+            np.testing.assert_allclose(C1, Cb, rtol=1e-12, atol=1e-15 * np.abs(Cb).max(),
                                        err_msg=form)
-            np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max(),
+            np.testing.assert_allclose(g1, gb, rtol=1e-9, atol=1e-12 * np.abs(gb).max(),
                                        err_msg=form)
         # the sorted form carries dL/dX between segments exactly (FP32 values; sums over
         # particles are FP64) but restarts each particle's FP32 parameter sums every 64
@@ -286,7 +295,7 @@ def test_adjoint_with_gridded_kh_matches_oracle_in_every_storage_form():
     w = np.linspace(-1.0, 1.0, rec.shape[0])
     ref = oracle.adjoint(cfg, rec, SIGMA, 18, w)
     assert np.abs(ref[27:28]).max() > 0
-    for limit, sort in ((1 << 37, 60), (1 << 37, 0), (0, 60)):
+    for limit, sort in ((1 << 37, 60), (1 << 37, 0), (0, 60), (0, 0)):
         with Sim(cfg) as sim:
             lpm.lpm_set_sort(sim.ctx, sort)
             lpm.lpm_set_adjoint_storage(sim.ctx, limit)
