@@ -435,11 +435,15 @@ lpm_status lpm_adjoint(lpm_ctx *ctx, const double *receptors, int R, double band
  * 64-step segments over the particles re-sorted by weather cell at each segment start
  * (about the same size); otherwise in release order.
  * Otherwise, and always with max_bytes = 0, it keeps a checkpoint every 64 steps (16 B per
- * particle each) and the backward recomputes each 64-step segment from its checkpoint.
- * Both give the same gradients up to the order of the FP64 sums. Default 128 GiB. Drops
- * the held forward. An allocation that fails falls back to checkpoints (no error).
- * lpm_adjoint_storage: *trajectory = 1 when the last receptor forward kept the trajectory,
- * *bytes = device bytes held for the adjoint's states (trajectory or checkpoints).
+ * particle each) and the backward recomputes each 64-step segment from its checkpoint:
+ * with one scenario and sorting on, the segments in the same cell order into a scratch of
+ * one segment's states (16 B per particle and step of the widest segment, taken only when
+ * it fits in free device memory with 8 GiB spare), else each particle's segment in release
+ * order. All forms give the same gradients up to the order of the FP64 sums. Default
+ * 128 GiB. Drops the held forward. An allocation that fails falls back to checkpoints (no
+ * error). lpm_adjoint_storage: *trajectory = 1 when the last receptor forward kept the
+ * trajectory, *bytes = device bytes held for the adjoint's states (trajectory, or
+ * checkpoints and scratch).
  */
 lpm_status lpm_set_adjoint_storage(lpm_ctx *ctx, uint64_t max_bytes);
 lpm_status lpm_adjoint_storage(lpm_ctx *ctx, int *trajectory, uint64_t *bytes);
