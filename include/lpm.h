@@ -437,9 +437,9 @@ lpm_status lpm_adjoint(lpm_ctx *ctx, const double *receptors, int R, double band
  * Otherwise, and always with max_bytes = 0, it keeps a checkpoint every 64 steps (16 B per
  * particle each) and the backward recomputes each 64-step segment from its checkpoint:
  * with one scenario and sorting on, the segments in the same cell order into a scratch of
- * one segment's states (16 B per particle and step of the widest segment, taken only when
- * it fits in free device memory with 8 GiB spare), else each particle's segment in release
- * order. All forms give the same gradients up to the order of the FP64 sums. Default
+ * two segments' states (2 x 16 B per particle and step of the widest segment, taken only
+ * when it fits in free device memory with 8 GiB spare; one segment is recomputed while the
+ * other is swept), else each particle's segment in release order. All forms give the same gradients up to the order of the FP64 sums. Default
  * 128 GiB. Drops the held forward. An allocation that fails falls back to checkpoints (no
  * error). lpm_adjoint_storage: *trajectory = 1 when the last receptor forward kept the
  * trajectory, *bytes = device bytes held for the adjoint's states (trajectory, or

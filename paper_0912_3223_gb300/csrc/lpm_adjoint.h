@@ -70,7 +70,8 @@ struct AdjSeg {
     float4 *mu;                       // [slots] dL/dX at the segment's end, by home slot
     float4 *ck;                       // checkpoint form: [tiles_a * ADJ_BLOCK] the sorted
                                       // entries' states at k_lo, kept by the receptor forward
-                                      // for the recomputation (traj, fin: one segment's scratch)
+                                      // for the recomputation (traj, fin: the segment's half
+                                      // of a two-segment scratch)
 };
 
 // What a launch of the segment forward does (adj_forward_seg_kernel):

@@ -61,6 +61,11 @@ struct lpm_ctx {
     bool any_rain = false;
     // asynchronous weather uploads from page-locked host memory
     cudaStream_t copy_stream = nullptr;
+    // the adjoint's checkpoint form recomputes the next segment on its own stream while the
+    // current one is swept; events: a scratch half recomputed (ev_adj[0..1]) and swept
+    // (ev_adj[2..3]), and the sweep's start (ev_adj[4])
+    cudaStream_t adj_stream = nullptr;
+    cudaEvent_t ev_adj[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t ev_main = nullptr;          // orders a copy after the context stream's work
     std::vector<cudaEvent_t> ev_pair;       // time pair h packed (copy stream)
     std::vector<char> pair_pending;
@@ -180,7 +185,7 @@ struct lpm_ctx {
     } as;
     bool adj_sorted = false;                    // the held forward used the sorted form
                                                 // (with adj_traj false: its checkpoint form,
-                                                // d_traj / d_fin one segment's scratch)
+                                                // d_traj / d_fin two segments' scratch)
     float4 *d_rec = nullptr;
     int *d_rbin_off = nullptr;              // receptor bins (AdjParams)
     unsigned char *d_rbin_idx = nullptr;
@@ -837,6 +842,10 @@ void lpm_destroy(lpm_ctx *c)
         if (e) cudaEventDestroy(e);
     if (c->ev_main) cudaEventDestroy(c->ev_main);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->adj_stream) cudaStreamSynchronize(c->adj_stream);
+    for (cudaEvent_t e : c->ev_adj)
+        if (e) cudaEventDestroy(e);
+    if (c->adj_stream) cudaStreamDestroy(c->adj_stream);
     drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -2011,8 +2020,9 @@ AdjSeg adj_segment(const lpm_ctx *c, int s, int cur)
     G.tiles = S.d_tiles;
     G.b_first = S.seg_tile[(size_t)s];
     G.width = (long long)(G.tiles_a + S.seg_tile[(size_t)s + 1] - G.b_first) * ADJ_BLOCK;
-    G.traj = c->d_traj + (c->adj_traj ? S.off[(size_t)s] : 0);
-    G.fin = c->d_fin + (c->adj_traj ? S.foff[(size_t)s] : 0);
+    // checkpoint form: the scratch has two halves, segment s in half s & 1
+    G.traj = c->d_traj + (c->adj_traj ? S.off[(size_t)s] : (s & 1) * (long long)CK * S.max_width);
+    G.fin = c->d_fin + (c->adj_traj ? S.foff[(size_t)s] : (s & 1) * S.max_width);
     G.mu = S.mu;
     G.ck = c->adj_traj ? nullptr : c->d_ckpt + S.ckoff[(size_t)s];
     return G;
@@ -2070,18 +2080,65 @@ lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &
     return LPM_OK;
 }
 
-// Backward of the sorted form, last segment first; the checkpoint form first recomputes
-// each segment from its checkpoint into the scratch (the same keyed draws and FP32
-// arithmetic in the same entry order, so the same states and events as the receptor forward).
+// Backward of the checkpoint form of the sorted segments, last segment first: each
+// segment is recomputed from its checkpoint (the same keyed draws and FP32 arithmetic in
+// the same entry order, so the same states and events as the receptor forward) into one
+// half of the scratch, on the context's second stream, so that segment s - 1 is recomputed
+// into the other half while segment s is swept; each sweep waits for its own
+// recomputation, and the sweeps stay in order on the context stream (they hand dL/dX down
+// through G.mu).
+lpm_status adj_backward_ckpt(lpm_ctx *c, const StepParams &P, const AdjParams &A)
+{
+    const int n_seg = (int)c->as.tiles_a.size();
+    if (n_seg < 1) return LPM_OK;
+    if (!c->adj_stream)
+        LPM_CUDA(c, cudaStreamCreateWithFlags(&c->adj_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : c->ev_adj)
+        if (!e) LPM_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEvent_t *recomputed = c->ev_adj, *swept = c->ev_adj + 2;
+    auto recompute = [&](int s) -> lpm_status {
+        const AdjSeg G = adj_segment(c, s, 0);
+        LPM_CUDA(c, launch_adj_forward_seg(c->adj_stream, P, A, G, (int)(G.width / ADJ_BLOCK),
+                                           SEG_RECOMPUTE));
+        LPM_CUDA(c, cudaEventRecord(recomputed[s & 1], c->adj_stream));
+        c->n_launches++;
+        return LPM_OK;
+    };
+    LPM_CUDA(c, cudaEventRecord(c->ev_adj[4], c->stream));       // the forward's states
+    LPM_CUDA(c, cudaStreamWaitEvent(c->adj_stream, c->ev_adj[4], 0));
+    lpm_status st = recompute(n_seg - 1);
+    if (st != LPM_OK) return st;
+    for (int s = n_seg - 1; s >= 0; --s) {
+        if (s > 0) {
+            // half (s - 1) & 1 was last read by the sweep of segment s + 1
+            if (s + 1 < n_seg)
+                LPM_CUDA(c, cudaStreamWaitEvent(c->adj_stream, swept[(s + 1) & 1], 0));
+            if ((st = recompute(s - 1)) != LPM_OK) return st;
+        }
+        const AdjSeg G = adj_segment(c, s, 0);
+        LPM_CUDA(c, cudaStreamWaitEvent(c->stream, recomputed[s & 1], 0));
+        LPM_CUDA(c, launch_adj_backward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK)));
+        LPM_CUDA(c, cudaEventRecord(swept[s & 1], c->stream));
+        c->n_launches++;
+    }
+    return LPM_OK;
+}
+
+// Backward of the sorted form, last segment first: the trajectory form sweeps the stored
+// segments; the checkpoint form recomputes them (adj_backward_ckpt).
 lpm_status adj_backward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &A)
 {
+    if (!c->adj_traj) {
+        const lpm_status st = adj_backward_ckpt(c, P, A);
+        // whatever ran on the second stream is ordered before the context stream's next
+        // work, also when a launch failed part-way
+        if (c->adj_stream && c->ev_adj[4] &&
+            cudaEventRecord(c->ev_adj[4], c->adj_stream) == cudaSuccess)
+            (void)cudaStreamWaitEvent(c->stream, c->ev_adj[4], 0);
+        return st;
+    }
     for (int s = (int)c->as.tiles_a.size() - 1; s >= 0; --s) {
         const AdjSeg G = adj_segment(c, s, 0);
-        if (!c->adj_traj) {
-            LPM_CUDA(c, launch_adj_forward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK),
-                                               SEG_RECOMPUTE));
-            c->n_launches++;
-        }
         LPM_CUDA(c, launch_adj_backward_seg(c->stream, P, A, G, (int)(G.width / ADJ_BLOCK)));
         c->n_launches++;
     }
@@ -2091,7 +2148,7 @@ lpm_status adj_backward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams 
 // Storage of the forward's states for the backward: the whole trajectory (nt_need rows,
 // nf_need end states) when it fits in the limit and in free device memory (keeping 8 GiB
 // spare), else checkpoints every CK steps. For the checkpoint form of the sorted segments
-// the trajectory buffers become one segment's scratch (st_need rows, sf_need end states;
+// the trajectory buffers become the recomputation's scratch (st_need rows, sf_need end states;
 // `scratch` tells whether it fits in free memory); st_need = 0 frees them.
 lpm_status adj_storage(lpm_ctx *c, size_t nt_need, size_t nf_need, size_t st_need,
                        size_t sf_need, bool &scratch)
@@ -2231,7 +2288,8 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
         bool scratch = false;
         lpm_status sst =
             want_sorted ? adj_storage(c, (size_t)S.off.back(), (size_t)S.foff.back(),
-                                      (size_t)CK * (size_t)S.max_width, (size_t)S.max_width, scratch)
+                                      2 * (size_t)CK * (size_t)S.max_width,
+                                      2 * (size_t)S.max_width, scratch)
                         : adj_storage(c, c->traj_need, (size_t)c->n_slots_used, 0, 0, scratch);
         if (sst != LPM_OK) return sst;
         c->adj_sorted = want_sorted && (c->adj_traj || scratch);
