@@ -283,6 +283,34 @@ def test_sorted_trajectory_with_late_release_and_partial_segment_matches_oracle(
     np.testing.assert_allclose(g[27:], ref[27:], atol=0.01 * np.abs(ref[27:]).max())
 
 
+def test_checkpoint_segments_on_two_streams_match_the_trajectory():
+    """The checkpoint form recomputes segment s - 1 on a second stream while segment s is
+    swept, the two segments in the two halves of a scratch: runs of one, two, three and
+    seven segments (the last one partial) give the sorted trajectory form's receptors and
+    gradients, and repeated sweeps of the same held forward give the same gradients."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    for steps in (50, 128, 150, 401):
+        cfg, rec = _realistic(n=2500, steps=steps)
+        every = 9
+        w = np.linspace(-1.0, 1.0, rec.shape[0])[None, :]
+        out = {}
+        for limit in (1 << 37, 0):
+            with Sim(cfg) as sim:
+                lpm.lpm_set_adjoint_storage(sim.ctx, limit)
+                C = lpm.lpm_receptors(sim.ctx, 1, rec, SIGMA, every)
+                gs = [lpm.lpm_adjoint(sim.ctx, rec, SIGMA, every, w, 24) for _ in range(3)]
+                assert lpm.lpm_adjoint_storage(sim.ctx)[0] == (limit != 0)
+            for g in gs[1:]:
+                np.testing.assert_allclose(g, gs[0], rtol=1e-12, atol=1e-15 * np.abs(gs[0]).max())
+            out[limit] = (C, gs[0])
+        (C0, g0), (C1, g1) = out[1 << 37], out[0]
+        assert np.abs(g0).max() > 0, steps
+        np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max(),
+                                   err_msg=str(steps))
+        np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max(),
+                                   err_msg=str(steps))
+
+
 def test_adjoint_with_gridded_kh_matches_oracle_in_every_storage_form():
     """A gridded K_h field brings its spatial gradient into the transposed Jacobian (the
     sqrt(K_h) derivative of the horizontal displacement): the cell-sorted trajectory, the
