@@ -484,8 +484,10 @@ __device__ __forceinline__ bool seg_entry(const AdjSeg &G, const ScenDev &sc, lo
     return ok;
 }
 
+// 8 blocks per SM (64 registers) for the trajectory form; 7 (72 registers, no spills) for
+// the checkpoint form's forward and recomputation, measured 2 % faster there
 template <int MODE>
-__global__ void __launch_bounds__(ADJ_BLOCK, 8)
+__global__ void __launch_bounds__(ADJ_BLOCK, MODE == SEG_STORE ? 8 : 7)
 adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
 {
     constexpr bool SAMPLE = MODE != SEG_RECOMPUTE;          // receptor sums, sort inputs
