@@ -269,7 +269,7 @@ def measure_batched(args, stream, cfg=None):
             # the autotuner's choice of launch shape and sort interval, timed fresh here
             from paper_0912_3223_gb300.autotune import autotune_with_sort
             shape, every, tried = autotune_with_sort(
-                sim, shapes=[(512, 1, 2), (256, 1, 2), (128, 1, 2), (256, 2, 1)],
+                sim, shapes=[(512, 1, 2), (256, 1, 2), (128, 1, 2), (256, 1, 1), (256, 2, 1)],
                 sort_intervals=(30, 60, 90), use_cache=False, reps=1)
             tuned = {"launch": list(shape), "sort_every": every,
                      "ms_per_run_tried": {k: round(v, 2) for k, v in tried.items()}}
