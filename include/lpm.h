@@ -431,15 +431,17 @@ lpm_status lpm_adjoint(lpm_ctx *ctx, const double *receptors, int R, double band
  * trajectory (16 B per particle and step, from the first release step of each block of
  * 128 particles on, plus 16 B per particle) when that is at most max_bytes and leaves
  * 8 GiB of device memory free; the backward then reads the states back in reverse. With
- * one scenario and sorting on (lpm_set_sort > 0, the default) the trajectory is kept in
- * 64-step segments over the particles re-sorted by weather cell at each segment start
- * (about the same size); otherwise in release order.
+ * sorting on (lpm_set_sort > 0, the default) the trajectory is kept in 64-step segments
+ * over the particles re-sorted at each segment start (about the same size): by weather
+ * cell for one scenario, by scenario and then cell tile for several; with sorting off in
+ * release order.
  * Otherwise, and always with max_bytes = 0, it keeps a checkpoint every 64 steps (16 B per
  * particle each) and the backward recomputes each 64-step segment from its checkpoint:
- * with one scenario and sorting on, the segments in the same cell order into a scratch of
- * two segments' states (2 x 16 B per particle and step of the widest segment, taken only
- * when it fits in free device memory with 8 GiB spare; one segment is recomputed while the
- * other is swept), else each particle's segment in release order. All forms give the same gradients up to the order of the FP64 sums. Default
+ * with sorting on, the segments in the same sorted order into a scratch of two segments'
+ * states (2 x 16 B per particle and step of the widest segment, taken only when it fits in
+ * free device memory with 8 GiB spare; one segment is recomputed while the other is
+ * swept), else each particle's segment in release order. All forms give the same
+ * gradients up to the order of the FP64 sums and of the per-segment FP32 partial sums. Default
  * 128 GiB. Drops the held forward. An allocation that fails falls back to checkpoints (no
  * error). lpm_adjoint_storage: *trajectory = 1 when the last receptor forward kept the
  * trajectory, *bytes = device bytes held for the adjoint's states (trajectory, or

@@ -6,13 +6,14 @@
 // transposed Jacobian of each step and accumulating the parameter partials; events
 // (deposition, exit) are frozen; sums over particles are reduced in FP64. The backward
 // needs the forward's states, kept in one of three forms:
-//  - trajectory, cell-sorted (one scenario, sorting on): CK-step segments over the
-//    particles re-sorted by weather cell between segments, every state stored;
-//  - trajectory in release order (several scenarios, or sorting off): every state stored,
-//    one thread per particle over the whole horizon;
+//  - trajectory, sorted (sorting on): CK-step segments over the particles re-sorted
+//    between segments (by weather cell; several scenarios: by scenario, then cell tile),
+//    every state stored;
+//  - trajectory in release order (sorting off): every state stored, one thread per
+//    particle over the whole horizon;
 //  - checkpoints every CK steps when the trajectory does not fit: each CK-step segment is
 //    recomputed from its checkpoint (same keyed draws and FP32 arithmetic, so the same
-//    path and events) before it is swept.
+//    path and events) before it is swept, in the sorted segments or in release order.
 #include <mutex>
 
 #include "lpm_advance.cuh"
@@ -213,14 +214,17 @@ struct Adjoint {
 
 // One step of the reverse sweep: the receptor term of the state Xa after step k (when k
 // is a sample step and not the step that ended the run), then mu <- J_k^T mu with the
-// Jacobian of step k at the state X before it (fold = the step's reflection sign).
+// Jacobian of step k at the state X before it (fold = the step's reflection sign). The
+// receptor weights dL/dC / n_s come from s_w, or from wg (the particle's scenario's row of
+// A.w) for a particle whose scenario is not its block's.
 template <bool KHG, class LEV>
 __device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParams &A,
                                              const LEV &LV, const ScenDev &sc,
                                              const float4 *s_rec, const float *s_w,
                                              unsigned long long gid, int sp, float m0, float mq,
                                              float sig_h_uniform, float sq2dt, int k, float4 X,
-                                             float fold, float4 Xa, bool sample, Adjoint &J)
+                                             float fold, float4 Xa, bool sample, Adjoint &J,
+                                             const double *wg = nullptr)
 {
     if (sample) {
         const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
@@ -236,7 +240,7 @@ __device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParam
             if (d1 > A.cut2 && d2 > A.cut2) continue;
             const float e1 = A.norm * expf(-d1 * A.inv2s2);
             const float e2 = A.norm * expf(-d2 * A.inv2s2);
-            const float wr = s_w[r];
+            const float wr = wg ? (float)(wg[r] * (double)A.inv_ns) : s_w[r];
             const float c1 = -wr * m * A.inv_s2;
             J.mu0 += c1 * (e1 + e2) * dx;
             J.mu1 += c1 * (e1 + e2) * dy;
@@ -466,29 +470,51 @@ static size_t adj_smem_backward(const StepParams &P, const AdjParams &A)
 }
 
 // ---------------------------------------------------------------------------------
-// Sorted trajectory form (one scenario): one launch per CK-step segment over the
-// particles alive at its start in weather-cell order, then its releases; between
-// segments the survivors are re-sorted by cell (lpm_sort.cu). The states of a segment are
-// stored row by row in that order; the backward sweeps the segments in reverse and hands
-// dL/dX from one segment to the previous one through G.mu, indexed by home slot.
+// Sorted form: one launch per CK-step segment over the particles alive at its start in
+// weather-cell order (with several scenarios: by scenario, then cell tile), then its
+// releases; between segments the survivors are re-sorted (lpm_sort.cu). The states of a
+// segment are stored row by row in that order; the backward sweeps the segments in
+// reverse and hands dL/dX from one segment to the previous one through G.mu, indexed by
+// home slot. A block keeps the receptor sums and gradients of one scenario (its first
+// entry's) in shared memory; entries of another scenario, at a scenario boundary of the
+// sorted order, add theirs to the global sums directly.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ bool seg_entry(const AdjSeg &G, const ScenDev &sc, long long e,
-                                          bool from_a, unsigned int live, long long &home)
+template <bool MULTI>
+__device__ __forceinline__ bool seg_entry(const StepParams &P, const AdjSeg &G, long long e,
+                                          bool from_a, unsigned int live, long long &home,
+                                          int &scen)
 {
     if (from_a) {
-        if (e >= (long long)live) { home = sc.first_slot; return false; }
+        if (e >= (long long)live) {
+            scen = 0;
+            home = P.scen[0].first_slot;
+            return false;
+        }
         home = G.ord[e];
+        scen = MULTI ? scen_of(P, home) : 0;
         return true;
     }
     const Tile t = G.tiles[G.b_first + (blockIdx.x - G.tiles_a)];
     const bool ok = (int)threadIdx.x < t.count;
+    scen = MULTI ? t.scen : 0;
     home = t.first + (ok ? threadIdx.x : 0);
     return ok;
 }
 
+// The block's scenario: that of its first entry (a sorted block starts below the live
+// count, or the launch returned before).
+template <bool MULTI>
+__device__ __forceinline__ int seg_block_scen(const StepParams &P, const AdjSeg &G, bool from_a)
+{
+    if (!MULTI) return 0;
+    if (from_a) return scen_of(P, G.ord[(long long)blockIdx.x * ADJ_BLOCK]);
+    return G.tiles[G.b_first + (blockIdx.x - G.tiles_a)].scen;
+}
+
 // 8 blocks per SM (64 registers) for the trajectory form; 7 (72 registers, no spills) for
-// the checkpoint form's forward and recomputation, measured 2 % faster there
-template <int MODE>
+// the checkpoint form's forward and recomputation, measured 2 % faster there. MULTI:
+// entries of several scenarios (else all of scenario 0).
+template <int MODE, bool MULTI>
 __global__ void __launch_bounds__(ADJ_BLOCK, MODE == SEG_STORE ? 8 : 7)
 adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
 {
@@ -508,11 +534,13 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
             s_C[r] = 0.0;
         }
     __syncthreads();
-    const ScenDev sc = P.scen[0];
+    const int bs = SAMPLE ? seg_block_scen<MULTI>(P, G, from_a) : 0;
     const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
     const long long e = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
     long long home;
-    if (seg_entry(G, sc, e, from_a, live, home)) {
+    int scen;
+    if (seg_entry<MULTI>(P, G, e, from_a, live, home, scen)) {
+        const ScenDev sc = P.scen[scen];
         const unsigned long long gid = (unsigned long long)(sc.id0 + (home - sc.first_slot));
         const int sp = (int)release_step_of(sc, home);
         const float m0 = __ldg(P.m0 + sc.m0_off + (sp - sc.rel_first));
@@ -547,7 +575,8 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
                     const float d1 = h2 + dz * dz, d2 = h2 + dzi * dzi;
                     if (d1 > A.cut2 && d2 > A.cut2) continue;
                     const float Gk = A.norm * (expf(-d1 * A.inv2s2) + expf(-d2 * A.inv2s2));
-                    atomicAdd(&s_C[r], (double)(m * Gk));
+                    if (scen == bs) atomicAdd(&s_C[r], (double)(m * Gk));
+                    else atomicAdd(A.C + (long long)scen * A.R + r, (double)(m * Gk));
                 }
             }
         }
@@ -563,11 +592,11 @@ adj_forward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     if (SAMPLE) {
         __syncthreads();
         for (int r = threadIdx.x; r < A.R; r += ADJ_BLOCK)
-            if (s_C[r] != 0.0) atomicAdd(A.C + r, s_C[r]);
+            if (s_C[r] != 0.0) atomicAdd(A.C + (long long)bs * A.R + r, s_C[r]);
     }
 }
 
-template <bool KHG>
+template <bool KHG, bool MULTI>
 __global__ void __launch_bounds__(ADJ_BLOCK, 5)
 adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
 {
@@ -581,14 +610,18 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
     unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_w + A.R);   // [n_lut]
     const Levels LV = load_levels(P, s_lut);
-    const Tile tile0{0, 0, 0};
-    load_receptors(A, tile0, s_rec, s_w, s_g, s_gq);
-    const ScenDev sc = P.scen[0];
+    Tile tb{0, 0, 0};
+    tb.scen = seg_block_scen<MULTI>(P, G, from_a);
+    load_receptors(A, tb, s_rec, s_w, s_g, s_gq);
     const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
     const float sq2dt = sqrtf(2.0f * P.k_scale * P.dt);
     const long long e = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
     long long home;
-    const bool valid = seg_entry(G, sc, e, from_a, live, home);
+    int scen;
+    const bool valid = seg_entry<MULTI>(P, G, e, from_a, live, home, scen);
+    const ScenDev sc = P.scen[scen];
+    // receptor weights of another scenario than the block's come from global memory
+    const double *wg = MULTI && scen != tb.scen ? A.w + (long long)scen * A.R : nullptr;
     const unsigned long long gid = (unsigned long long)(sc.id0 + (home - sc.first_slot));
     const int sp = (int)release_step_of(sc, home);
     const int tix = sc.m0_off + (sp - sc.rel_first);
@@ -618,7 +651,7 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
         if (!act) continue;
         const bool sample = (k + 1) % A.every == 0 && !(ev && k == kn - 1);
         reverse_step<KHG>(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
-                     X.w, Xa, sample, J);
+                     X.w, Xa, sample, J, wg);
         Xa = X;
     }
     // released earlier: hand mu to the previous segment; released here: mu is the
@@ -627,7 +660,18 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
         if (valid) G.mu[home] = make_float4(J.mu0, J.mu1, J.mu2, 0.f);
         J.mu0 = J.mu1 = J.mu2 = 0.f;
     }
-    reduce_gradient(A, tile0, J, valid, qidx, s_g, s_gq);
+    if (MULTI && valid && scen != tb.scen) {
+        // another scenario than the block's: its partials straight into its gradient
+        double *Gs = A.grad + (long long)scen * A.ng;
+        atomicAdd(Gs + 0, (double)J.mu0);
+        atomicAdd(Gs + 1, (double)J.mu1);
+        atomicAdd(Gs + 2, (double)J.mu2);
+        atomicAdd(Gs + 3 + A.nq + 0, (double)J.gsk);
+        atomicAdd(Gs + 3 + A.nq + 1, (double)J.gbu);
+        atomicAdd(Gs + 3 + A.nq + 2, (double)J.gbv);
+        if (J.gq != 0.f) atomicAdd(Gs + 3 + qidx, (double)J.gq);
+    }
+    reduce_gradient(A, tb, J, valid && scen == tb.scen, qidx, s_g, s_gq);
 }
 
 // The kernels need a few KB of shared memory per block: ask for a small carve-out so the
@@ -641,11 +685,18 @@ static void adj_set_carveout()
     cudaFuncSetAttribute(adj_backward_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_backward_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     cudaFuncSetAttribute(adj_backward_traj_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_forward_seg_kernel<SEG_STORE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_forward_seg_kernel<SEG_CKPT>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_forward_seg_kernel<SEG_RECOMPUTE>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_backward_seg_kernel<false>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    cudaFuncSetAttribute(adj_backward_seg_kernel<true>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    const void *seg[] = {
+        (const void *)adj_forward_seg_kernel<SEG_STORE, false>,
+        (const void *)adj_forward_seg_kernel<SEG_CKPT, false>,
+        (const void *)adj_forward_seg_kernel<SEG_RECOMPUTE, false>,
+        (const void *)adj_forward_seg_kernel<SEG_STORE, true>,
+        (const void *)adj_forward_seg_kernel<SEG_CKPT, true>,
+        (const void *)adj_forward_seg_kernel<SEG_RECOMPUTE, true>,
+        (const void *)adj_backward_seg_kernel<false, false>,
+        (const void *)adj_backward_seg_kernel<true, false>,
+        (const void *)adj_backward_seg_kernel<false, true>,
+        (const void *)adj_backward_seg_kernel<true, true>};
+    for (const void *f : seg) cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     (void)cudaGetLastError();
 }
 
@@ -661,14 +712,17 @@ cudaError_t launch_adj_forward_seg(cudaStream_t s, const StepParams &P, const Ad
     if (n_blocks <= 0) return cudaSuccess;
     adj_prefer_l1();
     const size_t sm = adj_smem_forward(P, A);
+    const bool multi = P.n_scen > 1;
+#define LPM_SEG_FWD(M)                                                                   \
+    (multi ? adj_forward_seg_kernel<M, true><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G)     \
+           : adj_forward_seg_kernel<M, false><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G))
     switch (mode) {
-    case SEG_STORE: adj_forward_seg_kernel<SEG_STORE><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G); break;
-    case SEG_CKPT: adj_forward_seg_kernel<SEG_CKPT><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G); break;
-    case SEG_RECOMPUTE:
-        adj_forward_seg_kernel<SEG_RECOMPUTE><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G);
-        break;
+    case SEG_STORE: LPM_SEG_FWD(SEG_STORE); break;
+    case SEG_CKPT: LPM_SEG_FWD(SEG_CKPT); break;
+    case SEG_RECOMPUTE: LPM_SEG_FWD(SEG_RECOMPUTE); break;
     default: return cudaErrorInvalidValue;
     }
+#undef LPM_SEG_FWD
     return cudaGetLastError();
 }
 
@@ -677,10 +731,16 @@ cudaError_t launch_adj_backward_seg(cudaStream_t s, const StepParams &P, const A
 {
     if (n_blocks <= 0) return cudaSuccess;
     adj_prefer_l1();
-    if (P.khpair)
-        adj_backward_seg_kernel<true><<<n_blocks, ADJ_BLOCK, adj_smem_backward(P, A), s>>>(P, A, G);
+    const size_t sm = adj_smem_backward(P, A);
+    const bool multi = P.n_scen > 1;
+    if (P.khpair && multi)
+        adj_backward_seg_kernel<true, true><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G);
+    else if (P.khpair)
+        adj_backward_seg_kernel<true, false><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G);
+    else if (multi)
+        adj_backward_seg_kernel<false, true><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G);
     else
-        adj_backward_seg_kernel<false><<<n_blocks, ADJ_BLOCK, adj_smem_backward(P, A), s>>>(P, A, G);
+        adj_backward_seg_kernel<false, false><<<n_blocks, ADJ_BLOCK, sm, s>>>(P, A, G);
     return cudaGetLastError();
 }
 

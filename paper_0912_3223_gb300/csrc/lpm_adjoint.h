@@ -48,11 +48,11 @@ struct AdjParams {
     const short *qi;                  // emission-series index of each release step
 };
 
-// One CK-step segment [k_lo, k_hi) of the sorted trajectory form (one scenario). Entries
-// [0, tiles_a * ADJ_BLOCK) are the particles alive at k_lo in weather-cell order (the first
-// *live valid: home slot ord[i], state sorted[i]); then come the release tiles
-// tiles[b_first, ...) of the segment at their home slots. Entry e of block b is
-// b * ADJ_BLOCK + lane.
+// One CK-step segment [k_lo, k_hi) of the sorted form. Entries [0, tiles_a * ADJ_BLOCK)
+// are the particles alive at k_lo in weather-cell order (several scenarios: by scenario,
+// then cell tile), the first *live valid (home slot ord[i], state sorted[i]); then come
+// the release tiles tiles[b_first, ...) of the segment, scenario by scenario, at their
+// home slots. Entry e of block b is b * ADJ_BLOCK + lane.
 struct AdjSeg {
     int k_lo, k_hi;
     const unsigned int *live;

@@ -167,9 +167,9 @@ struct lpm_ctx {
     size_t traj_need = 0;
     size_t adj_store_max = (size_t)128 << 30;   // bytes; 0 keeps checkpoints only
     bool adj_traj = false;                      // storage of the held forward
-    // sorted trajectory form (one scenario, sorting on): CK-step segments over the
-    // particles in weather-cell order, with the adjoint's own sort buffers (the run's sort
-    // state is not touched)
+    // sorted form (sorting on): CK-step segments over the particles in weather-cell order
+    // (several scenarios: scenario, then cell tile), with the adjoint's own sort buffers (the
+    // run's sort state is not touched)
     struct AdjSorted {
         std::vector<Tile> tiles;                // release tiles grouped by segment
         std::vector<int> seg_tile;              // [n_seg + 1] first release tile of a segment
@@ -1926,10 +1926,10 @@ int adj_nq(const lpm_ctx *c)
     return (int)nq;
 }
 
-// Segments of the sorted form (one scenario): segment s covers steps [s CK, (s+1) CK); its
-// entries are blocks over the particles released before s CK (a bound of those alive) and
-// the tiles of the particles released within it; its trajectory rows and end states are
-// laid out back to back.
+// Segments of the sorted form: segment s covers steps [s CK, (s+1) CK); its entries are
+// blocks over the particles of every scenario released before s CK (a bound of those
+// alive) and the tiles, scenario by scenario, of the particles released within it; its
+// trajectory rows and end states are laid out back to back.
 lpm_status adj_plan_segments(lpm_ctx *c)
 {
     lpm_ctx::AdjSorted &S = c->as;
@@ -1942,18 +1942,22 @@ lpm_status adj_plan_segments(lpm_ctx *c)
     S.foff.assign((size_t)n_seg + 1, 0);
     S.ckoff.assign((size_t)n_seg + 1, 0);
     S.max_width = 0;
-    const ScenHost &h = c->scen[0];
     long long off = 0, foff = 0, ckoff = 0;
     for (int s = 0; s < n_seg; ++s) {
         S.seg_tile[(size_t)s] = (int)S.tiles.size();
-        const long long a = released_before(h, (long long)s * CK);
-        const long long b = released_before(h, (long long)(s + 1) * CK);
-        for (long long p = a; p < b; p += ADJ_BLOCK) {
-            Tile t;
-            t.scen = 0;
-            t.first = h.first_slot + p;
-            t.count = (int)std::min<long long>(ADJ_BLOCK, b - p);
-            S.tiles.push_back(t);
+        long long a = 0;
+        for (size_t q = 0; q < c->scen.size(); ++q) {
+            const ScenHost &h = c->scen[q];
+            const long long a_q = released_before(h, (long long)s * CK);
+            const long long b_q = released_before(h, (long long)(s + 1) * CK);
+            a += a_q;
+            for (long long p = a_q; p < b_q; p += ADJ_BLOCK) {
+                Tile t;
+                t.scen = (int)q;
+                t.first = h.first_slot + p;
+                t.count = (int)std::min<long long>(ADJ_BLOCK, b_q - p);
+                S.tiles.push_back(t);
+            }
         }
         S.tiles_a[(size_t)s] = s ? (int)((a + ADJ_BLOCK - 1) / ADJ_BLOCK) : 0;
         const long long width =
@@ -1980,13 +1984,21 @@ lpm_status adj_plan_segments(lpm_ctx *c)
     return LPM_OK;
 }
 
+// Sort keys of the adjoint's segments: cells for one scenario; with several, scenario and
+// cell tile, so that each scenario's particles stay together (blocks of one scenario keep
+// their receptor sums and gradients in shared memory).
+int adj_key_scen(const lpm_ctx *c)
+{
+    return c->scen.size() > 1 ? (int)c->scen.size() : 0;
+}
+
 // The sorted form's own buffers (allocates whatever is still missing).
 lpm_status adj_sorted_buffers(lpm_ctx *c)
 {
     lpm_ctx::AdjSorted &S = c->as;
     const size_t ns = std::max<size_t>(1, (size_t)c->n_slots_used);
     const size_t nseg = S.tiles_a.size();
-    const size_t nb = (size_t)sort_key_range(c->cfg.nx, c->cfg.ny, c->cfg.nz) + 1;
+    const size_t nb = (size_t)sort_dead_key(c->cfg.nx, c->cfg.ny, c->cfg.nz, adj_key_scen(c)) + 1;
     auto need = [&](auto *&p, size_t bytes) -> cudaError_t {
         return p ? cudaSuccess : cudaMalloc(&p, bytes);
     };
@@ -2059,6 +2071,7 @@ lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &
             in.T = ADJ_BLOCK;
             in.w_a = in.w_b = nullptr;
             in.keys_ready = false;
+            in.key_scen = adj_key_scen(c);
             SortBuffers out;
             out.state_out = S.st[cur ^ 1];
             out.pidx_out = S.ord + (size_t)(s + 1) * std::max<size_t>(1, (size_t)c->n_slots_used);
@@ -2276,14 +2289,12 @@ lpm_status adj_prepare(lpm_ctx *c, const double *rec, int R, double bandwidth, i
         LPM_CUDA(c, cudaMemcpy(c->d_traj_tile, tt.data(), tt.size() * sizeof(longlong2),
                                cudaMemcpyHostToDevice));
         c->traj_need = rows;
-        if (g.n_scenarios == 1) {
-            lpm_status pst = adj_plan_segments(c);
-            if (pst != LPM_OK) return pst;
-        }
+        lpm_status pst = adj_plan_segments(c);
+        if (pst != LPM_OK) return pst;
         c->adj_tiles_valid = true;
     }
     if (!reuse) {
-        const bool want_sorted = g.n_scenarios == 1 && c->sort_every > 0;
+        const bool want_sorted = c->sort_every > 0;
         const lpm_ctx::AdjSorted &S = c->as;
         bool scratch = false;
         lpm_status sst =

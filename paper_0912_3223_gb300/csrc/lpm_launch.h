@@ -66,6 +66,8 @@ struct SortSource {
     int b_first, n_b, T;
     const float *w_a, *w_b;       // Langevin w' (moved with the particles), or nullptr
     bool keys_ready;              // keys and histogram already written (fused key pass)
+    int key_scen;                 // 0: cell keys; n > 0: keys (scenario, cell tile) over n
+                                  // scenarios, scenario-major (sort_dead_key)
 };
 
 struct SortBuffers {
@@ -93,6 +95,15 @@ __host__ __device__ inline long long sort_key_range(int nx, int ny, int nz)
 }
 
 constexpr unsigned int KEY_NONE_U = 0xffffffffu;     // sort input that is no particle
+
+// Key of the particles that left the working set (the last key of a sort): after the cell
+// keys, or after key_scen scenarios' tile keys (scenario s, tile t: s * tiles + t, one
+// key per tile of 2^(2 SORT_TILE_BITS + SORT_TILE_ZBITS) cells).
+__host__ __device__ inline long long sort_dead_key(int nx, int ny, int nz, int key_scen)
+{
+    const long long r = sort_key_range(nx, ny, nz);
+    return key_scen > 0 ? (long long)key_scen * (r >> (2 * SORT_TILE_BITS + SORT_TILE_ZBITS)) : r;
+}
 
 // Key of cell (ix, jy, kz): its tile, then its place in the tile.
 __device__ __forceinline__ unsigned int cell_key(const StepParams &P, int ix, int jy, int kz)

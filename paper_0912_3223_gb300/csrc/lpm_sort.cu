@@ -48,8 +48,8 @@ __device__ __forceinline__ bool sort_input(const SortSource &S, long long i, uns
     return true;
 }
 
-// Key = weather cell (cell_key order) of an active particle;
-// dead_key for the rest.
+// Key = weather cell (cell_key order) of an active particle, or with S.key_scen its
+// scenario and cell tile (scenario-major); dead_key for the rest.
 __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                                  const unsigned int *__restrict__ meta, long long n_max,
                                  unsigned int *__restrict__ keys, unsigned int *__restrict__ hist,
@@ -80,6 +80,11 @@ __global__ void sort_keys_kernel(const StepParams P, const SortSource S,
                     axis(s.y, P.y0, P.inv_dy, P.ny, jy, b);
                     level(P, LV, s.z, kz, c);
                     key = cell_key(P, ix, jy, kz);
+                    if (S.key_scen > 0) {
+                        constexpr int TBITS = 2 * SORT_TILE_BITS + SORT_TILE_ZBITS;
+                        const unsigned int n_tiles = (unsigned int)(sort_key_range(P.nx, P.ny, P.nz) >> TBITS);
+                        key = (unsigned int)scen_of(P, home) * n_tiles + (key >> TBITS);
+                    }
                 } else {
                     key = dead_key;
                 }
@@ -270,8 +275,8 @@ static unsigned int grid_for(long long n, int block)
 cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &in,
                         const SortBuffers &B)
 {
-    // keys 0..dead_key-1 are cells, dead_key the dead particles
-    const unsigned int dead_key = (unsigned int)sort_key_range(P.nx, P.ny, P.nz);
+    // keys 0..dead_key-1 are cells (or scenarios' cell tiles), dead_key the dead particles
+    const unsigned int dead_key = (unsigned int)sort_dead_key(P.nx, P.ny, P.nz, in.key_scen);
     const long long nb = (long long)dead_key + 1;
     cudaError_t e;
     if (!in.keys_ready && (e = cudaMemsetAsync(B.hist, 0, nb * sizeof(unsigned int), s)) != cudaSuccess)

@@ -43,4 +43,13 @@ def run_cases() -> dict:
                 lpm.lpm_set_adjoint_storage(sim.ctx, storage)
             out[f"{name}_C"] = lpm.lpm_receptors(sim.ctx, 1, rec, 200.0, 18)
             out[f"{name}_grad"] = lpm.lpm_adjoint(sim.ctx, rec, 200.0, 18, w, 24)
+    # a batch of candidates: segments sorted by scenario, then cell tile
+    cand, _, _ = li.make_cfg4(n_candidates=3, n_per=2000, n_steps=200, n_obs=500)
+    wb = np.linspace(-1.0, 1.0, cand.n_scenarios * rec.shape[0]).reshape(cand.n_scenarios, -1)
+    for name, storage in [("adj_batch_traj", None), ("adj_batch_ckpt", 0)]:
+        with Sim(cand) as sim:
+            if storage is not None:
+                lpm.lpm_set_adjoint_storage(sim.ctx, storage)
+            out[f"{name}_C"] = lpm.lpm_receptors(sim.ctx, cand.n_scenarios, rec, 200.0, 18)
+            out[f"{name}_grad"] = lpm.lpm_adjoint(sim.ctx, rec, 200.0, 18, wb, 24)
     return out

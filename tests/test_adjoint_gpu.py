@@ -202,8 +202,8 @@ def test_trajectory_and_checkpoint_storage_agree():
     to the order of the FP64 sums: the trajectory re-sorted by weather cell every 64 steps
     (one scenario, sorting on), the trajectory in release order (sorting off, or a batch of
     candidates), and 64-step checkpoints with recomputation (a limit below the trajectory's
-    size), in cell-sorted segments (one scenario, sorting on) or in release order. One
-    scenario with deposition and exits, and a batch of three."""
+    size), in sorted segments (sorting on) or in release order. One scenario with
+    deposition and exits, and a batch of three (sorted by scenario, then cell tile)."""
     from paper_0912_3223_gb300 import Sim, lpm
     cfg, rec = _realistic(n=5000, steps=400)
     cand, _, _ = li.make_cfg4(n_candidates=3, n_per=3000, n_steps=300, n_obs=1000)
@@ -227,12 +227,10 @@ def test_trajectory_and_checkpoint_storage_agree():
         # same order of the per-particle FP32 sums: agree to the order of the FP64 sums
         C0, g0 = out["release order"]
         assert np.abs(g0).max() > 0
-        # one scenario: the sorted checkpoint form sweeps the same entries in the same order
-        # as the sorted trajectory; a batch has no sorted form, so both limits give the
-        # release-order checkpoints
+        # the sorted checkpoint form sweeps the same entries in the same order as the
+        # sorted trajectory (for a batch: sorted by scenario, then cell tile)
         pairs = [("checkpoints in release order", "release order")]
-        pairs += [(f, "trajectory" if c.n_scenarios == 1 else "release order")
-                  for f in ("checkpoints", "checkpoints (limit)")]
+        pairs += [(f, "trajectory") for f in ("checkpoints", "checkpoints (limit)")]
         for form, base in pairs:
             C1, g1 = out[form]
             Cb, gb = out[base]
