@@ -647,7 +647,7 @@ advance_kernel(const StepParams P, const Ranges R, int n_tiles, unsigned int *qu
         }
 
         // ---- sort keys for the sort that follows (its inputs: A slots, then B lanes) ----
-        if (!MIXED && R.keys) {
+        if (R.keys) {
             const unsigned int dead_key = (unsigned int)sort_key_range(P.nx, P.ny, P.nz);
             const int lane = threadIdx.x & 31;
 #pragma unroll
