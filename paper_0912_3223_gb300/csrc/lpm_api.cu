@@ -123,6 +123,8 @@ struct lpm_ctx {
     unsigned int *d_hist = nullptr, *d_bsums = nullptr, *d_live = nullptr;   // d_live = meta[4]
     float4 *d_grave = nullptr;              // particles found dead at a sort (read-back only)
     unsigned int *d_grave_n = nullptr;
+    unsigned int *d_grave_home = nullptr;   // home slot of each entry of d_grave
+    bool slot_map_stale = false;            // d_slot_of predates the last sort
 
     // decay chain (species 1..: daughters)
     int n_species = 1;
@@ -634,6 +636,7 @@ lpm_status ensure_sort_buffers(lpm_ctx *c, size_t keys_need)
         LPM_CUDA(c, cudaMemsetAsync(c->d_live, 0, 4 * sizeof(unsigned int), c->stream));
     }
     LPM_CUDA(c, need(c->d_grave, n * sizeof(float4)));
+    LPM_CUDA(c, need(c->d_grave_home, n * sizeof(unsigned int)));
     if (!c->d_grave_n) {
         LPM_CUDA(c, need(c->d_grave_n, sizeof(unsigned int)));
         LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
@@ -650,10 +653,27 @@ lpm_status ensure_sort_buffers(lpm_ctx *c, size_t keys_need)
     return LPM_OK;
 }
 
+// The slot map (home slot -> sorted slot, dead entry or home) for the read-back paths: the
+// sorts leave it to be rebuilt here, from the sorted and dead sets, when it is asked for.
+lpm_status ensure_slot_map(lpm_ctx *c)
+{
+    if (!c->slot_map_stale || !c->d_slot_of) return LPM_OK;
+    LPM_CUDA(c, launch_slot_map(c->stream, c->d_pidx[c->cur], c->d_live, c->d_grave_home,
+                                c->d_grave_n, c->d_slot_of, (long long)c->cfg.max_particles,
+                                c->d_err));
+    c->n_launches++;
+    c->slot_map_stale = false;
+    return LPM_OK;
+}
+
 // Empties the sorted set: every particle back to its home slot.
 lpm_status clear_sort_state(lpm_ctx *c, bool move_back)
 {
     if (c->d_sorted[0]) {
+        if (move_back && c->sorted_upto > 0) {
+            lpm_status st = ensure_slot_map(c);
+            if (st != LPM_OK) return st;
+        }
         if (move_back && c->sorted_upto > 0)
             LPM_CUDA(c, launch_unsort(c->stream, c->d_state, c->d_sorted[c->cur], c->d_slot_of,
                                       c->d_grave, c->n_slots_used,
@@ -667,6 +687,7 @@ lpm_status clear_sort_state(lpm_ctx *c, bool move_back)
         LPM_CUDA(c, cudaMemsetAsync(c->d_grave_n, 0, sizeof(unsigned int), c->stream));
         c->n_launches++;
     }
+    c->slot_map_stale = false;               // every slot is home again
     c->sorted_upto = 0;
     c->cur = 0;
     return LPM_OK;
@@ -823,7 +844,7 @@ void lpm_destroy(lpm_ctx *c)
                     c->d_zlut, c->d_mq, c->d_qi, c->d_ckpt, c->d_rec, c->d_rC, c->d_rw,
                     c->d_rgrad, c->d_adj_tiles, c->d_sorted[0], c->d_sorted[1], c->d_pidx[0],
                     c->d_pidx[1], c->d_slot_of, c->d_keys, c->d_hist, c->d_bsums, c->d_live,
-                    c->d_grave, c->d_grave_n, c->d_dose, c->d_bl, c->d_blpair,
+                    c->d_grave, c->d_grave_n, c->d_grave_home, c->d_dose, c->d_bl, c->d_blpair,
                     c->d_sp_conc, c->d_sp_dep, c->d_w_home, c->d_w_sorted[0],
                     c->d_w_sorted[1], c->d_traj, c->d_fin, c->d_traj_tile, c->d_conv,
                     c->d_rbin_off, c->d_rbin_idx, c->d_mode_sc};
@@ -1205,7 +1226,8 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             SortBuffers out{};
             out.state_out = c->d_sorted[1 - cur];
             out.pidx_out = c->d_pidx[1 - cur];
-            out.slot_of = c->d_slot_of;
+            out.slot_of = nullptr;               // rebuilt on request (ensure_slot_map)
+            out.grave_home = c->d_grave_home;
             out.keys = c->d_keys;
             out.hist = c->d_hist;
             out.block_sums = c->d_bsums;
@@ -1216,6 +1238,7 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             out.cap = c->cfg.max_particles;
             out.err = c->d_err;
             LPM_CUDA(c, launch_sort(s, P, in, out));
+            c->slot_map_stale = true;
             cur = 1 - cur;
             upto = sg.k;
             kernels += keys_ready ? 6 : 7;
@@ -1429,6 +1452,7 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
             LPM_CUDA(c, cudaEventRecord(e0, c->stream));
         }
         LPM_CUDA(c, cudaGraphLaunch(gr->exec, c->stream));
+        c->slot_map_stale = true;                // (when the graph holds sorts)
         if (e1) LPM_CUDA(c, cudaEventRecord(e1, c->stream));
         c->n_launches += gr->kernels;
         c->n_adv_launches++;
@@ -1520,6 +1544,10 @@ lpm_status lpm_budget(lpm_ctx *c, int scenario, double out[8])
     StepParams P;
     fill_params(c, P);
     const bool sorted = c->sorted_upto > 0;
+    {
+        const lpm_status sm = ensure_slot_map(c);
+        if (sm != LPM_OK) return sm;
+    }
     LPM_CUDA(c, launch_budget(c->stream, P, c->d_state, c->n_slots_used, c->d_slot_of,
                               c->d_sorted[c->cur], c->d_pidx[c->cur], sorted ? c->d_live : nullptr,
                               sorted ? released_total(c, c->sorted_upto) : 0, (int)c->k));
@@ -1564,6 +1592,10 @@ lpm_status lpm_particles(lpm_ctx *c, int64_t first, int64_t count, float *xyz, u
         // slot order: gather from the home slots, the sorted set and the dead array into
         // the spare sorted buffer (free until the next sort)
         float4 *tmp = c->d_sorted[1 - c->cur];
+        {
+            const lpm_status sm = ensure_slot_map(c);
+            if (sm != LPM_OK) return sm;
+        }
         LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_sorted[c->cur], c->d_slot_of,
                                   c->d_grave, first, count, tmp));
         LPM_CUDA(c, cudaMemcpyAsync(h.data(), tmp, h.size() * sizeof(float4),
@@ -1675,6 +1707,10 @@ lpm_status lpm_particle_velocity(lpm_ctx *c, int64_t first, int64_t count, float
     if (st != LPM_OK) return st;
     if (count == 0) return LPM_OK;
     float *tmp = c->d_w_sorted[1 - c->cur];  // free until the next sort
+    {
+        const lpm_status sm = ensure_slot_map(c);
+        if (sm != LPM_OK) return sm;
+    }
     LPM_CUDA(c, launch_gather_w(c->stream, c->d_w_home, c->d_w_sorted[c->cur], c->d_slot_of,
                                 first, count, tmp));
     LPM_CUDA(c, cudaMemcpyAsync(w, tmp, (size_t)count * sizeof(float), cudaMemcpyDeviceToHost,
@@ -2009,7 +2045,6 @@ lpm_status adj_sorted_buffers(lpm_ctx *c)
     LPM_CUDA(c, need(S.hist, nb * sizeof(unsigned int)));
     LPM_CUDA(c, need(S.bsums, ((nb + 1023) / 1024) * sizeof(unsigned int)));
     LPM_CUDA(c, need(S.meta, 4 * sizeof(unsigned int)));
-    LPM_CUDA(c, need(S.slot_of, ns * sizeof(unsigned int)));
     LPM_CUDA(c, need(S.grave_n, sizeof(unsigned int)));
     for (float4 **p : {&S.st[0], &S.st[1], &S.home, &S.mu, &S.grave})
         LPM_CUDA(c, need(*p, ns * sizeof(float4)));
@@ -2076,7 +2111,8 @@ lpm_status adj_forward_sorted(lpm_ctx *c, const StepParams &P, const AdjParams &
             SortBuffers out;
             out.state_out = S.st[cur ^ 1];
             out.pidx_out = S.ord + (size_t)(s + 1) * std::max<size_t>(1, (size_t)c->n_slots_used);
-            out.slot_of = S.slot_of;
+            out.slot_of = nullptr;                // the adjoint reads no slot map
+            out.grave_home = nullptr;
             out.keys = S.keys;
             out.hist = S.hist;
             out.block_sums = S.bsums;
@@ -2578,6 +2614,10 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
     const size_t sb = (size_t)c->n_slots_used * sizeof(float4);
     if (c->d_sorted[0]) {
         float4 *tmp = c->d_sorted[1 - c->cur];
+        {
+            const lpm_status sm = ensure_slot_map(c);
+            if (sm != LPM_OK) return sm;
+        }
         LPM_CUDA(c, launch_gather(c->stream, c->d_state, c->d_sorted[c->cur], c->d_slot_of,
                                   c->d_grave, 0, c->n_slots_used, tmp));
         LPM_CUDA(c, cudaMemcpyAsync(o, tmp, sb, cudaMemcpyDeviceToHost, c->stream));
@@ -2610,6 +2650,10 @@ lpm_status lpm_save(lpm_ctx *c, void *buf, size_t *n)
         // the spare sorted-w buffer is free here (the gather of the particles above used
         // the spare state buffer)
         float *tmp = c->d_w_sorted[1 - c->cur];
+        {
+            const lpm_status sm = ensure_slot_map(c);
+            if (sm != LPM_OK) return sm;
+        }
         LPM_CUDA(c, launch_gather_w(c->stream, c->d_w_home, c->d_w_sorted[c->cur], c->d_slot_of, 0,
                                     c->n_slots_used, tmp));
         LPM_CUDA(c, cudaMemcpyAsync(o, tmp, (size_t)c->n_slots_used * sizeof(float),

@@ -73,7 +73,9 @@ struct SortSource {
 struct SortBuffers {
     float4 *state_out;
     unsigned int *pidx_out;
-    unsigned int *slot_of;        // per home slot: sorted slot, GRAVE | index, or SLOT_HOME
+    unsigned int *slot_of;        // per home slot: sorted slot, GRAVE | index, or SLOT_HOME;
+                                  // nullptr: not kept (launch_slot_map rebuilds it)
+    unsigned int *grave_home;     // home slot of each dead-particle entry, or nullptr
     unsigned int *keys, *hist, *block_sums, *meta;
     float4 *grave;
     unsigned int *grave_count;
@@ -121,6 +123,12 @@ __device__ __forceinline__ unsigned int cell_key(const StepParams &P, int ix, in
 constexpr unsigned int SLOT_HOME = 0xffffffffu;   // slot_of: the particle is at its home slot
 constexpr unsigned int SLOT_GRAVE = 0x80000000u;  // slot_of flag: index into the dead array
 
+// slot_of for every home slot [0, n_slots): SLOT_HOME, then the sorted slot of each of the
+// meta[0] live particles (pidx: sorted slot -> home slot) and GRAVE | index of each of the
+// *grave_n dead ones (grave_home: index -> home slot).
+cudaError_t launch_slot_map(cudaStream_t s, const unsigned int *pidx, const unsigned int *meta,
+                            const unsigned int *grave_home, const unsigned int *grave_n,
+                            unsigned int *slot_of, long long n_slots, unsigned int *err);
 cudaError_t launch_release(cudaStream_t s, float4 *state, long long first_slot, long long count,
                            long long part_first, long long n_total, int rel_first, int rel_len,
                            float sx, float sy, float sz);

@@ -205,14 +205,34 @@ __global__ void sort_scatter_kernel(const SortSource S, const unsigned int *__re
                 continue;
             if (key == dead_key) {
                 B.grave[dst] = src[slot];
-                B.slot_of[home] = SLOT_GRAVE | dst;
+                if (B.grave_home) B.grave_home[dst] = home;
+                if (B.slot_of) B.slot_of[home] = SLOT_GRAVE | dst;
             } else {
                 B.state_out[dst] = src[slot];
                 B.pidx_out[dst] = home;
-                B.slot_of[home] = dst;
+                if (B.slot_of) B.slot_of[home] = dst;
                 if (B.w_out) B.w_out[dst] = (i < (long long)live_old ? S.w_a : S.w_b)[slot];
             }
         }
+    }
+}
+
+// The slot map from the sorted and dead sets (the sorts do not keep it up to date: its
+// random 4-byte writes cost 1.7 % of the ensemble's run; it is only read back on request).
+__global__ void slot_map_kernel(const unsigned int *__restrict__ pidx,
+                                const unsigned int *__restrict__ meta,
+                                const unsigned int *__restrict__ grave_home,
+                                const unsigned int *__restrict__ grave_n,
+                                unsigned int *__restrict__ slot_of, long long n_slots,
+                                unsigned int *err)
+{
+    const long long live = meta[0], n = live + (long long)*grave_n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const bool is_live = i < live;
+        const unsigned int h = is_live ? pidx[i] : grave_home[i - live];
+        if (!LPM_IN_BOUNDS(err, (long long)h < n_slots)) continue;
+        slot_of[h] = is_live ? (unsigned int)i : (SLOT_GRAVE | (unsigned int)(i - live));
     }
 }
 
@@ -296,6 +316,18 @@ cudaError_t launch_sort(cudaStream_t s, const StepParams &P, const SortSource &i
     if (n_max > 0)
         sort_scatter_kernel<<<grid_for(n_max, 256), 256, 0, s>>>(in, B.meta, n_max, B.keys,
                                                                  dead_key, B.hist, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_map(cudaStream_t s, const unsigned int *pidx, const unsigned int *meta,
+                            const unsigned int *grave_home, const unsigned int *grave_n,
+                            unsigned int *slot_of, long long n_slots, unsigned int *err)
+{
+    if (n_slots <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(slot_of, 0xff, (size_t)n_slots * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    slot_map_kernel<<<grid_for(n_slots, 256), 256, 0, s>>>(pidx, meta, grave_home, grave_n,
+                                                           slot_of, n_slots, err);
     return cudaGetLastError();
 }
 
