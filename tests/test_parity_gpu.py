@@ -372,16 +372,28 @@ def test_partitioned_contexts_sum_to_single_run():
 @pytest.mark.parametrize("every", [7, 60])
 def test_sorting_particles_by_cell_changes_nothing(every):
     """Re-ordering the released particles by weather cell is a layout change only: the
-    particles (read back in index order), grids and counters are bit-identical."""
+    particles (read back in index order), grids, counters and budget are bit-identical. The
+    read-backs go through the slot map the sorts leave stale; reading back in mid-run,
+    sorting on and reading back again rebuilds it twice."""
     cfg = li.make_cfg1(n_particles=7001, n_steps=300, n_hours=4)
     from paper_0912_3223_gb300 import Sim
     ref = run_gpu(cfg, sort_every=0)
+    with Sim(cfg, sort_every=0) as sim:
+        sim.step(137)
+        mid_ref = sim.particles()
+        mid_budget_ref = sim.budget()
     with Sim(cfg, sort_every=every) as sim:
         sim.step(137)
+        mid = sim.particles()
+        mid_budget = sim.budget()
         sim.step(cfg.n_steps - 137)
         xyz, tag = sim.particles()
         part = sim.particles(1234, 99)
         cfix, dfix, ctr, _ = sim.fixed_state()
+        budget = sim.budget()
+    assert np.array_equal(mid[0], mid_ref[0]) and np.array_equal(mid[1], mid_ref[1])
+    assert np.array_equal(mid_budget, mid_budget_ref)
+    assert np.array_equal(budget, ref["budget"])
     assert np.array_equal(xyz.astype(np.float64), ref["pos"]) and np.array_equal(tag, ref["tag"])
     assert np.array_equal(part[0], xyz[1234:1333]) and np.array_equal(part[1], tag[1234:1333])
     assert np.array_equal(cfix, ref["conc_fixed"]) and np.array_equal(dfix, ref["dep_fixed"])
