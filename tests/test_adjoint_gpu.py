@@ -357,6 +357,48 @@ def test_batched_adjoint_matches_oracle_per_scenario():
     assert seen >= 1
 
 
+def test_sorted_batch_with_many_small_scenarios_matches_release_order_and_oracle():
+    """Twenty-four candidates of 230 particles: blocks of 128 sorted entries straddle the
+    scenario boundaries, so many entries add their receptor sums and gradients to their own
+    scenario's global sums instead of their block's. The sorted trajectory and checkpoint
+    forms against the release-order trajectory (source partials to the order of the FP64
+    sums; the others to FP32 rounding of the per-segment sums), and two scenarios against
+    the oracle."""
+    from paper_0912_3223_gb300 import Sim, lpm
+    cand, _, _ = li.make_cfg4(n_candidates=24, n_per=230, n_steps=260, n_obs=500)
+    rec = li.make_receptors()
+    rng = np.random.default_rng(11)
+    w = rng.normal(0.0, 1.0, (cand.n_scenarios, rec.shape[0]))
+    out = {}
+    for form, limit, sort in [("sorted", 1 << 37, 60), ("sorted checkpoints", 0, 60),
+                              ("release order", 1 << 37, 0)]:
+        with Sim(cand) as sim:
+            lpm.lpm_set_sort(sim.ctx, sort)
+            lpm.lpm_set_adjoint_storage(sim.ctx, limit)
+            C = lpm.lpm_receptors(sim.ctx, cand.n_scenarios, rec, SIGMA, 18)
+            g = lpm.lpm_adjoint(sim.ctx, rec, SIGMA, 18, w, 24)
+        out[form] = (C, g)
+    C0, g0 = out["release order"]
+    assert np.abs(C0).max() > 0 and np.abs(g0).max() > 0
+    for form in ("sorted", "sorted checkpoints"):
+        C1, g1 = out[form]
+        np.testing.assert_allclose(C1, C0, rtol=1e-12, atol=1e-15 * np.abs(C0).max(), err_msg=form)
+        np.testing.assert_allclose(g1[:, :3], g0[:, :3], rtol=1e-9,
+                                   atol=1e-12 * np.abs(g0[:, :3]).max(), err_msg=form)
+        np.testing.assert_allclose(g1[:, 3:], g0[:, 3:], rtol=0,
+                                   atol=2e-5 * np.abs(g0[:, 3:]).max(), err_msg=form)
+    np.testing.assert_allclose(out["sorted checkpoints"][1], out["sorted"][1], rtol=1e-9,
+                               atol=1e-12 * np.abs(out["sorted"][1]).max())
+    g = out["sorted"][1]
+    hit = [s for s in range(cand.n_scenarios) if np.abs(g0[s, :3]).max() > 0]
+    assert len(hit) >= 2
+    for s in hit[:2]:
+        ref = oracle.adjoint(cand, rec, SIGMA, 18, w[s], scenario=s)
+        np.testing.assert_allclose(g[s, :3], ref[:3], atol=0.01 * np.abs(ref[:3]).max())
+        np.testing.assert_allclose(g[s, 3:27], ref[3:27], rtol=1e-3,
+                                   atol=1e-6 * np.abs(ref[3:27]).max())
+
+
 def test_partitioned_receptors_and_adjoint_sum_to_single_context():
     """Three contexts holding disjoint particle ranges of one release, run one after
     another on this GPU as the ranks of a partitioned run would: their receptor sums, and
