@@ -308,6 +308,14 @@ def test_error_paths():
         with pytest.raises(lpm.LpmError) as e:
             lpm.lpm_step(ctx, 1)
         assert e.value.status == lpm.LPM_E_STATE
+        lpm.lpm_step(ctx, 0)                        # an empty step is a no-op
+        # empty, oversized and ill-formed releases are refused and change nothing
+        for args in [(0, [1.0], 3600.0, 0, 20), (cfg.n_particles + 1, [1.0], 3600.0, 0, 20),
+                     (100, [1.0], 3600.0, 5, 5), (100, [1.0], 3600.0, 0, 21),
+                     (100, [-1.0], 3600.0, 0, 20), (100, [1.0], 0.0, 0, 20)]:
+            with pytest.raises(lpm.LpmError) as e:
+                lpm.lpm_release(ctx, 0, *args)
+            assert e.value.status == lpm.LPM_E_INVALID, args
         lpm.lpm_release(ctx, 0, 100, [1.0], 3600.0, 0, 20)
         with pytest.raises(lpm.LpmError) as e:
             lpm.lpm_release(ctx, 0, 100, [1.0], 3600.0, 0, 20)
