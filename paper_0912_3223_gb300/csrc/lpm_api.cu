@@ -1280,15 +1280,11 @@ lpm_status run_segments(lpm_ctx *c, const StepParams &P, const std::vector<Segme
             L.ranges.hist = c->d_hist;
             keys_ready = true;
         }
-        if (batched) {
-            // persistent grid over an atomic tile queue
-            LPM_CUDA(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), s));
-            L.queue = c->d_queue;
-            L.grid = (unsigned)std::max(1, std::min(n_tiles, occ_blocks * c->sm_count));
-        } else {
-            L.queue = nullptr;
-            L.grid = (unsigned)n_tiles;
-        }
+        // persistent grid over an atomic tile queue (the plain run: measured +0.8 % against
+        // a grid of all tiles, each block loading the level table once for many tiles)
+        LPM_CUDA(c, cudaMemsetAsync(c->d_queue, 0, sizeof(unsigned int), s));
+        L.queue = c->d_queue;
+        L.grid = (unsigned)std::max(1, std::min(n_tiles, occ_blocks * c->sm_count));
         const bool timed = direct && c->profiling;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (timed) {
@@ -1398,7 +1394,13 @@ lpm_status lpm_step(lpm_ctx *c, int64_t n)
     // ---- run ------------------------------------------------------------------------------
     if (!batched) {
         long long kernels = 0;
-        st = run_segments(c, P, plan, c->stream, c->sorted_upto, c->cur, kernels, true, 1);
+        const bool ext_opts = P.dose_every > 0 || P.blpair != nullptr || P.n_species > 1 ||
+                              P.langevin;
+        const int occ_blocks = std::max(1, advance_occupancy(
+            c->block, c->ppt, c->occ, false, ext_opts ? 1 : P.n_modes > 0 ? 2 : 0,
+            adv_dyn_smem(P.n_lut)));
+        st = run_segments(c, P, plan, c->stream, c->sorted_upto, c->cur, kernels, true,
+                          occ_blocks);
         c->n_launches += kernels;
         if (st != LPM_OK) return st;
     } else {
