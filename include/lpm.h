@@ -275,8 +275,10 @@ lpm_status lpm_set_launch(lpm_ctx *ctx, int block, int particles_per_thread, int
  * the threads of a warp gather from neighbouring cells (a layout change only: every
  * particle keeps its id, hence its random numbers, and all results are bit-identical).
  * 0 turns it off; default 60. A change moves every particle back to its home slot first.
- * Needs about 56 bytes of extra device memory per particle slot, allocated at the first
- * sort. */
+ * Needs about 60 bytes of extra device memory per particle slot, allocated at the first
+ * sort. The sorts do not keep the map from home slots to sorted places: the first
+ * lpm_particles, lpm_particle_velocity, lpm_budget or lpm_save after a sort rebuilds it
+ * (one pass over the slots). */
 lpm_status lpm_set_sort(lpm_ctx *ctx, int every_steps);
 
 /*
