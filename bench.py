@@ -44,12 +44,12 @@ OPS_PER_PARTICLE_STEP_LOW = 350
 # DRAM traffic per advance launch from an ncu capture of two mid-run 60-step launches
 # (hours 10-11 of the realistic workload, persistent grid of 2 blocks per SM; read + write,
 # mean of the two), valid while the kernel sources hash to the values below.
-ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.370304 + 0.00128) + (23.753984 + 0.017664)) * 1e6
-ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "158f9384", "lpm_device.cuh": "c030129e"}
+ADVANCE_TRAFFIC_BYTES = 0.5 * ((22.372096 + 0.0) + (23.778816 + 0.01792)) * 1e6
+ADVANCE_TRAFFIC_SOURCES = {"lpm_advance.cuh": "fdaaeb52", "lpm_device.cuh": "c030129e"}
 # Busiest hardware units of the same capture (% of peak, mean of the two launches): the
 # L1 data pipe carrying the weather gathers, and the warp-instruction issue slots.
-ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (80.09 + 80.19) / 100.0,
-                         "issue_slots": 0.5 * (76.70 + 76.53) / 100.0}
+ADVANCE_BUSIEST_UNITS = {"l1tex_data_pipe": 0.5 * (82.04 + 82.09) / 100.0,
+                         "issue_slots": 0.5 * (74.43 + 74.28) / 100.0}
 LANES_PER_SM = 128          # 4 sub-partitions x 32 lanes issue one op per clock
 
 
