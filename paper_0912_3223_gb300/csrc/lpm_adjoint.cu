@@ -96,6 +96,39 @@ __device__ __forceinline__ void sample_met_grad(const StepParams &P, const LEV &
     (void)sig_h_uniform;
 }
 
+// The time parts of step k (time pair h0 / h1, fraction, t_k) as step_time computes them,
+// packed for a per-block table: the steps of a segment are the same for every particle.
+__device__ __forceinline__ float4 step_time_parts(const StepParams &P, int k)
+{
+    const StepTime T = step_time(P, nullptr, k);
+    return make_float4(__int_as_float(T.ts.h0), T.ts.f, T.tk, __int_as_float(T.ts.h1));
+}
+
+// step_time(P, wind_offset, k) from the packed time parts of step k (the same values: the
+// parts are step_time's own, the pointers and the offset follow its expressions).
+__device__ __forceinline__ StepTime step_time_from(const StepParams &P, const float2 *wind_offset,
+                                                   float4 a, int k)
+{
+    StepTime T;
+    T.k = k;
+    T.tk = a.z;
+    T.ts.h0 = __float_as_int(a.x);
+    T.ts.h1 = __float_as_int(a.w);
+    T.ts.f = a.y;
+    T.pair = P.pair + (long long)T.ts.h0 * P.slab * 2;
+    T.khp = P.khpair ? P.khpair + (long long)T.ts.h0 * P.slab : nullptr;
+    T.blp = P.blpair ? P.blpair + (long long)T.ts.h0 * P.nx * P.ny * 2 : nullptr;
+    T.du = P.bias_u;
+    T.dv = P.bias_v;
+    if (wind_offset) {
+        const float2 o0 = __ldg(wind_offset + T.ts.h0);
+        const float2 o1 = __ldg(wind_offset + T.ts.h1);
+        T.du += fmaf(T.ts.f, o1.x - o0.x, o0.x);
+        T.dv += fmaf(T.ts.f, o1.y - o0.y, o0.y);
+    }
+    return T;
+}
+
 __device__ __forceinline__ long long release_step_of(const ScenDev &sc, long long slot)
 {
     const long long p = sc.part_first + (slot - sc.first_slot);
@@ -224,7 +257,8 @@ __device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParam
                                              unsigned long long gid, int sp, float m0, float mq,
                                              float sig_h_uniform, float sq2dt, int k, float4 X,
                                              float fold, float4 Xa, bool sample, Adjoint &J,
-                                             const double *wg = nullptr)
+                                             const double *wg = nullptr,
+                                             const float4 *ta = nullptr, int ta_k0 = 0)
 {
     if (sample) {
         const float decay = expf(-P.lambda * (float)(k + 1 - sp) * P.dt);
@@ -248,7 +282,8 @@ __device__ __forceinline__ void reverse_step(const StepParams &P, const AdjParam
             J.gq += wr * mq * decay * (e1 + e2);
         }
     }
-    const StepTime T = step_time(P, sc.wind_offset, k);
+    const StepTime T = ta ? step_time_from(P, sc.wind_offset, ta[k - ta_k0], k)
+                          : step_time(P, sc.wind_offset, k);
     float val[5], g[5][3];
     sample_met_grad<KHG>(P, LV, T, sig_h_uniform, X.x, X.y, X.z, val, g);
     const U4 w = philox4x32_10((uint32_t)gid, (uint32_t)(gid >> 32), (uint32_t)k, 0u,
@@ -610,9 +645,14 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
     float *s_w = reinterpret_cast<float *>(s_gq + A.nq);      // [R]
     unsigned char *s_lut = reinterpret_cast<unsigned char *>(s_w + A.R);   // [n_lut]
     const Levels LV = load_levels(P, s_lut);
+    // the segment's step times, once per block (measured: backward 1 % faster; the forward
+    // kernels, at more blocks per SM, lost more to the extra shared memory than they gained)
+    __shared__ float4 s_ta[CK];
+    for (int i = threadIdx.x; i < G.k_hi - G.k_lo; i += ADJ_BLOCK)
+        s_ta[i] = step_time_parts(P, G.k_lo + i);
     Tile tb{0, 0, 0};
     tb.scen = seg_block_scen<MULTI>(P, G, from_a);
-    load_receptors(A, tb, s_rec, s_w, s_g, s_gq);
+    load_receptors(A, tb, s_rec, s_w, s_g, s_gq);     // (ends with a barrier)
     const float sig_h_uniform = sqrtf(2.0f * P.k_scale * fmaxf(P.kh_uniform, 0.0f) * P.dt);
     const float sq2dt = sqrtf(2.0f * P.k_scale * P.dt);
     const long long e = (long long)blockIdx.x * ADJ_BLOCK + threadIdx.x;
@@ -651,7 +691,7 @@ adj_backward_seg_kernel(const StepParams P, const AdjParams A, const AdjSeg G)
         if (!act) continue;
         const bool sample = (k + 1) % A.every == 0 && !(ev && k == kn - 1);
         reverse_step<KHG>(P, A, LV, sc, s_rec, s_w, gid, sp, m0, mq, sig_h_uniform, sq2dt, k, X,
-                     X.w, Xa, sample, J, wg);
+                     X.w, Xa, sample, J, wg, s_ta, G.k_lo);
         Xa = X;
     }
     // released earlier: hand mu to the previous segment; released here: mu is the
